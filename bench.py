@@ -1,0 +1,388 @@
+#!/usr/bin/env python3
+"""ENUF-DPD force evaluations per second on one polyelectrolyte system.
+
+Workload (synthetic, seeded): 81000 DPD beads in a periodic box L = 30
+(density 3); ten chains of 50 beads with harmonic bonds (K = 4, r0 = 0) and
+charge fraction 0.5 (q = -1), 250 +1 counterions, 1:1 salt at 0.1 bead
+fraction (8100 beads), neutral solvent; a_ij = 25, gamma = 4.5, sigma = 3,
+dt = 0.04, lambda = 0.65; electrostatics alpha = 0.975, r_c = 3,
+lambda_e = 0.25 (beta = 4), Gamma = 13.87, p = 4, sigma_s = 2, M = 48
+(n = 96). One step = one modified velocity-Verlet step of Table 2 with a full
+force evaluation: DPD pair + bond forces, real-space erfc + Slater pairs, and
+the ENUF reciprocal sum (bin, spread, pruned FFT, convolution, inverse FFT,
+gather), plus FP64 totals. The headline is the FP32 path (float arithmetic,
+FP64 table and reductions); the FP64 path runs the same workload beside it.
+
+L2 (129 MB) is flushed between timed steps by writing a 256 MB buffer; each
+step is timed with CUDA events on the plan's stream.
+
+--impl reference times the FP64 CPU oracle (the only reference there is) on
+the host cores, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "ENUF-DPD force evals/sec at N=81k (FP32 vs FP64, same GPU); p50/p99 latency"
+UNIT = "force evals/s"
+WORKLOAD = ("polyelectrolyte DPD, N=81000, L=30, 10x50-bead chains f=0.5, 1:1 salt 0.1, "
+            "Nq=8600, alpha=0.975, r_c=3, beta=4, Gamma=13.87, p=4, M=48 (n=96); "
+            "one Table-2 step with full ENUF+DPD forces per unit")
+DPD_SAMPLE_STRIDE = 40
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out = ""
+        return False
+
+    def summary(self):
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = max(smax, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_bytes(info, nq, N, esz):
+    """Algorithmic DRAM bytes of one launch of each kernel group:
+    every array the stage must read or write, once."""
+    n, nc = info.n, info.n_c
+    K, nc1 = 2 * nc + 1, nc + 1
+    n3 = n ** 3
+    c = 2 * esz
+    bead = 4 * esz * 2 + 4          # sorted (x,y,z,q) + (frac, index) + packed base
+    return {
+        "spread": nq * bead + n3 * esz,
+        "gather": nq * bead + 3 * n3 * esz + nq * 6 * esz,
+        "fft": (n3 * esz + n * nc1 * n * c) + (n * nc1 * n * c + nc1 * K * n * c)
+        + (nc1 * K * n * c + 3 * n * nc1 * K * c + nc1 * K * K * (8 + 8 + esz))
+        + (3 * n * nc1 * K * c + 3 * n * n * nc1 * c) + (3 * n * n * nc1 * c + 3 * n3 * esz),
+        "real": nq * bead + nq * 6 * esz,
+        "dpd": N * (8 * esz) + N * 3 * esz + N * 4,
+    }
+
+
+def run_ours(args, rank, world, dist):
+    import torch
+
+    from paper_1303_4523_gb300 import enuf
+    from paper_1303_4523_gb300 import workloads as W
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    s = W.polyelectrolyte()
+    dp = W.dpd_params(5)
+    P = dict(L=s.L, M=s.M, **s.params)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    peaks, peak_kind = _peaks()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def run_prec(prec, steps, warmup, timing):
+        plan = enuf.Plan(enuf.make_params(prec=prec, **P), s.N)
+        sysm = enuf.DpdSystem(plan, dp["a"], dp["gamma"], dp["sigma"], dp["dt"], s.pos, s.vel, s.types, s.q,
+                              s.bonds, lambda_vv=dp["lambda_vv"], K_bond=dp["K_bond"], r0_bond=dp["r0_bond"],
+                              seed=dp["seed"])
+        plan.enable_timing(timing)
+        for _ in range(warmup):
+            sysm.step(1)
+        torch.cuda.synchronize()
+        st = plan.stream
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        stage_ms = {k: [] for k in ("spread", "fft", "gather", "real", "dpd", "cell", "bin")}
+        barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(dev) as clk:
+            t0 = time.perf_counter()
+            for k in range(steps):
+                with torch.cuda.stream(st):
+                    flush.fill_(float(k))
+                ev[k][0].record(st)
+                sysm.step(1)
+                ev[k][1].record(st)
+                if timing:
+                    for name in stage_ms:
+                        stage_ms[name].append(plan.stage_time(name))
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+        barrier()
+        per = [a.elapsed_time(b) for a, b in ev]
+        E = sysm.step(0, want_energy=True)
+        launches = plan.launches()
+        sysm.close()
+        plan.close()
+        return per, wall, clk.summary(), stage_ms, E, launches
+
+    per32, wall32, clk32, stage32, E32, launches = run_prec("fp32", args.steps, args.warmup, True)
+    steps64 = max(3, min(args.steps, 50))
+    per64, wall64, clk64, stage64, E64, _ = run_prec("fp64", steps64, args.warmup, False)
+
+    tot32 = sum(per32)
+    tot64 = sum(per64)
+    if dist is not None:
+        t = torch.tensor([tot32, tot64], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot32, tot64 = t.tolist()
+    ms32 = tot32 / args.steps
+    ms64 = tot64 / steps64
+
+    # end to end through the public API: host state in (pinned), one step, host state out
+    e2e = e2e_run(args, s, dp, P, torch, enuf)
+
+    # roofline of the dominant kernel (FP32 path)
+    plan = enuf.Plan(enuf.make_params(prec="fp32", **P), s.N)
+    info = plan.info
+    plan.close()
+    ab = algorithmic_bytes(info, s.n_charged, s.N, 4)
+    means = {k: (sum(v) / len(v) if v else 0.0) for k, v in stage32.items()}
+    single = {k: means[k] for k in ("spread", "gather", "real", "dpd")}
+    dom = max(single, key=single.get)
+    achieved = ab[dom] / (means[dom] * 1e-3) / 1e9 if means[dom] > 0 else 0.0
+    traffic = _profiled_traffic(dom)
+    roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
+            "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
+            "peak_kind": peak_kind, "stage_ms": {k: round(v, 5) for k, v in means.items()},
+            "stage_bytes": ab, "note": "working set ~35 MB < L2: L2 flushed between steps, intermediates L2-resident"}
+
+    srt = sorted(per32)
+    p50 = srt[len(srt) // 2]
+    p99 = srt[min(len(srt) - 1, int(math.ceil(0.99 * len(srt))) - 1)]
+    s64 = sorted(per64)
+    out = {
+        "metric": METRIC, "value": round(world * 1000.0 * args.steps / tot32, 2), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms32, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded polyelectrolyte box)",
+        "config": {"workload": WORKLOAD, "N": s.N, "n_charged": s.n_charged, "grid_n": info.n,
+                   "tile": info.tile, "l2": "flushed between steps (256 MB write)",
+                   "parallelism": f"replicas x{world}"},
+        "latency_ms": {"p50": round(p50, 5), "p99": round(p99, 5), "mean": round(ms32, 5)},
+        "fp64": {"value": round(world * 1000.0 * steps64 / tot64, 2), "ms_per_step": round(ms64, 5),
+                 "steps": steps64, "p50": round(s64[len(s64) // 2], 5),
+                 "p99": round(s64[min(len(s64) - 1, int(math.ceil(0.99 * len(s64))) - 1)], 5),
+                 "clocks": clk64},
+        "fp32_over_fp64": round(ms64 / ms32, 2),
+        "energies_fp32": [round(x, 6) for x in E32[:8]],
+        "energies_fp64": [round(x, 6) for x in E64[:8]],
+        "clocks": clk32,
+        "e2e": e2e,
+        "gpu_launches": launches * args.steps,
+        "launches_per_step": launches,
+        "roofline": roof,
+    }
+    return out
+
+
+def e2e_run(args, s, dp, P, torch, enuf):
+    """Same metric through the public API with HOST buffers: each step uploads
+    the state (pos, vel, F) from pinned memory, advances one step and reads the
+    state and energies back."""
+    plan = enuf.Plan(enuf.make_params(prec="fp32", **P), s.N)
+    sysm = enuf.DpdSystem(plan, dp["a"], dp["gamma"], dp["sigma"], dp["dt"], s.pos, s.vel, s.types, s.q, s.bonds,
+                          lambda_vv=dp["lambda_vv"], K_bond=dp["K_bond"], r0_bond=dp["r0_bond"], seed=dp["seed"])
+    pos = torch.empty((s.N, 3), dtype=torch.float32).pin_memory()
+    vel = torch.empty((s.N, 3), dtype=torch.float32).pin_memory()
+    F = torch.empty((s.N, 3), dtype=torch.float32).pin_memory()
+    step = sysm.get_state_into(pos, vel, F)
+    import ctypes as C
+    from paper_1303_4523_gb300.enuf import _check, _ptr, lib
+    steps = max(3, min(args.steps, 100))
+    for k in range(args.warmup + steps):
+        if k == args.warmup:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+        _check(lib.dpd_set_state(sysm.h, _ptr(pos), _ptr(vel), _ptr(F), step), plan.h)
+        sysm.step(1, want_energy=True)
+        step = sysm.get_state_into(pos, vel, F)
+    dt = time.perf_counter() - t0
+    sysm.close()
+    plan.close()
+    nb = s.N * 3 * 4 * 3
+    return {"value": round(steps / dt, 2), "unit": UNIT, "h2d_bytes_per_step": nb + 8,
+            "d2h_bytes_per_step": nb + 8 * 16, "ms_per_step": round(1000 * dt / steps, 4), "steps": steps}
+
+
+def _profiled_traffic(kernel):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, when it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return d.get(kernel)
+    except (OSError, ValueError):
+        return None
+
+
+def cpu_oracle_eval(s, dp, P, stride):
+    """One oracle force evaluation on the host: naive ENUF and real space on all
+    charged beads, DPD pair + bond forces on every stride-th bead. Returns
+    (seconds for the sample, seconds scaled to a full evaluation)."""
+    import oracle
+    Po = oracle.EwaldParams(**P)
+    Do = oracle.DpdParams(**dp)
+    sample = np.arange(0, s.N, stride, dtype=np.int32)
+    t0 = time.perf_counter()
+    oracle.recip_enuf(Po, s.pos, s.q)
+    t1 = time.perf_counter()
+    oracle.real_space(Po, s.pos, s.q)
+    t2 = time.perf_counter()
+    oracle.dpd_forces(Po, Do, s.pos, s.vel, s.types, s.bonds, step=1, sample=sample)
+    t3 = time.perf_counter()
+    full = (t1 - t0) + (t2 - t1) + (t3 - t2) * s.N / len(sample)
+    return t3 - t0, full
+
+
+def _cores():
+    try:
+        return int(os.environ.get("OMP_NUM_THREADS") or len(os.sched_getaffinity(0)))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def cpu_baseline():
+    from paper_1303_4523_gb300 import workloads as W
+    s = W.polyelectrolyte()
+    dp = W.dpd_params(5)
+    P = dict(L=s.L, M=s.M, **s.params)
+    samp, full = cpu_oracle_eval(s, dp, P, DPD_SAMPLE_STRIDE)
+    return {"value": round(1.0 / full, 5), "unit": UNIT, "cores": _cores(), "kind": "oracle",
+            "sample": f"naive ENUF + real space on all {s.n_charged} charged beads; DPD pair forces on "
+                      f"{len(range(0, s.N, DPD_SAMPLE_STRIDE))} of {s.N} beads, scaled x{DPD_SAMPLE_STRIDE}; "
+                      f"{samp:.2f} s measured, {full:.2f} s per full evaluation"}
+
+
+def run_reference(args):
+    from paper_1303_4523_gb300 import workloads as W
+    s = W.polyelectrolyte()
+    dp = W.dpd_params(5)
+    P = dict(L=s.L, M=s.M, **s.params)
+    budget = 150.0
+    for _ in range(max(0, min(args.warmup, 1))):
+        cpu_oracle_eval(s, dp, P, DPD_SAMPLE_STRIDE)
+    fulls, samples = [], []
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        samp, full = cpu_oracle_eval(s, dp, P, DPD_SAMPLE_STRIDE)
+        fulls.append(full)
+        samples.append(samp)
+        if time.perf_counter() - t0 > budget:
+            break
+    ms = 1000.0 * sum(fulls) / len(fulls)
+    value = 1000.0 / ms
+    srt = sorted(fulls)
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": 1,
+        "steps": len(fulls), "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded polyelectrolyte box)",
+        "config": {"workload": WORKLOAD, "N": s.N, "n_charged": s.n_charged, "parallelism": "host cores"},
+        "latency_ms": {"p50": round(1000 * srt[len(srt) // 2], 2), "p99": round(1000 * srt[-1], 2)},
+        "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": _cores(), "kind": "oracle",
+                         "sample": f"each step: naive ENUF + real space on all {s.n_charged} charged beads, "
+                                   f"DPD on 1/{DPD_SAMPLE_STRIDE} of the beads scaled to all {s.N}; "
+                                   f"{len(fulls)} of {args.steps} requested steps within {budget:.0f} s"},
+        "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)))
+        return
+
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        tdist.init_process_group("nccl")
+        dist = tdist
+    from paper_1303_4523_gb300 import build
+    if rank == 0:
+        build.build()
+    if dist is not None:
+        dist.barrier()
+    out = run_ours(args, rank, world, dist)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,218 @@
+/*
+ * enuf.h -- C ABI of the GB300-native ENUF-DPD hot path.
+ *
+ * Method: Wang, Laaksonen & Lu, "Implementation of non-uniform FFT based
+ * Ewald summation in Dissipative Particle Dynamics method" (arXiv 1303.4523).
+ * The library evaluates, for beads with charges q_i at positions r_i in a
+ * cubic periodic box of edge L (reduced DPD units, R_c = m = k_B T = 1):
+ *
+ *   E = E_real + E_recip + E_self + E_neutral                       (Eq. 16)
+ *   E_real  = kappa sum_{i<j, r<r_c} q_i q_j [erfc(alpha r) - (1 + beta r) e^{-2 beta r}] / r
+ *             (Eq. 31 with the Slater correction of Eq. 27, applied in real space only, Sec. 5)
+ *   E_recip = kappa/(2 pi L) sum_{k != 0, |k_t| <= n_c} e^{-(pi k)^2/(alpha L)^2}/k^2 |S(k)|^2
+ *             with S(k) from the transposed NFFT (Eq. 14, 18-20, Table 2 step 4(ii))
+ *   F_i     = -grad_i E_real + kappa (2 q_i/L^2) Im g_i,  g_i from the conjugated NFFT (Eq. 24-25)
+ *   E_self  = -kappa alpha/sqrt(pi) sum q_i^2,  E_neutral = -kappa pi Q^2 / (2 V alpha^2)
+ *
+ * and, for DPD systems, the pair forces of Eq. 2-7, harmonic bonds (Sec. 2)
+ * and the modified velocity-Verlet step of Table 2.
+ *
+ * Conventions for every entry point:
+ *  - Functions return an enuf_status; none aborts or exits. On failure the
+ *    plan's message is available from enuf_last_error().
+ *  - Arrays are dense, C order. Positions/forces/velocities are [n][3].
+ *    Floating arrays use double for ENUF_FP64 plans and float for ENUF_FP32
+ *    plans ("real" below). Positions may lie outside [0, L); they are
+ *    wrapped internally.
+ *  - "device" pointers are CUDA device memory on the plan's device; "host"
+ *    pointers are host memory (pinned memory makes copies faster). The caller
+ *    owns every array it passes; plans and systems own their workspace.
+ *  - Work is enqueued on the plan's stream. A call returns after enqueueing,
+ *    except when it must return host results (energies), in which case it
+ *    synchronises that stream.
+ */
+#ifndef ENUF_H
+#define ENUF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ENUF_OK = 0,
+    ENUF_ERR_INVALID = 1,     /* bad argument or parameter combination */
+    ENUF_ERR_OOM = 2,         /* device allocation failed */
+    ENUF_ERR_CUDA = 3,        /* a CUDA call failed (message has the CUDA error) */
+    ENUF_ERR_TIMEOUT = 4,     /* a bounded device wait ran out */
+    ENUF_ERR_UNSUPPORTED = 5  /* grid size / window combination not supported */
+} enuf_status;
+
+typedef enum {
+    ENUF_FP64 = 0,  /* every stage in double */
+    ENUF_FP32 = 1   /* spread, FFT, convolution, gather and pair forces in float;
+                       influence table, self/neutral terms and all energy and
+                       virial reductions (Kahan-compensated) in double */
+} enuf_precision;
+
+/* Parameters of one ENUF evaluation (Table 1; Sec. 5). */
+typedef struct {
+    double L;         /* cubic box edge */
+    double alpha;     /* Ewald splitting parameter (Eq. 16) */
+    double r_cut;     /* real-space cutoff r_c, 0 < r_c <= L/2 (Eq. 29) */
+    double beta;      /* R_c / lambda_e of the Slater density (Eq. 26-27); <= 0: point charges */
+    double kappa;     /* Coulomb prefactor 1/(4 pi eps0 eps_r) in reduced units */
+    int    M;         /* base grid per dimension, even, >= 4; n_c = M/2 - 1.
+                         0: M = 1.6 L rounded to the nearest even 2^a 3^b 5^c */
+    int    p;         /* NFFT window cutoff: 2p taps per dimension, 1 <= p <= 8 */
+    int    sigma_s;   /* oversampling factor; only 2 is supported (Sec. 5) */
+    int    kmask;     /* 0: cubic mode set |k_t| <= n_c; 1: spherical |k| <= n_c */
+    int    prec;      /* enuf_precision */
+    int    tile;      /* spreading tile edge in grid points; 0 = automatic */
+    int    reserved[6];
+} enuf_params;
+
+typedef struct enuf_plan_s* enuf_plan_t;
+
+/* Derived sizes of a plan. */
+typedef struct {
+    int    M, n, n_c;          /* base grid, oversampled grid n = sigma_s M, kept modes */
+    int    tile, n_tiles;      /* spreading tile edge and tile count */
+    int    n_max;              /* capacity in beads */
+    size_t device_bytes;       /* device memory the plan holds */
+} enuf_plan_info;
+
+/* Create a plan for systems of up to n_max beads with the given parameters
+ * (Table 2 step 4). cuda_stream is a cudaStream_t (NULL: the plan creates
+ * its own). Allocates the plan's device workspace and builds the FP64
+ * influence/deconvolution table on the host. Errors: ENUF_ERR_INVALID for
+ * n_max < 0, L <= 0, alpha <= 0, r_c outside (0, L/2], odd or too small M,
+ * p outside [1, 8], sigma_s != 2, kappa not finite; ENUF_ERR_UNSUPPORTED when
+ * no tile edge divides n; ENUF_ERR_OOM / ENUF_ERR_CUDA. *out is NULL on error. */
+enuf_status enuf_plan(const enuf_params* params, int n_max, void* cuda_stream, enuf_plan_t* out);
+
+/* Device bytes a plan with these parameters would hold (admission control). */
+enuf_status enuf_footprint(const enuf_params* params, int n_max, size_t* bytes);
+
+enuf_status enuf_get_info(enuf_plan_t plan, enuf_plan_info* info);
+
+/* Electrostatic energy and forces (Eq. 16-25; Table 2 step 4).
+ *   n      : number of beads, 0 <= n <= n_max
+ *   pos    : device real[n][3]
+ *   q      : device real[n]; beads with q = 0 take no part
+ *   F      : device real[n][3], OVERWRITTEN with F_real + F_recip (zero for q = 0)
+ *   E      : host double[4] = {E_real, E_recip, E_self + E_neutral, E_total}, or NULL
+ *   virial : host double[1] = -L dE/dL at fixed fractional coordinates, or NULL
+ * The call runs as one CUDA graph on the plan's stream (captured on first use
+ * and again whenever n or a pointer changes). With E and virial NULL it
+ * returns after enqueueing. */
+enuf_status enuf_energy_forces(enuf_plan_t plan, int n, const void* pos, const void* q,
+                               void* F, double* E, double* virial);
+
+/* Same, with HOST pos, q and F: the call copies the inputs to the device,
+ * evaluates, copies F back and synchronises. */
+enuf_status enuf_energy_forces_host(enuf_plan_t plan, int n, const void* pos, const void* q,
+                                    void* F, double* E, double* virial);
+
+/* Copy an internal buffer of the last evaluation to host memory (tests):
+ *   ENUF_BUF_GRID  : spread grid, real[n^3], index (z*n + y)*n + x        (Eq. 14, first half)
+ *   ENUF_BUF_FIELD : the three conjugated-NFFT fields, real[3][n^3]      (Eq. 25 before gather)
+ * bytes must equal the buffer size. Synchronises the plan's stream. */
+enum { ENUF_BUF_GRID = 0, ENUF_BUF_FIELD = 1 };
+enuf_status enuf_debug_buffer(enuf_plan_t plan, int which, void* host, size_t bytes);
+
+/* Kernel timing: when enabled, the next captured graph records CUDA events
+ * around the kernels of the given stage; enuf_stage_time() returns the
+ * device time of that stage in the last evaluation (ms). Stages: */
+enum { ENUF_STAGE_BIN = 0,      /* charged-bead binning (3 kernels) */
+       ENUF_STAGE_SPREAD = 1,   /* spreading kernel */
+       ENUF_STAGE_FFT = 2,      /* the five FFT passes incl. the fused convolution */
+       ENUF_STAGE_GATHER = 3,   /* gather kernel */
+       ENUF_STAGE_REAL = 4,     /* real-space electrostatics kernel */
+       ENUF_STAGE_DPD = 5,      /* DPD pair + bond kernel */
+       ENUF_STAGE_ALL = 6,      /* the whole evaluation / DPD step */
+       ENUF_STAGE_CELL = 7,     /* all-bead cell list (3 kernels) */
+       ENUF_NUM_STAGES = 8 };
+enuf_status enuf_enable_timing(enuf_plan_t plan, int on);
+enuf_status enuf_stage_time(enuf_plan_t plan, int stage, float* ms);
+/* Number of kernel launches one evaluation (or one DPD step) enqueues. */
+int enuf_launches_per_eval(enuf_plan_t plan);
+
+void enuf_destroy(enuf_plan_t plan);
+const char* enuf_status_string(enuf_status s);
+const char* enuf_last_error(enuf_plan_t plan);
+
+/* ------------------------------------------------------------------ */
+/* DPD systems (Eq. 2-7, Sec. 2 bonds, Table 2 integrator)              */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    int           ntypes;     /* number of bead types */
+    const double* a;          /* host double[ntypes][ntypes] conservative amplitudes a_ij (Eq. 3) */
+    double        gamma;      /* dissipation strength (Eq. 4) */
+    double        sigma;      /* noise amplitude (Eq. 5), sigma^2 = 2 gamma k_B T (Eq. 6) */
+    double        dt;         /* time step */
+    double        lambda_vv;  /* velocity-prediction parameter (Table 2 step 0) */
+    double        K_bond;     /* harmonic spring constant (Sec. 2) */
+    double        r0_bond;    /* equilibrium bond length */
+    uint64_t      seed;       /* key of the Philox4x32-10 stream of theta_ij (Eq. 5) */
+} dpd_params;
+
+typedef struct dpd_system_s* dpd_system_t;
+
+/* Create a device-resident DPD system on a plan (the plan's precision and
+ * box). pos, vel: HOST real[n][3]; type: host int[n] in [0, ntypes);
+ * q: host real[n]; bonds: host int[n_bonds][2] (may be NULL when n_bonds = 0).
+ * The system copies everything to the device, builds the per-bead bond list
+ * and evaluates the initial force at step 0. Requires L >= 3 (cell list of
+ * edge >= 1). The plan must outlive the system. */
+enuf_status dpd_create(enuf_plan_t plan, const dpd_params* params, int n, const void* pos,
+                       const void* vel, const int* type, const void* q, int n_bonds,
+                       const int* bonds, dpd_system_t* out);
+
+/* Advance nsteps steps of Table 2 (steps 0-6): predict v0, half kick, drift,
+ * DPD pair + bond forces (theta keyed by the new step number), electrostatics
+ * (real + ENUF reciprocal), half kick. E: host double[8] or NULL =
+ * {E_real, E_recip, E_self + E_neutral, E_elec, E_conservative, E_bond,
+ *  E_kinetic, virial_elec} of the last step (synchronises when non-NULL). */
+enuf_status dpd_step(dpd_system_t sys, int nsteps, double* E);
+
+/* Checkpoint / restart: copy the state to or from HOST real[n][3] arrays
+ * (any pointer may be NULL). The force F is part of the state because the
+ * next step's velocity prediction (Table 2 step 0) uses it. dpd_set_state
+ * with F = NULL recomputes the force of the new configuration at the given
+ * step (taking v0 = vel); with F given, set_state(get_state()) resumes the
+ * run exactly (the random stream is keyed by the step number). */
+enuf_status dpd_get_state(dpd_system_t sys, void* pos, void* vel, void* F, uint64_t* step);
+enuf_status dpd_set_state(dpd_system_t sys, const void* pos, const void* vel, const void* F, uint64_t step);
+/* Current total force (HOST real[n][3]). */
+enuf_status dpd_get_forces(dpd_system_t sys, void* F);
+/* Device pointers of the resident state (real[n][3] each; owned by the system). */
+enuf_status dpd_device_state(dpd_system_t sys, void** pos, void** vel, void** F);
+void dpd_destroy(dpd_system_t sys);
+
+/* ------------------------------------------------------------------ */
+/* Batches: many independent systems in one captured launch sequence    */
+/* ------------------------------------------------------------------ */
+
+typedef struct enuf_batch_s* enuf_batch_t;
+
+/* One plan per system (params[s], capacity n[s]); all systems share the
+ * given stream and are evaluated by one CUDA graph with one branch per
+ * system. */
+enuf_status enuf_batch_plan(int nsys, const enuf_params* params, const int* n, void* cuda_stream,
+                            enuf_batch_t* out);
+/* pos[s], q[s], F[s]: device pointers as in enuf_energy_forces, for n[s] beads.
+ * E: host double[nsys][4] or NULL (synchronises when non-NULL). */
+enuf_status enuf_batch_energy_forces(enuf_batch_t batch, const void* const* pos,
+                                     const void* const* q, void* const* F, double* E);
+/* Kernel launches in one replay of the batch graph. */
+int enuf_batch_launches(enuf_batch_t batch);
+void enuf_batch_destroy(enuf_batch_t batch);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

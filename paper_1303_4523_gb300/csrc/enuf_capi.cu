@@ -1,0 +1,900 @@
+// enuf_capi.cu -- host side of the C ABI declared in include/enuf.h: plan
+// construction (grid sizes, FP64 influence/deconvolution table, workspace),
+// CUDA-graph capture of one evaluation / one DPD step, DPD systems and batches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "enuf.h"
+#include "enuf_internal.h"
+
+using namespace enuf;
+
+namespace {
+
+constexpr int kMaxTiles = 32768;      // shared-memory histogram limit (128 KB)
+constexpr int kMaxSmem = 200 * 1024;  // dynamic shared memory the kernels may request
+constexpr int kSMs = 152;
+
+bool g_configured[2] = {false, false};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+bool smooth(int m) {
+    if (m <= 0) return false;
+    for (int f : {2, 3, 5})
+        while (m % f == 0) m /= f;
+    return m == 1;
+}
+
+// M = 1.6 L rounded to the nearest even 2^a 3^b 5^c integer (ties to the smaller).
+int grid_rule(double L) {
+    const double target = 1.6 * L;
+    int best = -1;
+    for (int m = 2; m < (int)(4 * target) + 8; m += 2) {
+        if (!smooth(m)) continue;
+        if (best < 0 || std::fabs(m - target) < std::fabs(best - target) - 1e-12) best = m;
+    }
+    return std::max(best, 8);
+}
+
+bool fft_radices(int n, FftPlanDev& fp) {
+    fp.n = n;
+    fp.nst = 0;
+    int m = n;
+    auto push = [&](int r) {
+        if (fp.nst >= 8) return false;
+        fp.rad[fp.nst++] = r;
+        m /= r;
+        return true;
+    };
+    while (m % 8 == 0) if (!push(8)) return false;
+    while (m % 4 == 0) if (!push(4)) return false;
+    while (m % 2 == 0) if (!push(2)) return false;
+    while (m % 3 == 0) if (!push(3)) return false;
+    while (m % 5 == 0) if (!push(5)) return false;
+    return m == 1;
+}
+
+int lines_for(int n, int nbuf, int esz, int budget, int cap) {
+    const int l = (budget - n * esz) / (nbuf * n * esz);
+    return std::max(1, std::min(cap, l));
+}
+
+}  // namespace
+
+struct enuf_plan_s {
+    enuf_params P{};
+    int n_max = 0;
+    int prec = ENUF_FP64;
+    size_t rsz = 8;  // bytes of one real
+    cudaStream_t stream = nullptr, aux = nullptr;
+    bool own_stream = false;
+    cudaEvent_t evFork = nullptr, evJoin = nullptr, evA = nullptr;
+    Geo g{};
+    FftShape fs{};
+    FftPlanDev fp{};
+    Work w{};
+    void* dmem = nullptr;
+    size_t dbytes = 0;
+    double* hE = nullptr;  // pinned [16]
+    cudaGraphExec_t gexec = nullptr;
+    int g_n = -1;
+    const void* g_pos = nullptr;
+    const void* g_q = nullptr;
+    void* g_F = nullptr;
+    bool g_timing = false;
+    Events ev{};
+    int launches = 0;
+    void* stage = nullptr;  // device staging for the host-buffer entry point
+    char err[512] = {0};
+};
+
+namespace {
+
+enuf_status fail(enuf_plan_t p, enuf_status s, const char* fmt, ...) {
+    if (p) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(p->err, sizeof(p->err), fmt, ap);
+        va_end(ap);
+    }
+    return s;
+}
+
+#define CU(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return fail(plan, ENUF_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                        __LINE__);                                                                \
+    } while (0)
+
+// Derive every size of a plan; no allocation. Returns the device bytes.
+enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* bytes) {
+    if (n_max < 0) return fail(plan, ENUF_ERR_INVALID, "n_max < 0");
+    if (!(P.L > 0) || !std::isfinite(P.L)) return fail(plan, ENUF_ERR_INVALID, "L must be > 0");
+    if (!(P.alpha > 0) || !std::isfinite(P.alpha)) return fail(plan, ENUF_ERR_INVALID, "alpha must be > 0");
+    if (!(P.r_cut > 0) || P.r_cut > 0.5 * P.L) return fail(plan, ENUF_ERR_INVALID, "r_cut must be in (0, L/2]");
+    if (!std::isfinite(P.kappa) || !std::isfinite(P.beta)) return fail(plan, ENUF_ERR_INVALID, "kappa/beta not finite");
+    if (P.sigma_s != 2) return fail(plan, ENUF_ERR_INVALID, "only sigma_s = 2 is supported");
+    if (P.p < 1 || P.p > 8) return fail(plan, ENUF_ERR_INVALID, "p must be in [1, 8]");
+    if (P.prec != ENUF_FP64 && P.prec != ENUF_FP32) return fail(plan, ENUF_ERR_INVALID, "bad precision");
+    if (P.kmask != 0 && P.kmask != 1) return fail(plan, ENUF_ERR_INVALID, "kmask must be 0 or 1");
+    const int M = P.M == 0 ? grid_rule(P.L) : P.M;
+    if (M < 4 || (M & 1)) return fail(plan, ENUF_ERR_INVALID, "M must be even and >= 4 (got %d)", M);
+    const int n = P.sigma_s * M;
+    if (n > 1024) return fail(plan, ENUF_ERR_UNSUPPORTED, "grid n = %d > 1024", n);
+    FftPlanDev fp{};
+    if (!fft_radices(n, fp)) return fail(plan, ENUF_ERR_UNSUPPORTED, "grid n = %d is not 2^a 3^b 5^c", n);
+    if (2 * P.p > n) return fail(plan, ENUF_ERR_INVALID, "window 2p = %d wider than the grid", 2 * P.p);
+    // tile edge: divides n, >= p, histogram fits in shared memory
+    int T = 0;
+    if (P.tile > 0) {
+        T = P.tile;
+        if (n % T || T < P.p || (n / T) * (n / T) * (n / T) > kMaxTiles || T > 32)
+            return fail(plan, ENUF_ERR_INVALID, "tile %d does not divide n = %d, is < p, or too small/large", T, n);
+    } else {
+        for (int c = std::max(P.p, 8); c <= 32 && !T; ++c)
+            if (n % c == 0 && (n / c) * (n / c) * (n / c) <= kMaxTiles) T = c;
+        for (int c = P.p; c < 8 && !T; ++c)
+            if (n % c == 0 && (n / c) * (n / c) * (n / c) <= kMaxTiles) T = c;
+        if (!T) return fail(plan, ENUF_ERR_UNSUPPORTED, "no tile edge for n = %d, p = %d", n, P.p);
+    }
+    const int esz = P.prec == ENUF_FP32 ? 4 : 8;
+    const int csz = 2 * esz;
+    Geo g{};
+    g.n = n;
+    g.nc = M / 2 - 1;
+    g.K = 2 * g.nc + 1;
+    g.p = P.p;
+    g.T = T;
+    g.ntd = n / T;
+    g.ntiles = g.ntd * g.ntd * g.ntd;
+    const double tw = T * P.L / n;
+    g.rs = (int)std::ceil(P.r_cut / tw - 1e-12);
+    g.chunk = std::max(2048, (n_max + 63) / 64);
+    g.nbin = std::max(1, (n_max + g.chunk - 1) / g.chunk);
+    g.kmask = P.kmask;
+    g.L = P.L;
+    g.alpha = P.alpha;
+    g.beta = P.beta;
+    g.kappa = P.kappa;
+    g.rc = P.r_cut;
+    g.b = 2.0 * P.sigma_s * P.p / ((2.0 * P.sigma_s - 1.0) * M_PI);
+    g.wnorm = 1.0 / std::sqrt(M_PI * g.b);
+
+    FftShape fs{};
+    const int budget = 64 * 1024;
+    fs.lx = lines_for(n, 2, csz, budget, 32);
+    fs.ly = lines_for(n, 2, csz, budget, 32);
+    fs.lz = lines_for(n, 3, csz, budget, 32);
+    fs.liy = lines_for(n, 2, csz, budget, 32);
+    fs.lix = lines_for(n, 2, csz, budget, 32);
+    fs.smem_x = (1 + 2 * fs.lx) * n * csz;
+    fs.smem_y = (1 + 2 * fs.ly) * n * csz;
+    fs.smem_z = (1 + 3 * fs.lz) * n * csz;
+    fs.smem_iy = (1 + 2 * fs.liy) * n * csz;
+    fs.smem_ix = (1 + 2 * fs.lix) * n * csz;
+    const int nc1 = g.nc + 1;
+    fs.grid_x = (n * n / 2 + fs.lx - 1) / fs.lx;
+    fs.grid_y_z = (n + fs.ly - 1) / fs.ly;
+    fs.grid_z = (nc1 * g.K + fs.lz - 1) / fs.lz;
+    fs.grid_iy = (3 * n * nc1 + fs.liy - 1) / fs.liy;
+    fs.grid_ix = (3 * n * n / 2 + fs.lix - 1) / fs.lix;
+
+    Work w{};
+    w.nblk_real = 2 * kSMs;
+    w.nblk_conv = fs.grid_z;
+    w.nblk_dpd = 4 * kSMs;
+    w.nblk_kin = 4 * kSMs;
+    w.nblk_gather = 4 * kSMs;
+    w.off_q = 0;
+    w.off_real = w.off_q + 2 * g.nbin;
+    w.off_recip = w.off_real + 2 * w.nblk_real;
+    w.off_dpd = w.off_recip + 2 * w.nblk_conv;
+    w.off_kin = w.off_dpd + 2 * w.nblk_dpd;
+    const int npart = w.off_kin + w.nblk_kin;
+
+    const size_t nm = (size_t)std::max(n_max, 1);
+    const size_t n3 = (size_t)n * n * n;
+    const size_t ntab = (size_t)nc1 * g.K * g.K;
+    size_t off = 0;
+    auto take = [&](size_t b) { size_t o = off; off += align256(b); return o; };
+    // record offsets in w as integers for now (cast later)
+    size_t o_key = take(nm * 4), o_bhist = take((size_t)g.nbin * g.ntiles * 4),
+           o_boff = take((size_t)g.nbin * g.ntiles * 4), o_tstart = take((size_t)(g.ntiles + 1) * 4),
+           o_sq = take(nm * 4 * esz), o_sw = take(nm * 4 * esz), o_sb = take(nm * 4), o_grid = take(n3 * esz),
+           o_s1 = take((size_t)n * nc1 * n * csz), o_s2 = take((size_t)nc1 * g.K * n * csz),
+           o_s3 = take((size_t)3 * n * nc1 * g.K * csz), o_s4 = take((size_t)3 * n * n * nc1 * csz),
+           o_h = take(3 * n3 * esz), o_tab = take(ntab * 8), o_tabv = take(ntab * 8), o_tabr = take(ntab * esz),
+           o_tw = take((size_t)n * csz), o_part = take((size_t)npart * 8), o_E = take(16 * 8);
+    if (bytes) *bytes = off;
+    if (plan) {
+        plan->P = P;
+        plan->P.M = M;
+        plan->P.tile = T;
+        plan->n_max = n_max;
+        plan->prec = P.prec;
+        plan->rsz = esz;
+        plan->g = g;
+        plan->fs = fs;
+        plan->fp = fp;
+        // stash offsets; bound to the allocation in bind()
+        w.key = (int*)o_key; w.bhist = (int*)o_bhist; w.boff = (int*)o_boff; w.tstart = (int*)o_tstart;
+        w.sq = (void*)o_sq; w.sw = (void*)o_sw; w.sb = (int*)o_sb; w.grid = (void*)o_grid;
+        w.spec1 = (void*)o_s1; w.spec2 = (void*)o_s2; w.spec3 = (void*)o_s3; w.spec4 = (void*)o_s4;
+        w.h = (void*)o_h; w.tab = (double*)o_tab; w.tabv = (double*)o_tabv; w.tabr = (void*)o_tabr;
+        w.tw = (void*)o_tw; w.part = (double*)o_part; w.Edev = (double*)o_E;
+        plan->w = w;
+        plan->dbytes = off;
+    }
+    return ENUF_OK;
+}
+
+void bind(enuf_plan_t p) {
+    char* b = static_cast<char*>(p->dmem);
+    Work& w = p->w;
+    auto at = [&](auto ptr) { return reinterpret_cast<decltype(ptr)>(b + reinterpret_cast<size_t>(ptr)); };
+    w.key = at(w.key); w.bhist = at(w.bhist); w.boff = at(w.boff); w.tstart = at(w.tstart);
+    w.sq = at(w.sq); w.sw = at(w.sw); w.sb = at(w.sb); w.grid = at(w.grid);
+    w.spec1 = at(w.spec1); w.spec2 = at(w.spec2); w.spec3 = at(w.spec3); w.spec4 = at(w.spec4);
+    w.h = at(w.h); w.tab = at(w.tab); w.tabv = at(w.tabv); w.tabr = at(w.tabr);
+    w.tw = at(w.tw); w.part = at(w.part); w.Edev = at(w.Edev);
+}
+
+// FP64 influence x deconvolution table over the half space kx = 0..nc:
+// D(k) = e^{-(pi k)^2/(alpha L)^2} / (k^2 prod_t c(k_t)^2), c(k) = e^{-b (pi k/n)^2}
+// (Eq. 18/20 divided by the window's Fourier factor twice: once for the
+// transposed, once for the conjugated NFFT); 0 at k = 0 and outside the mode set.
+enuf_status upload_tables(enuf_plan_t plan) {
+    const Geo& g = plan->g;
+    const int nc = g.nc, K = g.K, n = g.n;
+    const size_t ntab = (size_t)(nc + 1) * K * K;
+    std::vector<double> D(ntab, 0.0), Dv(ntab, 0.0);
+    std::vector<double> c(K);
+    for (int i = 0; i < K; ++i) {
+        const double t = M_PI * (i - nc) / n;
+        c[i] = std::exp(-g.b * t * t);
+    }
+    const double aL = g.alpha * g.L;
+    for (int kx = 0; kx <= nc; ++kx)
+        for (int iy = 0; iy < K; ++iy)
+            for (int iz = 0; iz < K; ++iz) {
+                const int ky = iy - nc, kz = iz - nc;
+                const double k2 = (double)kx * kx + (double)ky * ky + (double)kz * kz;
+                if (k2 == 0) continue;
+                if (g.kmask == 1 && k2 > (double)nc * nc) continue;
+                const double cc = c[kx + nc] * c[iy] * c[iz];
+                const double d = std::exp(-M_PI * M_PI * k2 / (aL * aL)) / k2 / (cc * cc);
+                const size_t id = ((size_t)kx * K + iy) * K + iz;
+                D[id] = d;
+                Dv[id] = d * (1.0 - 2.0 * M_PI * M_PI * k2 / (aL * aL));
+            }
+    CU(cudaMemcpy(plan->w.tab, D.data(), ntab * 8, cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(plan->w.tabv, Dv.data(), ntab * 8, cudaMemcpyHostToDevice));
+    std::vector<double> tw(2 * n);
+    for (int t = 0; t < n; ++t) {
+        tw[2 * t] = std::cos(2.0 * M_PI * t / n);
+        tw[2 * t + 1] = -std::sin(2.0 * M_PI * t / n);
+    }
+    if (plan->prec == ENUF_FP32) {
+        std::vector<float> Df(D.begin(), D.end()), twf(tw.begin(), tw.end());
+        CU(cudaMemcpy(plan->w.tabr, Df.data(), ntab * 4, cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(plan->w.tw, twf.data(), 2 * n * 4, cudaMemcpyHostToDevice));
+    } else {
+        CU(cudaMemcpy(plan->w.tabr, D.data(), ntab * 8, cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(plan->w.tw, tw.data(), 2 * n * 8, cudaMemcpyHostToDevice));
+    }
+    return ENUF_OK;
+}
+
+enuf_status enqueue_eval(enuf_plan_t plan, const EvalArgs& a, cudaStream_t s0, cudaStream_t s1,
+                         cudaEvent_t evFork, cudaEvent_t evJoin, Events* ev, LaunchLog* log) {
+    cudaError_t e;
+    if (plan->prec == ENUF_FP32)
+        e = enqueue_enuf<float>(plan->g, plan->fs, plan->fp, plan->w, a, s0, s1, evFork, evJoin, ev, log);
+    else
+        e = enqueue_enuf<double>(plan->g, plan->fs, plan->fp, plan->w, a, s0, s1, evFork, evJoin, ev, log);
+    if (e != cudaSuccess) return fail(plan, ENUF_ERR_CUDA, "enqueue: %s", cudaGetErrorString(e));
+    return ENUF_OK;
+}
+
+enuf_status enqueue_tot(enuf_plan_t plan, bool dpd, cudaStream_t s, LaunchLog* log) {
+    cudaError_t e = plan->prec == ENUF_FP32 ? enqueue_totals<float>(plan->g, plan->w, dpd, s, log)
+                                            : enqueue_totals<double>(plan->g, plan->w, dpd, s, log);
+    if (e != cudaSuccess) return fail(plan, ENUF_ERR_CUDA, "totals: %s", cudaGetErrorString(e));
+    return ENUF_OK;
+}
+
+void drop_graph(enuf_plan_t p) {
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    p->gexec = nullptr;
+    p->g_n = -1;
+}
+
+// Capture one evaluation (and the D2H copy of the totals) as a graph.
+enuf_status capture_eval(enuf_plan_t plan, int n, const void* pos, const void* q, void* F) {
+    drop_graph(plan);
+    cudaGraph_t graph = nullptr;
+    CU(cudaStreamBeginCapture(plan->stream, cudaStreamCaptureModeThreadLocal));
+    LaunchLog log;
+    Events* ev = plan->ev.on ? &plan->ev : nullptr;
+    if (ev) cudaEventRecordWithFlags(ev->start[6], plan->stream, cudaEventRecordExternal);
+    EvalArgs a{n, pos, q, F, true};
+    enuf_status st = enqueue_eval(plan, a, plan->stream, plan->aux, plan->evFork, plan->evJoin, ev, &log);
+    if (st == ENUF_OK) st = enqueue_tot(plan, false, plan->stream, &log);
+    if (st == ENUF_OK) {
+        cudaError_t e = cudaMemcpyAsync(plan->hE, plan->w.Edev, 16 * sizeof(double), cudaMemcpyDeviceToHost,
+                                        plan->stream);
+        if (e != cudaSuccess) st = fail(plan, ENUF_ERR_CUDA, "memcpy: %s", cudaGetErrorString(e));
+    }
+    if (ev) cudaEventRecordWithFlags(ev->stop[6], plan->stream, cudaEventRecordExternal);
+    cudaError_t e = cudaStreamEndCapture(plan->stream, &graph);
+    if (st != ENUF_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return fail(plan, ENUF_ERR_CUDA, "capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&plan->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(plan, ENUF_ERR_CUDA, "instantiate: %s", cudaGetErrorString(e));
+    plan->g_n = n;
+    plan->g_pos = pos;
+    plan->g_q = q;
+    plan->g_F = F;
+    plan->g_timing = plan->ev.on;
+    plan->launches = log.kernels;
+    return ENUF_OK;
+}
+
+enuf_status finish_energies(enuf_plan_t plan, double* E, double* virial) {
+    if (!E && !virial) return ENUF_OK;
+    CU(cudaStreamSynchronize(plan->stream));
+    if (E)
+        for (int i = 0; i < 4; ++i) E[i] = plan->hE[i];
+    if (virial) *virial = plan->hE[7];
+    return ENUF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* enuf_status_string(enuf_status s) {
+    switch (s) {
+        case ENUF_OK: return "ok";
+        case ENUF_ERR_INVALID: return "invalid argument";
+        case ENUF_ERR_OOM: return "out of device memory";
+        case ENUF_ERR_CUDA: return "CUDA error";
+        case ENUF_ERR_TIMEOUT: return "device wait timed out";
+        case ENUF_ERR_UNSUPPORTED: return "unsupported configuration";
+    }
+    return "unknown status";
+}
+
+const char* enuf_last_error(enuf_plan_t plan) { return plan ? plan->err : "no plan"; }
+
+enuf_status enuf_footprint(const enuf_params* params, int n_max, size_t* bytes) {
+    if (!params || !bytes) return ENUF_ERR_INVALID;
+    return derive(nullptr, *params, n_max, bytes);
+}
+
+enuf_status enuf_plan(const enuf_params* params, int n_max, void* cuda_stream, enuf_plan_t* out) {
+    if (!out || !params) return ENUF_ERR_INVALID;
+    *out = nullptr;
+    enuf_plan_t plan = new (std::nothrow) enuf_plan_s();
+    if (!plan) return ENUF_ERR_OOM;
+    enuf_status st = derive(plan, *params, n_max, nullptr);
+    if (st != ENUF_OK) {
+        fprintf(stderr, "enuf_plan: %s\n", plan->err);
+        delete plan;
+        return st;
+    }
+    auto bail = [&](enuf_status s) {
+        fprintf(stderr, "enuf_plan: %s\n", plan->err);
+        enuf_destroy(plan);
+        return s;
+    };
+    const int pi = plan->prec == ENUF_FP32 ? 0 : 1;
+    if (!g_configured[pi]) {
+        cudaError_t e = plan->prec == ENUF_FP32 ? configure_kernels<float>(kMaxSmem) : configure_kernels<double>(kMaxSmem);
+        if (e != cudaSuccess) return bail(fail(plan, ENUF_ERR_CUDA, "configure: %s", cudaGetErrorString(e)));
+        g_configured[pi] = true;
+    }
+    if (cuda_stream) {
+        plan->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&plan->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return bail(fail(plan, ENUF_ERR_CUDA, "stream create failed"));
+        plan->own_stream = true;
+    }
+    if (cudaStreamCreateWithFlags(&plan->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&plan->evFork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&plan->evJoin, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&plan->evA, cudaEventDisableTiming) != cudaSuccess)
+        return bail(fail(plan, ENUF_ERR_CUDA, "stream/event create failed"));
+    for (int i = 0; i < kStageCount; ++i)
+        if (cudaEventCreate(&plan->ev.start[i]) != cudaSuccess || cudaEventCreate(&plan->ev.stop[i]) != cudaSuccess)
+            return bail(fail(plan, ENUF_ERR_CUDA, "event create failed"));
+    cudaError_t e = cudaMalloc(&plan->dmem, plan->dbytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        plan->dmem = nullptr;
+        return bail(fail(plan, ENUF_ERR_OOM, "cudaMalloc(%zu): %s", plan->dbytes, cudaGetErrorString(e)));
+    }
+    bind(plan);
+    if (cudaMemset(plan->dmem, 0, plan->dbytes) != cudaSuccess)
+        return bail(fail(plan, ENUF_ERR_CUDA, "memset failed"));
+    if (cudaMallocHost(&plan->hE, 16 * sizeof(double)) != cudaSuccess)
+        return bail(fail(plan, ENUF_ERR_OOM, "pinned alloc failed"));
+    st = upload_tables(plan);
+    if (st != ENUF_OK) return bail(st);
+    *out = plan;
+    return ENUF_OK;
+}
+
+enuf_status enuf_get_info(enuf_plan_t plan, enuf_plan_info* info) {
+    if (!plan || !info) return ENUF_ERR_INVALID;
+    info->M = plan->P.M;
+    info->n = plan->g.n;
+    info->n_c = plan->g.nc;
+    info->tile = plan->g.T;
+    info->n_tiles = plan->g.ntiles;
+    info->n_max = plan->n_max;
+    info->device_bytes = plan->dbytes;
+    return ENUF_OK;
+}
+
+enuf_status enuf_energy_forces(enuf_plan_t plan, int n, const void* pos, const void* q, void* F, double* E,
+                               double* virial) {
+    if (!plan) return ENUF_ERR_INVALID;
+    if (n < 0 || n > plan->n_max) return fail(plan, ENUF_ERR_INVALID, "n = %d outside [0, n_max = %d]", n, plan->n_max);
+    if (n > 0 && (!pos || !q || !F)) return fail(plan, ENUF_ERR_INVALID, "null array");
+    if (!plan->gexec || plan->g_n != n || plan->g_pos != pos || plan->g_q != q || plan->g_F != F ||
+        plan->g_timing != plan->ev.on) {
+        enuf_status st = capture_eval(plan, n, pos, q, F);
+        if (st != ENUF_OK) return st;
+    }
+    CU(cudaGraphLaunch(plan->gexec, plan->stream));
+    return finish_energies(plan, E, virial);
+}
+
+enuf_status enuf_energy_forces_host(enuf_plan_t plan, int n, const void* pos, const void* q, void* F, double* E,
+                                    double* virial) {
+    if (!plan) return ENUF_ERR_INVALID;
+    if (n < 0 || n > plan->n_max) return fail(plan, ENUF_ERR_INVALID, "n = %d outside [0, n_max = %d]", n, plan->n_max);
+    if (n > 0 && (!pos || !q || !F)) return fail(plan, ENUF_ERR_INVALID, "null array");
+    const size_t nm = (size_t)std::max(plan->n_max, 1);
+    if (!plan->stage) {
+        cudaError_t e = cudaMalloc(&plan->stage, align256(nm * 3 * plan->rsz) * 2 + align256(nm * plan->rsz));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            plan->stage = nullptr;
+            return fail(plan, ENUF_ERR_OOM, "staging alloc: %s", cudaGetErrorString(e));
+        }
+    }
+    char* b = static_cast<char*>(plan->stage);
+    void* dpos = b;
+    void* dF = b + align256(nm * 3 * plan->rsz);
+    void* dq = b + 2 * align256(nm * 3 * plan->rsz);
+    if (n > 0) {
+        CU(cudaMemcpyAsync(dpos, pos, (size_t)n * 3 * plan->rsz, cudaMemcpyHostToDevice, plan->stream));
+        CU(cudaMemcpyAsync(dq, q, (size_t)n * plan->rsz, cudaMemcpyHostToDevice, plan->stream));
+    }
+    enuf_status st = enuf_energy_forces(plan, n, dpos, dq, dF, nullptr, nullptr);
+    if (st != ENUF_OK) return st;
+    if (n > 0) CU(cudaMemcpyAsync(F, dF, (size_t)n * 3 * plan->rsz, cudaMemcpyDeviceToHost, plan->stream));
+    CU(cudaStreamSynchronize(plan->stream));
+    if (E)
+        for (int i = 0; i < 4; ++i) E[i] = plan->hE[i];
+    if (virial) *virial = plan->hE[7];
+    return ENUF_OK;
+}
+
+enuf_status enuf_debug_buffer(enuf_plan_t plan, int which, void* host, size_t bytes) {
+    if (!plan || !host) return ENUF_ERR_INVALID;
+    const size_t n3 = (size_t)plan->g.n * plan->g.n * plan->g.n;
+    const void* src = nullptr;
+    size_t need = 0;
+    if (which == ENUF_BUF_GRID) { src = plan->w.grid; need = n3 * plan->rsz; }
+    else if (which == ENUF_BUF_FIELD) { src = plan->w.h; need = 3 * n3 * plan->rsz; }
+    else return fail(plan, ENUF_ERR_INVALID, "unknown buffer %d", which);
+    if (bytes != need) return fail(plan, ENUF_ERR_INVALID, "buffer needs %zu bytes, got %zu", need, bytes);
+    CU(cudaStreamSynchronize(plan->stream));
+    CU(cudaMemcpy(host, src, need, cudaMemcpyDeviceToHost));
+    return ENUF_OK;
+}
+
+enuf_status enuf_enable_timing(enuf_plan_t plan, int on) {
+    if (!plan) return ENUF_ERR_INVALID;
+    plan->ev.on = on != 0;
+    return ENUF_OK;
+}
+
+enuf_status enuf_stage_time(enuf_plan_t plan, int stage, float* ms) {
+    if (!plan || !ms || stage < 0 || stage >= kStageCount) return ENUF_ERR_INVALID;
+    if (!plan->ev.on) return fail(plan, ENUF_ERR_INVALID, "timing is off");
+    CU(cudaEventSynchronize(plan->ev.stop[stage]));
+    CU(cudaEventElapsedTime(ms, plan->ev.start[stage], plan->ev.stop[stage]));
+    return ENUF_OK;
+}
+
+int enuf_launches_per_eval(enuf_plan_t plan) { return plan ? plan->launches : 0; }
+
+void enuf_destroy(enuf_plan_t plan) {
+    if (!plan) return;
+    if (plan->stream) cudaStreamSynchronize(plan->stream);
+    drop_graph(plan);
+    if (plan->dmem) cudaFree(plan->dmem);
+    if (plan->stage) cudaFree(plan->stage);
+    if (plan->hE) cudaFreeHost(plan->hE);
+    for (int i = 0; i < kStageCount; ++i) {
+        if (plan->ev.start[i]) cudaEventDestroy(plan->ev.start[i]);
+        if (plan->ev.stop[i]) cudaEventDestroy(plan->ev.stop[i]);
+    }
+    if (plan->evFork) cudaEventDestroy(plan->evFork);
+    if (plan->evJoin) cudaEventDestroy(plan->evJoin);
+    if (plan->evA) cudaEventDestroy(plan->evA);
+    if (plan->aux) cudaStreamDestroy(plan->aux);
+    if (plan->own_stream && plan->stream) cudaStreamDestroy(plan->stream);
+    delete plan;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// DPD systems
+// ---------------------------------------------------------------------------
+struct dpd_system_s {
+    enuf_plan_t plan = nullptr;
+    DpdDev d{};
+    void* dmem = nullptr;
+    cudaGraphExec_t gstep = nullptr;
+    bool g_timing = false;
+    uint64_t step = 0;
+    int launches = 0;
+};
+
+namespace {
+
+enuf_status enqueue_force_eval(dpd_system_t sys, cudaStream_t s0, cudaStream_t s1, Events* ev, LaunchLog* log) {
+    enuf_plan_t plan = sys->plan;
+    // DPD pair + bond forces on s1 (F overwritten), after what s0 did so far
+    CU(cudaEventRecord(plan->evA, s0));
+    CU(cudaStreamWaitEvent(s1, plan->evA, 0));
+    cudaError_t e = plan->prec == ENUF_FP32 ? enqueue_dpd_forces<float>(plan->w, sys->d, s1, ev, log)
+                                            : enqueue_dpd_forces<double>(plan->w, sys->d, s1, ev, log);
+    if (e != cudaSuccess) return fail(plan, ENUF_ERR_CUDA, "dpd enqueue: %s", cudaGetErrorString(e));
+    // electrostatics added into F (real space follows the DPD kernel on s1)
+    EvalArgs a{sys->d.N, sys->d.pos, sys->d.q, sys->d.F, false};
+    return enqueue_eval(plan, a, s0, s1, plan->evFork, plan->evJoin, ev, log);
+}
+
+enuf_status initial_force(dpd_system_t sys) {
+    enuf_plan_t plan = sys->plan;
+    LaunchLog log;
+    CU(cudaMemcpyAsync(sys->d.v0, sys->d.vel, (size_t)sys->d.N * 3 * plan->rsz, cudaMemcpyDeviceToDevice,
+                       plan->stream));
+    enuf_status st = enqueue_force_eval(sys, plan->stream, plan->aux, nullptr, &log);
+    if (st != ENUF_OK) return st;
+    st = enqueue_tot(plan, true, plan->stream, &log);
+    if (st != ENUF_OK) return st;
+    CU(cudaStreamSynchronize(plan->stream));
+    CU(cudaGetLastError());
+    return ENUF_OK;
+}
+
+enuf_status capture_step(dpd_system_t sys) {
+    enuf_plan_t plan = sys->plan;
+    if (sys->gstep) cudaGraphExecDestroy(sys->gstep);
+    sys->gstep = nullptr;
+    cudaGraph_t graph = nullptr;
+    CU(cudaStreamBeginCapture(plan->stream, cudaStreamCaptureModeThreadLocal));
+    LaunchLog log;
+    Events* ev = plan->ev.on ? &plan->ev : nullptr;
+    if (ev) cudaEventRecordWithFlags(ev->start[6], plan->stream, cudaEventRecordExternal);
+    cudaError_t e = plan->prec == ENUF_FP32 ? enqueue_vv_pre<float>(sys->d, plan->stream, &log)
+                                            : enqueue_vv_pre<double>(sys->d, plan->stream, &log);
+    enuf_status st = e == cudaSuccess ? ENUF_OK : fail(plan, ENUF_ERR_CUDA, "vv_pre: %s", cudaGetErrorString(e));
+    if (st == ENUF_OK) st = enqueue_force_eval(sys, plan->stream, plan->aux, ev, &log);
+    if (st == ENUF_OK) {
+        e = plan->prec == ENUF_FP32 ? enqueue_vv_post<float>(plan->w, sys->d, plan->stream, &log)
+                                    : enqueue_vv_post<double>(plan->w, sys->d, plan->stream, &log);
+        if (e != cudaSuccess) st = fail(plan, ENUF_ERR_CUDA, "vv_post: %s", cudaGetErrorString(e));
+    }
+    if (st == ENUF_OK) st = enqueue_tot(plan, true, plan->stream, &log);
+    if (st == ENUF_OK) {
+        e = cudaMemcpyAsync(plan->hE, plan->w.Edev, 16 * sizeof(double), cudaMemcpyDeviceToHost, plan->stream);
+        if (e != cudaSuccess) st = fail(plan, ENUF_ERR_CUDA, "memcpy: %s", cudaGetErrorString(e));
+    }
+    if (ev) cudaEventRecordWithFlags(ev->stop[6], plan->stream, cudaEventRecordExternal);
+    e = cudaStreamEndCapture(plan->stream, &graph);
+    if (st != ENUF_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return fail(plan, ENUF_ERR_CUDA, "capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&sys->gstep, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(plan, ENUF_ERR_CUDA, "instantiate: %s", cudaGetErrorString(e));
+    sys->g_timing = plan->ev.on;
+    sys->launches = log.kernels;
+    plan->launches = log.kernels;
+    return ENUF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+enuf_status dpd_create(enuf_plan_t plan, const dpd_params* params, int n, const void* pos, const void* vel,
+                       const int* type, const void* q, int n_bonds, const int* bonds, dpd_system_t* out) {
+    if (!plan || !params || !out) return ENUF_ERR_INVALID;
+    *out = nullptr;
+    if (n < 1 || n > plan->n_max) return fail(plan, ENUF_ERR_INVALID, "n = %d outside [1, n_max]", n);
+    if (!pos || !vel || !type || !q || (n_bonds > 0 && !bonds) || n_bonds < 0)
+        return fail(plan, ENUF_ERR_INVALID, "null array");
+    if (params->ntypes < 1 || !params->a) return fail(plan, ENUF_ERR_INVALID, "ntypes < 1 or a == NULL");
+    if (!(params->dt > 0)) return fail(plan, ENUF_ERR_INVALID, "dt must be > 0");
+    const double L = plan->P.L;
+    if (L < 2.0) return fail(plan, ENUF_ERR_INVALID, "DPD needs L >= 2 (cutoff 1 with minimum image)");
+    for (int i = 0; i < n; ++i)
+        if (type[i] < 0 || type[i] >= params->ntypes) return fail(plan, ENUF_ERR_INVALID, "type[%d] out of range", i);
+    for (int k = 0; k < 2 * n_bonds; ++k)
+        if (bonds[k] < 0 || bonds[k] >= n) return fail(plan, ENUF_ERR_INVALID, "bond index out of range");
+
+    dpd_system_t sys = new (std::nothrow) dpd_system_s();
+    if (!sys) return ENUF_ERR_OOM;
+    sys->plan = plan;
+    DpdDev& d = sys->d;
+    d.N = n;
+    d.ntypes = params->ntypes;
+    d.ncd = std::max(1, (int)std::floor(L * (1.0 - 1e-12)));
+    d.ncells = d.ncd * d.ncd * d.ncd;
+    d.L = L;
+    d.gamma = params->gamma;
+    d.sigma = params->sigma;
+    d.dt = params->dt;
+    d.lambda_vv = params->lambda_vv;
+    d.K_bond = params->K_bond;
+    d.r0_bond = params->r0_bond;
+    d.seed = params->seed;
+    const size_t rs = plan->rsz;
+    // per-bead bond lists (CSR over both ends)
+    std::vector<int> bptr(n + 1, 0), blist(2 * (size_t)n_bonds);
+    for (int k = 0; k < n_bonds; ++k) {
+        ++bptr[bonds[2 * k] + 1];
+        ++bptr[bonds[2 * k + 1] + 1];
+    }
+    for (int i = 0; i < n; ++i) bptr[i + 1] += bptr[i];
+    {
+        std::vector<int> cur(bptr.begin(), bptr.end() - 1);
+        for (int k = 0; k < n_bonds; ++k) {
+            blist[cur[bonds[2 * k]]++] = bonds[2 * k + 1];
+            blist[cur[bonds[2 * k + 1]]++] = bonds[2 * k];
+        }
+    }
+    size_t off = 0;
+    auto take = [&](size_t b) { size_t o = off; off += align256(b); return o; };
+    const size_t o_pos = take(n * 3 * rs), o_vel = take(n * 3 * rs), o_v0 = take(n * 3 * rs),
+                 o_F = take(n * 3 * rs), o_q = take(n * rs), o_type = take(n * 4),
+                 o_atab = take((size_t)d.ntypes * d.ntypes * rs), o_bptr = take((n + 1) * 4),
+                 o_blist = take(std::max<size_t>(1, blist.size()) * 4), o_ckey = take(n * 4),
+                 o_ccount = take((size_t)d.ncells * 4), o_cstart = take(((size_t)d.ncells + 1) * 4),
+                 o_ccur = take((size_t)d.ncells * 4), o_sp = take(n * 4 * rs), o_sv = take(n * 4 * rs),
+                 o_step = take(8);
+    cudaError_t e = cudaMalloc(&sys->dmem, off);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete sys;
+        return fail(plan, ENUF_ERR_OOM, "dpd alloc(%zu): %s", off, cudaGetErrorString(e));
+    }
+    char* b = static_cast<char*>(sys->dmem);
+    d.pos = b + o_pos; d.vel = b + o_vel; d.v0 = b + o_v0; d.F = b + o_F; d.q = b + o_q;
+    d.type = reinterpret_cast<int*>(b + o_type); d.atab = b + o_atab;
+    d.bptr = reinterpret_cast<int*>(b + o_bptr); d.blist = reinterpret_cast<int*>(b + o_blist);
+    d.ckey = reinterpret_cast<int*>(b + o_ckey); d.ccount = reinterpret_cast<int*>(b + o_ccount);
+    d.cstart = reinterpret_cast<int*>(b + o_cstart); d.ccur = reinterpret_cast<int*>(b + o_ccur);
+    d.sp = b + o_sp; d.sv = b + o_sv; d.step_dev = reinterpret_cast<uint64_t*>(b + o_step);
+    auto bail = [&](enuf_status s) { dpd_destroy(sys); return s; };
+    if (cudaMemset(sys->dmem, 0, off) != cudaSuccess) return bail(fail(plan, ENUF_ERR_CUDA, "memset failed"));
+    std::vector<char> at((size_t)d.ntypes * d.ntypes * rs);
+    for (int k = 0; k < d.ntypes * d.ntypes; ++k) {
+        if (rs == 4) reinterpret_cast<float*>(at.data())[k] = (float)params->a[k];
+        else reinterpret_cast<double*>(at.data())[k] = params->a[k];
+    }
+    if (cudaMemcpy(d.pos, pos, n * 3 * rs, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d.vel, vel, n * 3 * rs, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d.q, q, n * rs, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d.type, type, n * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d.atab, at.data(), at.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d.bptr, bptr.data(), (n + 1) * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        (!blist.empty() && cudaMemcpy(d.blist, blist.data(), blist.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess))
+        return bail(fail(plan, ENUF_ERR_CUDA, "upload failed"));
+    enuf_status st = initial_force(sys);
+    if (st != ENUF_OK) return bail(st);
+    *out = sys;
+    return ENUF_OK;
+}
+
+enuf_status dpd_step(dpd_system_t sys, int nsteps, double* E) {
+    if (!sys) return ENUF_ERR_INVALID;
+    enuf_plan_t plan = sys->plan;
+    if (nsteps < 0) return fail(plan, ENUF_ERR_INVALID, "nsteps < 0");
+    if (!sys->gstep || sys->g_timing != plan->ev.on) {
+        enuf_status st = capture_step(sys);
+        if (st != ENUF_OK) return st;
+    }
+    for (int s = 0; s < nsteps; ++s) CU(cudaGraphLaunch(sys->gstep, plan->stream));
+    sys->step += (uint64_t)nsteps;
+    if (E) {
+        CU(cudaStreamSynchronize(plan->stream));
+        for (int i = 0; i < 8; ++i) E[i] = plan->hE[i];
+    }
+    return ENUF_OK;
+}
+
+enuf_status dpd_get_state(dpd_system_t sys, void* pos, void* vel, void* F, uint64_t* step) {
+    if (!sys) return ENUF_ERR_INVALID;
+    enuf_plan_t plan = sys->plan;
+    const size_t b = (size_t)sys->d.N * 3 * plan->rsz;
+    if (pos) CU(cudaMemcpyAsync(pos, sys->d.pos, b, cudaMemcpyDeviceToHost, plan->stream));
+    if (vel) CU(cudaMemcpyAsync(vel, sys->d.vel, b, cudaMemcpyDeviceToHost, plan->stream));
+    if (F) CU(cudaMemcpyAsync(F, sys->d.F, b, cudaMemcpyDeviceToHost, plan->stream));
+    CU(cudaStreamSynchronize(plan->stream));
+    if (step) *step = sys->step;
+    return ENUF_OK;
+}
+
+enuf_status dpd_set_state(dpd_system_t sys, const void* pos, const void* vel, const void* F, uint64_t step) {
+    if (!sys) return ENUF_ERR_INVALID;
+    enuf_plan_t plan = sys->plan;
+    const size_t b = (size_t)sys->d.N * 3 * plan->rsz;
+    if (pos) CU(cudaMemcpyAsync(sys->d.pos, pos, b, cudaMemcpyHostToDevice, plan->stream));
+    if (vel) CU(cudaMemcpyAsync(sys->d.vel, vel, b, cudaMemcpyHostToDevice, plan->stream));
+    CU(cudaMemcpyAsync(sys->d.step_dev, &step, 8, cudaMemcpyHostToDevice, plan->stream));
+    CU(cudaStreamSynchronize(plan->stream));
+    sys->step = step;
+    if (F) {
+        CU(cudaMemcpyAsync(sys->d.F, F, b, cudaMemcpyHostToDevice, plan->stream));
+        CU(cudaStreamSynchronize(plan->stream));
+        return ENUF_OK;
+    }
+    return initial_force(sys);
+}
+
+enuf_status dpd_get_forces(dpd_system_t sys, void* F) { return dpd_get_state(sys, nullptr, nullptr, F, nullptr); }
+
+enuf_status dpd_device_state(dpd_system_t sys, void** pos, void** vel, void** F) {
+    if (!sys) return ENUF_ERR_INVALID;
+    if (pos) *pos = sys->d.pos;
+    if (vel) *vel = sys->d.vel;
+    if (F) *F = sys->d.F;
+    return ENUF_OK;
+}
+
+void dpd_destroy(dpd_system_t sys) {
+    if (!sys) return;
+    if (sys->plan && sys->plan->stream) cudaStreamSynchronize(sys->plan->stream);
+    if (sys->gstep) cudaGraphExecDestroy(sys->gstep);
+    if (sys->dmem) cudaFree(sys->dmem);
+    delete sys;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches
+// ---------------------------------------------------------------------------
+struct enuf_batch_s {
+    std::vector<enuf_plan_t> plans;
+    std::vector<int> n;
+    std::vector<cudaStream_t> s0, s1;
+    std::vector<cudaEvent_t> evDone;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaEvent_t evStart = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<const void*> g_pos, g_q;
+    std::vector<void*> g_F;
+    int launches = 0;
+};
+
+extern "C" {
+
+enuf_status enuf_batch_plan(int nsys, const enuf_params* params, const int* n, void* cuda_stream,
+                            enuf_batch_t* out) {
+    if (!out || nsys < 1 || !params || !n) return ENUF_ERR_INVALID;
+    *out = nullptr;
+    enuf_batch_t b = new (std::nothrow) enuf_batch_s();
+    if (!b) return ENUF_ERR_OOM;
+    auto bail = [&](enuf_status s) { enuf_batch_destroy(b); return s; };
+    if (cuda_stream) b->stream = static_cast<cudaStream_t>(cuda_stream);
+    else {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(ENUF_ERR_CUDA);
+        b->own_stream = true;
+    }
+    if (cudaEventCreateWithFlags(&b->evStart, cudaEventDisableTiming) != cudaSuccess) return bail(ENUF_ERR_CUDA);
+    for (int s = 0; s < nsys; ++s) {
+        enuf_plan_t p = nullptr;
+        enuf_status st = enuf_plan(&params[s], n[s], nullptr, &p);
+        if (st != ENUF_OK) return bail(st);
+        b->plans.push_back(p);
+        b->n.push_back(n[s]);
+        cudaEvent_t e;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return bail(ENUF_ERR_CUDA);
+        b->evDone.push_back(e);
+    }
+    *out = b;
+    return ENUF_OK;
+}
+
+enuf_status enuf_batch_energy_forces(enuf_batch_t b, const void* const* pos, const void* const* q, void* const* F,
+                                     double* E) {
+    if (!b || !pos || !q || !F) return ENUF_ERR_INVALID;
+    const int ns = (int)b->plans.size();
+    bool same = b->gexec && (int)b->g_pos.size() == ns;
+    for (int s = 0; same && s < ns; ++s) same = b->g_pos[s] == pos[s] && b->g_q[s] == q[s] && b->g_F[s] == F[s];
+    if (!same) {
+        if (b->gexec) cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return ENUF_ERR_CUDA;
+        cudaEventRecord(b->evStart, b->stream);
+        LaunchLog log;
+        enuf_status st = ENUF_OK;
+        for (int s = 0; s < ns && st == ENUF_OK; ++s) {
+            enuf_plan_t p = b->plans[s];
+            cudaStreamWaitEvent(p->stream, b->evStart, 0);
+            EvalArgs a{b->n[s], pos[s], q[s], F[s], true};
+            st = enqueue_eval(p, a, p->stream, p->aux, p->evFork, p->evJoin, nullptr, &log);
+            if (st == ENUF_OK) st = enqueue_tot(p, false, p->stream, &log);
+            if (st == ENUF_OK)
+                cudaMemcpyAsync(p->hE, p->w.Edev, 16 * sizeof(double), cudaMemcpyDeviceToHost, p->stream);
+            cudaEventRecord(b->evDone[s], p->stream);
+            cudaStreamWaitEvent(b->stream, b->evDone[s], 0);
+        }
+        cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+        if (st != ENUF_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (e != cudaSuccess) return ENUF_ERR_CUDA;
+        e = cudaGraphInstantiate(&b->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return ENUF_ERR_CUDA;
+        b->g_pos.assign(pos, pos + ns);
+        b->g_q.assign(q, q + ns);
+        b->g_F.assign(F, F + ns);
+        b->launches = log.kernels;
+    }
+    if (cudaGraphLaunch(b->gexec, b->stream) != cudaSuccess) return ENUF_ERR_CUDA;
+    if (E) {
+        if (cudaStreamSynchronize(b->stream) != cudaSuccess) return ENUF_ERR_CUDA;
+        for (int s = 0; s < ns; ++s)
+            for (int i = 0; i < 4; ++i) E[4 * s + i] = b->plans[s]->hE[i];
+    }
+    return ENUF_OK;
+}
+
+int enuf_batch_launches(enuf_batch_t b) { return b ? b->launches : 0; }
+
+void enuf_batch_destroy(enuf_batch_t b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    for (auto p : b->plans) enuf_destroy(p);
+    for (auto e : b->evDone) cudaEventDestroy(e);
+    if (b->evStart) cudaEventDestroy(b->evStart);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+}  // extern "C"

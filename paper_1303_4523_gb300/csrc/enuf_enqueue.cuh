@@ -1,0 +1,160 @@
+// enuf_enqueue.cuh -- launch sequences of one ENUF evaluation and one DPD
+// step. Two streams: s0 carries binning -> spread -> FFT passes -> gather, s1
+// carries the DPD pair forces and the real-space electrostatics, which only
+// depend on the binning and write F; the branches join before the gather.
+// Every sequence is stream-ordered and capturable into a CUDA graph.
+#pragma once
+#include "enuf_kernels.cuh"
+
+namespace enuf {
+
+constexpr int kBinThreads = 512;
+
+inline void rec(Events* ev, int stage, bool start, cudaStream_t s) {
+    if (ev && ev->on)
+        cudaEventRecordWithFlags(start ? ev->start[stage] : ev->stop[stage], s, cudaEventRecordExternal);
+}
+
+template <typename R>
+cudaError_t configure_kernels(int max_smem) {
+    cudaError_t e = cudaSuccess;
+    auto set = [&](const void* f) {
+        cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+        if (r != cudaSuccess) e = r;
+    };
+    set((const void*)k_bin_count<R>);
+    set((const void*)k_bin_scatter<R>);
+    set((const void*)k_spread<R>);
+    set((const void*)k_fft_x<R>);
+    set((const void*)k_fft_y<R>);
+    set((const void*)k_fft_z<R>);
+    set((const void*)k_fft_iy<R>);
+    set((const void*)k_fft_ix<R>);
+    return e;
+}
+
+template <typename R>
+int spread_smem(const Geo& g) {
+    const int T3 = g.T * g.T * g.T;
+    return T3 * (int)sizeof(R) + (kSpreadThreads / 32) * 3 * kMaxTaps * ((int)sizeof(R) + 4);
+}
+
+template <typename R>
+cudaError_t enqueue_enuf(const Geo& g, const FftShape& fs, const FftPlanDev& fp, const Work& w,
+                         const EvalArgs& a, cudaStream_t s0, cudaStream_t s1, cudaEvent_t evFork,
+                         cudaEvent_t evJoin, Events* ev, LaunchLog* log) {
+    using C = typename Cx<R>::T;
+    using V = typename V4<R>::T;
+    const R* pos = static_cast<const R*>(a.pos);
+    const R* q = static_cast<const R*>(a.q);
+    R* F = static_cast<R*>(a.F);
+    V* sq = static_cast<V*>(w.sq);
+    V* sw = static_cast<V*>(w.sw);
+    C* tw = static_cast<C*>(w.tw);
+    const int hsm = g.ntiles * (int)sizeof(int);
+
+    rec(ev, 0, true, s0);
+    k_bin_count<R><<<g.nbin, kBinThreads, hsm, s0>>>(g, a.N, pos, q, w.key, w.bhist, a.zeroF ? F : nullptr,
+                                                     w.part + w.off_q);
+    k_bin_scan<<<1, 1024, 0, s0>>>(g, w.bhist, w.boff, w.tstart);
+    k_bin_scatter<R><<<g.nbin, kBinThreads, hsm, s0>>>(g, a.N, pos, q, w.key, w.boff, sq, sw, w.sb);
+    rec(ev, 0, false, s0);
+    log->kernels += 3;
+
+    // real-space branch
+    cudaEventRecord(evFork, s0);
+    cudaStreamWaitEvent(s1, evFork, 0);
+    rec(ev, 4, true, s1);
+    k_real<R><<<w.nblk_real, kRealThreads, 0, s1>>>(g, w.tstart, sq, sw, w.sb, F, w.part + w.off_real);
+    rec(ev, 4, false, s1);
+    cudaEventRecord(evJoin, s1);
+    log->kernels += 1;
+
+    // reciprocal branch
+    rec(ev, 1, true, s0);
+    k_spread<R><<<g.ntiles, kSpreadThreads, spread_smem<R>(g), s0>>>(g, w.tstart, sq, sw, w.sb,
+                                                                     static_cast<R*>(w.grid));
+    rec(ev, 1, false, s0);
+    rec(ev, 2, true, s0);
+    k_fft_x<R><<<fs.grid_x, 256, fs.smem_x, s0>>>(g, fp, static_cast<const R*>(w.grid), tw,
+                                                  static_cast<C*>(w.spec1), fs.lx);
+    k_fft_y<R><<<dim3(g.nc + 1, fs.grid_y_z), 256, fs.smem_y, s0>>>(g, fp, static_cast<const C*>(w.spec1), tw,
+                                                                   static_cast<C*>(w.spec2), fs.ly);
+    k_fft_z<R><<<fs.grid_z, 256, fs.smem_z, s0>>>(g, fp, static_cast<const C*>(w.spec2), tw, w.tab, w.tabv,
+                                                  static_cast<const R*>(w.tabr), static_cast<C*>(w.spec3),
+                                                  w.part + w.off_recip, fs.lz);
+    k_fft_iy<R><<<fs.grid_iy, 256, fs.smem_iy, s0>>>(g, fp, static_cast<const C*>(w.spec3), tw,
+                                                     static_cast<C*>(w.spec4), fs.liy);
+    k_fft_ix<R><<<fs.grid_ix, 256, fs.smem_ix, s0>>>(g, fp, static_cast<const C*>(w.spec4), tw,
+                                                     static_cast<R*>(w.h), fs.lix);
+    rec(ev, 2, false, s0);
+    log->kernels += 6;
+
+    cudaStreamWaitEvent(s0, evJoin, 0);
+    rec(ev, 3, true, s0);
+    k_gather<R><<<w.nblk_gather, kGatherThreads, 0, s0>>>(g, w.tstart, sq, sw, w.sb,
+                                                          static_cast<const R*>(w.h), F);
+    rec(ev, 3, false, s0);
+    log->kernels += 1;
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t enqueue_totals(const Geo& g, const Work& w, bool dpd, cudaStream_t s, LaunchLog* log) {
+    k_totals<<<1, 256, 0, s>>>(g, w.part, w.off_q, g.nbin, w.off_real, w.nblk_real, w.off_recip, w.nblk_conv,
+                               w.off_dpd, dpd ? w.nblk_dpd : 0, w.off_kin, dpd ? w.nblk_kin : 0, w.Edev);
+    log->kernels += 1;
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t enqueue_dpd_forces(const Work& w, const DpdDev& d, cudaStream_t s, Events* ev, LaunchLog* log) {
+    using V = typename V4<R>::T;
+    const int blocks = (d.N + 255) / 256 > 0 ? (d.N + 255) / 256 : 1;
+    rec(ev, 7, true, s);
+    k_cell_count<R><<<blocks, 256, 0, s>>>(d.N, d.ncd, d.L, static_cast<const R*>(d.pos), d.ckey, d.ccount);
+    k_cell_scan<<<1, 1024, 0, s>>>(d.ncells, d.ccount, d.cstart, d.ccur);
+    k_cell_scatter<R><<<blocks, 256, 0, s>>>(d.N, d.L, static_cast<const R*>(d.pos), static_cast<const R*>(d.v0),
+                                             d.type, d.ckey, d.ccur, static_cast<V*>(d.sp), static_cast<V*>(d.sv));
+    rec(ev, 7, false, s);
+    rec(ev, 5, true, s);
+    k_dpd<R><<<w.nblk_dpd, 256, 0, s>>>(d, static_cast<const V*>(d.sp), static_cast<const V*>(d.sv), d.ckey,
+                                        d.cstart, static_cast<const R*>(d.atab), static_cast<const R*>(d.pos),
+                                        d.bptr, d.blist, d.step_dev, static_cast<R*>(d.F),
+                                        w.part + w.off_dpd);
+    rec(ev, 5, false, s);
+    log->kernels += 4;
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t enqueue_vv_pre(const DpdDev& d, cudaStream_t s, LaunchLog* log) {
+    const int blocks = (3 * d.N + 255) / 256 > 0 ? (3 * d.N + 255) / 256 : 1;
+    k_vv_pre<R><<<blocks, 256, 0, s>>>(d.N, (R)d.lambda_vv, (R)d.dt, static_cast<R*>(d.pos),
+                                       static_cast<R*>(d.vel), static_cast<R*>(d.v0),
+                                       static_cast<const R*>(d.F), d.step_dev);
+    log->kernels += 1;
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t enqueue_vv_post(const Work& w, const DpdDev& d, cudaStream_t s, LaunchLog* log) {
+    k_vv_post<R><<<w.nblk_kin, 256, 0, s>>>(d.N, (R)d.dt, static_cast<R*>(d.vel), static_cast<const R*>(d.F),
+                                            w.part + w.off_kin);
+    log->kernels += 1;
+    return cudaGetLastError();
+}
+
+#define ENUF_INSTANTIATE(R)                                                                                  \
+    template cudaError_t configure_kernels<R>(int);                                                          \
+    template int spread_smem<R>(const Geo&);                                                                 \
+    template cudaError_t enqueue_enuf<R>(const Geo&, const FftShape&, const FftPlanDev&, const Work&,        \
+                                         const EvalArgs&, cudaStream_t, cudaStream_t, cudaEvent_t,           \
+                                         cudaEvent_t, Events*, LaunchLog*);                                  \
+    template cudaError_t enqueue_totals<R>(const Geo&, const Work&, bool, cudaStream_t, LaunchLog*);         \
+    template cudaError_t enqueue_dpd_forces<R>(const Work&, const DpdDev&, cudaStream_t, Events*,            \
+                                               LaunchLog*);                                                  \
+    template cudaError_t enqueue_vv_pre<R>(const DpdDev&, cudaStream_t, LaunchLog*);                         \
+    template cudaError_t enqueue_vv_post<R>(const Work&, const DpdDev&, cudaStream_t, LaunchLog*);
+
+}  // namespace enuf

@@ -1,0 +1,185 @@
+// enuf_fft.cuh -- batched shared-memory FFT of length n = 2^a 3^b 5^c (n <= 512).
+//
+// The 3-D transforms of the NFFT (the "standard FFT" of Sec. 3.3 inside the
+// transposed and conjugated NFFT, Eq. 13-14) are done one dimension at a time;
+// each CTA loads a batch of lines into shared memory and runs this Stockham
+// auto-sort FFT on all of them. Stage s with radix R combines R sub-transforms
+// of length Ns (product of the earlier radices): butterfly j of a line reads
+// x[j + r n/R], twiddles element r by w^{r k n/(Ns R)} (k = j mod Ns,
+// w = e^{-+2 pi i/n}), does an R-point DFT and writes the results to
+// (j - k) R + k + m Ns. After the last stage the line is in natural order.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace enuf {
+
+template <typename R> struct Cx;
+template <> struct Cx<float> { using T = float2; };
+template <> struct Cx<double> { using T = double2; };
+
+struct FftPlanDev {
+    int n;
+    int nst;
+    int rad[8];
+};
+
+template <typename C>
+__device__ __forceinline__ C cmul(C a, C b) {
+    C r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+template <typename C>
+__device__ __forceinline__ C cadd(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <typename C>
+__device__ __forceinline__ C csub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+// multiply by -i (forward) or +i (inverse): the rotation of the 4-point DFT
+template <typename C, bool INV>
+__device__ __forceinline__ C rot_i(C a) {
+    C r;
+    if (INV) { r.x = -a.y; r.y = a.x; }   // +i a
+    else     { r.x = a.y;  r.y = -a.x; }  // -i a
+    return r;
+}
+
+template <typename R, int RAD, bool INV> struct SmallDft;
+
+template <typename R, bool INV> struct SmallDft<R, 2, INV> {
+    template <typename C> __device__ __forceinline__ static void run(C* v) {
+        C a = cadd(v[0], v[1]), b = csub(v[0], v[1]);
+        v[0] = a; v[1] = b;
+    }
+};
+
+template <typename R, bool INV> struct SmallDft<R, 4, INV> {
+    template <typename C> __device__ __forceinline__ static void run(C* v) {
+        C s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+        C s13 = cadd(v[1], v[3]), d13 = rot_i<C, INV>(csub(v[1], v[3]));
+        v[0] = cadd(s02, s13);
+        v[2] = csub(s02, s13);
+        v[1] = cadd(d02, d13);
+        v[3] = csub(d02, d13);
+    }
+};
+
+template <typename R, bool INV> struct SmallDft<R, 8, INV> {
+    template <typename C> __device__ __forceinline__ static void run(C* v) {
+        // even / odd 4-point DFTs, then combine with w8^m
+        C e[4] = {v[0], v[2], v[4], v[6]};
+        C o[4] = {v[1], v[3], v[5], v[7]};
+        SmallDft<R, 4, INV>::run(e);
+        SmallDft<R, 4, INV>::run(o);
+        const R h = (R)0.70710678118654752440;
+        C t1, t3;
+        // w8 = (1 -+ i)/sqrt2 ; w8^2 = -+ i ; w8^3 = (-1 -+ i)/sqrt2
+        if (INV) {
+            t1.x = h * (o[1].x - o[1].y); t1.y = h * (o[1].x + o[1].y);
+            t3.x = -h * (o[3].x + o[3].y); t3.y = h * (o[3].x - o[3].y);
+        } else {
+            t1.x = h * (o[1].x + o[1].y); t1.y = h * (o[1].y - o[1].x);
+            t3.x = h * (o[3].y - o[3].x); t3.y = -h * (o[3].x + o[3].y);
+        }
+        C t2 = rot_i<C, INV>(o[2]);
+        v[0] = cadd(e[0], o[0]); v[4] = csub(e[0], o[0]);
+        v[1] = cadd(e[1], t1);   v[5] = csub(e[1], t1);
+        v[2] = cadd(e[2], t2);   v[6] = csub(e[2], t2);
+        v[3] = cadd(e[3], t3);   v[7] = csub(e[3], t3);
+    }
+};
+
+template <typename R, bool INV> struct SmallDft<R, 3, INV> {
+    template <typename C> __device__ __forceinline__ static void run(C* v) {
+        const R s3 = (R)0.86602540378443864676;  // sqrt(3)/2
+        C t = cadd(v[1], v[2]);
+        C d = csub(v[1], v[2]);
+        C m;
+        m.x = v[0].x - (R)0.5 * t.x;
+        m.y = v[0].y - (R)0.5 * t.y;
+        // forward: y1 = m - i s3 d, y2 = m + i s3 d ; inverse swaps the sign of i
+        C id = rot_i<C, INV>(d);   // -i d (fwd) or +i d (inv)
+        v[0] = cadd(v[0], t);
+        v[1].x = m.x + s3 * id.x; v[1].y = m.y + s3 * id.y;
+        v[2].x = m.x - s3 * id.x; v[2].y = m.y - s3 * id.y;
+    }
+};
+
+template <typename R, bool INV> struct SmallDft<R, 5, INV> {
+    template <typename C> __device__ __forceinline__ static void run(C* v) {
+        const R c1 = (R)0.30901699437494742410, c2 = (R)-0.80901699437494742410;
+        const R s1 = (R)0.95105651629515357212, s2 = (R)0.58778525229247312917;
+        C a1 = cadd(v[1], v[4]), b1 = csub(v[1], v[4]);
+        C a2 = cadd(v[2], v[3]), b2 = csub(v[2], v[3]);
+        C m1, m2, u1, u2;
+        m1.x = v[0].x + c1 * a1.x + c2 * a2.x; m1.y = v[0].y + c1 * a1.y + c2 * a2.y;
+        m2.x = v[0].x + c2 * a1.x + c1 * a2.x; m2.y = v[0].y + c2 * a1.y + c1 * a2.y;
+        u1.x = s1 * b1.x + s2 * b2.x; u1.y = s1 * b1.y + s2 * b2.y;
+        u2.x = s2 * b1.x - s1 * b2.x; u2.y = s2 * b1.y - s1 * b2.y;
+        C iu1 = rot_i<C, INV>(u1), iu2 = rot_i<C, INV>(u2);  // -i u (fwd)
+        v[0].x = v[0].x + a1.x + a2.x; v[0].y = v[0].y + a1.y + a2.y;
+        v[1] = cadd(m1, iu1); v[4] = csub(m1, iu1);
+        v[2] = cadd(m2, iu2); v[3] = csub(m2, iu2);
+    }
+};
+
+// One Stockham stage over nlines lines (line l at offset l*ls).
+template <typename R, int RAD, bool INV>
+__device__ __forceinline__ void fft_stage(const typename Cx<R>::T* __restrict__ src,
+                                          typename Cx<R>::T* __restrict__ dst,
+                                          const typename Cx<R>::T* __restrict__ tw,
+                                          int n, int Ns, int nlines, int ls) {
+    using C = typename Cx<R>::T;
+    const int m = n / RAD;
+    const int tstep = n / (Ns * RAD);
+    const int total = nlines * m;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int line = idx / m;
+        const int j = idx - line * m;
+        const int k = j % Ns;
+        const C* s = src + line * ls;
+        C* d = dst + line * ls;
+        C v[RAD];
+#pragma unroll
+        for (int r = 0; r < RAD; ++r) v[r] = s[j + r * m];
+        if (k != 0) {
+#pragma unroll
+            for (int r = 1; r < RAD; ++r) {
+                C w = tw[r * k * tstep];
+                if (INV) w.y = -w.y;
+                v[r] = cmul(v[r], w);
+            }
+        }
+        SmallDft<R, RAD, INV>::run(v);
+        const int base = (j - k) * RAD + k;
+#pragma unroll
+        for (int r = 0; r < RAD; ++r) d[base + r * Ns] = v[r];
+    }
+}
+
+// Transform nlines lines held in b0; b1 is scratch of the same size. Returns
+// the buffer holding the result. Contains __syncthreads (call from all threads).
+template <typename R, bool INV>
+__device__ typename Cx<R>::T* fft_lines(typename Cx<R>::T* b0, typename Cx<R>::T* b1,
+                                        const typename Cx<R>::T* tw, const FftPlanDev& fp,
+                                        int nlines, int ls) {
+    using C = typename Cx<R>::T;
+    C* src = b0;
+    C* dst = b1;
+    int Ns = 1;
+    for (int st = 0; st < fp.nst; ++st) {
+        const int rad = fp.rad[st];
+        switch (rad) {
+            case 8: fft_stage<R, 8, INV>(src, dst, tw, fp.n, Ns, nlines, ls); break;
+            case 4: fft_stage<R, 4, INV>(src, dst, tw, fp.n, Ns, nlines, ls); break;
+            case 2: fft_stage<R, 2, INV>(src, dst, tw, fp.n, Ns, nlines, ls); break;
+            case 3: fft_stage<R, 3, INV>(src, dst, tw, fp.n, Ns, nlines, ls); break;
+            default: fft_stage<R, 5, INV>(src, dst, tw, fp.n, Ns, nlines, ls); break;
+        }
+        __syncthreads();
+        C* t = src; src = dst; dst = t;
+        Ns *= rad;
+    }
+    return src;
+}
+
+}  // namespace enuf

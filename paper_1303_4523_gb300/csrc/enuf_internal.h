@@ -1,0 +1,121 @@
+// enuf_internal.h -- plan layout shared by the C-ABI layer and the kernel
+// translation units (one per precision).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+#include "enuf_fft.cuh"
+
+namespace enuf {
+
+// Geometry and constants every kernel needs, passed by value.
+struct Geo {
+    int n;        // oversampled grid per dimension (sigma_s * M)
+    int nc;       // kept modes per side, |k_t| <= nc
+    int K;        // 2 nc + 1
+    int p;        // window cutoff (2p taps per dimension)
+    int T;        // spreading tile edge (grid points)
+    int ntd;      // tiles per dimension
+    int ntiles;   // ntd^3
+    int rs;       // real-space stencil radius in tiles
+    int nbin;     // blocks of the charged-bead binning
+    int chunk;    // beads per binning block
+    int kmask;
+    int pad0;
+    double L, alpha, beta, kappa, rc;
+    double b;      // Gaussian window parameter 2 sigma p / ((2 sigma - 1) pi)
+    double wnorm;  // (pi b)^{-1/2}
+};
+
+// Lines per CTA of each FFT pass.
+struct FftShape {
+    int lx;    // complex lines (pairs of real rows) per CTA, forward x
+    int ly;    // lines per CTA, forward y
+    int lz;    // lines per CTA, z pass (forward + convolve + 3 inverses)
+    int liy;   // lines per CTA, inverse y
+    int lix;   // complex lines per CTA, inverse x
+    int smem_x, smem_y, smem_z, smem_iy, smem_ix;   // dynamic smem bytes
+    int grid_x, grid_y_z, grid_z, grid_iy, grid_ix; // CTAs (grid_y_z: z-chunks of the y pass)
+};
+
+// Device workspace of one plan (all pointers device memory, one allocation).
+struct Work {
+    // charged binning
+    int* key;        // [n_max] tile of each bead, -1 if uncharged
+    int* bhist;      // [nbin][ntiles]
+    int* boff;       // [nbin][ntiles]
+    int* tstart;     // [ntiles + 1]
+    void* sq;        // real4 [n_max]  wrapped x, y, z, q (sorted)
+    void* sw;        // real4 [n_max]  fractional grid coordinates, original index bits
+    int* sb;         // [n_max]  packed base grid index
+    // grids and spectra
+    void* grid;      // real [n^3]
+    void* spec1;     // cplx [n][nc+1][n]      after forward x   ([z][kx][y])
+    void* spec2;     // cplx [nc+1][K][n]      after forward y   ([kx][ky][z])
+    void* spec3;     // cplx [3][n][nc+1][K]   after z pass      ([a][z][kx][ky])
+    void* spec4;     // cplx [3][n][n][nc+1]   after inverse y   ([a][z][y][kx])
+    void* h;         // real [3][n^3]          conjugated-NFFT fields
+    double* tab;     // [nc+1][K][K] influence/deconvolution table D(k) (0 outside the mode set)
+    double* tabv;    // [nc+1][K][K] D(k) times the virial weight 1 - 2 pi^2 k^2/(alpha L)^2
+    void* tabr;      // real copy of tab
+    void* tw;        // cplx [n] twiddles e^{-2 pi i t/n}
+    double* part;    // per-block partial sums
+    double* Edev;    // [16] reduced totals
+    // partial-sum segments (offsets into part, in doubles)
+    int off_q, off_real, off_recip, off_dpd, off_kin;
+    int nblk_real, nblk_conv, nblk_dpd, nblk_kin, nblk_gather;
+};
+
+// Arguments of one electrostatics evaluation.
+struct EvalArgs {
+    int N;
+    const void* pos;   // real [N][3] (device)
+    const void* q;     // real [N]
+    void* F;           // real [N][3]
+    bool zeroF;        // overwrite F (pure electrostatics) vs add into it (DPD step)
+};
+
+// DPD device state and cell list (one per system).
+struct DpdDev {
+    int N, ntypes, ncd, ncells;
+    double L, gamma, sigma, dt, lambda_vv, K_bond, r0_bond;
+    uint64_t seed;
+    void* pos; void* vel; void* v0; void* F; void* q;   // real
+    int* type;
+    void* atab;        // real [ntypes^2]
+    int* bptr; int* blist;   // per-bead bond lists (CSR)
+    int* ckey; int* ccount; int* cstart; int* ccur;
+    void* sp; void* sv;      // real4 [N] sorted: (x, y, z, orig) and (v0, type)
+    uint64_t* step_dev;      // device copy of the step counter
+};
+
+constexpr int kStageCount = 8;
+
+// Host-side record of the launches one enqueue made (for the launch count).
+struct LaunchLog {
+    int kernels = 0;
+};
+
+struct Events {
+    cudaEvent_t start[kStageCount];
+    cudaEvent_t stop[kStageCount];
+    bool on = false;
+};
+
+template <typename R> cudaError_t configure_kernels(int max_smem);
+template <typename R> int spread_smem(const Geo& g);
+template <typename R>
+cudaError_t enqueue_enuf(const Geo& g, const FftShape& fs, const FftPlanDev& fp, const Work& w,
+                         const EvalArgs& a, cudaStream_t s0, cudaStream_t s1, cudaEvent_t evFork,
+                         cudaEvent_t evJoin, Events* ev, LaunchLog* log);
+template <typename R>
+cudaError_t enqueue_totals(const Geo& g, const Work& w, bool dpd, cudaStream_t s, LaunchLog* log);
+template <typename R>
+cudaError_t enqueue_dpd_forces(const Work& w, const DpdDev& d, cudaStream_t s, Events* ev, LaunchLog* log);
+template <typename R>
+cudaError_t enqueue_vv_pre(const DpdDev& d, cudaStream_t s, LaunchLog* log);
+template <typename R>
+cudaError_t enqueue_vv_post(const Work& w, const DpdDev& d, cudaStream_t s, LaunchLog* log);
+
+}  // namespace enuf

@@ -1,0 +1,144 @@
+"""GPU parity of the DPD step (Table 2) against the FP64 CPU oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as orc
+from paper_1303_4523_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def enuf():
+    from paper_1303_4523_gb300 import build
+    build.build()
+    from paper_1303_4523_gb300 import enuf as e
+    return e
+
+
+def _system(L=8.0, chains=3, f=0.5, valency=1):
+    s = W.polyelectrolyte(L=L, n_chains=chains, chain_len=20, f=f, salt_fraction=0.1, valency=valency,
+                          seed_offset=40)
+    return s
+
+
+def _prep(prec, s):
+    cast = (lambda a: np.asarray(a, np.float32).astype(np.float64)) if prec == "fp32" else (
+        lambda a: np.asarray(a, np.float64))
+    return cast(s.pos), cast(s.vel), cast(s.q)
+
+
+def _make(enuf, prec, s, pos, vel, q, dp):
+    P = dict(L=s.L, M=s.M, **s.params)
+    plan = enuf.Plan(enuf.make_params(prec=prec, **P), s.N)
+    sysm = enuf.DpdSystem(plan, dp["a"], dp["gamma"], dp["sigma"], dp["dt"], pos, vel, s.types, q, s.bonds,
+                          lambda_vv=dp["lambda_vv"], K_bond=dp["K_bond"], r0_bond=dp["r0_bond"], seed=dp["seed"])
+    Po = orc.EwaldParams(fp32_cut=1 if prec == "fp32" else 0, **P)
+    Do = orc.DpdParams(**dp)
+    return plan, sysm, Po, Do
+
+
+def _rel(a, b):
+    return math.sqrt(((a - b) ** 2).sum() / (b ** 2).sum())
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 1e-5)])
+def test_initial_force_parity(enuf, prec, tol):
+    """Table 2 steps 3-5 at step 0: DPD C + D + R/sqrt(dt) + bonds + electrostatics."""
+    s = _system()
+    dp = W.dpd_params(5)
+    pos, vel, q = _prep(prec, s)
+    plan, sysm, Po, Do = _make(enuf, prec, s, pos, vel, q, dp)
+    _, _, F, step = sysm.get_state()
+    Fr, Er = orc.total_forces(Po, Do, pos, vel, s.types, q, s.bonds, step=0)
+    assert step == 0
+    assert _rel(F.astype(np.float64), Fr) < tol
+    sysm.close()
+    plan.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_trajectory_parity(enuf, prec):
+    """Three modified velocity-Verlet steps; positions, velocities, forces and
+    energies against the oracle's Table 2 integrator."""
+    s = _system(valency=2)
+    dp = W.dpd_params(5)
+    pos, vel, q = _prep(prec, s)
+    plan, sysm, Po, Do = _make(enuf, prec, s, pos, vel, q, dp)
+    F0, _ = orc.total_forces(Po, Do, pos, vel, s.types, q, s.bonds, step=0)
+    pr, vr, Fr, st, Er = orc.dpd_run(Po, Do, pos, vel, F0, s.types, q, s.bonds, step=0, nsteps=3)
+    E = sysm.step(3, want_energy=True)
+    p, v, F, step = sysm.get_state()
+    assert step == st == 3
+    tp, tv, tF, tE = (1e-12, 1e-10, 1e-9, 1e-10) if prec == "fp64" else (1e-6, 2e-5, 2e-4, 1e-5)
+    assert np.abs(p - pr).max() < tp * s.L
+    assert _rel(v.astype(np.float64), vr) < tv
+    assert _rel(F.astype(np.float64), Fr) < tF
+    scale = max(abs(Er[0]), abs(Er[1]), abs(Er[2]))
+    for k in range(4):
+        assert abs(E[k] - Er[k]) < tE * scale, (k, E[:6], Er)
+    assert abs(E[4] - Er[4]) < tE * abs(Er[4])
+    assert abs(E[5] - Er[5]) < tE * max(abs(Er[5]), 1.0)
+    assert abs(E[6] - 0.5 * (vr ** 2).sum()) < tE * 0.5 * (vr ** 2).sum()
+    sysm.close()
+    plan.close()
+
+
+def test_restart_resumes_exactly(enuf):
+    s = _system()
+    dp = W.dpd_params(5)
+    pos, vel, q = _prep("fp64", s)
+    plan, sysm, _, _ = _make(enuf, "fp64", s, pos, vel, q, dp)
+    sysm.step(4)
+    pa, va, Fa, sa = sysm.get_state()
+    sysm.set_state(pos, vel, None, 0)
+    sysm.step(2)
+    ck = sysm.get_state()
+    sysm.set_state(ck[0], ck[1], ck[2], ck[3])
+    sysm.step(2)
+    pb, vb, Fb, sb = sysm.get_state()
+    assert sa == sb == 4
+    assert np.abs(pa - pb).max() < 1e-12 and np.abs(va - vb).max() < 1e-10
+    sysm.close()
+    plan.close()
+
+
+def test_bad_inputs_are_rejected(enuf):
+    s = _system()
+    dp = W.dpd_params(5)
+    P = dict(L=s.L, M=s.M, **s.params)
+    plan = enuf.Plan(enuf.make_params(**P), s.N)
+    bad_types = s.types.copy()
+    bad_types[3] = 99
+    with pytest.raises(enuf.EnufError):
+        enuf.DpdSystem(plan, dp["a"], dp["gamma"], dp["sigma"], dp["dt"], s.pos, s.vel, bad_types, s.q, s.bonds)
+    bad_bonds = s.bonds.copy()
+    bad_bonds[0, 1] = s.N + 5
+    with pytest.raises(enuf.EnufError):
+        enuf.DpdSystem(plan, dp["a"], dp["gamma"], dp["sigma"], dp["dt"], s.pos, s.vel, s.types, s.q, bad_bonds)
+    plan.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 1e-5)])
+def test_full_size_polyelectrolyte_sampled(enuf, prec, tol):
+    """The bench workload (81000 beads, L = 30): initial ENUF-DPD force of 256
+    sampled beads against the oracle bead by bead."""
+    s = W.polyelectrolyte()
+    dp = W.dpd_params(5)
+    pos, vel, q = _prep(prec, s)
+    plan, sysm, Po, Do = _make(enuf, prec, s, pos, vel, q, dp)
+    _, _, F, _ = sysm.get_state()
+    rng = np.random.default_rng(3)
+    sample = np.sort(np.concatenate([rng.choice(np.nonzero(q)[0], 128, replace=False),
+                                     rng.choice(np.nonzero(q == 0)[0], 128, replace=False),
+                                     s.bonds[:8].ravel()]))
+    sample = np.unique(sample)
+    Fd, _ = orc.dpd_forces(Po, Do, pos, vel, s.types, s.bonds, step=0, sample=sample)
+    Fe, _, _ = orc.electrostatics(Po, pos, q, recip="enuf", sample=sample)
+    Fr = Fd + Fe
+    assert _rel(F[sample].astype(np.float64), Fr) < tol
+    sysm.close()
+    plan.close()

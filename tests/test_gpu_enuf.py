@@ -1,0 +1,272 @@
+"""GPU parity of the ENUF electrostatics path against the FP64 CPU oracle.
+
+Every comparison calls the CUDA path through the C ABI (libenuf.so via the
+ctypes binding) and the oracle on the same seeded inputs. Tolerances: FP64
+relative RMS force 1e-11 and relative energy 1e-12; FP32 relative RMS force
+1e-5 and relative energy 1e-6 (the stated targets of the FP32 path).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as orc
+from paper_1303_4523_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": dict(F=1e-11, E=1e-12, stage=1e-12), "fp32": dict(F=1e-5, E=1e-6, stage=1e-5)}
+
+
+@pytest.fixture(scope="module")
+def enuf():
+    from paper_1303_4523_gb300 import build
+    build.build()
+    from paper_1303_4523_gb300 import enuf as e
+    return e
+
+
+def _inputs(prec, pos, q):
+    """Inputs as the GPU sees them (float32-rounded for FP32) and as doubles."""
+    if prec == "fp32":
+        pos = np.asarray(pos, np.float32).astype(np.float64)
+        q = np.asarray(q, np.float32).astype(np.float64)
+    return np.asarray(pos, np.float64), np.asarray(q, np.float64)
+
+
+def _gpu(enuf, prec, P, pos, q, n_max=None):
+    dt = torch.float32 if prec == "fp32" else torch.float64
+    plan = enuf.Plan(enuf.make_params(prec=prec, **P), n_max if n_max is not None else len(q))
+    tp = torch.tensor(pos, dtype=dt, device="cuda").reshape(-1, 3).contiguous()
+    tq = torch.tensor(q, dtype=dt, device="cuda").contiguous()
+    F = torch.full_like(tp, float("nan"))
+    E, Wv = plan.energy_forces(tp, tq, F)
+    return plan, F.double().cpu().numpy(), E, Wv
+
+
+def _oparams(prec, P):
+    """Oracle parameters: the GPU-only tiling choice does not change the result."""
+    return orc.EwaldParams(fp32_cut=1 if prec == "fp32" else 0, **{k: v for k, v in P.items() if k != "tile"})
+
+
+def _ref(prec, P, pos, q, sample=None):
+    Po = _oparams(prec, P)
+    F, E, Wv = orc.electrostatics(Po, pos, q, recip="enuf", sample=sample)
+    return F, E, Wv
+
+
+def _rel_rms(F, R):
+    den = (R ** 2).sum()
+    return math.sqrt(((F - R) ** 2).sum() / den) if den > 0 else math.sqrt((F ** 2).sum())
+
+
+def _check(prec, F, E, Wv, Fr, Er, Wr):
+    t = TOL[prec]
+    assert np.all(np.isfinite(F))
+    assert _rel_rms(F, Fr) < t["F"], _rel_rms(F, Fr)
+    scale = max(abs(Er[0]), abs(Er[1]), abs(Er[2]), 1e-300)
+    for k in range(4):
+        assert abs(E[k] - Er[k]) < t["E"] * scale, (k, E, Er)
+    assert abs(Wv - Wr) < 10 * t["E"] * max(abs(Wr), scale)
+
+
+def _sys_small(pset):
+    s = W.electrolyte_small(pset)
+    return dict(L=s.L, M=s.M, **s.params), s.pos, s.q
+
+
+CASES = {
+    # name: (params, N, L, n_charged, seed)
+    "paper_set_M16_p2": ("paper", None),
+    "baseline_set_M16_p4": ("baseline", None),
+    "radix3_M24_p3": (dict(L=15.0, alpha=0.975, r_cut=3.0, beta=4.0, kappa=1.1, M=24, p=3), (3000, 15.0, 600)),
+    "radix5_M20_p5_spherical": (dict(L=12.5, alpha=1.1, r_cut=3.0, beta=1.125, kappa=0.8, M=20, p=5, kmask=1),
+                                (2500, 12.5, 400)),
+    "two_tiles_M8_p4": (dict(L=6.0, alpha=1.2, r_cut=3.0, beta=4.0, kappa=1.0, M=8, p=4), (300, 6.0, 120)),
+    "one_tile_M4_p2": (dict(L=6.0, alpha=1.2, r_cut=3.0, beta=0.0, kappa=1.0, M=4, p=2), (100, 6.0, 40)),
+    "p8_M32_point_charges": (dict(L=10.0, alpha=1.5, r_cut=5.0, beta=0.0, kappa=1.0, M=32, p=8),
+                             (1000, 10.0, 200)),
+    "tile12_M36_p6": (dict(L=20.0, alpha=0.8, r_cut=4.0, beta=4.0, kappa=1.1, M=36, p=6, tile=12),
+                      (4000, 20.0, 500)),
+}
+
+
+def _case(name):
+    spec, shape = CASES[name]
+    if isinstance(spec, str):
+        return _sys_small(spec)
+    N, L, nq = shape
+    s = W.electrolyte(N, L, n_charged=nq, seed_offset=50 + len(name))
+    return spec, s.pos, s.q
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", list(CASES))
+def test_energy_forces_parity(enuf, name, prec):
+    P, pos, q = _case(name)
+    pos, q = _inputs(prec, pos, q)
+    plan, F, E, Wv = _gpu(enuf, prec, P, pos, q)
+    Fr, Er, Wr = _ref(prec, P, pos, q)
+    _check(prec, F, E, Wv, Fr, Er, Wr)
+    # uncharged beads get exactly zero force
+    assert np.all(F[q == 0] == 0.0)
+    plan.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_spread_grid_and_fields_match_oracle(enuf, prec):
+    """Stage parity: the spread grid (Eq. 14, first half) and the three
+    conjugated-NFFT fields before the gather (Eq. 25)."""
+    P, pos, q = _sys_small("baseline")
+    pos, q = _inputs(prec, pos, q)
+    plan, F, E, Wv = _gpu(enuf, prec, P, pos, q)
+    grid = plan.debug_buffer(enuf.ENUF_BUF_GRID).astype(np.float64)
+    h = plan.debug_buffer(enuf.ENUF_BUF_FIELD).astype(np.float64)
+    Po = _oparams(prec, P)
+    _, _, g_ref, h_ref = orc.recip_enuf(Po, pos, q, want_grid=True, want_h=True)
+    t = TOL[prec]["stage"]
+    assert np.abs(grid - g_ref).max() < t * np.abs(g_ref).max()
+    assert np.abs(h - h_ref).max() < 10 * t * np.abs(h_ref).max()
+    plan.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_edge_cases(enuf, prec):
+    P = dict(L=8.0, alpha=1.0, r_cut=3.0, beta=4.0, kappa=1.0, M=16, p=4)
+    rng = np.random.default_rng(4)
+    # (a) no beads at all
+    plan = enuf.Plan(enuf.make_params(prec=prec, **P), 10)
+    dt = torch.float32 if prec == "fp32" else torch.float64
+    e = torch.empty((0, 3), dtype=dt, device="cuda")
+    E, Wv = plan.energy_forces(e, torch.empty(0, dtype=dt, device="cuda"), torch.empty_like(e))
+    assert np.all(E == 0.0) and Wv == 0.0
+    plan.close()
+    # (b) all uncharged, (c) a single charge, (d) net charge with positions
+    # far outside the box, (e) fewer beads than the plan's capacity
+    pos = rng.uniform(-20, 30, (257, 3))
+    cases = [np.zeros(257), np.eye(1, 257, 100)[0] * 2.0,
+             np.where(rng.uniform(size=257) < 0.3, rng.choice([-1.0, 1.0, 2.0], 257), 0.0)]
+    for qq in cases:
+        p_, q_ = _inputs(prec, pos, qq)
+        plan, F, E, Wv = _gpu(enuf, prec, P, p_, q_, n_max=1000)
+        Fr, Er, Wr = _ref(prec, P, p_, q_)
+        if np.all(qq == 0):
+            assert np.all(F == 0.0) and np.all(E == 0.0)
+        elif np.count_nonzero(qq) == 1:
+            # a lone charge feels only the NFFT's spurious self-force (exactly 0 in
+            # the Ewald sum): compare on the scale of a unit pair force at r = 1
+            f0 = P["kappa"] * 4.0
+            assert np.abs(F - Fr).max() < TOL[prec]["F"] * f0 and np.abs(Fr).max() < 1e-3 * f0
+            assert np.allclose(E, Er, rtol=TOL[prec]["E"], atol=TOL[prec]["E"] * abs(Er[2]))
+        else:
+            _check(prec, F, E, Wv, Fr, Er, Wr)
+        plan.close()
+
+
+def test_n_above_capacity_is_rejected(enuf):
+    P = dict(L=8.0, alpha=1.0, r_cut=3.0, beta=4.0, kappa=1.0, M=16, p=4)
+    plan = enuf.Plan(enuf.make_params(**P), 10)
+    x = torch.zeros((11, 3), dtype=torch.float64, device="cuda")
+    with pytest.raises(enuf.EnufError) as ei:
+        plan.energy_forces(x, torch.zeros(11, dtype=torch.float64, device="cuda"), x.clone())
+    assert ei.value.status == 1
+    plan.close()
+
+
+def test_repeat_and_pointer_change(enuf):
+    """Graph replay gives the same result; new pointers trigger a new capture."""
+    P, pos, q = _sys_small("baseline")
+    plan = enuf.Plan(enuf.make_params(**P), len(q))
+    tp = torch.tensor(pos, device="cuda")
+    tq = torch.tensor(q, device="cuda")
+    F1, F2 = torch.empty_like(tp), torch.empty_like(tp)
+    E1, _ = plan.energy_forces(tp, tq, F1)
+    E2, _ = plan.energy_forces(tp, tq, F2)
+    E3, _ = plan.energy_forces(tp.clone(), tq.clone(), F1)
+    assert np.allclose(E1, E2, rtol=1e-14, atol=0) and np.allclose(E1, E3, rtol=1e-14, atol=0)
+    assert torch.allclose(F1, F2, rtol=1e-12, atol=1e-14)
+    plan.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_host_buffer_entry_point(enuf, prec):
+    P, pos, q = _sys_small("paper")
+    pos, q = _inputs(prec, pos, q)
+    plan, F, E, Wv = _gpu(enuf, prec, P, pos, q)
+    npd = np.float32 if prec == "fp32" else np.float64
+    Fh = np.empty((len(q), 3), npd)
+    Eh, Wh = plan.energy_forces_host(pos.astype(npd), q.astype(npd), Fh)
+    assert np.allclose(Fh, F, rtol=1e-5 if prec == "fp32" else 1e-12, atol=1e-6 if prec == "fp32" else 1e-13)
+    assert np.allclose(Eh, E, rtol=1e-6 if prec == "fp32" else 1e-12)
+    plan.close()
+
+
+def test_stage_timing(enuf):
+    P, pos, q = _sys_small("baseline")
+    plan = enuf.Plan(enuf.make_params(**P), len(q))
+    plan.enable_timing(True)
+    tp = torch.tensor(pos, device="cuda")
+    tq = torch.tensor(q, device="cuda")
+    F = torch.empty_like(tp)
+    plan.energy_forces(tp, tq, F)
+    for st in ("bin", "spread", "fft", "gather", "real", "all"):
+        assert plan.stage_time(st) > 0.0
+    assert plan.launches() == 12
+    plan.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batch_equals_single_plans(enuf, prec):
+    systems = [W.electrolyte(N, seed_offset=70 + i) for i, N in enumerate([1500, 3000, 6000, 2000])]
+    dt = torch.float32 if prec == "fp32" else torch.float64
+    params, pos_l, q_l, F_l, singles = [], [], [], [], []
+    for s in systems:
+        P = dict(L=s.L, M=s.M, **s.params)
+        params.append(enuf.make_params(prec=prec, **P))
+        tp = torch.tensor(s.pos, dtype=dt, device="cuda")
+        tq = torch.tensor(s.q, dtype=dt, device="cuda")
+        pos_l.append(tp)
+        q_l.append(tq)
+        F_l.append(torch.empty_like(tp))
+        pl = enuf.Plan(params[-1], s.N)
+        Fs = torch.empty_like(tp)
+        Es, _ = pl.energy_forces(tp, tq, Fs)
+        singles.append((Fs.double().cpu().numpy(), Es))
+        pl.close()
+    b = enuf.Batch(params, [s.N for s in systems])
+    E = b.energy_forces(pos_l, q_l, F_l)
+    E2 = b.energy_forces(pos_l, q_l, F_l)
+    assert b.launches() == 12 * len(systems)
+    for k, (Fs, Es) in enumerate(singles):
+        Fb = F_l[k].double().cpu().numpy()
+        tol = 1e-6 if prec == "fp32" else 1e-12
+        assert _rel_rms(Fb, Fs) < tol
+        assert np.allclose(E[k], Es, rtol=tol) and np.allclose(E2[k], Es, rtol=tol)
+    b.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("which", ["poly81k", "sweep192k"])
+def test_full_size_sampled(enuf, prec, which):
+    """Full-size systems in the bench's configuration: forces of 256 sampled
+    beads against the oracle bead by bead; energies against the full oracle."""
+    s = W.polyelectrolyte() if which == "poly81k" else W.electrolyte_sweep(192000)
+    P = dict(L=s.L, M=s.M, **s.params)
+    pos, q = _inputs(prec, s.pos, s.q)
+    plan, F, E, Wv = _gpu(enuf, prec, P, pos, q)
+    rng = np.random.default_rng(9)
+    ch = np.nonzero(q)[0]
+    sample = np.sort(rng.choice(ch, 256, replace=False))
+    Fr, Er, Wr = _ref(prec, P, pos, q, sample=sample)
+    t = TOL[prec]
+    assert _rel_rms(F[sample], Fr) < t["F"]
+    scale = max(abs(Er[0]), abs(Er[1]))
+    for k in range(4):
+        assert abs(E[k] - Er[k]) < t["E"] * scale, (k, E, Er)
+    # properties at any size: net force (ik differentiation, symmetric mode set)
+    # and zero force on the neutral beads
+    Fk = F.sum(0)
+    assert np.abs(Fk).max() < (1e-8 if prec == "fp64" else 2e-2) * np.abs(F).max()
+    assert np.all(F[q == 0] == 0.0)
+    plan.close()
