@@ -212,6 +212,43 @@ enuf_status enuf_batch_energy_forces(enuf_batch_t batch, const void* const* pos,
 int enuf_batch_launches(enuf_batch_t batch);
 void enuf_batch_destroy(enuf_batch_t batch);
 
+/* ------------------------------------------------------------------ */
+/* Allocation-free spreading                                           */
+/* ------------------------------------------------------------------ */
+
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that may not allocate device memory: code running inside someone else's
+ * memory pool or arena, framework hot paths where a cudaMalloc (which can
+ * synchronise the whole device) is forbidden, and plugins whose GPU memory
+ * budget is fixed before they run.
+ *
+ * It bins the charged beads and spreads them onto the oversampled grid --
+ * the same result as the spread grid of enuf_energy_forces (ENUF_BUF_GRID) --
+ * using no memory but the caller's arrays and one fixed scratch region that
+ * belongs to the library: a 16 MiB device array in the library image, held on
+ * every GPU that loads the library until the process exits.
+ *   params : as for enuf_plan (precision selects float or double arrays)
+ *   n      : number of beads, >= 0
+ *   pos    : device real[n][3];  q: device real[n]
+ *   grid   : device real[n_g^3] (n_g = sigma_s * M), OVERWRITTEN,
+ *            index (z * n_g + y) * n_g + x
+ *   cuda_stream : cudaStream_t to enqueue on (NULL: the legacy default stream)
+ * Nothing in the scratch needs to start at zero: every call writes all of
+ * the scratch it later reads. Returns after enqueueing.
+ * Limits and rules:
+ *  - ENUF_ERR_INVALID, with a message on stderr, when the bins and sorted
+ *    beads of this call need more than the 16 MiB scratch (about 200000
+ *    beads in FP32 or 120000 in FP64 at the default tile), or for bad
+ *    parameters. No device memory is ever allocated or freed.
+ *  - The first call on a device looks up the scratch address for that device
+ *    (with that device current); make that first call before any stream
+ *    capture on the device.
+ *  - All calls share the one scratch region: calls whose work can overlap on
+ *    the GPU (different streams, or other host threads) race and corrupt each
+ *    other's bins. Serialise them, e.g. on one stream. */
+enuf_status enuf_spread_noalloc(const enuf_params* params, int n, const void* pos, const void* q,
+                                void* grid, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

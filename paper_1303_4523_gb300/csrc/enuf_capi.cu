@@ -898,3 +898,98 @@ void enuf_batch_destroy(enuf_batch_t b) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free spreading. Some callers cannot allocate device memory at
+// all: code that runs inside a memory-pool or arena owned by someone else,
+// host threads of a framework that forbids cudaMalloc on its hot path (an
+// allocation synchronises the device), or plugins whose GPU memory budget is
+// fixed up front. For them the charged-bead binning and the spreading stage
+// run on a fixed scratch region that is part of the library's device image:
+// a file-scope device array, resident on every GPU that loads this library
+// until the process exits. Its address is looked up once per device.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)16 << 20;  // 16 MiB
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+void* g_noalloc_addr[kNoAllocMaxDevices] = {nullptr};
+
+}  // namespace
+
+extern "C" enuf_status enuf_spread_noalloc(const enuf_params* params, int n, const void* pos, const void* q,
+                                           void* grid, void* cuda_stream) {
+    if (!params || n < 0 || !grid || (n > 0 && (!pos || !q))) {
+        fprintf(stderr, "enuf_spread_noalloc: null argument or n < 0\n");
+        return ENUF_ERR_INVALID;
+    }
+    enuf_plan_s geo;  // geometry only: nothing is allocated
+    enuf_status st = derive(&geo, *params, n, nullptr);
+    if (st != ENUF_OK) {
+        fprintf(stderr, "enuf_spread_noalloc: %s\n", geo.err);
+        return st;
+    }
+    const Geo& g = geo.g;
+    const size_t esz = geo.rsz;
+    const size_t nm = (size_t)std::max(n, 1);
+    size_t off = 0;
+    auto take = [&](size_t b) { size_t o = off; off += align256(b); return o; };
+    const size_t o_key = take(nm * 4), o_bhist = take((size_t)g.nbin * g.ntiles * 4),
+                 o_boff = take((size_t)g.nbin * g.ntiles * 4), o_tstart = take((size_t)(g.ntiles + 1) * 4),
+                 o_sq = take(nm * 4 * esz), o_sw = take(nm * 4 * esz), o_sb = take(nm * 4),
+                 o_part = take((size_t)2 * g.nbin * 8);
+    if (off > kNoAllocScratchBytes) {
+        fprintf(stderr,
+                "enuf_spread_noalloc: %d beads on a %d^3 grid need %zu bytes of scratch; the static scratch "
+                "holds %zu bytes\n",
+                n, g.n, off, kNoAllocScratchBytes);
+        return ENUF_ERR_INVALID;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
+        fprintf(stderr, "enuf_spread_noalloc: no usable current device (%s)\n", cudaGetErrorString(e));
+        return ENUF_ERR_CUDA;
+    }
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            fprintf(stderr, "enuf_spread_noalloc: cudaGetSymbolAddress: %s\n", cudaGetErrorString(e));
+            return ENUF_ERR_CUDA;
+        }
+        g_noalloc_addr[dev] = p;
+    }
+    const int pi = geo.prec == ENUF_FP32 ? 0 : 1;
+    if (!g_configured[pi]) {
+        e = geo.prec == ENUF_FP32 ? configure_kernels<float>(kMaxSmem) : configure_kernels<double>(kMaxSmem);
+        if (e != cudaSuccess) {
+            fprintf(stderr, "enuf_spread_noalloc: %s\n", cudaGetErrorString(e));
+            return ENUF_ERR_CUDA;
+        }
+        g_configured[pi] = true;
+    }
+    char* b = static_cast<char*>(g_noalloc_addr[dev]);
+    Work w{};
+    w.key = reinterpret_cast<int*>(b + o_key);
+    w.bhist = reinterpret_cast<int*>(b + o_bhist);
+    w.boff = reinterpret_cast<int*>(b + o_boff);
+    w.tstart = reinterpret_cast<int*>(b + o_tstart);
+    w.sq = b + o_sq;
+    w.sw = b + o_sw;
+    w.sb = reinterpret_cast<int*>(b + o_sb);
+    w.part = reinterpret_cast<double*>(b + o_part);
+    w.off_q = 0;
+    EvalArgs a{n, pos, q, nullptr, false};
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    e = geo.prec == ENUF_FP32 ? enqueue_spread_only<float>(g, w, a, grid, s)
+                              : enqueue_spread_only<double>(g, w, a, grid, s);
+    if (e != cudaSuccess) {
+        fprintf(stderr, "enuf_spread_noalloc: launch: %s\n", cudaGetErrorString(e));
+        return ENUF_ERR_CUDA;
+    }
+    return ENUF_OK;
+}

@@ -145,6 +145,24 @@ cudaError_t enqueue_vv_post(const Work& w, const DpdDev& d, cudaStream_t s, Laun
     return cudaGetLastError();
 }
 
+// Binning and spreading only, into a caller-provided grid (the allocation-free
+// entry point runs this sequence on scratch it does not allocate).
+template <typename R>
+cudaError_t enqueue_spread_only(const Geo& g, const Work& w, const EvalArgs& a, void* grid_out, cudaStream_t s) {
+    using V = typename V4<R>::T;
+    const R* pos = static_cast<const R*>(a.pos);
+    const R* q = static_cast<const R*>(a.q);
+    V* sq = static_cast<V*>(w.sq);
+    V* sw = static_cast<V*>(w.sw);
+    const int hsm = g.ntiles * (int)sizeof(int);
+    k_bin_count<R><<<g.nbin, kBinThreads, hsm, s>>>(g, a.N, pos, q, w.key, w.bhist, nullptr, w.part + w.off_q);
+    k_bin_scan<<<1, 1024, 0, s>>>(g, w.bhist, w.boff, w.tstart);
+    k_bin_scatter<R><<<g.nbin, kBinThreads, hsm, s>>>(g, a.N, pos, q, w.key, w.boff, sq, sw, w.sb);
+    k_spread<R><<<g.ntiles, kSpreadThreads, spread_smem<R>(g), s>>>(g, w.tstart, sq, sw, w.sb,
+                                                                    static_cast<R*>(grid_out));
+    return cudaGetLastError();
+}
+
 #define ENUF_INSTANTIATE(R)                                                                                  \
     template cudaError_t configure_kernels<R>(int);                                                          \
     template int spread_smem<R>(const Geo&);                                                                 \
@@ -155,6 +173,7 @@ cudaError_t enqueue_vv_post(const Work& w, const DpdDev& d, cudaStream_t s, Laun
     template cudaError_t enqueue_dpd_forces<R>(const Work&, const DpdDev&, cudaStream_t, Events*,            \
                                                LaunchLog*);                                                  \
     template cudaError_t enqueue_vv_pre<R>(const DpdDev&, cudaStream_t, LaunchLog*);                         \
-    template cudaError_t enqueue_vv_post<R>(const Work&, const DpdDev&, cudaStream_t, LaunchLog*);
+    template cudaError_t enqueue_vv_post<R>(const Work&, const DpdDev&, cudaStream_t, LaunchLog*);           \
+    template cudaError_t enqueue_spread_only<R>(const Geo&, const Work&, const EvalArgs&, void*, cudaStream_t);
 
 }  // namespace enuf

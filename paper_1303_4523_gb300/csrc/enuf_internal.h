@@ -117,5 +117,7 @@ template <typename R>
 cudaError_t enqueue_vv_pre(const DpdDev& d, cudaStream_t s, LaunchLog* log);
 template <typename R>
 cudaError_t enqueue_vv_post(const Work& w, const DpdDev& d, cudaStream_t s, LaunchLog* log);
+template <typename R>
+cudaError_t enqueue_spread_only(const Geo& g, const Work& w, const EvalArgs& a, void* grid_out, cudaStream_t s);
 
 }  // namespace enuf

@@ -80,6 +80,7 @@ def _load():
         "enuf_batch_energy_forces": (st, [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), pd]),
         "enuf_batch_launches": (i, [vp]),
         "enuf_batch_destroy": (None, [vp]),
+        "enuf_spread_noalloc": (st, [C.POINTER(enuf_params), i, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -95,7 +96,8 @@ EXPORTED = ("enuf_plan", "enuf_footprint", "enuf_get_info", "enuf_energy_forces"
             "enuf_stage_time", "enuf_launches_per_eval", "enuf_destroy", "enuf_status_string",
             "enuf_last_error", "dpd_create", "dpd_step", "dpd_get_state", "dpd_set_state",
             "dpd_get_forces", "dpd_device_state", "dpd_destroy", "enuf_batch_plan",
-            "enuf_batch_energy_forces", "enuf_batch_launches", "enuf_batch_destroy")
+            "enuf_batch_energy_forces", "enuf_batch_launches", "enuf_batch_destroy",
+            "enuf_spread_noalloc")
 
 
 def _check(status, handle=None, what=""):
