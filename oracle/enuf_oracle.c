@@ -299,12 +299,13 @@ static double window_hat(double b, int k, int ng)
     return exp(-b * t * t);
 }
 
-/* Grid coordinate of a wrapped position: u = n * x / L in [0, n), base = floor(u). */
+/* Grid coordinate of a wrapped position: u = x_w * (n/L) in [0, n), base = floor(u).
+ * The ratio n/L is formed once in FP64; one product and the floor decide the
+ * integer base (the same FP64 sequence on every side that must agree on it). */
 static void grid_coord(double xw, double L, int ng, int* base, double* frac)
 {
-    double s = xw / L;
-    s = s - floor(s);
-    double u = s * (double)ng;
+    const double ratio = (double)ng / L;
+    double u = xw * ratio;
     if (u >= (double)ng) u -= (double)ng;
     const double bse = floor(u);
     *base = (int)bse;
