@@ -54,7 +54,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         list(ex.map(run, jobs))
     objs = [os.path.join(BUILD, s.replace(".cu", ".o")) for s in SOURCES]
-    if jobs or not os.path.exists(LIB):
+    if jobs or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
         tmp = LIB + f".tmp{os.getpid()}"
         run([NVCC, *ARCH, "-shared", "-o", tmp, *objs])
         os.replace(tmp, LIB)

@@ -62,6 +62,13 @@ bool fft_radices(int n, FftPlanDev& fp) {
     return m == 1;
 }
 
+// Largest float strictly below L: a float x lies in [0, L) iff 0 <= x <= this.
+float largest_float_below(double L) {
+    float f = (float)L;
+    while ((double)f >= L) f = std::nextafter(f, 0.0f);
+    return f;
+}
+
 int lines_for(int n, int nbuf, int esz, int budget, int cap) {
     const int l = (budget - n * esz) / (nbuf * n * esz);
     return std::max(1, std::min(cap, l));
@@ -159,7 +166,14 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
     g.ntiles = g.ntd * g.ntd * g.ntd;
     const double tw = T * P.L / n;
     g.rs = (int)std::ceil(P.r_cut / tw - 1e-12);
-    g.chunk = std::max(2048, (n_max + 63) / 64);
+    {   // the real-space kernel stages the stencil of one tile: at most 1024 tiles
+        const int hs = std::min(2 * g.rs + 1, n / T);
+        if (hs * hs * hs > 1024)
+            return fail(plan, ENUF_ERR_UNSUPPORTED, "real-space stencil of %d^3 tiles too large (r_cut/tile)", hs);
+    }
+    // binning blocks: the count kernel holds a chunk-sized list plus the tile
+    // histogram in shared memory (<= 200 KB)
+    g.chunk = std::min(16384, std::max(2048, (n_max + 63) / 64));
     g.nbin = std::max(1, (n_max + g.chunk - 1) / g.chunk);
     g.kmask = P.kmask;
     g.L = P.L;
@@ -170,27 +184,37 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
     g.b = 2.0 * P.sigma_s * P.p / ((2.0 * P.sigma_s - 1.0) * M_PI);
     g.wnorm = 1.0 / std::sqrt(M_PI * g.b);
 
+    // FFT passes: enough lines per CTA to keep ~2 CTAs per SM busy, within a
+    // 64 KB shared-memory budget; threads ~ one butterfly of radix 4 per line point
     FftShape fs{};
     const int budget = 64 * 1024;
-    fs.lx = lines_for(n, 2, csz, budget, 32);
-    fs.ly = lines_for(n, 2, csz, budget, 32);
-    fs.lz = lines_for(n, 3, csz, budget, 32);
-    fs.liy = lines_for(n, 2, csz, budget, 32);
-    fs.lix = lines_for(n, 2, csz, budget, 32);
+    const int nc1 = g.nc + 1;
+    auto shape = [&](int total_lines, int nbuf, int& lines, int& threads, int& grid) {
+        const int cap = lines_for(n, nbuf, csz, budget, 64);
+        lines = std::max(1, std::min(cap, (total_lines + 2 * kSMs - 1) / (2 * kSMs)));
+        grid = (total_lines + lines - 1) / lines;
+        threads = std::min(256, std::max(64, ((lines * n / 4 + 31) / 32) * 32));
+    };
+    int gyz = 0;
+    shape(n * n / 2, 2, fs.lx, fs.tx, fs.grid_x);
+    shape(n * nc1, 2, fs.ly, fs.ty, gyz);
+    fs.grid_y_z = (n + fs.ly - 1) / fs.ly;
+    shape(nc1 * g.K, 3, fs.lz, fs.tz, fs.grid_z);
+    shape(3 * n * nc1, 2, fs.liy, fs.tiy, fs.grid_iy);
+    shape(3 * n * n / 2, 2, fs.lix, fs.tix, fs.grid_ix);
     fs.smem_x = (1 + 2 * fs.lx) * n * csz;
     fs.smem_y = (1 + 2 * fs.ly) * n * csz;
     fs.smem_z = (1 + 3 * fs.lz) * n * csz;
     fs.smem_iy = (1 + 2 * fs.liy) * n * csz;
     fs.smem_ix = (1 + 2 * fs.lix) * n * csz;
-    const int nc1 = g.nc + 1;
-    fs.grid_x = (n * n / 2 + fs.lx - 1) / fs.lx;
-    fs.grid_y_z = (n + fs.ly - 1) / fs.ly;
-    fs.grid_z = (nc1 * g.K + fs.lz - 1) / fs.lz;
-    fs.grid_iy = (3 * n * nc1 + fs.liy - 1) / fs.liy;
-    fs.grid_ix = (3 * n * n / 2 + fs.lix - 1) / fs.lix;
+    g.ratio = (double)n / P.L;
+    g.rb = 1.0 / g.b;
+    g.pref = P.kappa * 2.0 / (P.L * P.L);
+    g.c2a = 2.0 * P.alpha / std::sqrt(M_PI);
+    g.xmaxf = largest_float_below(P.L);
 
     Work w{};
-    w.nblk_real = 2 * kSMs;
+    w.nblk_real = 8 * kSMs;
     w.nblk_conv = fs.grid_z;
     w.nblk_dpd = 4 * kSMs;
     w.nblk_kin = 4 * kSMs;
@@ -208,8 +232,11 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
     size_t off = 0;
     auto take = [&](size_t b) { size_t o = off; off += align256(b); return o; };
     // record offsets in w as integers for now (cast later)
-    size_t o_key = take(nm * 4), o_bhist = take((size_t)g.nbin * g.ntiles * 4),
-           o_boff = take((size_t)g.nbin * g.ntiles * 4), o_tstart = take((size_t)(g.ntiles + 1) * 4),
+    const size_t ncmp = (size_t)g.nbin * g.chunk;   // compacted-bead slots
+    size_t o_cnt = take((size_t)g.nbin * 4), o_bhist = take((size_t)g.nbin * g.ntiles * 4),
+           o_boff = take((size_t)g.nbin * g.ntiles * 4), o_ttot = take((size_t)g.ntiles * 4),
+           o_tstart = take((size_t)(g.ntiles + 1) * 4), o_ctile = take(ncmp * 4), o_cpos = take(ncmp * 4 * esz),
+           o_cfrac = take(ncmp * 4 * esz), o_cbase = take(ncmp * 4),
            o_sq = take(nm * 4 * esz), o_sw = take(nm * 4 * esz), o_sb = take(nm * 4), o_grid = take(n3 * esz),
            o_s1 = take((size_t)n * nc1 * n * csz), o_s2 = take((size_t)nc1 * g.K * n * csz),
            o_s3 = take((size_t)3 * n * nc1 * g.K * csz), o_s4 = take((size_t)3 * n * n * nc1 * csz),
@@ -227,7 +254,9 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
         plan->fs = fs;
         plan->fp = fp;
         // stash offsets; bound to the allocation in bind()
-        w.key = (int*)o_key; w.bhist = (int*)o_bhist; w.boff = (int*)o_boff; w.tstart = (int*)o_tstart;
+        w.cnt_blk = (int*)o_cnt; w.bhist = (int*)o_bhist; w.boff = (int*)o_boff; w.ttot = (int*)o_ttot;
+        w.tstart = (int*)o_tstart; w.ctile = (int*)o_ctile; w.cpos = (void*)o_cpos; w.cfrac = (void*)o_cfrac;
+        w.cbase = (int*)o_cbase;
         w.sq = (void*)o_sq; w.sw = (void*)o_sw; w.sb = (int*)o_sb; w.grid = (void*)o_grid;
         w.spec1 = (void*)o_s1; w.spec2 = (void*)o_s2; w.spec3 = (void*)o_s3; w.spec4 = (void*)o_s4;
         w.h = (void*)o_h; w.tab = (double*)o_tab; w.tabv = (double*)o_tabv; w.tabr = (void*)o_tabr;
@@ -242,7 +271,9 @@ void bind(enuf_plan_t p) {
     char* b = static_cast<char*>(p->dmem);
     Work& w = p->w;
     auto at = [&](auto ptr) { return reinterpret_cast<decltype(ptr)>(b + reinterpret_cast<size_t>(ptr)); };
-    w.key = at(w.key); w.bhist = at(w.bhist); w.boff = at(w.boff); w.tstart = at(w.tstart);
+    w.cnt_blk = at(w.cnt_blk); w.bhist = at(w.bhist); w.boff = at(w.boff); w.ttot = at(w.ttot);
+    w.tstart = at(w.tstart); w.ctile = at(w.ctile); w.cpos = at(w.cpos); w.cfrac = at(w.cfrac);
+    w.cbase = at(w.cbase);
     w.sq = at(w.sq); w.sw = at(w.sw); w.sb = at(w.sb); w.grid = at(w.grid);
     w.spec1 = at(w.spec1); w.spec2 = at(w.spec2); w.spec3 = at(w.spec3); w.spec4 = at(w.spec4);
     w.h = at(w.h); w.tab = at(w.tab); w.tabv = at(w.tabv); w.tabr = at(w.tabr);
@@ -644,7 +675,7 @@ enuf_status dpd_create(enuf_plan_t plan, const dpd_params* params, int n, const 
     if (params->ntypes < 1 || !params->a) return fail(plan, ENUF_ERR_INVALID, "ntypes < 1 or a == NULL");
     if (!(params->dt > 0)) return fail(plan, ENUF_ERR_INVALID, "dt must be > 0");
     const double L = plan->P.L;
-    if (L < 2.0) return fail(plan, ENUF_ERR_INVALID, "DPD needs L >= 2 (cutoff 1 with minimum image)");
+    if (L < 3.0) return fail(plan, ENUF_ERR_INVALID, "DPD needs L >= 3 (cell list of edge >= 1, 3 cells per edge)");
     for (int i = 0; i < n; ++i)
         if (type[i] < 0 || type[i] >= params->ntypes) return fail(plan, ENUF_ERR_INVALID, "type[%d] out of range", i);
     for (int k = 0; k < 2 * n_bonds; ++k)
@@ -656,7 +687,9 @@ enuf_status dpd_create(enuf_plan_t plan, const dpd_params* params, int n, const 
     DpdDev& d = sys->d;
     d.N = n;
     d.ntypes = params->ntypes;
-    d.ncd = std::max(1, (int)std::floor(L * (1.0 - 1e-12)));
+    // cell edge L/ncd >= 1 + 1e-5: float rounding of x * ncd/L cannot put two
+    // beads closer than the cutoff 1 two cells apart
+    d.ncd = std::max(1, (int)std::floor(L / (1.0 + 1e-5)));
     d.ncells = d.ncd * d.ncd * d.ncd;
     d.L = L;
     d.gamma = params->gamma;
@@ -666,6 +699,10 @@ enuf_status dpd_create(enuf_plan_t plan, const dpd_params* params, int n, const 
     d.K_bond = params->K_bond;
     d.r0_bond = params->r0_bond;
     d.seed = params->seed;
+    d.rdt = 1.0 / std::sqrt(params->dt);
+    d.B = std::max(1, std::min(4, d.ncd - 2));
+    d.cinv = (double)d.ncd / L;
+    d.xmaxf = largest_float_below(L);
     const size_t rs = plan->rsz;
     // per-bead bond lists (CSR over both ends)
     std::vector<int> bptr(n + 1, 0), blist(2 * (size_t)n_bonds);
@@ -688,7 +725,7 @@ enuf_status dpd_create(enuf_plan_t plan, const dpd_params* params, int n, const 
                  o_atab = take((size_t)d.ntypes * d.ntypes * rs), o_bptr = take((n + 1) * 4),
                  o_blist = take(std::max<size_t>(1, blist.size()) * 4), o_ckey = take(n * 4),
                  o_ccount = take((size_t)d.ncells * 4), o_cstart = take(((size_t)d.ncells + 1) * 4),
-                 o_ccur = take((size_t)d.ncells * 4), o_sp = take(n * 4 * rs), o_sv = take(n * 4 * rs),
+                 o_ccur = take(((size_t)d.ncells + 1) * 4), o_sp = take(n * 4 * rs), o_sv = take(n * 4 * rs),
                  o_step = take(8);
     cudaError_t e = cudaMalloc(&sys->dmem, off);
     if (e != cudaSuccess) {
@@ -937,8 +974,11 @@ extern "C" enuf_status enuf_spread_noalloc(const enuf_params* params, int n, con
     const size_t nm = (size_t)std::max(n, 1);
     size_t off = 0;
     auto take = [&](size_t b) { size_t o = off; off += align256(b); return o; };
-    const size_t o_key = take(nm * 4), o_bhist = take((size_t)g.nbin * g.ntiles * 4),
-                 o_boff = take((size_t)g.nbin * g.ntiles * 4), o_tstart = take((size_t)(g.ntiles + 1) * 4),
+    const size_t ncmp = (size_t)g.nbin * g.chunk;
+    const size_t o_cnt = take((size_t)g.nbin * 4), o_bhist = take((size_t)g.nbin * g.ntiles * 4),
+                 o_boff = take((size_t)g.nbin * g.ntiles * 4), o_ttot = take((size_t)g.ntiles * 4),
+                 o_tstart = take((size_t)(g.ntiles + 1) * 4), o_ctile = take(ncmp * 4),
+                 o_cpos = take(ncmp * 4 * esz), o_cfrac = take(ncmp * 4 * esz), o_cbase = take(ncmp * 4),
                  o_sq = take(nm * 4 * esz), o_sw = take(nm * 4 * esz), o_sb = take(nm * 4),
                  o_part = take((size_t)2 * g.nbin * 8);
     if (off > kNoAllocScratchBytes) {
@@ -974,10 +1014,15 @@ extern "C" enuf_status enuf_spread_noalloc(const enuf_params* params, int n, con
     }
     char* b = static_cast<char*>(g_noalloc_addr[dev]);
     Work w{};
-    w.key = reinterpret_cast<int*>(b + o_key);
+    w.cnt_blk = reinterpret_cast<int*>(b + o_cnt);
     w.bhist = reinterpret_cast<int*>(b + o_bhist);
     w.boff = reinterpret_cast<int*>(b + o_boff);
+    w.ttot = reinterpret_cast<int*>(b + o_ttot);
     w.tstart = reinterpret_cast<int*>(b + o_tstart);
+    w.ctile = reinterpret_cast<int*>(b + o_ctile);
+    w.cpos = b + o_cpos;
+    w.cfrac = b + o_cfrac;
+    w.cbase = reinterpret_cast<int*>(b + o_cbase);
     w.sq = b + o_sq;
     w.sw = b + o_sw;
     w.sb = reinterpret_cast<int*>(b + o_sb);

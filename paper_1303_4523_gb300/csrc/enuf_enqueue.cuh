@@ -8,7 +8,7 @@
 
 namespace enuf {
 
-constexpr int kBinThreads = 512;
+constexpr int kBinThreads = 1024;
 
 inline void rec(Events* ev, int stage, bool start, cudaStream_t s) {
     if (ev && ev->on)
@@ -30,13 +30,30 @@ cudaError_t configure_kernels(int max_smem) {
     set((const void*)k_fft_z<R>);
     set((const void*)k_fft_iy<R>);
     set((const void*)k_fft_ix<R>);
+    set((const void*)k_real<R>);
+    set((const void*)k_dpd<R>);
     return e;
 }
 
 template <typename R>
 int spread_smem(const Geo& g) {
     const int T3 = g.T * g.T * g.T;
-    return T3 * (int)sizeof(R) + (kSpreadThreads / 32) * 3 * kMaxTaps * ((int)sizeof(R) + 4);
+    return kSpreadCap * (int)sizeof(typename V4<R>::T) + T3 * (int)sizeof(R) +
+           (kSpreadThreads / 32) * 3 * kMaxTaps * ((int)sizeof(R) + 4) + kSpreadCap * 4;
+}
+
+// a1: compaction + coordinates + tile histograms, tile offsets, tile scan, scatter.
+template <typename R>
+void enqueue_bin(const Geo& g, const Work& w, int N, const R* pos, const R* q, R* Fzero, cudaStream_t s) {
+    using V = typename V4<R>::T;
+    k_bin_count<R><<<g.nbin, kBinThreads, (g.ntiles + g.chunk) * (int)sizeof(int), s>>>(
+        g, N, pos, q, w.cnt_blk, w.bhist, w.ctile, static_cast<V*>(w.cpos), static_cast<V*>(w.cfrac), w.cbase,
+        Fzero, w.part + w.off_q);
+    k_tile_offsets<<<(g.ntiles + 255) / 256, 256, 0, s>>>(g, w.bhist, w.boff, w.ttot);
+    k_scan<<<1, 1024, 0, s>>>(w.ttot, w.tstart, g.ntiles, nullptr, 0);
+    k_bin_scatter<R><<<g.nbin, kBinThreads, g.ntiles * (int)sizeof(int), s>>>(
+        g, w.cnt_blk, w.ctile, static_cast<const V*>(w.cpos), static_cast<const V*>(w.cfrac), w.cbase, w.boff,
+        w.tstart, static_cast<V*>(w.sq), static_cast<V*>(w.sw), w.sb);
 }
 
 template <typename R>
@@ -51,21 +68,17 @@ cudaError_t enqueue_enuf(const Geo& g, const FftShape& fs, const FftPlanDev& fp,
     V* sq = static_cast<V*>(w.sq);
     V* sw = static_cast<V*>(w.sw);
     C* tw = static_cast<C*>(w.tw);
-    const int hsm = g.ntiles * (int)sizeof(int);
-
     rec(ev, 0, true, s0);
-    k_bin_count<R><<<g.nbin, kBinThreads, hsm, s0>>>(g, a.N, pos, q, w.key, w.bhist, a.zeroF ? F : nullptr,
-                                                     w.part + w.off_q);
-    k_bin_scan<<<1, 1024, 0, s0>>>(g, w.bhist, w.boff, w.tstart);
-    k_bin_scatter<R><<<g.nbin, kBinThreads, hsm, s0>>>(g, a.N, pos, q, w.key, w.boff, sq, sw, w.sb);
+    enqueue_bin<R>(g, w, a.N, pos, q, a.zeroF ? F : nullptr, s0);
     rec(ev, 0, false, s0);
-    log->kernels += 3;
+    log->kernels += 4;
 
     // real-space branch
     cudaEventRecord(evFork, s0);
     cudaStreamWaitEvent(s1, evFork, 0);
     rec(ev, 4, true, s1);
-    k_real<R><<<w.nblk_real, kRealThreads, 0, s1>>>(g, w.tstart, sq, sw, w.sb, F, w.part + w.off_real);
+    const int real_smem = (kRealCap + (kRealThreads / 32) * 64) * (int)sizeof(V) + (2 * kRealHalo + 1) * 4;
+    k_real<R><<<w.nblk_real, kRealThreads, real_smem, s1>>>(g, w.tstart, sq, sw, F, w.part + w.off_real);
     rec(ev, 4, false, s1);
     cudaEventRecord(evJoin, s1);
     log->kernels += 1;
@@ -76,16 +89,16 @@ cudaError_t enqueue_enuf(const Geo& g, const FftShape& fs, const FftPlanDev& fp,
                                                                      static_cast<R*>(w.grid));
     rec(ev, 1, false, s0);
     rec(ev, 2, true, s0);
-    k_fft_x<R><<<fs.grid_x, 256, fs.smem_x, s0>>>(g, fp, static_cast<const R*>(w.grid), tw,
+    k_fft_x<R><<<fs.grid_x, fs.tx, fs.smem_x, s0>>>(g, fp, static_cast<const R*>(w.grid), tw,
                                                   static_cast<C*>(w.spec1), fs.lx);
-    k_fft_y<R><<<dim3(g.nc + 1, fs.grid_y_z), 256, fs.smem_y, s0>>>(g, fp, static_cast<const C*>(w.spec1), tw,
+    k_fft_y<R><<<dim3(g.nc + 1, fs.grid_y_z), fs.ty, fs.smem_y, s0>>>(g, fp, static_cast<const C*>(w.spec1), tw,
                                                                    static_cast<C*>(w.spec2), fs.ly);
-    k_fft_z<R><<<fs.grid_z, 256, fs.smem_z, s0>>>(g, fp, static_cast<const C*>(w.spec2), tw, w.tab, w.tabv,
+    k_fft_z<R><<<fs.grid_z, fs.tz, fs.smem_z, s0>>>(g, fp, static_cast<const C*>(w.spec2), tw, w.tab, w.tabv,
                                                   static_cast<const R*>(w.tabr), static_cast<C*>(w.spec3),
                                                   w.part + w.off_recip, fs.lz);
-    k_fft_iy<R><<<fs.grid_iy, 256, fs.smem_iy, s0>>>(g, fp, static_cast<const C*>(w.spec3), tw,
+    k_fft_iy<R><<<fs.grid_iy, fs.tiy, fs.smem_iy, s0>>>(g, fp, static_cast<const C*>(w.spec3), tw,
                                                      static_cast<C*>(w.spec4), fs.liy);
-    k_fft_ix<R><<<fs.grid_ix, 256, fs.smem_ix, s0>>>(g, fp, static_cast<const C*>(w.spec4), tw,
+    k_fft_ix<R><<<fs.grid_ix, fs.tix, fs.smem_ix, s0>>>(g, fp, static_cast<const C*>(w.spec4), tw,
                                                      static_cast<R*>(w.h), fs.lix);
     rec(ev, 2, false, s0);
     log->kernels += 6;
@@ -112,16 +125,20 @@ cudaError_t enqueue_dpd_forces(const Work& w, const DpdDev& d, cudaStream_t s, E
     using V = typename V4<R>::T;
     const int blocks = (d.N + 255) / 256 > 0 ? (d.N + 255) / 256 : 1;
     rec(ev, 7, true, s);
-    k_cell_count<R><<<blocks, 256, 0, s>>>(d.N, d.ncd, d.L, static_cast<const R*>(d.pos), d.ckey, d.ccount);
-    k_cell_scan<<<1, 1024, 0, s>>>(d.ncells, d.ccount, d.cstart, d.ccur);
-    k_cell_scatter<R><<<blocks, 256, 0, s>>>(d.N, d.L, static_cast<const R*>(d.pos), static_cast<const R*>(d.v0),
+    k_cell_count<R><<<blocks, 256, 0, s>>>(d.N, d.ncd, d.L, d.cinv, d.xmaxf, static_cast<const R*>(d.pos), d.ckey,
+                                           d.ccount);
+    k_scan<<<1, 1024, 0, s>>>(d.ccount, d.cstart, d.ncells, d.ccur, 1);
+    k_cell_scatter<R><<<blocks, 256, 0, s>>>(d.N, d.L, d.xmaxf, static_cast<const R*>(d.pos), static_cast<const R*>(d.v0),
                                              d.type, d.ckey, d.ccur, static_cast<V*>(d.sp), static_cast<V*>(d.sv));
     rec(ev, 7, false, s);
     rec(ev, 5, true, s);
-    k_dpd<R><<<w.nblk_dpd, 256, 0, s>>>(d, static_cast<const V*>(d.sp), static_cast<const V*>(d.sv), d.ckey,
-                                        d.cstart, static_cast<const R*>(d.atab), static_cast<const R*>(d.pos),
-                                        d.bptr, d.blist, d.step_dev, static_cast<R*>(d.F),
-                                        w.part + w.off_dpd);
+    const int dpd_smem = 2 * kDpdCap * (int)sizeof(V) + (kDpdThreads / 32) * (kDpdIMax * 3 * (int)sizeof(R) +
+                                                                             64 * 8 + kDpdCand * 4);
+    k_dpd<R><<<w.nblk_dpd, kDpdThreads, dpd_smem, s>>>(d, d.B, static_cast<const V*>(d.sp),
+                                                      static_cast<const V*>(d.sv), d.cstart,
+                                                      static_cast<const R*>(d.atab), static_cast<const R*>(d.pos),
+                                                      d.bptr, d.blist, d.step_dev, static_cast<R*>(d.F),
+                                                      w.part + w.off_dpd);
     rec(ev, 5, false, s);
     log->kernels += 4;
     return cudaGetLastError();
@@ -150,15 +167,9 @@ cudaError_t enqueue_vv_post(const Work& w, const DpdDev& d, cudaStream_t s, Laun
 template <typename R>
 cudaError_t enqueue_spread_only(const Geo& g, const Work& w, const EvalArgs& a, void* grid_out, cudaStream_t s) {
     using V = typename V4<R>::T;
-    const R* pos = static_cast<const R*>(a.pos);
-    const R* q = static_cast<const R*>(a.q);
-    V* sq = static_cast<V*>(w.sq);
-    V* sw = static_cast<V*>(w.sw);
-    const int hsm = g.ntiles * (int)sizeof(int);
-    k_bin_count<R><<<g.nbin, kBinThreads, hsm, s>>>(g, a.N, pos, q, w.key, w.bhist, nullptr, w.part + w.off_q);
-    k_bin_scan<<<1, 1024, 0, s>>>(g, w.bhist, w.boff, w.tstart);
-    k_bin_scatter<R><<<g.nbin, kBinThreads, hsm, s>>>(g, a.N, pos, q, w.key, w.boff, sq, sw, w.sb);
-    k_spread<R><<<g.ntiles, kSpreadThreads, spread_smem<R>(g), s>>>(g, w.tstart, sq, sw, w.sb,
+    enqueue_bin<R>(g, w, a.N, static_cast<const R*>(a.pos), static_cast<const R*>(a.q), nullptr, s);
+    k_spread<R><<<g.ntiles, kSpreadThreads, spread_smem<R>(g), s>>>(g, w.tstart, static_cast<const V*>(w.sq),
+                                                                    static_cast<const V*>(w.sw), w.sb,
                                                                     static_cast<R*>(grid_out));
     return cudaGetLastError();
 }

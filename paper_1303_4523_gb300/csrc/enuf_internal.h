@@ -26,6 +26,12 @@ struct Geo {
     double L, alpha, beta, kappa, rc;
     double b;      // Gaussian window parameter 2 sigma p / ((2 sigma - 1) pi)
     double wnorm;  // (pi b)^{-1/2}
+    double ratio;  // n / L: grid coordinate u = x * ratio (one FP64 product)
+    double rb;     // 1 / b
+    double pref;   // kappa * 2 / L^2 (Eq. 25 prefactor)
+    double c2a;    // 2 alpha / sqrt(pi)
+    float xmaxf;   // largest float below L: float x is inside [0, L) iff 0 <= x <= xmaxf
+    int pad1;
 };
 
 // Lines per CTA of each FFT pass.
@@ -35,6 +41,7 @@ struct FftShape {
     int lz;    // lines per CTA, z pass (forward + convolve + 3 inverses)
     int liy;   // lines per CTA, inverse y
     int lix;   // complex lines per CTA, inverse x
+    int tx, ty, tz, tiy, tix;   // threads per CTA of each pass
     int smem_x, smem_y, smem_z, smem_iy, smem_ix;   // dynamic smem bytes
     int grid_x, grid_y_z, grid_z, grid_iy, grid_ix; // CTAs (grid_y_z: z-chunks of the y pass)
 };
@@ -42,10 +49,15 @@ struct FftShape {
 // Device workspace of one plan (all pointers device memory, one allocation).
 struct Work {
     // charged binning
-    int* key;        // [n_max] tile of each bead, -1 if uncharged
-    int* bhist;      // [nbin][ntiles]
-    int* boff;       // [nbin][ntiles]
+    int* cnt_blk;    // [nbin] charged beads of each binning block
+    int* bhist;      // [nbin][ntiles] per-block tile counts
+    int* boff;       // [nbin][ntiles] offset of each block's beads within each tile
+    int* ttot;       // [ntiles] beads per tile
     int* tstart;     // [ntiles + 1]
+    int* ctile;      // [nbin * chunk] tile of each compacted charged bead
+    void* cpos;      // real4 [nbin * chunk] wrapped x, y, z, q of each compacted charged bead
+    void* cfrac;     // real4 [nbin * chunk] fractional grid coordinates, original index bits
+    int* cbase;      // [nbin * chunk] packed base grid index
     void* sq;        // real4 [n_max]  wrapped x, y, z, q (sorted)
     void* sw;        // real4 [n_max]  fractional grid coordinates, original index bits
     int* sb;         // [n_max]  packed base grid index
@@ -79,7 +91,11 @@ struct EvalArgs {
 // DPD device state and cell list (one per system).
 struct DpdDev {
     int N, ntypes, ncd, ncells;
+    int B;             // cells per block edge of the DPD kernel (<= 4, B + 2 <= ncd)
     double L, gamma, sigma, dt, lambda_vv, K_bond, r0_bond;
+    double rdt;    // 1 / sqrt(dt)
+    double cinv;   // ncd / L
+    float xmaxf;   // largest float below L
     uint64_t seed;
     void* pos; void* vel; void* v0; void* F; void* q;   // real
     int* type;

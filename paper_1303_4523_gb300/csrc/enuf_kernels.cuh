@@ -36,6 +36,9 @@ __device__ __forceinline__ float r_erfc(float x) { return erfcf(x); }
 __device__ __forceinline__ double r_erfc(double x) { return erfc(x); }
 __device__ __forceinline__ float r_sqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double r_sqrt(double x) { return sqrt(x); }
+// 1/sqrt: the hardware approximation in float (2 ulp), the exact quotient in double
+__device__ __forceinline__ float r_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double r_rsqrt(double x) { return 1.0 / sqrt(x); }
 
 // ---------------------------------------------------------------------------
 // Coordinates. Wrapping and grid coordinates are computed in double with the
@@ -56,10 +59,19 @@ __device__ __forceinline__ double wrap_to_real(R x, double L) {
     return w;
 }
 
-__device__ __forceinline__ void grid_coord(double xw, double L, int n, int& base, double& frac) {
-    double s = __ddiv_rn(xw, L);
-    s = __dsub_rn(s, floor(s));
-    double u = __dmul_rn(s, (double)n);
+// Wrapped position in the working precision. Inside [0, L) the value is kept
+// as is (decided in float for float: x <= xmaxf, the largest float below L);
+// outside it goes through the FP64 wrap.
+__device__ __forceinline__ float wrap_r(float x, double L, float xmaxf) {
+    if (x >= 0.0f && x <= xmaxf) return x;
+    return __double2float_rn(wrap_pos((double)x, L));
+}
+__device__ __forceinline__ double wrap_r(double x, double L, float) { return wrap_pos(x, L); }
+
+// Grid coordinate u = x_w * (n/L) in [0, n): one FP64 product and one floor
+// (n/L formed once on the host), u >= n wraps to 0.
+__device__ __forceinline__ void grid_coord(double xw, double ratio, int n, int& base, double& frac) {
+    double u = __dmul_rn(xw, ratio);
     if (u >= (double)n) u = __dsub_rn(u, (double)n);
     const double bb = floor(u);
     base = (int)bb;
@@ -131,43 +143,78 @@ struct Kahan {
 
 // ---------------------------------------------------------------------------
 // a1: binning of the charged beads into tiles of the oversampled grid.
-// Block-local histograms in shared memory, one scan, one scatter: the only
-// atomics are shared-memory ones.
+// k_bin_count: each block compacts the charged beads of its chunk (warp
+//   ballots into a shared list), computes their grid coordinates in FP64 on
+//   dense warps, histograms their tiles in shared memory and stores each
+//   compacted bead's record.
+// k_tile_offsets: one thread per tile walks the per-block counts (coalesced)
+//   and writes each block's offset inside the tile and the tile total.
+// k_scan over the tile totals gives the tile starts; k_bin_scatter moves the
+//   records to their sorted slots. The only atomics are shared-memory ones.
 // ---------------------------------------------------------------------------
 template <typename R>
-__global__ void __launch_bounds__(512) k_bin_count(Geo g, int N, const R* __restrict__ pos,
-                                                  const R* __restrict__ q, int* __restrict__ key,
-                                                  int* __restrict__ bhist, R* __restrict__ Fzero,
-                                                  double* __restrict__ qpart) {
-    extern __shared__ int hist[];
+__global__ void __launch_bounds__(1024) k_bin_count(Geo g, int N, const R* __restrict__ pos,
+                                                   const R* __restrict__ q, int* __restrict__ cnt_blk,
+                                                   int* __restrict__ bhist, int* __restrict__ ctile,
+                                                   typename V4<R>::T* __restrict__ cpos,
+                                                   typename V4<R>::T* __restrict__ cfrac, int* __restrict__ cbase,
+                                                   R* __restrict__ Fzero, double* __restrict__ qpart) {
+    extern __shared__ int sm_bin[];
+    int* hist = sm_bin;                 // [ntiles]
+    int* slist = sm_bin + g.ntiles;     // [chunk]
+    __shared__ int scount;
     for (int t = threadIdx.x; t < g.ntiles; t += blockDim.x) hist[t] = 0;
+    if (threadIdx.x == 0) scount = 0;
     __syncthreads();
-    const int b = blockIdx.x;
+    const int b = blockIdx.x, lane = threadIdx.x & 31;
     const int i0 = b * g.chunk;
     const int i1 = min(N, i0 + g.chunk);
     double s1 = 0.0, s2 = 0.0;
-    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-        const R qi = q[i];
-        int kk = -1;
-        if (qi != (R)0) {
-            int bs[3];
-#pragma unroll
-            for (int t = 0; t < 3; ++t) {
-                double fr;
-                grid_coord(wrap_to_real<R>(pos[3 * i + t], g.L), g.L, g.n, bs[t], fr);
+    for (int ib = i0; ib < i0 + g.chunk; ib += blockDim.x) {
+        const int i = ib + threadIdx.x;
+        R qi = (R)0;
+        if (i < i1) {
+            qi = q[i];
+            if (Fzero) {
+                Fzero[3 * i] = (R)0;
+                Fzero[3 * i + 1] = (R)0;
+                Fzero[3 * i + 2] = (R)0;
             }
-            kk = ((bs[2] / g.T) * g.ntd + bs[1] / g.T) * g.ntd + bs[0] / g.T;
-            atomicAdd(&hist[kk], 1);
+        }
+        const bool charged = qi != (R)0;
+        const unsigned m = __ballot_sync(0xffffffffu, charged);
+        int basei = 0;
+        if (lane == 0 && m) basei = atomicAdd(&scount, __popc(m));
+        basei = __shfl_sync(0xffffffffu, basei, 0);
+        if (charged) {
+            slist[basei + __popc(m & ((1u << lane) - 1u))] = i;
             s1 += (double)qi;
             s2 += (double)qi * (double)qi;
         }
-        key[i] = kk;
-        if (Fzero) {
-            Fzero[3 * i] = (R)0;
-            Fzero[3 * i + 1] = (R)0;
-            Fzero[3 * i + 2] = (R)0;
-        }
     }
+    __syncthreads();
+    const int nc = scount;
+    for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+        const int i = slist[k];
+        double xw[3], fr[3];
+        int bs[3];
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            xw[t] = (double)wrap_r(pos[3 * i + t], g.L, g.xmaxf);
+            grid_coord(xw[t], g.ratio, g.n, bs[t], fr[t]);
+        }
+        const int tile = ((bs[2] / g.T) * g.ntd + bs[1] / g.T) * g.ntd + bs[0] / g.T;
+        atomicAdd(&hist[tile], 1);
+        const int o = i0 + k;
+        typename V4<R>::T a, c;
+        a.x = (R)xw[0]; a.y = (R)xw[1]; a.z = (R)xw[2]; a.w = q[i];
+        c.x = (R)fr[0]; c.y = (R)fr[1]; c.z = (R)fr[2]; c.w = int_as_real(i, (R)0);
+        ctile[o] = tile;
+        cpos[o] = a;
+        cfrac[o] = c;
+        cbase[o] = bs[0] | (bs[1] << 10) | (bs[2] << 20);
+    }
+    if (threadIdx.x == 0) cnt_blk[b] = nc;
     block_sum2(s1, s2);
     if (threadIdx.x == 0) {
         qpart[2 * b] = s1;
@@ -177,77 +224,130 @@ __global__ void __launch_bounds__(512) k_bin_count(Geo g, int N, const R* __rest
     for (int t = threadIdx.x; t < g.ntiles; t += blockDim.x) bhist[b * g.ntiles + t] = hist[t];
 }
 
-// Exclusive scan over (tile, block) in tile-major order; one CTA of 1024 threads.
-static __global__ void __launch_bounds__(1024) k_bin_scan(Geo g, const int* __restrict__ bhist,
-                                                   int* __restrict__ boff, int* __restrict__ tstart) {
-    __shared__ int wsum[32];
-    const int nt = g.ntiles, nb = g.nbin;
-    const int per = (nt + blockDim.x - 1) / blockDim.x;
-    const int t0 = min(nt, (int)threadIdx.x * per), t1 = min(nt, t0 + per);
-    int local = 0;
-    for (int t = t0; t < t1; ++t)
-        for (int b = 0; b < nb; ++b) local += bhist[b * nt + t];
-    // block exclusive scan of local
-    const int l = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int v = local;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int u = __shfl_up_sync(0xffffffffu, v, o);
-        if (l >= o) v += u;
+// One thread per tile: offsets of each block's beads inside the tile, and the tile total.
+static __global__ void __launch_bounds__(256) k_tile_offsets(Geo g, const int* __restrict__ bhist, int* __restrict__ boff,
+                                                      int* __restrict__ ttot) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= g.ntiles) return;
+    int run = 0;
+    int b = 0;
+    for (; b + 4 <= g.nbin; b += 4) {
+        const int v0 = bhist[b * g.ntiles + t], v1 = bhist[(b + 1) * g.ntiles + t];
+        const int v2 = bhist[(b + 2) * g.ntiles + t], v3 = bhist[(b + 3) * g.ntiles + t];
+        boff[b * g.ntiles + t] = run;
+        boff[(b + 1) * g.ntiles + t] = run + v0;
+        boff[(b + 2) * g.ntiles + t] = run + v0 + v1;
+        boff[(b + 3) * g.ntiles + t] = run + v0 + v1 + v2;
+        run += v0 + v1 + v2 + v3;
     }
-    if (l == 31) wsum[w] = v;
-    __syncthreads();
-    if (w == 0) {
-        int x = wsum[l];
+    for (; b < g.nbin; ++b) {
+        const int v = bhist[b * g.ntiles + t];
+        boff[b * g.ntiles + t] = run;
+        run += v;
+    }
+    ttot[t] = run;
+}
+
+// Exclusive scan of in[0, count) into out[0, count], out[count] = total; one
+// CTA of 1024 threads, 16 elements per thread and round (four 16-byte loads).
+// aux, when given, receives a copy of out; zero_in clears the input.
+static __global__ void __launch_bounds__(1024) k_scan(int* __restrict__ in, int* __restrict__ out, int count,
+                                                      int* __restrict__ aux, int zero_in) {
+    constexpr int IPT = 16;
+    __shared__ int wsum[32];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    int carry = 0;
+    for (int base = 0; base < count; base += 1024 * IPT) {
+        const int i0 = base + IPT * tid;
+        int v[IPT];
+        if (i0 + IPT <= count) {
+#pragma unroll
+            for (int k = 0; k < IPT; k += 4) {
+                const int4 x = *reinterpret_cast<const int4*>(in + i0 + k);
+                v[k] = x.x; v[k + 1] = x.y; v[k + 2] = x.z; v[k + 3] = x.w;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < IPT; ++k) v[k] = i0 + k < count ? in[i0 + k] : 0;
+        }
+        int sum = 0;
+#pragma unroll
+        for (int k = 0; k < IPT; ++k) sum += v[k];
+        int x = sum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const int u = __shfl_up_sync(0xffffffffu, x, o);
-            if (l >= o) x += u;
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
         }
-        wsum[l] = x;
-    }
-    __syncthreads();
-    int run = v - local + (w > 0 ? wsum[w - 1] : 0);
-    for (int t = t0; t < t1; ++t) {
-        tstart[t] = run;
-        for (int b = 0; b < nb; ++b) {
-            boff[b * nt + t] = run;
-            run += bhist[b * nt + t];
+        if (lane == 31) wsum[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            int z = wsum[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, z, o);
+                if (lane >= o) z += y;
+            }
+            wsum[lane] = z;
         }
+        __syncthreads();
+        int run = carry + (x - sum) + (w > 0 ? wsum[w - 1] : 0);
+        const int total = wsum[31];
+        if (i0 + IPT <= count) {
+#pragma unroll
+            for (int k = 0; k < IPT; k += 4) {
+                int4 o4;
+                o4.x = run; run += v[k];
+                o4.y = run; run += v[k + 1];
+                o4.z = run; run += v[k + 2];
+                o4.w = run; run += v[k + 3];
+                *reinterpret_cast<int4*>(out + i0 + k) = o4;
+                if (aux) *reinterpret_cast<int4*>(aux + i0 + k) = o4;
+                if (zero_in) *reinterpret_cast<int4*>(in + i0 + k) = make_int4(0, 0, 0, 0);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < IPT; ++k) {
+                const int idx = i0 + k;
+                if (idx < count) {
+                    out[idx] = run;
+                    if (aux) aux[idx] = run;
+                    if (zero_in) in[idx] = 0;
+                }
+                run += v[k];
+            }
+        }
+        carry += total;
+        __syncthreads();
     }
-    if (threadIdx.x == blockDim.x - 1) tstart[nt] = wsum[31];
+    if (tid == 0) {
+        out[count] = carry;
+        if (aux) aux[count] = carry;
+    }
 }
 
 template <typename R>
-__global__ void __launch_bounds__(512) k_bin_scatter(Geo g, int N, const R* __restrict__ pos,
-                                                    const R* __restrict__ q, const int* __restrict__ key,
-                                                    const int* __restrict__ boff,
-                                                    typename V4<R>::T* __restrict__ sq,
-                                                    typename V4<R>::T* __restrict__ sw,
-                                                    int* __restrict__ sb) {
+__global__ void __launch_bounds__(1024) k_bin_scatter(Geo g, const int* __restrict__ cnt_blk,
+                                                     const int* __restrict__ ctile,
+                                                     const typename V4<R>::T* __restrict__ cpos,
+                                                     const typename V4<R>::T* __restrict__ cfrac,
+                                                     const int* __restrict__ cbase, const int* __restrict__ boff,
+                                                     const int* __restrict__ tstart,
+                                                     typename V4<R>::T* __restrict__ sq,
+                                                     typename V4<R>::T* __restrict__ sw, int* __restrict__ sb) {
     extern __shared__ int cur[];
     const int b = blockIdx.x;
-    for (int t = threadIdx.x; t < g.ntiles; t += blockDim.x) cur[t] = boff[b * g.ntiles + t];
+    for (int t = threadIdx.x; t < g.ntiles; t += blockDim.x) cur[t] = 0;
     __syncthreads();
+    const int nc = cnt_blk[b];
     const int i0 = b * g.chunk;
-    const int i1 = min(N, i0 + g.chunk);
-    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-        const int kk = key[i];
-        if (kk < 0) continue;
-        const int slot = atomicAdd(&cur[kk], 1);
-        double xw[3], fr[3];
-        int bs[3];
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {
-            xw[t] = wrap_to_real<R>(pos[3 * i + t], g.L);
-            grid_coord(xw[t], g.L, g.n, bs[t], fr[t]);
-        }
-        typename V4<R>::T a, c;
-        a.x = (R)xw[0]; a.y = (R)xw[1]; a.z = (R)xw[2]; a.w = q[i];
-        c.x = (R)fr[0]; c.y = (R)fr[1]; c.z = (R)fr[2]; c.w = int_as_real(i, (R)0);
-        sq[slot] = a;
-        sw[slot] = c;
-        sb[slot] = bs[0] | (bs[1] << 10) | (bs[2] << 20);
+    for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+        const int o = i0 + k;
+        const int t = ctile[o];
+        const int slot = tstart[t] + boff[b * g.ntiles + t] + atomicAdd(&cur[t], 1);
+        sq[slot] = cpos[o];
+        sw[slot] = cfrac[o];
+        sb[slot] = cbase[o];
     }
 }
 
@@ -259,6 +359,7 @@ __global__ void __launch_bounds__(512) k_bin_scatter(Geo g, int N, const R* __re
 // ---------------------------------------------------------------------------
 constexpr int kSpreadThreads = 256;
 constexpr int kMaxTaps = 16;
+constexpr int kSpreadCap = 512;   // beads staged in shared memory per round
 
 template <typename R>
 __global__ void __launch_bounds__(kSpreadThreads) k_spread(Geo g, const int* __restrict__ tstart,
@@ -266,35 +367,41 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(Geo g, const int* __r
                                                            const typename V4<R>::T* __restrict__ sw,
                                                            const int* __restrict__ sb,
                                                            R* __restrict__ grid) {
-    extern __shared__ unsigned char smraw[];
+    using V = typename V4<R>::T;
+    extern __shared__ __align__(16) unsigned char smraw[];
     const int T = g.T, T3 = T * T * T;
-    R* acc = reinterpret_cast<R*>(smraw);
     constexpr int NW = kSpreadThreads / 32;
-    R* wts = acc + T3;                                        // [NW][3][16]
-    int* lix = reinterpret_cast<int*>(wts + NW * 3 * kMaxTaps); // [NW][3][16]
-    __shared__ int nb_start[27], nb_pre[28];
+    V* stg = reinterpret_cast<V*>(smraw);                          // [cap] (fx, fy, fz, q)
+    R* acc = reinterpret_cast<R*>(stg + kSpreadCap);                // [T^3]
+    R* wts = acc + T3;                                              // [NW][3][16]
+    int* lix = reinterpret_cast<int*>(wts + NW * 3 * kMaxTaps);     // [NW][3][16]
+    int* sbase = lix + NW * 3 * kMaxTaps;                           // [cap]
+    __shared__ int nb_start[27], nb_cnt[27], nb_pre[28];
     __shared__ int nnb;
 
     const int tile = blockIdx.x;
     const int tx = tile % g.ntd, ty = (tile / g.ntd) % g.ntd, tz = tile / (g.ntd * g.ntd);
     const int o[3] = {tx * T, ty * T, tz * T};
     for (int e = threadIdx.x; e < T3; e += blockDim.x) acc[e] = (R)0;
+    const int no = g.ntd >= 3 ? 3 : g.ntd;
+    if (threadIdx.x < no * no * no) {
+        const int dx = threadIdx.x % no, dy = (threadIdx.x / no) % no, dz = threadIdx.x / (no * no);
+        const int nz = g.ntd >= 3 ? (tz + dz - 1 + g.ntd) % g.ntd : dz;
+        const int ny = g.ntd >= 3 ? (ty + dy - 1 + g.ntd) % g.ntd : dy;
+        const int nx = g.ntd >= 3 ? (tx + dx - 1 + g.ntd) % g.ntd : dx;
+        const int nt = (nz * g.ntd + ny) * g.ntd + nx;
+        const int st = tstart[nt];
+        nb_start[threadIdx.x] = st;
+        nb_cnt[threadIdx.x] = tstart[nt + 1] - st;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        const int no = g.ntd >= 3 ? 3 : g.ntd;
-        int cnt = 0, pre = 0;
-        for (int dz = 0; dz < no; ++dz)
-            for (int dy = 0; dy < no; ++dy)
-                for (int dx = 0; dx < no; ++dx) {
-                    const int nz = g.ntd >= 3 ? (tz + dz - 1 + g.ntd) % g.ntd : dz;
-                    const int ny = g.ntd >= 3 ? (ty + dy - 1 + g.ntd) % g.ntd : dy;
-                    const int nx = g.ntd >= 3 ? (tx + dx - 1 + g.ntd) % g.ntd : dx;
-                    const int nt = (nz * g.ntd + ny) * g.ntd + nx;
-                    const int s = tstart[nt], c = tstart[nt + 1] - s;
-                    nb_start[cnt] = s;
-                    nb_pre[cnt] = pre;
-                    pre += c;
-                    ++cnt;
-                }
+        const int cnt = no * no * no;
+        int pre = 0;
+        for (int k = 0; k < cnt; ++k) {
+            nb_pre[k] = pre;
+            pre += nb_cnt[k];
+        }
         nb_pre[cnt] = pre;
         nnb = cnt;
     }
@@ -304,50 +411,66 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(Geo g, const int* __r
     int* myl = lix + warp * 3 * kMaxTaps;
     const int P2 = 2 * g.p;
     const int total = nb_pre[nnb];
-    const R rb = (R)(1.0 / g.b), wn = (R)g.wnorm;
-    for (int cand = warp; cand < total; cand += NW) {
-        int k = 0;
-        while (nb_pre[k + 1] <= cand) ++k;
-        const int j = nb_start[k] + cand - nb_pre[k];
-        const typename V4<R>::T wv = sw[j];
-        const R qj = sq[j].w;
-        const int pb = sb[j];
-        const int base[3] = {pb & 1023, (pb >> 10) & 1023, (pb >> 20) & 1023};
-        const R fr[3] = {wv.x, wv.y, wv.z};
-        unsigned msk[3];
-        int lw[3];
-        bool inside[3];
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {
-            int l = base[t] - g.p + 1 + lane;
-            l = l < 0 ? l + g.n : (l >= g.n ? l - g.n : l);
-            lw[t] = l - o[t];
-            inside[t] = lane < P2 && (unsigned)lw[t] < (unsigned)T;
-            msk[t] = __ballot_sync(0xffffffffu, inside[t]);
-        }
-        if (!msk[0] || !msk[1] || !msk[2]) continue;
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {
-            if (inside[t]) {
-                const int slot = __popc(msk[t] & ((1u << lane) - 1u));
-                const R d = fr[t] + (R)(g.p - 1 - lane);
-                myw[t * kMaxTaps + slot] = wn * r_exp(-d * d * rb);
-                myl[t * kMaxTaps + slot] = lw[t];
+    const R rb = (R)g.rb, wn = (R)g.wnorm;
+    for (int cb = 0; cb < total; cb += kSpreadCap) {
+        const int cn = min(kSpreadCap, total - cb);
+        // stage this round's candidates (coalesced runs of each neighbouring bin)
+        for (int k = 0; k < nnb; ++k) {
+            const int lo = max(nb_pre[k], cb), hi = min(nb_pre[k + 1], cb + cn);
+            for (int idx = lo + threadIdx.x; idx < hi; idx += blockDim.x) {
+                const int j = nb_start[k] + idx - nb_pre[k];
+                V v = sw[j];
+                v.w = sq[j].w;
+                stg[idx - cb] = v;
+                sbase[idx - cb] = sb[j];
             }
         }
-        __syncwarp();
-        const int cx = __popc(msk[0]), cy = __popc(msk[1]), cz = __popc(msk[2]);
-        const int npt = cx * cy * cz;
-        for (int s = lane; s < npt; s += 32) {
-            const int ix = s % cx;
-            const int r2 = s / cx;
-            const int iy = r2 % cy, iz = r2 / cy;
-            const R v = qj * myw[ix] * myw[kMaxTaps + iy] * myw[2 * kMaxTaps + iz];
-            atomicAdd(&acc[(myl[2 * kMaxTaps + iz] * T + myl[kMaxTaps + iy]) * T + myl[ix]], v);
+        __syncthreads();
+        for (int c = warp; c < cn; c += NW) {
+            const V wv = stg[c];
+            const int pb = sbase[c];
+            const int base[3] = {pb & 1023, (pb >> 10) & 1023, (pb >> 20) & 1023};
+            const R fr[3] = {wv.x, wv.y, wv.z};
+            unsigned msk[3];
+            int lw[3];
+            bool inside[3];
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                int l = base[t] - g.p + 1 + lane;
+                l = l < 0 ? l + g.n : (l >= g.n ? l - g.n : l);
+                lw[t] = l - o[t];
+                inside[t] = lane < P2 && (unsigned)lw[t] < (unsigned)T;
+                msk[t] = __ballot_sync(0xffffffffu, inside[t]);
+            }
+            if (!msk[0] || !msk[1] || !msk[2]) continue;
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                if (inside[t]) {
+                    const int slot = __popc(msk[t] & ((1u << lane) - 1u));
+                    const R d = fr[t] + (R)(g.p - 1 - lane);
+                    myw[t * kMaxTaps + slot] = wn * r_exp(-d * d * rb);
+                    myl[t * kMaxTaps + slot] = lw[t];
+                }
+            }
+            __syncwarp();
+            const int cx = __popc(msk[0]), cy = __popc(msk[1]), cz = __popc(msk[2]);
+            const int cxy = cx * cy, npt = cxy * cz;
+            // s -> (ix, iy, iz) by float reciprocals: s < 4096 and the true quotient
+            // of s + 1/2 is at least 1/32 away from an integer, far above the error
+            const float icx = 1.0f / (float)cx, icxy = 1.0f / (float)cxy;
+            const R qj = wv.w;
+            for (int s = lane; s < npt; s += 32) {
+                const int iz = (int)(((float)s + 0.5f) * icxy);
+                const int r2 = s - iz * cxy;
+                const int iy = (int)(((float)r2 + 0.5f) * icx);
+                const int ix = r2 - iy * cx;
+                const R v = qj * myw[ix] * myw[kMaxTaps + iy] * myw[2 * kMaxTaps + iz];
+                atomicAdd(&acc[(myl[2 * kMaxTaps + iz] * T + myl[kMaxTaps + iy]) * T + myl[ix]], v);
+            }
+            __syncwarp();
         }
-        __syncwarp();
+        __syncthreads();
     }
-    __syncthreads();
     const int n = g.n;
     for (int e = threadIdx.x; e < T3; e += blockDim.x) {
         const int lx = e % T, ly = (e / T) % T, lz = e / (T * T);
@@ -602,8 +725,8 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Geo g, const int* __r
     const int n = g.n;
     const size_t n3 = (size_t)n * n * n;
     const int P2 = 2 * g.p, ntap = P2 * P2 * P2;
-    const R rb = (R)(1.0 / g.b), wn = (R)g.wnorm;
-    const R pref = (R)(g.kappa * 2.0 / (g.L * g.L));
+    const R rb = (R)g.rb, wn = (R)g.wnorm;
+    const R pref = (R)g.pref;
     for (int s = blockIdx.x * NW + warp; s < Nq; s += gridDim.x * NW) {
         const typename V4<R>::T wv = sw[s];
         const R qs = sq[s].w;
@@ -652,117 +775,218 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Geo g, const int* __r
 // stride over the candidates of each contiguous run of tiles.
 // ---------------------------------------------------------------------------
 constexpr int kRealThreads = 256;
+constexpr int kRealCap = 2048;     // staged beads (x, y, z, q)
+constexpr int kRealHalo = 1024;    // halo tiles (stencil up to 9 x 9 x 9 + 1 for the prefix)
 
-__device__ __forceinline__ void stencil_dim(int t, int rs, int ntd, int& lo, int& cnt, bool& whole) {
-    whole = 2 * rs + 1 >= ntd;
-    if (whole) { lo = 0; cnt = ntd; }
+// Pair energy u(r) and radial force f(r) = -du/dr of the real-space sum:
+// erfc(alpha r)/r minus the Slater correction (1 + beta r) e^{-2 beta r}/r.
+template <typename R>
+__device__ __forceinline__ void real_pair(R r2, R al, R c2a, R be, bool slater, R& u, R& fr_over_r, R& f_r) {
+    const R ir = r_rsqrt(r2);
+    const R r = r2 * ir;
+    const R ar = al * r;
+    const R ec = r_erfc(ar);
+    R uu = ec * ir;
+    R ff = ec * ir * ir + c2a * r_exp(-ar * ar) * ir;
+    if (slater) {
+        const R br = be * r;
+        const R e2 = r_exp((R)-2 * br);
+        uu -= ((R)1 + br) * e2 * ir;
+        ff -= ((R)1 + (R)2 * br + (R)2 * br * br) * e2 * ir * ir;
+    }
+    u = uu;
+    fr_over_r = ff * ir;   // multiplies the displacement vector
+    f_r = ff * r;          // virial term r f(r)
+}
+
+// One lane per queued pair (lanes < m).
+template <typename R, typename V>
+__device__ __forceinline__ void real_drain(const V* qu, int m, int lane, R qi, R kap, R al, R c2a, R be, bool slater,
+                                           R& fx, R& fy, R& fz, R& eacc, R& wacc) {
+    if (lane < m) {
+        const V e = qu[lane];
+        const R r2 = dist2(e.x, e.y, e.z);
+        R u, fo, fr;
+        real_pair<R>(r2, al, c2a, be, slater, u, fo, fr);
+        const R qq = kap * qi * e.w;
+        fx += qq * fo * e.x;
+        fy += qq * fo * e.y;
+        fz += qq * fo * e.z;
+        eacc += (R)0.5 * qq * u;
+        wacc += (R)0.5 * qq * fr;
+    }
+}
+
+// Halo of a tile: per dimension either the whole periodic row of tiles (when
+// the stencil 2 rs + 1 covers it) or the tiles t - rs .. t + rs.
+__device__ __forceinline__ void halo_dim(int t, int rs, int ntd, int& lo, int& cnt) {
+    if (2 * rs + 1 >= ntd) { lo = 0; cnt = ntd; }
     else { lo = t - rs; cnt = 2 * rs + 1; }
 }
 
+// Real-space erfc + Slater-correction pairs (Eq. 31, corrected Eq. 32,
+// Eq. 27-28). One CTA per grid tile: the beads of the tiles within r_c (the
+// stencil) are staged in shared memory with coalesced loads; one warp per
+// bead of the central tile runs over the staged candidates; accepted pairs
+// are compacted in a per-warp queue so the erfc/exp arithmetic runs on full
+// warps.
 template <typename R>
 __global__ void __launch_bounds__(kRealThreads) k_real(Geo g, const int* __restrict__ tstart,
                                                        const typename V4<R>::T* __restrict__ sq,
                                                        const typename V4<R>::T* __restrict__ sw,
-                                                       const int* __restrict__ sb,
                                                        R* __restrict__ F, double* __restrict__ rpart) {
+    using V = typename V4<R>::T;
     constexpr int NW = kRealThreads / 32;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int Nq = tstart[g.ntiles];
+    extern __shared__ __align__(16) unsigned char smraw[];
+    V* stg = reinterpret_cast<V*>(smraw);                       // [kRealCap]
+    V* queue = stg + kRealCap;                                  // [NW][64]
+    int* hoff = reinterpret_cast<int*>(queue + NW * 64);        // [kRealHalo + 1]
+    int* gst = hoff + kRealHalo + 1;                            // [kRealHalo]
+    __shared__ int wtot[NW];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    V* qu = queue + warp * 64;
     const R L = (R)g.L, hL = (R)(0.5 * g.L);
     const R rc2 = (R)(g.rc * g.rc);
-    const R al = (R)g.alpha, c2a = (R)(2.0 * g.alpha / 1.7724538509055160273);
-    const R be = (R)g.beta;
+    const R al = (R)g.alpha, c2a = (R)g.c2a, be = (R)g.beta, kap = (R)g.kappa;
     const bool slater = g.beta > 0.0;
-    double eacc = 0.0, wacc = 0.0;
-    for (int s = blockIdx.x * NW + warp; s < Nq; s += gridDim.x * NW) {
-        const typename V4<R>::T pi = sq[s];
-        const int pb = sb[s];
-        const int tx = (pb & 1023) / g.T, ty = ((pb >> 10) & 1023) / g.T, tz = ((pb >> 20) & 1023) / g.T;
-        R fx = 0, fy = 0, fz = 0;
-        int zlo, zc, ylo, yc, xlo, xc;
-        bool zw, yw, xw;
-        stencil_dim(tz, g.rs, g.ntd, zlo, zc, zw);
-        stencil_dim(ty, g.rs, g.ntd, ylo, yc, yw);
-        stencil_dim(tx, g.rs, g.ntd, xlo, xc, xw);
-        for (int iz = 0; iz < zc; ++iz) {
-            const int nz = (zlo + iz + g.ntd) % g.ntd;
-            for (int iy = 0; iy < yc; ++iy) {
-                const int ny = (ylo + iy + g.ntd) % g.ntd;
-                const int rowbase = (nz * g.ntd + ny) * g.ntd;
-                // the x run is contiguous unless it wraps: at most two ranges
-                int r0s[2], r0e[2], nr;
-                if (xw) {
-                    r0s[0] = tstart[rowbase]; r0e[0] = tstart[rowbase + g.ntd]; nr = 1;
-                } else if (xlo >= 0 && xlo + xc <= g.ntd) {
-                    r0s[0] = tstart[rowbase + xlo]; r0e[0] = tstart[rowbase + xlo + xc]; nr = 1;
-                } else if (xlo < 0) {
-                    r0s[0] = tstart[rowbase + xlo + g.ntd]; r0e[0] = tstart[rowbase + g.ntd];
-                    r0s[1] = tstart[rowbase]; r0e[1] = tstart[rowbase + xlo + xc]; nr = 2;
-                } else {
-                    r0s[0] = tstart[rowbase + xlo]; r0e[0] = tstart[rowbase + g.ntd];
-                    r0s[1] = tstart[rowbase]; r0e[1] = tstart[rowbase + xlo + xc - g.ntd]; nr = 2;
+    R eacc = 0, wacc = 0;
+    for (int tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x) {
+        const int tx = tile % g.ntd, ty = (tile / g.ntd) % g.ntd, tz = tile / (g.ntd * g.ntd);
+        int xlo, xc, ylo, yc, zlo, zc;
+        halo_dim(tx, g.rs, g.ntd, xlo, xc);
+        halo_dim(ty, g.rs, g.ntd, ylo, yc);
+        halo_dim(tz, g.rs, g.ntd, zlo, zc);
+        const int nh = xc * yc * zc;   // <= kRealHalo by construction of the plan
+        // halo tile ranges and their exclusive prefix (block scan, <= 4 per thread)
+        int cnt4[4], sum = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int h = 4 * tid + k;
+            cnt4[k] = 0;
+            if (h < nh) {
+                const int hx = h % xc, hy = (h / xc) % yc, hz = h / (xc * yc);
+                const int ax = (xlo + hx + g.ntd) % g.ntd, ay = (ylo + hy + g.ntd) % g.ntd,
+                          az = (zlo + hz + g.ntd) % g.ntd;
+                const int t = (az * g.ntd + ay) * g.ntd + ax;
+                const int st = tstart[t];
+                gst[h] = st;
+                cnt4[k] = tstart[t + 1] - st;
+            }
+            sum += cnt4[k];
+        }
+        int x = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wtot[warp] = x;
+        __syncthreads();
+        int run = x - sum;
+        for (int w = 0; w < warp; ++w) run += wtot[w];
+        int total = 0;
+        for (int w = 0; w < NW; ++w) total += wtot[w];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int h = 4 * tid + k;
+            if (h < nh) hoff[h] = run;
+            run += cnt4[k];
+        }
+        if (tid == 0) hoff[nh] = total;
+        __syncthreads();
+        const bool staged = total <= kRealCap;
+        if (staged) {
+            for (int f = tid; f < total; f += blockDim.x) {
+                int lo = 0, hi = nh;   // last h with hoff[h] <= f
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (hoff[mid] <= f) lo = mid; else hi = mid;
                 }
-                for (int rr = 0; rr < nr; ++rr) {
-                    for (int j = r0s[rr] + lane; j < r0e[rr]; j += 32) {
-                        if (j == s) continue;
-                        const typename V4<R>::T pj = sq[j];
-                        const R dx = min_image(pi.x, pj.x, L, hL);
-                        const R dy = min_image(pi.y, pj.y, L, hL);
-                        const R dz = min_image(pi.z, pj.z, L, hL);
-                        const R r2 = dist2(dx, dy, dz);
-                        if (!(r2 < rc2) || r2 <= (R)0) continue;
-                        const R r = r_sqrt(r2);
-                        const R ir = (R)1 / r;
-                        const R ar = al * r;
-                        const R ec = r_erfc(ar);
-                        R u = ec * ir;
-                        R f = ec * ir * ir + c2a * r_exp(-ar * ar) * ir;
-                        if (slater) {
-                            const R br = be * r;
-                            const R e2 = r_exp((R)-2 * br);
-                            u -= ((R)1 + br) * e2 * ir;
-                            f -= ((R)1 + (R)2 * br + (R)2 * br * br) * e2 * ir * ir;
-                        }
-                        const R qq = (R)g.kappa * pi.w * pj.w;
-                        const R fm = qq * f * ir;
-                        fx += fm * dx;
-                        fy += fm * dy;
-                        fz += fm * dz;
-                        eacc += 0.5 * (double)(qq * u);
-                        wacc += 0.5 * (double)(qq * f * r);
-                    }
-                }
+                stg[f] = sq[gst[lo] + f - hoff[lo]];
             }
         }
-        fx = warp_sum_r(fx);
-        fy = warp_sum_r(fy);
-        fz = warp_sum_r(fz);
-        if (lane == 0) {
-            const int i = real_as_int(sw[s].w);
-            F[3 * i] += fx;
-            F[3 * i + 1] += fy;
-            F[3 * i + 2] += fz;
+        __syncthreads();
+        // the central tile's own beads
+        const int c0 = tstart[tile], c1 = tstart[tile + 1];
+        const int hc = (((tz - zlo + g.ntd) % g.ntd) * yc + (ty - ylo + g.ntd) % g.ntd) * xc + (tx - xlo + g.ntd) % g.ntd;
+        for (int s = c0 + warp; s < c1; s += NW) {
+            const V pi = sq[s];
+            const int self = hoff[hc] + (s - c0);
+            R fx = 0, fy = 0, fz = 0;
+            int cnt = 0;
+            int hseg = 0;
+            for (int fb = 0; fb < total; fb += 32) {
+                const int f = fb + lane;
+                bool hit = false;
+                R dx = 0, dy = 0, dz = 0, qj = 0;
+                if (f < total && f != self) {
+                    V pj;
+                    if (staged) {
+                        pj = stg[f];
+                    } else {
+                        while (hoff[hseg + 1] <= f) ++hseg;
+                        pj = sq[gst[hseg] + f - hoff[hseg]];
+                    }
+                    dx = min_image(pi.x, pj.x, L, hL);
+                    dy = min_image(pi.y, pj.y, L, hL);
+                    dz = min_image(pi.z, pj.z, L, hL);
+                    const R r2 = dist2(dx, dy, dz);
+                    hit = r2 < rc2 && r2 > (R)0;
+                    qj = pj.w;
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, hit);
+                if (hit) {
+                    V e;
+                    e.x = dx; e.y = dy; e.z = dz; e.w = qj;
+                    qu[cnt + __popc(m & ((1u << lane) - 1u))] = e;
+                }
+                cnt += __popc(m);
+                if (cnt >= 32) {
+                    __syncwarp();
+                    real_drain<R, V>(qu, 32, lane, pi.w, kap, al, c2a, be, slater, fx, fy, fz, eacc, wacc);
+                    __syncwarp();
+                    if (lane < cnt - 32) qu[lane] = qu[32 + lane];
+                    __syncwarp();
+                    cnt -= 32;
+                }
+            }
+            __syncwarp();
+            real_drain<R, V>(qu, cnt, lane, pi.w, kap, al, c2a, be, slater, fx, fy, fz, eacc, wacc);
+            __syncwarp();
+            fx = warp_sum_r(fx);
+            fy = warp_sum_r(fy);
+            fz = warp_sum_r(fz);
+            if (lane == 0) {
+                const int i = real_as_int(sw[s].w);
+                F[3 * i] += fx;
+                F[3 * i + 1] += fy;
+                F[3 * i + 2] += fz;
+            }
         }
+        __syncthreads();
     }
-    block_sum2(eacc, wacc);
+    double e = (double)eacc, w = (double)wacc;
+    block_sum2(e, w);
     if (threadIdx.x == 0) {
-        rpart[2 * blockIdx.x] = eacc;
-        rpart[2 * blockIdx.x + 1] = wacc;
+        rpart[2 * blockIdx.x] = e;
+        rpart[2 * blockIdx.x + 1] = w;
     }
 }
 
 // ---------------------------------------------------------------------------
 // DPD: cell list of all beads (edge >= 1) by a counting sort.
 // ---------------------------------------------------------------------------
+// Cells of edge L/ncd > 1 (the plan keeps a relative margin so that rounding
+// of x * ncd/L cannot separate two beads closer than 1 by two cells).
 template <typename R>
-__global__ void k_cell_count(int N, int ncd, double L, const R* __restrict__ pos, int* __restrict__ ckey,
-                             int* __restrict__ ccount) {
-    const double inv = (double)ncd / L;
+__global__ void k_cell_count(int N, int ncd, double L, double inv, float xmaxf, const R* __restrict__ pos,
+                             int* __restrict__ ckey, int* __restrict__ ccount) {
+    const R rinv = (R)inv;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
         int c[3];
 #pragma unroll
         for (int t = 0; t < 3; ++t) {
-            int v = (int)floor(wrap_to_real<R>(pos[3 * i + t], L) * inv);
+            int v = (int)(wrap_r(pos[3 * i + t], L, xmaxf) * rinv);
             c[t] = v < 0 ? 0 : (v >= ncd ? ncd - 1 : v);
         }
         const int cell = (c[2] * ncd + c[1]) * ncd + c[0];
@@ -771,53 +995,17 @@ __global__ void k_cell_count(int N, int ncd, double L, const R* __restrict__ pos
     }
 }
 
-static __global__ void __launch_bounds__(1024) k_cell_scan(int ncells, int* __restrict__ ccount,
-                                                    int* __restrict__ cstart, int* __restrict__ ccur) {
-    __shared__ int wsum[32];
-    const int per = (ncells + blockDim.x - 1) / blockDim.x;
-    const int t0 = min(ncells, (int)threadIdx.x * per), t1 = min(ncells, t0 + per);
-    int local = 0;
-    for (int t = t0; t < t1; ++t) local += ccount[t];
-    const int l = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int v = local;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int u = __shfl_up_sync(0xffffffffu, v, o);
-        if (l >= o) v += u;
-    }
-    if (l == 31) wsum[w] = v;
-    __syncthreads();
-    if (w == 0) {
-        int x = wsum[l];
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int u = __shfl_up_sync(0xffffffffu, x, o);
-            if (l >= o) x += u;
-        }
-        wsum[l] = x;
-    }
-    __syncthreads();
-    int run = v - local + (w > 0 ? wsum[w - 1] : 0);
-    for (int t = t0; t < t1; ++t) {
-        cstart[t] = run;
-        ccur[t] = run;
-        run += ccount[t];
-        ccount[t] = 0;   // ready for the next step
-    }
-    if (threadIdx.x == blockDim.x - 1) cstart[ncells] = wsum[31];
-}
-
 template <typename R>
-__global__ void k_cell_scatter(int N, double L, const R* __restrict__ pos, const R* __restrict__ v0,
+__global__ void k_cell_scatter(int N, double L, float xmaxf, const R* __restrict__ pos, const R* __restrict__ v0,
                                const int* __restrict__ type, const int* __restrict__ ckey,
                                int* __restrict__ ccur, typename V4<R>::T* __restrict__ sp,
                                typename V4<R>::T* __restrict__ sv) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
         const int slot = atomicAdd(&ccur[ckey[i]], 1);
         typename V4<R>::T a, b;
-        a.x = (R)wrap_to_real<R>(pos[3 * i], L);
-        a.y = (R)wrap_to_real<R>(pos[3 * i + 1], L);
-        a.z = (R)wrap_to_real<R>(pos[3 * i + 2], L);
+        a.x = wrap_r(pos[3 * i], L, xmaxf);
+        a.y = wrap_r(pos[3 * i + 1], L, xmaxf);
+        a.z = wrap_r(pos[3 * i + 2], L, xmaxf);
         a.w = int_as_real(i, (R)0);
         b.x = v0[3 * i];
         b.y = v0[3 * i + 1];
@@ -859,91 +1047,259 @@ __device__ __forceinline__ R dpd_theta(uint64_t seed, uint64_t step, int i, int 
     return (R)1.7320508075688772935 * ((R)2 * u - (R)1);
 }
 
-// DPD pair forces (Eq. 2-7, R_c = 1) + bonds (Sec. 2); thread per bead in
-// cell order; F[i] = F^C + F^D + F^R/sqrt(dt) + F^S (overwrites F).
-template <typename R>
-__global__ void __launch_bounds__(256) k_dpd(DpdDev d, const typename V4<R>::T* __restrict__ sp,
-                                            const typename V4<R>::T* __restrict__ sv,
-                                            const int* __restrict__ ckey, const int* __restrict__ cstart,
-                                            const R* __restrict__ atab, const R* __restrict__ pos,
-                                            const int* __restrict__ bptr, const int* __restrict__ blist,
-                                            const uint64_t* __restrict__ stepp, R* __restrict__ F,
-                                            double* __restrict__ dpart) {
-    const R L = (R)d.L, hL = (R)(0.5 * d.L);
-    const R gam = (R)d.gamma, sig = (R)d.sigma, rdt = (R)(1.0 / sqrt(d.dt));
-    const R Kb = (R)d.K_bond, r0b = (R)d.r0_bond;
-    const uint64_t step = *stepp;
-    const int ncd = d.ncd;
-    double ec = 0.0, eb = 0.0;
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < d.N; s += gridDim.x * blockDim.x) {
-        const typename V4<R>::T pi = sp[s];
-        const typename V4<R>::T vi = sv[s];
-        const int i = real_as_int(pi.w), ti = real_as_int(vi.w);
-        const int cell = ckey[i];
-        const int cx = cell % ncd, cy = (cell / ncd) % ncd, cz = cell / (ncd * ncd);
-        R fx = 0, fy = 0, fz = 0;
-        const int no = ncd >= 3 ? 3 : ncd;
-        for (int dz = 0; dz < no; ++dz) {
-            const int nz = ncd >= 3 ? (cz + dz - 1 + ncd) % ncd : dz;
-            for (int dy = 0; dy < no; ++dy) {
-                const int ny = ncd >= 3 ? (cy + dy - 1 + ncd) % ncd : dy;
-                for (int dx = 0; dx < no; ++dx) {
-                    const int nx = ncd >= 3 ? (cx + dx - 1 + ncd) % ncd : dx;
-                    const int nb = (nz * ncd + ny) * ncd + nx;
-                    const int e = cstart[nb + 1];
-                    for (int j = cstart[nb]; j < e; ++j) {
-                        if (j == s) continue;
-                        const typename V4<R>::T pj = sp[j];
-                        const R rx = min_image(pi.x, pj.x, L, hL);
-                        const R ry = min_image(pi.y, pj.y, L, hL);
-                        const R rz = min_image(pi.z, pj.z, L, hL);
-                        const R r2 = dist2(rx, ry, rz);
-                        if (!(r2 < (R)1) || r2 <= (R)0) continue;
-                        const typename V4<R>::T vj = sv[j];
-                        const int jj = real_as_int(pj.w), tj = real_as_int(vj.w);
-                        const R r = r_sqrt(r2);
-                        const R ir = (R)1 / r;
-                        const R ex = rx * ir, ey = ry * ir, ez = rz * ir;
-                        const R w = (R)1 - r;
-                        const R a = atab[ti * d.ntypes + tj];
-                        const R vr = (vi.x - vj.x) * ex + (vi.y - vj.y) * ey + (vi.z - vj.z) * ez;
-                        const R th = dpd_theta<R>(d.seed, step, i, jj);
-                        const R fm = a * w - gam * w * w * vr + sig * w * th * rdt;
-                        fx += fm * ex;
-                        fy += fm * ey;
-                        fz += fm * ez;
-                        ec += 0.25 * (double)(a * w * w);
-                    }
+// DPD pair forces (Eq. 2-7, R_c = 1) + bonds (Sec. 2); F[i] = F^C + F^D +
+// F^R/sqrt(dt) + F^S (overwrites F). One CTA per B^3 block of cells: the beads
+// of the (B+2)^3 halo cells are staged in shared memory with coalesced loads.
+// One warp per central cell: the cell's 27-cell neighbourhood is laid out as
+// one candidate map, lanes sweep it for each bead of the cell, accepted pairs
+// go to a per-warp queue, and the pair arithmetic (Philox draw, weights,
+// dissipation) runs on full warps; forces accumulate per bead in shared memory.
+constexpr int kDpdThreads = 256;
+constexpr int kDpdCap = 1024;    // staged beads
+constexpr int kDpdCand = 384;    // candidate map entries per warp
+constexpr int kDpdIMax = 32;     // beads of one cell handled together
+constexpr int kDpdMaxB = 4;      // cells per block edge
+
+struct DpdShared {
+    int* cand;    // [kDpdCand] candidate map of this warp
+    int2* queue;  // [64] accepted (bead slot, candidate) pairs
+};
+
+template <typename R, typename V>
+__device__ __forceinline__ void dpd_drain(int m, int lane, const int2* queue, int cb, const V* P, const V* Pv,
+                                          R* acc, const R* atab, int ntypes, R L, R hL, R gam, R sig, R rdt,
+                                          uint64_t seed, uint64_t step, R& ec) {
+    if (lane < m) {
+        const int2 e = queue[lane];
+        const V pi = P[cb + e.x], vi = Pv[cb + e.x];
+        const V pj = P[e.y], vj = Pv[e.y];
+        const R rx = min_image(pi.x, pj.x, L, hL);
+        const R ry = min_image(pi.y, pj.y, L, hL);
+        const R rz = min_image(pi.z, pj.z, L, hL);
+        const R r2 = dist2(rx, ry, rz);
+        const R ir = r_rsqrt(r2);
+        const R r = r2 * ir;
+        const R w = (R)1 - r;
+        const int i = real_as_int(pi.w), jj = real_as_int(pj.w);
+        const int ti = real_as_int(vi.w), tj = real_as_int(vj.w);
+        const R a = atab[ti * ntypes + tj];
+        const R vr = ((vi.x - vj.x) * rx + (vi.y - vj.y) * ry + (vi.z - vj.z) * rz) * ir;
+        const R th = dpd_theta<R>(seed, step, i, jj);
+        const R fm = (a * w - gam * w * w * vr + sig * w * th * rdt) * ir;
+        atomicAdd(&acc[3 * e.x], fm * rx);
+        atomicAdd(&acc[3 * e.x + 1], fm * ry);
+        atomicAdd(&acc[3 * e.x + 2], fm * rz);
+        ec += (R)0.25 * a * w * w;
+    }
+}
+
+// Sweep the candidate map (mc entries) for the ni beads of the current chunk.
+template <typename R, typename V>
+__device__ __forceinline__ void dpd_sweep(int mc, int ni, int i0, int lane, const int* cand, int2* queue, int& cnt,
+                                          int cb, const V* P, const V* Pv, R* acc, const R* atab, int ntypes, R L,
+                                          R hL, R gam, R sig, R rdt, uint64_t seed, uint64_t step, R& ec) {
+    for (int ii = 0; ii < ni; ++ii) {
+        const int me = cb + i0 + ii;
+        const V pi = P[me];
+        for (int jb = 0; jb < mc; jb += 32) {
+            const int jf = jb + lane;
+            bool hit = false;
+            int j = 0;
+            if (jf < mc) {
+                j = cand[jf];
+                if (j != me) {
+                    const V pj = P[j];
+                    const R rx = min_image(pi.x, pj.x, L, hL);
+                    const R ry = min_image(pi.y, pj.y, L, hL);
+                    const R rz = min_image(pi.z, pj.z, L, hL);
+                    const R r2 = dist2(rx, ry, rz);
+                    hit = r2 < (R)1 && r2 > (R)0;
                 }
             }
-        }
-        // harmonic bonds
-        for (int k = bptr[i]; k < bptr[i + 1]; ++k) {
-            const int j = blist[k];
-            R dd[3];
-#pragma unroll
-            for (int t = 0; t < 3; ++t) {
-                const R xi = (R)wrap_to_real<R>(pos[3 * i + t], d.L);
-                const R xj = (R)wrap_to_real<R>(pos[3 * j + t], d.L);
-                dd[t] = min_image(xi, xj, L, hL);
-            }
-            const R r = r_sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
-            eb += 0.25 * (double)(Kb * (r - r0b) * (r - r0b));
-            if (r > (R)0) {
-                const R fm = -Kb * (r - r0b) / r;
-                fx += fm * dd[0];
-                fy += fm * dd[1];
-                fz += fm * dd[2];
+            const unsigned m = __ballot_sync(0xffffffffu, hit);
+            if (hit) queue[cnt + __popc(m & ((1u << lane) - 1u))] = make_int2(i0 + ii, j);
+            cnt += __popc(m);
+            if (cnt >= 32) {
+                __syncwarp();
+                dpd_drain<R, V>(32, lane, queue, cb, P, Pv, acc, atab, ntypes, L, hL, gam, sig, rdt, seed, step, ec);
+                __syncwarp();
+                if (lane < cnt - 32) queue[lane] = queue[32 + lane];
+                __syncwarp();
+                cnt -= 32;
             }
         }
-        F[3 * i] = fx;
-        F[3 * i + 1] = fy;
-        F[3 * i + 2] = fz;
     }
-    block_sum2(ec, eb);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kDpdThreads) k_dpd(DpdDev d, int B, const typename V4<R>::T* __restrict__ sp,
+                                                     const typename V4<R>::T* __restrict__ sv,
+                                                     const int* __restrict__ cstart, const R* __restrict__ atab,
+                                                     const R* __restrict__ pos, const int* __restrict__ bptr,
+                                                     const int* __restrict__ blist,
+                                                     const uint64_t* __restrict__ stepp, R* __restrict__ F,
+                                                     double* __restrict__ dpart) {
+    using V = typename V4<R>::T;
+    constexpr int NW = kDpdThreads / 32;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    V* spos = reinterpret_cast<V*>(smraw);                                  // [kDpdCap]
+    V* svel = spos + kDpdCap;                                               // [kDpdCap]
+    R* accs = reinterpret_cast<R*>(svel + kDpdCap);                         // [NW][kDpdIMax][3]
+    int2* queues = reinterpret_cast<int2*>(accs + NW * kDpdIMax * 3);       // [NW][64]
+    int* cands = reinterpret_cast<int*>(queues + NW * 64);                  // [NW][kDpdCand]
+    constexpr int HMAX = (kDpdMaxB + 2) * (kDpdMaxB + 2) * (kDpdMaxB + 2);
+    __shared__ int hoff[HMAX + 1], gst[HMAX];
+    __shared__ int chalo[kDpdMaxB * kDpdMaxB * kDpdMaxB];
+    const R L = (R)d.L, hL = (R)(0.5 * d.L);
+    const R gam = (R)d.gamma, sig = (R)d.sigma, rdt = (R)d.rdt;
+    const R Kb = (R)d.K_bond, r0b = (R)d.r0_bond;
+    const uint64_t step = *stepp;
+    const int ncd = d.ncd, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    R* acc = accs + warp * kDpdIMax * 3;
+    int2* queue = queues + warp * 64;
+    int* cand = cands + warp * kDpdCand;
+    const int H = B + 2, H3 = H * H * H, B3 = B * B * B;
+    const int nblk = (ncd + B - 1) / B;
+    R ec = 0, eb = 0;
+    for (int blk = blockIdx.x; blk < nblk * nblk * nblk; blk += gridDim.x) {
+        const int bx = blk % nblk, by = (blk / nblk) % nblk, bz = blk / (nblk * nblk);
+        const int c0x = bx * B, c0y = by * B, c0z = bz * B;
+        if (tid < H3) {   // halo cell ranges (H^3 <= 216 cells)
+            const int hx = tid % H, hy = (tid / H) % H, hz = tid / (H * H);
+            const int cx = (c0x - 1 + hx + ncd) % ncd, cy = (c0y - 1 + hy + ncd) % ncd,
+                      cz = (c0z - 1 + hz + ncd) % ncd;
+            const int c = (cz * ncd + cy) * ncd + cx;
+            const int st = cstart[c];
+            gst[tid] = st;
+            hoff[tid] = cstart[c + 1] - st;
+        }
+        if (tid < B3) {   // central cells of this block (clipped at the box edge)
+            const int ix = tid % B, iy = (tid / B) % B, iz = tid / (B * B);
+            const bool ok = c0x + ix < ncd && c0y + iy < ncd && c0z + iz < ncd;
+            chalo[tid] = ok ? ((iz + 1) * H + (iy + 1)) * H + (ix + 1) : -1;
+        }
+        __syncthreads();
+        if (warp == 0) {   // exclusive prefix of the halo counts (<= 7 per lane)
+            const int per = (H3 + 31) / 32;
+            int v[7], sum = 0;
+#pragma unroll
+            for (int k = 0; k < 7; ++k) {
+                const int h = lane * per + k;
+                v[k] = (k < per && h < H3) ? hoff[h] : 0;
+                sum += v[k];
+            }
+            int x = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            int run = x - sum;
+#pragma unroll
+            for (int k = 0; k < 7; ++k) {
+                const int h = lane * per + k;
+                if (k < per && h < H3) hoff[h] = run;
+                run += v[k];
+            }
+            if (lane == 31) hoff[H3] = x;
+        }
+        __syncthreads();
+        const int total = hoff[H3];
+        const bool staged = total <= kDpdCap;
+        if (staged) {
+            for (int f = tid; f < total; f += blockDim.x) {
+                int lo = 0, hi = H3;
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (hoff[mid] <= f) lo = mid; else hi = mid;
+                }
+                const int j = gst[lo] + f - hoff[lo];
+                spos[f] = sp[j];
+                svel[f] = sv[j];
+            }
+        }
+        __syncthreads();
+        const V* P = staged ? spos : sp;
+        const V* Pv = staged ? svel : sv;
+        for (int cc = warp; cc < B3; cc += NW) {
+            const int h = chalo[cc];
+            if (h < 0) continue;
+            const int cb = staged ? hoff[h] : gst[h];
+            const int nall = hoff[h + 1] - hoff[h];
+            for (int i0 = 0; i0 < nall; i0 += kDpdIMax) {
+                const int ni = min(kDpdIMax, nall - i0);
+                for (int k = lane; k < 3 * kDpdIMax; k += 32) acc[k] = (R)0;
+                int cnt = 0, mc = 0;
+                __syncwarp();
+                // candidate segments: 9 rows of 3 contiguous cells when staged, else 27 cells
+                const int nseg = staged ? 9 : 27;
+                for (int seg = 0; seg < nseg; ++seg) {
+                    int sbase, slen;
+                    if (staged) {
+                        const int hr = h + ((seg / 3 - 1) * H + (seg % 3 - 1)) * H - 1;
+                        sbase = hoff[hr];
+                        slen = hoff[hr + 3] - sbase;
+                    } else {
+                        const int hc = h + ((seg / 9 - 1) * H + ((seg / 3) % 3 - 1)) * H + (seg % 3 - 1);
+                        sbase = gst[hc];
+                        slen = hoff[hc + 1] - hoff[hc];
+                    }
+                    while (slen > 0) {
+                        if (mc == kDpdCand) {
+                            dpd_sweep<R, V>(mc, ni, i0, lane, cand, queue, cnt, cb, P, Pv, acc, atab, d.ntypes, L,
+                                            hL, gam, sig, rdt, d.seed, step, ec);
+                            mc = 0;
+                        }
+                        const int take = min(slen, kDpdCand - mc);
+                        for (int t = lane; t < take; t += 32) cand[mc + t] = sbase + t;
+                        __syncwarp();
+                        mc += take;
+                        sbase += take;
+                        slen -= take;
+                    }
+                }
+                dpd_sweep<R, V>(mc, ni, i0, lane, cand, queue, cnt, cb, P, Pv, acc, atab, d.ntypes, L, hL, gam, sig,
+                                rdt, d.seed, step, ec);
+                __syncwarp();
+                dpd_drain<R, V>(cnt, lane, queue, cb, P, Pv, acc, atab, d.ntypes, L, hL, gam, sig, rdt, d.seed,
+                                step, ec);
+                __syncwarp();
+                if (lane < ni) {
+                    const int i = real_as_int(P[cb + i0 + lane].w);
+                    R fx = acc[3 * lane], fy = acc[3 * lane + 1], fz = acc[3 * lane + 2];
+                    // harmonic bonds
+                    for (int k = bptr[i]; k < bptr[i + 1]; ++k) {
+                        const int j = blist[k];
+                        R dd[3];
+#pragma unroll
+                        for (int t = 0; t < 3; ++t) {
+                            const R xi = wrap_r(pos[3 * i + t], d.L, d.xmaxf);
+                            const R xj = wrap_r(pos[3 * j + t], d.L, d.xmaxf);
+                            dd[t] = min_image(xi, xj, L, hL);
+                        }
+                        const R r = r_sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+                        eb += (R)0.25 * Kb * (r - r0b) * (r - r0b);
+                        if (r > (R)0) {
+                            const R fm = -Kb * (r - r0b) / r;
+                            fx += fm * dd[0];
+                            fy += fm * dd[1];
+                            fz += fm * dd[2];
+                        }
+                    }
+                    F[3 * i] = fx;
+                    F[3 * i + 1] = fy;
+                    F[3 * i + 2] = fz;
+                }
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+    }
+    double e1 = (double)ec, e2 = (double)eb;
+    block_sum2(e1, e2);
     if (threadIdx.x == 0) {
-        dpart[2 * blockIdx.x] = ec;
-        dpart[2 * blockIdx.x + 1] = eb;
+        dpart[2 * blockIdx.x] = e1;
+        dpart[2 * blockIdx.x + 1] = e2;
     }
 }
 
