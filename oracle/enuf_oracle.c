@@ -312,6 +312,28 @@ static void grid_coord(double xw, double L, int ng, int* base, double* frac)
     *frac = u - bse;
 }
 
+/* The same coordinate for an FP32 path, decided in float arithmetic: n/L is
+ * split into two floats r_hi + r_lo, p = fl(x r_hi) and t = fl(x r_lo +
+ * (x r_hi - p)) (the exact product error via fmaf) represent u = p + t to
+ * about 1e-13 relative. floor(u) is floor(p), less one when p is an integer
+ * and t < 0; the fraction is (p - base) + t. */
+static void grid_coord_f32(double xw, double L, int ng, int* base, double* frac)
+{
+    const double ratio = (double)ng / L;
+    const float rhi = (float)ratio, rlo = (float)(ratio - (double)rhi);
+    const float x = (float)xw;
+    float p = x * rhi;
+    const float e = fmaf(x, rhi, -p);
+    const float t = fmaf(x, rlo, e);
+    if (p >= (float)ng) p -= (float)ng;
+    float b = floorf(p);
+    if (p == b && t < 0.0f) b -= 1.0f;
+    const float fr = (p - b) + t;
+    if (b < 0.0f) b += (float)ng;
+    *base = (int)b;
+    *frac = (double)fr;
+}
+
 static int imod(int a, int m)
 {
     int r = a % m;
@@ -349,7 +371,10 @@ int orc_recip_enuf(const orc_params* P, int n, const double* pos, const double* 
     for (int j = 0; j < n; ++j) {
         for (int t = 0; t < 3; ++t) {
             double fr;
-            grid_coord(x[3 * j + t], L, ng, &base[3 * j + t], &fr);
+            if (P->fp32_cut)
+                grid_coord_f32(x[3 * j + t], L, ng, &base[3 * j + t], &fr);
+            else
+                grid_coord(x[3 * j + t], L, ng, &base[3 * j + t], &fr);
             for (int a = 0; a < T; ++a)
                 wgt[((size_t)j * 3 + t) * T + a] = window(b, fr + (double)(p - 1 - a));
         }
