@@ -131,7 +131,7 @@ def run_ours(args, rank, world, dist):
     torch.cuda.set_device(dev)
     s = W.polyelectrolyte()
     dp = W.dpd_params(5)
-    P = dict(L=s.L, M=s.M, **s.params)
+    P = dict(L=s.L, M=s.M, tile=args.tile, **s.params)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     peaks, peak_kind = _peaks()
 
@@ -353,6 +353,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tile", type=int, default=0, help="spreading tile edge (0: the plan's choice)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 

@@ -148,6 +148,11 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
         if (n % T || T < P.p || (n / T) * (n / T) * (n / T) > kMaxTiles || T > 32)
             return fail(plan, ENUF_ERR_INVALID, "tile %d does not divide n = %d, is < p, or too small/large", T, n);
     } else {
+        // default: the smallest tile at least r_c wide (the real-space stencil is
+        // then 3^3 tiles) that divides n, is >= p and keeps the histogram in shared memory
+        const int tmin = std::max(P.p, (int)std::ceil(P.r_cut * n / P.L - 1e-9));
+        for (int c = tmin; c <= 32 && !T; ++c)
+            if (n % c == 0 && (n / c) * (n / c) * (n / c) <= kMaxTiles) T = c;
         for (int c = std::max(P.p, 8); c <= 32 && !T; ++c)
             if (n % c == 0 && (n / c) * (n / c) * (n / c) <= kMaxTiles) T = c;
         for (int c = P.p; c < 8 && !T; ++c)
@@ -212,6 +217,11 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
     g.pref = P.kappa * 2.0 / (P.L * P.L);
     g.c2a = 2.0 * P.alpha / std::sqrt(M_PI);
     g.xmaxf = largest_float_below(P.L);
+    g.c_self = -P.kappa * P.alpha / std::sqrt(M_PI);
+    g.c_neut = -P.kappa * M_PI / (2.0 * P.L * P.L * P.L * P.alpha * P.alpha);
+    g.c_recip = P.kappa / (2.0 * M_PI * P.L);
+    g.rhi = (float)g.ratio;
+    g.rlo = (float)(g.ratio - (double)g.rhi);
 
     Work w{};
     w.nblk_real = 8 * kSMs;

@@ -114,7 +114,7 @@ cudaError_t enqueue_enuf(const Geo& g, const FftShape& fs, const FftPlanDev& fp,
 
 template <typename R>
 cudaError_t enqueue_totals(const Geo& g, const Work& w, bool dpd, cudaStream_t s, LaunchLog* log) {
-    k_totals<<<1, 256, 0, s>>>(g, w.part, w.off_q, g.nbin, w.off_real, w.nblk_real, w.off_recip, w.nblk_conv,
+    k_totals<<<1, 1024, 0, s>>>(g, w.part, w.off_q, g.nbin, w.off_real, w.nblk_real, w.off_recip, w.nblk_conv,
                                w.off_dpd, dpd ? w.nblk_dpd : 0, w.off_kin, dpd ? w.nblk_kin : 0, w.Edev);
     log->kernels += 1;
     return cudaGetLastError();

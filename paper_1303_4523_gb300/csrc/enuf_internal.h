@@ -31,6 +31,10 @@ struct Geo {
     double pref;   // kappa * 2 / L^2 (Eq. 25 prefactor)
     double c2a;    // 2 alpha / sqrt(pi)
     float xmaxf;   // largest float below L: float x is inside [0, L) iff 0 <= x <= xmaxf
+    float rhi, rlo;  // n/L split into two floats (compensated float grid coordinate)
+    double c_self;   // -kappa alpha / sqrt(pi)           (E_self = c_self * sum q^2)
+    double c_neut;   // -kappa pi / (2 V alpha^2)         (E_neutral = c_neut * Q^2)
+    double c_recip;  // kappa / (2 pi L)                  (E_recip = c_recip * sum D |F|^2)
     int pad1;
 };
 

@@ -78,6 +78,30 @@ __device__ __forceinline__ void grid_coord(double xw, double ratio, int n, int& 
     frac = __dsub_rn(u, bb);
 }
 
+// FP32 path: the same floor decided in float on a compensated product. With
+// n/L = rhi + rlo (two floats), p = fl(x rhi) and t = fl(x rlo + (x rhi - p))
+// represent u = p + t to ~1e-13 relative; floor(u) = floor(p), less one when
+// p is an integer and t < 0.
+__device__ __forceinline__ void grid_coord_f(float x, float rhi, float rlo, int n, int& base, float& frac) {
+    float p = __fmul_rn(x, rhi);
+    const float e = __fmaf_rn(x, rhi, -p);
+    const float t = __fmaf_rn(x, rlo, e);
+    if (p >= (float)n) p = __fsub_rn(p, (float)n);
+    float b = floorf(p);
+    if (p == b && t < 0.0f) b = __fsub_rn(b, 1.0f);
+    frac = __fadd_rn(__fsub_rn(p, b), t);
+    if (b < 0.0f) b = __fadd_rn(b, (float)n);
+    base = (int)b;
+}
+
+// Grid base and fraction in the working precision.
+__device__ __forceinline__ void grid_coord_r(float xw, const Geo& g, int& base, float& frac) {
+    grid_coord_f(xw, g.rhi, g.rlo, g.n, base, frac);
+}
+__device__ __forceinline__ void grid_coord_r(double xw, const Geo& g, int& base, double& frac) {
+    grid_coord(xw, g.ratio, g.n, base, frac);
+}
+
 // Minimum-image difference and squared distance. For float the sequence is
 // fixed with explicit intrinsics (the same sequence decides the cutoff in the
 // oracle's float mode).
@@ -196,19 +220,19 @@ __global__ void __launch_bounds__(1024) k_bin_count(Geo g, int N, const R* __res
     const int nc = scount;
     for (int k = threadIdx.x; k < nc; k += blockDim.x) {
         const int i = slist[k];
-        double xw[3], fr[3];
+        R xw[3], fr[3];
         int bs[3];
 #pragma unroll
         for (int t = 0; t < 3; ++t) {
-            xw[t] = (double)wrap_r(pos[3 * i + t], g.L, g.xmaxf);
-            grid_coord(xw[t], g.ratio, g.n, bs[t], fr[t]);
+            xw[t] = wrap_r(pos[3 * i + t], g.L, g.xmaxf);
+            grid_coord_r(xw[t], g, bs[t], fr[t]);
         }
         const int tile = ((bs[2] / g.T) * g.ntd + bs[1] / g.T) * g.ntd + bs[0] / g.T;
         atomicAdd(&hist[tile], 1);
         const int o = i0 + k;
         typename V4<R>::T a, c;
-        a.x = (R)xw[0]; a.y = (R)xw[1]; a.z = (R)xw[2]; a.w = q[i];
-        c.x = (R)fr[0]; c.y = (R)fr[1]; c.z = (R)fr[2]; c.w = int_as_real(i, (R)0);
+        a.x = xw[0]; a.y = xw[1]; a.z = xw[2]; a.w = q[i];
+        c.x = fr[0]; c.y = fr[1]; c.z = fr[2]; c.w = int_as_real(i, (R)0);
         ctile[o] = tile;
         cpos[o] = a;
         cfrac[o] = c;
@@ -824,6 +848,80 @@ __device__ __forceinline__ void halo_dim(int t, int rs, int ntd, int& lo, int& c
     else { lo = t - rs; cnt = 2 * rs + 1; }
 }
 
+// Beads [c0, c1) of one tile against the nh-tile halo (total beads). STAGED:
+// candidates from the shared-memory copy; else from global memory through
+// the halo prefix.
+template <typename R, bool STAGED>
+__device__ __forceinline__ void real_beads(const Geo& g, int c0, int c1, int selfbase, int total, int nh,
+                                           const typename V4<R>::T* stg, const int* hoff, const int* gst,
+                                           const typename V4<R>::T* __restrict__ sq,
+                                           const typename V4<R>::T* __restrict__ sw, typename V4<R>::T* qu,
+                                           R* __restrict__ F, R& eacc, R& wacc) {
+    using V = typename V4<R>::T;
+    constexpr int NW = kRealThreads / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const R L = (R)g.L, hL = (R)(0.5 * g.L);
+    const R rc2 = (R)(g.rc * g.rc);
+    const R al = (R)g.alpha, c2a = (R)g.c2a, be = (R)g.beta, kap = (R)g.kappa;
+    const bool slater = g.beta > 0.0;
+    for (int s = c0 + warp; s < c1; s += NW) {
+        const V pi = sq[s];
+        const int self = selfbase + (s - c0);
+        R fx = 0, fy = 0, fz = 0;
+        int cnt = 0;
+        int hseg = 0;
+        const int steps = (total + 31) / 32 + 1;   // the extra step drains the queue
+        for (int it = 0; it < steps; ++it) {
+            const bool last = it == steps - 1;
+            if (!last) {
+                const int f = it * 32 + lane;
+                bool hit = false;
+                R dx = 0, dy = 0, dz = 0, qj = 0;
+                if (f < total && f != self) {
+                    V pj;
+                    if (STAGED) {
+                        pj = stg[f];
+                    } else {
+                        while (hseg + 1 < nh && hoff[hseg + 1] <= f) ++hseg;
+                        pj = sq[gst[hseg] + f - hoff[hseg]];
+                    }
+                    dx = min_image(pi.x, pj.x, L, hL);
+                    dy = min_image(pi.y, pj.y, L, hL);
+                    dz = min_image(pi.z, pj.z, L, hL);
+                    const R r2 = dist2(dx, dy, dz);
+                    hit = r2 < rc2 && r2 > (R)0;
+                    qj = pj.w;
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, hit);
+                if (hit) {
+                    V e;
+                    e.x = dx; e.y = dy; e.z = dz; e.w = qj;
+                    qu[cnt + __popc(m & ((1u << lane) - 1u))] = e;
+                }
+                cnt += __popc(m);
+            }
+            if (cnt >= 32 || (last && cnt > 0)) {
+                const int m = min(cnt, 32);
+                __syncwarp();
+                real_drain<R, V>(qu, m, lane, pi.w, kap, al, c2a, be, slater, fx, fy, fz, eacc, wacc);
+                __syncwarp();
+                if (lane < cnt - m) qu[lane] = qu[m + lane];
+                __syncwarp();
+                cnt -= m;
+            }
+        }
+        fx = warp_sum_r(fx);
+        fy = warp_sum_r(fy);
+        fz = warp_sum_r(fz);
+        if (lane == 0) {
+            const int i = real_as_int(sw[s].w);
+            F[3 * i] += fx;
+            F[3 * i + 1] += fy;
+            F[3 * i + 2] += fz;
+        }
+    }
+}
+
 // Real-space erfc + Slater-correction pairs (Eq. 31, corrected Eq. 32,
 // Eq. 27-28). One CTA per grid tile: the beads of the tiles within r_c (the
 // stencil) are staged in shared memory with coalesced loads; one warp per
@@ -906,63 +1004,13 @@ __global__ void __launch_bounds__(kRealThreads) k_real(Geo g, const int* __restr
             }
         }
         __syncthreads();
-        // the central tile's own beads
+        // the central tile's own beads, one warp each
         const int c0 = tstart[tile], c1 = tstart[tile + 1];
         const int hc = (((tz - zlo + g.ntd) % g.ntd) * yc + (ty - ylo + g.ntd) % g.ntd) * xc + (tx - xlo + g.ntd) % g.ntd;
-        for (int s = c0 + warp; s < c1; s += NW) {
-            const V pi = sq[s];
-            const int self = hoff[hc] + (s - c0);
-            R fx = 0, fy = 0, fz = 0;
-            int cnt = 0;
-            int hseg = 0;
-            for (int fb = 0; fb < total; fb += 32) {
-                const int f = fb + lane;
-                bool hit = false;
-                R dx = 0, dy = 0, dz = 0, qj = 0;
-                if (f < total && f != self) {
-                    V pj;
-                    if (staged) {
-                        pj = stg[f];
-                    } else {
-                        while (hoff[hseg + 1] <= f) ++hseg;
-                        pj = sq[gst[hseg] + f - hoff[hseg]];
-                    }
-                    dx = min_image(pi.x, pj.x, L, hL);
-                    dy = min_image(pi.y, pj.y, L, hL);
-                    dz = min_image(pi.z, pj.z, L, hL);
-                    const R r2 = dist2(dx, dy, dz);
-                    hit = r2 < rc2 && r2 > (R)0;
-                    qj = pj.w;
-                }
-                const unsigned m = __ballot_sync(0xffffffffu, hit);
-                if (hit) {
-                    V e;
-                    e.x = dx; e.y = dy; e.z = dz; e.w = qj;
-                    qu[cnt + __popc(m & ((1u << lane) - 1u))] = e;
-                }
-                cnt += __popc(m);
-                if (cnt >= 32) {
-                    __syncwarp();
-                    real_drain<R, V>(qu, 32, lane, pi.w, kap, al, c2a, be, slater, fx, fy, fz, eacc, wacc);
-                    __syncwarp();
-                    if (lane < cnt - 32) qu[lane] = qu[32 + lane];
-                    __syncwarp();
-                    cnt -= 32;
-                }
-            }
-            __syncwarp();
-            real_drain<R, V>(qu, cnt, lane, pi.w, kap, al, c2a, be, slater, fx, fy, fz, eacc, wacc);
-            __syncwarp();
-            fx = warp_sum_r(fx);
-            fy = warp_sum_r(fy);
-            fz = warp_sum_r(fz);
-            if (lane == 0) {
-                const int i = real_as_int(sw[s].w);
-                F[3 * i] += fx;
-                F[3 * i + 1] += fy;
-                F[3 * i + 2] += fz;
-            }
-        }
+        if (staged)
+            real_beads<R, true>(g, c0, c1, hoff[hc], total, nh, stg, hoff, gst, sq, sw, qu, F, eacc, wacc);
+        else
+            real_beads<R, false>(g, c0, c1, hoff[hc], total, nh, stg, hoff, gst, sq, sw, qu, F, eacc, wacc);
         __syncthreads();
     }
     double e = (double)eacc, w = (double)wacc;
@@ -1060,73 +1108,156 @@ constexpr int kDpdCand = 384;    // candidate map entries per warp
 constexpr int kDpdIMax = 32;     // beads of one cell handled together
 constexpr int kDpdMaxB = 4;      // cells per block edge
 
-struct DpdShared {
-    int* cand;    // [kDpdCand] candidate map of this warp
-    int2* queue;  // [64] accepted (bead slot, candidate) pairs
-};
-
 template <typename R, typename V>
-__device__ __forceinline__ void dpd_drain(int m, int lane, const int2* queue, int cb, const V* P, const V* Pv,
-                                          R* acc, const R* atab, int ntypes, R L, R hL, R gam, R sig, R rdt,
-                                          uint64_t seed, uint64_t step, R& ec) {
-    if (lane < m) {
-        const int2 e = queue[lane];
-        const V pi = P[cb + e.x], vi = Pv[cb + e.x];
-        const V pj = P[e.y], vj = Pv[e.y];
-        const R rx = min_image(pi.x, pj.x, L, hL);
-        const R ry = min_image(pi.y, pj.y, L, hL);
-        const R rz = min_image(pi.z, pj.z, L, hL);
-        const R r2 = dist2(rx, ry, rz);
-        const R ir = r_rsqrt(r2);
-        const R r = r2 * ir;
-        const R w = (R)1 - r;
-        const int i = real_as_int(pi.w), jj = real_as_int(pj.w);
-        const int ti = real_as_int(vi.w), tj = real_as_int(vj.w);
-        const R a = atab[ti * ntypes + tj];
-        const R vr = ((vi.x - vj.x) * rx + (vi.y - vj.y) * ry + (vi.z - vj.z) * rz) * ir;
-        const R th = dpd_theta<R>(seed, step, i, jj);
-        const R fm = (a * w - gam * w * w * vr + sig * w * th * rdt) * ir;
-        atomicAdd(&acc[3 * e.x], fm * rx);
-        atomicAdd(&acc[3 * e.x + 1], fm * ry);
-        atomicAdd(&acc[3 * e.x + 2], fm * rz);
-        ec += (R)0.25 * a * w * w;
-    }
+__device__ __forceinline__ void dpd_pair(const int2 e, int cb, const V* __restrict__ P, const V* __restrict__ Pv,
+                                         R* acc, const R* __restrict__ atab, int ntypes, R L, R hL, R gam, R sig,
+                                         R rdt, uint64_t seed, uint64_t step, R& ec) {
+    const V pi = P[cb + e.x], vi = Pv[cb + e.x];
+    const V pj = P[e.y], vj = Pv[e.y];
+    const R rx = min_image(pi.x, pj.x, L, hL);
+    const R ry = min_image(pi.y, pj.y, L, hL);
+    const R rz = min_image(pi.z, pj.z, L, hL);
+    const R r2 = dist2(rx, ry, rz);
+    const R ir = r_rsqrt(r2);
+    const R r = r2 * ir;
+    const R w = (R)1 - r;
+    const int i = real_as_int(pi.w), jj = real_as_int(pj.w);
+    const int ti = real_as_int(vi.w), tj = real_as_int(vj.w);
+    const R a = atab[ti * ntypes + tj];
+    const R vr = ((vi.x - vj.x) * rx + (vi.y - vj.y) * ry + (vi.z - vj.z) * rz) * ir;
+    const R th = dpd_theta<R>(seed, step, i, jj);
+    const R fm = (a * w - gam * w * w * vr + sig * w * th * rdt) * ir;
+    atomicAdd(&acc[3 * e.x], fm * rx);
+    atomicAdd(&acc[3 * e.x + 1], fm * ry);
+    atomicAdd(&acc[3 * e.x + 2], fm * rz);
+    ec += (R)0.25 * a * w * w;
 }
 
-// Sweep the candidate map (mc entries) for the ni beads of the current chunk.
-template <typename R, typename V>
-__device__ __forceinline__ void dpd_sweep(int mc, int ni, int i0, int lane, const int* cand, int2* queue, int& cnt,
-                                          int cb, const V* P, const V* Pv, R* acc, const R* atab, int ntypes, R L,
-                                          R hL, R gam, R sig, R rdt, uint64_t seed, uint64_t step, R& ec) {
-    for (int ii = 0; ii < ni; ++ii) {
-        const int me = cb + i0 + ii;
-        const V pi = P[me];
-        for (int jb = 0; jb < mc; jb += 32) {
-            const int jf = jb + lane;
-            bool hit = false;
-            int j = 0;
-            if (jf < mc) {
-                j = cand[jf];
-                if (j != me) {
-                    const V pj = P[j];
-                    const R rx = min_image(pi.x, pj.x, L, hL);
-                    const R ry = min_image(pi.y, pj.y, L, hL);
-                    const R rz = min_image(pi.z, pj.z, L, hL);
-                    const R r2 = dist2(rx, ry, rz);
-                    hit = r2 < (R)1 && r2 > (R)0;
+// All central cells of one block, one warp per cell. STAGED: P/Pv are the
+// shared-memory copies and cell starts are hoff; else global arrays and gst.
+template <typename R, bool STAGED>
+__device__ __forceinline__ void dpd_cells(const DpdDev& d, int H, int B3, const int* chalo, const int* hoff,
+                                          const int* gst, const typename V4<R>::T* __restrict__ P,
+                                          const typename V4<R>::T* __restrict__ Pv, R* acc, int2* queue, int* cand,
+                                          const R* __restrict__ atab, const R* __restrict__ pos,
+                                          const int* __restrict__ bptr, const int* __restrict__ blist,
+                                          uint64_t step, R* __restrict__ F, R& ec, R& eb) {
+    using V = typename V4<R>::T;
+    constexpr int NW = kDpdThreads / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const R L = (R)d.L, hL = (R)(0.5 * d.L);
+    const R gam = (R)d.gamma, sig = (R)d.sigma, rdt = (R)d.rdt;
+    const R Kb = (R)d.K_bond, r0b = (R)d.r0_bond;
+    constexpr int nseg = STAGED ? 9 : 27;
+    for (int cc = warp; cc < B3; cc += NW) {
+        const int h = chalo[cc];
+        if (h < 0) continue;
+        const int cb = STAGED ? hoff[h] : gst[h];
+        const int nall = hoff[h + 1] - hoff[h];
+        for (int i0 = 0; i0 < nall; i0 += kDpdIMax) {
+            const int ni = min(kDpdIMax, nall - i0);
+            for (int k = lane; k < 3 * kDpdIMax; k += 32) acc[k] = (R)0;
+            int cnt = 0;
+            int seg = 0, soff = 0;
+            bool more = true;
+            while (more) {
+                // fill the candidate map: rows of 3 contiguous staged cells, or single cells
+                int mc = 0;
+                while (seg < nseg && mc < kDpdCand) {
+                    int sbase, slen;
+                    if (STAGED) {
+                        const int hr = h + ((seg / 3 - 1) * H + (seg % 3 - 1)) * H - 1;
+                        sbase = hoff[hr];
+                        slen = hoff[hr + 3] - sbase;
+                    } else {
+                        const int hc = h + ((seg / 9 - 1) * H + ((seg / 3) % 3 - 1)) * H + (seg % 3 - 1);
+                        sbase = gst[hc];
+                        slen = hoff[hc + 1] - hoff[hc];
+                    }
+                    const int take = min(slen - soff, kDpdCand - mc);
+                    for (int t = lane; t < take; t += 32) cand[mc + t] = sbase + soff + t;
+                    mc += take;
+                    soff += take;
+                    if (soff == slen) {
+                        ++seg;
+                        soff = 0;
+                    }
+                }
+                __syncwarp();
+                more = seg < nseg;
+                // sweep: every bead of the chunk against the map; one extra step drains the queue
+                const int nj = (mc + 31) >> 5;
+                const int steps = ni * nj + (more ? 0 : 1);
+                int ii = 0, jb = 0;
+                for (int it = 0; it < steps; ++it) {
+                    const bool last = it == ni * nj;
+                    if (!last) {
+                        const int me = cb + i0 + ii;
+                        const int jf = jb + lane;
+                        bool hit = false;
+                        int j = 0;
+                        if (jf < mc) {
+                            j = cand[jf];
+                            if (j != me) {
+                                const V pi = P[me];
+                                const V pj = P[j];
+                                const R rx = min_image(pi.x, pj.x, L, hL);
+                                const R ry = min_image(pi.y, pj.y, L, hL);
+                                const R rz = min_image(pi.z, pj.z, L, hL);
+                                const R r2 = dist2(rx, ry, rz);
+                                hit = r2 < (R)1 && r2 > (R)0;
+                            }
+                        }
+                        const unsigned m = __ballot_sync(0xffffffffu, hit);
+                        if (hit) queue[cnt + __popc(m & ((1u << lane) - 1u))] = make_int2(i0 + ii, j);
+                        cnt += __popc(m);
+                        jb += 32;
+                        if (jb >= mc) {
+                            jb = 0;
+                            ++ii;
+                        }
+                    }
+                    if (cnt >= 32 || (last && cnt > 0)) {
+                        const int m = min(cnt, 32);
+                        __syncwarp();
+                        if (lane < m)
+                            dpd_pair<R, V>(queue[lane], cb, P, Pv, acc, atab, d.ntypes, L, hL, gam, sig, rdt, d.seed,
+                                           step, ec);
+                        __syncwarp();
+                        if (lane < cnt - m) queue[lane] = queue[m + lane];
+                        __syncwarp();
+                        cnt -= m;
+                    }
                 }
             }
-            const unsigned m = __ballot_sync(0xffffffffu, hit);
-            if (hit) queue[cnt + __popc(m & ((1u << lane) - 1u))] = make_int2(i0 + ii, j);
-            cnt += __popc(m);
-            if (cnt >= 32) {
-                __syncwarp();
-                dpd_drain<R, V>(32, lane, queue, cb, P, Pv, acc, atab, ntypes, L, hL, gam, sig, rdt, seed, step, ec);
-                __syncwarp();
-                if (lane < cnt - 32) queue[lane] = queue[32 + lane];
-                __syncwarp();
-                cnt -= 32;
+            __syncwarp();
+            if (lane < ni) {
+                const int i = real_as_int(P[cb + i0 + lane].w);
+                R fx = acc[3 * lane], fy = acc[3 * lane + 1], fz = acc[3 * lane + 2];
+                // harmonic bonds
+                for (int k = bptr[i]; k < bptr[i + 1]; ++k) {
+                    const int j = blist[k];
+                    R dd[3];
+#pragma unroll
+                    for (int t = 0; t < 3; ++t) {
+                        const R xi = wrap_r(pos[3 * i + t], d.L, d.xmaxf);
+                        const R xj = wrap_r(pos[3 * j + t], d.L, d.xmaxf);
+                        dd[t] = min_image(xi, xj, L, hL);
+                    }
+                    const R r = r_sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+                    eb += (R)0.25 * Kb * (r - r0b) * (r - r0b);
+                    if (r > (R)0) {
+                        const R fm = -Kb * (r - r0b) / r;
+                        fx += fm * dd[0];
+                        fy += fm * dd[1];
+                        fz += fm * dd[2];
+                    }
+                }
+                F[3 * i] = fx;
+                F[3 * i + 1] = fy;
+                F[3 * i + 2] = fz;
             }
+            __syncwarp();
         }
     }
 }
@@ -1150,9 +1281,6 @@ __global__ void __launch_bounds__(kDpdThreads) k_dpd(DpdDev d, int B, const type
     constexpr int HMAX = (kDpdMaxB + 2) * (kDpdMaxB + 2) * (kDpdMaxB + 2);
     __shared__ int hoff[HMAX + 1], gst[HMAX];
     __shared__ int chalo[kDpdMaxB * kDpdMaxB * kDpdMaxB];
-    const R L = (R)d.L, hL = (R)(0.5 * d.L);
-    const R gam = (R)d.gamma, sig = (R)d.sigma, rdt = (R)d.rdt;
-    const R Kb = (R)d.K_bond, r0b = (R)d.r0_bond;
     const uint64_t step = *stepp;
     const int ncd = d.ncd, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     R* acc = accs + warp * kDpdIMax * 3;
@@ -1219,80 +1347,12 @@ __global__ void __launch_bounds__(kDpdThreads) k_dpd(DpdDev d, int B, const type
             }
         }
         __syncthreads();
-        const V* P = staged ? spos : sp;
-        const V* Pv = staged ? svel : sv;
-        for (int cc = warp; cc < B3; cc += NW) {
-            const int h = chalo[cc];
-            if (h < 0) continue;
-            const int cb = staged ? hoff[h] : gst[h];
-            const int nall = hoff[h + 1] - hoff[h];
-            for (int i0 = 0; i0 < nall; i0 += kDpdIMax) {
-                const int ni = min(kDpdIMax, nall - i0);
-                for (int k = lane; k < 3 * kDpdIMax; k += 32) acc[k] = (R)0;
-                int cnt = 0, mc = 0;
-                __syncwarp();
-                // candidate segments: 9 rows of 3 contiguous cells when staged, else 27 cells
-                const int nseg = staged ? 9 : 27;
-                for (int seg = 0; seg < nseg; ++seg) {
-                    int sbase, slen;
-                    if (staged) {
-                        const int hr = h + ((seg / 3 - 1) * H + (seg % 3 - 1)) * H - 1;
-                        sbase = hoff[hr];
-                        slen = hoff[hr + 3] - sbase;
-                    } else {
-                        const int hc = h + ((seg / 9 - 1) * H + ((seg / 3) % 3 - 1)) * H + (seg % 3 - 1);
-                        sbase = gst[hc];
-                        slen = hoff[hc + 1] - hoff[hc];
-                    }
-                    while (slen > 0) {
-                        if (mc == kDpdCand) {
-                            dpd_sweep<R, V>(mc, ni, i0, lane, cand, queue, cnt, cb, P, Pv, acc, atab, d.ntypes, L,
-                                            hL, gam, sig, rdt, d.seed, step, ec);
-                            mc = 0;
-                        }
-                        const int take = min(slen, kDpdCand - mc);
-                        for (int t = lane; t < take; t += 32) cand[mc + t] = sbase + t;
-                        __syncwarp();
-                        mc += take;
-                        sbase += take;
-                        slen -= take;
-                    }
-                }
-                dpd_sweep<R, V>(mc, ni, i0, lane, cand, queue, cnt, cb, P, Pv, acc, atab, d.ntypes, L, hL, gam, sig,
-                                rdt, d.seed, step, ec);
-                __syncwarp();
-                dpd_drain<R, V>(cnt, lane, queue, cb, P, Pv, acc, atab, d.ntypes, L, hL, gam, sig, rdt, d.seed,
-                                step, ec);
-                __syncwarp();
-                if (lane < ni) {
-                    const int i = real_as_int(P[cb + i0 + lane].w);
-                    R fx = acc[3 * lane], fy = acc[3 * lane + 1], fz = acc[3 * lane + 2];
-                    // harmonic bonds
-                    for (int k = bptr[i]; k < bptr[i + 1]; ++k) {
-                        const int j = blist[k];
-                        R dd[3];
-#pragma unroll
-                        for (int t = 0; t < 3; ++t) {
-                            const R xi = wrap_r(pos[3 * i + t], d.L, d.xmaxf);
-                            const R xj = wrap_r(pos[3 * j + t], d.L, d.xmaxf);
-                            dd[t] = min_image(xi, xj, L, hL);
-                        }
-                        const R r = r_sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
-                        eb += (R)0.25 * Kb * (r - r0b) * (r - r0b);
-                        if (r > (R)0) {
-                            const R fm = -Kb * (r - r0b) / r;
-                            fx += fm * dd[0];
-                            fy += fm * dd[1];
-                            fz += fm * dd[2];
-                        }
-                    }
-                    F[3 * i] = fx;
-                    F[3 * i + 1] = fy;
-                    F[3 * i + 2] = fz;
-                }
-                __syncwarp();
-            }
-        }
+        if (staged)
+            dpd_cells<R, true>(d, H, B3, chalo, hoff, gst, spos, svel, acc, queue, cand, atab, pos, bptr, blist,
+                               step, F, ec, eb);
+        else
+            dpd_cells<R, false>(d, H, B3, chalo, hoff, gst, sp, sv, acc, queue, cand, atab, pos, bptr, blist, step,
+                                F, ec, eb);
         __syncthreads();
     }
     double e1 = (double)ec, e2 = (double)eb;
@@ -1332,42 +1392,42 @@ __global__ void __launch_bounds__(256) k_vv_post(int N, R dt, R* __restrict__ ve
     if (threadIdx.x == 0) kpart[blockIdx.x] = ke;
 }
 
-// Final FP64 totals (Kahan over the per-block partials), one CTA of 256 threads.
+// Final FP64 totals (Kahan over the per-block partials), one CTA of 1024
+// threads: 32 warps share 9 quantities (Sum q, Sum q^2, E_real, W_real,
+// E_recip, W_recip, E_c, E_bond, E_kin).
 // Edev: [0] E_real [1] E_recip [2] E_self+E_neutral [3] E_elec [4] E_conservative
 //       [5] E_bond [6] E_kinetic [7] virial_elec
-static __global__ void __launch_bounds__(256) k_totals(Geo g, const double* __restrict__ part, int off_q, int nq,
-                                               int off_real, int nreal, int off_recip, int nrecip,
-                                               int off_dpd, int ndpd, int off_kin, int nkin,
-                                               double* __restrict__ Edev) {
-    __shared__ double vals[16];
+static __global__ void __launch_bounds__(1024) k_totals(Geo g, const double* __restrict__ part, int off_q, int nq,
+                                                        int off_real, int nreal, int off_recip, int nrecip,
+                                                        int off_dpd, int ndpd, int off_kin, int nkin,
+                                                        double* __restrict__ Edev) {
+    __shared__ double wv[32];
+    __shared__ double vals[9];
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    // warp w reduces quantity w: 0 sum q, 1 sum q^2, 2 E_real, 3 W_real, 4 E_k, 5 W_k, 6 E_c, 7 E_b
-    if (w < 8) {
-        int off, cnt, stride = 2, sub = w & 1;
-        if (w < 2) { off = off_q; cnt = nq; }
-        else if (w < 4) { off = off_real; cnt = nreal; }
-        else if (w < 6) { off = off_recip; cnt = nrecip; }
-        else { off = off_dpd; cnt = ndpd; }
-        Kahan k;
-        for (int i = l; i < cnt; i += 32) k.add(part[off + stride * i + sub]);
-        double v = warp_sum(k.s);
-        if (l == 0) vals[w] = v;
-    }
-    if (w == 0) {
-        Kahan k;
-        for (int i = l; i < nkin; i += 32) k.add(part[off_kin + i]);
-        const double v = warp_sum(k.s);
-        if (l == 0) vals[8] = v;
+    const int qd = w % 9, sub = w / 9, nsub = (32 - qd + 8) / 9;   // warps on this quantity
+    int off, cnt, stride;
+    if (qd < 2) { off = off_q + qd; cnt = nq; stride = 2; }
+    else if (qd < 4) { off = off_real + (qd - 2); cnt = nreal; stride = 2; }
+    else if (qd < 6) { off = off_recip + (qd - 4); cnt = nrecip; stride = 2; }
+    else if (qd < 8) { off = off_dpd + (qd - 6); cnt = ndpd; stride = 2; }
+    else { off = off_kin; cnt = nkin; stride = 1; }
+    Kahan k;
+    for (int i = sub * 32 + l; i < cnt; i += nsub * 32) k.add(part[off + stride * i]);
+    const double v = warp_sum(k.s);
+    if (l == 0) wv[w] = v;
+    __syncthreads();
+    if (threadIdx.x < 9) {
+        Kahan kk;
+        for (int ww = threadIdx.x; ww < 32; ww += 9) kk.add(wv[ww]);
+        vals[threadIdx.x] = kk.s;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        const double pi = 3.14159265358979323846;
-        const double V = g.L * g.L * g.L;
+        // constants formed on the host: no FP64 division or square root here
         const double Q = vals[0], Q2 = vals[1];
-        const double e_self = -g.kappa * g.alpha / sqrt(pi) * Q2;
-        const double e_neut = -g.kappa * pi * Q * Q / (2.0 * V * g.alpha * g.alpha);
-        const double pk = g.kappa / (2.0 * pi * g.L);
-        const double e_real = vals[2], e_recip = pk * vals[4];
+        const double e_self = g.c_self * Q2;
+        const double e_neut = g.c_neut * Q * Q;
+        const double e_real = vals[2], e_recip = g.c_recip * vals[4];
         Edev[0] = e_real;
         Edev[1] = e_recip;
         Edev[2] = e_self + e_neut;
@@ -1375,7 +1435,7 @@ static __global__ void __launch_bounds__(256) k_totals(Geo g, const double* __re
         Edev[4] = vals[6];
         Edev[5] = vals[7];
         Edev[6] = vals[8];
-        Edev[7] = vals[3] + pk * vals[5] + 3.0 * e_neut;
+        Edev[7] = vals[3] + g.c_recip * vals[5] + 3.0 * e_neut;
         for (int i = 8; i < 16; ++i) Edev[i] = 0.0;
     }
 }
