@@ -142,18 +142,22 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
     if (!fft_radices(n, fp)) return fail(plan, ENUF_ERR_UNSUPPORTED, "grid n = %d is not 2^a 3^b 5^c", n);
     if (2 * P.p > n) return fail(plan, ENUF_ERR_INVALID, "window 2p = %d wider than the grid", 2 * P.p);
     // tile edge: divides n, >= p, histogram fits in shared memory
+    // the spreading kernel holds a T^3 tile of the grid in shared memory: T <= 24
+    // (110 KB in FP64); the binning kernels hold the tile histogram (<= 32768 tiles)
+    constexpr int kMaxTile = 24;
     int T = 0;
     if (P.tile > 0) {
         T = P.tile;
-        if (n % T || T < P.p || (n / T) * (n / T) * (n / T) > kMaxTiles || T > 32)
-            return fail(plan, ENUF_ERR_INVALID, "tile %d does not divide n = %d, is < p, or too small/large", T, n);
+        if (n % T || T < P.p || (n / T) * (n / T) * (n / T) > kMaxTiles || T > kMaxTile)
+            return fail(plan, ENUF_ERR_INVALID, "tile %d does not divide n = %d, is < p, or outside [p, %d]", T, n,
+                        kMaxTile);
     } else {
         // default: the smallest tile at least r_c wide (the real-space stencil is
         // then 3^3 tiles) that divides n, is >= p and keeps the histogram in shared memory
         const int tmin = std::max(P.p, (int)std::ceil(P.r_cut * n / P.L - 1e-9));
-        for (int c = tmin; c <= 32 && !T; ++c)
+        for (int c = tmin; c <= kMaxTile && !T; ++c)
             if (n % c == 0 && (n / c) * (n / c) * (n / c) <= kMaxTiles) T = c;
-        for (int c = std::max(P.p, 8); c <= 32 && !T; ++c)
+        for (int c = std::max(P.p, 8); c <= kMaxTile && !T; ++c)
             if (n % c == 0 && (n / c) * (n / c) * (n / c) <= kMaxTiles) T = c;
         for (int c = P.p; c < 8 && !T; ++c)
             if (n % c == 0 && (n / c) * (n / c) * (n / c) <= kMaxTiles) T = c;

@@ -1095,24 +1095,26 @@ __device__ __forceinline__ R dpd_theta(uint64_t seed, uint64_t step, int i, int 
     return (R)1.7320508075688772935 * ((R)2 * u - (R)1);
 }
 
-// DPD pair forces (Eq. 2-7, R_c = 1) + bonds (Sec. 2); F[i] = F^C + F^D +
-// F^R/sqrt(dt) + F^S (overwrites F). One CTA per B^3 block of cells: the beads
-// of the (B+2)^3 halo cells are staged in shared memory with coalesced loads.
-// One warp per central cell: the cell's 27-cell neighbourhood is laid out as
-// one candidate map, lanes sweep it for each bead of the cell, accepted pairs
-// go to a per-warp queue, and the pair arithmetic (Philox draw, weights,
-// dissipation) runs on full warps; forces accumulate per bead in shared memory.
+// DPD pair forces (Eq. 2-7, R_c = 1) + bonds (Sec. 2), added into F (which
+// the caller zeroes): F[i] += F^C + F^D + F^R/sqrt(dt) + F^S. One CTA per B^3
+// block of cells; the beads of the (B+2)^3 halo cells are staged in shared
+// memory with coalesced loads. One warp per central cell sweeps the cell's
+// forward half shell (the cell itself with j > i, and the 13 neighbouring
+// cells lexicographically after it), so every pair is evaluated once
+// (Newton's third law; theta_ij is symmetric). Accepted pairs go to a
+// per-warp queue and the pair arithmetic (Philox draw, weights, dissipation)
+// runs on full warps; +f and -f accumulate in a shared-memory force array
+// over the staged beads, which is added to F once per block.
 constexpr int kDpdThreads = 256;
 constexpr int kDpdCap = 1024;    // staged beads
 constexpr int kDpdCand = 384;    // candidate map entries per warp
-constexpr int kDpdIMax = 32;     // beads of one cell handled together
 constexpr int kDpdMaxB = 4;      // cells per block edge
 
-template <typename R, typename V>
-__device__ __forceinline__ void dpd_pair(const int2 e, int cb, const V* __restrict__ P, const V* __restrict__ Pv,
-                                         R* acc, const R* __restrict__ atab, int ntypes, R L, R hL, R gam, R sig,
-                                         R rdt, uint64_t seed, uint64_t step, R& ec) {
-    const V pi = P[cb + e.x], vi = Pv[cb + e.x];
+template <typename R, typename V, bool STAGED>
+__device__ __forceinline__ void dpd_pair(const int2 e, const V* __restrict__ P, const V* __restrict__ Pv,
+                                         R* fh, R* __restrict__ F, const R* __restrict__ atab, int ntypes, R L,
+                                         R hL, R gam, R sig, R rdt, uint64_t seed, uint64_t step, R& ec) {
+    const V pi = P[e.x], vi = Pv[e.x];
     const V pj = P[e.y], vj = Pv[e.y];
     const R rx = min_image(pi.x, pj.x, L, hL);
     const R ry = min_image(pi.y, pj.y, L, hL);
@@ -1121,16 +1123,29 @@ __device__ __forceinline__ void dpd_pair(const int2 e, int cb, const V* __restri
     const R ir = r_rsqrt(r2);
     const R r = r2 * ir;
     const R w = (R)1 - r;
-    const int i = real_as_int(pi.w), jj = real_as_int(pj.w);
+    const int i = real_as_int(pi.w), j = real_as_int(pj.w);
     const int ti = real_as_int(vi.w), tj = real_as_int(vj.w);
     const R a = atab[ti * ntypes + tj];
     const R vr = ((vi.x - vj.x) * rx + (vi.y - vj.y) * ry + (vi.z - vj.z) * rz) * ir;
-    const R th = dpd_theta<R>(seed, step, i, jj);
+    const R th = dpd_theta<R>(seed, step, i, j);
     const R fm = (a * w - gam * w * w * vr + sig * w * th * rdt) * ir;
-    atomicAdd(&acc[3 * e.x], fm * rx);
-    atomicAdd(&acc[3 * e.x + 1], fm * ry);
-    atomicAdd(&acc[3 * e.x + 2], fm * rz);
-    ec += (R)0.25 * a * w * w;
+    const R fx = fm * rx, fy = fm * ry, fz = fm * rz;
+    if (STAGED) {
+        atomicAdd(&fh[3 * e.x], fx);
+        atomicAdd(&fh[3 * e.x + 1], fy);
+        atomicAdd(&fh[3 * e.x + 2], fz);
+        atomicAdd(&fh[3 * e.y], -fx);
+        atomicAdd(&fh[3 * e.y + 1], -fy);
+        atomicAdd(&fh[3 * e.y + 2], -fz);
+    } else {
+        atomicAdd(&F[3 * i], fx);
+        atomicAdd(&F[3 * i + 1], fy);
+        atomicAdd(&F[3 * i + 2], fz);
+        atomicAdd(&F[3 * j], -fx);
+        atomicAdd(&F[3 * j + 1], -fy);
+        atomicAdd(&F[3 * j + 2], -fz);
+    }
+    ec += (R)0.5 * a * w * w;
 }
 
 // All central cells of one block, one warp per cell. STAGED: P/Pv are the
@@ -1138,7 +1153,7 @@ __device__ __forceinline__ void dpd_pair(const int2 e, int cb, const V* __restri
 template <typename R, bool STAGED>
 __device__ __forceinline__ void dpd_cells(const DpdDev& d, int H, int B3, const int* chalo, const int* hoff,
                                           const int* gst, const typename V4<R>::T* __restrict__ P,
-                                          const typename V4<R>::T* __restrict__ Pv, R* acc, int2* queue, int* cand,
+                                          const typename V4<R>::T* __restrict__ Pv, R* fh, int2* queue, int* cand,
                                           const R* __restrict__ atab, const R* __restrict__ pos,
                                           const int* __restrict__ bptr, const int* __restrict__ blist,
                                           uint64_t step, R* __restrict__ F, R& ec, R& eb) {
@@ -1148,95 +1163,106 @@ __device__ __forceinline__ void dpd_cells(const DpdDev& d, int H, int B3, const 
     const R L = (R)d.L, hL = (R)(0.5 * d.L);
     const R gam = (R)d.gamma, sig = (R)d.sigma, rdt = (R)d.rdt;
     const R Kb = (R)d.K_bond, r0b = (R)d.r0_bond;
-    constexpr int nseg = STAGED ? 9 : 27;
+    // forward half shell: the cell itself, (0,0,+1), the row (0,+1,*), the rows (+1,*,*).
+    // Staged cells of a row are contiguous, so it takes 6 segments; else 14 single cells.
+    constexpr int nseg = STAGED ? 6 : 14;
     for (int cc = warp; cc < B3; cc += NW) {
         const int h = chalo[cc];
         if (h < 0) continue;
         const int cb = STAGED ? hoff[h] : gst[h];
-        const int nall = hoff[h + 1] - hoff[h];
-        for (int i0 = 0; i0 < nall; i0 += kDpdIMax) {
-            const int ni = min(kDpdIMax, nall - i0);
-            for (int k = lane; k < 3 * kDpdIMax; k += 32) acc[k] = (R)0;
-            int cnt = 0;
-            int seg = 0, soff = 0;
-            bool more = true;
-            while (more) {
-                // fill the candidate map: rows of 3 contiguous staged cells, or single cells
-                int mc = 0;
-                while (seg < nseg && mc < kDpdCand) {
-                    int sbase, slen;
-                    if (STAGED) {
-                        const int hr = h + ((seg / 3 - 1) * H + (seg % 3 - 1)) * H - 1;
+        const int nself = hoff[h + 1] - hoff[h];
+        if (nself == 0) continue;
+        int cnt = 0;
+        int seg = 0, soff = 0;
+        bool more = true;
+        while (more) {
+            int mc = 0;
+            while (seg < nseg && mc < kDpdCand) {
+                int sbase, slen;
+                if (STAGED) {
+                    if (seg == 0) { sbase = cb; slen = nself; }
+                    else if (seg == 1) { sbase = hoff[h + 1]; slen = hoff[h + 2] - sbase; }
+                    else {
+                        const int hr = seg == 2 ? h + H - 1 : h + H * H + (seg - 4) * H - 1;
                         sbase = hoff[hr];
                         slen = hoff[hr + 3] - sbase;
-                    } else {
-                        const int hc = h + ((seg / 9 - 1) * H + ((seg / 3) % 3 - 1)) * H + (seg % 3 - 1);
-                        sbase = gst[hc];
-                        slen = hoff[hc + 1] - hoff[hc];
                     }
-                    const int take = min(slen - soff, kDpdCand - mc);
-                    for (int t = lane; t < take; t += 32) cand[mc + t] = sbase + soff + t;
-                    mc += take;
-                    soff += take;
-                    if (soff == slen) {
-                        ++seg;
-                        soff = 0;
-                    }
+                } else {
+                    int hc;
+                    if (seg == 0) hc = h;
+                    else if (seg == 1) hc = h + 1;
+                    else if (seg < 5) hc = h + H + (seg - 3);
+                    else hc = h + H * H + ((seg - 5) / 3 - 1) * H + ((seg - 5) % 3 - 1);
+                    sbase = gst[hc];
+                    slen = hoff[hc + 1] - hoff[hc];
                 }
-                __syncwarp();
-                more = seg < nseg;
-                // sweep: every bead of the chunk against the map; one extra step drains the queue
-                const int nj = (mc + 31) >> 5;
-                const int steps = ni * nj + (more ? 0 : 1);
-                int ii = 0, jb = 0;
-                for (int it = 0; it < steps; ++it) {
-                    const bool last = it == ni * nj;
-                    if (!last) {
-                        const int me = cb + i0 + ii;
-                        const int jf = jb + lane;
-                        bool hit = false;
-                        int j = 0;
-                        if (jf < mc) {
-                            j = cand[jf];
-                            if (j != me) {
-                                const V pi = P[me];
-                                const V pj = P[j];
-                                const R rx = min_image(pi.x, pj.x, L, hL);
-                                const R ry = min_image(pi.y, pj.y, L, hL);
-                                const R rz = min_image(pi.z, pj.z, L, hL);
-                                const R r2 = dist2(rx, ry, rz);
-                                hit = r2 < (R)1 && r2 > (R)0;
-                            }
-                        }
-                        const unsigned m = __ballot_sync(0xffffffffu, hit);
-                        if (hit) queue[cnt + __popc(m & ((1u << lane) - 1u))] = make_int2(i0 + ii, j);
-                        cnt += __popc(m);
-                        jb += 32;
-                        if (jb >= mc) {
-                            jb = 0;
-                            ++ii;
-                        }
-                    }
-                    if (cnt >= 32 || (last && cnt > 0)) {
-                        const int m = min(cnt, 32);
-                        __syncwarp();
-                        if (lane < m)
-                            dpd_pair<R, V>(queue[lane], cb, P, Pv, acc, atab, d.ntypes, L, hL, gam, sig, rdt, d.seed,
-                                           step, ec);
-                        __syncwarp();
-                        if (lane < cnt - m) queue[lane] = queue[m + lane];
-                        __syncwarp();
-                        cnt -= m;
-                    }
+                const int take = min(slen - soff, kDpdCand - mc);
+                for (int t = lane; t < take; t += 32) cand[mc + t] = sbase + soff + t;
+                mc += take;
+                soff += take;
+                if (soff == slen) {
+                    ++seg;
+                    soff = 0;
                 }
             }
             __syncwarp();
-            if (lane < ni) {
-                const int i = real_as_int(P[cb + i0 + lane].w);
-                R fx = acc[3 * lane], fy = acc[3 * lane + 1], fz = acc[3 * lane + 2];
-                // harmonic bonds
-                for (int k = bptr[i]; k < bptr[i + 1]; ++k) {
-                    const int j = blist[k];
+            more = seg < nseg;
+            // sweep: every bead of the cell against the map; one extra step drains the queue
+            const int nj = (mc + 31) >> 5;
+            const int steps = nself * nj + (more ? 0 : 1);
+            int ii = 0, jb = 0;
+            for (int it = 0; it < steps; ++it) {
+                const bool last = it == nself * nj;
+                if (!last) {
+                    const int me = cb + ii;
+                    const int jf = jb + lane;
+                    bool hit = false;
+                    int j = 0;
+                    if (jf < mc) {
+                        j = cand[jf];
+                        // within the cell itself only j > i (each pair once)
+                        const bool ok = (j >= cb && j < cb + nself) ? j > me : true;
+                        if (ok) {
+                            const V pi = P[me];
+                            const V pj = P[j];
+                            const R rx = min_image(pi.x, pj.x, L, hL);
+                            const R ry = min_image(pi.y, pj.y, L, hL);
+                            const R rz = min_image(pi.z, pj.z, L, hL);
+                            const R r2 = dist2(rx, ry, rz);
+                            hit = r2 < (R)1 && r2 > (R)0;
+                        }
+                    }
+                    const unsigned m = __ballot_sync(0xffffffffu, hit);
+                    if (hit) queue[cnt + __popc(m & ((1u << lane) - 1u))] = make_int2(me, j);
+                    cnt += __popc(m);
+                    jb += 32;
+                    if (jb >= mc) {
+                        jb = 0;
+                        ++ii;
+                    }
+                }
+                if (cnt >= 32 || (last && cnt > 0)) {
+                    const int m = min(cnt, 32);
+                    __syncwarp();
+                    if (lane < m)
+                        dpd_pair<R, V, STAGED>(queue[lane], P, Pv, fh, F, atab, d.ntypes, L, hL, gam, sig, rdt,
+                                               d.seed, step, ec);
+                    __syncwarp();
+                    if (lane < cnt - m) queue[lane] = queue[m + lane];
+                    __syncwarp();
+                    cnt -= m;
+                }
+            }
+        }
+        // harmonic bonds of the cell's beads (each bond is seen from both ends)
+        for (int k0 = 0; k0 < nself; k0 += 32) {
+            const int k = k0 + lane;
+            if (k < nself) {
+                const int slot = cb + k;
+                const int i = real_as_int(P[slot].w);
+                R fx = 0, fy = 0, fz = 0;
+                for (int kb = bptr[i]; kb < bptr[i + 1]; ++kb) {
+                    const int j = blist[kb];
                     R dd[3];
 #pragma unroll
                     for (int t = 0; t < 3; ++t) {
@@ -1253,12 +1279,20 @@ __device__ __forceinline__ void dpd_cells(const DpdDev& d, int H, int B3, const 
                         fz += fm * dd[2];
                     }
                 }
-                F[3 * i] = fx;
-                F[3 * i + 1] = fy;
-                F[3 * i + 2] = fz;
+                if (fx != (R)0 || fy != (R)0 || fz != (R)0) {
+                    if (STAGED) {
+                        atomicAdd(&fh[3 * slot], fx);
+                        atomicAdd(&fh[3 * slot + 1], fy);
+                        atomicAdd(&fh[3 * slot + 2], fz);
+                    } else {
+                        atomicAdd(&F[3 * i], fx);
+                        atomicAdd(&F[3 * i + 1], fy);
+                        atomicAdd(&F[3 * i + 2], fz);
+                    }
+                }
             }
-            __syncwarp();
         }
+        __syncwarp();
     }
 }
 
@@ -1271,19 +1305,17 @@ __global__ void __launch_bounds__(kDpdThreads) k_dpd(DpdDev d, int B, const type
                                                      const uint64_t* __restrict__ stepp, R* __restrict__ F,
                                                      double* __restrict__ dpart) {
     using V = typename V4<R>::T;
-    constexpr int NW = kDpdThreads / 32;
     extern __shared__ __align__(16) unsigned char smraw[];
     V* spos = reinterpret_cast<V*>(smraw);                                  // [kDpdCap]
     V* svel = spos + kDpdCap;                                               // [kDpdCap]
-    R* accs = reinterpret_cast<R*>(svel + kDpdCap);                         // [NW][kDpdIMax][3]
-    int2* queues = reinterpret_cast<int2*>(accs + NW * kDpdIMax * 3);       // [NW][64]
-    int* cands = reinterpret_cast<int*>(queues + NW * 64);                  // [NW][kDpdCand]
+    R* fh = reinterpret_cast<R*>(svel + kDpdCap);                           // [kDpdCap][3]
+    int2* queues = reinterpret_cast<int2*>(fh + 3 * kDpdCap);               // [NW][64]
+    int* cands = reinterpret_cast<int*>(queues + (kDpdThreads / 32) * 64);  // [NW][kDpdCand]
     constexpr int HMAX = (kDpdMaxB + 2) * (kDpdMaxB + 2) * (kDpdMaxB + 2);
     __shared__ int hoff[HMAX + 1], gst[HMAX];
     __shared__ int chalo[kDpdMaxB * kDpdMaxB * kDpdMaxB];
     const uint64_t step = *stepp;
     const int ncd = d.ncd, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    R* acc = accs + warp * kDpdIMax * 3;
     int2* queue = queues + warp * 64;
     int* cand = cands + warp * kDpdCand;
     const int H = B + 2, H3 = H * H * H, B3 = B * B * B;
@@ -1345,14 +1377,22 @@ __global__ void __launch_bounds__(kDpdThreads) k_dpd(DpdDev d, int B, const type
                 spos[f] = sp[j];
                 svel[f] = sv[j];
             }
+            for (int k = tid; k < 3 * total; k += blockDim.x) fh[k] = (R)0;
         }
         __syncthreads();
         if (staged)
-            dpd_cells<R, true>(d, H, B3, chalo, hoff, gst, spos, svel, acc, queue, cand, atab, pos, bptr, blist,
+            dpd_cells<R, true>(d, H, B3, chalo, hoff, gst, spos, svel, fh, queue, cand, atab, pos, bptr, blist,
                                step, F, ec, eb);
         else
-            dpd_cells<R, false>(d, H, B3, chalo, hoff, gst, sp, sv, acc, queue, cand, atab, pos, bptr, blist, step,
+            dpd_cells<R, false>(d, H, B3, chalo, hoff, gst, sp, sv, fh, queue, cand, atab, pos, bptr, blist, step,
                                 F, ec, eb);
+        __syncthreads();
+        if (staged) {   // add the block's contributions to F
+            for (int k = tid; k < 3 * total; k += blockDim.x) {
+                const R v = fh[k];
+                if (v != (R)0) atomicAdd(&F[3 * real_as_int(spos[k / 3].w) + k % 3], v);
+            }
+        }
         __syncthreads();
     }
     double e1 = (double)ec, e2 = (double)eb;
