@@ -346,6 +346,168 @@ def run_reference(args):
     }
 
 
+def _stage_roof(plan, info, nq, N, esz, hbm):
+    ab = algorithmic_bytes(info, nq, N, esz)
+    out = {}
+    for k in ("spread", "fft", "gather"):
+        ms = plan.stage_time(k)
+        out[k] = {"ms": round(ms, 5), "GBps": round(ab[k] / (ms * 1e-3) / 1e9, 1),
+                  "frac": round(ab[k] / (ms * 1e-3) / 1e9 / hbm, 3), "bytes": ab[k]}
+    return out
+
+
+def run_sizes(args):
+    """Electrolyte scaling sweep (density 3, 10% charged): one ENUF evaluation
+    per size, FP32 and FP64, stage times and HBM fractions; cuFFT (through
+    torch.fft) on the same grid timed beside the hand-written FFT."""
+    import torch
+
+    from paper_1303_4523_gb300 import enuf
+    from paper_1303_4523_gb300 import workloads as W
+    peaks, _ = _peaks()
+    hbm = peaks["hbm_gbs"]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    rows = []
+    for N in (3000, 24000, 81000, 192000, 375000, 3000000):
+        s = W.electrolyte_sweep(N) if N < 3_000_000 else W.electrolyte(N, seed_offset=499)
+        row = {"N": N, "L": round(s.L, 3), "M": s.M}
+        for prec, dt, esz in (("fp32", torch.float32, 4), ("fp64", torch.float64, 8)):
+            P = dict(L=s.L, M=s.M, **s.params)
+            plan = enuf.Plan(enuf.make_params(prec=prec, **P), s.N)
+            plan.enable_timing(True)
+            pos = torch.tensor(s.pos, dtype=dt, device="cuda")
+            q = torch.tensor(s.q, dtype=dt, device="cuda")
+            F = torch.empty_like(pos)
+            for _ in range(3):
+                plan.energy_forces(pos, q, F, want_energy=False)
+            reps = 20 if N < 1_000_000 else 5
+            tot, stages = 0.0, []
+            for _ in range(reps):
+                with torch.cuda.stream(plan.stream):
+                    flush.fill_(1.0)
+                plan.energy_forces(pos, q, F, want_energy=False)
+                torch.cuda.synchronize()
+                tot += plan.stage_time("all")
+                stages.append(_stage_roof(plan, plan.info, s.n_charged, s.N, esz, hbm))
+            best = {k: min(stages, key=lambda d: d[k]["ms"])[k] for k in ("spread", "fft", "gather")}
+            row[prec] = {"ms": round(tot / reps, 4), "evals_per_s": round(reps * 1000 / tot, 1), "n": plan.info.n,
+                         "stages": best}
+            plan.close()
+        # cuFFT (torch.fft) on the same grid: R2C forward + 3 C2R inverses, FP32
+        n = row["fp32"]["n"]
+        g = torch.randn((n, n, n), device="cuda")
+        for _ in range(2):
+            spec = torch.fft.rfftn(g)
+            for _ in range(3):
+                torch.fft.irfftn(spec * 1.0001, s=(n, n, n))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ts = []
+        for _ in range(5):
+            flush.fill_(2.0)
+            e0.record()
+            spec = torch.fft.rfftn(g)
+            for _ in range(3):
+                torch.fft.irfftn(spec * 1.0001, s=(n, n, n))
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        row["cufft_fp32_ms"] = round(min(ts), 4)
+        rows.append(row)
+        print(json.dumps(row), file=sys.stderr)
+    return {"mode": "sizes", "hbm_peak_gbs": hbm, "rows": rows}
+
+
+def run_batch(args):
+    """64 uneven systems (N log-uniform in [3000, 81000], z:1 electrolytes and
+    polyelectrolytes) evaluated by one captured graph, against the same plans
+    one after another."""
+    import torch
+
+    from paper_1303_4523_gb300 import enuf
+    from paper_1303_4523_gb300 import workloads as W
+    systems = W.batch_sweep(64)
+    out = {"mode": "batch", "systems": len(systems), "beads": int(sum(s.N for s in systems))}
+    for prec, dt in (("fp32", torch.float32), ("fp64", torch.float64)):
+        params = [enuf.make_params(prec=prec, L=s.L, M=s.M, **s.params) for s in systems]
+        pos = [torch.tensor(s.pos, dtype=dt, device="cuda") for s in systems]
+        q = [torch.tensor(s.q, dtype=dt, device="cuda") for s in systems]
+        F = [torch.empty_like(p) for p in pos]
+        b = enuf.Batch(params, [s.N for s in systems])
+        for _ in range(3):
+            b.energy_forces(pos, q, F, want_energy=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 20
+        e0.record(b.stream)
+        for _ in range(reps):
+            b.energy_forces(pos, q, F, want_energy=False)
+        e1.record(b.stream)
+        torch.cuda.synchronize()
+        ms_batch = e0.elapsed_time(e1) / reps
+        launches = b.launches()
+        b.close()
+        plans = [enuf.Plan(p, s.N) for p, s in zip(params, systems)]
+        for _ in range(2):
+            for pl, a, c, f in zip(plans, pos, q, F):
+                pl.energy_forces(a, c, f, want_energy=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(5):
+            for pl, a, c, f in zip(plans, pos, q, F):
+                pl.energy_forces(a, c, f, want_energy=True)
+        seq_ms = (time.perf_counter() - t0) * 1000 / 5
+        for pl in plans:
+            pl.close()
+        out[prec] = {"graph_ms": round(ms_batch, 4), "systems_per_s": round(64 * 1000 / ms_batch, 1),
+                     "beads_per_s": round(out["beads"] * 1000 / ms_batch, 1), "launches": launches,
+                     "one_by_one_ms": round(seq_ms, 3)}
+    return out
+
+
+def run_serve(args):
+    """Poisson arrivals of ENUF force evaluations (70%) and 10-step DPD blocks
+    (30%) on systems of 1e3..1e6 beads plus one 3.0M-bead system, at ~0.8 of
+    the measured capacity; continuous batching with admission by HBM
+    footprint. Reports p50/p99 latency and aggregate beads*steps/s."""
+    import torch
+
+    from paper_1303_4523_gb300.serving import GpuBackend, Server, latency_stats, synthetic_load
+    probe = synthetic_load(60, rate_hz=1.0, seed=11)
+    be = GpuBackend()
+    srv = Server(be, budget_bytes=60 << 30, max_inflight=1)
+    for r in probe:
+        r.arrival = 0.0
+        srv.submit(r)
+    t0 = time.perf_counter()
+    res = srv.run(realtime=False)
+    busy = time.perf_counter() - t0
+    mean_service = busy / len(res)
+    srv.close()
+    rate = 0.8 / mean_service
+    reqs = synthetic_load(args.serve_requests, rate_hz=rate, seed=12)
+    srv2 = Server(be, budget_bytes=60 << 30, max_inflight=8)
+    for r in reqs:
+        srv2.submit(r)
+    t0 = time.perf_counter()
+    res = srv2.run(realtime=True)
+    wall = time.perf_counter() - t0
+    srv2.close()
+    torch.cuda.synchronize()
+    st = latency_stats(res)
+    bs = sum(r.beads_steps for r in res if r.ok)
+    errors = {}
+    for r in res:
+        if not r.ok:
+            key = f"{r.kind}: {r.error[:160]}"
+            errors[key] = errors.get(key, 0) + 1
+    return {"mode": "serve", "requests": len(res), "rate_hz": round(rate, 1), "wall_s": round(wall, 3),
+            "latency": {k: (round(v, 3) if isinstance(v, float) else v) for k, v in st.items()},
+            "beads_steps_per_s": round(bs / wall, 1), "max_concurrent": srv2.max_concurrent,
+            "max_resident_bytes": srv2.max_used, "mean_service_ms_alone": round(1000 * mean_service, 3),
+            "errors": errors}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -354,6 +516,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile", type=int, default=0, help="spreading tile edge (0: the plan's choice)")
+    ap.add_argument("--mode", default="main", choices=["main", "sizes", "batch", "serve"],
+                    help="main: the bench line; sizes/batch/serve: the scaling sweep, the 64-system batch and the "
+                         "serving load (each prints its own JSON line)")
+    ap.add_argument("--serve-requests", type=int, default=400)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -362,6 +528,13 @@ def main():
     if args.impl == "reference":
         if rank == 0:
             print(json.dumps(run_reference(args)))
+        return
+
+    if args.mode != "main":
+        from paper_1303_4523_gb300 import build
+        build.build()
+        fn = {"sizes": run_sizes, "batch": run_batch, "serve": run_serve}[args.mode]
+        print(json.dumps(fn(args)))
         return
 
     dist = None

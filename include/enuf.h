@@ -111,6 +111,13 @@ enuf_status enuf_get_info(enuf_plan_t plan, enuf_plan_info* info);
 enuf_status enuf_energy_forces(enuf_plan_t plan, int n, const void* pos, const void* q,
                                void* F, double* E, double* virial);
 
+/* Energies of the last evaluation (or DPD step) this plan completed, without
+ * synchronising: E = host double[8] laid out as dpd_step's E (the first four
+ * entries are enuf_energy_forces' E), virial may be NULL. The caller must know
+ * the work has finished (e.g. an event recorded after the call has completed);
+ * every evaluation copies its totals to pinned host memory as its last step. */
+enuf_status enuf_last_energies(enuf_plan_t plan, double* E, double* virial);
+
 /* Same, with HOST pos, q and F: the call copies the inputs to the device,
  * evaluates, copies F back and synchronises. */
 enuf_status enuf_energy_forces_host(enuf_plan_t plan, int n, const void* pos, const void* q,

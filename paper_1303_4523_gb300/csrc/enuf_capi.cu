@@ -511,6 +511,13 @@ enuf_status enuf_energy_forces(enuf_plan_t plan, int n, const void* pos, const v
     return finish_energies(plan, E, virial);
 }
 
+enuf_status enuf_last_energies(enuf_plan_t plan, double* E, double* virial) {
+    if (!plan || !E) return ENUF_ERR_INVALID;
+    for (int i = 0; i < 8; ++i) E[i] = plan->hE[i];
+    if (virial) *virial = plan->hE[7];
+    return ENUF_OK;
+}
+
 enuf_status enuf_energy_forces_host(enuf_plan_t plan, int n, const void* pos, const void* q, void* F, double* E,
                                     double* virial) {
     if (!plan) return ENUF_ERR_INVALID;

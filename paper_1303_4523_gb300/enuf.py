@@ -62,6 +62,7 @@ def _load():
         "enuf_get_info": (st, [vp, C.POINTER(enuf_plan_info)]),
         "enuf_energy_forces": (st, [vp, i, vp, vp, vp, pd, pd]),
         "enuf_energy_forces_host": (st, [vp, i, vp, vp, vp, pd, pd]),
+        "enuf_last_energies": (st, [vp, pd, pd]),
         "enuf_debug_buffer": (st, [vp, i, vp, C.c_size_t]),
         "enuf_enable_timing": (st, [vp, i]),
         "enuf_stage_time": (st, [vp, i, C.POINTER(C.c_float)]),
@@ -91,7 +92,7 @@ def _load():
 
 lib = _load()
 
-EXPORTED = ("enuf_plan", "enuf_footprint", "enuf_get_info", "enuf_energy_forces",
+EXPORTED = ("enuf_plan", "enuf_footprint", "enuf_get_info", "enuf_energy_forces", "enuf_last_energies",
             "enuf_energy_forces_host", "enuf_debug_buffer", "enuf_enable_timing",
             "enuf_stage_time", "enuf_launches_per_eval", "enuf_destroy", "enuf_status_string",
             "enuf_last_error", "dpd_create", "dpd_step", "dpd_get_state", "dpd_set_state",
@@ -197,6 +198,18 @@ class Plan:
                                           E if want_energy else None, C.byref(W) if want_energy else None),
                    self.h)
         return (np.array(E[:]), W.value) if want_energy else None
+
+    def enqueue(self, pos, q, F):
+        """Enqueue one evaluation on the plan's stream and return at once (no
+        synchronisation, no fence against torch's stream: the caller orders
+        its inputs and outputs). Energies: last_energies() once it completed."""
+        n = q.shape[0]
+        _check(lib.enuf_energy_forces(self.h, n, _ptr(pos), _ptr(q), _ptr(F), None, None), self.h)
+
+    def last_energies(self):
+        E = (C.c_double * 8)()
+        _check(lib.enuf_last_energies(self.h, E, None), self.h)
+        return np.array(E[:])
 
     def energy_forces_host(self, pos, q, F):
         """Host numpy arrays (dtype of the plan). Returns (E[4], virial)."""
