@@ -39,7 +39,7 @@ template <typename R>
 int spread_smem(const Geo& g) {
     const int T3 = g.T * g.T * g.T;
     return kSpreadCap * (int)sizeof(typename V4<R>::T) + T3 * (int)sizeof(R) +
-           (kSpreadThreads / 32) * 3 * kMaxTaps * ((int)sizeof(R) + 4) + kSpreadCap * 4;
+           (kSpreadThreads / 32) * 3 * kMaxTaps * ((int)sizeof(R) + 4) + kSpreadCap * 4 + kSpreadCap * 8;
 }
 
 // a1: compaction + coordinates + tile histograms, tile offsets, tile scan, scatter.

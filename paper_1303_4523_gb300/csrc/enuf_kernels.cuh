@@ -385,8 +385,36 @@ constexpr int kSpreadThreads = 256;
 constexpr int kMaxTaps = 16;
 constexpr int kSpreadCap = 512;   // beads staged in shared memory per round
 
+// Taps of a bead (base b, 2p taps from b - p + 1) that fall in the tile [o, o+T)
+// of a periodic grid of n points, as a bit mask over the taps. With at least
+// 3 tiles per dimension the window (2p <= 2T) meets tile tb - 1, tb or tb + 1
+// of the bead's tile tb in one contiguous run, found arithmetically; otherwise
+// the taps are tested one by one.
+__device__ __forceinline__ unsigned tap_mask(int b, int o, int T, int n, int ntd, int p) {
+    const int P2 = 2 * p;
+    if (ntd >= 3) {
+        const int tb = b / T, tc = o / T;
+        int dt = tc - tb;
+        if (dt > 1) dt -= ntd;
+        else if (dt < -1) dt += ntd;
+        if (dt < -1 || dt > 1) return 0u;
+        const int ou = (tb + dt) * T;        // tile origin in the bead's unwrapped frame
+        const int l0 = b - p + 1;
+        const int a0 = max(0, ou - l0), a1 = min(P2, ou + T - l0);
+        if (a1 <= a0) return 0u;
+        return ((a1 - a0) >= 32 ? 0xffffffffu : ((1u << (a1 - a0)) - 1u)) << a0;
+    }
+    unsigned m = 0u;
+    for (int a = 0; a < P2; ++a) {
+        int l = b - p + 1 + a;
+        l = l < 0 ? l + n : (l >= n ? l - n : l);
+        if ((unsigned)(l - o) < (unsigned)T) m |= 1u << a;
+    }
+    return m;
+}
+
 template <typename R>
-__global__ void __launch_bounds__(kSpreadThreads) k_spread(Geo g, const int* __restrict__ tstart,
+__global__ void __launch_bounds__(kSpreadThreads, 5) k_spread(Geo g, const int* __restrict__ tstart,
                                                            const typename V4<R>::T* __restrict__ sq,
                                                            const typename V4<R>::T* __restrict__ sw,
                                                            const int* __restrict__ sb,
@@ -400,37 +428,44 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(Geo g, const int* __r
     R* wts = acc + T3;                                              // [NW][3][16]
     int* lix = reinterpret_cast<int*>(wts + NW * 3 * kMaxTaps);     // [NW][3][16]
     int* sbase = lix + NW * 3 * kMaxTaps;                           // [cap]
-    __shared__ int nb_start[27], nb_cnt[27], nb_pre[28];
-    __shared__ int nnb;
+    int2* items = reinterpret_cast<int2*>(sbase + kSpreadCap);      // [cap] (bead | x mask, y mask | z mask)
+    __shared__ int nb_start[27], nb_pre[28];
+    __shared__ int nnb, nitems;
 
     const int tile = blockIdx.x;
     const int tx = tile % g.ntd, ty = (tile / g.ntd) % g.ntd, tz = tile / (g.ntd * g.ntd);
     const int o[3] = {tx * T, ty * T, tz * T};
     for (int e = threadIdx.x; e < T3; e += blockDim.x) acc[e] = (R)0;
     const int no = g.ntd >= 3 ? 3 : g.ntd;
-    if (threadIdx.x < no * no * no) {
-        const int dx = threadIdx.x % no, dy = (threadIdx.x / no) % no, dz = threadIdx.x / (no * no);
-        const int nz = g.ntd >= 3 ? (tz + dz - 1 + g.ntd) % g.ntd : dz;
-        const int ny = g.ntd >= 3 ? (ty + dy - 1 + g.ntd) % g.ntd : dy;
-        const int nx = g.ntd >= 3 ? (tx + dx - 1 + g.ntd) % g.ntd : dx;
-        const int nt = (nz * g.ntd + ny) * g.ntd + nx;
-        const int st = tstart[nt];
-        nb_start[threadIdx.x] = st;
-        nb_cnt[threadIdx.x] = tstart[nt + 1] - st;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const int cnt = no * no * no;
-        int pre = 0;
-        for (int k = 0; k < cnt; ++k) {
-            nb_pre[k] = pre;
-            pre += nb_cnt[k];
-        }
-        nb_pre[cnt] = pre;
-        nnb = cnt;
-    }
-    __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (warp == 0) {   // neighbouring bins (<= 27): starts and an exclusive prefix of their sizes
+        const int cntn = no * no * no;
+        int st = 0, c = 0;
+        if (lane < cntn) {
+            const int dx = lane % no, dy = (lane / no) % no, dz = lane / (no * no);
+            const int nz = g.ntd >= 3 ? (tz + dz - 1 + g.ntd) % g.ntd : dz;
+            const int ny = g.ntd >= 3 ? (ty + dy - 1 + g.ntd) % g.ntd : dy;
+            const int nx = g.ntd >= 3 ? (tx + dx - 1 + g.ntd) % g.ntd : dx;
+            const int nt = (nz * g.ntd + ny) * g.ntd + nx;
+            st = tstart[nt];
+            c = tstart[nt + 1] - st;
+        }
+        int x = c;
+#pragma unroll
+        for (int of = 1; of < 32; of <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, of);
+            if (lane >= of) x += y;
+        }
+        if (lane < cntn) {
+            nb_start[lane] = st;
+            nb_pre[lane] = x - c;
+        }
+        if (lane == cntn - 1) {
+            nb_pre[cntn] = x;
+            nnb = cntn;
+        }
+    }
+    __syncthreads();
     R* myw = wts + warp * 3 * kMaxTaps;
     int* myl = lix + warp * 3 * kMaxTaps;
     const int P2 = 2 * g.p;
@@ -438,58 +473,77 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(Geo g, const int* __r
     const R rb = (R)g.rb, wn = (R)g.wnorm;
     for (int cb = 0; cb < total; cb += kSpreadCap) {
         const int cn = min(kSpreadCap, total - cb);
-        // stage this round's candidates (coalesced runs of each neighbouring bin)
-        for (int k = 0; k < nnb; ++k) {
-            const int lo = max(nb_pre[k], cb), hi = min(nb_pre[k + 1], cb + cn);
-            for (int idx = lo + threadIdx.x; idx < hi; idx += blockDim.x) {
-                const int j = nb_start[k] + idx - nb_pre[k];
-                V v = sw[j];
-                v.w = sq[j].w;
-                stg[idx - cb] = v;
-                sbase[idx - cb] = sb[j];
+        if (threadIdx.x == 0) nitems = 0;
+        // stage this round's candidates: one thread per bead, its bin by binary search
+        for (int idx = threadIdx.x; idx < cn; idx += blockDim.x) {
+            const int f = cb + idx;
+            int lo = 0, hi = nnb;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (nb_pre[mid] <= f) lo = mid; else hi = mid;
             }
+            const int j = nb_start[lo] + f - nb_pre[lo];
+            V v = sw[j];
+            v.w = sq[j].w;
+            stg[idx] = v;
+            sbase[idx] = sb[j];
         }
         __syncthreads();
-        for (int c = warp; c < cn; c += NW) {
+        // phase A: one lane per candidate; beads whose window meets this tile become work items
+        for (int c0 = 0; c0 < cn; c0 += blockDim.x) {
+            const int c = c0 + threadIdx.x;
+            unsigned mx = 0u, my = 0u, mz = 0u;
+            if (c < cn) {
+                const int pb = sbase[c];
+                mx = tap_mask(pb & 1023, o[0], T, g.n, g.ntd, g.p);
+                if (mx) my = tap_mask((pb >> 10) & 1023, o[1], T, g.n, g.ntd, g.p);
+                if (my) mz = tap_mask((pb >> 20) & 1023, o[2], T, g.n, g.ntd, g.p);
+            }
+            const bool keep = mz != 0u;
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            int basei = 0;
+            if (lane == 0 && bal) basei = atomicAdd(&nitems, __popc(bal));
+            basei = __shfl_sync(0xffffffffu, basei, 0);
+            if (keep) items[basei + __popc(bal & ((1u << lane) - 1u))] = make_int2(c | (int)(mx << 16), (int)(my | (mz << 16)));
+        }
+        __syncthreads();
+        const int ni = nitems;
+        // phase B: one warp per work item
+        for (int it = warp; it < ni; it += NW) {
+            const int2 e = items[it];
+            const int c = e.x & 0xffff;
+            const unsigned msk[3] = {(unsigned)e.x >> 16, (unsigned)e.y & 0xffffu, (unsigned)e.y >> 16};
             const V wv = stg[c];
             const int pb = sbase[c];
-            const int base[3] = {pb & 1023, (pb >> 10) & 1023, (pb >> 20) & 1023};
-            const R fr[3] = {wv.x, wv.y, wv.z};
-            unsigned msk[3];
-            int lw[3];
-            bool inside[3];
+            if (lane < P2) {
+                const int base[3] = {pb & 1023, (pb >> 10) & 1023, (pb >> 20) & 1023};
+                const R fr[3] = {wv.x, wv.y, wv.z};
 #pragma unroll
-            for (int t = 0; t < 3; ++t) {
-                int l = base[t] - g.p + 1 + lane;
-                l = l < 0 ? l + g.n : (l >= g.n ? l - g.n : l);
-                lw[t] = l - o[t];
-                inside[t] = lane < P2 && (unsigned)lw[t] < (unsigned)T;
-                msk[t] = __ballot_sync(0xffffffffu, inside[t]);
-            }
-            if (!msk[0] || !msk[1] || !msk[2]) continue;
-#pragma unroll
-            for (int t = 0; t < 3; ++t) {
-                if (inside[t]) {
-                    const int slot = __popc(msk[t] & ((1u << lane) - 1u));
-                    const R d = fr[t] + (R)(g.p - 1 - lane);
-                    myw[t * kMaxTaps + slot] = wn * r_exp(-d * d * rb);
-                    myl[t * kMaxTaps + slot] = lw[t];
+                for (int t = 0; t < 3; ++t) {
+                    if ((msk[t] >> lane) & 1u) {
+                        const int slot = __popc(msk[t] & ((1u << lane) - 1u));
+                        int l = base[t] - g.p + 1 + lane;
+                        l = l < 0 ? l + g.n : (l >= g.n ? l - g.n : l);
+                        const R d = fr[t] + (R)(g.p - 1 - lane);
+                        myw[t * kMaxTaps + slot] = wn * r_exp(-d * d * rb);
+                        myl[t * kMaxTaps + slot] = l - o[t];
+                    }
                 }
             }
             __syncwarp();
             const int cx = __popc(msk[0]), cy = __popc(msk[1]), cz = __popc(msk[2]);
-            const int cxy = cx * cy, npt = cxy * cz;
-            // s -> (ix, iy, iz) by float reciprocals: s < 4096 and the true quotient
-            // of s + 1/2 is at least 1/32 away from an integer, far above the error
-            const float icx = 1.0f / (float)cx, icxy = 1.0f / (float)cxy;
+            const int cxy = cx * cy;
+            // xy -> (ix, iy) by a float reciprocal: xy < 256 and the true quotient of
+            // xy + 1/2 is at least 1/32 away from an integer, far above the error
+            const float icx = 1.0f / (float)cx;
             const R qj = wv.w;
-            for (int s = lane; s < npt; s += 32) {
-                const int iz = (int)(((float)s + 0.5f) * icxy);
-                const int r2 = s - iz * cxy;
-                const int iy = (int)(((float)r2 + 0.5f) * icx);
-                const int ix = r2 - iy * cx;
-                const R v = qj * myw[ix] * myw[kMaxTaps + iy] * myw[2 * kMaxTaps + iz];
-                atomicAdd(&acc[(myl[2 * kMaxTaps + iz] * T + myl[kMaxTaps + iy]) * T + myl[ix]], v);
+            for (int xy = lane; xy < cxy; xy += 32) {
+                const int iy = (int)(((float)xy + 0.5f) * icx);
+                const int ix = xy - iy * cx;
+                const R wxy = qj * myw[ix] * myw[kMaxTaps + iy];
+                const int rowo = myl[kMaxTaps + iy] * T + myl[ix];
+                for (int iz = 0; iz < cz; ++iz)
+                    atomicAdd(&acc[myl[2 * kMaxTaps + iz] * T * T + rowo], wxy * myw[2 * kMaxTaps + iz]);
             }
             __syncwarp();
         }
