@@ -183,7 +183,9 @@ enuf_status dpd_create(enuf_plan_t plan, const dpd_params* params, int n, const 
  * DPD pair + bond forces (theta keyed by the new step number), electrostatics
  * (real + ENUF reciprocal), half kick. E: host double[8] or NULL =
  * {E_real, E_recip, E_self + E_neutral, E_elec, E_conservative, E_bond,
- *  E_kinetic, virial_elec} of the last step (synchronises when non-NULL). */
+ *  E_kinetic, virial_elec} of the last step, or of the force evaluation of
+ *  dpd_create / dpd_set_state when no step has run since (nsteps = 0 reads
+ *  them without stepping); synchronises when non-NULL. */
 enuf_status dpd_step(dpd_system_t sys, int nsteps, double* E);
 
 /* Checkpoint / restart: copy the state to or from HOST real[n][3] arrays

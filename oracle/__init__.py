@@ -38,7 +38,7 @@ class _Params(C.Structure):
     _fields_ = [("L", C.c_double), ("alpha", C.c_double), ("r_cut", C.c_double),
                 ("beta", C.c_double), ("kappa", C.c_double), ("M", C.c_int),
                 ("p", C.c_int), ("sigma_s", C.c_int), ("kmask", C.c_int),
-                ("fp32_cut", C.c_int)]
+                ("fp32_cut", C.c_int), ("deriv", C.c_int)]
 
 
 class _DpdParams(C.Structure):
@@ -96,10 +96,11 @@ class EwaldParams:
     sigma_s: int = 2
     kmask: int = 0
     fp32_cut: int = 0
+    deriv: int = 0       # ENUF forces: 0 ik-differentiation (Eq. 24-25), 1 analytic gradient
 
     def c(self) -> _Params:
         return _Params(self.L, self.alpha, self.r_cut, self.beta, self.kappa,
-                       self.M, self.p, self.sigma_s, self.kmask, self.fp32_cut)
+                       self.M, self.p, self.sigma_s, self.kmask, self.fp32_cut, self.deriv)
 
     @property
     def ng(self) -> int:
@@ -200,7 +201,7 @@ def recip_enuf(P: EwaldParams, pos, q, sample=None, want_grid=False, want_h=Fals
     EW = np.zeros(2)
     ng = P.ng
     grid = np.zeros((ng, ng, ng)) if want_grid else None
-    h = np.zeros((3, ng, ng, ng)) if want_h else None
+    h = np.zeros((1 if P.deriv else 3, ng, ng, ng)) if want_h else None
     _check(lib().orc_recip_enuf(C.byref(P.c()), n, _pd(pos), _pd(q), _pd(F), _pd(EW),
                                 _pd(grid), _pd(h), _pi(s), 0 if s is None else s.shape[0]),
            "recip_enuf")

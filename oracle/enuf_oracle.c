@@ -347,6 +347,7 @@ int orc_recip_enuf(const orc_params* P, int n, const double* pos, const double* 
     const int M = P->M, nc = M / 2 - 1, p = P->p, sg = P->sigma_s;
     const int ng = sg * M;
     if (n < 0 || nc < 1 || p < 1 || sg < 2 || 2 * p > ng) return ORC_EINVAL;
+    if (P->deriv && p > 8) return ORC_EINVAL;   /* the gradient path keeps 2p <= 16 taps */
     const double L = P->L, kap = P->kappa;
     const double b = 2.0 * sg * p / ((2.0 * sg - 1.0) * M_PI);
     const int K = 2 * nc + 1, T = 2 * p;
@@ -478,6 +479,8 @@ int orc_recip_enuf(const orc_params* P, int n, const double* pos, const double* 
         free(Gr); free(Gi);
         return ORC_ENOMEM;
     }
+    const int deriv = P->deriv;
+    const int nfield = deriv ? 1 : 3;
     double E = 0.0, W = 0.0;
     for (int ix = 0; ix < K; ++ix)
         for (int iy = 0; iy < K; ++iy)
@@ -491,10 +494,15 @@ int orc_recip_enuf(const orc_params* P, int n, const double* pos, const double* 
                 const double e = f * (Sr * Sr + Si * Si);
                 E += e;
                 W += e * virial_weight(P, kx, ky, kz);
-                const int kv[3] = {kx, ky, kz};
-                for (int a = 0; a < 3; ++a) {
-                    Gr[a * nF + id] = kv[a] * f * Sr / c;
-                    Gi[a * nF + id] = kv[a] * f * Si / c;
+                if (deriv) {   /* the potential-like field: f S / c */
+                    Gr[id] = f * Sr / c;
+                    Gi[id] = f * Si / c;
+                } else {
+                    const int kv[3] = {kx, ky, kz};
+                    for (int a = 0; a < 3; ++a) {
+                        Gr[a * nF + id] = kv[a] * f * Sr / c;
+                        Gi[a * nF + id] = kv[a] * f * Si / c;
+                    }
                 }
             }
     if (EW) {
@@ -521,7 +529,7 @@ int orc_recip_enuf(const orc_params* P, int n, const double* pos, const double* 
             free(Gr); free(Gi);
             return ORC_ENOMEM;
         }
-        for (int a = 0; a < 3; ++a) {
+        for (int a = 0; a < nfield; ++a) {
             const double* gr = &Gr[a * nF];
             const double* gi = &Gi[a * nF];
             /* B1[kx][ky][lz] = sum_kz G[kx][ky][kz] e^{+2 pi i kz lz / n} */
@@ -556,22 +564,61 @@ int orc_recip_enuf(const orc_params* P, int n, const double* pos, const double* 
                         B2r[((size_t)ix * ng + lz) * ng + ly] = sr;
                         B2i[((size_t)ix * ng + lz) * ng + ly] = si;
                     }
-            /* Im h[lz][ly][lx] = Im sum_kx B2[kx][lz][ly] e^{+2 pi i kx lx / n} */
+            /* Im h[lz][ly][lx] = Im sum_kx B2[kx][lz][ly] e^{+2 pi i kx lx / n}
+             * (deriv = 1: the real part, h being real) */
             #pragma omp parallel for schedule(static)
             for (int lz = 0; lz < ng; ++lz)
                 for (int ly = 0; ly < ng; ++ly)
                     for (int lx = 0; lx < ng; ++lx) {
-                        double si = 0.0;
+                        double sr = 0.0, si = 0.0;
                         for (int ix = 0; ix < K; ++ix) {
                             const int m = imod((ix - nc) * lx, ng);
                             const double br = B2r[((size_t)ix * ng + lz) * ng + ly];
                             const double bi = B2i[((size_t)ix * ng + lz) * ng + ly];
+                            sr += br * cs[m] - bi * sn[m];
                             si += bi * cs[m] + br * sn[m];
                         }
-                        Hi[((size_t)lz * ng + ly) * ng + lx] = si;
+                        Hi[((size_t)lz * ng + ly) * ng + lx] = deriv ? sr : si;
                     }
             if (hfield) memcpy(&hfield[(size_t)a * ng3], Hi, sizeof(double) * ng3);
-            if (F) {
+            if (F && deriv) {
+                /* F_{i,t} = -(kappa q_i n/(pi L^2)) sum_l dPsi_t(n x_i - l) h(l) */
+                #pragma omp parallel for schedule(static)
+                for (int s = 0; s < nout; ++s) {
+                    const int i = sample ? sample[s] : s;
+                    if (q[i] == 0.0) continue;
+                    double w[3][16], dw[3][16];
+                    for (int t = 0; t < 3; ++t) {
+                        double fr;
+                        int bt;
+                        if (P->fp32_cut)
+                            grid_coord_f32(x[3 * i + t], L, ng, &bt, &fr);
+                        else
+                            grid_coord(x[3 * i + t], L, ng, &bt, &fr);
+                        for (int aa = 0; aa < T; ++aa) {
+                            const double d = fr + (double)(p - 1 - aa);   /* n x - l */
+                            w[t][aa] = wgt[((size_t)i * 3 + t) * T + aa];
+                            dw[t][aa] = -2.0 * d / b * w[t][aa];
+                        }
+                    }
+                    double acc[3] = {0.0, 0.0, 0.0};
+                    for (int c = 0; c < T; ++c) {
+                        const int lz = imod(base[3 * i + 2] - p + 1 + c, ng);
+                        for (int bb = 0; bb < T; ++bb) {
+                            const int ly = imod(base[3 * i + 1] - p + 1 + bb, ng);
+                            for (int aa = 0; aa < T; ++aa) {
+                                const int lx = imod(base[3 * i] - p + 1 + aa, ng);
+                                const double hv = Hi[((size_t)lz * ng + ly) * ng + lx];
+                                acc[0] += dw[0][aa] * w[1][bb] * w[2][c] * hv;
+                                acc[1] += w[0][aa] * dw[1][bb] * w[2][c] * hv;
+                                acc[2] += w[0][aa] * w[1][bb] * dw[2][c] * hv;
+                            }
+                        }
+                    }
+                    for (int t = 0; t < 3; ++t) F[3 * s + t] = -kap * q[i] * ng / (M_PI * L * L) * acc[t];
+                }
+            }
+            if (F && !deriv) {
                 #pragma omp parallel for schedule(static)
                 for (int s = 0; s < nout; ++s) {
                     const int i = sample ? sample[s] : s;

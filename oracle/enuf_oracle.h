@@ -48,6 +48,8 @@ typedef struct {
     int    sigma_s; /* oversampling factor; grid n = sigma_s * M */
     int    kmask;   /* 0: cubic |k_t| <= n_c; 1: spherical |k| <= n_c */
     int    fp32_cut;/* 1: take pair-cutoff decisions in float, as an FP32 path does */
+    int    deriv;   /* ENUF forces: 0 = ik-differentiation (Eq. 24-25); 1 = analytic
+                       gradient of the window (one real field, see orc_recip_enuf) */
 } orc_params;
 
 /* Position wrapping into [0, L): identity inside, else x - L floor(x/L). */
@@ -78,6 +80,13 @@ int orc_recip_direct(const orc_params* P, int n, const double* pos, const double
  * Optional intermediate outputs (NULL to skip):
  *   grid   : n_g^3 spread grid, index (lz*n_g + ly)*n_g + lx      (n_g = sigma_s*M)
  *   hfield : 3 x n_g^3, Im of the conjugated-NFFT field of g_n/c for a = x,y,z
+ *            (deriv = 1: n_g^3, the real field h below)
+ * deriv = 1 replaces Eq. 24-25 by the exact gradient of the NFFT energy:
+ * with h(l) = sum_k f(k) S(k)/c(k) e^{2 pi i k.l/n} (real) and d = n x_i - l,
+ *   F_{i,a} = -(kappa q_i n / (pi L^2)) sum_l psi'(d_a) prod_{t!=a} psi(d_t) h(l),
+ *   psi'(d) = -(2 d / b) psi(d)
+ * (derivation: differentiate kappa/(2 pi L) sum_k f |Fhat/c|^2 through the
+ * spread of Eq. 14; one inverse transform instead of three).
  * F/EW/sample as in orc_real_space. */
 int orc_recip_enuf(const orc_params* P, int n, const double* pos, const double* q,
                    double* F, double* EW, double* grid, double* hfield,

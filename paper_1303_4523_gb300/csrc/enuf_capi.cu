@@ -638,6 +638,7 @@ enuf_status initial_force(dpd_system_t sys) {
     if (st != ENUF_OK) return st;
     st = enqueue_tot(plan, true, plan->stream, &log);
     if (st != ENUF_OK) return st;
+    CU(cudaMemcpyAsync(plan->hE, plan->w.Edev, 16 * sizeof(double), cudaMemcpyDeviceToHost, plan->stream));
     CU(cudaStreamSynchronize(plan->stream));
     CU(cudaGetLastError());
     return ENUF_OK;
@@ -693,6 +694,7 @@ enuf_status dpd_create(enuf_plan_t plan, const dpd_params* params, int n, const 
     if (n < 1 || n > plan->n_max) return fail(plan, ENUF_ERR_INVALID, "n = %d outside [1, n_max]", n);
     if (!pos || !vel || !type || !q || (n_bonds > 0 && !bonds) || n_bonds < 0)
         return fail(plan, ENUF_ERR_INVALID, "null array");
+    if (n_bonds > (1 << 28)) return fail(plan, ENUF_ERR_INVALID, "n_bonds = %d too large", n_bonds);
     if (params->ntypes < 1 || !params->a) return fail(plan, ENUF_ERR_INVALID, "ntypes < 1 or a == NULL");
     if (!(params->dt > 0)) return fail(plan, ENUF_ERR_INVALID, "dt must be > 0");
     const double L = plan->P.L;
@@ -725,26 +727,13 @@ enuf_status dpd_create(enuf_plan_t plan, const dpd_params* params, int n, const 
     d.cinv = (double)d.ncd / L;
     d.xmaxf = largest_float_below(L);
     const size_t rs = plan->rsz;
-    // per-bead bond lists (CSR over both ends)
-    std::vector<int> bptr(n + 1, 0), blist(2 * (size_t)n_bonds);
-    for (int k = 0; k < n_bonds; ++k) {
-        ++bptr[bonds[2 * k] + 1];
-        ++bptr[bonds[2 * k + 1] + 1];
-    }
-    for (int i = 0; i < n; ++i) bptr[i + 1] += bptr[i];
-    {
-        std::vector<int> cur(bptr.begin(), bptr.end() - 1);
-        for (int k = 0; k < n_bonds; ++k) {
-            blist[cur[bonds[2 * k]]++] = bonds[2 * k + 1];
-            blist[cur[bonds[2 * k + 1]]++] = bonds[2 * k];
-        }
-    }
+    d.nbonds = n_bonds;
     size_t off = 0;
     auto take = [&](size_t b) { size_t o = off; off += align256(b); return o; };
     const size_t o_pos = take(n * 3 * rs), o_vel = take(n * 3 * rs), o_v0 = take(n * 3 * rs),
                  o_F = take(n * 3 * rs), o_q = take(n * rs), o_type = take(n * 4),
-                 o_atab = take((size_t)d.ntypes * d.ntypes * rs), o_bptr = take((n + 1) * 4),
-                 o_blist = take(std::max<size_t>(1, blist.size()) * 4), o_ckey = take(n * 4),
+                 o_atab = take((size_t)d.ntypes * d.ntypes * rs), o_bnd = take(std::max<size_t>(1, (size_t)n_bonds) * 8),
+                 o_ckey = take(n * 4),
                  o_ccount = take((size_t)d.ncells * 4), o_cstart = take(((size_t)d.ncells + 1) * 4),
                  o_ccur = take(((size_t)d.ncells + 1) * 4), o_sp = take(n * 4 * rs), o_sv = take(n * 4 * rs),
                  o_step = take(8);
@@ -757,7 +746,7 @@ enuf_status dpd_create(enuf_plan_t plan, const dpd_params* params, int n, const 
     char* b = static_cast<char*>(sys->dmem);
     d.pos = b + o_pos; d.vel = b + o_vel; d.v0 = b + o_v0; d.F = b + o_F; d.q = b + o_q;
     d.type = reinterpret_cast<int*>(b + o_type); d.atab = b + o_atab;
-    d.bptr = reinterpret_cast<int*>(b + o_bptr); d.blist = reinterpret_cast<int*>(b + o_blist);
+    d.bnd = reinterpret_cast<int*>(b + o_bnd);
     d.ckey = reinterpret_cast<int*>(b + o_ckey); d.ccount = reinterpret_cast<int*>(b + o_ccount);
     d.cstart = reinterpret_cast<int*>(b + o_cstart); d.ccur = reinterpret_cast<int*>(b + o_ccur);
     d.sp = b + o_sp; d.sv = b + o_sv; d.step_dev = reinterpret_cast<uint64_t*>(b + o_step);
@@ -773,8 +762,7 @@ enuf_status dpd_create(enuf_plan_t plan, const dpd_params* params, int n, const 
         cudaMemcpy(d.q, q, n * rs, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(d.type, type, n * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(d.atab, at.data(), at.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(d.bptr, bptr.data(), (n + 1) * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
-        (!blist.empty() && cudaMemcpy(d.blist, blist.data(), blist.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess))
+        (n_bonds > 0 && cudaMemcpy(d.bnd, bonds, (size_t)n_bonds * 8, cudaMemcpyHostToDevice) != cudaSuccess))
         return bail(fail(plan, ENUF_ERR_CUDA, "upload failed"));
     enuf_status st = initial_force(sys);
     if (st != ENUF_OK) return bail(st);

@@ -132,13 +132,12 @@ cudaError_t enqueue_dpd_forces(const Work& w, const DpdDev& d, cudaStream_t s, E
                                              d.type, d.ckey, d.ccur, static_cast<V*>(d.sp), static_cast<V*>(d.sv));
     rec(ev, 7, false, s);
     rec(ev, 5, true, s);
-    const int dpd_smem = 2 * kDpdCap * (int)sizeof(V) + 3 * kDpdCap * (int)sizeof(R) +
-                         (kDpdThreads / 32) * (64 * 8 + kDpdCand * 4);
+    const int dpd_smem = dpd_smem_bytes<R>();
     cudaMemsetAsync(d.F, 0, (size_t)d.N * 3 * sizeof(R), s);   // the pair kernel adds into F
     k_dpd<R><<<w.nblk_dpd, kDpdThreads, dpd_smem, s>>>(d, d.B, static_cast<const V*>(d.sp),
                                                       static_cast<const V*>(d.sv), d.cstart,
                                                       static_cast<const R*>(d.atab), static_cast<const R*>(d.pos),
-                                                      d.bptr, d.blist, d.step_dev, static_cast<R*>(d.F),
+                                                      d.bnd, d.step_dev, static_cast<R*>(d.F),
                                                       w.part + w.off_dpd);
     rec(ev, 5, false, s);
     log->kernels += 4;

@@ -23,6 +23,15 @@ struct FftPlanDev {
     int rad[8];
 };
 
+// a / b for 0 <= a < 2^23, b >= 1, given rb = 1/b in float: the float quotient
+// of a + 1/2 is within one of the true one, and one integer step corrects it.
+__device__ __forceinline__ int qdiv(int a, int b, float rb) {
+    int q = (int)(((float)a + 0.5f) * rb);
+    const int r = a - q * b;
+    q += (r >= b ? 1 : 0) - (r < 0 ? 1 : 0);
+    return q;
+}
+
 template <typename C>
 __device__ __forceinline__ C cmul(C a, C b) {
     C r;
@@ -132,10 +141,11 @@ __device__ __forceinline__ void fft_stage(const typename Cx<R>::T* __restrict__ 
     const int m = n / RAD;
     const int tstep = n / (Ns * RAD);
     const int total = nlines * m;
+    const float rm = 1.0f / (float)m, rNs = 1.0f / (float)Ns;
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-        const int line = idx / m;
+        const int line = qdiv(idx, m, rm);
         const int j = idx - line * m;
-        const int k = j % Ns;
+        const int k = j - qdiv(j, Ns, rNs) * Ns;
         const C* s = src + line * ls;
         C* d = dst + line * ls;
         C v[RAD];

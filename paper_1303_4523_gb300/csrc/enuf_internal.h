@@ -104,7 +104,8 @@ struct DpdDev {
     void* pos; void* vel; void* v0; void* F; void* q;   // real
     int* type;
     void* atab;        // real [ntypes^2]
-    int* bptr; int* blist;   // per-bead bond lists (CSR)
+    int nbonds;
+    int* bnd;                // bond pairs [nbonds][2]
     int* ckey; int* ccount; int* cstart; int* ccur;
     void* sp; void* sv;      // real4 [N] sorted: (x, y, z, orig) and (v0, type)
     uint64_t* step_dev;      // device copy of the step counter

@@ -550,9 +550,13 @@ __global__ void __launch_bounds__(kSpreadThreads, 5) k_spread(Geo g, const int* 
         __syncthreads();
     }
     const int n = g.n;
-    for (int e = threadIdx.x; e < T3; e += blockDim.x) {
-        const int lx = e % T, ly = (e / T) % T, lz = e / (T * T);
-        grid[((size_t)(o[2] + lz) * n + (o[1] + ly)) * n + (o[0] + lx)] = acc[e];
+    // write-back, one row of T <= 24 points per warp iteration
+    int ly = warp, lz = 0;
+    while (ly >= T) { ly -= T; ++lz; }
+    while (lz < T) {
+        if (lane < T) grid[((size_t)(o[2] + lz) * n + (o[1] + ly)) * n + (o[0] + lane)] = acc[(lz * T + ly) * T + lane];
+        ly += NW;
+        while (ly >= T) { ly -= T; ++lz; }
     }
 }
 
@@ -571,11 +575,13 @@ __global__ void __launch_bounds__(256) k_fft_x(Geo g, FftPlanDev fp, const R* __
     C* b0 = tw + n;
     C* b1 = b0 + LP * n;
     for (int t = threadIdx.x; t < n; t += blockDim.x) tw[t] = twg[t];
+    const float rn = 1.0f / (float)n;
     const int row0 = blockIdx.x * 2 * LP;     // first real row (z*n + y), y even
     const int nrows = n * n;
     const int nl = min(LP, (nrows - row0) / 2);
+    const float rnl = 1.0f / (float)max(nl, 1);
     for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
-        const int c = idx / n, x = idx - c * n;
+        const int c = qdiv(idx, n, rn), x = idx - c * n;
         C v;
         v.x = grid[(size_t)(row0 + 2 * c) * n + x];
         v.y = grid[(size_t)(row0 + 2 * c + 1) * n + x];
@@ -585,7 +591,7 @@ __global__ void __launch_bounds__(256) k_fft_x(Geo g, FftPlanDev fp, const R* __
     C* res = fft_lines<R, false>(b0, b1, tw, fp, nl, n);
     // split the two real transforms: A = (Z_k + conj Z_{n-k})/2, B = -i (Z_k - conj Z_{n-k})/2
     for (int idx = threadIdx.x; idx < nl * nc1; idx += blockDim.x) {
-        const int k = idx / nl, c = idx - k * nl;
+        const int k = qdiv(idx, nl, rnl), c = idx - k * nl;
         const C z = res[c * n + k];
         const C zm = res[c * n + (k == 0 ? 0 : n - k)];
         C A, B;
@@ -594,7 +600,7 @@ __global__ void __launch_bounds__(256) k_fft_x(Geo g, FftPlanDev fp, const R* __
         B.x = (R)0.5 * (z.y + zm.y);
         B.y = (R)0.5 * (zm.x - z.x);
         const int row = row0 + 2 * c;
-        const int zz = row / n, y = row - zz * n;
+        const int zz = qdiv(row, n, rn), y = row - zz * n;
         C* dst = spec1 + ((size_t)zz * nc1 + k) * n + y;
         dst[0] = A;
         dst[1] = B;
@@ -613,17 +619,19 @@ __global__ void __launch_bounds__(256) k_fft_y(Geo g, FftPlanDev fp, const typen
     C* b0 = tw + n;
     C* b1 = b0 + LB * n;
     for (int t = threadIdx.x; t < n; t += blockDim.x) tw[t] = twg[t];
+    const float rn = 1.0f / (float)n;
     const int kx = blockIdx.x;
     const int z0 = blockIdx.y * LB;
     const int nl = min(LB, n - z0);
+    const float rnl = 1.0f / (float)max(nl, 1);
     for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
-        const int c = idx / n, y = idx - c * n;
+        const int c = qdiv(idx, n, rn), y = idx - c * n;
         b0[c * n + y] = spec1[((size_t)(z0 + c) * nc1 + kx) * n + y];
     }
     __syncthreads();
     C* res = fft_lines<R, false>(b0, b1, tw, fp, nl, n);
     for (int idx = threadIdx.x; idx < nl * K; idx += blockDim.x) {
-        const int ki = idx / nl, c = idx - ki * nl;
+        const int ki = qdiv(idx, nl, rnl), c = idx - ki * nl;
         const int ky = ki - g.nc;
         spec2[((size_t)kx * K + ki) * n + z0 + c] = res[c * n + (ky < 0 ? ky + n : ky)];
     }
@@ -641,13 +649,16 @@ __global__ void __launch_bounds__(256) k_fft_z(Geo g, FftPlanDev fp, const typen
     extern __shared__ unsigned char smraw[];
     const int n = g.n, nc = g.nc, K = g.K;
     const int NL = (nc + 1) * K;
+    const float rK = 1.0f / (float)K;
     C* tw = reinterpret_cast<C*>(smraw);
     C* b0 = tw + n;
     C* b1 = b0 + LB * n;
     C* b2 = b1 + LB * n;
     for (int t = threadIdx.x; t < n; t += blockDim.x) tw[t] = twg[t];
+    const float rn = 1.0f / (float)n;
     const int l0 = blockIdx.x * LB;
     const int nl = min(LB, NL - l0);
+    const float rnl = 1.0f / (float)max(nl, 1);
     for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) b0[idx] = spec2[(size_t)l0 * n + idx];
     __syncthreads();
     C* Fh = fft_lines<R, false>(b0, b1, tw, fp, nl, n);
@@ -656,9 +667,9 @@ __global__ void __launch_bounds__(256) k_fft_z(Geo g, FftPlanDev fp, const typen
     // energy and virial of the kept modes (half space kx >= 0, kx > 0 counted twice)
     Kahan ke, kw;
     for (int idx = threadIdx.x; idx < nl * K; idx += blockDim.x) {
-        const int c = idx / K, kzi = idx - c * K;
+        const int c = qdiv(idx, K, rK), kzi = idx - c * K;
         const int l = l0 + c;
-        const int kx = l / K;
+        const int kx = qdiv(l, K, rK);
         const int kz = kzi - nc;
         const C f = Fh[c * n + (kz < 0 ? kz + n : kz)];
         const double a2 = (double)f.x * (double)f.x + (double)f.y * (double)f.y;
@@ -675,14 +686,14 @@ __global__ void __launch_bounds__(256) k_fft_z(Geo g, FftPlanDev fp, const typen
     for (int a = 0; a < 3; ++a) {
         __syncthreads();
         for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
-            const int c = idx / n, m = idx - c * n;
+            const int c = qdiv(idx, n, rn), m = idx - c * n;
             const int kz = m <= n / 2 ? m : m - n;
             C v;
             v.x = (R)0;
             v.y = (R)0;
             if (kz >= -nc && kz <= nc) {
                 const int l = l0 + c;
-                const int kx = l / K, ky = (l - kx * K) - nc;
+                const int kx = qdiv(l, K, rK), ky = (l - kx * K) - nc;
                 const int ka = a == 0 ? kx : (a == 1 ? ky : kz);
                 const R s = (R)ka * tabr[(size_t)l * K + (kz + nc)];
                 const C f = Fh[c * n + m];
@@ -694,7 +705,7 @@ __global__ void __launch_bounds__(256) k_fft_z(Geo g, FftPlanDev fp, const typen
         __syncthreads();
         C* res = fft_lines<R, true>(wa, wb, tw, fp, nl, n);
         for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
-            const int z = idx / nl, c = idx - z * nl;
+            const int z = qdiv(idx, nl, rnl), c = idx - z * nl;
             spec3[((size_t)a * n + z) * NL + l0 + c] = res[c * n + z];
         }
         // res is wa or wb; the next field rebuilds into wa, so keep both free
@@ -711,14 +722,17 @@ __global__ void __launch_bounds__(256) k_fft_iy(Geo g, FftPlanDev fp, const type
     extern __shared__ unsigned char smraw[];
     const int n = g.n, nc = g.nc, nc1 = nc + 1, K = g.K;
     const int NLT = 3 * n * nc1;
+    const float rnc1 = 1.0f / (float)nc1;
     C* tw = reinterpret_cast<C*>(smraw);
     C* b0 = tw + n;
     C* b1 = b0 + LB * n;
     for (int t = threadIdx.x; t < n; t += blockDim.x) tw[t] = twg[t];
+    const float rn = 1.0f / (float)n;
     const int l0 = blockIdx.x * LB;
     const int nl = min(LB, NLT - l0);
+    const float rnl = 1.0f / (float)max(nl, 1);
     for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
-        const int c = idx / n, m = idx - c * n;
+        const int c = qdiv(idx, n, rn), m = idx - c * n;
         const int ky = m <= n / 2 ? m : m - n;
         C v;
         v.x = (R)0;
@@ -729,9 +743,9 @@ __global__ void __launch_bounds__(256) k_fft_iy(Geo g, FftPlanDev fp, const type
     __syncthreads();
     C* res = fft_lines<R, true>(b0, b1, tw, fp, nl, n);
     for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
-        const int y = idx / nl, c = idx - y * nl;
+        const int y = qdiv(idx, nl, rnl), c = idx - y * nl;
         const int l = l0 + c;
-        const int az = l / nc1, kx = l - az * nc1;
+        const int az = qdiv(l, nc1, rnc1), kx = l - az * nc1;
         spec4[((size_t)az * n + y) * nc1 + kx] = res[c * n + y];
     }
 }
@@ -749,10 +763,12 @@ __global__ void __launch_bounds__(256) k_fft_ix(Geo g, FftPlanDev fp, const type
     C* b0 = tw + n;
     C* b1 = b0 + LP * n;
     for (int t = threadIdx.x; t < n; t += blockDim.x) tw[t] = twg[t];
+    const float rn = 1.0f / (float)n;
     const int row0 = blockIdx.x * 2 * LP;
     const int nl = min(LP, (nrows - row0) / 2);
+    const float rnl = 1.0f / (float)max(nl, 1);
     for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
-        const int c = idx / n, m = idx - c * n;
+        const int c = qdiv(idx, n, rn), m = idx - c * n;
         const C* A = spec4 + (size_t)(row0 + 2 * c) * nc1;
         const C* B = A + nc1;
         C a, b;
@@ -777,7 +793,7 @@ __global__ void __launch_bounds__(256) k_fft_ix(Geo g, FftPlanDev fp, const type
     __syncthreads();
     C* res = fft_lines<R, true>(b0, b1, tw, fp, nl, n);
     for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
-        const int c = idx / n, x = idx - c * n;
+        const int c = qdiv(idx, n, rn), x = idx - c * n;
         const C v = res[idx];
         h[(size_t)(row0 + 2 * c) * n + x] = v.x;
         h[(size_t)(row0 + 2 * c + 1) * n + x] = v.y;
@@ -801,8 +817,12 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Geo g, const int* __r
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int Nq = tstart[g.ntiles];
     const int n = g.n;
-    const size_t n3 = (size_t)n * n * n;
-    const int P2 = 2 * g.p, ntap = P2 * P2 * P2;
+    const size_t n3 = (size_t)n * n * n;   // n <= 1024: one grid's offsets fit an int
+    const R* __restrict__ h0 = h;
+    const R* __restrict__ h1 = h + n3;
+    const R* __restrict__ h2 = h + 2 * n3;
+    const int P2 = 2 * g.p;
+    const float iP2 = 1.0f / (float)P2;
     const R rb = (R)g.rb, wn = (R)g.wnorm;
     const R pref = (R)g.pref;
     for (int s = blockIdx.x * NW + warp; s < Nq; s += gridDim.x * NW) {
@@ -816,22 +836,27 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Geo g, const int* __r
             for (int t = 0; t < 3; ++t) {
                 int l = base[t] - g.p + 1 + lane;
                 l = l < 0 ? l + n : (l >= n ? l - n : l);
-                lix[warp][t][lane] = l;
+                lix[warp][t][lane] = t == 2 ? l * n * n : l;
                 const R d = fr[t] + (R)(g.p - 1 - lane);
                 wts[warp][t][lane] = wn * r_exp(-d * d * rb);
             }
         }
         __syncwarp();
         R ax = 0, ay = 0, az = 0;
-        for (int tap = lane; tap < ntap; tap += 32) {
-            const int a = tap % P2;
-            const int r2 = tap / P2;
-            const int b = r2 % P2, c = r2 / P2;
-            const R w = wts[warp][0][a] * wts[warp][1][b] * wts[warp][2][c];
-            const size_t off = ((size_t)lix[warp][2][c] * n + lix[warp][1][b]) * n + lix[warp][0][a];
-            ax += w * h[off];
-            ay += w * h[n3 + off];
-            az += w * h[2 * n3 + off];
+        // lanes over the (x, y) taps, a loop over z; ab -> (a, b) by a float
+        // reciprocal (ab < 256, so the quotient of ab + 1/2 is 1/32 from an integer)
+        for (int ab = lane; ab < P2 * P2; ab += 32) {
+            const int b = (int)(((float)ab + 0.5f) * iP2);
+            const int a = ab - b * P2;
+            const R wab = wts[warp][0][a] * wts[warp][1][b];
+            const int rowo = lix[warp][1][b] * n + lix[warp][0][a];
+            for (int c = 0; c < P2; ++c) {
+                const R w = wab * wts[warp][2][c];
+                const int off = lix[warp][2][c] + rowo;   // z index pre-scaled by n^2
+                ax += w * h0[off];
+                ay += w * h1[off];
+                az += w * h2[off];
+            }
         }
         ax = warp_sum_r(ax);
         ay = warp_sum_r(ay);
@@ -1152,229 +1177,290 @@ __device__ __forceinline__ R dpd_theta(uint64_t seed, uint64_t step, int i, int 
 // DPD pair forces (Eq. 2-7, R_c = 1) + bonds (Sec. 2), added into F (which
 // the caller zeroes): F[i] += F^C + F^D + F^R/sqrt(dt) + F^S. One CTA per B^3
 // block of cells; the beads of the (B+2)^3 halo cells are staged in shared
-// memory with coalesced loads. One warp per central cell sweeps the cell's
-// forward half shell (the cell itself with j > i, and the 13 neighbouring
-// cells lexicographically after it), so every pair is evaluated once
-// (Newton's third law; theta_ij is symmetric). Accepted pairs go to a
-// per-warp queue and the pair arithmetic (Philox draw, weights, dissipation)
-// runs on full warps; +f and -f accumulate in a shared-memory force array
-// over the staged beads, which is added to F once per block.
+// memory with coalesced loads, in halo-cell order. One warp per central cell
+// sweeps the cell's forward half shell (the cell itself with j > i, and the
+// 13 neighbouring cells lexicographically after it), so every pair is
+// evaluated once (Newton's third law; theta_ij is symmetric). In the staged
+// copy the half shell is 5 contiguous runs of slots (own cell + next cell,
+// the row (0,+1,*), the rows (+1,*,*)) and "forward" is just slot_j > slot_i.
+// Each lane takes one candidate j and loops over the cell's beads i; accepted
+// pairs go to a per-warp queue kept across the warp's cells, and the pair arithmetic
+// (Philox draw, weights, dissipation) runs on full warps. -f goes to j with
+// one shared-memory atomic per pair; the +f of a run of pairs with the same
+// i is summed in the warp first (queue runs are contiguous in i), then added
+// once. The staged force array is added to F once per block. The harmonic
+// bonds run as one thread per bond into F.
+//
+// FP64: the cutoff test r^2 < 1 is taken on a float copy of the staged
+// positions first and redone in double only inside a band around 1 (and
+// near 0) that covers the float error, so the decision is the double one.
 constexpr int kDpdThreads = 256;
-constexpr int kDpdCap = 1024;    // staged beads
-constexpr int kDpdCand = 384;    // candidate map entries per warp
+constexpr int kDpdCap = 896;     // staged beads
 constexpr int kDpdMaxB = 4;      // cells per block edge
+constexpr int kDpdSegU = 14;     // unstaged half shell: single cells
 
+template <typename R>
+constexpr int dpd_smem_bytes() {
+    return 2 * kDpdCap * (int)sizeof(typename V4<R>::T) + 3 * kDpdCap * (int)sizeof(R) +
+           (sizeof(R) == 8 ? kDpdCap * (int)sizeof(float4) : 0) + (kDpdThreads / 32) * 64 * 8;
+}
+
+// One warp-wide batch of up to 32 queued pairs (valid lanes), all lanes call.
 template <typename R, typename V, bool STAGED>
-__device__ __forceinline__ void dpd_pair(const int2 e, const V* __restrict__ P, const V* __restrict__ Pv,
-                                         R* fh, R* __restrict__ F, const R* __restrict__ atab, int ntypes, R L,
-                                         R hL, R gam, R sig, R rdt, uint64_t seed, uint64_t step, R& ec) {
-    const V pi = P[e.x], vi = Pv[e.x];
-    const V pj = P[e.y], vj = Pv[e.y];
+__device__ __forceinline__ void dpd_pairs(const bool valid, const int2 e, const V* __restrict__ P,
+                                          const V* __restrict__ Pv, R* fh, R* __restrict__ F,
+                                          const R* __restrict__ atab, int ntypes, R L, R hL, R gam, R sig, R rdt,
+                                          uint64_t seed, uint64_t step, R& ec) {
+    const int lane = threadIdx.x & 31;
+    R fx = 0, fy = 0, fz = 0;
+    int key = -1, oi = 0;
+    if (valid) {
+        const V pi = P[e.x], vi = Pv[e.x];
+        const V pj = P[e.y], vj = Pv[e.y];
+        const R rx = min_image(pi.x, pj.x, L, hL);
+        const R ry = min_image(pi.y, pj.y, L, hL);
+        const R rz = min_image(pi.z, pj.z, L, hL);
+        const R r2 = dist2(rx, ry, rz);
+        const R ir = r_rsqrt(r2);
+        const R r = r2 * ir;
+        const R w = (R)1 - r;
+        const int i = real_as_int(pi.w), j = real_as_int(pj.w);
+        const int ti = real_as_int(vi.w), tj = real_as_int(vj.w);
+        const R a = atab[ti * ntypes + tj];
+        const R vr = ((vi.x - vj.x) * rx + (vi.y - vj.y) * ry + (vi.z - vj.z) * rz) * ir;
+        const R th = dpd_theta<R>(seed, step, i, j);
+        const R fm = (a * w - gam * w * w * vr + sig * w * th * rdt) * ir;
+        fx = fm * rx;
+        fy = fm * ry;
+        fz = fm * rz;
+        if (STAGED) {
+            atomicAdd(&fh[3 * e.y], -fx);
+            atomicAdd(&fh[3 * e.y + 1], -fy);
+            atomicAdd(&fh[3 * e.y + 2], -fz);
+        } else {
+            atomicAdd(&F[3 * j], -fx);
+            atomicAdd(&F[3 * j + 1], -fy);
+            atomicAdd(&F[3 * j + 2], -fz);
+        }
+        ec += (R)0.5 * a * w * w;
+        key = e.x;
+        oi = i;
+    }
+    // runs of equal i: sum each run into its first lane (segmented suffix sums)
+    const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+    const bool head = lane == 0 || prev != key;
+    const unsigned heads = __ballot_sync(0xffffffffu, head);
+    const unsigned after = lane == 31 ? 0u : heads & (0xffffffffu << (lane + 1));
+    const int end = after ? __ffs(after) - 1 : 32;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const R ax = __shfl_down_sync(0xffffffffu, fx, o);
+        const R ay = __shfl_down_sync(0xffffffffu, fy, o);
+        const R az = __shfl_down_sync(0xffffffffu, fz, o);
+        if (lane + o < end) {
+            fx += ax;
+            fy += ay;
+            fz += az;
+        }
+    }
+    if (head && key >= 0) {
+        if (STAGED) {
+            atomicAdd(&fh[3 * key], fx);
+            atomicAdd(&fh[3 * key + 1], fy);
+            atomicAdd(&fh[3 * key + 2], fz);
+        } else {
+            atomicAdd(&F[3 * oi], fx);
+            atomicAdd(&F[3 * oi + 1], fy);
+            atomicAdd(&F[3 * oi + 2], fz);
+        }
+    }
+}
+
+// The exact cutoff decision 0 < r^2 < 1 in the working precision.
+template <typename R, typename V>
+__device__ __forceinline__ bool dpd_within(const V& pi, const V& pj, R L, R hL) {
     const R rx = min_image(pi.x, pj.x, L, hL);
     const R ry = min_image(pi.y, pj.y, L, hL);
     const R rz = min_image(pi.z, pj.z, L, hL);
     const R r2 = dist2(rx, ry, rz);
-    const R ir = r_rsqrt(r2);
-    const R r = r2 * ir;
-    const R w = (R)1 - r;
-    const int i = real_as_int(pi.w), j = real_as_int(pj.w);
-    const int ti = real_as_int(vi.w), tj = real_as_int(vj.w);
-    const R a = atab[ti * ntypes + tj];
-    const R vr = ((vi.x - vj.x) * rx + (vi.y - vj.y) * ry + (vi.z - vj.z) * rz) * ir;
-    const R th = dpd_theta<R>(seed, step, i, j);
-    const R fm = (a * w - gam * w * w * vr + sig * w * th * rdt) * ir;
-    const R fx = fm * rx, fy = fm * ry, fz = fm * rz;
-    if (STAGED) {
-        atomicAdd(&fh[3 * e.x], fx);
-        atomicAdd(&fh[3 * e.x + 1], fy);
-        atomicAdd(&fh[3 * e.x + 2], fz);
-        atomicAdd(&fh[3 * e.y], -fx);
-        atomicAdd(&fh[3 * e.y + 1], -fy);
-        atomicAdd(&fh[3 * e.y + 2], -fz);
-    } else {
-        atomicAdd(&F[3 * i], fx);
-        atomicAdd(&F[3 * i + 1], fy);
-        atomicAdd(&F[3 * i + 2], fz);
-        atomicAdd(&F[3 * j], -fx);
-        atomicAdd(&F[3 * j + 1], -fy);
-        atomicAdd(&F[3 * j + 2], -fz);
-    }
-    ec += (R)0.5 * a * w * w;
+    return r2 < (R)1 && r2 > (R)0;
 }
 
+struct DpdBand {   // float pre-test of the FP64 path: r2f > hi: out; lo0 < r2f < lo: in; else exact
+    float L, hL, lo0, lo, hi;
+};
+
 // All central cells of one block, one warp per cell. STAGED: P/Pv are the
-// shared-memory copies and cell starts are hoff; else global arrays and gst.
+// shared-memory copies (Pf the float copy of P when R is double) and slots
+// follow hoff; else global sorted arrays and slots follow gst.
 template <typename R, bool STAGED>
 __device__ __forceinline__ void dpd_cells(const DpdDev& d, int H, int B3, const int* chalo, const int* hoff,
                                           const int* gst, const typename V4<R>::T* __restrict__ P,
-                                          const typename V4<R>::T* __restrict__ Pv, R* fh, int2* queue, int* cand,
-                                          const R* __restrict__ atab, const R* __restrict__ pos,
-                                          const int* __restrict__ bptr, const int* __restrict__ blist,
-                                          uint64_t step, R* __restrict__ F, R& ec, R& eb) {
+                                          const typename V4<R>::T* __restrict__ Pv, const float4* Pf,
+                                          const DpdBand band, R* fh, int2* queue, const R* __restrict__ atab,
+                                          uint64_t step, R* __restrict__ F, R& ec) {
     using V = typename V4<R>::T;
     constexpr int NW = kDpdThreads / 32;
+    constexpr bool PRE = STAGED && sizeof(R) == 8;
+    constexpr int nseg = STAGED ? 5 : kDpdSegU;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const R L = (R)d.L, hL = (R)(0.5 * d.L);
     const R gam = (R)d.gamma, sig = (R)d.sigma, rdt = (R)d.rdt;
-    const R Kb = (R)d.K_bond, r0b = (R)d.r0_bond;
-    // forward half shell: the cell itself, (0,0,+1), the row (0,+1,*), the rows (+1,*,*).
-    // Staged cells of a row are contiguous, so it takes 6 segments; else 14 single cells.
-    constexpr int nseg = STAGED ? 6 : 14;
+    int cnt = 0;   // queued pairs of this warp, carried across its cells
     for (int cc = warp; cc < B3; cc += NW) {
         const int h = chalo[cc];
         if (h < 0) continue;
         const int cb = STAGED ? hoff[h] : gst[h];
         const int nself = hoff[h + 1] - hoff[h];
         if (nself == 0) continue;
-        int cnt = 0;
-        int seg = 0, soff = 0;
-        bool more = true;
-        while (more) {
-            int mc = 0;
-            while (seg < nseg && mc < kDpdCand) {
-                int sbase, slen;
-                if (STAGED) {
-                    if (seg == 0) { sbase = cb; slen = nself; }
-                    else if (seg == 1) { sbase = hoff[h + 1]; slen = hoff[h + 2] - sbase; }
-                    else {
-                        const int hr = seg == 2 ? h + H - 1 : h + H * H + (seg - 4) * H - 1;
-                        sbase = hoff[hr];
-                        slen = hoff[hr + 3] - sbase;
-                    }
-                } else {
-                    int hc;
-                    if (seg == 0) hc = h;
-                    else if (seg == 1) hc = h + 1;
-                    else if (seg < 5) hc = h + H + (seg - 3);
-                    else hc = h + H * H + ((seg - 5) / 3 - 1) * H + ((seg - 5) % 3 - 1);
-                    sbase = gst[hc];
-                    slen = hoff[hc + 1] - hoff[hc];
-                }
-                const int take = min(slen - soff, kDpdCand - mc);
-                for (int t = lane; t < take; t += 32) cand[mc + t] = sbase + soff + t;
-                mc += take;
-                soff += take;
-                if (soff == slen) {
-                    ++seg;
-                    soff = 0;
-                }
-            }
-            __syncwarp();
-            more = seg < nseg;
-            // sweep: every bead of the cell against the map; one extra step drains the queue
-            const int nj = (mc + 31) >> 5;
-            const int steps = nself * nj + (more ? 0 : 1);
-            int ii = 0, jb = 0;
-            for (int it = 0; it < steps; ++it) {
-                const bool last = it == nself * nj;
-                if (!last) {
-                    const int me = cb + ii;
-                    const int jf = jb + lane;
-                    bool hit = false;
-                    int j = 0;
-                    if (jf < mc) {
-                        j = cand[jf];
-                        // within the cell itself only j > i (each pair once)
-                        const bool ok = (j >= cb && j < cb + nself) ? j > me : true;
-                        if (ok) {
-                            const V pi = P[me];
-                            const V pj = P[j];
-                            const R rx = min_image(pi.x, pj.x, L, hL);
-                            const R ry = min_image(pi.y, pj.y, L, hL);
-                            const R rz = min_image(pi.z, pj.z, L, hL);
-                            const R r2 = dist2(rx, ry, rz);
-                            hit = r2 < (R)1 && r2 > (R)0;
-                        }
-                    }
-                    const unsigned m = __ballot_sync(0xffffffffu, hit);
-                    if (hit) queue[cnt + __popc(m & ((1u << lane) - 1u))] = make_int2(me, j);
-                    cnt += __popc(m);
-                    jb += 32;
-                    if (jb >= mc) {
-                        jb = 0;
-                        ++ii;
-                    }
-                }
-                if (cnt >= 32 || (last && cnt > 0)) {
-                    const int m = min(cnt, 32);
-                    __syncwarp();
-                    if (lane < m)
-                        dpd_pair<R, V, STAGED>(queue[lane], P, Pv, fh, F, atab, d.ntypes, L, hL, gam, sig, rdt,
-                                               d.seed, step, ec);
-                    __syncwarp();
-                    if (lane < cnt - m) queue[lane] = queue[m + lane];
-                    __syncwarp();
-                    cnt -= m;
-                }
+        // lane s < nseg: run s of the half shell as (start slot, length)
+        int sst = 0, sln = 0;
+        if (lane < nseg) {
+            if (STAGED) {
+                int h0, h1;
+                if (lane == 0) { h0 = h; h1 = h + 2; }
+                else if (lane == 1) { h0 = h + H - 1; h1 = h0 + 3; }
+                else { h0 = h + H * H + (lane - 3) * H - 1; h1 = h0 + 3; }
+                sst = hoff[h0];
+                sln = hoff[h1] - sst;
+            } else {
+                int hc;
+                if (lane == 0) hc = h;
+                else if (lane == 1) hc = h + 1;
+                else if (lane < 5) hc = h + H + (lane - 3);
+                else hc = h + H * H + ((lane - 5) / 3 - 1) * H + ((lane - 5) % 3 - 1);
+                sst = gst[hc];
+                sln = hoff[hc + 1] - hoff[hc];
             }
         }
-        // harmonic bonds of the cell's beads (each bond is seen from both ends)
-        for (int k0 = 0; k0 < nself; k0 += 32) {
-            const int k = k0 + lane;
-            if (k < nself) {
-                const int slot = cb + k;
-                const int i = real_as_int(P[slot].w);
-                R fx = 0, fy = 0, fz = 0;
-                for (int kb = bptr[i]; kb < bptr[i + 1]; ++kb) {
-                    const int j = blist[kb];
-                    R dd[3];
+        int x = sln;   // inclusive prefix of the run lengths
 #pragma unroll
-                    for (int t = 0; t < 3; ++t) {
-                        const R xi = wrap_r(pos[3 * i + t], d.L, d.xmaxf);
-                        const R xj = wrap_r(pos[3 * j + t], d.L, d.xmaxf);
-                        dd[t] = min_image(xi, xj, L, hL);
-                    }
-                    const R r = r_sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
-                    eb += (R)0.25 * Kb * (r - r0b) * (r - r0b);
-                    if (r > (R)0) {
-                        const R fm = -Kb * (r - r0b) / r;
-                        fx += fm * dd[0];
-                        fy += fm * dd[1];
-                        fz += fm * dd[2];
+        for (int o = 1; o < 16; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        const int soff = x - sln;          // run s starts at map position soff
+        const int delta = sst - soff;      // slot = map position + delta
+        const int mc = __shfl_sync(0xffffffffu, x, nseg - 1);
+        int bnd[4];                        // staged: run boundaries 1..4 in map positions
+        if constexpr (STAGED) {
+#pragma unroll
+            for (int s = 1; s < nseg; ++s) bnd[s - 1] = __shfl_sync(0xffffffffu, soff, s);
+        }
+        // lanes over the map (one candidate j per lane per chunk), loop over the
+        // cell's beads i (broadcast loads); queue runs are then runs of one i
+        for (int jb = 0; jb < mc; jb += 32) {
+            const int jf = jb + lane;
+            int s = 0;
+            if constexpr (STAGED) {
+#pragma unroll
+                for (int k = 0; k < nseg - 1; ++k) s += jf >= bnd[k] ? 1 : 0;
+            } else {
+                for (int k = 1; k < nseg; ++k) s += jf >= __shfl_sync(0xffffffffu, soff, k) ? 1 : 0;
+            }
+            const int j = jf + __shfl_sync(0xffffffffu, delta, s);
+            const bool vj = jf < mc;
+            V pj;
+            float4 pjf;
+            if (vj) {
+                pj = P[j];
+                if constexpr (PRE) pjf = Pf[j];
+            }
+            for (int ii = 0; ii < nself; ++ii) {
+                const int me = cb + ii;
+                // forward only: staged slots are in halo order, so j > i; unstaged,
+                // only the cell itself (run 0) needs it
+                bool hit = false;
+                if (vj && (STAGED ? j > me : (s != 0 || j > me))) {
+                    if constexpr (PRE) {
+                        const float4 a = Pf[me];
+                        const float rx = min_image(a.x, pjf.x, band.L, band.hL);
+                        const float ry = min_image(a.y, pjf.y, band.L, band.hL);
+                        const float rz = min_image(a.z, pjf.z, band.L, band.hL);
+                        const float r2 = dist2(rx, ry, rz);
+                        if (r2 <= band.hi) hit = (r2 < band.lo && r2 > band.lo0) || dpd_within<R, V>(P[me], pj, L, hL);
+                    } else {
+                        hit = dpd_within<R, V>(P[me], pj, L, hL);
                     }
                 }
-                if (fx != (R)0 || fy != (R)0 || fz != (R)0) {
-                    if (STAGED) {
-                        atomicAdd(&fh[3 * slot], fx);
-                        atomicAdd(&fh[3 * slot + 1], fy);
-                        atomicAdd(&fh[3 * slot + 2], fz);
-                    } else {
-                        atomicAdd(&F[3 * i], fx);
-                        atomicAdd(&F[3 * i + 1], fy);
-                        atomicAdd(&F[3 * i + 2], fz);
-                    }
+                const unsigned m = __ballot_sync(0xffffffffu, hit);
+                if (hit) queue[cnt + __popc(m & ((1u << lane) - 1u))] = make_int2(me, j);
+                cnt += __popc(m);
+                if (cnt >= 32) {
+                    __syncwarp();
+                    dpd_pairs<R, V, STAGED>(true, queue[lane], P, Pv, fh, F, atab, d.ntypes, L, hL, gam, sig, rdt,
+                                            d.seed, step, ec);
+                    __syncwarp();
+                    if (lane < cnt - 32) queue[lane] = queue[32 + lane];
+                    __syncwarp();
+                    cnt -= 32;
                 }
             }
         }
-        __syncwarp();
     }
+    __syncwarp();
+    if (cnt > 0)
+        dpd_pairs<R, V, STAGED>(lane < cnt, queue[lane], P, Pv, fh, F, atab, d.ntypes, L, hL, gam, sig, rdt, d.seed,
+                                step, ec);
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kDpdThreads) k_dpd(DpdDev d, int B, const typename V4<R>::T* __restrict__ sp,
-                                                     const typename V4<R>::T* __restrict__ sv,
-                                                     const int* __restrict__ cstart, const R* __restrict__ atab,
-                                                     const R* __restrict__ pos, const int* __restrict__ bptr,
-                                                     const int* __restrict__ blist,
-                                                     const uint64_t* __restrict__ stepp, R* __restrict__ F,
-                                                     double* __restrict__ dpart) {
+__global__ void __launch_bounds__(kDpdThreads, sizeof(R) == 4 ? 4 : 2)
+    k_dpd(DpdDev d, int B, const typename V4<R>::T* __restrict__ sp, const typename V4<R>::T* __restrict__ sv,
+          const int* __restrict__ cstart, const R* __restrict__ atab, const R* __restrict__ pos,
+          const int* __restrict__ bnd, const uint64_t* __restrict__ stepp, R* __restrict__ F,
+          double* __restrict__ dpart) {
     using V = typename V4<R>::T;
+    constexpr bool F64 = sizeof(R) == 8;
     extern __shared__ __align__(16) unsigned char smraw[];
     V* spos = reinterpret_cast<V*>(smraw);                                  // [kDpdCap]
     V* svel = spos + kDpdCap;                                               // [kDpdCap]
-    R* fh = reinterpret_cast<R*>(svel + kDpdCap);                           // [kDpdCap][3]
+    float4* spf = reinterpret_cast<float4*>(svel + kDpdCap);                // [kDpdCap] (FP64 only)
+    R* fh = reinterpret_cast<R*>(spf + (F64 ? kDpdCap : 0));                // [kDpdCap][3]
     int2* queues = reinterpret_cast<int2*>(fh + 3 * kDpdCap);               // [NW][64]
-    int* cands = reinterpret_cast<int*>(queues + (kDpdThreads / 32) * 64);  // [NW][kDpdCand]
     constexpr int HMAX = (kDpdMaxB + 2) * (kDpdMaxB + 2) * (kDpdMaxB + 2);
     __shared__ int hoff[HMAX + 1], gst[HMAX];
     __shared__ int chalo[kDpdMaxB * kDpdMaxB * kDpdMaxB];
     const uint64_t step = *stepp;
     const int ncd = d.ncd, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     int2* queue = queues + warp * 64;
-    int* cand = cands + warp * kDpdCand;
     const int H = B + 2, H3 = H * H * H, B3 = B * B * B;
     const int nblk = (ncd + B - 1) / B;
+    const R L = (R)d.L, hL = (R)(0.5 * d.L);
     R ec = 0, eb = 0;
+    // harmonic bonds (Sec. 2): one thread per bond, +f to i and -f to j
+    {
+        const R Kb = (R)d.K_bond, r0b = (R)d.r0_bond;
+        for (int k = blockIdx.x * blockDim.x + tid; k < d.nbonds; k += gridDim.x * blockDim.x) {
+            const int i = bnd[2 * k], j = bnd[2 * k + 1];
+            R dd[3];
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                const R xi = wrap_r(pos[3 * i + t], d.L, d.xmaxf);
+                const R xj = wrap_r(pos[3 * j + t], d.L, d.xmaxf);
+                dd[t] = min_image(xi, xj, L, hL);
+            }
+            const R r = r_sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+            eb += (R)0.5 * Kb * (r - r0b) * (r - r0b);
+            if (r > (R)0) {
+                const R fm = -Kb * (r - r0b) / r;
+#pragma unroll
+                for (int t = 0; t < 3; ++t) {
+                    atomicAdd(&F[3 * i + t], fm * dd[t]);
+                    atomicAdd(&F[3 * j + t], -fm * dd[t]);
+                }
+            }
+        }
+    }
+    // float band of the FP64 cutoff test: float positions and L carry at most
+    // L 2^-24 each, so |r2f - r2| <= 1.3e-6 L + 3e-7 for r2 near 1
+    DpdBand band;
+    band.L = (float)d.L;
+    band.hL = (float)(0.5 * d.L);
+    const float eps = 1e-4f + 4e-6f * (float)d.L;
+    band.lo0 = eps;
+    band.lo = 1.0f - eps;
+    band.hi = 1.0f + eps;
     for (int blk = blockIdx.x; blk < nblk * nblk * nblk; blk += gridDim.x) {
         const int bx = blk % nblk, by = (blk / nblk) % nblk, bz = blk / (nblk * nblk);
         const int c0x = bx * B, c0y = by * B, c0z = bz * B;
@@ -1428,18 +1514,18 @@ __global__ void __launch_bounds__(kDpdThreads) k_dpd(DpdDev d, int B, const type
                     if (hoff[mid] <= f) lo = mid; else hi = mid;
                 }
                 const int j = gst[lo] + f - hoff[lo];
-                spos[f] = sp[j];
+                const V p = sp[j];
+                spos[f] = p;
                 svel[f] = sv[j];
+                if (F64) spf[f] = make_float4((float)p.x, (float)p.y, (float)p.z, 0.f);
             }
             for (int k = tid; k < 3 * total; k += blockDim.x) fh[k] = (R)0;
         }
         __syncthreads();
         if (staged)
-            dpd_cells<R, true>(d, H, B3, chalo, hoff, gst, spos, svel, fh, queue, cand, atab, pos, bptr, blist,
-                               step, F, ec, eb);
+            dpd_cells<R, true>(d, H, B3, chalo, hoff, gst, spos, svel, spf, band, fh, queue, atab, step, F, ec);
         else
-            dpd_cells<R, false>(d, H, B3, chalo, hoff, gst, sp, sv, fh, queue, cand, atab, pos, bptr, blist, step,
-                                F, ec, eb);
+            dpd_cells<R, false>(d, H, B3, chalo, hoff, gst, sp, sv, spf, band, fh, queue, atab, step, F, ec);
         __syncthreads();
         if (staged) {   // add the block's contributions to F
             for (int k = tid; k < 3 * total; k += blockDim.x) {

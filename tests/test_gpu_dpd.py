@@ -142,3 +142,39 @@ def test_full_size_polyelectrolyte_sampled(enuf, prec, tol):
     assert _rel(F[sample].astype(np.float64), Fr) < tol
     sysm.close()
     plan.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 1e-5)])
+def test_dense_blob_uses_both_block_paths(enuf, prec, tol):
+    """A blob of 600 extra beads in a 2^3 corner region: every cell block whose
+    halo holds it has more beads than the kernel stages in shared memory and
+    takes the global-memory path, the rest stay staged; forces and the DPD
+    energies still match the oracle."""
+    s = _system()
+    rng = np.random.default_rng(11)
+    nb = 600
+    pos = np.concatenate([s.pos, rng.uniform(1.0, 3.0, size=(nb, 3))])
+    vel = np.concatenate([s.vel, rng.normal(0.0, 1.0, size=(nb, 3))])
+    types = np.concatenate([s.types, np.zeros(nb, np.int32)]).astype(np.int32)
+    qq = np.concatenate([s.q, np.zeros(nb)])
+    cast = (lambda a: np.asarray(a, np.float32).astype(np.float64)) if prec == "fp32" else np.asarray
+    pos, vel, qq = cast(pos), cast(vel), cast(qq)
+    # the busiest 6^3-cell halo (4^3 cell blocks of edge L/ncd) holds more than 896 beads
+    ncd = int(np.floor(s.L / (1.0 + 1e-5)))
+    assert len(pos) > 896 and nb > 896 - 216 * 3
+    dp = W.dpd_params(5)
+    P = dict(L=s.L, M=s.M, **s.params)
+    plan = enuf.Plan(enuf.make_params(prec=prec, **P), len(pos))
+    sysm = enuf.DpdSystem(plan, dp["a"], dp["gamma"], dp["sigma"], dp["dt"], pos, vel, types, qq, s.bonds,
+                          lambda_vv=dp["lambda_vv"], K_bond=dp["K_bond"], r0_bond=dp["r0_bond"], seed=dp["seed"])
+    Po = orc.EwaldParams(fp32_cut=1 if prec == "fp32" else 0, **P)
+    Do = orc.DpdParams(**dp)
+    _, _, F, _ = sysm.get_state()
+    E = sysm.step(0, want_energy=True)
+    Fr, Er = orc.total_forces(Po, Do, pos, vel, types, qq, s.bonds, step=0)
+    assert ncd >= 3
+    assert _rel(F.astype(np.float64), Fr) < tol
+    assert abs(E[4] - Er[4]) < (1e-10 if prec == "fp64" else 1e-5) * abs(Er[4])
+    assert abs(E[5] - Er[5]) < (1e-10 if prec == "fp64" else 1e-5) * max(abs(Er[5]), 1.0)
+    sysm.close()
+    plan.close()

@@ -144,3 +144,87 @@ def test_spherical_mask_converges(orc, small):
     P.kmask = 0
     _, Ec = orc.recip_direct(P, pos, q)
     assert Ed[0] != Ec[0]
+
+
+# --- analytic-gradient forces (one inverse transform instead of three) -------
+
+
+def _interior_beads(s, pos, P, k=4, margin=0.2):
+    """Beads whose grid coordinate n x / L is at least `margin` from an integer
+    in every dimension, so that a small move keeps the same 2p taps."""
+    u = np.mod(pos, s.L) * P.ng / s.L
+    fr = u - np.floor(u)
+    ok = np.all((fr > margin) & (fr < 1 - margin), axis=1)
+    return np.nonzero(ok)[0][:k]
+
+
+@pytest.mark.parametrize("p", [2, 4, 6])
+def test_gradient_mode_is_minus_gradient_of_the_nfft_energy(orc, small, p):
+    """The gradient-mode force is the exact derivative of the oracle's own NFFT
+    energy (which the convergence and Madelung tests pin): central differences
+    of E_K in every coordinate of a few beads reproduce it."""
+    s, pos, q = small
+    P = _params(orc, s, p=p, deriv=1)
+    F, EW, _, _ = orc.recip_enuf(P, pos, q)
+    beads = _interior_beads(s, pos, P)
+    assert len(beads) >= 3
+    h = 1e-5
+    fscale = np.abs(F).max()
+    for i in beads:
+        for a in range(3):
+            xp, xm = pos.copy(), pos.copy()
+            xp[i, a] += h
+            xm[i, a] -= h
+            Ep = orc.recip_enuf(P, xp, q)[1][0]
+            Em = orc.recip_enuf(P, xm, q)[1][0]
+            fd = -(Ep - Em) / (2 * h)
+            assert abs(fd - F[i, a]) < 2e-7 * fscale, (p, i, a, fd, F[i, a])
+
+
+@pytest.mark.parametrize("M", [16, 32])
+def test_gradient_mode_converges_to_direct_ewald(orc, small, M):
+    s, pos, q = small
+    P = _params(orc, s, M=M, deriv=1)
+    Fd, _ = orc.recip_direct(P, pos, q)
+    eF = []
+    for p in range(1, 9):
+        P.p = p
+        Fe, _, _, _ = orc.recip_enuf(P, pos, q)
+        eF.append(math.sqrt(((Fe - Fd) ** 2).sum() / (Fd ** 2).sum()))
+    eF = np.array(eF)
+    # same exp(-2 pi p/3) envelope as the ik forces, with a larger constant: the
+    # derivative of the window carries the factor 2 d / b (measured at M = 32:
+    # eF / envelope = 14, 10, 7.0, 4.6, 3.2, 2.2, 1.5, 1.1 for p = 1..8)
+    envelope = np.exp(-2 * math.pi * np.arange(1, 9) / 3)
+    assert np.all(eF[1:] < eF[:-1] / 3)
+    assert np.all(eF < 16.0 * envelope)
+    assert eF[-1] < 1e-7
+
+
+def test_gradient_mode_field_matches_library_fft(orc, small):
+    """The one real field of the gradient mode, rebuilt from the oracle's own
+    spread grid with numpy's FFT."""
+    s, pos, q = small
+    P = _params(orc, s, M=16, p=4, deriv=1)
+    _, EW, grid, h = orc.recip_enuf(P, pos, q, want_grid=True, want_h=True)
+    n = grid.shape[0]
+    nc = P.M // 2 - 1
+    b = 2.0 * P.sigma_s * P.p / ((2.0 * P.sigma_s - 1.0) * math.pi)
+    Fh = np.fft.fftn(grid.transpose(2, 1, 0))
+    k = np.fft.fftfreq(n, 1.0 / n)
+    KX, KY, KZ = np.meshgrid(k, k, k, indexing="ij")
+    mask = (np.abs(KX) <= nc) & (np.abs(KY) <= nc) & (np.abs(KZ) <= nc) & (KX ** 2 + KY ** 2 + KZ ** 2 > 0)
+    K2 = np.where(mask, KX ** 2 + KY ** 2 + KZ ** 2, 1.0)
+    c = np.exp(-b * (math.pi / n) ** 2 * (KX ** 2 + KY ** 2 + KZ ** 2))
+    f = np.where(mask, np.exp(-math.pi ** 2 * K2 / (P.alpha * P.L) ** 2) / K2, 0.0)
+    field = np.fft.ifftn(f * Fh / c ** 2) * n ** 3
+    assert np.abs(field.imag).max() < 1e-10 * np.abs(field.real).max()
+    assert np.abs(h[0] - field.real.transpose(2, 1, 0)).max() < 1e-11 * np.abs(field.real).max()
+
+
+def test_gradient_and_ik_forces_agree_at_large_p(orc, small):
+    s, pos, q = small
+    Fi, Ei, _, _ = orc.recip_enuf(_params(orc, s, p=8), pos, q)
+    Fg, Eg, _, _ = orc.recip_enuf(_params(orc, s, p=8, deriv=1), pos, q)
+    assert Ei[0] == Eg[0] and Ei[1] == Eg[1]
+    assert math.sqrt(((Fg - Fi) ** 2).sum() / (Fi ** 2).sum()) < 1e-7
