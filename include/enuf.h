@@ -71,7 +71,12 @@ typedef struct {
     int    kmask;     /* 0: cubic mode set |k_t| <= n_c; 1: spherical |k| <= n_c */
     int    prec;      /* enuf_precision */
     int    tile;      /* spreading tile edge in grid points; 0 = automatic */
-    int    reserved[6];
+    int    deriv;     /* reciprocal forces: 0 = ik-differentiation, three fields
+                         -i k_a D F (Eq. 24-25); 1 = gradient of the window: one
+                         field h = D F and F_i = -(kappa q_i n/(pi L^2)) sum_l
+                         grad Psi(n x_i - l) h(l), the exact derivative of the NFFT
+                         energy (one inverse transform instead of three) */
+    int    reserved[5];
 } enuf_params;
 
 typedef struct enuf_plan_s* enuf_plan_t;
@@ -125,7 +130,8 @@ enuf_status enuf_energy_forces_host(enuf_plan_t plan, int n, const void* pos, co
 
 /* Copy an internal buffer of the last evaluation to host memory (tests):
  *   ENUF_BUF_GRID  : spread grid, real[n^3], index (z*n + y)*n + x        (Eq. 14, first half)
- *   ENUF_BUF_FIELD : the three conjugated-NFFT fields, real[3][n^3]      (Eq. 25 before gather)
+ *   ENUF_BUF_FIELD : the conjugated-NFFT fields before the gather: real[3][n^3]
+ *                    (deriv 0, Eq. 25) or the one field h, real[1][n^3] (deriv 1)
  * bytes must equal the buffer size. Synchronises the plan's stream. */
 enum { ENUF_BUF_GRID = 0, ENUF_BUF_FIELD = 1 };
 enuf_status enuf_debug_buffer(enuf_plan_t plan, int which, void* host, size_t bytes);

@@ -134,6 +134,7 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
     if (P.p < 1 || P.p > 8) return fail(plan, ENUF_ERR_INVALID, "p must be in [1, 8]");
     if (P.prec != ENUF_FP64 && P.prec != ENUF_FP32) return fail(plan, ENUF_ERR_INVALID, "bad precision");
     if (P.kmask != 0 && P.kmask != 1) return fail(plan, ENUF_ERR_INVALID, "kmask must be 0 or 1");
+    if (P.deriv != 0 && P.deriv != 1) return fail(plan, ENUF_ERR_INVALID, "deriv must be 0 or 1");
     const int M = P.M == 0 ? grid_rule(P.L) : P.M;
     if (M < 4 || (M & 1)) return fail(plan, ENUF_ERR_INVALID, "M must be even and >= 4 (got %d)", M);
     const int n = P.sigma_s * M;
@@ -185,6 +186,7 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
     g.chunk = std::min(16384, std::max(2048, (n_max + 63) / 64));
     g.nbin = std::max(1, (n_max + g.chunk - 1) / g.chunk);
     g.kmask = P.kmask;
+    g.nf = P.deriv ? 1 : 3;
     g.L = P.L;
     g.alpha = P.alpha;
     g.beta = P.beta;
@@ -198,8 +200,8 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
     FftShape fs{};
     const int budget = 64 * 1024;
     const int nc1 = g.nc + 1;
-    auto shape = [&](int total_lines, int nbuf, int& lines, int& threads, int& grid) {
-        const int cap = lines_for(n, nbuf, csz, budget, 64);
+    auto shape = [&](int total_lines, int nbuf, int& lines, int& threads, int& grid, int bud = 0) {
+        const int cap = lines_for(n, nbuf, csz, bud > 0 ? bud : budget, 64);
         lines = std::max(1, std::min(cap, (total_lines + 2 * kSMs - 1) / (2 * kSMs)));
         grid = (total_lines + lines - 1) / lines;
         threads = std::min(256, std::max(64, ((lines * n / 4 + 31) / 32) * 32));
@@ -208,17 +210,19 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
     shape(n * n / 2, 2, fs.lx, fs.tx, fs.grid_x);
     shape(n * nc1, 2, fs.ly, fs.ty, gyz);
     fs.grid_y_z = (n + fs.ly - 1) / fs.ly;
-    shape(nc1 * g.K, 3, fs.lz, fs.tz, fs.grid_z);
-    shape(3 * n * nc1, 2, fs.liy, fs.tiy, fs.grid_iy);
-    shape(3 * n * n / 2, 2, fs.lix, fs.tix, fs.grid_ix);
+    // z pass: forward lines (2 buffers) and the nf fields transformed together (2 nf)
+    shape(nc1 * g.K, 2 + 2 * g.nf, fs.lz, fs.tz, fs.grid_z, 96 * 1024);
+    fs.tz = std::min(256, std::max(fs.tz, ((g.nf * fs.lz * n / 4 + 31) / 32) * 32));
+    shape(g.nf * n * nc1, 2, fs.liy, fs.tiy, fs.grid_iy);
+    shape(g.nf * n * n / 2, 2, fs.lix, fs.tix, fs.grid_ix);
     fs.smem_x = (1 + 2 * fs.lx) * n * csz;
     fs.smem_y = (1 + 2 * fs.ly) * n * csz;
-    fs.smem_z = (1 + 3 * fs.lz) * n * csz;
+    fs.smem_z = (1 + (2 + 2 * g.nf) * fs.lz) * n * csz;
     fs.smem_iy = (1 + 2 * fs.liy) * n * csz;
     fs.smem_ix = (1 + 2 * fs.lix) * n * csz;
     g.ratio = (double)n / P.L;
     g.rb = 1.0 / g.b;
-    g.pref = P.kappa * 2.0 / (P.L * P.L);
+    g.pref = P.deriv ? -P.kappa * n / (M_PI * P.L * P.L) : P.kappa * 2.0 / (P.L * P.L);
     g.c2a = 2.0 * P.alpha / std::sqrt(M_PI);
     g.xmaxf = largest_float_below(P.L);
     g.c_self = -P.kappa * P.alpha / std::sqrt(M_PI);
@@ -253,8 +257,8 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
            o_cfrac = take(ncmp * 4 * esz), o_cbase = take(ncmp * 4),
            o_sq = take(nm * 4 * esz), o_sw = take(nm * 4 * esz), o_sb = take(nm * 4), o_grid = take(n3 * esz),
            o_s1 = take((size_t)n * nc1 * n * csz), o_s2 = take((size_t)nc1 * g.K * n * csz),
-           o_s3 = take((size_t)3 * n * nc1 * g.K * csz), o_s4 = take((size_t)3 * n * n * nc1 * csz),
-           o_h = take(3 * n3 * esz), o_tab = take(ntab * 8), o_tabv = take(ntab * 8), o_tabr = take(ntab * esz),
+           o_s3 = take((size_t)g.nf * n * nc1 * g.K * csz), o_s4 = take((size_t)g.nf * n * n * nc1 * csz),
+           o_h = take(g.nf * n3 * esz), o_tab = take(ntab * 8), o_tabv = take(ntab * 8), o_tabr = take(ntab * esz),
            o_tw = take((size_t)n * csz), o_part = take((size_t)npart * 8), o_E = take(16 * 8);
     if (bytes) *bytes = off;
     if (plan) {
@@ -556,7 +560,7 @@ enuf_status enuf_debug_buffer(enuf_plan_t plan, int which, void* host, size_t by
     const void* src = nullptr;
     size_t need = 0;
     if (which == ENUF_BUF_GRID) { src = plan->w.grid; need = n3 * plan->rsz; }
-    else if (which == ENUF_BUF_FIELD) { src = plan->w.h; need = 3 * n3 * plan->rsz; }
+    else if (which == ENUF_BUF_FIELD) { src = plan->w.h; need = (size_t)plan->g.nf * n3 * plan->rsz; }
     else return fail(plan, ENUF_ERR_INVALID, "unknown buffer %d", which);
     if (bytes != need) return fail(plan, ENUF_ERR_INVALID, "buffer needs %zu bytes, got %zu", need, bytes);
     CU(cudaStreamSynchronize(plan->stream));

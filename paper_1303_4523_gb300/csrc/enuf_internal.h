@@ -22,13 +22,13 @@ struct Geo {
     int nbin;     // blocks of the charged-bead binning
     int chunk;    // beads per binning block
     int kmask;
-    int pad0;
+    int nf;       // reciprocal force fields: 3 (ik-differentiation) or 1 (window gradient)
     double L, alpha, beta, kappa, rc;
     double b;      // Gaussian window parameter 2 sigma p / ((2 sigma - 1) pi)
     double wnorm;  // (pi b)^{-1/2}
     double ratio;  // n / L: grid coordinate u = x * ratio (one FP64 product)
     double rb;     // 1 / b
-    double pref;   // kappa * 2 / L^2 (Eq. 25 prefactor)
+    double pref;   // kappa * 2 / L^2 (Eq. 25 prefactor); gradient mode: -kappa n / (pi L^2)
     double c2a;    // 2 alpha / sqrt(pi)
     float xmaxf;   // largest float below L: float x is inside [0, L) iff 0 <= x <= xmaxf
     float rhi, rlo;  // n/L split into two floats (compensated float grid coordinate)

@@ -637,8 +637,10 @@ __global__ void __launch_bounds__(256) k_fft_y(Geo g, FftPlanDev fp, const typen
     }
 }
 
-// z pass: forward z; E += w D |F|^2, W += w D v |F|^2 (FP64, Kahan);
-// G_a = -i k_a D F (a = x, y, z); inverse z of each G_a; output spec3[a][z][kx][ky].
+// z pass: forward z; E += w D |F|^2, W += w D v |F|^2 (FP64, Kahan); the
+// fields G_a = -i k_a D F (a = x, y, z; Eq. 24) or, in gradient mode, the one
+// field G = D F; all fields of the CTA's lines inverse-transformed together;
+// output spec3[a][z][kx][ky].
 template <typename R>
 __global__ void __launch_bounds__(256) k_fft_z(Geo g, FftPlanDev fp, const typename Cx<R>::T* __restrict__ spec2,
                                               const typename Cx<R>::T* __restrict__ twg,
@@ -647,23 +649,21 @@ __global__ void __launch_bounds__(256) k_fft_z(Geo g, FftPlanDev fp, const typen
                                               double* __restrict__ epart, int LB) {
     using C = typename Cx<R>::T;
     extern __shared__ unsigned char smraw[];
-    const int n = g.n, nc = g.nc, K = g.K;
+    const int n = g.n, nc = g.nc, K = g.K, nf = g.nf;
     const int NL = (nc + 1) * K;
-    const float rK = 1.0f / (float)K;
+    const float rK = 1.0f / (float)K, rn = 1.0f / (float)n;
     C* tw = reinterpret_cast<C*>(smraw);
-    C* b0 = tw + n;
-    C* b1 = b0 + LB * n;
-    C* b2 = b1 + LB * n;
+    C* b0 = tw + n;               // [LB][n] forward lines
+    C* b1 = b0 + LB * n;          // [LB][n] scratch
+    C* X = b1 + LB * n;           // [nf][LB][n] fields
+    C* Y = X + nf * LB * n;       // [nf][LB][n] scratch
     for (int t = threadIdx.x; t < n; t += blockDim.x) tw[t] = twg[t];
-    const float rn = 1.0f / (float)n;
     const int l0 = blockIdx.x * LB;
     const int nl = min(LB, NL - l0);
     const float rnl = 1.0f / (float)max(nl, 1);
     for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) b0[idx] = spec2[(size_t)l0 * n + idx];
     __syncthreads();
     C* Fh = fft_lines<R, false>(b0, b1, tw, fp, nl, n);
-    C* wa = (Fh == b0) ? b1 : b0;
-    C* wb = b2;
     // energy and virial of the kept modes (half space kx >= 0, kx > 0 counted twice)
     Kahan ke, kw;
     for (int idx = threadIdx.x; idx < nl * K; idx += blockDim.x) {
@@ -683,33 +683,39 @@ __global__ void __launch_bounds__(256) k_fft_z(Geo g, FftPlanDev fp, const typen
         epart[2 * blockIdx.x] = se;
         epart[2 * blockIdx.x + 1] = sv;
     }
-    for (int a = 0; a < 3; ++a) {
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
-            const int c = qdiv(idx, n, rn), m = idx - c * n;
-            const int kz = m <= n / 2 ? m : m - n;
-            C v;
-            v.x = (R)0;
-            v.y = (R)0;
-            if (kz >= -nc && kz <= nc) {
-                const int l = l0 + c;
+    // fields: line a * nl + c of X
+    const int per = nl * n;
+    const float rper = 1.0f / (float)per;
+    for (int idx = threadIdx.x; idx < nf * per; idx += blockDim.x) {
+        const int a = qdiv(idx, per, rper), e = idx - a * per;
+        const int c = qdiv(e, n, rn), m = e - c * n;
+        const int kz = m <= n / 2 ? m : m - n;
+        C v;
+        v.x = (R)0;
+        v.y = (R)0;
+        if (kz >= -nc && kz <= nc) {
+            const int l = l0 + c;
+            const R d = tabr[(size_t)l * K + (kz + nc)];
+            const C f = Fh[c * n + m];
+            if (nf == 1) {
+                v.x = d * f.x;     // D F
+                v.y = d * f.y;
+            } else {
                 const int kx = qdiv(l, K, rK), ky = (l - kx * K) - nc;
                 const int ka = a == 0 ? kx : (a == 1 ? ky : kz);
-                const R s = (R)ka * tabr[(size_t)l * K + (kz + nc)];
-                const C f = Fh[c * n + m];
-                v.x = s * f.y;     // -i s F
+                const R s = (R)ka * d;
+                v.x = s * f.y;     // -i k_a D F
                 v.y = -s * f.x;
             }
-            wa[idx] = v;
         }
-        __syncthreads();
-        C* res = fft_lines<R, true>(wa, wb, tw, fp, nl, n);
-        for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
-            const int z = qdiv(idx, nl, rnl), c = idx - z * nl;
-            spec3[((size_t)a * n + z) * NL + l0 + c] = res[c * n + z];
-        }
-        // res is wa or wb; the next field rebuilds into wa, so keep both free
-        __syncthreads();
+        X[idx] = v;
+    }
+    __syncthreads();
+    C* res = fft_lines<R, true>(X, Y, tw, fp, nf * nl, n);
+    for (int idx = threadIdx.x; idx < nf * per; idx += blockDim.x) {
+        const int a = qdiv(idx, per, rper), e = idx - a * per;
+        const int z = qdiv(e, nl, rnl), c = e - z * nl;
+        spec3[((size_t)a * n + z) * NL + l0 + c] = res[(a * nl + c) * n + z];
     }
 }
 
@@ -721,7 +727,7 @@ __global__ void __launch_bounds__(256) k_fft_iy(Geo g, FftPlanDev fp, const type
     using C = typename Cx<R>::T;
     extern __shared__ unsigned char smraw[];
     const int n = g.n, nc = g.nc, nc1 = nc + 1, K = g.K;
-    const int NLT = 3 * n * nc1;
+    const int NLT = g.nf * n * nc1;
     const float rnc1 = 1.0f / (float)nc1;
     C* tw = reinterpret_cast<C*>(smraw);
     C* b0 = tw + n;
@@ -758,7 +764,7 @@ __global__ void __launch_bounds__(256) k_fft_ix(Geo g, FftPlanDev fp, const type
     using C = typename Cx<R>::T;
     extern __shared__ unsigned char smraw[];
     const int n = g.n, nc = g.nc, nc1 = nc + 1;
-    const int nrows = 3 * n * n;
+    const int nrows = g.nf * n * n;
     C* tw = reinterpret_cast<C*>(smraw);
     C* b0 = tw + n;
     C* b1 = b0 + LP * n;
@@ -813,18 +819,20 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Geo g, const int* __r
                                                            const R* __restrict__ h, R* __restrict__ F) {
     constexpr int NW = kGatherThreads / 32;
     __shared__ R wts[NW][3][kMaxTaps];
+    __shared__ R dwts[NW][3][kMaxTaps];   // gradient mode: psi'(d) = -(2 d / b) psi(d)
     __shared__ int lix[NW][3][kMaxTaps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int Nq = tstart[g.ntiles];
     const int n = g.n;
     const size_t n3 = (size_t)n * n * n;   // n <= 1024: one grid's offsets fit an int
     const R* __restrict__ h0 = h;
-    const R* __restrict__ h1 = h + n3;
-    const R* __restrict__ h2 = h + 2 * n3;
+    const R* __restrict__ h1 = g.nf == 3 ? h + n3 : h;
+    const R* __restrict__ h2 = g.nf == 3 ? h + 2 * n3 : h;
     const int P2 = 2 * g.p;
     const float iP2 = 1.0f / (float)P2;
     const R rb = (R)g.rb, wn = (R)g.wnorm;
     const R pref = (R)g.pref;
+    const bool grad = g.nf == 1;
     for (int s = blockIdx.x * NW + warp; s < Nq; s += gridDim.x * NW) {
         const typename V4<R>::T wv = sw[s];
         const R qs = sq[s].w;
@@ -837,25 +845,44 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Geo g, const int* __r
                 int l = base[t] - g.p + 1 + lane;
                 l = l < 0 ? l + n : (l >= n ? l - n : l);
                 lix[warp][t][lane] = t == 2 ? l * n * n : l;
-                const R d = fr[t] + (R)(g.p - 1 - lane);
-                wts[warp][t][lane] = wn * r_exp(-d * d * rb);
+                const R d = fr[t] + (R)(g.p - 1 - lane);   // n x - l
+                const R w = wn * r_exp(-d * d * rb);
+                wts[warp][t][lane] = w;
+                dwts[warp][t][lane] = (R)-2 * d * rb * w;
             }
         }
         __syncwarp();
         R ax = 0, ay = 0, az = 0;
-        // lanes over the (x, y) taps, a loop over z; ab -> (a, b) by a float
-        // reciprocal (ab < 256, so the quotient of ab + 1/2 is 1/32 from an integer)
-        for (int ab = lane; ab < P2 * P2; ab += 32) {
-            const int b = (int)(((float)ab + 0.5f) * iP2);
-            const int a = ab - b * P2;
-            const R wab = wts[warp][0][a] * wts[warp][1][b];
-            const int rowo = lix[warp][1][b] * n + lix[warp][0][a];
-            for (int c = 0; c < P2; ++c) {
-                const R w = wab * wts[warp][2][c];
-                const int off = lix[warp][2][c] + rowo;   // z index pre-scaled by n^2
-                ax += w * h0[off];
-                ay += w * h1[off];
-                az += w * h2[off];
+        if (grad) {   // one field: sum_l grad Psi(n x - l) h(l)
+            for (int ab = lane; ab < P2 * P2; ab += 32) {
+                const int b = (int)(((float)ab + 0.5f) * iP2);
+                const int a = ab - b * P2;
+                const R wx = wts[warp][0][a], wy = wts[warp][1][b];
+                const R cx = dwts[warp][0][a] * wy, cy = wx * dwts[warp][1][b], cz = wx * wy;
+                const int rowo = lix[warp][1][b] * n + lix[warp][0][a];
+                for (int c = 0; c < P2; ++c) {
+                    const R hv = h0[lix[warp][2][c] + rowo];
+                    const R t = hv * wts[warp][2][c];
+                    ax += cx * t;
+                    ay += cy * t;
+                    az += cz * (hv * dwts[warp][2][c]);
+                }
+            }
+        } else {
+            // lanes over the (x, y) taps, a loop over z; ab -> (a, b) by a float
+            // reciprocal (ab < 256, so the quotient of ab + 1/2 is 1/32 from an integer)
+            for (int ab = lane; ab < P2 * P2; ab += 32) {
+                const int b = (int)(((float)ab + 0.5f) * iP2);
+                const int a = ab - b * P2;
+                const R wab = wts[warp][0][a] * wts[warp][1][b];
+                const int rowo = lix[warp][1][b] * n + lix[warp][0][a];
+                for (int c = 0; c < P2; ++c) {
+                    const R w = wab * wts[warp][2][c];
+                    const int off = lix[warp][2][c] + rowo;   // z index pre-scaled by n^2
+                    ax += w * h0[off];
+                    ay += w * h1[off];
+                    az += w * h2[off];
+                }
             }
         }
         ax = warp_sum_r(ax);

@@ -35,7 +35,7 @@ class enuf_params(C.Structure):
     _fields_ = [("L", C.c_double), ("alpha", C.c_double), ("r_cut", C.c_double),
                 ("beta", C.c_double), ("kappa", C.c_double), ("M", C.c_int), ("p", C.c_int),
                 ("sigma_s", C.c_int), ("kmask", C.c_int), ("prec", C.c_int), ("tile", C.c_int),
-                ("reserved", C.c_int * 6)]
+                ("deriv", C.c_int), ("reserved", C.c_int * 5)]
 
 
 class enuf_plan_info(C.Structure):
@@ -108,10 +108,10 @@ def _check(status, handle=None, what=""):
 
 
 def make_params(L, alpha, r_cut, beta, kappa, M=0, p=4, sigma_s=2, kmask=0,
-                prec="fp64", tile=0) -> enuf_params:
+                prec="fp64", tile=0, deriv=0) -> enuf_params:
     pr = {"fp64": ENUF_FP64, "fp32": ENUF_FP32}[prec] if isinstance(prec, str) else int(prec)
     return enuf_params(float(L), float(alpha), float(r_cut), float(beta), float(kappa), int(M),
-                       int(p), int(sigma_s), int(kmask), pr, int(tile), (C.c_int * 6)())
+                       int(p), int(sigma_s), int(kmask), pr, int(tile), int(deriv), (C.c_int * 5)())
 
 
 def _ptr(x):
@@ -221,7 +221,7 @@ class Plan:
 
     def debug_buffer(self, which):
         n = self.info.n
-        shape = (n, n, n) if which == ENUF_BUF_GRID else (3, n, n, n)
+        shape = (n, n, n) if which == ENUF_BUF_GRID else (1 if self.params.deriv else 3, n, n, n)
         out = np.empty(shape, dtype=self.dtype_np)
         _check(lib.enuf_debug_buffer(self.h, which, _ptr(out), out.nbytes), self.h)
         return out

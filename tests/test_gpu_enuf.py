@@ -115,6 +115,36 @@ def test_energy_forces_parity(enuf, name, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", list(CASES))
+def test_gradient_mode_parity(enuf, name, prec):
+    """Gradient-mode reciprocal forces (one inverse transform, derivative of the
+    window in the gather) against the oracle's gradient mode."""
+    P, pos, q = _case(name)
+    P = dict(P, deriv=1)
+    pos, q = _inputs(prec, pos, q)
+    plan, F, E, Wv = _gpu(enuf, prec, P, pos, q)
+    Fr, Er, Wr = _ref(prec, P, pos, q)
+    _check(prec, F, E, Wv, Fr, Er, Wr)
+    assert np.all(F[q == 0] == 0.0)
+    h = plan.debug_buffer(enuf.ENUF_BUF_FIELD)
+    assert h.shape[0] == 1
+    plan.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_gradient_mode_field_matches_oracle(enuf, prec):
+    P, pos, q = _sys_small("baseline")
+    P = dict(P, deriv=1)
+    pos, q = _inputs(prec, pos, q)
+    plan, F, E, Wv = _gpu(enuf, prec, P, pos, q)
+    h = plan.debug_buffer(enuf.ENUF_BUF_FIELD).astype(np.float64)
+    _, _, _, h_ref = orc.recip_enuf(_oparams(prec, P), pos, q, want_h=True)
+    t = TOL[prec]["stage"]
+    assert np.abs(h - h_ref).max() < 10 * t * np.abs(h_ref).max()
+    plan.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_spread_grid_and_fields_match_oracle(enuf, prec):
     """Stage parity: the spread grid (Eq. 14, first half) and the three
     conjugated-NFFT fields before the gather (Eq. 25)."""
@@ -268,5 +298,25 @@ def test_full_size_sampled(enuf, prec, which):
     # and zero force on the neutral beads
     Fk = F.sum(0)
     assert np.abs(Fk).max() < (1e-8 if prec == "fp64" else 2e-2) * np.abs(F).max()
+    assert np.all(F[q == 0] == 0.0)
+    plan.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_full_size_gradient_mode_sampled(enuf, prec):
+    """The 81000-bead polyelectrolyte in gradient mode: 256 sampled forces and
+    the energies against the oracle's gradient mode."""
+    s = W.polyelectrolyte()
+    P = dict(L=s.L, M=s.M, deriv=1, **s.params)
+    pos, q = _inputs(prec, s.pos, s.q)
+    plan, F, E, Wv = _gpu(enuf, prec, P, pos, q)
+    rng = np.random.default_rng(19)
+    sample = np.sort(rng.choice(np.nonzero(q)[0], 256, replace=False))
+    Fr, Er, Wr = _ref(prec, P, pos, q, sample=sample)
+    t = TOL[prec]
+    assert _rel_rms(F[sample], Fr) < t["F"]
+    scale = max(abs(Er[0]), abs(Er[1]))
+    for k in range(4):
+        assert abs(E[k] - Er[k]) < t["E"] * scale, (k, E, Er)
     assert np.all(F[q == 0] == 0.0)
     plan.close()
