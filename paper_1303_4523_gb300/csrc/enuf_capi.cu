@@ -356,8 +356,9 @@ enuf_status enqueue_eval(enuf_plan_t plan, const EvalArgs& a, cudaStream_t s0, c
 }
 
 enuf_status enqueue_tot(enuf_plan_t plan, bool dpd, cudaStream_t s, LaunchLog* log) {
-    cudaError_t e = plan->prec == ENUF_FP32 ? enqueue_totals<float>(plan->g, plan->w, dpd, s, log)
-                                            : enqueue_totals<double>(plan->g, plan->w, dpd, s, log);
+    const bool pdl = !plan->ev.on;   // with stage events the predecessor is an event node
+    cudaError_t e = plan->prec == ENUF_FP32 ? enqueue_totals<float>(plan->g, plan->w, dpd, s, log, pdl)
+                                            : enqueue_totals<double>(plan->g, plan->w, dpd, s, log, pdl);
     if (e != cudaSuccess) return fail(plan, ENUF_ERR_CUDA, "totals: %s", cudaGetErrorString(e));
     return ENUF_OK;
 }
@@ -662,8 +663,8 @@ enuf_status capture_step(dpd_system_t sys) {
     enuf_status st = e == cudaSuccess ? ENUF_OK : fail(plan, ENUF_ERR_CUDA, "vv_pre: %s", cudaGetErrorString(e));
     if (st == ENUF_OK) st = enqueue_force_eval(sys, plan->stream, plan->aux, ev, &log);
     if (st == ENUF_OK) {
-        e = plan->prec == ENUF_FP32 ? enqueue_vv_post<float>(plan->w, sys->d, plan->stream, &log)
-                                    : enqueue_vv_post<double>(plan->w, sys->d, plan->stream, &log);
+        e = plan->prec == ENUF_FP32 ? enqueue_vv_post<float>(plan->w, sys->d, plan->stream, &log, !plan->ev.on)
+                                    : enqueue_vv_post<double>(plan->w, sys->d, plan->stream, &log, !plan->ev.on);
         if (e != cudaSuccess) st = fail(plan, ENUF_ERR_CUDA, "vv_post: %s", cudaGetErrorString(e));
     }
     if (st == ENUF_OK) st = enqueue_tot(plan, true, plan->stream, &log);

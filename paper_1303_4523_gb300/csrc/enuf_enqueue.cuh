@@ -4,6 +4,8 @@
 // depend on the binning and write F; the branches join before the gather.
 // Every sequence is stream-ordered and capturable into a CUDA graph.
 #pragma once
+#include <utility>
+
 #include "enuf_kernels.cuh"
 
 namespace enuf {
@@ -14,6 +16,28 @@ inline void rec(Events* ev, int stage, bool start, cudaStream_t s) {
     if (ev && ev->on)
         cudaEventRecordWithFlags(start ? ev->start[stage] : ev->stop[stage], s, cudaEventRecordExternal);
 }
+
+// Programmatic dependent launch where pdl is set: the launch of the kernel is
+// prepared while the previous kernel of the stream runs; every kernel opens
+// with griddepcontrol.wait, so it touches no memory before that kernel has
+// completed. pdl is off for a kernel whose stream predecessor is not a kernel
+// (an event wait, an event record, the start of a graph).
+template <typename... P, typename... A>
+inline void launch(bool pdl, void (*k)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
+}
+
+inline bool pdl_ok(const Events* ev) { return !(ev && ev->on); }
 
 template <typename R>
 cudaError_t configure_kernels(int max_smem) {
@@ -44,16 +68,16 @@ int spread_smem(const Geo& g) {
 
 // a1: compaction + coordinates + tile histograms, tile offsets, tile scan, scatter.
 template <typename R>
-void enqueue_bin(const Geo& g, const Work& w, int N, const R* pos, const R* q, R* Fzero, cudaStream_t s) {
+void enqueue_bin(const Geo& g, const Work& w, int N, const R* pos, const R* q, R* Fzero, cudaStream_t s, bool pdl) {
     using V = typename V4<R>::T;
-    k_bin_count<R><<<g.nbin, kBinThreads, (g.ntiles + g.chunk) * (int)sizeof(int), s>>>(
-        g, N, pos, q, w.cnt_blk, w.bhist, w.ctile, static_cast<V*>(w.cpos), static_cast<V*>(w.cfrac), w.cbase,
-        Fzero, w.part + w.off_q);
-    k_tile_offsets<<<(g.ntiles + 255) / 256, 256, 0, s>>>(g, w.bhist, w.boff, w.ttot);
-    k_scan<<<1, 1024, 0, s>>>(w.ttot, w.tstart, g.ntiles, nullptr, 0);
-    k_bin_scatter<R><<<g.nbin, kBinThreads, g.ntiles * (int)sizeof(int), s>>>(
-        g, w.cnt_blk, w.ctile, static_cast<const V*>(w.cpos), static_cast<const V*>(w.cfrac), w.cbase, w.boff,
-        w.tstart, static_cast<V*>(w.sq), static_cast<V*>(w.sw), w.sb);
+    launch(false, k_bin_count<R>, g.nbin, kBinThreads, (g.ntiles + g.chunk) * sizeof(int), s, g, N, pos, q,
+           w.cnt_blk, w.bhist, w.ctile, static_cast<V*>(w.cpos), static_cast<V*>(w.cfrac), w.cbase, Fzero,
+           w.part + w.off_q);
+    launch(pdl, k_tile_offsets, (g.ntiles + 255) / 256, 256, 0, s, g, (const int*)w.bhist, w.boff, w.ttot);
+    launch(pdl, k_scan, 1, 1024, 0, s, w.ttot, w.tstart, g.ntiles, (int*)nullptr, 0);
+    launch(pdl, k_bin_scatter<R>, g.nbin, kBinThreads, g.ntiles * sizeof(int), s, g, (const int*)w.cnt_blk,
+           (const int*)w.ctile, static_cast<const V*>(w.cpos), static_cast<const V*>(w.cfrac), (const int*)w.cbase,
+           (const int*)w.boff, (const int*)w.tstart, static_cast<V*>(w.sq), static_cast<V*>(w.sw), w.sb);
 }
 
 template <typename R>
@@ -68,8 +92,9 @@ cudaError_t enqueue_enuf(const Geo& g, const FftShape& fs, const FftPlanDev& fp,
     V* sq = static_cast<V*>(w.sq);
     V* sw = static_cast<V*>(w.sw);
     C* tw = static_cast<C*>(w.tw);
+    const bool pdl = pdl_ok(ev);
     rec(ev, 0, true, s0);
-    enqueue_bin<R>(g, w, a.N, pos, q, a.zeroF ? F : nullptr, s0);
+    enqueue_bin<R>(g, w, a.N, pos, q, a.zeroF ? F : nullptr, s0, pdl);
     rec(ev, 0, false, s0);
     log->kernels += 4;
 
@@ -78,44 +103,45 @@ cudaError_t enqueue_enuf(const Geo& g, const FftShape& fs, const FftPlanDev& fp,
     cudaStreamWaitEvent(s1, evFork, 0);
     rec(ev, 4, true, s1);
     const int real_smem = (kRealCap + (kRealThreads / 32) * 64) * (int)sizeof(V) + (2 * kRealHalo + 1) * 4;
-    k_real<R><<<w.nblk_real, kRealThreads, real_smem, s1>>>(g, w.tstart, sq, sw, F, w.part + w.off_real);
+    launch(false, k_real<R>, w.nblk_real, kRealThreads, real_smem, s1, g, (const int*)w.tstart, (const V*)sq,
+           (const V*)sw, F, w.part + w.off_real);
     rec(ev, 4, false, s1);
     cudaEventRecord(evJoin, s1);
     log->kernels += 1;
 
     // reciprocal branch
     rec(ev, 1, true, s0);
-    k_spread<R><<<g.ntiles, kSpreadThreads, spread_smem<R>(g), s0>>>(g, w.tstart, sq, sw, w.sb,
-                                                                     static_cast<R*>(w.grid));
+    launch(pdl, k_spread<R>, g.ntiles, kSpreadThreads, spread_smem<R>(g), s0, g, (const int*)w.tstart,
+           (const V*)sq, (const V*)sw, (const int*)w.sb, static_cast<R*>(w.grid));
     rec(ev, 1, false, s0);
     rec(ev, 2, true, s0);
-    k_fft_x<R><<<fs.grid_x, fs.tx, fs.smem_x, s0>>>(g, fp, static_cast<const R*>(w.grid), tw,
-                                                  static_cast<C*>(w.spec1), fs.lx);
-    k_fft_y<R><<<dim3(g.nc + 1, fs.grid_y_z), fs.ty, fs.smem_y, s0>>>(g, fp, static_cast<const C*>(w.spec1), tw,
-                                                                   static_cast<C*>(w.spec2), fs.ly);
-    k_fft_z<R><<<fs.grid_z, fs.tz, fs.smem_z, s0>>>(g, fp, static_cast<const C*>(w.spec2), tw, w.tab, w.tabv,
-                                                  static_cast<const R*>(w.tabr), static_cast<C*>(w.spec3),
-                                                  w.part + w.off_recip, fs.lz);
-    k_fft_iy<R><<<fs.grid_iy, fs.tiy, fs.smem_iy, s0>>>(g, fp, static_cast<const C*>(w.spec3), tw,
-                                                     static_cast<C*>(w.spec4), fs.liy);
-    k_fft_ix<R><<<fs.grid_ix, fs.tix, fs.smem_ix, s0>>>(g, fp, static_cast<const C*>(w.spec4), tw,
-                                                     static_cast<R*>(w.h), fs.lix);
+    launch(pdl, k_fft_x<R>, fs.grid_x, fs.tx, fs.smem_x, s0, g, fp, static_cast<const R*>(w.grid), (const C*)tw,
+           static_cast<C*>(w.spec1), fs.lx);
+    launch(pdl, k_fft_y<R>, dim3(g.nc + 1, fs.grid_y_z), fs.ty, fs.smem_y, s0, g, fp,
+           static_cast<const C*>(w.spec1), (const C*)tw, static_cast<C*>(w.spec2), fs.ly);
+    launch(pdl, k_fft_z<R>, fs.grid_z, fs.tz, fs.smem_z, s0, g, fp, static_cast<const C*>(w.spec2), (const C*)tw,
+           (const double*)w.tab, (const double*)w.tabv, static_cast<const R*>(w.tabr), static_cast<C*>(w.spec3),
+           w.part + w.off_recip, fs.lz);
+    launch(pdl, k_fft_iy<R>, fs.grid_iy, fs.tiy, fs.smem_iy, s0, g, fp, static_cast<const C*>(w.spec3),
+           (const C*)tw, static_cast<C*>(w.spec4), fs.liy);
+    launch(pdl, k_fft_ix<R>, fs.grid_ix, fs.tix, fs.smem_ix, s0, g, fp, static_cast<const C*>(w.spec4),
+           (const C*)tw, static_cast<R*>(w.h), fs.lix);
     rec(ev, 2, false, s0);
     log->kernels += 6;
 
     cudaStreamWaitEvent(s0, evJoin, 0);
     rec(ev, 3, true, s0);
-    k_gather<R><<<w.nblk_gather, kGatherThreads, 0, s0>>>(g, w.tstart, sq, sw, w.sb,
-                                                          static_cast<const R*>(w.h), F);
+    launch(false, k_gather<R>, w.nblk_gather, kGatherThreads, 0, s0, g, (const int*)w.tstart, (const V*)sq,
+           (const V*)sw, (const int*)w.sb, static_cast<const R*>(w.h), F);
     rec(ev, 3, false, s0);
     log->kernels += 1;
     return cudaGetLastError();
 }
 
 template <typename R>
-cudaError_t enqueue_totals(const Geo& g, const Work& w, bool dpd, cudaStream_t s, LaunchLog* log) {
-    k_totals<<<1, 1024, 0, s>>>(g, w.part, w.off_q, g.nbin, w.off_real, w.nblk_real, w.off_recip, w.nblk_conv,
-                               w.off_dpd, dpd ? w.nblk_dpd : 0, w.off_kin, dpd ? w.nblk_kin : 0, w.Edev);
+cudaError_t enqueue_totals(const Geo& g, const Work& w, bool dpd, cudaStream_t s, LaunchLog* log, bool pdl) {
+    launch(pdl, k_totals, 1, 1024, 0, s, g, (const double*)w.part, w.off_q, g.nbin, w.off_real, w.nblk_real,
+           w.off_recip, w.nblk_conv, w.off_dpd, dpd ? w.nblk_dpd : 0, w.off_kin, dpd ? w.nblk_kin : 0, w.Edev);
     log->kernels += 1;
     return cudaGetLastError();
 }
@@ -124,21 +150,22 @@ template <typename R>
 cudaError_t enqueue_dpd_forces(const Work& w, const DpdDev& d, cudaStream_t s, Events* ev, LaunchLog* log) {
     using V = typename V4<R>::T;
     const int blocks = (d.N + 255) / 256 > 0 ? (d.N + 255) / 256 : 1;
+    const bool pdl = pdl_ok(ev);
     rec(ev, 7, true, s);
-    k_cell_count<R><<<blocks, 256, 0, s>>>(d.N, d.ncd, d.L, d.cinv, d.xmaxf, static_cast<const R*>(d.pos), d.ckey,
-                                           d.ccount);
-    k_scan<<<1, 1024, 0, s>>>(d.ccount, d.cstart, d.ncells, d.ccur, 1);
-    k_cell_scatter<R><<<blocks, 256, 0, s>>>(d.N, d.L, d.xmaxf, static_cast<const R*>(d.pos), static_cast<const R*>(d.v0),
-                                             d.type, d.ckey, d.ccur, static_cast<V*>(d.sp), static_cast<V*>(d.sv));
+    // the cell count also zeroes F, which the pair kernel adds into
+    launch(false, k_cell_count<R>, blocks, 256, 0, s, d.N, d.ncd, d.L, d.cinv, d.xmaxf, static_cast<const R*>(d.pos),
+           d.ckey, d.ccount, static_cast<R*>(d.F));
+    launch(pdl, k_scan, 1, 1024, 0, s, d.ccount, d.cstart, d.ncells, d.ccur, 1);
+    launch(pdl, k_cell_scatter<R>, blocks, 256, 0, s, d.N, d.L, d.xmaxf, static_cast<const R*>(d.pos),
+           static_cast<const R*>(d.v0), (const int*)d.type, (const int*)d.ckey, d.ccur, static_cast<V*>(d.sp),
+           static_cast<V*>(d.sv));
     rec(ev, 7, false, s);
     rec(ev, 5, true, s);
     const int dpd_smem = dpd_smem_bytes<R>();
-    cudaMemsetAsync(d.F, 0, (size_t)d.N * 3 * sizeof(R), s);   // the pair kernel adds into F
-    k_dpd<R><<<w.nblk_dpd, kDpdThreads, dpd_smem, s>>>(d, d.B, static_cast<const V*>(d.sp),
-                                                      static_cast<const V*>(d.sv), d.cstart,
-                                                      static_cast<const R*>(d.atab), static_cast<const R*>(d.pos),
-                                                      d.bnd, d.step_dev, static_cast<R*>(d.F),
-                                                      w.part + w.off_dpd);
+    launch(pdl, k_dpd<R>, w.nblk_dpd, kDpdThreads, dpd_smem, s, d, d.B, static_cast<const V*>(d.sp),
+           static_cast<const V*>(d.sv), (const int*)d.cstart, static_cast<const R*>(d.atab),
+           static_cast<const R*>(d.pos), (const int*)d.bnd, (const uint64_t*)d.step_dev, static_cast<R*>(d.F),
+           w.part + w.off_dpd);
     rec(ev, 5, false, s);
     log->kernels += 4;
     return cudaGetLastError();
@@ -147,17 +174,16 @@ cudaError_t enqueue_dpd_forces(const Work& w, const DpdDev& d, cudaStream_t s, E
 template <typename R>
 cudaError_t enqueue_vv_pre(const DpdDev& d, cudaStream_t s, LaunchLog* log) {
     const int blocks = (3 * d.N + 255) / 256 > 0 ? (3 * d.N + 255) / 256 : 1;
-    k_vv_pre<R><<<blocks, 256, 0, s>>>(d.N, (R)d.lambda_vv, (R)d.dt, static_cast<R*>(d.pos),
-                                       static_cast<R*>(d.vel), static_cast<R*>(d.v0),
-                                       static_cast<const R*>(d.F), d.step_dev);
+    launch(false, k_vv_pre<R>, blocks, 256, 0, s, d.N, (R)d.lambda_vv, (R)d.dt, static_cast<R*>(d.pos),
+           static_cast<R*>(d.vel), static_cast<R*>(d.v0), static_cast<const R*>(d.F), d.step_dev);
     log->kernels += 1;
     return cudaGetLastError();
 }
 
 template <typename R>
-cudaError_t enqueue_vv_post(const Work& w, const DpdDev& d, cudaStream_t s, LaunchLog* log) {
-    k_vv_post<R><<<w.nblk_kin, 256, 0, s>>>(d.N, (R)d.dt, static_cast<R*>(d.vel), static_cast<const R*>(d.F),
-                                            w.part + w.off_kin);
+cudaError_t enqueue_vv_post(const Work& w, const DpdDev& d, cudaStream_t s, LaunchLog* log, bool pdl) {
+    launch(pdl, k_vv_post<R>, w.nblk_kin, 256, 0, s, d.N, (R)d.dt, static_cast<R*>(d.vel),
+           static_cast<const R*>(d.F), w.part + w.off_kin);
     log->kernels += 1;
     return cudaGetLastError();
 }
@@ -167,10 +193,9 @@ cudaError_t enqueue_vv_post(const Work& w, const DpdDev& d, cudaStream_t s, Laun
 template <typename R>
 cudaError_t enqueue_spread_only(const Geo& g, const Work& w, const EvalArgs& a, void* grid_out, cudaStream_t s) {
     using V = typename V4<R>::T;
-    enqueue_bin<R>(g, w, a.N, static_cast<const R*>(a.pos), static_cast<const R*>(a.q), nullptr, s);
-    k_spread<R><<<g.ntiles, kSpreadThreads, spread_smem<R>(g), s>>>(g, w.tstart, static_cast<const V*>(w.sq),
-                                                                    static_cast<const V*>(w.sw), w.sb,
-                                                                    static_cast<R*>(grid_out));
+    enqueue_bin<R>(g, w, a.N, static_cast<const R*>(a.pos), static_cast<const R*>(a.q), nullptr, s, true);
+    launch(true, k_spread<R>, g.ntiles, kSpreadThreads, spread_smem<R>(g), s, g, (const int*)w.tstart,
+           static_cast<const V*>(w.sq), static_cast<const V*>(w.sw), (const int*)w.sb, static_cast<R*>(grid_out));
     return cudaGetLastError();
 }
 
@@ -180,11 +205,11 @@ cudaError_t enqueue_spread_only(const Geo& g, const Work& w, const EvalArgs& a, 
     template cudaError_t enqueue_enuf<R>(const Geo&, const FftShape&, const FftPlanDev&, const Work&,        \
                                          const EvalArgs&, cudaStream_t, cudaStream_t, cudaEvent_t,           \
                                          cudaEvent_t, Events*, LaunchLog*);                                  \
-    template cudaError_t enqueue_totals<R>(const Geo&, const Work&, bool, cudaStream_t, LaunchLog*);         \
+    template cudaError_t enqueue_totals<R>(const Geo&, const Work&, bool, cudaStream_t, LaunchLog*, bool);   \
     template cudaError_t enqueue_dpd_forces<R>(const Work&, const DpdDev&, cudaStream_t, Events*,            \
                                                LaunchLog*);                                                  \
     template cudaError_t enqueue_vv_pre<R>(const DpdDev&, cudaStream_t, LaunchLog*);                         \
-    template cudaError_t enqueue_vv_post<R>(const Work&, const DpdDev&, cudaStream_t, LaunchLog*);           \
+    template cudaError_t enqueue_vv_post<R>(const Work&, const DpdDev&, cudaStream_t, LaunchLog*, bool);     \
     template cudaError_t enqueue_spread_only<R>(const Geo&, const Work&, const EvalArgs&, void*, cudaStream_t);
 
 }  // namespace enuf

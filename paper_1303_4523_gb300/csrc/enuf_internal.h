@@ -131,13 +131,13 @@ cudaError_t enqueue_enuf(const Geo& g, const FftShape& fs, const FftPlanDev& fp,
                          const EvalArgs& a, cudaStream_t s0, cudaStream_t s1, cudaEvent_t evFork,
                          cudaEvent_t evJoin, Events* ev, LaunchLog* log);
 template <typename R>
-cudaError_t enqueue_totals(const Geo& g, const Work& w, bool dpd, cudaStream_t s, LaunchLog* log);
+cudaError_t enqueue_totals(const Geo& g, const Work& w, bool dpd, cudaStream_t s, LaunchLog* log, bool pdl);
 template <typename R>
 cudaError_t enqueue_dpd_forces(const Work& w, const DpdDev& d, cudaStream_t s, Events* ev, LaunchLog* log);
 template <typename R>
 cudaError_t enqueue_vv_pre(const DpdDev& d, cudaStream_t s, LaunchLog* log);
 template <typename R>
-cudaError_t enqueue_vv_post(const Work& w, const DpdDev& d, cudaStream_t s, LaunchLog* log);
+cudaError_t enqueue_vv_post(const Work& w, const DpdDev& d, cudaStream_t s, LaunchLog* log, bool pdl);
 template <typename R>
 cudaError_t enqueue_spread_only(const Geo& g, const Work& w, const EvalArgs& a, void* grid_out, cudaStream_t s);
 

@@ -30,6 +30,15 @@ __device__ __forceinline__ double int_as_real(int v, double) { return __longlong
 __device__ __forceinline__ int real_as_int(float v) { return __float_as_int(v); }
 __device__ __forceinline__ int real_as_int(double v) { return (int)__double_as_longlong(v); }
 
+// Programmatic dependent launch (sm_90 and later): every kernel first waits
+// until the grid before it in the stream has completed and its writes are
+// visible (griddepcontrol.wait, a no-op when it was launched without the
+// programmatic attribute). Nothing touches global memory before the wait. No
+// kernel triggers its dependents early: CTAs of the next grid parked in the
+// wait would hold shared memory that the other stream's kernels need, so the
+// next grid launches at completion, with its launch work already done.
+__device__ __forceinline__ void pdl_enter() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ float r_exp(float x) { return expf(x); }
 __device__ __forceinline__ double r_exp(double x) { return exp(x); }
 __device__ __forceinline__ float r_erfc(float x) { return erfcf(x); }
@@ -183,6 +192,7 @@ __global__ void __launch_bounds__(1024) k_bin_count(Geo g, int N, const R* __res
                                                    typename V4<R>::T* __restrict__ cpos,
                                                    typename V4<R>::T* __restrict__ cfrac, int* __restrict__ cbase,
                                                    R* __restrict__ Fzero, double* __restrict__ qpart) {
+    pdl_enter();
     extern __shared__ int sm_bin[];
     int* hist = sm_bin;                 // [ntiles]
     int* slist = sm_bin + g.ntiles;     // [chunk]
@@ -251,6 +261,7 @@ __global__ void __launch_bounds__(1024) k_bin_count(Geo g, int N, const R* __res
 // One thread per tile: offsets of each block's beads inside the tile, and the tile total.
 static __global__ void __launch_bounds__(256) k_tile_offsets(Geo g, const int* __restrict__ bhist, int* __restrict__ boff,
                                                       int* __restrict__ ttot) {
+    pdl_enter();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= g.ntiles) return;
     int run = 0;
@@ -277,6 +288,7 @@ static __global__ void __launch_bounds__(256) k_tile_offsets(Geo g, const int* _
 // aux, when given, receives a copy of out; zero_in clears the input.
 static __global__ void __launch_bounds__(1024) k_scan(int* __restrict__ in, int* __restrict__ out, int count,
                                                       int* __restrict__ aux, int zero_in) {
+    pdl_enter();
     constexpr int IPT = 16;
     __shared__ int wsum[32];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -359,6 +371,7 @@ __global__ void __launch_bounds__(1024) k_bin_scatter(Geo g, const int* __restri
                                                      const int* __restrict__ tstart,
                                                      typename V4<R>::T* __restrict__ sq,
                                                      typename V4<R>::T* __restrict__ sw, int* __restrict__ sb) {
+    pdl_enter();
     extern __shared__ int cur[];
     const int b = blockIdx.x;
     for (int t = threadIdx.x; t < g.ntiles; t += blockDim.x) cur[t] = 0;
@@ -419,6 +432,7 @@ __global__ void __launch_bounds__(kSpreadThreads, 5) k_spread(Geo g, const int* 
                                                            const typename V4<R>::T* __restrict__ sw,
                                                            const int* __restrict__ sb,
                                                            R* __restrict__ grid) {
+    pdl_enter();
     using V = typename V4<R>::T;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int T = g.T, T3 = T * T * T;
@@ -568,6 +582,7 @@ template <typename R>
 __global__ void __launch_bounds__(256) k_fft_x(Geo g, FftPlanDev fp, const R* __restrict__ grid,
                                               const typename Cx<R>::T* __restrict__ twg,
                                               typename Cx<R>::T* __restrict__ spec1, int LP) {
+    pdl_enter();
     using C = typename Cx<R>::T;
     extern __shared__ unsigned char smraw[];
     const int n = g.n, nc1 = g.nc + 1;
@@ -612,6 +627,7 @@ template <typename R>
 __global__ void __launch_bounds__(256) k_fft_y(Geo g, FftPlanDev fp, const typename Cx<R>::T* __restrict__ spec1,
                                               const typename Cx<R>::T* __restrict__ twg,
                                               typename Cx<R>::T* __restrict__ spec2, int LB) {
+    pdl_enter();
     using C = typename Cx<R>::T;
     extern __shared__ unsigned char smraw[];
     const int n = g.n, nc1 = g.nc + 1, K = g.K;
@@ -647,6 +663,7 @@ __global__ void __launch_bounds__(256) k_fft_z(Geo g, FftPlanDev fp, const typen
                                               const double* __restrict__ tab, const double* __restrict__ tabv,
                                               const R* __restrict__ tabr, typename Cx<R>::T* __restrict__ spec3,
                                               double* __restrict__ epart, int LB) {
+    pdl_enter();
     using C = typename Cx<R>::T;
     extern __shared__ unsigned char smraw[];
     const int n = g.n, nc = g.nc, K = g.K, nf = g.nf;
@@ -724,6 +741,7 @@ template <typename R>
 __global__ void __launch_bounds__(256) k_fft_iy(Geo g, FftPlanDev fp, const typename Cx<R>::T* __restrict__ spec3,
                                                const typename Cx<R>::T* __restrict__ twg,
                                                typename Cx<R>::T* __restrict__ spec4, int LB) {
+    pdl_enter();
     using C = typename Cx<R>::T;
     extern __shared__ unsigned char smraw[];
     const int n = g.n, nc = g.nc, nc1 = nc + 1, K = g.K;
@@ -761,6 +779,7 @@ template <typename R>
 __global__ void __launch_bounds__(256) k_fft_ix(Geo g, FftPlanDev fp, const typename Cx<R>::T* __restrict__ spec4,
                                                const typename Cx<R>::T* __restrict__ twg,
                                                R* __restrict__ h, int LP) {
+    pdl_enter();
     using C = typename Cx<R>::T;
     extern __shared__ unsigned char smraw[];
     const int n = g.n, nc = g.nc, nc1 = nc + 1;
@@ -817,6 +836,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Geo g, const int* __r
                                                            const typename V4<R>::T* __restrict__ sw,
                                                            const int* __restrict__ sb,
                                                            const R* __restrict__ h, R* __restrict__ F) {
+    pdl_enter();
     constexpr int NW = kGatherThreads / 32;
     __shared__ R wts[NW][3][kMaxTaps];
     __shared__ R dwts[NW][3][kMaxTaps];   // gradient mode: psi'(d) = -(2 d / b) psi(d)
@@ -1039,6 +1059,7 @@ __global__ void __launch_bounds__(kRealThreads) k_real(Geo g, const int* __restr
                                                        const typename V4<R>::T* __restrict__ sq,
                                                        const typename V4<R>::T* __restrict__ sw,
                                                        R* __restrict__ F, double* __restrict__ rpart) {
+    pdl_enter();
     using V = typename V4<R>::T;
     constexpr int NW = kRealThreads / 32;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -1134,9 +1155,13 @@ __global__ void __launch_bounds__(kRealThreads) k_real(Geo g, const int* __restr
 // of x * ncd/L cannot separate two beads closer than 1 by two cells).
 template <typename R>
 __global__ void k_cell_count(int N, int ncd, double L, double inv, float xmaxf, const R* __restrict__ pos,
-                             int* __restrict__ ckey, int* __restrict__ ccount) {
+                             int* __restrict__ ckey, int* __restrict__ ccount, R* __restrict__ F) {
+    pdl_enter();
     const R rinv = (R)inv;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        F[3 * i] = (R)0;   // the pair kernel adds into F
+        F[3 * i + 1] = (R)0;
+        F[3 * i + 2] = (R)0;
         int c[3];
 #pragma unroll
         for (int t = 0; t < 3; ++t) {
@@ -1154,6 +1179,7 @@ __global__ void k_cell_scatter(int N, double L, float xmaxf, const R* __restrict
                                const int* __restrict__ type, const int* __restrict__ ckey,
                                int* __restrict__ ccur, typename V4<R>::T* __restrict__ sp,
                                typename V4<R>::T* __restrict__ sv) {
+    pdl_enter();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
         const int slot = atomicAdd(&ccur[ckey[i]], 1);
         typename V4<R>::T a, b;
@@ -1437,6 +1463,7 @@ __global__ void __launch_bounds__(kDpdThreads, sizeof(R) == 4 ? 4 : 2)
           const int* __restrict__ cstart, const R* __restrict__ atab, const R* __restrict__ pos,
           const int* __restrict__ bnd, const uint64_t* __restrict__ stepp, R* __restrict__ F,
           double* __restrict__ dpart) {
+    pdl_enter();
     using V = typename V4<R>::T;
     constexpr bool F64 = sizeof(R) == 8;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -1574,6 +1601,7 @@ __global__ void __launch_bounds__(kDpdThreads, sizeof(R) == 4 ? 4 : 2)
 template <typename R>
 __global__ void k_vv_pre(int N, R lam, R dt, R* __restrict__ pos, R* __restrict__ vel, R* __restrict__ v0,
                          const R* __restrict__ F, uint64_t* __restrict__ stepp) {
+    pdl_enter();
     if (blockIdx.x == 0 && threadIdx.x == 0) *stepp += 1;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < 3 * N; k += gridDim.x * blockDim.x) {
         const R f = F[k];
@@ -1589,6 +1617,7 @@ __global__ void k_vv_pre(int N, R lam, R dt, R* __restrict__ pos, R* __restrict_
 template <typename R>
 __global__ void __launch_bounds__(256) k_vv_post(int N, R dt, R* __restrict__ vel, const R* __restrict__ F,
                                                 double* __restrict__ kpart) {
+    pdl_enter();
     double ke = 0.0, dummy = 0.0;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < 3 * N; k += gridDim.x * blockDim.x) {
         const R v = vel[k] + (R)0.5 * F[k] * dt;
@@ -1608,6 +1637,7 @@ static __global__ void __launch_bounds__(1024) k_totals(Geo g, const double* __r
                                                         int off_real, int nreal, int off_recip, int nrecip,
                                                         int off_dpd, int ndpd, int off_kin, int nkin,
                                                         double* __restrict__ Edev) {
+    pdl_enter();
     __shared__ double wv[32];
     __shared__ double vals[9];
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
