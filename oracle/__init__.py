@@ -38,7 +38,7 @@ class _Params(C.Structure):
     _fields_ = [("L", C.c_double), ("alpha", C.c_double), ("r_cut", C.c_double),
                 ("beta", C.c_double), ("kappa", C.c_double), ("M", C.c_int),
                 ("p", C.c_int), ("sigma_s", C.c_int), ("kmask", C.c_int),
-                ("fp32_cut", C.c_int), ("deriv", C.c_int)]
+                ("fp32_cut", C.c_int), ("deriv", C.c_int), ("slater_k", C.c_int)]
 
 
 class _DpdParams(C.Structure):
@@ -97,10 +97,12 @@ class EwaldParams:
     kmask: int = 0
     fp32_cut: int = 0
     deriv: int = 0       # ENUF forces: 0 ik-differentiation (Eq. 24-25), 1 analytic gradient
+    slater_k: int = 0    # Slater smearing: 0 real-space correction, 1 k-space form factor
 
     def c(self) -> _Params:
         return _Params(self.L, self.alpha, self.r_cut, self.beta, self.kappa,
-                       self.M, self.p, self.sigma_s, self.kmask, self.fp32_cut, self.deriv)
+                       self.M, self.p, self.sigma_s, self.kmask, self.fp32_cut, self.deriv,
+                       self.slater_k)
 
     @property
     def ng(self) -> int:
@@ -206,6 +208,13 @@ def recip_enuf(P: EwaldParams, pos, q, sample=None, want_grid=False, want_h=Fals
                                 _pd(grid), _pd(h), _pi(s), 0 if s is None else s.shape[0]),
            "recip_enuf")
     return F, EW, grid, h
+
+
+def slater_I(P: EwaldParams, r, rho_one=False):
+    """(I(r), I'(r)) of the k-space Slater kernel (orc_slater_I)."""
+    I, dI = C.c_double(), C.c_double()
+    lib().orc_slater_I(C.byref(P.c()), C.c_double(r), int(rho_one), C.byref(I), C.byref(dI))
+    return I.value, dI.value
 
 
 def self_neutral(P: EwaldParams, q):

@@ -105,8 +105,73 @@ double orc_slater_force(double beta, double r) { return orc_B2(beta, r) / (r * r
 /* Pair energy u(r), and f(r) = -du/dr (the corrected Eq. 32).         */
 /* ------------------------------------------------------------------ */
 
+/* Gauss-Legendre nodes and weights on [-1, 1] by Newton's method on P_n
+ * (initial guesses cos(pi (i - 1/4)/(n + 1/2))). */
+#define GL_N 16
+static void gauss_legendre(double* x, double* w)
+{
+    for (int i = 0; i < GL_N; ++i) {
+        double z = cos(M_PI * (i + 0.75) / (GL_N + 0.5)), dp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= GL_N; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = GL_N * (z * p1 - p0) / (z * z - 1.0);
+            const double dz = p1 / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-16) break;
+        }
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+void orc_slater_I(const orc_params* P, double r, int rho_one, double* I, double* dI)
+{
+    double gx[GL_N], gw[GL_N];
+    gauss_legendre(gx, gw);
+    const double a = P->alpha, be = P->beta;
+    /* e^{-k^2/(4 alpha^2)} < 1e-21 beyond kmax; 512 panels of 16 nodes */
+    const double kmax = 2.0 * a * sqrt(50.0);
+    const int npan = 512;
+    const double h = kmax / npan;
+    double si = 0.0, sd = 0.0;
+    for (int pnl = 0; pnl < npan; ++pnl) {
+        const double k0 = pnl * h;
+        for (int t = 0; t < GL_N; ++t) {
+            const double k = k0 + 0.5 * h * (gx[t] + 1.0);
+            double wk = exp(-k * k / (4.0 * a * a));
+            if (!rho_one) {
+                const double c = 1.0 + k * k / (4.0 * be * be);
+                wk /= c * c;
+            }
+            const double kr = k * r;
+            si += 0.5 * h * gw[t] * wk * (r == 0.0 ? 0.0 : sin(kr) / k);
+            sd += 0.5 * h * gw[t] * wk * cos(kr);
+        }
+    }
+    *I = 2.0 / M_PI * si;
+    *dI = 2.0 / M_PI * sd;
+}
+
+/* Reading C real-space pair: u = phi_S(r) - I(r)/r, f = -du/dr. */
+static void real_pair_c(const orc_params* P, double r, double* u, double* f)
+{
+    double I, dI;
+    orc_slater_I(P, r, 0, &I, &dI);
+    *u = orc_slater_energy(P->beta, r) - I / r;
+    *f = orc_slater_force(P->beta, r) + (dI * r - I) / (r * r);
+}
+
 static void real_pair(const orc_params* P, double r, double* u, double* f)
 {
+    if (P->slater_k) {
+        real_pair_c(P, r, u, f);
+        return;
+    }
     const double a = P->alpha;
     double uu = erfc(a * r) / r;
     double ff = erfc(a * r) / (r * r) + (2.0 * a / sqrt(M_PI)) * exp(-a * a * r * r) / r;
@@ -123,7 +188,7 @@ static void real_pair(const orc_params* P, double r, double* u, double* f)
 int orc_real_space(const orc_params* P, int n, const double* pos, const double* q,
                    double* F, double* EW, const int* sample, int nsample)
 {
-    if (n < 0 || P->r_cut > 0.5 * P->L) return ORC_EINVAL;
+    if (n < 0 || P->r_cut > 0.5 * P->L || (P->slater_k && P->beta <= 0.0)) return ORC_EINVAL;
     double* x = wrapped_positions(P, n, pos);
     if (!x) return ORC_ENOMEM;
     const double rc = P->r_cut, kap = P->kappa;
@@ -182,11 +247,22 @@ static int in_mask(const orc_params* P, int kx, int ky, int kz)
 }
 
 /* Ewald influence function of Eq. 18 for integer k: e^{-(pi k)^2/(alpha L)^2}/k^2 */
+/* Slater form factor (1 + k^2/(4 beta^2))^{-2}, k = 2 pi |m| / L, as (1 + t)^{-2} */
+static double slater_t(const orc_params* P, double m2)
+{
+    const double bL = P->beta * P->L;
+    return M_PI * M_PI * m2 / (bL * bL);
+}
 static double influence(const orc_params* P, int kx, int ky, int kz)
 {
     const double k2 = (double)kx * kx + (double)ky * ky + (double)kz * kz;
     const double aL = P->alpha * P->L;
-    return exp(-M_PI * M_PI * k2 / (aL * aL)) / k2;
+    double f = exp(-M_PI * M_PI * k2 / (aL * aL)) / k2;
+    if (P->slater_k) {
+        const double t = 1.0 + slater_t(P, k2);
+        f /= t * t;
+    }
+    return f;
 }
 
 /* Virial weight of one mode: -L d/dL of its energy term over the term. */
@@ -194,7 +270,12 @@ static double virial_weight(const orc_params* P, int kx, int ky, int kz)
 {
     const double k2 = (double)kx * kx + (double)ky * ky + (double)kz * kz;
     const double aL = P->alpha * P->L;
-    return 1.0 - 2.0 * M_PI * M_PI * k2 / (aL * aL);
+    double w = 1.0 - 2.0 * M_PI * M_PI * k2 / (aL * aL);
+    if (P->slater_k) {   /* the form factor depends on L through k = 2 pi |m| / L */
+        const double t = slater_t(P, k2);
+        w -= 4.0 * t / (1.0 + t);
+    }
+    return w;
 }
 
 /* ------------------------------------------------------------------ */
@@ -660,8 +741,15 @@ void orc_self_neutral(const orc_params* P, int n, const double* q, double* out)
         Q += q[i];
     }
     const double V = P->L * P->L * P->L;
-    out[0] = -P->kappa * P->alpha / sqrt(M_PI) * q2;
-    out[1] = -P->kappa * M_PI * Q * Q / (2.0 * V * P->alpha * P->alpha);
+    if (P->slater_k && P->beta > 0.0) {
+        double I, I0;
+        orc_slater_I(P, 0.0, 0, &I, &I0);   /* lim_{r->0} I(r)/r = I'(0) */
+        out[0] = -0.5 * P->kappa * I0 * q2;
+        out[1] = -P->kappa * Q * Q * (M_PI / (P->alpha * P->alpha) + 2.0 * M_PI / (P->beta * P->beta)) / (2.0 * V);
+    } else {
+        out[0] = -P->kappa * P->alpha / sqrt(M_PI) * q2;
+        out[1] = -P->kappa * M_PI * Q * Q / (2.0 * V * P->alpha * P->alpha);
+    }
     out[2] = 3.0 * out[1];
 }
 

@@ -50,7 +50,24 @@ typedef struct {
     int    fp32_cut;/* 1: take pair-cutoff decisions in float, as an FP32 path does */
     int    deriv;   /* ENUF forces: 0 = ik-differentiation (Eq. 24-25); 1 = analytic
                        gradient of the window (one real field, see orc_recip_enuf) */
+    int    slater_k;/* where the Slater smearing enters (Eq. 26-28):
+                       0 = real space only, the correction -(1+beta r)e^{-2 beta r}/r
+                           on the erfc pair term (Sec. 5: B1, B2 applied in real space);
+                       1 = k space: the influence times the Slater form factor
+                           rho(k) = (1 + k^2/(4 beta^2))^{-2} (k = 2 pi |m|/L), the real
+                           space pair kernel phi_S(r) - I(r)/r with
+                           I(r) = (2/pi) int_0^inf rho(k) e^{-k^2/(4 alpha^2)} sin(kr)/k dk,
+                           self term -(kappa/2) lim I(r)/r sum q^2 and background term
+                           -kappa Q^2 (pi/alpha^2 + 2 pi/beta^2)/(2V). Needs beta > 0.
+                       Both give the same total energy for untruncated sums. */
 } orc_params;
+
+/* The radial integral of the k-space Slater kernel and its r-derivative,
+ *   I(r)  = (2/pi) int_0^inf w(k) e^{-k^2/(4 alpha^2)} sin(k r)/k dk,
+ *   I'(r) = (2/pi) int_0^inf w(k) e^{-k^2/(4 alpha^2)} cos(k r) dk,
+ * w(k) = (1 + k^2/(4 beta^2))^{-2}, or w = 1 when rho_one (then I = erf(alpha r)),
+ * by composite Gauss-Legendre quadrature; r = 0 gives I'(0) = lim I(r)/r. */
+void orc_slater_I(const orc_params* P, double r, int rho_one, double* I, double* dI);
 
 /* Position wrapping into [0, L): identity inside, else x - L floor(x/L). */
 double orc_wrap(double x, double L);
