@@ -76,7 +76,16 @@ typedef struct {
                          field h = D F and F_i = -(kappa q_i n/(pi L^2)) sum_l
                          grad Psi(n x_i - l) h(l), the exact derivative of the NFFT
                          energy (one inverse transform instead of three) */
-    int    reserved[5];
+    int    slater_k;  /* where the Slater smearing of Eq. 26-27 enters (needs beta > 0):
+                         0 = the real-space pair term carries the correction
+                             -(1 + beta r) e^{-2 beta r}/r (B1, B2 in real space, Sec. 5);
+                         1 = the influence function carries the Slater form factor
+                             (1 + k^2/(4 beta^2))^{-2} and the real-space kernel is
+                             phi_S(r) - I(r)/r, I(r) = (2/pi) int rho(k) e^{-k^2/(4 alpha^2)}
+                             sin(kr)/k dk, interpolated from a table built at plan time;
+                             self and background terms change to match. Same total
+                             energy for converged sums. */
+    int    reserved[4];
 } enuf_params;
 
 typedef struct enuf_plan_s* enuf_plan_t;

@@ -124,6 +124,59 @@ enuf_status fail(enuf_plan_t p, enuf_status s, const char* fmt, ...) {
     } while (0)
 
 // Derive every size of a plan; no allocation. Returns the device bytes.
+// Radial integrals of the k-space Slater kernel (form factor rho(k) = (1 + k^2/(4 beta^2))^{-2}
+// times the Ewald Gaussian e^{-k^2/(4 alpha^2)}), FP64 on the host:
+//   out[0] = I(r)   = (2/pi) int_0^inf rho e^{..} sin(kr)/k dk
+//   out[1] = I'(r)  = (2/pi) int_0^inf rho e^{..} cos(kr) dk          (r = 0: lim I(r)/r)
+//   out[2] = I''(r) = -(2/pi) int_0^inf rho e^{..} k sin(kr) dk
+// Composite 16-point Gauss-Legendre over [0, 2 alpha sqrt(50)] (the Gaussian is below
+// 1e-21 beyond), 192 panels; the nodes come from Newton's method on P_16.
+struct GaussLegendre16 {
+    double x[16], w[16];
+    GaussLegendre16() {
+        for (int i = 0; i < 16; ++i) {
+            double z = std::cos(M_PI * (i + 0.75) / 16.5), dp = 1.0;
+            for (int it = 0; it < 100; ++it) {
+                double p0 = 1.0, p1 = z;
+                for (int k = 2; k <= 16; ++k) {
+                    const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                    p0 = p1;
+                    p1 = p2;
+                }
+                dp = 16.0 * (z * p1 - p0) / (z * z - 1.0);
+                const double dz = p1 / dp;
+                z -= dz;
+                if (std::fabs(dz) < 1e-16) break;
+            }
+            x[i] = z;
+            w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+        }
+    }
+};
+
+void slater_kernel(double alpha, double beta, double r, double* out) {
+    static const GaussLegendre16 gl;   // thread-safe one-time setup
+    const double* gx = gl.x;
+    const double* gw = gl.w;
+    const double kmax = 2.0 * alpha * std::sqrt(50.0);
+    const int npan = 192;
+    const double h = kmax / npan;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int pnl = 0; pnl < npan; ++pnl)
+        for (int t = 0; t < 16; ++t) {
+            const double k = (pnl + 0.5 * (gx[t] + 1.0)) * h;
+            const double c = 1.0 + k * k / (4.0 * beta * beta);
+            const double wk = 0.5 * h * gw[t] * std::exp(-k * k / (4.0 * alpha * alpha)) / (c * c);
+            const double sn = std::sin(k * r), cs = std::cos(k * r);
+            s0 += wk * sn / k;
+            s1 += wk * cs;
+            s2 -= wk * k * sn;
+        }
+    out[0] = 2.0 / M_PI * s0;
+    out[1] = 2.0 / M_PI * s1;
+    out[2] = 2.0 / M_PI * s2;
+}
+
 enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* bytes) {
     if (n_max < 0) return fail(plan, ENUF_ERR_INVALID, "n_max < 0");
     if (!(P.L > 0) || !std::isfinite(P.L)) return fail(plan, ENUF_ERR_INVALID, "L must be > 0");
@@ -135,6 +188,8 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
     if (P.prec != ENUF_FP64 && P.prec != ENUF_FP32) return fail(plan, ENUF_ERR_INVALID, "bad precision");
     if (P.kmask != 0 && P.kmask != 1) return fail(plan, ENUF_ERR_INVALID, "kmask must be 0 or 1");
     if (P.deriv != 0 && P.deriv != 1) return fail(plan, ENUF_ERR_INVALID, "deriv must be 0 or 1");
+    if (P.slater_k != 0 && P.slater_k != 1) return fail(plan, ENUF_ERR_INVALID, "slater_k must be 0 or 1");
+    if (P.slater_k && !(P.beta > 0)) return fail(plan, ENUF_ERR_INVALID, "slater_k = 1 needs beta > 0");
     const int M = P.M == 0 ? grid_rule(P.L) : P.M;
     if (M < 4 || (M & 1)) return fail(plan, ENUF_ERR_INVALID, "M must be even and >= 4 (got %d)", M);
     const int n = P.sigma_s * M;
@@ -225,8 +280,22 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
     g.pref = P.deriv ? -P.kappa * n / (M_PI * P.L * P.L) : P.kappa * 2.0 / (P.L * P.L);
     g.c2a = 2.0 * P.alpha / std::sqrt(M_PI);
     g.xmaxf = largest_float_below(P.L);
-    g.c_self = -P.kappa * P.alpha / std::sqrt(M_PI);
-    g.c_neut = -P.kappa * M_PI / (2.0 * P.L * P.L * P.L * P.alpha * P.alpha);
+    g.slater_k = P.slater_k;
+    if (P.slater_k) {
+        // kernel table on [0, r_c]: quintic Hermite nodes every <= 0.004 (interpolation
+        // error of I' ~ h^5, far below FP64 parity); I'(0) = lim I(r)/r gives the self term
+        g.kn = std::max(64, (int)std::ceil(P.r_cut / 0.004));
+        g.kh = P.r_cut / g.kn;
+        g.kinv = g.kn / P.r_cut;
+        double i0[3];
+        slater_kernel(P.alpha, P.beta, 0.0, i0);
+        g.c_self = -0.5 * P.kappa * i0[1];
+        g.c_neut = -P.kappa * (M_PI / (P.alpha * P.alpha) + 2.0 * M_PI / (P.beta * P.beta)) /
+                   (2.0 * P.L * P.L * P.L);
+    } else {
+        g.c_self = -P.kappa * P.alpha / std::sqrt(M_PI);
+        g.c_neut = -P.kappa * M_PI / (2.0 * P.L * P.L * P.L * P.alpha * P.alpha);
+    }
     g.c_recip = P.kappa / (2.0 * M_PI * P.L);
     g.rhi = (float)g.ratio;
     g.rlo = (float)(g.ratio - (double)g.rhi);
@@ -259,7 +328,8 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
            o_s1 = take((size_t)n * nc1 * n * csz), o_s2 = take((size_t)nc1 * g.K * n * csz),
            o_s3 = take((size_t)g.nf * n * nc1 * g.K * csz), o_s4 = take((size_t)g.nf * n * n * nc1 * csz),
            o_h = take(g.nf * n3 * esz), o_tab = take(ntab * 8), o_tabv = take(ntab * 8), o_tabr = take(ntab * esz),
-           o_tw = take((size_t)n * csz), o_part = take((size_t)npart * 8), o_E = take(16 * 8);
+           o_tw = take((size_t)n * csz), o_part = take((size_t)npart * 8), o_E = take(16 * 8),
+           o_ktab = take(g.slater_k ? (size_t)(g.kn + 1) * 3 * esz : 0);
     if (bytes) *bytes = off;
     if (plan) {
         plan->P = P;
@@ -278,7 +348,7 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
         w.sq = (void*)o_sq; w.sw = (void*)o_sw; w.sb = (int*)o_sb; w.grid = (void*)o_grid;
         w.spec1 = (void*)o_s1; w.spec2 = (void*)o_s2; w.spec3 = (void*)o_s3; w.spec4 = (void*)o_s4;
         w.h = (void*)o_h; w.tab = (double*)o_tab; w.tabv = (double*)o_tabv; w.tabr = (void*)o_tabr;
-        w.tw = (void*)o_tw; w.part = (double*)o_part; w.Edev = (double*)o_E;
+        w.tw = (void*)o_tw; w.part = (double*)o_part; w.Edev = (double*)o_E; w.ktab = (void*)o_ktab;
         plan->w = w;
         plan->dbytes = off;
     }
@@ -295,7 +365,8 @@ void bind(enuf_plan_t p) {
     w.sq = at(w.sq); w.sw = at(w.sw); w.sb = at(w.sb); w.grid = at(w.grid);
     w.spec1 = at(w.spec1); w.spec2 = at(w.spec2); w.spec3 = at(w.spec3); w.spec4 = at(w.spec4);
     w.h = at(w.h); w.tab = at(w.tab); w.tabv = at(w.tabv); w.tabr = at(w.tabr);
-    w.tw = at(w.tw); w.part = at(w.part); w.Edev = at(w.Edev);
+    w.tw = at(w.tw); w.part = at(w.part); w.Edev = at(w.Edev); w.ktab = at(w.ktab);
+    p->g.ktab = p->g.slater_k ? w.ktab : nullptr;
 }
 
 // FP64 influence x deconvolution table over the half space kx = 0..nc:
@@ -321,13 +392,39 @@ enuf_status upload_tables(enuf_plan_t plan) {
                 if (k2 == 0) continue;
                 if (g.kmask == 1 && k2 > (double)nc * nc) continue;
                 const double cc = c[kx + nc] * c[iy] * c[iz];
-                const double d = std::exp(-M_PI * M_PI * k2 / (aL * aL)) / k2 / (cc * cc);
+                double d = std::exp(-M_PI * M_PI * k2 / (aL * aL)) / k2 / (cc * cc);
+                double vw = 1.0 - 2.0 * M_PI * M_PI * k2 / (aL * aL);   // -L d/dL per mode
+                if (g.slater_k) {   // form factor (1 + t)^{-2}, t = (pi |m| / (beta L))^2
+                    const double bL = g.beta * g.L;
+                    const double t = M_PI * M_PI * k2 / (bL * bL);
+                    d /= (1.0 + t) * (1.0 + t);
+                    vw -= 4.0 * t / (1.0 + t);
+                }
                 const size_t id = ((size_t)kx * K + iy) * K + iz;
                 D[id] = d;
-                Dv[id] = d * (1.0 - 2.0 * M_PI * M_PI * k2 / (aL * aL));
+                Dv[id] = d * vw;
             }
     CU(cudaMemcpy(plan->w.tab, D.data(), ntab * 8, cudaMemcpyHostToDevice));
     CU(cudaMemcpy(plan->w.tabv, Dv.data(), ntab * 8, cudaMemcpyHostToDevice));
+    if (g.slater_k) {
+        // J(r) = B1(r) - I(r) and its first two derivatives, formed in FP64 (the two
+        // terms nearly cancel over the cutoff range): u = J/r, f = (J - J' r)/r^2
+        std::vector<double> kt((size_t)(g.kn + 1) * 3);
+        for (int j = 0; j <= g.kn; ++j) {
+            const double r = j * g.kh, be = g.beta, e = std::exp(-2.0 * be * r);
+            double I[3];
+            slater_kernel(g.alpha, be, r, I);
+            kt[3 * (size_t)j] = 1.0 - (1.0 + be * r) * e - I[0];
+            kt[3 * (size_t)j + 1] = be * (1.0 + 2.0 * be * r) * e - I[1];
+            kt[3 * (size_t)j + 2] = -4.0 * be * be * be * r * e - I[2];
+        }
+        if (plan->prec == ENUF_FP32) {
+            std::vector<float> ktf(kt.begin(), kt.end());
+            CU(cudaMemcpy(plan->w.ktab, ktf.data(), ktf.size() * 4, cudaMemcpyHostToDevice));
+        } else {
+            CU(cudaMemcpy(plan->w.ktab, kt.data(), kt.size() * 8, cudaMemcpyHostToDevice));
+        }
+    }
     std::vector<double> tw(2 * n);
     for (int t = 0; t < n; ++t) {
         tw[2 * t] = std::cos(2.0 * M_PI * t / n);

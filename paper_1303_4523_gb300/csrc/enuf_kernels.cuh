@@ -929,11 +929,37 @@ constexpr int kRealCap = 2048;     // staged beads (x, y, z, q)
 constexpr int kRealHalo = 1024;    // halo tiles (stencil up to 9 x 9 x 9 + 1 for the prefix)
 
 // Pair energy u(r) and radial force f(r) = -du/dr of the real-space sum:
-// erfc(alpha r)/r minus the Slater correction (1 + beta r) e^{-2 beta r}/r.
+// erfc(alpha r)/r minus the Slater correction (1 + beta r) e^{-2 beta r}/r;
+// with the Slater form factor in k space (kt != null), phi_S(r) - I(r)/r =
+// J(r)/r with J = B1 - I from the quintic Hermite table kt[j] = (J, J', J'')
+// at r = j h, and f = (J - J' r)/r^2.
 template <typename R>
-__device__ __forceinline__ void real_pair(R r2, R al, R c2a, R be, bool slater, R& u, R& fr_over_r, R& f_r) {
+__device__ __forceinline__ void real_pair(R r2, R al, R c2a, R be, bool slater, R& u, R& fr_over_r, R& f_r,
+                                          const R* __restrict__ kt = nullptr, int kn = 0, R kinv = 0, R kh = 0) {
     const R ir = r_rsqrt(r2);
     const R r = r2 * ir;
+    if (kt) {
+        const R x = r * kinv;
+        int j = (int)x;
+        j = j < 0 ? 0 : (j >= kn ? kn - 1 : j);
+        const R t = x - (R)j;
+        const R* a = kt + 3 * j;
+        const R y0 = a[0], d0 = a[1] * kh, s0 = a[2] * kh * kh;
+        const R y1 = a[3], d1 = a[4] * kh, s1 = a[5] * kh * kh;
+        const R t2 = t * t, t3 = t2 * t, t4 = t3 * t, t5 = t4 * t;
+        const R J = y0 * ((R)1 - (R)10 * t3 + (R)15 * t4 - (R)6 * t5) + d0 * (t - (R)6 * t3 + (R)8 * t4 - (R)3 * t5) +
+                    s0 * (R)0.5 * (t2 - (R)3 * t3 + (R)3 * t4 - t5) + y1 * ((R)10 * t3 - (R)15 * t4 + (R)6 * t5) +
+                    d1 * ((R)-4 * t3 + (R)7 * t4 - (R)3 * t5) + s1 * (R)0.5 * (t3 - (R)2 * t4 + t5);
+        const R dJ = (y0 * ((R)-30 * t2 + (R)60 * t3 - (R)30 * t4) + d0 * ((R)1 - (R)18 * t2 + (R)32 * t3 - (R)15 * t4) +
+                      s0 * (R)0.5 * ((R)2 * t - (R)9 * t2 + (R)12 * t3 - (R)5 * t4) +
+                      y1 * ((R)30 * t2 - (R)60 * t3 + (R)30 * t4) + d1 * ((R)-12 * t2 + (R)28 * t3 - (R)15 * t4) +
+                      s1 * (R)0.5 * ((R)3 * t2 - (R)8 * t3 + (R)5 * t4)) * kinv;
+        const R ff = (J - dJ * r) * ir * ir;
+        u = J * ir;
+        fr_over_r = ff * ir;
+        f_r = ff * r;
+        return;
+    }
     const R ar = al * r;
     const R ec = r_erfc(ar);
     R uu = ec * ir;
@@ -951,13 +977,13 @@ __device__ __forceinline__ void real_pair(R r2, R al, R c2a, R be, bool slater, 
 
 // One lane per queued pair (lanes < m).
 template <typename R, typename V>
-__device__ __forceinline__ void real_drain(const V* qu, int m, int lane, R qi, R kap, R al, R c2a, R be, bool slater,
-                                           R& fx, R& fy, R& fz, R& eacc, R& wacc) {
+__device__ __forceinline__ void real_drain(const Geo& g, const V* qu, int m, int lane, R qi, R kap, R al, R c2a, R be,
+                                           bool slater, R& fx, R& fy, R& fz, R& eacc, R& wacc) {
     if (lane < m) {
         const V e = qu[lane];
         const R r2 = dist2(e.x, e.y, e.z);
         R u, fo, fr;
-        real_pair<R>(r2, al, c2a, be, slater, u, fo, fr);
+        real_pair<R>(r2, al, c2a, be, slater, u, fo, fr, static_cast<const R*>(g.ktab), g.kn, (R)g.kinv, (R)g.kh);
         const R qq = kap * qi * e.w;
         fx += qq * fo * e.x;
         fy += qq * fo * e.y;
@@ -1029,7 +1055,7 @@ __device__ __forceinline__ void real_beads(const Geo& g, int c0, int c1, int sel
             if (cnt >= 32 || (last && cnt > 0)) {
                 const int m = min(cnt, 32);
                 __syncwarp();
-                real_drain<R, V>(qu, m, lane, pi.w, kap, al, c2a, be, slater, fx, fy, fz, eacc, wacc);
+                real_drain<R, V>(g, qu, m, lane, pi.w, kap, al, c2a, be, slater, fx, fy, fz, eacc, wacc);
                 __syncwarp();
                 if (lane < cnt - m) qu[lane] = qu[m + lane];
                 __syncwarp();

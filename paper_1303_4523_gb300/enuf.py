@@ -35,7 +35,7 @@ class enuf_params(C.Structure):
     _fields_ = [("L", C.c_double), ("alpha", C.c_double), ("r_cut", C.c_double),
                 ("beta", C.c_double), ("kappa", C.c_double), ("M", C.c_int), ("p", C.c_int),
                 ("sigma_s", C.c_int), ("kmask", C.c_int), ("prec", C.c_int), ("tile", C.c_int),
-                ("deriv", C.c_int), ("reserved", C.c_int * 5)]
+                ("deriv", C.c_int), ("slater_k", C.c_int), ("reserved", C.c_int * 4)]
 
 
 class enuf_plan_info(C.Structure):
@@ -108,10 +108,11 @@ def _check(status, handle=None, what=""):
 
 
 def make_params(L, alpha, r_cut, beta, kappa, M=0, p=4, sigma_s=2, kmask=0,
-                prec="fp64", tile=0, deriv=0) -> enuf_params:
+                prec="fp64", tile=0, deriv=0, slater_k=0) -> enuf_params:
     pr = {"fp64": ENUF_FP64, "fp32": ENUF_FP32}[prec] if isinstance(prec, str) else int(prec)
     return enuf_params(float(L), float(alpha), float(r_cut), float(beta), float(kappa), int(M),
-                       int(p), int(sigma_s), int(kmask), pr, int(tile), int(deriv), (C.c_int * 5)())
+                       int(p), int(sigma_s), int(kmask), pr, int(tile), int(deriv), int(slater_k),
+                       (C.c_int * 4)())
 
 
 def _ptr(x):

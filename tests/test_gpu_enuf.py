@@ -320,3 +320,42 @@ def test_full_size_gradient_mode_sampled(enuf, prec):
         assert abs(E[k] - Er[k]) < t["E"] * scale, (k, E, Er)
     assert np.all(F[q == 0] == 0.0)
     plan.close()
+
+
+SLATER_CASES = [n for n in CASES if (CASES[n][0] if isinstance(CASES[n][0], dict) else {"beta": 1.0}).get("beta", 1.0) > 0]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", SLATER_CASES)
+def test_kspace_slater_parity(enuf, name, prec):
+    """Slater form factor in k space with the tabulated real-space kernel
+    against the oracle's k-space Slater reading (radial quadrature per pair)."""
+    P, pos, q = _case(name)
+    P = dict(P, slater_k=1)
+    pos, q = _inputs(prec, pos, q)
+    plan, F, E, Wv = _gpu(enuf, prec, P, pos, q)
+    Fr, Er, Wr = _ref(prec, P, pos, q)
+    _check(prec, F, E, Wv, Fr, Er, Wr)
+    plan.close()
+
+
+def test_kspace_slater_needs_beta(enuf):
+    with pytest.raises(enuf.EnufError):
+        enuf.Plan(enuf.make_params(L=8.0, alpha=1.0, r_cut=3.0, beta=0.0, kappa=1.0, M=16, p=4, slater_k=1), 10)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_full_size_kspace_slater_sampled(enuf, prec):
+    s = W.polyelectrolyte()
+    P = dict(L=s.L, M=s.M, slater_k=1, **s.params)
+    pos, q = _inputs(prec, s.pos, s.q)
+    plan, F, E, Wv = _gpu(enuf, prec, P, pos, q)
+    rng = np.random.default_rng(29)
+    sample = np.sort(rng.choice(np.nonzero(q)[0], 128, replace=False))
+    Fr, Er, Wr = _ref(prec, P, pos, q, sample=sample)
+    t = TOL[prec]
+    assert _rel_rms(F[sample], Fr) < t["F"]
+    scale = max(abs(Er[0]), abs(Er[1]))
+    for k in range(4):
+        assert abs(E[k] - Er[k]) < t["E"] * scale, (k, E, Er)
+    plan.close()
