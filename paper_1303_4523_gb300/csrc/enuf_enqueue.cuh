@@ -102,7 +102,7 @@ cudaError_t enqueue_enuf(const Geo& g, const FftShape& fs, const FftPlanDev& fp,
     cudaEventRecord(evFork, s0);
     cudaStreamWaitEvent(s1, evFork, 0);
     rec(ev, 4, true, s1);
-    const int real_smem = (kRealCap + (kRealThreads / 32) * 64) * (int)sizeof(V) + (2 * kRealHalo + 1) * 4;
+    const int real_smem = real_smem_bytes<R>();
     launch(false, k_real<R>, w.nblk_real, kRealThreads, real_smem, s1, g, (const int*)w.tstart, (const V*)sq,
            (const V*)sw, F, w.part + w.off_real);
     rec(ev, 4, false, s1);

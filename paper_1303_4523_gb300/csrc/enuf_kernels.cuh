@@ -927,6 +927,13 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Geo g, const int* __r
 constexpr int kRealThreads = 256;
 constexpr int kRealCap = 2048;     // staged beads (x, y, z, q)
 constexpr int kRealHalo = 1024;    // halo tiles (stencil up to 9 x 9 x 9 + 1 for the prefix)
+// FP64 also stages a float copy of the positions for the cutoff pre-test
+template <typename R> __host__ __device__ constexpr int real_cap() { return sizeof(R) == 8 ? 1536 : kRealCap; }
+template <typename R>
+constexpr int real_smem_bytes() {
+    return (real_cap<R>() + (kRealThreads / 32) * 64) * (int)sizeof(typename V4<R>::T) +
+           (sizeof(R) == 8 ? real_cap<R>() * (int)sizeof(float4) : 0) + (2 * kRealHalo + 1) * 4;
+}
 
 // Pair energy u(r) and radial force f(r) = -du/dr of the real-space sum:
 // erfc(alpha r)/r minus the Slater correction (1 + beta r) e^{-2 beta r}/r;
@@ -1005,12 +1012,18 @@ __device__ __forceinline__ void halo_dim(int t, int rs, int ntd, int& lo, int& c
 // the halo prefix.
 template <typename R, bool STAGED>
 __device__ __forceinline__ void real_beads(const Geo& g, int c0, int c1, int selfbase, int total, int nh,
-                                           const typename V4<R>::T* stg, const int* hoff, const int* gst,
-                                           const typename V4<R>::T* __restrict__ sq,
+                                           const typename V4<R>::T* stg, const float4* stgf, const int* hoff,
+                                           const int* gst, const typename V4<R>::T* __restrict__ sq,
                                            const typename V4<R>::T* __restrict__ sw, typename V4<R>::T* qu,
                                            R* __restrict__ F, R& eacc, R& wacc) {
     using V = typename V4<R>::T;
     constexpr int NW = kRealThreads / 32;
+    // FP64: the cutoff test r^2 < r_c^2 runs on the float copy first; candidates
+    // above a band that covers the float error (positions and L rounded to float,
+    // |r2f - r2| <= ~1.5e-6 L r_c) are out, the rest are decided in double
+    constexpr bool PRE = STAGED && sizeof(R) == 8;
+    const float Lf = (float)g.L, hLf = (float)(0.5 * g.L);
+    const float r2hi = (float)(g.rc * g.rc) * (1.0f + 1e-4f) + 4e-6f * (float)(g.L * g.rc) + 1e-6f;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const R L = (R)g.L, hL = (R)(0.5 * g.L);
     const R rc2 = (R)(g.rc * g.rc);
@@ -1018,6 +1031,7 @@ __device__ __forceinline__ void real_beads(const Geo& g, int c0, int c1, int sel
     const bool slater = g.beta > 0.0;
     for (int s = c0 + warp; s < c1; s += NW) {
         const V pi = sq[s];
+        const float4 pif = make_float4((float)pi.x, (float)pi.y, (float)pi.z, 0.f);
         const int self = selfbase + (s - c0);
         R fx = 0, fy = 0, fz = 0;
         int cnt = 0;
@@ -1029,7 +1043,15 @@ __device__ __forceinline__ void real_beads(const Geo& g, int c0, int c1, int sel
                 const int f = it * 32 + lane;
                 bool hit = false;
                 R dx = 0, dy = 0, dz = 0, qj = 0;
-                if (f < total && f != self) {
+                bool cand = f < total && f != self;
+                if (PRE && cand) {
+                    const float4 b = stgf[f];
+                    const float rx = min_image(pif.x, b.x, Lf, hLf);
+                    const float ry = min_image(pif.y, b.y, Lf, hLf);
+                    const float rz = min_image(pif.z, b.z, Lf, hLf);
+                    cand = dist2(rx, ry, rz) <= r2hi;
+                }
+                if (cand) {
                     V pj;
                     if (STAGED) {
                         pj = stg[f];
@@ -1089,9 +1111,11 @@ __global__ void __launch_bounds__(kRealThreads) k_real(Geo g, const int* __restr
     using V = typename V4<R>::T;
     constexpr int NW = kRealThreads / 32;
     extern __shared__ __align__(16) unsigned char smraw[];
-    V* stg = reinterpret_cast<V*>(smraw);                       // [kRealCap]
-    V* queue = stg + kRealCap;                                  // [NW][64]
-    int* hoff = reinterpret_cast<int*>(queue + NW * 64);        // [kRealHalo + 1]
+    constexpr int CAP = real_cap<R>();
+    V* stg = reinterpret_cast<V*>(smraw);                       // [CAP]
+    V* queue = stg + CAP;                                       // [NW][64]
+    float4* stgf = reinterpret_cast<float4*>(queue + NW * 64);  // [CAP] float positions (FP64 only)
+    int* hoff = reinterpret_cast<int*>(stgf + (sizeof(R) == 8 ? CAP : 0));   // [kRealHalo + 1]
     int* gst = hoff + kRealHalo + 1;                            // [kRealHalo]
     __shared__ int wtot[NW];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1145,7 +1169,7 @@ __global__ void __launch_bounds__(kRealThreads) k_real(Geo g, const int* __restr
         }
         if (tid == 0) hoff[nh] = total;
         __syncthreads();
-        const bool staged = total <= kRealCap;
+        const bool staged = total <= CAP;
         if (staged) {
             for (int f = tid; f < total; f += blockDim.x) {
                 int lo = 0, hi = nh;   // last h with hoff[h] <= f
@@ -1153,7 +1177,9 @@ __global__ void __launch_bounds__(kRealThreads) k_real(Geo g, const int* __restr
                     const int mid = (lo + hi) >> 1;
                     if (hoff[mid] <= f) lo = mid; else hi = mid;
                 }
-                stg[f] = sq[gst[lo] + f - hoff[lo]];
+                const V v = sq[gst[lo] + f - hoff[lo]];
+                stg[f] = v;
+                if (sizeof(R) == 8) stgf[f] = make_float4((float)v.x, (float)v.y, (float)v.z, 0.f);
             }
         }
         __syncthreads();
@@ -1161,9 +1187,9 @@ __global__ void __launch_bounds__(kRealThreads) k_real(Geo g, const int* __restr
         const int c0 = tstart[tile], c1 = tstart[tile + 1];
         const int hc = (((tz - zlo + g.ntd) % g.ntd) * yc + (ty - ylo + g.ntd) % g.ntd) * xc + (tx - xlo + g.ntd) % g.ntd;
         if (staged)
-            real_beads<R, true>(g, c0, c1, hoff[hc], total, nh, stg, hoff, gst, sq, sw, qu, F, eacc, wacc);
+            real_beads<R, true>(g, c0, c1, hoff[hc], total, nh, stg, stgf, hoff, gst, sq, sw, qu, F, eacc, wacc);
         else
-            real_beads<R, false>(g, c0, c1, hoff[hc], total, nh, stg, hoff, gst, sq, sw, qu, F, eacc, wacc);
+            real_beads<R, false>(g, c0, c1, hoff[hc], total, nh, stg, stgf, hoff, gst, sq, sw, qu, F, eacc, wacc);
         __syncthreads();
     }
     double e = (double)eacc, w = (double)wacc;
