@@ -200,20 +200,31 @@ def run_ours(args, rank, world, dist):
     # end to end through the public API: host state in (pinned), one step, host state out
     e2e = e2e_run(args, s, dp, P, torch, enuf)
 
-    # roofline of the dominant kernel (FP32 path)
+    # roofline of the dominant kernel of the FP32 step (the DPD pair kernel, the
+    # largest share of the launch list): ALU-bound, algorithmic work = the pairs
+    # within the DPD cutoff x OPS_PER_PAIR lane operations
     plan = enuf.Plan(enuf.make_params(prec="fp32", **P), s.N)
     info = plan.info
     plan.close()
     ab = algorithmic_bytes(info, s.n_charged, s.N, 4)
     means = {k: (sum(v) / len(v) if v else 0.0) for k, v in stage32.items()}
-    single = {k: means[k] for k in ("spread", "gather", "real", "dpd")}
-    dom = max(single, key=single.get)
-    achieved = ab[dom] / (means[dom] * 1e-3) / 1e9 if means[dom] > 0 else 0.0
-    traffic = _profiled_traffic(dom)
-    roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
-            "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
-            "peak_kind": peak_kind, "stage_ms": {k: round(v, 5) for k, v in means.items()},
-            "stage_bytes": ab, "note": "working set ~35 MB < L2: L2 flushed between steps, intermediates L2-resident"}
+    npairs, how = dpd_pair_count(s)
+    sm_mhz = clk32.get("sm_mhz") or 2070.0
+    peak_ops = ALU_LANES * sm_mhz * 1e6 / 1e12
+    t_dpd = means["dpd"] * 1e-3
+    achieved = npairs * OPS_PER_PAIR / t_dpd / 1e12 if t_dpd > 0 else 0.0
+    hbm = {k: {"ms": round(means[k], 5), "GBps": round(ab[k] / (means[k] * 1e-3) / 1e9, 1),
+               "frac": round(ab[k] / (means[k] * 1e-3) / 1e9 / peaks["hbm_gbs"], 4)}
+           for k in ("spread", "fft", "gather") if means[k] > 0}
+    roof = {"bound": "alu", "kernel": "k_dpd", "achieved": round(achieved, 4), "peak": round(peak_ops, 2),
+            "unit": "Tops/s", "frac": round(achieved / peak_ops, 4), "traffic": _profiled_traffic("k_dpd"),
+            "peak_kind": f"derived: {ALU_LANES // 128} SMs x 128 lanes x {sm_mhz:.0f} MHz (sampled), 1 op/lane/clock",
+            "work": {"pairs": npairs, "pairs_from": how, "ops_per_pair": OPS_PER_PAIR,
+                     "algorithmic_bytes": ab["dpd"]},
+            "stage_ms": {k: round(v, 5) for k, v in means.items()},
+            "hbm_stages": {"peak_gbs": peaks["hbm_gbs"], "peak_kind": peak_kind, "stages": hbm,
+                           "note": "ENUF working set ~35 MB < L2: L2 flushed between steps, intermediates "
+                                   "L2-resident; HBM-scale fractions are in --mode sizes"}}
 
     srt = sorted(per32)
     p50 = srt[len(srt) // 2]
@@ -277,16 +288,37 @@ def e2e_run(args, s, dp, P, torch, enuf):
             "d2h_bytes_per_step": nb + 8 * 16, "ms_per_step": round(1000 * dt / steps, 4), "steps": steps}
 
 
+# DPD pair work: Eq. 3-7 arithmetic (distance, weights, dissipative and random
+# terms, forces on both beads) ~40 FP32 operations, plus the Philox4x32-10 draw
+# of theta_ij, 10 rounds of 2 wide multiplies, 2 three-way xors and 2 key adds.
+OPS_PER_PAIR = 100
+ALU_LANES = 152 * 128      # SMs x FP32/INT32 lanes
+
+
+def dpd_pair_count(s):
+    """Pairs within the DPD cutoff 1 in the initial configuration (periodic)."""
+    try:
+        from scipy.spatial import cKDTree
+    except ImportError:
+        rho = s.N / s.L ** 3
+        return int(round(s.N * rho * 2.0 * math.pi / 3.0)), "estimated N rho 2 pi/3"
+    t = cKDTree(np.mod(s.pos, s.L), boxsize=s.L)
+    return int(len(t.query_pairs(1.0, output_type="ndarray"))), "counted (k-d tree)"
+
+
 def _profiled_traffic(kernel):
-    """DRAM bytes per launch of the dominant kernel from the committed ncu
-    summary, when it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    """DRAM bytes per launch of `kernel` from the committed ncu summary
+    (profiles/dram_traffic_poly81k.md, rows `| kernel | bytes |`), or None."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic_poly81k.md")
     try:
         with open(path) as fh:
-            d = json.load(fh)
-        return d.get(kernel)
+            for line in fh:
+                f = [x.strip() for x in line.strip().strip("|").split("|")]
+                if len(f) >= 2 and f[0] == kernel:
+                    return int(float(f[1]))
     except (OSError, ValueError):
         return None
+    return None
 
 
 def cpu_oracle_eval(s, dp, P, stride):
