@@ -122,6 +122,23 @@ def algorithmic_bytes(info, nq, N, esz, nf=3):
     }
 
 
+def max_over_ranks(dist, totals, device):
+    """Timed totals (ms) of this rank -> the maximum over all ranks (the job
+    ends when its slowest replica does); identity without a process group."""
+    if dist is None:
+        return list(totals)
+    import torch
+    t = torch.tensor(list(totals), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_throughput(world, steps, tot_ms):
+    """Whole-job force evaluations per second: every replica ran `steps` steps
+    (weak scaling, one system per GPU) within the slowest rank's time."""
+    return round(world * 1000.0 * steps / tot_ms, 2)
+
+
 def run_ours(args, rank, world, dist):
     import torch
 
@@ -188,12 +205,7 @@ def run_ours(args, rank, world, dist):
     # the same step with gradient-mode reciprocal forces (one inverse transform)
     perg, _, clkg, _, Eg, _ = run_prec("fp32", steps64, args.warmup, False, deriv=1)
 
-    tot32 = sum(per32)
-    tot64 = sum(per64)
-    if dist is not None:
-        t = torch.tensor([tot32, tot64], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot32, tot64 = t.tolist()
+    tot32, tot64, totg = max_over_ranks(dist, [sum(per32), sum(per64), sum(perg)], "cuda")
     ms32 = tot32 / args.steps
     ms64 = tot64 / steps64
 
@@ -231,7 +243,7 @@ def run_ours(args, rank, world, dist):
     p99 = srt[min(len(srt) - 1, int(math.ceil(0.99 * len(srt))) - 1)]
     s64 = sorted(per64)
     out = {
-        "metric": METRIC, "value": round(world * 1000.0 * args.steps / tot32, 2), "unit": UNIT,
+        "metric": METRIC, "value": job_throughput(world, args.steps, tot32), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms32, 5),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded polyelectrolyte box)",
@@ -239,12 +251,12 @@ def run_ours(args, rank, world, dist):
                    "tile": info.tile, "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{world}"},
         "latency_ms": {"p50": round(p50, 5), "p99": round(p99, 5), "mean": round(ms32, 5)},
-        "fp64": {"value": round(world * 1000.0 * steps64 / tot64, 2), "ms_per_step": round(ms64, 5),
+        "fp64": {"value": job_throughput(world, steps64, tot64), "ms_per_step": round(ms64, 5),
                  "steps": steps64, "p50": round(s64[len(s64) // 2], 5),
                  "p99": round(s64[min(len(s64) - 1, int(math.ceil(0.99 * len(s64))) - 1)], 5),
                  "clocks": clk64},
-        "fp32_gradient_mode": {"value": round(world * 1000.0 * len(perg) / sum(perg), 2),
-                               "ms_per_step": round(sum(perg) / len(perg), 5),
+        "fp32_gradient_mode": {"value": job_throughput(world, len(perg), totg),
+                               "ms_per_step": round(totg / len(perg), 5),
                                "p50": round(sorted(perg)[len(perg) // 2], 5), "steps": len(perg),
                                "note": "reciprocal forces as the gradient of the window (deriv = 1)"},
         "fp32_over_fp64": round(ms64 / ms32, 2),
