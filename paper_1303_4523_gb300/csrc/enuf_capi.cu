@@ -489,7 +489,7 @@ enuf_status capture_eval(enuf_plan_t plan, int n, const void* pos, const void* q
         return st;
     }
     if (e != cudaSuccess) return fail(plan, ENUF_ERR_CUDA, "capture: %s", cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&plan->gexec, graph, 0);
+    e = cudaGraphInstantiateWithFlags(&plan->gexec, graph, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return fail(plan, ENUF_ERR_CUDA, "instantiate: %s", cudaGetErrorString(e));
     plan->g_n = n;
@@ -776,7 +776,7 @@ enuf_status capture_step(dpd_system_t sys) {
         return st;
     }
     if (e != cudaSuccess) return fail(plan, ENUF_ERR_CUDA, "capture: %s", cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&sys->gstep, graph, 0);
+    e = cudaGraphInstantiateWithFlags(&sys->gstep, graph, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return fail(plan, ENUF_ERR_CUDA, "instantiate: %s", cudaGetErrorString(e));
     sys->g_timing = plan->ev.on;
@@ -1015,7 +1015,7 @@ enuf_status enuf_batch_energy_forces(enuf_batch_t b, const void* const* pos, con
             return st;
         }
         if (e != cudaSuccess) return ENUF_ERR_CUDA;
-        e = cudaGraphInstantiate(&b->gexec, graph, 0);
+        e = cudaGraphInstantiateWithFlags(&b->gexec, graph, cudaGraphInstantiateFlagUseNodePriority);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) return ENUF_ERR_CUDA;
         b->g_pos.assign(pos, pos + ns);

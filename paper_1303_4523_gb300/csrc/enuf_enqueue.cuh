@@ -22,18 +22,36 @@ inline void rec(Events* ev, int stage, bool start, cudaStream_t s) {
 // with griddepcontrol.wait, so it touches no memory before that kernel has
 // completed. pdl is off for a kernel whose stream predecessor is not a kernel
 // (an event wait, an event record, the start of a graph).
+//
+// Priority: the reciprocal chain (binning, spreading, FFT passes, gather,
+// integrator, totals) is the critical path of a step; its kernels launch at
+// the device's greatest priority and the DPD / real-space branch at the
+// lowest, so the block scheduler gives the chain its CTAs first and the other
+// branch fills the gaps (graphs are instantiated with node priorities).
+inline int launch_priority(bool critical) {
+    static const int greatest = [] {
+        int least = 0, great = 0;
+        cudaDeviceGetStreamPriorityRange(&least, &great);
+        return great;
+    }();
+    return critical ? greatest : 0;
+}
+
 template <typename... P, typename... A>
-inline void launch(bool pdl, void (*k)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A&&... args) {
+inline void launch(bool pdl, bool critical, void (*k)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                   A&&... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = block;
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributePriority;
+    at[0].val.priority = launch_priority(critical);
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
-    cfg.numAttrs = pdl ? 1 : 0;
+    cfg.numAttrs = pdl ? 2 : 1;
     cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
 }
 
@@ -70,12 +88,12 @@ int spread_smem(const Geo& g) {
 template <typename R>
 void enqueue_bin(const Geo& g, const Work& w, int N, const R* pos, const R* q, R* Fzero, cudaStream_t s, bool pdl) {
     using V = typename V4<R>::T;
-    launch(false, k_bin_count<R>, g.nbin, kBinThreads, (g.ntiles + g.chunk) * sizeof(int), s, g, N, pos, q,
+    launch(false, true, k_bin_count<R>, g.nbin, kBinThreads, (g.ntiles + g.chunk) * sizeof(int), s, g, N, pos, q,
            w.cnt_blk, w.bhist, w.ctile, static_cast<V*>(w.cpos), static_cast<V*>(w.cfrac), w.cbase, Fzero,
            w.part + w.off_q);
-    launch(pdl, k_tile_offsets, (g.ntiles + 255) / 256, 256, 0, s, g, (const int*)w.bhist, w.boff, w.ttot);
-    launch(pdl, k_scan, 1, 1024, 0, s, w.ttot, w.tstart, g.ntiles, (int*)nullptr, 0);
-    launch(pdl, k_bin_scatter<R>, g.nbin, kBinThreads, g.ntiles * sizeof(int), s, g, (const int*)w.cnt_blk,
+    launch(pdl, true, k_tile_offsets, (g.ntiles + 255) / 256, 256, 0, s, g, (const int*)w.bhist, w.boff, w.ttot);
+    launch(pdl, true, k_scan, 1, 1024, 0, s, w.ttot, w.tstart, g.ntiles, (int*)nullptr, 0);
+    launch(pdl, true, k_bin_scatter<R>, g.nbin, kBinThreads, g.ntiles * sizeof(int), s, g, (const int*)w.cnt_blk,
            (const int*)w.ctile, static_cast<const V*>(w.cpos), static_cast<const V*>(w.cfrac), (const int*)w.cbase,
            (const int*)w.boff, (const int*)w.tstart, static_cast<V*>(w.sq), static_cast<V*>(w.sw), w.sb);
 }
@@ -103,7 +121,7 @@ cudaError_t enqueue_enuf(const Geo& g, const FftShape& fs, const FftPlanDev& fp,
     cudaStreamWaitEvent(s1, evFork, 0);
     rec(ev, 4, true, s1);
     const int real_smem = real_smem_bytes<R>();
-    launch(false, k_real<R>, w.nblk_real, kRealThreads, real_smem, s1, g, (const int*)w.tstart, (const V*)sq,
+    launch(false, false, k_real<R>, w.nblk_real, kRealThreads, real_smem, s1, g, (const int*)w.tstart, (const V*)sq,
            (const V*)sw, F, w.part + w.off_real);
     rec(ev, 4, false, s1);
     cudaEventRecord(evJoin, s1);
@@ -111,27 +129,27 @@ cudaError_t enqueue_enuf(const Geo& g, const FftShape& fs, const FftPlanDev& fp,
 
     // reciprocal branch
     rec(ev, 1, true, s0);
-    launch(pdl, k_spread<R>, g.ntiles, kSpreadThreads, spread_smem<R>(g), s0, g, (const int*)w.tstart,
+    launch(pdl, true, k_spread<R>, g.ntiles, kSpreadThreads, spread_smem<R>(g), s0, g, (const int*)w.tstart,
            (const V*)sq, (const V*)sw, (const int*)w.sb, static_cast<R*>(w.grid));
     rec(ev, 1, false, s0);
     rec(ev, 2, true, s0);
-    launch(pdl, k_fft_x<R>, fs.grid_x, fs.tx, fs.smem_x, s0, g, fp, static_cast<const R*>(w.grid), (const C*)tw,
+    launch(pdl, true, k_fft_x<R>, fs.grid_x, fs.tx, fs.smem_x, s0, g, fp, static_cast<const R*>(w.grid), (const C*)tw,
            static_cast<C*>(w.spec1), fs.lx);
-    launch(pdl, k_fft_y<R>, dim3(g.nc + 1, fs.grid_y_z), fs.ty, fs.smem_y, s0, g, fp,
+    launch(pdl, true, k_fft_y<R>, dim3(g.nc + 1, fs.grid_y_z), fs.ty, fs.smem_y, s0, g, fp,
            static_cast<const C*>(w.spec1), (const C*)tw, static_cast<C*>(w.spec2), fs.ly);
-    launch(pdl, k_fft_z<R>, fs.grid_z, fs.tz, fs.smem_z, s0, g, fp, static_cast<const C*>(w.spec2), (const C*)tw,
+    launch(pdl, true, k_fft_z<R>, fs.grid_z, fs.tz, fs.smem_z, s0, g, fp, static_cast<const C*>(w.spec2), (const C*)tw,
            (const double*)w.tab, (const double*)w.tabv, static_cast<const R*>(w.tabr), static_cast<C*>(w.spec3),
            w.part + w.off_recip, fs.lz);
-    launch(pdl, k_fft_iy<R>, fs.grid_iy, fs.tiy, fs.smem_iy, s0, g, fp, static_cast<const C*>(w.spec3),
+    launch(pdl, true, k_fft_iy<R>, fs.grid_iy, fs.tiy, fs.smem_iy, s0, g, fp, static_cast<const C*>(w.spec3),
            (const C*)tw, static_cast<C*>(w.spec4), fs.liy);
-    launch(pdl, k_fft_ix<R>, fs.grid_ix, fs.tix, fs.smem_ix, s0, g, fp, static_cast<const C*>(w.spec4),
+    launch(pdl, true, k_fft_ix<R>, fs.grid_ix, fs.tix, fs.smem_ix, s0, g, fp, static_cast<const C*>(w.spec4),
            (const C*)tw, static_cast<R*>(w.h), fs.lix);
     rec(ev, 2, false, s0);
     log->kernels += 6;
 
     cudaStreamWaitEvent(s0, evJoin, 0);
     rec(ev, 3, true, s0);
-    launch(false, k_gather<R>, w.nblk_gather, kGatherThreads, 0, s0, g, (const int*)w.tstart, (const V*)sq,
+    launch(false, true, k_gather<R>, w.nblk_gather, kGatherThreads, 0, s0, g, (const int*)w.tstart, (const V*)sq,
            (const V*)sw, (const int*)w.sb, static_cast<const R*>(w.h), F);
     rec(ev, 3, false, s0);
     log->kernels += 1;
@@ -140,7 +158,7 @@ cudaError_t enqueue_enuf(const Geo& g, const FftShape& fs, const FftPlanDev& fp,
 
 template <typename R>
 cudaError_t enqueue_totals(const Geo& g, const Work& w, bool dpd, cudaStream_t s, LaunchLog* log, bool pdl) {
-    launch(pdl, k_totals, 1, 1024, 0, s, g, (const double*)w.part, w.off_q, g.nbin, w.off_real, w.nblk_real,
+    launch(pdl, true, k_totals, 1, 1024, 0, s, g, (const double*)w.part, w.off_q, g.nbin, w.off_real, w.nblk_real,
            w.off_recip, w.nblk_conv, w.off_dpd, dpd ? w.nblk_dpd : 0, w.off_kin, dpd ? w.nblk_kin : 0, w.Edev);
     log->kernels += 1;
     return cudaGetLastError();
@@ -153,16 +171,16 @@ cudaError_t enqueue_dpd_forces(const Work& w, const DpdDev& d, cudaStream_t s, E
     const bool pdl = pdl_ok(ev);
     rec(ev, 7, true, s);
     // the cell count also zeroes F, which the pair kernel adds into
-    launch(false, k_cell_count<R>, blocks, 256, 0, s, d.N, d.ncd, d.L, d.cinv, d.xmaxf, static_cast<const R*>(d.pos),
+    launch(false, false, k_cell_count<R>, blocks, 256, 0, s, d.N, d.ncd, d.L, d.cinv, d.xmaxf, static_cast<const R*>(d.pos),
            d.ckey, d.ccount, static_cast<R*>(d.F));
-    launch(pdl, k_scan, 1, 1024, 0, s, d.ccount, d.cstart, d.ncells, d.ccur, 1);
-    launch(pdl, k_cell_scatter<R>, blocks, 256, 0, s, d.N, d.L, d.xmaxf, static_cast<const R*>(d.pos),
+    launch(pdl, false, k_scan, 1, 1024, 0, s, d.ccount, d.cstart, d.ncells, d.ccur, 1);
+    launch(pdl, false, k_cell_scatter<R>, blocks, 256, 0, s, d.N, d.L, d.xmaxf, static_cast<const R*>(d.pos),
            static_cast<const R*>(d.v0), (const int*)d.type, (const int*)d.ckey, d.ccur, static_cast<V*>(d.sp),
            static_cast<V*>(d.sv));
     rec(ev, 7, false, s);
     rec(ev, 5, true, s);
     const int dpd_smem = dpd_smem_bytes<R>();
-    launch(pdl, k_dpd<R>, w.nblk_dpd, kDpdThreads, dpd_smem, s, d, d.B, static_cast<const V*>(d.sp),
+    launch(pdl, false, k_dpd<R>, w.nblk_dpd, kDpdThreads, dpd_smem, s, d, d.B, static_cast<const V*>(d.sp),
            static_cast<const V*>(d.sv), (const int*)d.cstart, static_cast<const R*>(d.atab),
            static_cast<const R*>(d.pos), (const int*)d.bnd, (const uint64_t*)d.step_dev, static_cast<R*>(d.F),
            w.part + w.off_dpd);
@@ -174,7 +192,7 @@ cudaError_t enqueue_dpd_forces(const Work& w, const DpdDev& d, cudaStream_t s, E
 template <typename R>
 cudaError_t enqueue_vv_pre(const DpdDev& d, cudaStream_t s, LaunchLog* log) {
     const int blocks = (3 * d.N + 255) / 256 > 0 ? (3 * d.N + 255) / 256 : 1;
-    launch(false, k_vv_pre<R>, blocks, 256, 0, s, d.N, (R)d.lambda_vv, (R)d.dt, static_cast<R*>(d.pos),
+    launch(false, true, k_vv_pre<R>, blocks, 256, 0, s, d.N, (R)d.lambda_vv, (R)d.dt, static_cast<R*>(d.pos),
            static_cast<R*>(d.vel), static_cast<R*>(d.v0), static_cast<const R*>(d.F), d.step_dev);
     log->kernels += 1;
     return cudaGetLastError();
@@ -182,7 +200,7 @@ cudaError_t enqueue_vv_pre(const DpdDev& d, cudaStream_t s, LaunchLog* log) {
 
 template <typename R>
 cudaError_t enqueue_vv_post(const Work& w, const DpdDev& d, cudaStream_t s, LaunchLog* log, bool pdl) {
-    launch(pdl, k_vv_post<R>, w.nblk_kin, 256, 0, s, d.N, (R)d.dt, static_cast<R*>(d.vel),
+    launch(pdl, true, k_vv_post<R>, w.nblk_kin, 256, 0, s, d.N, (R)d.dt, static_cast<R*>(d.vel),
            static_cast<const R*>(d.F), w.part + w.off_kin);
     log->kernels += 1;
     return cudaGetLastError();
@@ -194,7 +212,7 @@ template <typename R>
 cudaError_t enqueue_spread_only(const Geo& g, const Work& w, const EvalArgs& a, void* grid_out, cudaStream_t s) {
     using V = typename V4<R>::T;
     enqueue_bin<R>(g, w, a.N, static_cast<const R*>(a.pos), static_cast<const R*>(a.q), nullptr, s, true);
-    launch(true, k_spread<R>, g.ntiles, kSpreadThreads, spread_smem<R>(g), s, g, (const int*)w.tstart,
+    launch(true, true, k_spread<R>, g.ntiles, kSpreadThreads, spread_smem<R>(g), s, g, (const int*)w.tstart,
            static_cast<const V*>(w.sq), static_cast<const V*>(w.sw), (const int*)w.sb, static_cast<R*>(grid_out));
     return cudaGetLastError();
 }
