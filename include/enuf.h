@@ -85,7 +85,9 @@ typedef struct {
                              sin(kr)/k dk, interpolated from a table built at plan time;
                              self and background terms change to match. Same total
                              energy for converged sums. */
-    int    reserved[4];
+    int    fft_path;  /* 0: automatic (FP32 grids with n <= 112: whole z-planes in shared
+                         memory, x+y and y+x fused); 1: always the five line passes x, y, z, y, x */
+    int    reserved[3];
 } enuf_params;
 
 typedef struct enuf_plan_s* enuf_plan_t;
@@ -95,6 +97,8 @@ typedef struct {
     int    M, n, n_c;          /* base grid, oversampled grid n = sigma_s M, kept modes */
     int    tile, n_tiles;      /* spreading tile edge and tile count */
     int    n_max;              /* capacity in beads */
+    int    fft_kernels;        /* FFT kernels per evaluation: 3 with the fused plane passes
+                                  (see enuf_params.fft_path), else 5 */
     size_t device_bytes;       /* device memory the plan holds */
 } enuf_plan_info;
 

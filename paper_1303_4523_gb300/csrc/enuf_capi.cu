@@ -190,6 +190,7 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
     if (P.deriv != 0 && P.deriv != 1) return fail(plan, ENUF_ERR_INVALID, "deriv must be 0 or 1");
     if (P.slater_k != 0 && P.slater_k != 1) return fail(plan, ENUF_ERR_INVALID, "slater_k must be 0 or 1");
     if (P.slater_k && !(P.beta > 0)) return fail(plan, ENUF_ERR_INVALID, "slater_k = 1 needs beta > 0");
+    if (P.fft_path != 0 && P.fft_path != 1) return fail(plan, ENUF_ERR_INVALID, "fft_path must be 0 or 1");
     const int M = P.M == 0 ? grid_rule(P.L) : P.M;
     if (M < 4 || (M & 1)) return fail(plan, ENUF_ERR_INVALID, "M must be even and >= 4 (got %d)", M);
     const int n = P.sigma_s * M;
@@ -275,6 +276,15 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
     fs.smem_z = (1 + (2 + 2 * g.nf) * fs.lz) * n * csz;
     fs.smem_iy = (1 + 2 * fs.liy) * n * csz;
     fs.smem_ix = (1 + 2 * fs.lix) * n * csz;
+    // fused plane passes (one CTA per z-plane) for FP32 grids whose twiddles and two
+    // n^2/2-line buffers take <= 100 KB (n <= 112): measured faster there; larger planes
+    // and FP64 (1 CTA per SM, FP64-bound butterflies on n CTAs) keep the five passes
+    {
+        const long long plane = (long long)(n + n * n) * csz;
+        fs.fused = (P.prec == ENUF_FP32 && plane <= 100 * 1024 && P.fft_path == 0) ? 1 : 0;
+        fs.smem_xy = fs.smem_yx = (int)plane;
+        fs.t_xy = fs.t_yx = 512;
+    }
     g.ratio = (double)n / P.L;
     g.rb = 1.0 / g.b;
     g.pref = P.deriv ? -P.kappa * n / (M_PI * P.L * P.L) : P.kappa * 2.0 / (P.L * P.L);
@@ -595,6 +605,7 @@ enuf_status enuf_get_info(enuf_plan_t plan, enuf_plan_info* info) {
     info->tile = plan->g.T;
     info->n_tiles = plan->g.ntiles;
     info->n_max = plan->n_max;
+    info->fft_kernels = plan->fs.fused ? 3 : 5;
     info->device_bytes = plan->dbytes;
     return ENUF_OK;
 }

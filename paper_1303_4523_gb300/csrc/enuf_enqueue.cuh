@@ -72,6 +72,8 @@ cudaError_t configure_kernels(int max_smem) {
     set((const void*)k_fft_z<R>);
     set((const void*)k_fft_iy<R>);
     set((const void*)k_fft_ix<R>);
+    set((const void*)k_fft_xy<R>);
+    set((const void*)k_fft_yx<R>);
     set((const void*)k_real<R>);
     set((const void*)k_dpd<R>);
     return e;
@@ -133,19 +135,30 @@ cudaError_t enqueue_enuf(const Geo& g, const FftShape& fs, const FftPlanDev& fp,
            (const V*)sq, (const V*)sw, (const int*)w.sb, static_cast<R*>(w.grid));
     rec(ev, 1, false, s0);
     rec(ev, 2, true, s0);
-    launch(pdl, true, k_fft_x<R>, fs.grid_x, fs.tx, fs.smem_x, s0, g, fp, static_cast<const R*>(w.grid), (const C*)tw,
-           static_cast<C*>(w.spec1), fs.lx);
-    launch(pdl, true, k_fft_y<R>, dim3(g.nc + 1, fs.grid_y_z), fs.ty, fs.smem_y, s0, g, fp,
-           static_cast<const C*>(w.spec1), (const C*)tw, static_cast<C*>(w.spec2), fs.ly);
-    launch(pdl, true, k_fft_z<R>, fs.grid_z, fs.tz, fs.smem_z, s0, g, fp, static_cast<const C*>(w.spec2), (const C*)tw,
-           (const double*)w.tab, (const double*)w.tabv, static_cast<const R*>(w.tabr), static_cast<C*>(w.spec3),
-           w.part + w.off_recip, fs.lz);
-    launch(pdl, true, k_fft_iy<R>, fs.grid_iy, fs.tiy, fs.smem_iy, s0, g, fp, static_cast<const C*>(w.spec3),
-           (const C*)tw, static_cast<C*>(w.spec4), fs.liy);
-    launch(pdl, true, k_fft_ix<R>, fs.grid_ix, fs.tix, fs.smem_ix, s0, g, fp, static_cast<const C*>(w.spec4),
-           (const C*)tw, static_cast<R*>(w.h), fs.lix);
+    if (fs.fused) {   // whole z-planes in shared memory: x+y, z (+convolve), y+x
+        launch(pdl, true, k_fft_xy<R>, g.n, fs.t_xy, fs.smem_xy, s0, g, fp, static_cast<const R*>(w.grid),
+               (const C*)tw, static_cast<C*>(w.spec2));
+        launch(pdl, true, k_fft_z<R>, fs.grid_z, fs.tz, fs.smem_z, s0, g, fp, static_cast<const C*>(w.spec2),
+               (const C*)tw, (const double*)w.tab, (const double*)w.tabv, static_cast<const R*>(w.tabr),
+               static_cast<C*>(w.spec3), w.part + w.off_recip, fs.lz, 1);
+        launch(pdl, true, k_fft_yx<R>, g.nf * g.n, fs.t_yx, fs.smem_yx, s0, g, fp, static_cast<const C*>(w.spec3),
+               (const C*)tw, static_cast<R*>(w.h));
+        log->kernels += 4;
+    } else {
+        launch(pdl, true, k_fft_x<R>, fs.grid_x, fs.tx, fs.smem_x, s0, g, fp, static_cast<const R*>(w.grid),
+               (const C*)tw, static_cast<C*>(w.spec1), fs.lx);
+        launch(pdl, true, k_fft_y<R>, dim3(g.nc + 1, fs.grid_y_z), fs.ty, fs.smem_y, s0, g, fp,
+               static_cast<const C*>(w.spec1), (const C*)tw, static_cast<C*>(w.spec2), fs.ly);
+        launch(pdl, true, k_fft_z<R>, fs.grid_z, fs.tz, fs.smem_z, s0, g, fp, static_cast<const C*>(w.spec2),
+               (const C*)tw, (const double*)w.tab, (const double*)w.tabv, static_cast<const R*>(w.tabr),
+               static_cast<C*>(w.spec3), w.part + w.off_recip, fs.lz, 0);
+        launch(pdl, true, k_fft_iy<R>, fs.grid_iy, fs.tiy, fs.smem_iy, s0, g, fp, static_cast<const C*>(w.spec3),
+               (const C*)tw, static_cast<C*>(w.spec4), fs.liy);
+        launch(pdl, true, k_fft_ix<R>, fs.grid_ix, fs.tix, fs.smem_ix, s0, g, fp, static_cast<const C*>(w.spec4),
+               (const C*)tw, static_cast<R*>(w.h), fs.lix);
+        log->kernels += 6;
+    }
     rec(ev, 2, false, s0);
-    log->kernels += 6;
 
     cudaStreamWaitEvent(s0, evJoin, 0);
     rec(ev, 3, true, s0);

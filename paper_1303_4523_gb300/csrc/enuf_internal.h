@@ -52,6 +52,10 @@ struct FftShape {
     int tx, ty, tz, tiy, tix;   // threads per CTA of each pass
     int smem_x, smem_y, smem_z, smem_iy, smem_ix;   // dynamic smem bytes
     int grid_x, grid_y_z, grid_z, grid_iy, grid_ix; // CTAs (grid_y_z: z-chunks of the y pass)
+    // small grids: a whole z-plane per CTA, forward x+y and inverse y+x fused
+    // (two kernels instead of four); spec2 is then plane-major [z][kx][ky]
+    int fused;
+    int t_xy, t_yx, smem_xy, smem_yx;
 };
 
 // Device workspace of one plan (all pointers device memory, one allocation).

@@ -662,7 +662,7 @@ __global__ void __launch_bounds__(256) k_fft_z(Geo g, FftPlanDev fp, const typen
                                               const typename Cx<R>::T* __restrict__ twg,
                                               const double* __restrict__ tab, const double* __restrict__ tabv,
                                               const R* __restrict__ tabr, typename Cx<R>::T* __restrict__ spec3,
-                                              double* __restrict__ epart, int LB) {
+                                              double* __restrict__ epart, int LB, int plane_major) {
     pdl_enter();
     using C = typename Cx<R>::T;
     extern __shared__ unsigned char smraw[];
@@ -678,7 +678,14 @@ __global__ void __launch_bounds__(256) k_fft_z(Geo g, FftPlanDev fp, const typen
     const int l0 = blockIdx.x * LB;
     const int nl = min(LB, NL - l0);
     const float rnl = 1.0f / (float)max(nl, 1);
-    for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) b0[idx] = spec2[(size_t)l0 * n + idx];
+    if (plane_major) {   // spec2[z][l]: lines gathered across planes
+        for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
+            const int z = qdiv(idx, nl, rnl), c = idx - z * nl;
+            b0[c * n + z] = spec2[(size_t)z * NL + l0 + c];
+        }
+    } else {             // spec2[l][z]: lines contiguous
+        for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) b0[idx] = spec2[(size_t)l0 * n + idx];
+    }
     __syncthreads();
     C* Fh = fft_lines<R, false>(b0, b1, tw, fp, nl, n);
     // energy and virial of the kept modes (half space kx >= 0, kx > 0 counted twice)
@@ -733,6 +740,123 @@ __global__ void __launch_bounds__(256) k_fft_z(Geo g, FftPlanDev fp, const typen
         const int a = qdiv(idx, per, rper), e = idx - a * per;
         const int z = qdiv(e, nl, rnl), c = e - z * nl;
         spec3[((size_t)a * n + z) * NL + l0 + c] = res[(a * nl + c) * n + z];
+    }
+}
+
+// Forward x and y passes of one z-plane in shared memory (small grids): the
+// n real rows as n/2 complex lines (two rows each), FFT along x, split into
+// the two half spectra kx = 0..nc, FFT of the nc + 1 columns along y, keep
+// |ky| <= nc; output spec2[z][kx][ky] (plane-major).
+template <typename R>
+__global__ void __launch_bounds__(512) k_fft_xy(Geo g, FftPlanDev fp, const R* __restrict__ grid,
+                                               const typename Cx<R>::T* __restrict__ twg,
+                                               typename Cx<R>::T* __restrict__ spec2) {
+    pdl_enter();
+    using C = typename Cx<R>::T;
+    extern __shared__ unsigned char smraw[];
+    const int n = g.n, nc = g.nc, nc1 = nc + 1, K = g.K, h = n / 2;
+    const float rn = 1.0f / (float)n, rh = 1.0f / (float)h, rK = 1.0f / (float)K;
+    C* tw = reinterpret_cast<C*>(smraw);
+    C* L0 = tw + n;        // [n/2][n]
+    C* L1 = L0 + h * n;    // [n/2][n]
+    for (int t = threadIdx.x; t < n; t += blockDim.x) tw[t] = twg[t];
+    const int z = blockIdx.x;
+    const R* gz = grid + (size_t)z * n * n;
+    for (int idx = threadIdx.x; idx < h * n; idx += blockDim.x) {
+        const int c = qdiv(idx, n, rn), x = idx - c * n;
+        C v;
+        v.x = gz[(size_t)(2 * c) * n + x];
+        v.y = gz[(size_t)(2 * c + 1) * n + x];
+        L0[idx] = v;
+    }
+    __syncthreads();
+    C* X = fft_lines<R, false>(L0, L1, tw, fp, h, n);
+    C* P = X == L0 ? L1 : L0;   // [nc+1][n] columns over y, then scratch
+    C* S = P + nc1 * n;         // 2 (nc + 1) = n/2: P and S fill the other buffer
+    // split the two real transforms: A = (Z_k + conj Z_{n-k})/2, B = -i (Z_k - conj Z_{n-k})/2
+    for (int idx = threadIdx.x; idx < nc1 * h; idx += blockDim.x) {
+        const int k = qdiv(idx, h, rh), c = idx - k * h;
+        const C zk = X[c * n + k];
+        const C zm = X[c * n + (k == 0 ? 0 : n - k)];
+        C A, B;
+        A.x = (R)0.5 * (zk.x + zm.x);
+        A.y = (R)0.5 * (zk.y - zm.y);
+        B.x = (R)0.5 * (zk.y + zm.y);
+        B.y = (R)0.5 * (zm.x - zk.x);
+        P[k * n + 2 * c] = A;
+        P[k * n + 2 * c + 1] = B;
+    }
+    __syncthreads();
+    C* Y = fft_lines<R, false>(P, S, tw, fp, nc1, n);
+    C* out = spec2 + (size_t)z * nc1 * K;
+    for (int idx = threadIdx.x; idx < nc1 * K; idx += blockDim.x) {
+        const int kx = qdiv(idx, K, rK), ki = idx - kx * K;
+        const int ky = ki - nc;
+        out[idx] = Y[kx * n + (ky < 0 ? ky + n : ky)];
+    }
+}
+
+// Inverse y and x passes of one (field, z-plane) in shared memory (small
+// grids): the plane spec3[a][z][kx][ky], zero-padded to n along y, inverse
+// FFT of the nc + 1 columns, then two Hermitian rows per complex line
+// (C2R) inverse along x; output h[a][z][y][x].
+template <typename R>
+__global__ void __launch_bounds__(512) k_fft_yx(Geo g, FftPlanDev fp, const typename Cx<R>::T* __restrict__ spec3,
+                                               const typename Cx<R>::T* __restrict__ twg, R* __restrict__ h) {
+    pdl_enter();
+    using C = typename Cx<R>::T;
+    extern __shared__ unsigned char smraw[];
+    const int n = g.n, nc = g.nc, nc1 = nc + 1, K = g.K, hn = n / 2;
+    const float rn = 1.0f / (float)n;
+    C* tw = reinterpret_cast<C*>(smraw);
+    C* L0 = tw + n;         // [n/2][n]
+    C* L1 = L0 + hn * n;    // [n/2][n]
+    for (int t = threadIdx.x; t < n; t += blockDim.x) tw[t] = twg[t];
+    const int az = blockIdx.x;   // a * n + z
+    const C* in = spec3 + (size_t)az * nc1 * K;
+    C* P = L0;                   // [nc+1][n] columns over y
+    C* S = L0 + nc1 * n;
+    for (int idx = threadIdx.x; idx < nc1 * n; idx += blockDim.x) {
+        const int kx = qdiv(idx, n, rn), m = idx - kx * n;
+        const int ky = m <= n / 2 ? m : m - n;
+        C v;
+        v.x = (R)0;
+        v.y = (R)0;
+        if (ky >= -nc && ky <= nc) v = in[kx * K + (ky + nc)];
+        P[idx] = v;
+    }
+    __syncthreads();
+    C* Yc = fft_lines<R, true>(P, S, tw, fp, nc1, n);   // [kx][y], in L0
+    // x lines: row pair (2c, 2c+1) as A + i B with the Hermitian extension
+    for (int idx = threadIdx.x; idx < hn * n; idx += blockDim.x) {
+        const int c = qdiv(idx, n, rn), m = idx - c * n;
+        C a, b;
+        a.x = a.y = b.x = b.y = (R)0;
+        if (m == 0) {
+            a.x = Yc[2 * c].x;
+            b.x = Yc[2 * c + 1].x;
+        } else if (m <= nc) {
+            a = Yc[m * n + 2 * c];
+            b = Yc[m * n + 2 * c + 1];
+        } else if (m >= n - nc) {
+            a = Yc[(n - m) * n + 2 * c];
+            a.y = -a.y;
+            b = Yc[(n - m) * n + 2 * c + 1];
+            b.y = -b.y;
+        }
+        C zz;
+        zz.x = a.x - b.y;   // A + i B
+        zz.y = a.y + b.x;
+        L1[idx] = zz;
+    }
+    __syncthreads();
+    C* Xr = fft_lines<R, true>(L1, L0, tw, fp, hn, n);
+    R* out = h + (size_t)az * n * n;
+    for (int idx = threadIdx.x; idx < hn * n; idx += blockDim.x) {
+        const int c = qdiv(idx, n, rn), x = idx - c * n;
+        const C v = Xr[idx];
+        out[(size_t)(2 * c) * n + x] = v.x;
+        out[(size_t)(2 * c + 1) * n + x] = v.y;
     }
 }
 

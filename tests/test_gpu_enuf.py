@@ -46,8 +46,9 @@ def _gpu(enuf, prec, P, pos, q, n_max=None):
 
 
 def _oparams(prec, P):
-    """Oracle parameters: the GPU-only tiling choice does not change the result."""
-    return orc.EwaldParams(fp32_cut=1 if prec == "fp32" else 0, **{k: v for k, v in P.items() if k != "tile"})
+    """Oracle parameters: the GPU-only tiling and FFT-path choices do not change the result."""
+    return orc.EwaldParams(fp32_cut=1 if prec == "fp32" else 0,
+                           **{k: v for k, v in P.items() if k not in ("tile", "fft_path")})
 
 
 def _ref(prec, P, pos, q, sample=None):
@@ -111,6 +112,22 @@ def test_energy_forces_parity(enuf, name, prec):
     _check(prec, F, E, Wv, Fr, Er, Wr)
     # uncharged beads get exactly zero force
     assert np.all(F[q == 0] == 0.0)
+    plan.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("deriv", [0, 1])
+def test_five_pass_fft_parity(enuf, name, prec, deriv):
+    """The five line passes (the path of grids whose z-planes do not fit in
+    shared memory), forced on the small cases, in both force modes."""
+    P, pos, q = _case(name)
+    P = dict(P, fft_path=1, deriv=deriv)
+    pos, q = _inputs(prec, pos, q)
+    plan, F, E, Wv = _gpu(enuf, prec, P, pos, q)
+    assert plan.info.fft_kernels == 5
+    Fr, Er, Wr = _ref(prec, P, pos, q)
+    _check(prec, F, E, Wv, Fr, Er, Wr)
     plan.close()
 
 
@@ -242,7 +259,9 @@ def test_stage_timing(enuf):
     plan.energy_forces(tp, tq, F)
     for st in ("bin", "spread", "fft", "gather", "real", "all"):
         assert plan.stage_time(st) > 0.0
-    assert plan.launches() == 13
+    # binning 4, real space, spreading, the FFT kernels, gather, totals
+    assert plan.info.fft_kernels in (3, 5)
+    assert plan.launches() == 8 + plan.info.fft_kernels
     plan.close()
 
 
@@ -250,7 +269,7 @@ def test_stage_timing(enuf):
 def test_batch_equals_single_plans(enuf, prec):
     systems = [W.electrolyte(N, seed_offset=70 + i) for i, N in enumerate([1500, 3000, 6000, 2000])]
     dt = torch.float32 if prec == "fp32" else torch.float64
-    params, pos_l, q_l, F_l, singles = [], [], [], [], []
+    params, pos_l, q_l, F_l, singles, nfft = [], [], [], [], [], []
     for s in systems:
         P = dict(L=s.L, M=s.M, **s.params)
         params.append(enuf.make_params(prec=prec, **P))
@@ -263,11 +282,12 @@ def test_batch_equals_single_plans(enuf, prec):
         Fs = torch.empty_like(tp)
         Es, _ = pl.energy_forces(tp, tq, Fs)
         singles.append((Fs.double().cpu().numpy(), Es))
+        nfft.append(pl.info.fft_kernels)
         pl.close()
     b = enuf.Batch(params, [s.N for s in systems])
     E = b.energy_forces(pos_l, q_l, F_l)
     E2 = b.energy_forces(pos_l, q_l, F_l)
-    assert b.launches() == 13 * len(systems)
+    assert b.launches() == sum(8 + k for k in nfft)
     for k, (Fs, Es) in enumerate(singles):
         Fb = F_l[k].double().cpu().numpy()
         tol = 1e-6 if prec == "fp32" else 1e-12
