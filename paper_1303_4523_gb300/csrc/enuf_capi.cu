@@ -334,7 +334,8 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
            o_boff = take((size_t)g.nbin * g.ntiles * 4), o_ttot = take((size_t)g.ntiles * 4),
            o_tstart = take((size_t)(g.ntiles + 1) * 4), o_ctile = take(ncmp * 4), o_cpos = take(ncmp * 4 * esz),
            o_cfrac = take(ncmp * 4 * esz), o_cbase = take(ncmp * 4),
-           o_sq = take(nm * 4 * esz), o_sw = take(nm * 4 * esz), o_sb = take(nm * 4), o_grid = take(n3 * esz),
+           o_sq = take(nm * 4 * esz), o_sw = take(nm * 4 * esz), o_sb = take(nm * 4),
+           o_wb = take(nm * 3 * 2 * P.p * esz), o_grid = take(n3 * esz),
            o_s1 = take((size_t)n * nc1 * n * csz), o_s2 = take((size_t)nc1 * g.K * n * csz),
            o_s3 = take((size_t)g.nf * n * nc1 * g.K * csz), o_s4 = take((size_t)g.nf * n * n * nc1 * csz),
            o_h = take(g.nf * n3 * esz), o_tab = take(ntab * 8), o_tabv = take(ntab * 8), o_tabr = take(ntab * esz),
@@ -355,7 +356,7 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
         w.cnt_blk = (int*)o_cnt; w.bhist = (int*)o_bhist; w.boff = (int*)o_boff; w.ttot = (int*)o_ttot;
         w.tstart = (int*)o_tstart; w.ctile = (int*)o_ctile; w.cpos = (void*)o_cpos; w.cfrac = (void*)o_cfrac;
         w.cbase = (int*)o_cbase;
-        w.sq = (void*)o_sq; w.sw = (void*)o_sw; w.sb = (int*)o_sb; w.grid = (void*)o_grid;
+        w.sq = (void*)o_sq; w.sw = (void*)o_sw; w.sb = (int*)o_sb; w.wb = (void*)o_wb; w.grid = (void*)o_grid;
         w.spec1 = (void*)o_s1; w.spec2 = (void*)o_s2; w.spec3 = (void*)o_s3; w.spec4 = (void*)o_s4;
         w.h = (void*)o_h; w.tab = (double*)o_tab; w.tabv = (double*)o_tabv; w.tabr = (void*)o_tabr;
         w.tw = (void*)o_tw; w.part = (double*)o_part; w.Edev = (double*)o_E; w.ktab = (void*)o_ktab;
@@ -372,7 +373,7 @@ void bind(enuf_plan_t p) {
     w.cnt_blk = at(w.cnt_blk); w.bhist = at(w.bhist); w.boff = at(w.boff); w.ttot = at(w.ttot);
     w.tstart = at(w.tstart); w.ctile = at(w.ctile); w.cpos = at(w.cpos); w.cfrac = at(w.cfrac);
     w.cbase = at(w.cbase);
-    w.sq = at(w.sq); w.sw = at(w.sw); w.sb = at(w.sb); w.grid = at(w.grid);
+    w.sq = at(w.sq); w.sw = at(w.sw); w.sb = at(w.sb); w.wb = at(w.wb); w.grid = at(w.grid);
     w.spec1 = at(w.spec1); w.spec2 = at(w.spec2); w.spec3 = at(w.spec3); w.spec4 = at(w.spec4);
     w.h = at(w.h); w.tab = at(w.tab); w.tabv = at(w.tabv); w.tabr = at(w.tabr);
     w.tw = at(w.tw); w.part = at(w.part); w.Edev = at(w.Edev); w.ktab = at(w.ktab);

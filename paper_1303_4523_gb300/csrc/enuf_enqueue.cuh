@@ -4,6 +4,7 @@
 // depend on the binning and write F; the branches join before the gather.
 // Every sequence is stream-ordered and capturable into a CUDA graph.
 #pragma once
+#include <algorithm>
 #include <utility>
 
 #include "enuf_kernels.cuh"
@@ -72,6 +73,12 @@ cudaError_t configure_kernels(int max_smem) {
     set((const void*)k_fft_z<R>);
     set((const void*)k_fft_iy<R>);
     set((const void*)k_fft_ix<R>);
+    set((const void*)k_spread_col<R, 8>);
+    set((const void*)k_spread_col<R, 10>);
+    set((const void*)k_spread_col<R, 12>);
+    set((const void*)k_spread_col<R, 16>);
+    set((const void*)k_spread_col<R, 20>);
+    set((const void*)k_spread_col<R, 24>);
     set((const void*)k_fft_xy<R>);
     set((const void*)k_fft_yx<R>);
     set((const void*)k_real<R>);
@@ -87,6 +94,13 @@ int spread_smem(const Geo& g) {
 }
 
 // a1: compaction + coordinates + tile histograms, tile offsets, tile scan, scatter.
+// Blocks of the weights kernel: enough words per thread for the plan's capacity,
+// at most four CTAs per SM.
+inline int bin_weight_blocks(const Geo& g) {
+    const long long words = (long long)g.nbin * g.chunk * 6 * g.p;
+    return (int)std::max(1LL, std::min((long long)4 * 152, (words + 255) / 256));
+}
+
 template <typename R>
 void enqueue_bin(const Geo& g, const Work& w, int N, const R* pos, const R* q, R* Fzero, cudaStream_t s, bool pdl) {
     using V = typename V4<R>::T;
@@ -98,6 +112,39 @@ void enqueue_bin(const Geo& g, const Work& w, int N, const R* pos, const R* q, R
     launch(pdl, true, k_bin_scatter<R>, g.nbin, kBinThreads, g.ntiles * sizeof(int), s, g, (const int*)w.cnt_blk,
            (const int*)w.ctile, static_cast<const V*>(w.cpos), static_cast<const V*>(w.cfrac), (const int*)w.cbase,
            (const int*)w.boff, (const int*)w.tstart, static_cast<V*>(w.sq), static_cast<V*>(w.sw), w.sb);
+    if (w.wb)
+        launch(pdl, true, k_bin_weights<R>, bin_weight_blocks(g), 256, 0, s, g, (const int*)w.tstart,
+               static_cast<const V*>(w.sw), static_cast<R*>(w.wb));
+}
+
+// Kernels enqueue_bin launches.
+inline int bin_kernels(const Work& w) { return w.wb ? 5 : 4; }
+
+// Spreading: the column-stationary kernel for the common tile edges, the
+// work-item kernel with shared-memory atomics otherwise (or without weights).
+template <typename R, int T>
+inline void launch_col(const Geo& g, const Work& w, R* grid, cudaStream_t s, bool pdl) {
+    using V = typename V4<R>::T;
+    launch(pdl, true, k_spread_col<R, T>, g.ntiles, col_threads(T), col_smem<R>(T), s, g, (const int*)w.tstart,
+           static_cast<const V*>(w.sq), (const int*)w.sb, static_cast<const R*>(w.wb), grid);
+}
+
+template <typename R>
+inline void enqueue_spread(const Geo& g, const Work& w, R* grid, cudaStream_t s, bool pdl) {
+    using V = typename V4<R>::T;
+    if (w.wb) {
+        switch (g.T) {
+            case 8: launch_col<R, 8>(g, w, grid, s, pdl); return;
+            case 10: launch_col<R, 10>(g, w, grid, s, pdl); return;
+            case 12: launch_col<R, 12>(g, w, grid, s, pdl); return;
+            case 16: launch_col<R, 16>(g, w, grid, s, pdl); return;
+            case 20: launch_col<R, 20>(g, w, grid, s, pdl); return;
+            case 24: launch_col<R, 24>(g, w, grid, s, pdl); return;
+            default: break;
+        }
+    }
+    launch(pdl, true, k_spread<R>, g.ntiles, kSpreadThreads, spread_smem<R>(g), s, g, (const int*)w.tstart,
+           static_cast<const V*>(w.sq), static_cast<const V*>(w.sw), (const int*)w.sb, grid);
 }
 
 template <typename R>
@@ -116,7 +163,7 @@ cudaError_t enqueue_enuf(const Geo& g, const FftShape& fs, const FftPlanDev& fp,
     rec(ev, 0, true, s0);
     enqueue_bin<R>(g, w, a.N, pos, q, a.zeroF ? F : nullptr, s0, pdl);
     rec(ev, 0, false, s0);
-    log->kernels += 4;
+    log->kernels += bin_kernels(w);
 
     // real-space branch
     cudaEventRecord(evFork, s0);
@@ -131,8 +178,7 @@ cudaError_t enqueue_enuf(const Geo& g, const FftShape& fs, const FftPlanDev& fp,
 
     // reciprocal branch
     rec(ev, 1, true, s0);
-    launch(pdl, true, k_spread<R>, g.ntiles, kSpreadThreads, spread_smem<R>(g), s0, g, (const int*)w.tstart,
-           (const V*)sq, (const V*)sw, (const int*)w.sb, static_cast<R*>(w.grid));
+    enqueue_spread<R>(g, w, static_cast<R*>(w.grid), s0, pdl);
     rec(ev, 1, false, s0);
     rec(ev, 2, true, s0);
     if (fs.fused) {   // whole z-planes in shared memory: x+y, z (+convolve), y+x
@@ -163,7 +209,7 @@ cudaError_t enqueue_enuf(const Geo& g, const FftShape& fs, const FftPlanDev& fp,
     cudaStreamWaitEvent(s0, evJoin, 0);
     rec(ev, 3, true, s0);
     launch(false, true, k_gather<R>, w.nblk_gather, kGatherThreads, 0, s0, g, (const int*)w.tstart, (const V*)sq,
-           (const V*)sw, (const int*)w.sb, static_cast<const R*>(w.h), F);
+           (const V*)sw, (const int*)w.sb, static_cast<const R*>(w.wb), static_cast<const R*>(w.h), F);
     rec(ev, 3, false, s0);
     log->kernels += 1;
     return cudaGetLastError();

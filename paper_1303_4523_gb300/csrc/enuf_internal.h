@@ -73,6 +73,7 @@ struct Work {
     void* sq;        // real4 [n_max]  wrapped x, y, z, q (sorted)
     void* sw;        // real4 [n_max]  fractional grid coordinates, original index bits
     int* sb;         // [n_max]  packed base grid index
+    void* wb;        // real [n_max][3][2p]  window weights psi(u - l) of each sorted bead
     // grids and spectra
     void* grid;      // real [n^3]
     void* spec1;     // cplx [n][nc+1][n]      after forward x   ([z][kx][y])

@@ -372,7 +372,7 @@ __global__ void __launch_bounds__(1024) k_bin_scatter(Geo g, const int* __restri
                                                      typename V4<R>::T* __restrict__ sq,
                                                      typename V4<R>::T* __restrict__ sw, int* __restrict__ sb) {
     pdl_enter();
-    extern __shared__ int cur[];
+    extern __shared__ int cur[];   // [ntiles] running counts
     const int b = blockIdx.x;
     for (int t = threadIdx.x; t < g.ntiles; t += blockDim.x) cur[t] = 0;
     __syncthreads();
@@ -385,6 +385,29 @@ __global__ void __launch_bounds__(1024) k_bin_scatter(Geo g, const int* __restri
         sq[slot] = cpos[o];
         sw[slot] = cfrac[o];
         sb[slot] = cbase[o];
+    }
+}
+
+// Window weights of every sorted charged bead (Eq. 14), computed once and
+// read by the spreading and gathering kernels: wb[s][d][a] = psi(u_sd - l_a)
+// for the 2p taps a of dimension d. One thread per word, all SMs (in FP64 the
+// exponentials run on the FP64 units).
+template <typename R>
+__global__ void __launch_bounds__(256) k_bin_weights(Geo g, const int* __restrict__ tstart,
+                                                    const typename V4<R>::T* __restrict__ sw, R* __restrict__ wb) {
+    pdl_enter();
+    const int nq = tstart[g.ntiles];
+    const int P2 = 2 * g.p, W = 3 * P2;
+    const float rP2 = 1.0f / (float)P2;
+    const R rb = (R)g.rb, wn = (R)g.wnorm;
+    const long long tot = (long long)nq * W;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+        const int s = (int)(e / W), r = (int)(e - (long long)s * W);
+        const int d = qdiv(r, P2, rP2), a = r - d * P2;
+        const typename V4<R>::T fr = sw[s];
+        const R f = d == 0 ? fr.x : (d == 1 ? fr.y : fr.z);
+        const R u = f + (R)(g.p - 1 - a);
+        wb[e] = wn * r_exp(-u * u * rb);
     }
 }
 
@@ -571,6 +594,153 @@ __global__ void __launch_bounds__(kSpreadThreads, 5) k_spread(Geo g, const int* 
         if (lane < T) grid[((size_t)(o[2] + lz) * n + (o[1] + ly)) * n + (o[0] + lane)] = acc[(lz * T + ly) * T + lane];
         ly += NW;
         while (ly >= T) { ly -= T; ++lz; }
+    }
+}
+
+// Column-stationary spreading for the common tile edges T (template): one CTA
+// per T^3 tile; candidates are the charged beads of the 27 neighbouring bins;
+// those whose window meets the tile become items; per batch of items the
+// per-dimension weights restricted to the tile (T slots each, zero outside
+// the item's taps, q folded into z) are laid out in shared memory from the
+// per-bead weights; each thread owns one (x, y) column of the tile and adds
+// w_x w_y w_z(z) for every item into T registers. No atomics; the tile is
+// written once.
+constexpr int kColCand = 512;    // candidates staged per round
+constexpr int kColItems = 128;   // items per weight batch
+
+__host__ __device__ constexpr int col_threads(int T) { return T * T <= 128 ? 128 : ((T * T + 31) / 32) * 32; }
+
+template <typename R>
+__host__ __device__ constexpr int col_smem(int T) {
+    return kColCand * (4 + 4 + 8 + (int)sizeof(R)) + kColItems * 3 * T * (int)sizeof(R);
+}
+
+template <typename R, int T>
+__global__ void __launch_bounds__(col_threads(T)) k_spread_col(Geo g, const int* __restrict__ tstart,
+                                                               const typename V4<R>::T* __restrict__ sq,
+                                                               const int* __restrict__ sb,
+                                                               const R* __restrict__ wb, R* __restrict__ grid) {
+    pdl_enter();
+    constexpr int NT = col_threads(T);
+    constexpr int NW = NT / 32;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    R* wt = reinterpret_cast<R*>(smraw);                        // [kColItems][3][T]
+    R* cq = wt + kColItems * 3 * T;                             // [kColCand] charges
+    int* cslot = reinterpret_cast<int*>(cq + kColCand);         // [kColCand] sorted slots
+    int* cbase = cslot + kColCand;                              // [kColCand] packed bases
+    int2* items = reinterpret_cast<int2*>(cbase + kColCand);    // [kColCand] (candidate, masks)
+    __shared__ int nb_start[27], nb_pre[28];
+    __shared__ int nnb, nitems;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tile = blockIdx.x;
+    const int tx = tile % g.ntd, ty = (tile / g.ntd) % g.ntd, tz = tile / (g.ntd * g.ntd);
+    const int o[3] = {tx * T, ty * T, tz * T};
+    const int no = g.ntd >= 3 ? 3 : g.ntd;
+    if (warp == 0) {   // neighbouring bins (<= 27): starts and an exclusive prefix of their sizes
+        const int cntn = no * no * no;
+        int st = 0, c = 0;
+        if (lane < cntn) {
+            const int dx = lane % no, dy = (lane / no) % no, dz = lane / (no * no);
+            const int nz = g.ntd >= 3 ? (tz + dz - 1 + g.ntd) % g.ntd : dz;
+            const int ny = g.ntd >= 3 ? (ty + dy - 1 + g.ntd) % g.ntd : dy;
+            const int nx = g.ntd >= 3 ? (tx + dx - 1 + g.ntd) % g.ntd : dx;
+            const int nt = (nz * g.ntd + ny) * g.ntd + nx;
+            st = tstart[nt];
+            c = tstart[nt + 1] - st;
+        }
+        int x = c;
+#pragma unroll
+        for (int of = 1; of < 32; of <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, of);
+            if (lane >= of) x += y;
+        }
+        if (lane < cntn) {
+            nb_start[lane] = st;
+            nb_pre[lane] = x - c;
+        }
+        if (lane == cntn - 1) {
+            nb_pre[cntn] = x;
+            nnb = cntn;
+        }
+    }
+    __syncthreads();
+    const int P2 = 2 * g.p, n = g.n;
+    const int cx = tid % T, cy = tid / T;   // this thread's column (tid < T^2)
+    const bool owner = tid < T * T;
+    R acc[T];
+#pragma unroll
+    for (int z = 0; z < T; ++z) acc[z] = (R)0;
+    const int total = nb_pre[nnb];
+    for (int cb = 0; cb < total; cb += kColCand) {
+        const int cn = min(kColCand, total - cb);
+        if (tid == 0) nitems = 0;
+        for (int idx = tid; idx < cn; idx += NT) {   // stage: one thread per candidate
+            const int f = cb + idx;
+            int lo = 0, hi = nnb;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (nb_pre[mid] <= f) lo = mid; else hi = mid;
+            }
+            const int j = nb_start[lo] + f - nb_pre[lo];
+            cslot[idx] = j;
+            cbase[idx] = sb[j];
+            cq[idx] = sq[j].w;
+        }
+        __syncthreads();
+        for (int c0 = 0; c0 < cn; c0 += NT) {   // items: candidates whose window meets the tile
+            const int c = c0 + tid;
+            unsigned mx = 0u, my = 0u, mz = 0u;
+            if (c < cn) {
+                const int pb = cbase[c];
+                mx = tap_mask(pb & 1023, o[0], T, n, g.ntd, g.p);
+                if (mx) my = tap_mask((pb >> 10) & 1023, o[1], T, n, g.ntd, g.p);
+                if (my) mz = tap_mask((pb >> 20) & 1023, o[2], T, n, g.ntd, g.p);
+            }
+            const bool keep = mz != 0u;
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            int basei = 0;
+            if (lane == 0 && bal) basei = atomicAdd(&nitems, __popc(bal));
+            basei = __shfl_sync(0xffffffffu, basei, 0);
+            if (keep) items[basei + __popc(bal & ((1u << lane) - 1u))] = make_int2(c, 0);
+        }
+        __syncthreads();
+        const int ni = nitems;
+        for (int ib = 0; ib < ni; ib += kColItems) {
+            const int nb = min(kColItems, ni - ib);
+            // weights restricted to the tile: slot s of dimension d holds the weight of the
+            // tap on grid line o_d + s, or 0 when that line is outside the item's window
+            for (int e = tid; e < nb * 3 * T; e += NT) {
+                const int i = e / (3 * T), r = e - i * (3 * T);
+                const int d = r / T, sl = r - d * T;
+                const int c = items[ib + i].x;
+                const int base = (cbase[c] >> (10 * d)) & 1023;
+                int a = o[d] + sl - base + g.p - 1;
+                if (a < 0) a += n;
+                else if (a >= n) a -= n;
+                R v = (R)0;
+                if (a < P2) v = wb[(size_t)cslot[c] * 3 * P2 + d * P2 + a];
+                if (d == 2) v *= cq[c];
+                wt[e] = v;
+            }
+            __syncthreads();
+            if (owner) {
+                for (int i = 0; i < nb; ++i) {
+                    const R* wi = wt + i * 3 * T;
+                    const R w = wi[cx] * wi[T + cy];
+                    if (w != (R)0) {
+#pragma unroll
+                        for (int z = 0; z < T; ++z) acc[z] += w * wi[2 * T + z];
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (owner) {
+        R* col = grid + ((size_t)o[2] * n + (o[1] + cy)) * n + (o[0] + cx);
+        const size_t n2 = (size_t)n * n;
+#pragma unroll
+        for (int z = 0; z < T; ++z) col[z * n2] = acc[z];
     }
 }
 
@@ -958,7 +1128,7 @@ template <typename R>
 __global__ void __launch_bounds__(kGatherThreads) k_gather(Geo g, const int* __restrict__ tstart,
                                                            const typename V4<R>::T* __restrict__ sq,
                                                            const typename V4<R>::T* __restrict__ sw,
-                                                           const int* __restrict__ sb,
+                                                           const int* __restrict__ sb, const R* __restrict__ wb,
                                                            const R* __restrict__ h, R* __restrict__ F) {
     pdl_enter();
     constexpr int NW = kGatherThreads / 32;
@@ -990,7 +1160,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Geo g, const int* __r
                 l = l < 0 ? l + n : (l >= n ? l - n : l);
                 lix[warp][t][lane] = t == 2 ? l * n * n : l;
                 const R d = fr[t] + (R)(g.p - 1 - lane);   // n x - l
-                const R w = wn * r_exp(-d * d * rb);
+                const R w = wb ? wb[(size_t)s * 3 * P2 + t * P2 + lane] : wn * r_exp(-d * d * rb);
                 wts[warp][t][lane] = w;
                 dwts[warp][t][lane] = (R)-2 * d * rb * w;
             }
