@@ -1224,9 +1224,9 @@ constexpr int kRealHalo = 1024;    // halo tiles (stencil up to 9 x 9 x 9 + 1 fo
 // FP64 also stages a float copy of the positions for the cutoff pre-test
 template <typename R> __host__ __device__ constexpr int real_cap() { return sizeof(R) == 8 ? 1536 : kRealCap; }
 template <typename R>
-constexpr int real_smem_bytes() {
-    return (real_cap<R>() + (kRealThreads / 32) * 64) * (int)sizeof(typename V4<R>::T) +
-           (sizeof(R) == 8 ? real_cap<R>() * (int)sizeof(float4) : 0) + (2 * kRealHalo + 1) * 4;
+constexpr int real_smem_bytes() {   // FP64 adds the float copy, the staged slots and the partner queue
+    return (real_cap<R>() + (kRealThreads / 32) * 64) * (int)sizeof(typename V4<R>::T) + (2 * kRealHalo + 1) * 4 +
+           (sizeof(R) == 8 ? real_cap<R>() * ((int)sizeof(float4) + 4) + (kRealThreads / 32) * 64 * 4 : 0);
 }
 
 // Pair energy u(r) and radial force f(r) = -du/dr of the real-space sum:
@@ -1277,20 +1277,36 @@ __device__ __forceinline__ void real_pair(R r2, R al, R c2a, R be, bool slater, 
 }
 
 // One lane per queued pair (lanes < m).
+// FP64 evaluates each pair once (Newton's third law: +f for bead i in the
+// lane, -f to bead j, original index from its sorted slot, atomically): the
+// erfc/exp run on the FP64 units and halving them pays for the atomics. FP32
+// evaluates both directions (each bead only adds into its own force).
+template <typename R> __host__ __device__ constexpr bool real_half() { return sizeof(R) == 8; }
+
 template <typename R, typename V>
-__device__ __forceinline__ void real_drain(const Geo& g, const V* qu, int m, int lane, R qi, R kap, R al, R c2a, R be,
-                                           bool slater, R& fx, R& fy, R& fz, R& eacc, R& wacc) {
+__device__ __forceinline__ void real_drain(const Geo& g, const V* qu, const int* quj, int m, int lane, R qi, R kap,
+                                           R al, R c2a, R be, bool slater, const V* __restrict__ sw,
+                                           R* __restrict__ F, R& fx, R& fy, R& fz, R& eacc, R& wacc) {
+    constexpr bool HALF = real_half<R>();
     if (lane < m) {
         const V e = qu[lane];
         const R r2 = dist2(e.x, e.y, e.z);
         R u, fo, fr;
         real_pair<R>(r2, al, c2a, be, slater, u, fo, fr, static_cast<const R*>(g.ktab), g.kn, (R)g.kinv, (R)g.kh);
         const R qq = kap * qi * e.w;
-        fx += qq * fo * e.x;
-        fy += qq * fo * e.y;
-        fz += qq * fo * e.z;
-        eacc += (R)0.5 * qq * u;
-        wacc += (R)0.5 * qq * fr;
+        const R gx = qq * fo * e.x, gy = qq * fo * e.y, gz = qq * fo * e.z;
+        fx += gx;
+        fy += gy;
+        fz += gz;
+        if (HALF) {
+            const int j = real_as_int(sw[quj[lane]].w);
+            atomicAdd(&F[3 * j], -gx);
+            atomicAdd(&F[3 * j + 1], -gy);
+            atomicAdd(&F[3 * j + 2], -gz);
+        }
+        const R ws = HALF ? (R)1 : (R)0.5;   // energy and virial per pair
+        eacc += ws * qq * u;
+        wacc += ws * qq * fr;
     }
 }
 
@@ -1306,9 +1322,9 @@ __device__ __forceinline__ void halo_dim(int t, int rs, int ntd, int& lo, int& c
 // the halo prefix.
 template <typename R, bool STAGED>
 __device__ __forceinline__ void real_beads(const Geo& g, int c0, int c1, int selfbase, int total, int nh,
-                                           const typename V4<R>::T* stg, const float4* stgf, const int* hoff,
-                                           const int* gst, const typename V4<R>::T* __restrict__ sq,
-                                           const typename V4<R>::T* __restrict__ sw, typename V4<R>::T* qu,
+                                           const typename V4<R>::T* stg, const float4* stgf, const int* stgslot,
+                                           const int* hoff, const int* gst, const typename V4<R>::T* __restrict__ sq,
+                                           const typename V4<R>::T* __restrict__ sw, typename V4<R>::T* qu, int* quj,
                                            R* __restrict__ F, R& eacc, R& wacc) {
     using V = typename V4<R>::T;
     constexpr int NW = kRealThreads / 32;
@@ -1326,7 +1342,7 @@ __device__ __forceinline__ void real_beads(const Geo& g, int c0, int c1, int sel
     for (int s = c0 + warp; s < c1; s += NW) {
         const V pi = sq[s];
         const float4 pif = make_float4((float)pi.x, (float)pi.y, (float)pi.z, 0.f);
-        const int self = selfbase + (s - c0);
+        const int self = selfbase + (s - c0);   // the bead's own index in the halo order
         R fx = 0, fy = 0, fz = 0;
         int cnt = 0;
         int hseg = 0;
@@ -1337,7 +1353,27 @@ __device__ __forceinline__ void real_beads(const Geo& g, int c0, int c1, int sel
                 const int f = it * 32 + lane;
                 bool hit = false;
                 R dx = 0, dy = 0, dz = 0, qj = 0;
-                bool cand = f < total && f != self;
+                // FP64: each pair once, only candidates with a larger sorted slot;
+                // FP32: every candidate but the bead itself
+                int gs = -1;
+                bool cand;
+                if constexpr (real_half<R>()) {
+                    if (f < total) {
+                        if (STAGED) {
+                            gs = stgslot[f];
+                        } else {
+                            while (hseg + 1 < nh && hoff[hseg + 1] <= f) ++hseg;
+                            gs = gst[hseg] + f - hoff[hseg];
+                        }
+                    }
+                    cand = gs > s;
+                } else {
+                    cand = f < total && f != self;
+                    if (cand && !STAGED) {
+                        while (hseg + 1 < nh && hoff[hseg + 1] <= f) ++hseg;
+                        gs = gst[hseg] + f - hoff[hseg];
+                    }
+                }
                 if (PRE && cand) {
                     const float4 b = stgf[f];
                     const float rx = min_image(pif.x, b.x, Lf, hLf);
@@ -1347,12 +1383,7 @@ __device__ __forceinline__ void real_beads(const Geo& g, int c0, int c1, int sel
                 }
                 if (cand) {
                     V pj;
-                    if (STAGED) {
-                        pj = stg[f];
-                    } else {
-                        while (hseg + 1 < nh && hoff[hseg + 1] <= f) ++hseg;
-                        pj = sq[gst[hseg] + f - hoff[hseg]];
-                    }
+                    pj = STAGED ? stg[f] : sq[gs];
                     dx = min_image(pi.x, pj.x, L, hL);
                     dy = min_image(pi.y, pj.y, L, hL);
                     dz = min_image(pi.z, pj.z, L, hL);
@@ -1364,16 +1395,21 @@ __device__ __forceinline__ void real_beads(const Geo& g, int c0, int c1, int sel
                 if (hit) {
                     V e;
                     e.x = dx; e.y = dy; e.z = dz; e.w = qj;
-                    qu[cnt + __popc(m & ((1u << lane) - 1u))] = e;
+                    const int at = cnt + __popc(m & ((1u << lane) - 1u));
+                    qu[at] = e;
+                    if (real_half<R>()) quj[at] = gs;
                 }
                 cnt += __popc(m);
             }
             if (cnt >= 32 || (last && cnt > 0)) {
                 const int m = min(cnt, 32);
                 __syncwarp();
-                real_drain<R, V>(g, qu, m, lane, pi.w, kap, al, c2a, be, slater, fx, fy, fz, eacc, wacc);
+                real_drain<R, V>(g, qu, quj, m, lane, pi.w, kap, al, c2a, be, slater, sw, F, fx, fy, fz, eacc, wacc);
                 __syncwarp();
-                if (lane < cnt - m) qu[lane] = qu[m + lane];
+                if (lane < cnt - m) {
+                    qu[lane] = qu[m + lane];
+                    if (real_half<R>()) quj[lane] = quj[m + lane];
+                }
                 __syncwarp();
                 cnt -= m;
             }
@@ -1383,9 +1419,15 @@ __device__ __forceinline__ void real_beads(const Geo& g, int c0, int c1, int sel
         fz = warp_sum_r(fz);
         if (lane == 0) {
             const int i = real_as_int(sw[s].w);
-            F[3 * i] += fx;
-            F[3 * i + 1] += fy;
-            F[3 * i + 2] += fz;
+            if (real_half<R>()) {   // other warps add into this bead's force as its partners
+                atomicAdd(&F[3 * i], fx);
+                atomicAdd(&F[3 * i + 1], fy);
+                atomicAdd(&F[3 * i + 2], fz);
+            } else {
+                F[3 * i] += fx;
+                F[3 * i + 1] += fy;
+                F[3 * i + 2] += fz;
+            }
         }
     }
 }
@@ -1411,6 +1453,8 @@ __global__ void __launch_bounds__(kRealThreads) k_real(Geo g, const int* __restr
     float4* stgf = reinterpret_cast<float4*>(queue + NW * 64);  // [CAP] float positions (FP64 only)
     int* hoff = reinterpret_cast<int*>(stgf + (sizeof(R) == 8 ? CAP : 0));   // [kRealHalo + 1]
     int* gst = hoff + kRealHalo + 1;                            // [kRealHalo]
+    int* stgslot = gst + kRealHalo;                             // [CAP] sorted slot of each staged bead (FP64)
+    int* quj = stgslot + CAP;                                   // [NW][64] partner slots (FP64)
     __shared__ int wtot[NW];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     V* qu = queue + warp * 64;
@@ -1471,8 +1515,10 @@ __global__ void __launch_bounds__(kRealThreads) k_real(Geo g, const int* __restr
                     const int mid = (lo + hi) >> 1;
                     if (hoff[mid] <= f) lo = mid; else hi = mid;
                 }
-                const V v = sq[gst[lo] + f - hoff[lo]];
+                const int gsl = gst[lo] + f - hoff[lo];
+                const V v = sq[gsl];
                 stg[f] = v;
+                if (real_half<R>()) stgslot[f] = gsl;
                 if (sizeof(R) == 8) stgf[f] = make_float4((float)v.x, (float)v.y, (float)v.z, 0.f);
             }
         }
@@ -1481,9 +1527,11 @@ __global__ void __launch_bounds__(kRealThreads) k_real(Geo g, const int* __restr
         const int c0 = tstart[tile], c1 = tstart[tile + 1];
         const int hc = (((tz - zlo + g.ntd) % g.ntd) * yc + (ty - ylo + g.ntd) % g.ntd) * xc + (tx - xlo + g.ntd) % g.ntd;
         if (staged)
-            real_beads<R, true>(g, c0, c1, hoff[hc], total, nh, stg, stgf, hoff, gst, sq, sw, qu, F, eacc, wacc);
+            real_beads<R, true>(g, c0, c1, hoff[hc], total, nh, stg, stgf, stgslot, hoff, gst, sq, sw, qu,
+                                quj + warp * 64, F, eacc, wacc);
         else
-            real_beads<R, false>(g, c0, c1, hoff[hc], total, nh, stg, stgf, hoff, gst, sq, sw, qu, F, eacc, wacc);
+            real_beads<R, false>(g, c0, c1, hoff[hc], total, nh, stg, stgf, stgslot, hoff, gst, sq, sw, qu,
+                                 quj + warp * 64, F, eacc, wacc);
         __syncthreads();
     }
     double e = (double)eacc, w = (double)wacc;
