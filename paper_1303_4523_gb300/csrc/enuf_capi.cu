@@ -271,16 +271,18 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
     fs.tz = std::min(256, std::max(fs.tz, ((g.nf * fs.lz * n / 4 + 31) / 32) * 32));
     shape(g.nf * n * nc1, 2, fs.liy, fs.tiy, fs.grid_iy);
     shape(g.nf * n * n / 2, 2, fs.lix, fs.tix, fs.grid_ix);
-    fs.smem_x = (1 + 2 * fs.lx) * n * csz;
-    fs.smem_y = (1 + 2 * fs.ly) * n * csz;
-    fs.smem_z = (1 + (2 + 2 * g.nf) * fs.lz) * n * csz;
-    fs.smem_iy = (1 + 2 * fs.liy) * n * csz;
+    // twiddles + line buffers; the x, y, z and inverse-y passes pad their lines to n + 1
+    // (their transposed shared-memory accesses then fall on different banks)
+    fs.smem_x = (n + 2 * fs.lx * (n + 1)) * csz;
+    fs.smem_y = (n + 2 * fs.ly * (n + 1)) * csz;
+    fs.smem_z = (n + (2 + 2 * g.nf) * fs.lz * (n + 1)) * csz;
+    fs.smem_iy = (n + 2 * fs.liy * (n + 1)) * csz;
     fs.smem_ix = (1 + 2 * fs.lix) * n * csz;
     // fused plane passes (one CTA per z-plane) for FP32 grids whose twiddles and two
     // n^2/2-line buffers take <= 100 KB (n <= 112): measured faster there; larger planes
     // and FP64 (1 CTA per SM, FP64-bound butterflies on n CTAs) keep the five passes
     {
-        const long long plane = (long long)(n + n * n) * csz;
+        const long long plane = (long long)(n + n * (n + 1)) * csz;
         fs.fused = (P.prec == ENUF_FP32 && plane <= 100 * 1024 && P.fft_path == 0) ? 1 : 0;
         fs.smem_xy = fs.smem_yx = (int)plane;
         fs.t_xy = fs.t_yx = 512;

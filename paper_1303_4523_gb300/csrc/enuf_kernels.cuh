@@ -757,8 +757,9 @@ __global__ void __launch_bounds__(256) k_fft_x(Geo g, FftPlanDev fp, const R* __
     extern __shared__ unsigned char smraw[];
     const int n = g.n, nc1 = g.nc + 1;
     C* tw = reinterpret_cast<C*>(smraw);
+    const int ls = n + 1;   // padded line stride: the split reads across lines
     C* b0 = tw + n;
-    C* b1 = b0 + LP * n;
+    C* b1 = b0 + LP * ls;
     for (int t = threadIdx.x; t < n; t += blockDim.x) tw[t] = twg[t];
     const float rn = 1.0f / (float)n;
     const int row0 = blockIdx.x * 2 * LP;     // first real row (z*n + y), y even
@@ -770,15 +771,15 @@ __global__ void __launch_bounds__(256) k_fft_x(Geo g, FftPlanDev fp, const R* __
         C v;
         v.x = grid[(size_t)(row0 + 2 * c) * n + x];
         v.y = grid[(size_t)(row0 + 2 * c + 1) * n + x];
-        b0[c * n + x] = v;
+        b0[c * ls + x] = v;
     }
     __syncthreads();
-    C* res = fft_lines<R, false>(b0, b1, tw, fp, nl, n);
+    C* res = fft_lines<R, false>(b0, b1, tw, fp, nl, ls);
     // split the two real transforms: A = (Z_k + conj Z_{n-k})/2, B = -i (Z_k - conj Z_{n-k})/2
     for (int idx = threadIdx.x; idx < nl * nc1; idx += blockDim.x) {
         const int k = qdiv(idx, nl, rnl), c = idx - k * nl;
-        const C z = res[c * n + k];
-        const C zm = res[c * n + (k == 0 ? 0 : n - k)];
+        const C z = res[c * ls + k];
+        const C zm = res[c * ls + (k == 0 ? 0 : n - k)];
         C A, B;
         A.x = (R)0.5 * (z.x + zm.x);
         A.y = (R)0.5 * (z.y - zm.y);
@@ -802,8 +803,9 @@ __global__ void __launch_bounds__(256) k_fft_y(Geo g, FftPlanDev fp, const typen
     extern __shared__ unsigned char smraw[];
     const int n = g.n, nc1 = g.nc + 1, K = g.K;
     C* tw = reinterpret_cast<C*>(smraw);
+    const int ls = n + 1;   // padded line stride: the output reads across lines
     C* b0 = tw + n;
-    C* b1 = b0 + LB * n;
+    C* b1 = b0 + LB * ls;
     for (int t = threadIdx.x; t < n; t += blockDim.x) tw[t] = twg[t];
     const float rn = 1.0f / (float)n;
     const int kx = blockIdx.x;
@@ -812,14 +814,14 @@ __global__ void __launch_bounds__(256) k_fft_y(Geo g, FftPlanDev fp, const typen
     const float rnl = 1.0f / (float)max(nl, 1);
     for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
         const int c = qdiv(idx, n, rn), y = idx - c * n;
-        b0[c * n + y] = spec1[((size_t)(z0 + c) * nc1 + kx) * n + y];
+        b0[c * ls + y] = spec1[((size_t)(z0 + c) * nc1 + kx) * n + y];
     }
     __syncthreads();
-    C* res = fft_lines<R, false>(b0, b1, tw, fp, nl, n);
+    C* res = fft_lines<R, false>(b0, b1, tw, fp, nl, ls);
     for (int idx = threadIdx.x; idx < nl * K; idx += blockDim.x) {
         const int ki = qdiv(idx, nl, rnl), c = idx - ki * nl;
         const int ky = ki - g.nc;
-        spec2[((size_t)kx * K + ki) * n + z0 + c] = res[c * n + (ky < 0 ? ky + n : ky)];
+        spec2[((size_t)kx * K + ki) * n + z0 + c] = res[c * ls + (ky < 0 ? ky + n : ky)];
     }
 }
 
@@ -840,10 +842,11 @@ __global__ void __launch_bounds__(256) k_fft_z(Geo g, FftPlanDev fp, const typen
     const int NL = (nc + 1) * K;
     const float rK = 1.0f / (float)K, rn = 1.0f / (float)n;
     C* tw = reinterpret_cast<C*>(smraw);
-    C* b0 = tw + n;               // [LB][n] forward lines
-    C* b1 = b0 + LB * n;          // [LB][n] scratch
-    C* X = b1 + LB * n;           // [nf][LB][n] fields
-    C* Y = X + nf * LB * n;       // [nf][LB][n] scratch
+    const int ls = n + 1;         // padded line stride: loads and stores go across lines
+    C* b0 = tw + n;               // [LB][ls] forward lines
+    C* b1 = b0 + LB * ls;         // [LB][ls] scratch
+    C* X = b1 + LB * ls;          // [nf][LB][ls] fields
+    C* Y = X + nf * LB * ls;      // [nf][LB][ls] scratch
     for (int t = threadIdx.x; t < n; t += blockDim.x) tw[t] = twg[t];
     const int l0 = blockIdx.x * LB;
     const int nl = min(LB, NL - l0);
@@ -851,13 +854,16 @@ __global__ void __launch_bounds__(256) k_fft_z(Geo g, FftPlanDev fp, const typen
     if (plane_major) {   // spec2[z][l]: lines gathered across planes
         for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
             const int z = qdiv(idx, nl, rnl), c = idx - z * nl;
-            b0[c * n + z] = spec2[(size_t)z * NL + l0 + c];
+            b0[c * ls + z] = spec2[(size_t)z * NL + l0 + c];
         }
     } else {             // spec2[l][z]: lines contiguous
-        for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) b0[idx] = spec2[(size_t)l0 * n + idx];
+        for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
+            const int c = qdiv(idx, n, rn), z = idx - c * n;
+            b0[c * ls + z] = spec2[(size_t)l0 * n + idx];
+        }
     }
     __syncthreads();
-    C* Fh = fft_lines<R, false>(b0, b1, tw, fp, nl, n);
+    C* Fh = fft_lines<R, false>(b0, b1, tw, fp, nl, ls);
     // energy and virial of the kept modes (half space kx >= 0, kx > 0 counted twice)
     Kahan ke, kw;
     for (int idx = threadIdx.x; idx < nl * K; idx += blockDim.x) {
@@ -865,7 +871,7 @@ __global__ void __launch_bounds__(256) k_fft_z(Geo g, FftPlanDev fp, const typen
         const int l = l0 + c;
         const int kx = qdiv(l, K, rK);
         const int kz = kzi - nc;
-        const C f = Fh[c * n + (kz < 0 ? kz + n : kz)];
+        const C f = Fh[c * ls + (kz < 0 ? kz + n : kz)];
         const double a2 = (double)f.x * (double)f.x + (double)f.y * (double)f.y;
         const double wgt = kx == 0 ? 1.0 : 2.0;
         ke.add(wgt * tab[(size_t)l * K + kzi] * a2);
@@ -890,7 +896,7 @@ __global__ void __launch_bounds__(256) k_fft_z(Geo g, FftPlanDev fp, const typen
         if (kz >= -nc && kz <= nc) {
             const int l = l0 + c;
             const R d = tabr[(size_t)l * K + (kz + nc)];
-            const C f = Fh[c * n + m];
+            const C f = Fh[c * ls + m];
             if (nf == 1) {
                 v.x = d * f.x;     // D F
                 v.y = d * f.y;
@@ -902,14 +908,14 @@ __global__ void __launch_bounds__(256) k_fft_z(Geo g, FftPlanDev fp, const typen
                 v.y = -s * f.x;
             }
         }
-        X[idx] = v;
+        X[(a * nl + c) * ls + m] = v;
     }
     __syncthreads();
-    C* res = fft_lines<R, true>(X, Y, tw, fp, nf * nl, n);
+    C* res = fft_lines<R, true>(X, Y, tw, fp, nf * nl, ls);
     for (int idx = threadIdx.x; idx < nf * per; idx += blockDim.x) {
         const int a = qdiv(idx, per, rper), e = idx - a * per;
         const int z = qdiv(e, nl, rnl), c = e - z * nl;
-        spec3[((size_t)a * n + z) * NL + l0 + c] = res[(a * nl + c) * n + z];
+        spec3[((size_t)a * n + z) * NL + l0 + c] = res[(a * nl + c) * ls + z];
     }
 }
 
@@ -927,8 +933,9 @@ __global__ void __launch_bounds__(512) k_fft_xy(Geo g, FftPlanDev fp, const R* _
     const int n = g.n, nc = g.nc, nc1 = nc + 1, K = g.K, h = n / 2;
     const float rn = 1.0f / (float)n, rh = 1.0f / (float)h, rK = 1.0f / (float)K;
     C* tw = reinterpret_cast<C*>(smraw);
-    C* L0 = tw + n;        // [n/2][n]
-    C* L1 = L0 + h * n;    // [n/2][n]
+    const int ls = n + 1;  // padded stride of the x lines (the split reads across them)
+    C* L0 = tw + n;        // [n/2][ls]
+    C* L1 = L0 + h * ls;   // [n/2][ls]
     for (int t = threadIdx.x; t < n; t += blockDim.x) tw[t] = twg[t];
     const int z = blockIdx.x;
     const R* gz = grid + (size_t)z * n * n;
@@ -937,17 +944,17 @@ __global__ void __launch_bounds__(512) k_fft_xy(Geo g, FftPlanDev fp, const R* _
         C v;
         v.x = gz[(size_t)(2 * c) * n + x];
         v.y = gz[(size_t)(2 * c + 1) * n + x];
-        L0[idx] = v;
+        L0[c * ls + x] = v;
     }
     __syncthreads();
-    C* X = fft_lines<R, false>(L0, L1, tw, fp, h, n);
+    C* X = fft_lines<R, false>(L0, L1, tw, fp, h, ls);
     C* P = X == L0 ? L1 : L0;   // [nc+1][n] columns over y, then scratch
     C* S = P + nc1 * n;         // 2 (nc + 1) = n/2: P and S fill the other buffer
     // split the two real transforms: A = (Z_k + conj Z_{n-k})/2, B = -i (Z_k - conj Z_{n-k})/2
     for (int idx = threadIdx.x; idx < nc1 * h; idx += blockDim.x) {
         const int k = qdiv(idx, h, rh), c = idx - k * h;
-        const C zk = X[c * n + k];
-        const C zm = X[c * n + (k == 0 ? 0 : n - k)];
+        const C zk = X[c * ls + k];
+        const C zm = X[c * ls + (k == 0 ? 0 : n - k)];
         C A, B;
         A.x = (R)0.5 * (zk.x + zm.x);
         A.y = (R)0.5 * (zk.y - zm.y);
@@ -979,13 +986,14 @@ __global__ void __launch_bounds__(512) k_fft_yx(Geo g, FftPlanDev fp, const type
     const int n = g.n, nc = g.nc, nc1 = nc + 1, K = g.K, hn = n / 2;
     const float rn = 1.0f / (float)n;
     C* tw = reinterpret_cast<C*>(smraw);
-    C* L0 = tw + n;         // [n/2][n]
-    C* L1 = L0 + hn * n;    // [n/2][n]
+    const int ls = n + 1;   // padded stride of the y columns (the x lines read across them)
+    C* L0 = tw + n;         // [n/2][ls]: the nc + 1 columns and their scratch
+    C* L1 = L0 + hn * ls;   // [n/2][n]: the x lines
     for (int t = threadIdx.x; t < n; t += blockDim.x) tw[t] = twg[t];
     const int az = blockIdx.x;   // a * n + z
     const C* in = spec3 + (size_t)az * nc1 * K;
-    C* P = L0;                   // [nc+1][n] columns over y
-    C* S = L0 + nc1 * n;
+    C* P = L0;                   // [nc+1][ls] columns over y
+    C* S = L0 + nc1 * ls;
     for (int idx = threadIdx.x; idx < nc1 * n; idx += blockDim.x) {
         const int kx = qdiv(idx, n, rn), m = idx - kx * n;
         const int ky = m <= n / 2 ? m : m - n;
@@ -993,10 +1001,10 @@ __global__ void __launch_bounds__(512) k_fft_yx(Geo g, FftPlanDev fp, const type
         v.x = (R)0;
         v.y = (R)0;
         if (ky >= -nc && ky <= nc) v = in[kx * K + (ky + nc)];
-        P[idx] = v;
+        P[kx * ls + m] = v;
     }
     __syncthreads();
-    C* Yc = fft_lines<R, true>(P, S, tw, fp, nc1, n);   // [kx][y], in L0
+    C* Yc = fft_lines<R, true>(P, S, tw, fp, nc1, ls);   // [kx][y], in L0
     // x lines: row pair (2c, 2c+1) as A + i B with the Hermitian extension
     for (int idx = threadIdx.x; idx < hn * n; idx += blockDim.x) {
         const int c = qdiv(idx, n, rn), m = idx - c * n;
@@ -1006,12 +1014,12 @@ __global__ void __launch_bounds__(512) k_fft_yx(Geo g, FftPlanDev fp, const type
             a.x = Yc[2 * c].x;
             b.x = Yc[2 * c + 1].x;
         } else if (m <= nc) {
-            a = Yc[m * n + 2 * c];
-            b = Yc[m * n + 2 * c + 1];
+            a = Yc[m * ls + 2 * c];
+            b = Yc[m * ls + 2 * c + 1];
         } else if (m >= n - nc) {
-            a = Yc[(n - m) * n + 2 * c];
+            a = Yc[(n - m) * ls + 2 * c];
             a.y = -a.y;
-            b = Yc[(n - m) * n + 2 * c + 1];
+            b = Yc[(n - m) * ls + 2 * c + 1];
             b.y = -b.y;
         }
         C zz;
@@ -1042,8 +1050,9 @@ __global__ void __launch_bounds__(256) k_fft_iy(Geo g, FftPlanDev fp, const type
     const int NLT = g.nf * n * nc1;
     const float rnc1 = 1.0f / (float)nc1;
     C* tw = reinterpret_cast<C*>(smraw);
+    const int ls = n + 1;   // padded line stride: the output reads across lines
     C* b0 = tw + n;
-    C* b1 = b0 + LB * n;
+    C* b1 = b0 + LB * ls;
     for (int t = threadIdx.x; t < n; t += blockDim.x) tw[t] = twg[t];
     const float rn = 1.0f / (float)n;
     const int l0 = blockIdx.x * LB;
@@ -1056,15 +1065,15 @@ __global__ void __launch_bounds__(256) k_fft_iy(Geo g, FftPlanDev fp, const type
         v.x = (R)0;
         v.y = (R)0;
         if (ky >= -nc && ky <= nc) v = spec3[(size_t)(l0 + c) * K + (ky + nc)];
-        b0[idx] = v;
+        b0[c * ls + m] = v;
     }
     __syncthreads();
-    C* res = fft_lines<R, true>(b0, b1, tw, fp, nl, n);
+    C* res = fft_lines<R, true>(b0, b1, tw, fp, nl, ls);
     for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
         const int y = qdiv(idx, nl, rnl), c = idx - y * nl;
         const int l = l0 + c;
         const int az = qdiv(l, nc1, rnc1), kx = l - az * nc1;
-        spec4[((size_t)az * n + y) * nc1 + kx] = res[c * n + y];
+        spec4[((size_t)az * n + y) * nc1 + kx] = res[c * ls + y];
     }
 }
 
