@@ -334,7 +334,8 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
     const size_t ncmp = (size_t)g.nbin * g.chunk;   // compacted-bead slots
     size_t o_cnt = take((size_t)g.nbin * 4), o_bhist = take((size_t)g.nbin * g.ntiles * 4),
            o_boff = take((size_t)g.nbin * g.ntiles * 4), o_ttot = take((size_t)g.ntiles * 4),
-           o_tstart = take((size_t)(g.ntiles + 1) * 4), o_ctile = take(ncmp * 4), o_cpos = take(ncmp * 4 * esz),
+           o_tstart = take((size_t)(g.ntiles + 1) * 4), o_tk = take(16), o_ctile = take(ncmp * 4),
+           o_cpos = take(ncmp * 4 * esz),
            o_cfrac = take(ncmp * 4 * esz), o_cbase = take(ncmp * 4),
            o_sq = take(nm * 4 * esz), o_sw = take(nm * 4 * esz), o_sb = take(nm * 4),
            o_wb = take(nm * 3 * 2 * P.p * esz), o_grid = take(n3 * esz),
@@ -356,7 +357,7 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
         plan->fp = fp;
         // stash offsets; bound to the allocation in bind()
         w.cnt_blk = (int*)o_cnt; w.bhist = (int*)o_bhist; w.boff = (int*)o_boff; w.ttot = (int*)o_ttot;
-        w.tstart = (int*)o_tstart; w.ctile = (int*)o_ctile; w.cpos = (void*)o_cpos; w.cfrac = (void*)o_cfrac;
+        w.tstart = (int*)o_tstart; w.ticket = (int*)o_tk; w.ctile = (int*)o_ctile; w.cpos = (void*)o_cpos; w.cfrac = (void*)o_cfrac;
         w.cbase = (int*)o_cbase;
         w.sq = (void*)o_sq; w.sw = (void*)o_sw; w.sb = (int*)o_sb; w.wb = (void*)o_wb; w.grid = (void*)o_grid;
         w.spec1 = (void*)o_s1; w.spec2 = (void*)o_s2; w.spec3 = (void*)o_s3; w.spec4 = (void*)o_s4;
@@ -373,7 +374,7 @@ void bind(enuf_plan_t p) {
     Work& w = p->w;
     auto at = [&](auto ptr) { return reinterpret_cast<decltype(ptr)>(b + reinterpret_cast<size_t>(ptr)); };
     w.cnt_blk = at(w.cnt_blk); w.bhist = at(w.bhist); w.boff = at(w.boff); w.ttot = at(w.ttot);
-    w.tstart = at(w.tstart); w.ctile = at(w.ctile); w.cpos = at(w.cpos); w.cfrac = at(w.cfrac);
+    w.tstart = at(w.tstart); w.ticket = at(w.ticket); w.ctile = at(w.ctile); w.cpos = at(w.cpos); w.cfrac = at(w.cfrac);
     w.cbase = at(w.cbase);
     w.sq = at(w.sq); w.sw = at(w.sw); w.sb = at(w.sb); w.wb = at(w.wb); w.grid = at(w.grid);
     w.spec1 = at(w.spec1); w.spec2 = at(w.spec2); w.spec3 = at(w.spec3); w.spec4 = at(w.spec4);
@@ -454,13 +455,17 @@ enuf_status upload_tables(enuf_plan_t plan) {
     return ENUF_OK;
 }
 
+// fuse_totals: the gather's last block also reduces the energies (evaluations
+// outside a DPD step, where nothing follows the gather).
 enuf_status enqueue_eval(enuf_plan_t plan, const EvalArgs& a, cudaStream_t s0, cudaStream_t s1,
-                         cudaEvent_t evFork, cudaEvent_t evJoin, Events* ev, LaunchLog* log) {
+                         cudaEvent_t evFork, cudaEvent_t evJoin, Events* ev, LaunchLog* log, bool fuse_totals) {
     cudaError_t e;
     if (plan->prec == ENUF_FP32)
-        e = enqueue_enuf<float>(plan->g, plan->fs, plan->fp, plan->w, a, s0, s1, evFork, evJoin, ev, log);
+        e = enqueue_enuf<float>(plan->g, plan->fs, plan->fp, plan->w, a, s0, s1, evFork, evJoin, ev, log,
+                                fuse_totals);
     else
-        e = enqueue_enuf<double>(plan->g, plan->fs, plan->fp, plan->w, a, s0, s1, evFork, evJoin, ev, log);
+        e = enqueue_enuf<double>(plan->g, plan->fs, plan->fp, plan->w, a, s0, s1, evFork, evJoin, ev, log,
+                                 fuse_totals);
     if (e != cudaSuccess) return fail(plan, ENUF_ERR_CUDA, "enqueue: %s", cudaGetErrorString(e));
     return ENUF_OK;
 }
@@ -488,8 +493,7 @@ enuf_status capture_eval(enuf_plan_t plan, int n, const void* pos, const void* q
     Events* ev = plan->ev.on ? &plan->ev : nullptr;
     if (ev) cudaEventRecordWithFlags(ev->start[6], plan->stream, cudaEventRecordExternal);
     EvalArgs a{n, pos, q, F, true};
-    enuf_status st = enqueue_eval(plan, a, plan->stream, plan->aux, plan->evFork, plan->evJoin, ev, &log);
-    if (st == ENUF_OK) st = enqueue_tot(plan, false, plan->stream, &log);
+    enuf_status st = enqueue_eval(plan, a, plan->stream, plan->aux, plan->evFork, plan->evJoin, ev, &log, true);
     if (st == ENUF_OK) {
         cudaError_t e = cudaMemcpyAsync(plan->hE, plan->w.Edev, 16 * sizeof(double), cudaMemcpyDeviceToHost,
                                         plan->stream);
@@ -742,7 +746,7 @@ enuf_status enqueue_force_eval(dpd_system_t sys, cudaStream_t s0, cudaStream_t s
     if (e != cudaSuccess) return fail(plan, ENUF_ERR_CUDA, "dpd enqueue: %s", cudaGetErrorString(e));
     // electrostatics added into F (real space follows the DPD kernel on s1)
     EvalArgs a{sys->d.N, sys->d.pos, sys->d.q, sys->d.F, false};
-    return enqueue_eval(plan, a, s0, s1, plan->evFork, plan->evJoin, ev, log);
+    return enqueue_eval(plan, a, s0, s1, plan->evFork, plan->evJoin, ev, log, false);
 }
 
 enuf_status initial_force(dpd_system_t sys) {
@@ -774,11 +778,12 @@ enuf_status capture_step(dpd_system_t sys) {
     enuf_status st = e == cudaSuccess ? ENUF_OK : fail(plan, ENUF_ERR_CUDA, "vv_pre: %s", cudaGetErrorString(e));
     if (st == ENUF_OK) st = enqueue_force_eval(sys, plan->stream, plan->aux, ev, &log);
     if (st == ENUF_OK) {
-        e = plan->prec == ENUF_FP32 ? enqueue_vv_post<float>(plan->w, sys->d, plan->stream, &log, !plan->ev.on)
-                                    : enqueue_vv_post<double>(plan->w, sys->d, plan->stream, &log, !plan->ev.on);
+        // the last block of the half kick reduces the step's energies
+        e = plan->prec == ENUF_FP32
+                ? enqueue_vv_post<float>(plan->g, plan->w, sys->d, plan->stream, &log, !plan->ev.on)
+                : enqueue_vv_post<double>(plan->g, plan->w, sys->d, plan->stream, &log, !plan->ev.on);
         if (e != cudaSuccess) st = fail(plan, ENUF_ERR_CUDA, "vv_post: %s", cudaGetErrorString(e));
     }
-    if (st == ENUF_OK) st = enqueue_tot(plan, true, plan->stream, &log);
     if (st == ENUF_OK) {
         e = cudaMemcpyAsync(plan->hE, plan->w.Edev, 16 * sizeof(double), cudaMemcpyDeviceToHost, plan->stream);
         if (e != cudaSuccess) st = fail(plan, ENUF_ERR_CUDA, "memcpy: %s", cudaGetErrorString(e));
@@ -1016,8 +1021,7 @@ enuf_status enuf_batch_energy_forces(enuf_batch_t b, const void* const* pos, con
             enuf_plan_t p = b->plans[s];
             cudaStreamWaitEvent(p->stream, b->evStart, 0);
             EvalArgs a{b->n[s], pos[s], q[s], F[s], true};
-            st = enqueue_eval(p, a, p->stream, p->aux, p->evFork, p->evJoin, nullptr, &log);
-            if (st == ENUF_OK) st = enqueue_tot(p, false, p->stream, &log);
+            st = enqueue_eval(p, a, p->stream, p->aux, p->evFork, p->evJoin, nullptr, &log, true);
             if (st == ENUF_OK)
                 cudaMemcpyAsync(p->hE, p->w.Edev, 16 * sizeof(double), cudaMemcpyDeviceToHost, p->stream);
             cudaEventRecord(b->evDone[s], p->stream);
@@ -1102,7 +1106,7 @@ extern "C" enuf_status enuf_spread_noalloc(const enuf_params* params, int n, con
     const size_t ncmp = (size_t)g.nbin * g.chunk;
     const size_t o_cnt = take((size_t)g.nbin * 4), o_bhist = take((size_t)g.nbin * g.ntiles * 4),
                  o_boff = take((size_t)g.nbin * g.ntiles * 4), o_ttot = take((size_t)g.ntiles * 4),
-                 o_tstart = take((size_t)(g.ntiles + 1) * 4), o_ctile = take(ncmp * 4),
+                 o_tstart = take((size_t)(g.ntiles + 1) * 4), o_tk = take(16), o_ctile = take(ncmp * 4),
                  o_cpos = take(ncmp * 4 * esz), o_cfrac = take(ncmp * 4 * esz), o_cbase = take(ncmp * 4),
                  o_sq = take(nm * 4 * esz), o_sw = take(nm * 4 * esz), o_sb = take(nm * 4),
                  o_part = take((size_t)2 * g.nbin * 8);
@@ -1144,6 +1148,7 @@ extern "C" enuf_status enuf_spread_noalloc(const enuf_params* params, int n, con
     w.boff = reinterpret_cast<int*>(b + o_boff);
     w.ttot = reinterpret_cast<int*>(b + o_ttot);
     w.tstart = reinterpret_cast<int*>(b + o_tstart);
+    w.ticket = reinterpret_cast<int*>(b + o_tk);   // zero at load, returned to zero by each use
     w.ctile = reinterpret_cast<int*>(b + o_ctile);
     w.cpos = b + o_cpos;
     w.cfrac = b + o_cfrac;

@@ -58,6 +58,31 @@ inline void launch(bool pdl, bool critical, void (*k)(P...), dim3 grid, dim3 blo
 
 inline bool pdl_ok(const Events* ev) { return !(ev && ev->on); }
 
+// Totals inputs of a plan (dpd: include the DPD and kinetic partials); the
+// ticket index selects the arrival counter of the reducing kernel.
+inline TotalsArgs totals_args(const Geo& g, const Work& w, bool dpd, int ticket) {
+    TotalsArgs t;
+    t.part = w.part;
+    t.off_q = w.off_q;
+    t.nq = g.nbin;
+    t.off_real = w.off_real;
+    t.nreal = w.nblk_real;
+    t.off_recip = w.off_recip;
+    t.nrecip = w.nblk_conv;
+    t.off_dpd = w.off_dpd;
+    t.ndpd = dpd ? w.nblk_dpd : 0;
+    t.off_kin = w.off_kin;
+    t.nkin = dpd ? w.nblk_kin : 0;
+    t.Edev = w.Edev;
+    t.ticket = w.ticket + ticket;
+    return t;
+}
+inline TotalsArgs no_totals() {
+    TotalsArgs t{};
+    t.Edev = nullptr;
+    return t;
+}
+
 template <typename R>
 cudaError_t configure_kernels(int max_smem) {
     cudaError_t e = cudaSuccess;
@@ -106,9 +131,7 @@ void enqueue_bin(const Geo& g, const Work& w, int N, const R* pos, const R* q, R
     using V = typename V4<R>::T;
     launch(false, true, k_bin_count<R>, g.nbin, kBinThreads, (g.ntiles + g.chunk) * sizeof(int), s, g, N, pos, q,
            w.cnt_blk, w.bhist, w.ctile, static_cast<V*>(w.cpos), static_cast<V*>(w.cfrac), w.cbase, Fzero,
-           w.part + w.off_q);
-    launch(pdl, true, k_tile_offsets, (g.ntiles + 255) / 256, 256, 0, s, g, (const int*)w.bhist, w.boff, w.ttot);
-    launch(pdl, true, k_scan, 1, 1024, 0, s, w.ttot, w.tstart, g.ntiles, (int*)nullptr, 0);
+           w.part + w.off_q, w.ticket, w.boff, w.tstart);
     launch(pdl, true, k_bin_scatter<R>, g.nbin, kBinThreads, g.ntiles * sizeof(int), s, g, (const int*)w.cnt_blk,
            (const int*)w.ctile, static_cast<const V*>(w.cpos), static_cast<const V*>(w.cfrac), (const int*)w.cbase,
            (const int*)w.boff, (const int*)w.tstart, static_cast<V*>(w.sq), static_cast<V*>(w.sw), w.sb);
@@ -118,7 +141,7 @@ void enqueue_bin(const Geo& g, const Work& w, int N, const R* pos, const R* q, R
 }
 
 // Kernels enqueue_bin launches.
-inline int bin_kernels(const Work& w) { return w.wb ? 5 : 4; }
+inline int bin_kernels(const Work& w) { return w.wb ? 3 : 2; }
 
 // Spreading: the column-stationary kernel for the common tile edges, the
 // work-item kernel with shared-memory atomics otherwise (or without weights).
@@ -150,7 +173,7 @@ inline void enqueue_spread(const Geo& g, const Work& w, R* grid, cudaStream_t s,
 template <typename R>
 cudaError_t enqueue_enuf(const Geo& g, const FftShape& fs, const FftPlanDev& fp, const Work& w,
                          const EvalArgs& a, cudaStream_t s0, cudaStream_t s1, cudaEvent_t evFork,
-                         cudaEvent_t evJoin, Events* ev, LaunchLog* log) {
+                         cudaEvent_t evJoin, Events* ev, LaunchLog* log, bool fuse_totals) {
     using C = typename Cx<R>::T;
     using V = typename V4<R>::T;
     const R* pos = static_cast<const R*>(a.pos);
@@ -208,8 +231,10 @@ cudaError_t enqueue_enuf(const Geo& g, const FftShape& fs, const FftPlanDev& fp,
 
     cudaStreamWaitEvent(s0, evJoin, 0);
     rec(ev, 3, true, s0);
+    // with fuse_totals the gather's last block also reduces the energies
     launch(false, true, k_gather<R>, w.nblk_gather, kGatherThreads, 0, s0, g, (const int*)w.tstart, (const V*)sq,
-           (const V*)sw, (const int*)w.sb, static_cast<const R*>(w.wb), static_cast<const R*>(w.h), F);
+           (const V*)sw, (const int*)w.sb, static_cast<const R*>(w.wb), static_cast<const R*>(w.h), F,
+           fuse_totals ? totals_args(g, w, false, 1) : no_totals());
     rec(ev, 3, false, s0);
     log->kernels += 1;
     return cudaGetLastError();
@@ -217,8 +242,7 @@ cudaError_t enqueue_enuf(const Geo& g, const FftShape& fs, const FftPlanDev& fp,
 
 template <typename R>
 cudaError_t enqueue_totals(const Geo& g, const Work& w, bool dpd, cudaStream_t s, LaunchLog* log, bool pdl) {
-    launch(pdl, true, k_totals, 1, 1024, 0, s, g, (const double*)w.part, w.off_q, g.nbin, w.off_real, w.nblk_real,
-           w.off_recip, w.nblk_conv, w.off_dpd, dpd ? w.nblk_dpd : 0, w.off_kin, dpd ? w.nblk_kin : 0, w.Edev);
+    launch(pdl, true, k_totals, 1, 1024, 0, s, g, totals_args(g, w, dpd, 3));
     log->kernels += 1;
     return cudaGetLastError();
 }
@@ -257,10 +281,11 @@ cudaError_t enqueue_vv_pre(const DpdDev& d, cudaStream_t s, LaunchLog* log) {
     return cudaGetLastError();
 }
 
+// Step 6 of Table 2; the last block also reduces the step's energies.
 template <typename R>
-cudaError_t enqueue_vv_post(const Work& w, const DpdDev& d, cudaStream_t s, LaunchLog* log, bool pdl) {
-    launch(pdl, true, k_vv_post<R>, w.nblk_kin, 256, 0, s, d.N, (R)d.dt, static_cast<R*>(d.vel),
-           static_cast<const R*>(d.F), w.part + w.off_kin);
+cudaError_t enqueue_vv_post(const Geo& g, const Work& w, const DpdDev& d, cudaStream_t s, LaunchLog* log, bool pdl) {
+    launch(pdl, true, k_vv_post<R>, w.nblk_kin, 256, 0, s, g, d.N, (R)d.dt, static_cast<R*>(d.vel),
+           static_cast<const R*>(d.F), w.part + w.off_kin, totals_args(g, w, true, 2));
     log->kernels += 1;
     return cudaGetLastError();
 }
@@ -281,12 +306,13 @@ cudaError_t enqueue_spread_only(const Geo& g, const Work& w, const EvalArgs& a, 
     template int spread_smem<R>(const Geo&);                                                                 \
     template cudaError_t enqueue_enuf<R>(const Geo&, const FftShape&, const FftPlanDev&, const Work&,        \
                                          const EvalArgs&, cudaStream_t, cudaStream_t, cudaEvent_t,           \
-                                         cudaEvent_t, Events*, LaunchLog*);                                  \
+                                         cudaEvent_t, Events*, LaunchLog*, bool);                            \
     template cudaError_t enqueue_totals<R>(const Geo&, const Work&, bool, cudaStream_t, LaunchLog*, bool);   \
     template cudaError_t enqueue_dpd_forces<R>(const Work&, const DpdDev&, cudaStream_t, Events*,            \
                                                LaunchLog*);                                                  \
     template cudaError_t enqueue_vv_pre<R>(const DpdDev&, cudaStream_t, LaunchLog*);                         \
-    template cudaError_t enqueue_vv_post<R>(const Work&, const DpdDev&, cudaStream_t, LaunchLog*, bool);     \
+    template cudaError_t enqueue_vv_post<R>(const Geo&, const Work&, const DpdDev&, cudaStream_t, LaunchLog*,  \
+                                            bool);                                                           \
     template cudaError_t enqueue_spread_only<R>(const Geo&, const Work&, const EvalArgs&, void*, cudaStream_t);
 
 }  // namespace enuf

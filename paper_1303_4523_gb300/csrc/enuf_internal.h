@@ -66,6 +66,7 @@ struct Work {
     int* boff;       // [nbin][ntiles] offset of each block's beads within each tile
     int* ttot;       // [ntiles] beads per tile
     int* tstart;     // [ntiles + 1]
+    int* ticket;     // [4] arrival counters of last-block reductions (0 between launches)
     int* ctile;      // [nbin * chunk] tile of each compacted charged bead
     void* cpos;      // real4 [nbin * chunk] wrapped x, y, z, q of each compacted charged bead
     void* cfrac;     // real4 [nbin * chunk] fractional grid coordinates, original index bits
@@ -100,6 +101,16 @@ struct EvalArgs {
     const void* q;     // real [N]
     void* F;           // real [N][3]
     bool zeroF;        // overwrite F (pure electrostatics) vs add into it (DPD step)
+};
+
+// Where the final FP64 totals read their per-block partials (offsets into
+// Work::part, counts) and write Edev; ticket is the arrival counter of the
+// kernel whose last block reduces them. Edev == nullptr: no totals.
+struct TotalsArgs {
+    const double* part;
+    int off_q, nq, off_real, nreal, off_recip, nrecip, off_dpd, ndpd, off_kin, nkin;
+    double* Edev;
+    int* ticket;
 };
 
 // DPD device state and cell list (one per system).
@@ -139,7 +150,7 @@ template <typename R> int spread_smem(const Geo& g);
 template <typename R>
 cudaError_t enqueue_enuf(const Geo& g, const FftShape& fs, const FftPlanDev& fp, const Work& w,
                          const EvalArgs& a, cudaStream_t s0, cudaStream_t s1, cudaEvent_t evFork,
-                         cudaEvent_t evJoin, Events* ev, LaunchLog* log);
+                         cudaEvent_t evJoin, Events* ev, LaunchLog* log, bool fuse_totals);
 template <typename R>
 cudaError_t enqueue_totals(const Geo& g, const Work& w, bool dpd, cudaStream_t s, LaunchLog* log, bool pdl);
 template <typename R>
@@ -147,7 +158,7 @@ cudaError_t enqueue_dpd_forces(const Work& w, const DpdDev& d, cudaStream_t s, E
 template <typename R>
 cudaError_t enqueue_vv_pre(const DpdDev& d, cudaStream_t s, LaunchLog* log);
 template <typename R>
-cudaError_t enqueue_vv_post(const Work& w, const DpdDev& d, cudaStream_t s, LaunchLog* log, bool pdl);
+cudaError_t enqueue_vv_post(const Geo& g, const Work& w, const DpdDev& d, cudaStream_t s, LaunchLog* log, bool pdl);
 template <typename R>
 cudaError_t enqueue_spread_only(const Geo& g, const Work& w, const EvalArgs& a, void* grid_out, cudaStream_t s);
 

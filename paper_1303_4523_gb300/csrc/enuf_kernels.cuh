@@ -163,7 +163,6 @@ __device__ __forceinline__ void block_sum2(double& a, double& b) {
     }
 }
 
-// Kahan-compensated accumulator (FP64).
 struct Kahan {
     double s = 0.0, c = 0.0;
     __device__ __forceinline__ void add(double x) {
@@ -174,24 +173,120 @@ struct Kahan {
     }
 };
 
+// Final FP64 totals (Kahan over the per-block partials) by one block of any
+// multiple of 32 threads: warp w reduces the quantities q with q mod (warps)
+// = w among the 9 (Sum q, Sum q^2, E_real, W_real, E_recip, W_recip, E_c,
+// E_bond, E_kin). Partials come from other blocks and kernels: loads bypass L1.
+// Edev: [0] E_real [1] E_recip [2] E_self+E_neutral [3] E_elec [4] E_conservative
+//       [5] E_bond [6] E_kinetic [7] virial_elec
+static __device__ void totals_block(const Geo& g, const TotalsArgs& t) {
+    __shared__ double vals[9];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int qd = w; qd < 9; qd += nw) {
+        int off, cnt, stride;
+        if (qd < 2) { off = t.off_q + qd; cnt = t.nq; stride = 2; }
+        else if (qd < 4) { off = t.off_real + (qd - 2); cnt = t.nreal; stride = 2; }
+        else if (qd < 6) { off = t.off_recip + (qd - 4); cnt = t.nrecip; stride = 2; }
+        else if (qd < 8) { off = t.off_dpd + (qd - 6); cnt = t.ndpd; stride = 2; }
+        else { off = t.off_kin; cnt = t.nkin; stride = 1; }
+        Kahan k;
+        for (int i = l; i < cnt; i += 32) k.add(__ldcg(&t.part[off + stride * i]));
+        const double v = warp_sum(k.s);
+        if (l == 0) vals[qd] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double* Edev = t.Edev;
+        // constants formed on the host: no FP64 division or square root here
+        const double Q = vals[0], Q2 = vals[1];
+        const double e_self = g.c_self * Q2;
+        const double e_neut = g.c_neut * Q * Q;
+        const double e_real = vals[2], e_recip = g.c_recip * vals[4];
+        Edev[0] = e_real;
+        Edev[1] = e_recip;
+        Edev[2] = e_self + e_neut;
+        Edev[3] = e_real + e_recip + e_self + e_neut;
+        Edev[4] = vals[6];
+        Edev[5] = vals[7];
+        Edev[6] = vals[8];
+        Edev[7] = vals[3] + g.c_recip * vals[5] + 3.0 * e_neut;
+        for (int i = 8; i < 16; ++i) Edev[i] = 0.0;
+    }
+}
+
+// The last block of a kernel to finish (arrival counter) runs the totals.
+__device__ __forceinline__ void totals_if_last(const Geo& g, const TotalsArgs& t) {
+    __shared__ int last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(t.ticket, 1) == (int)(gridDim.x * gridDim.y) - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    totals_block(g, t);
+    if (threadIdx.x == 0) *t.ticket = 0;
+}
+
+
+// Kahan-compensated accumulator (FP64).
+
 // ---------------------------------------------------------------------------
 // a1: binning of the charged beads into tiles of the oversampled grid.
 // k_bin_count: each block compacts the charged beads of its chunk (warp
 //   ballots into a shared list), computes their grid coordinates in FP64 on
 //   dense warps, histograms their tiles in shared memory and stores each
 //   compacted bead's record.
-// k_tile_offsets: one thread per tile walks the per-block counts (coalesced)
-//   and writes each block's offset inside the tile and the tile total.
-// k_scan over the tile totals gives the tile starts; k_bin_scatter moves the
-//   records to their sorted slots. The only atomics are shared-memory ones.
+//   The last block to finish (arrival counter) walks the per-block counts of
+//   every tile (coalesced), writes each block's offset inside the tile and
+//   scans the tile totals into the tile starts.
+// k_bin_scatter moves the records to their sorted slots; k_bin_weights
+//   computes their window weights. Besides the arrival counter the only
+//   atomics are shared-memory ones.
 // ---------------------------------------------------------------------------
+// Exclusive scan of count ints held in shared memory into out[0..count] (out[count] =
+// total) by the whole block: contiguous chunks per thread, warp and block scans.
+__device__ __forceinline__ void block_exclusive_scan(const int* data, int count, int* __restrict__ out) {
+    __shared__ int wsum[32];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nwarp = (blockDim.x + 31) >> 5;
+    const int per = (count + blockDim.x - 1) / blockDim.x;
+    const int i0 = tid * per, i1 = min(count, i0 + per);
+    int sum = 0;
+    for (int i = i0; i < i1; ++i) sum += data[i];
+    int x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int z = lane < nwarp ? wsum[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, z, o);
+            if (lane >= o) z += y;
+        }
+        wsum[lane] = z;
+    }
+    __syncthreads();
+    int run = (x - sum) + (w > 0 ? wsum[w - 1] : 0);
+    for (int i = i0; i < i1; ++i) {
+        out[i] = run;
+        run += data[i];
+    }
+    if (tid == 0) out[count] = wsum[nwarp - 1];
+}
+
 template <typename R>
 __global__ void __launch_bounds__(1024) k_bin_count(Geo g, int N, const R* __restrict__ pos,
                                                    const R* __restrict__ q, int* __restrict__ cnt_blk,
                                                    int* __restrict__ bhist, int* __restrict__ ctile,
                                                    typename V4<R>::T* __restrict__ cpos,
                                                    typename V4<R>::T* __restrict__ cfrac, int* __restrict__ cbase,
-                                                   R* __restrict__ Fzero, double* __restrict__ qpart) {
+                                                   R* __restrict__ Fzero, double* __restrict__ qpart,
+                                                   int* __restrict__ ticket, int* __restrict__ boff,
+                                                   int* __restrict__ tstart) {
     pdl_enter();
     extern __shared__ int sm_bin[];
     int* hist = sm_bin;                 // [ntiles]
@@ -256,32 +351,30 @@ __global__ void __launch_bounds__(1024) k_bin_count(Geo g, int N, const R* __res
     }
     __syncthreads();
     for (int t = threadIdx.x; t < g.ntiles; t += blockDim.x) bhist[b * g.ntiles + t] = hist[t];
+    // the last block to arrive turns the per-block histograms into per-block
+    // offsets within each tile and the tile starts (exclusive scan of the totals)
+    __shared__ int last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int t = threadIdx.x; t < g.ntiles; t += blockDim.x) {
+        int run = 0;
+        for (int bb = 0; bb < g.nbin; ++bb) {
+            const int v = __ldcg(&bhist[bb * g.ntiles + t]);
+            boff[bb * g.ntiles + t] = run;
+            run += v;
+        }
+        hist[t] = run;   // tile totals
+    }
+    __syncthreads();
+    block_exclusive_scan(hist, g.ntiles, tstart);
+    if (threadIdx.x == 0) *ticket = 0;
 }
 
 // One thread per tile: offsets of each block's beads inside the tile, and the tile total.
-static __global__ void __launch_bounds__(256) k_tile_offsets(Geo g, const int* __restrict__ bhist, int* __restrict__ boff,
-                                                      int* __restrict__ ttot) {
-    pdl_enter();
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= g.ntiles) return;
-    int run = 0;
-    int b = 0;
-    for (; b + 4 <= g.nbin; b += 4) {
-        const int v0 = bhist[b * g.ntiles + t], v1 = bhist[(b + 1) * g.ntiles + t];
-        const int v2 = bhist[(b + 2) * g.ntiles + t], v3 = bhist[(b + 3) * g.ntiles + t];
-        boff[b * g.ntiles + t] = run;
-        boff[(b + 1) * g.ntiles + t] = run + v0;
-        boff[(b + 2) * g.ntiles + t] = run + v0 + v1;
-        boff[(b + 3) * g.ntiles + t] = run + v0 + v1 + v2;
-        run += v0 + v1 + v2 + v3;
-    }
-    for (; b < g.nbin; ++b) {
-        const int v = bhist[b * g.ntiles + t];
-        boff[b * g.ntiles + t] = run;
-        run += v;
-    }
-    ttot[t] = run;
-}
 
 // Exclusive scan of in[0, count) into out[0, count], out[count] = total; one
 // CTA of 1024 threads, 16 elements per thread and round (four 16-byte loads).
@@ -1138,7 +1231,8 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Geo g, const int* __r
                                                            const typename V4<R>::T* __restrict__ sq,
                                                            const typename V4<R>::T* __restrict__ sw,
                                                            const int* __restrict__ sb, const R* __restrict__ wb,
-                                                           const R* __restrict__ h, R* __restrict__ F) {
+                                                           const R* __restrict__ h, R* __restrict__ F,
+                                                           TotalsArgs tot) {
     pdl_enter();
     constexpr int NW = kGatherThreads / 32;
     __shared__ R wts[NW][3][kMaxTaps];
@@ -1220,6 +1314,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Geo g, const int* __r
         }
         __syncwarp();
     }
+    if (tot.Edev) totals_if_last(g, tot);
 }
 
 // ---------------------------------------------------------------------------
@@ -2017,9 +2112,10 @@ __global__ void k_vv_pre(int N, R lam, R dt, R* __restrict__ pos, R* __restrict_
 }
 
 // Table 2 step 6: v += F dt/2; kinetic energy partials.
+// The last block then reduces all energies of the step (totals).
 template <typename R>
-__global__ void __launch_bounds__(256) k_vv_post(int N, R dt, R* __restrict__ vel, const R* __restrict__ F,
-                                                double* __restrict__ kpart) {
+__global__ void __launch_bounds__(256) k_vv_post(Geo g, int N, R dt, R* __restrict__ vel, const R* __restrict__ F,
+                                                double* __restrict__ kpart, TotalsArgs tot) {
     pdl_enter();
     double ke = 0.0, dummy = 0.0;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < 3 * N; k += gridDim.x * blockDim.x) {
@@ -2029,55 +2125,13 @@ __global__ void __launch_bounds__(256) k_vv_post(int N, R dt, R* __restrict__ ve
     }
     block_sum2(ke, dummy);
     if (threadIdx.x == 0) kpart[blockIdx.x] = ke;
+    if (tot.Edev) totals_if_last(g, tot);
 }
 
-// Final FP64 totals (Kahan over the per-block partials), one CTA of 1024
-// threads: 32 warps share 9 quantities (Sum q, Sum q^2, E_real, W_real,
-// E_recip, W_recip, E_c, E_bond, E_kin).
-// Edev: [0] E_real [1] E_recip [2] E_self+E_neutral [3] E_elec [4] E_conservative
-//       [5] E_bond [6] E_kinetic [7] virial_elec
-static __global__ void __launch_bounds__(1024) k_totals(Geo g, const double* __restrict__ part, int off_q, int nq,
-                                                        int off_real, int nreal, int off_recip, int nrecip,
-                                                        int off_dpd, int ndpd, int off_kin, int nkin,
-                                                        double* __restrict__ Edev) {
+// Standalone totals (one CTA), for evaluations outside a step graph.
+static __global__ void __launch_bounds__(1024) k_totals(Geo g, TotalsArgs t) {
     pdl_enter();
-    __shared__ double wv[32];
-    __shared__ double vals[9];
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    const int qd = w % 9, sub = w / 9, nsub = (32 - qd + 8) / 9;   // warps on this quantity
-    int off, cnt, stride;
-    if (qd < 2) { off = off_q + qd; cnt = nq; stride = 2; }
-    else if (qd < 4) { off = off_real + (qd - 2); cnt = nreal; stride = 2; }
-    else if (qd < 6) { off = off_recip + (qd - 4); cnt = nrecip; stride = 2; }
-    else if (qd < 8) { off = off_dpd + (qd - 6); cnt = ndpd; stride = 2; }
-    else { off = off_kin; cnt = nkin; stride = 1; }
-    Kahan k;
-    for (int i = sub * 32 + l; i < cnt; i += nsub * 32) k.add(part[off + stride * i]);
-    const double v = warp_sum(k.s);
-    if (l == 0) wv[w] = v;
-    __syncthreads();
-    if (threadIdx.x < 9) {
-        Kahan kk;
-        for (int ww = threadIdx.x; ww < 32; ww += 9) kk.add(wv[ww]);
-        vals[threadIdx.x] = kk.s;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        // constants formed on the host: no FP64 division or square root here
-        const double Q = vals[0], Q2 = vals[1];
-        const double e_self = g.c_self * Q2;
-        const double e_neut = g.c_neut * Q * Q;
-        const double e_real = vals[2], e_recip = g.c_recip * vals[4];
-        Edev[0] = e_real;
-        Edev[1] = e_recip;
-        Edev[2] = e_self + e_neut;
-        Edev[3] = e_real + e_recip + e_self + e_neut;
-        Edev[4] = vals[6];
-        Edev[5] = vals[7];
-        Edev[6] = vals[8];
-        Edev[7] = vals[3] + g.c_recip * vals[5] + 3.0 * e_neut;
-        for (int i = 8; i < 16; ++i) Edev[i] = 0.0;
-    }
+    totals_block(g, t);
 }
 
 }  // namespace enuf
