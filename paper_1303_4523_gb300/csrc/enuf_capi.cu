@@ -241,6 +241,8 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
     // histogram in shared memory (<= 200 KB)
     g.chunk = std::min(16384, std::max(2048, (n_max + 63) / 64));
     g.nbin = std::max(1, (n_max + g.chunk - 1) / g.chunk);
+    // the last binning block walks ntiles x nbin counts: only when that is small
+    g.bin_last = (long long)g.ntiles * g.nbin <= 65536 ? 1 : 0;
     g.kmask = P.kmask;
     g.nf = P.deriv ? 1 : 3;
     g.L = P.L;
@@ -271,18 +273,20 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
     fs.tz = std::min(256, std::max(fs.tz, ((g.nf * fs.lz * n / 4 + 31) / 32) * 32));
     shape(g.nf * n * nc1, 2, fs.liy, fs.tiy, fs.grid_iy);
     shape(g.nf * n * n / 2, 2, fs.lix, fs.tix, fs.grid_ix);
-    // twiddles + line buffers; the x, y, z and inverse-y passes pad their lines to n + 1
-    // (their transposed shared-memory accesses then fall on different banks)
-    fs.smem_x = (n + 2 * fs.lx * (n + 1)) * csz;
-    fs.smem_y = (n + 2 * fs.ly * (n + 1)) * csz;
-    fs.smem_z = (n + (2 + 2 * g.nf) * fs.lz * (n + 1)) * csz;
-    fs.smem_iy = (n + 2 * fs.liy * (n + 1)) * csz;
-    fs.smem_ix = (1 + 2 * fs.lix) * n * csz;
+    // twiddles + line buffers; lines are padded to whole 128-byte bank rows plus one
+    // value (the kernels swizzle the index inside a line)
+    const int bank = 128 / csz;
+    const int ls = (n + bank - 1) / bank * bank + 1;
+    fs.smem_x = (n + 2 * fs.lx * ls) * csz;
+    fs.smem_y = (n + 2 * fs.ly * ls) * csz;
+    fs.smem_z = (n + (2 + 2 * g.nf) * fs.lz * ls) * csz;
+    fs.smem_iy = (n + 2 * fs.liy * ls) * csz;
+    fs.smem_ix = (n + 2 * fs.lix * ls) * csz;
     // fused plane passes (one CTA per z-plane) for FP32 grids whose twiddles and two
     // n^2/2-line buffers take <= 100 KB (n <= 112): measured faster there; larger planes
     // and FP64 (1 CTA per SM, FP64-bound butterflies on n CTAs) keep the five passes
     {
-        const long long plane = (long long)(n + n * (n + 1)) * csz;
+        const long long plane = (long long)(n + n * ls) * csz;
         fs.fused = (P.prec == ENUF_FP32 && plane <= 100 * 1024 && P.fft_path == 0) ? 1 : 0;
         fs.smem_xy = fs.smem_yx = (int)plane;
         fs.t_xy = fs.t_yx = 512;
@@ -313,7 +317,7 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
     g.rlo = (float)(g.ratio - (double)g.rhi);
 
     Work w{};
-    w.nblk_real = 8 * kSMs;
+    w.nblk_real = std::min(8 * kSMs, g.ntiles);   // one tile per CTA at most
     w.nblk_conv = fs.grid_z;
     w.nblk_dpd = 4 * kSMs;
     w.nblk_kin = 4 * kSMs;

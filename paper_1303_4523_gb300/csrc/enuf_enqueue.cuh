@@ -132,6 +132,10 @@ void enqueue_bin(const Geo& g, const Work& w, int N, const R* pos, const R* q, R
     launch(false, true, k_bin_count<R>, g.nbin, kBinThreads, (g.ntiles + g.chunk) * sizeof(int), s, g, N, pos, q,
            w.cnt_blk, w.bhist, w.ctile, static_cast<V*>(w.cpos), static_cast<V*>(w.cfrac), w.cbase, Fzero,
            w.part + w.off_q, w.ticket, w.boff, w.tstart);
+    if (!g.bin_last) {
+        launch(pdl, true, k_tile_offsets, (g.ntiles + 255) / 256, 256, 0, s, g, (const int*)w.bhist, w.boff, w.ttot);
+        launch(pdl, true, k_scan, 1, 1024, 0, s, w.ttot, w.tstart, g.ntiles, (int*)nullptr, 0);
+    }
     launch(pdl, true, k_bin_scatter<R>, g.nbin, kBinThreads, g.ntiles * sizeof(int), s, g, (const int*)w.cnt_blk,
            (const int*)w.ctile, static_cast<const V*>(w.cpos), static_cast<const V*>(w.cfrac), (const int*)w.cbase,
            (const int*)w.boff, (const int*)w.tstart, static_cast<V*>(w.sq), static_cast<V*>(w.sw), w.sb);
@@ -141,7 +145,7 @@ void enqueue_bin(const Geo& g, const Work& w, int N, const R* pos, const R* q, R
 }
 
 // Kernels enqueue_bin launches.
-inline int bin_kernels(const Work& w) { return w.wb ? 3 : 2; }
+inline int bin_kernels(const Geo& g, const Work& w) { return (g.bin_last ? 2 : 4) + (w.wb ? 1 : 0); }
 
 // Spreading: the column-stationary kernel for the common tile edges, the
 // work-item kernel with shared-memory atomics otherwise (or without weights).
@@ -186,7 +190,7 @@ cudaError_t enqueue_enuf(const Geo& g, const FftShape& fs, const FftPlanDev& fp,
     rec(ev, 0, true, s0);
     enqueue_bin<R>(g, w, a.N, pos, q, a.zeroF ? F : nullptr, s0, pdl);
     rec(ev, 0, false, s0);
-    log->kernels += bin_kernels(w);
+    log->kernels += bin_kernels(g, w);
 
     // real-space branch
     cudaEventRecord(evFork, s0);

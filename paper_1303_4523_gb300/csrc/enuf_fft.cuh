@@ -32,6 +32,25 @@ __device__ __forceinline__ int qdiv(int a, int b, float rb) {
     return q;
 }
 
+// Shared-memory layout of the line buffers. A bank row holds 128 B, i.e. B
+// complex values (16 float2 or 8 double2). The index inside a line is
+// swizzled, i -> i XOR (row of i mod B), so that both unit-stride accesses
+// and the strided writes of the early Stockham stages spread over all banks;
+// lines are padded to whole bank rows plus one value, which skews consecutive
+// lines for the accesses that run across lines.
+template <typename C> struct SwzBits;
+template <> struct SwzBits<float2> { static constexpr int v = 4; };
+template <> struct SwzBits<double2> { static constexpr int v = 3; };
+template <typename C>
+__device__ __forceinline__ int swz(int i) {
+    constexpr int b = SwzBits<C>::v;
+    return i ^ ((i >> b) & ((1 << b) - 1));
+}
+template <typename C>
+__host__ __device__ constexpr int line_stride(int n) {
+    return ((n + (1 << SwzBits<C>::v) - 1) >> SwzBits<C>::v << SwzBits<C>::v) + 1;
+}
+
 template <typename C>
 __device__ __forceinline__ C cmul(C a, C b) {
     C r;
@@ -131,7 +150,7 @@ template <typename R, bool INV> struct SmallDft<R, 5, INV> {
     }
 };
 
-// One Stockham stage over nlines lines (line l at offset l*ls).
+// One Stockham stage over nlines lines (line l at offset l*ls, swizzled inside).
 template <typename R, int RAD, bool INV>
 __device__ __forceinline__ void fft_stage(const typename Cx<R>::T* __restrict__ src,
                                           typename Cx<R>::T* __restrict__ dst,
@@ -150,7 +169,7 @@ __device__ __forceinline__ void fft_stage(const typename Cx<R>::T* __restrict__ 
         C* d = dst + line * ls;
         C v[RAD];
 #pragma unroll
-        for (int r = 0; r < RAD; ++r) v[r] = s[j + r * m];
+        for (int r = 0; r < RAD; ++r) v[r] = s[swz<C>(j + r * m)];
         if (k != 0) {
 #pragma unroll
             for (int r = 1; r < RAD; ++r) {
@@ -162,7 +181,7 @@ __device__ __forceinline__ void fft_stage(const typename Cx<R>::T* __restrict__ 
         SmallDft<R, RAD, INV>::run(v);
         const int base = (j - k) * RAD + k;
 #pragma unroll
-        for (int r = 0; r < RAD; ++r) d[base + r * Ns] = v[r];
+        for (int r = 0; r < RAD; ++r) d[swz<C>(base + r * Ns)] = v[r];
     }
 }
 

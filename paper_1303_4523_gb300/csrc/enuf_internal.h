@@ -23,6 +23,8 @@ struct Geo {
     int chunk;    // beads per binning block
     int kmask;
     int nf;       // reciprocal force fields: 3 (ik-differentiation) or 1 (window gradient)
+    int bin_last; // 1: the last binning block computes the tile offsets and starts
+                  //    (ntiles x nbin small); 0: separate offsets and scan kernels
     double L, alpha, beta, kappa, rc;
     double b;      // Gaussian window parameter 2 sigma p / ((2 sigma - 1) pi)
     double wnorm;  // (pi b)^{-1/2}

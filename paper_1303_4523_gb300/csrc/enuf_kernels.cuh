@@ -190,7 +190,16 @@ static __device__ void totals_block(const Geo& g, const TotalsArgs& t) {
         else if (qd < 8) { off = t.off_dpd + (qd - 6); cnt = t.ndpd; stride = 2; }
         else { off = t.off_kin; cnt = t.nkin; stride = 1; }
         Kahan k;
-        for (int i = l; i < cnt; i += 32) k.add(__ldcg(&t.part[off + stride * i]));
+        for (int i0 = l; i0 < cnt; i0 += 32 * 8) {   // eight independent loads in flight
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = i0 + 32 * u;
+                v[u] = i < cnt ? __ldcg(&t.part[off + stride * i]) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) k.add(v[u]);
+        }
         const double v = warp_sum(k.s);
         if (l == 0) vals[qd] = v;
     }
@@ -353,6 +362,7 @@ __global__ void __launch_bounds__(1024) k_bin_count(Geo g, int N, const R* __res
     for (int t = threadIdx.x; t < g.ntiles; t += blockDim.x) bhist[b * g.ntiles + t] = hist[t];
     // the last block to arrive turns the per-block histograms into per-block
     // offsets within each tile and the tile starts (exclusive scan of the totals)
+    if (!g.bin_last) return;
     __shared__ int last;
     __threadfence();
     __syncthreads();
@@ -362,10 +372,15 @@ __global__ void __launch_bounds__(1024) k_bin_count(Geo g, int N, const R* __res
     __threadfence();
     for (int t = threadIdx.x; t < g.ntiles; t += blockDim.x) {
         int run = 0;
-        for (int bb = 0; bb < g.nbin; ++bb) {
-            const int v = __ldcg(&bhist[bb * g.ntiles + t]);
-            boff[bb * g.ntiles + t] = run;
-            run += v;
+        for (int b0 = 0; b0 < g.nbin; b0 += 8) {   // eight independent loads in flight
+            int v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = b0 + u < g.nbin ? __ldcg(&bhist[(b0 + u) * g.ntiles + t]) : 0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                if (b0 + u < g.nbin) boff[(b0 + u) * g.ntiles + t] = run;
+                run += v[u];
+            }
         }
         hist[t] = run;   // tile totals
     }
@@ -453,6 +468,33 @@ static __global__ void __launch_bounds__(1024) k_scan(int* __restrict__ in, int*
         out[count] = carry;
         if (aux) aux[count] = carry;
     }
+}
+
+// Separate tile offsets for large tile x block counts: one thread per tile
+// walks the per-block counts (coalesced) and writes each block's offset inside
+// the tile and the tile total (then k_scan gives the tile starts).
+static __global__ void __launch_bounds__(256) k_tile_offsets(Geo g, const int* __restrict__ bhist, int* __restrict__ boff,
+                                                      int* __restrict__ ttot) {
+    pdl_enter();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= g.ntiles) return;
+    int run = 0;
+    int b = 0;
+    for (; b + 4 <= g.nbin; b += 4) {
+        const int v0 = bhist[b * g.ntiles + t], v1 = bhist[(b + 1) * g.ntiles + t];
+        const int v2 = bhist[(b + 2) * g.ntiles + t], v3 = bhist[(b + 3) * g.ntiles + t];
+        boff[b * g.ntiles + t] = run;
+        boff[(b + 1) * g.ntiles + t] = run + v0;
+        boff[(b + 2) * g.ntiles + t] = run + v0 + v1;
+        boff[(b + 3) * g.ntiles + t] = run + v0 + v1 + v2;
+        run += v0 + v1 + v2 + v3;
+    }
+    for (; b < g.nbin; ++b) {
+        const int v = bhist[b * g.ntiles + t];
+        boff[b * g.ntiles + t] = run;
+        run += v;
+    }
+    ttot[t] = run;
 }
 
 template <typename R>
@@ -850,7 +892,7 @@ __global__ void __launch_bounds__(256) k_fft_x(Geo g, FftPlanDev fp, const R* __
     extern __shared__ unsigned char smraw[];
     const int n = g.n, nc1 = g.nc + 1;
     C* tw = reinterpret_cast<C*>(smraw);
-    const int ls = n + 1;   // padded line stride: the split reads across lines
+    const int ls = line_stride<C>(n);   // padded, swizzled lines (the split reads across lines)
     C* b0 = tw + n;
     C* b1 = b0 + LP * ls;
     for (int t = threadIdx.x; t < n; t += blockDim.x) tw[t] = twg[t];
@@ -864,15 +906,15 @@ __global__ void __launch_bounds__(256) k_fft_x(Geo g, FftPlanDev fp, const R* __
         C v;
         v.x = grid[(size_t)(row0 + 2 * c) * n + x];
         v.y = grid[(size_t)(row0 + 2 * c + 1) * n + x];
-        b0[c * ls + x] = v;
+        b0[c * ls + swz<C>(x)] = v;
     }
     __syncthreads();
     C* res = fft_lines<R, false>(b0, b1, tw, fp, nl, ls);
     // split the two real transforms: A = (Z_k + conj Z_{n-k})/2, B = -i (Z_k - conj Z_{n-k})/2
     for (int idx = threadIdx.x; idx < nl * nc1; idx += blockDim.x) {
         const int k = qdiv(idx, nl, rnl), c = idx - k * nl;
-        const C z = res[c * ls + k];
-        const C zm = res[c * ls + (k == 0 ? 0 : n - k)];
+        const C z = res[c * ls + swz<C>(k)];
+        const C zm = res[c * ls + swz<C>(k == 0 ? 0 : n - k)];
         C A, B;
         A.x = (R)0.5 * (z.x + zm.x);
         A.y = (R)0.5 * (z.y - zm.y);
@@ -896,7 +938,7 @@ __global__ void __launch_bounds__(256) k_fft_y(Geo g, FftPlanDev fp, const typen
     extern __shared__ unsigned char smraw[];
     const int n = g.n, nc1 = g.nc + 1, K = g.K;
     C* tw = reinterpret_cast<C*>(smraw);
-    const int ls = n + 1;   // padded line stride: the output reads across lines
+    const int ls = line_stride<C>(n);   // padded, swizzled lines (the output reads across lines)
     C* b0 = tw + n;
     C* b1 = b0 + LB * ls;
     for (int t = threadIdx.x; t < n; t += blockDim.x) tw[t] = twg[t];
@@ -907,14 +949,14 @@ __global__ void __launch_bounds__(256) k_fft_y(Geo g, FftPlanDev fp, const typen
     const float rnl = 1.0f / (float)max(nl, 1);
     for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
         const int c = qdiv(idx, n, rn), y = idx - c * n;
-        b0[c * ls + y] = spec1[((size_t)(z0 + c) * nc1 + kx) * n + y];
+        b0[c * ls + swz<C>(y)] = spec1[((size_t)(z0 + c) * nc1 + kx) * n + y];
     }
     __syncthreads();
     C* res = fft_lines<R, false>(b0, b1, tw, fp, nl, ls);
     for (int idx = threadIdx.x; idx < nl * K; idx += blockDim.x) {
         const int ki = qdiv(idx, nl, rnl), c = idx - ki * nl;
         const int ky = ki - g.nc;
-        spec2[((size_t)kx * K + ki) * n + z0 + c] = res[c * ls + (ky < 0 ? ky + n : ky)];
+        spec2[((size_t)kx * K + ki) * n + z0 + c] = res[c * ls + swz<C>(ky < 0 ? ky + n : ky)];
     }
 }
 
@@ -935,7 +977,7 @@ __global__ void __launch_bounds__(256) k_fft_z(Geo g, FftPlanDev fp, const typen
     const int NL = (nc + 1) * K;
     const float rK = 1.0f / (float)K, rn = 1.0f / (float)n;
     C* tw = reinterpret_cast<C*>(smraw);
-    const int ls = n + 1;         // padded line stride: loads and stores go across lines
+    const int ls = line_stride<C>(n);   // padded, swizzled lines (loads and stores go across lines)
     C* b0 = tw + n;               // [LB][ls] forward lines
     C* b1 = b0 + LB * ls;         // [LB][ls] scratch
     C* X = b1 + LB * ls;          // [nf][LB][ls] fields
@@ -947,12 +989,12 @@ __global__ void __launch_bounds__(256) k_fft_z(Geo g, FftPlanDev fp, const typen
     if (plane_major) {   // spec2[z][l]: lines gathered across planes
         for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
             const int z = qdiv(idx, nl, rnl), c = idx - z * nl;
-            b0[c * ls + z] = spec2[(size_t)z * NL + l0 + c];
+            b0[c * ls + swz<C>(z)] = spec2[(size_t)z * NL + l0 + c];
         }
     } else {             // spec2[l][z]: lines contiguous
         for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
             const int c = qdiv(idx, n, rn), z = idx - c * n;
-            b0[c * ls + z] = spec2[(size_t)l0 * n + idx];
+            b0[c * ls + swz<C>(z)] = spec2[(size_t)l0 * n + idx];
         }
     }
     __syncthreads();
@@ -964,7 +1006,7 @@ __global__ void __launch_bounds__(256) k_fft_z(Geo g, FftPlanDev fp, const typen
         const int l = l0 + c;
         const int kx = qdiv(l, K, rK);
         const int kz = kzi - nc;
-        const C f = Fh[c * ls + (kz < 0 ? kz + n : kz)];
+        const C f = Fh[c * ls + swz<C>(kz < 0 ? kz + n : kz)];
         const double a2 = (double)f.x * (double)f.x + (double)f.y * (double)f.y;
         const double wgt = kx == 0 ? 1.0 : 2.0;
         ke.add(wgt * tab[(size_t)l * K + kzi] * a2);
@@ -989,7 +1031,7 @@ __global__ void __launch_bounds__(256) k_fft_z(Geo g, FftPlanDev fp, const typen
         if (kz >= -nc && kz <= nc) {
             const int l = l0 + c;
             const R d = tabr[(size_t)l * K + (kz + nc)];
-            const C f = Fh[c * ls + m];
+            const C f = Fh[c * ls + swz<C>(m)];
             if (nf == 1) {
                 v.x = d * f.x;     // D F
                 v.y = d * f.y;
@@ -1001,14 +1043,14 @@ __global__ void __launch_bounds__(256) k_fft_z(Geo g, FftPlanDev fp, const typen
                 v.y = -s * f.x;
             }
         }
-        X[(a * nl + c) * ls + m] = v;
+        X[(a * nl + c) * ls + swz<C>(m)] = v;
     }
     __syncthreads();
     C* res = fft_lines<R, true>(X, Y, tw, fp, nf * nl, ls);
     for (int idx = threadIdx.x; idx < nf * per; idx += blockDim.x) {
         const int a = qdiv(idx, per, rper), e = idx - a * per;
         const int z = qdiv(e, nl, rnl), c = e - z * nl;
-        spec3[((size_t)a * n + z) * NL + l0 + c] = res[(a * nl + c) * ls + z];
+        spec3[((size_t)a * n + z) * NL + l0 + c] = res[(a * nl + c) * ls + swz<C>(z)];
     }
 }
 
@@ -1026,7 +1068,7 @@ __global__ void __launch_bounds__(512) k_fft_xy(Geo g, FftPlanDev fp, const R* _
     const int n = g.n, nc = g.nc, nc1 = nc + 1, K = g.K, h = n / 2;
     const float rn = 1.0f / (float)n, rh = 1.0f / (float)h, rK = 1.0f / (float)K;
     C* tw = reinterpret_cast<C*>(smraw);
-    const int ls = n + 1;  // padded stride of the x lines (the split reads across them)
+    const int ls = line_stride<C>(n);   // padded, swizzled lines
     C* L0 = tw + n;        // [n/2][ls]
     C* L1 = L0 + h * ls;   // [n/2][ls]
     for (int t = threadIdx.x; t < n; t += blockDim.x) tw[t] = twg[t];
@@ -1037,32 +1079,32 @@ __global__ void __launch_bounds__(512) k_fft_xy(Geo g, FftPlanDev fp, const R* _
         C v;
         v.x = gz[(size_t)(2 * c) * n + x];
         v.y = gz[(size_t)(2 * c + 1) * n + x];
-        L0[c * ls + x] = v;
+        L0[c * ls + swz<C>(x)] = v;
     }
     __syncthreads();
     C* X = fft_lines<R, false>(L0, L1, tw, fp, h, ls);
-    C* P = X == L0 ? L1 : L0;   // [nc+1][n] columns over y, then scratch
-    C* S = P + nc1 * n;         // 2 (nc + 1) = n/2: P and S fill the other buffer
+    C* P = X == L0 ? L1 : L0;   // [nc+1][ls] columns over y, then scratch
+    C* S = P + nc1 * ls;        // 2 (nc + 1) = n/2: P and S fill the other buffer
     // split the two real transforms: A = (Z_k + conj Z_{n-k})/2, B = -i (Z_k - conj Z_{n-k})/2
     for (int idx = threadIdx.x; idx < nc1 * h; idx += blockDim.x) {
         const int k = qdiv(idx, h, rh), c = idx - k * h;
-        const C zk = X[c * ls + k];
-        const C zm = X[c * ls + (k == 0 ? 0 : n - k)];
+        const C zk = X[c * ls + swz<C>(k)];
+        const C zm = X[c * ls + swz<C>(k == 0 ? 0 : n - k)];
         C A, B;
         A.x = (R)0.5 * (zk.x + zm.x);
         A.y = (R)0.5 * (zk.y - zm.y);
         B.x = (R)0.5 * (zk.y + zm.y);
         B.y = (R)0.5 * (zm.x - zk.x);
-        P[k * n + 2 * c] = A;
-        P[k * n + 2 * c + 1] = B;
+        P[k * ls + swz<C>(2 * c)] = A;
+        P[k * ls + swz<C>(2 * c + 1)] = B;
     }
     __syncthreads();
-    C* Y = fft_lines<R, false>(P, S, tw, fp, nc1, n);
+    C* Y = fft_lines<R, false>(P, S, tw, fp, nc1, ls);
     C* out = spec2 + (size_t)z * nc1 * K;
     for (int idx = threadIdx.x; idx < nc1 * K; idx += blockDim.x) {
         const int kx = qdiv(idx, K, rK), ki = idx - kx * K;
         const int ky = ki - nc;
-        out[idx] = Y[kx * n + (ky < 0 ? ky + n : ky)];
+        out[idx] = Y[kx * ls + swz<C>(ky < 0 ? ky + n : ky)];
     }
 }
 
@@ -1079,9 +1121,9 @@ __global__ void __launch_bounds__(512) k_fft_yx(Geo g, FftPlanDev fp, const type
     const int n = g.n, nc = g.nc, nc1 = nc + 1, K = g.K, hn = n / 2;
     const float rn = 1.0f / (float)n;
     C* tw = reinterpret_cast<C*>(smraw);
-    const int ls = n + 1;   // padded stride of the y columns (the x lines read across them)
+    const int ls = line_stride<C>(n);   // padded, swizzled lines
     C* L0 = tw + n;         // [n/2][ls]: the nc + 1 columns and their scratch
-    C* L1 = L0 + hn * ls;   // [n/2][n]: the x lines
+    C* L1 = L0 + hn * ls;   // [n/2][ls]: the x lines
     for (int t = threadIdx.x; t < n; t += blockDim.x) tw[t] = twg[t];
     const int az = blockIdx.x;   // a * n + z
     const C* in = spec3 + (size_t)az * nc1 * K;
@@ -1094,7 +1136,7 @@ __global__ void __launch_bounds__(512) k_fft_yx(Geo g, FftPlanDev fp, const type
         v.x = (R)0;
         v.y = (R)0;
         if (ky >= -nc && ky <= nc) v = in[kx * K + (ky + nc)];
-        P[kx * ls + m] = v;
+        P[kx * ls + swz<C>(m)] = v;
     }
     __syncthreads();
     C* Yc = fft_lines<R, true>(P, S, tw, fp, nc1, ls);   // [kx][y], in L0
@@ -1104,28 +1146,28 @@ __global__ void __launch_bounds__(512) k_fft_yx(Geo g, FftPlanDev fp, const type
         C a, b;
         a.x = a.y = b.x = b.y = (R)0;
         if (m == 0) {
-            a.x = Yc[2 * c].x;
-            b.x = Yc[2 * c + 1].x;
+            a.x = Yc[swz<C>(2 * c)].x;
+            b.x = Yc[swz<C>(2 * c + 1)].x;
         } else if (m <= nc) {
-            a = Yc[m * ls + 2 * c];
-            b = Yc[m * ls + 2 * c + 1];
+            a = Yc[m * ls + swz<C>(2 * c)];
+            b = Yc[m * ls + swz<C>(2 * c + 1)];
         } else if (m >= n - nc) {
-            a = Yc[(n - m) * ls + 2 * c];
+            a = Yc[(n - m) * ls + swz<C>(2 * c)];
             a.y = -a.y;
-            b = Yc[(n - m) * ls + 2 * c + 1];
+            b = Yc[(n - m) * ls + swz<C>(2 * c + 1)];
             b.y = -b.y;
         }
         C zz;
         zz.x = a.x - b.y;   // A + i B
         zz.y = a.y + b.x;
-        L1[idx] = zz;
+        L1[c * ls + swz<C>(m)] = zz;
     }
     __syncthreads();
-    C* Xr = fft_lines<R, true>(L1, L0, tw, fp, hn, n);
+    C* Xr = fft_lines<R, true>(L1, L0, tw, fp, hn, ls);
     R* out = h + (size_t)az * n * n;
     for (int idx = threadIdx.x; idx < hn * n; idx += blockDim.x) {
         const int c = qdiv(idx, n, rn), x = idx - c * n;
-        const C v = Xr[idx];
+        const C v = Xr[c * ls + swz<C>(x)];
         out[(size_t)(2 * c) * n + x] = v.x;
         out[(size_t)(2 * c + 1) * n + x] = v.y;
     }
@@ -1143,7 +1185,7 @@ __global__ void __launch_bounds__(256) k_fft_iy(Geo g, FftPlanDev fp, const type
     const int NLT = g.nf * n * nc1;
     const float rnc1 = 1.0f / (float)nc1;
     C* tw = reinterpret_cast<C*>(smraw);
-    const int ls = n + 1;   // padded line stride: the output reads across lines
+    const int ls = line_stride<C>(n);   // padded, swizzled lines (the output reads across lines)
     C* b0 = tw + n;
     C* b1 = b0 + LB * ls;
     for (int t = threadIdx.x; t < n; t += blockDim.x) tw[t] = twg[t];
@@ -1158,7 +1200,7 @@ __global__ void __launch_bounds__(256) k_fft_iy(Geo g, FftPlanDev fp, const type
         v.x = (R)0;
         v.y = (R)0;
         if (ky >= -nc && ky <= nc) v = spec3[(size_t)(l0 + c) * K + (ky + nc)];
-        b0[c * ls + m] = v;
+        b0[c * ls + swz<C>(m)] = v;
     }
     __syncthreads();
     C* res = fft_lines<R, true>(b0, b1, tw, fp, nl, ls);
@@ -1166,7 +1208,7 @@ __global__ void __launch_bounds__(256) k_fft_iy(Geo g, FftPlanDev fp, const type
         const int y = qdiv(idx, nl, rnl), c = idx - y * nl;
         const int l = l0 + c;
         const int az = qdiv(l, nc1, rnc1), kx = l - az * nc1;
-        spec4[((size_t)az * n + y) * nc1 + kx] = res[c * ls + y];
+        spec4[((size_t)az * n + y) * nc1 + kx] = res[c * ls + swz<C>(y)];
     }
 }
 
@@ -1181,8 +1223,9 @@ __global__ void __launch_bounds__(256) k_fft_ix(Geo g, FftPlanDev fp, const type
     const int n = g.n, nc = g.nc, nc1 = nc + 1;
     const int nrows = g.nf * n * n;
     C* tw = reinterpret_cast<C*>(smraw);
+    const int ls = line_stride<C>(n);   // swizzled lines
     C* b0 = tw + n;
-    C* b1 = b0 + LP * n;
+    C* b1 = b0 + LP * ls;
     for (int t = threadIdx.x; t < n; t += blockDim.x) tw[t] = twg[t];
     const float rn = 1.0f / (float)n;
     const int row0 = blockIdx.x * 2 * LP;
@@ -1209,13 +1252,13 @@ __global__ void __launch_bounds__(256) k_fft_ix(Geo g, FftPlanDev fp, const type
         C z;
         z.x = a.x - b.y;   // A + i B
         z.y = a.y + b.x;
-        b0[idx] = z;
+        b0[c * ls + swz<C>(m)] = z;
     }
     __syncthreads();
-    C* res = fft_lines<R, true>(b0, b1, tw, fp, nl, n);
+    C* res = fft_lines<R, true>(b0, b1, tw, fp, nl, ls);
     for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
         const int c = qdiv(idx, n, rn), x = idx - c * n;
-        const C v = res[idx];
+        const C v = res[c * ls + swz<C>(x)];
         h[(size_t)(row0 + 2 * c) * n + x] = v.x;
         h[(size_t)(row0 + 2 * c + 1) * n + x] = v.y;
     }
