@@ -178,3 +178,31 @@ def test_dense_blob_uses_both_block_paths(enuf, prec, tol):
     assert abs(E[5] - Er[5]) < (1e-10 if prec == "fp64" else 1e-5) * max(abs(Er[5]), 1.0)
     sysm.close()
     plan.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 2e-3), ("fp32", 4e-3)])
+def test_energy_is_conserved_without_thermostat(enuf, prec, tol):
+    """With gamma = sigma = 0 the Table-2 integrator is velocity Verlet, and in
+    gradient mode the reciprocal forces are the exact gradient of the NFFT
+    energy; with the real-space and window errors made negligible (alpha r_c =
+    4.5, p = 8, beta = 4) the total E_kin + E_c + E_bond + E_elec of the whole
+    GPU step must stay flat: bounded fluctuation, no drift."""
+    s = W.polyelectrolyte(L=8.0, n_chains=3, chain_len=20, f=0.5, salt_fraction=0.1, seed_offset=41)
+    params = dict(s.params, alpha=1.5, p=8, beta=4.0)
+    P = dict(L=s.L, M=16, deriv=1, **params)
+    dp = W.dpd_params(5, gamma=0.0, sigma=0.0, dt=0.005)
+    plan = enuf.Plan(enuf.make_params(prec=prec, **P), s.N)
+    pos, vel, q = _prep(prec, s)
+    sysm = enuf.DpdSystem(plan, dp["a"], dp["gamma"], dp["sigma"], dp["dt"], pos, vel, s.types, q, s.bonds,
+                          lambda_vv=dp["lambda_vv"], K_bond=dp["K_bond"], r0_bond=dp["r0_bond"], seed=dp["seed"])
+    H = []
+    for _ in range(40):
+        E = sysm.step(10, want_energy=True)
+        H.append(E[3] + E[4] + E[5] + E[6])
+    H = np.array(H)
+    kin = E[6]
+    assert np.all(np.isfinite(H))
+    assert np.abs(H - H[0]).max() < tol * kin, (H.min(), H.max(), kin)
+    assert abs(H[-10:].mean() - H[:10].mean()) < tol * kin
+    sysm.close()
+    plan.close()
