@@ -192,8 +192,9 @@ typedef struct dpd_system_s* dpd_system_t;
  * box). pos, vel: HOST real[n][3]; type: host int[n] in [0, ntypes);
  * q: host real[n]; bonds: host int[n_bonds][2] (may be NULL when n_bonds = 0).
  * The system copies everything to the device, builds the per-bead bond list
- * and evaluates the initial force at step 0. Requires L >= 3 (cell list of
- * edge >= 1). The plan must outlive the system. */
+ * and evaluates the initial force at step 0. Requires L >= 3 (1 + 1e-5): a
+ * cell list of at least 3 cells of edge > 1 per box edge (ENUF_ERR_INVALID
+ * otherwise). The plan must outlive the system. */
 enuf_status dpd_create(enuf_plan_t plan, const dpd_params* params, int n, const void* pos,
                        const void* vel, const int* type, const void* q, int n_bonds,
                        const int* bonds, dpd_system_t* out);

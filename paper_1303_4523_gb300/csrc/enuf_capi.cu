@@ -297,12 +297,15 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
     g.c2a = 2.0 * P.alpha / std::sqrt(M_PI);
     g.xmaxf = largest_float_below(P.L);
     g.slater_k = P.slater_k;
-    if (P.slater_k) {
-        // kernel table on [0, r_c]: quintic Hermite nodes every <= 0.004 (interpolation
-        // error of I' ~ h^5, far below FP64 parity); I'(0) = lim I(r)/r gives the self term
+    if (P.slater_k || P.prec == ENUF_FP64) {
+        // real-space kernel table on [0, r_c]: quintic Hermite nodes every <= 0.004
+        // (interpolation error of J' ~ h^5, far below FP64 parity)
         g.kn = std::max(64, (int)std::ceil(P.r_cut / 0.004));
         g.kh = P.r_cut / g.kn;
         g.kinv = g.kn / P.r_cut;
+    }
+    if (P.slater_k) {
+        // I'(0) = lim I(r)/r gives the self term
         double i0[3];
         slater_kernel(P.alpha, P.beta, 0.0, i0);
         g.c_self = -0.5 * P.kappa * i0[1];
@@ -347,7 +350,7 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
            o_s3 = take((size_t)g.nf * n * nc1 * g.K * csz), o_s4 = take((size_t)g.nf * n * n * nc1 * csz),
            o_h = take(g.nf * n3 * esz), o_tab = take(ntab * 8), o_tabv = take(ntab * 8), o_tabr = take(ntab * esz),
            o_tw = take((size_t)n * csz), o_part = take((size_t)npart * 8), o_E = take(16 * 8),
-           o_ktab = take(g.slater_k ? (size_t)(g.kn + 1) * 3 * esz : 0);
+           o_ktab = take((size_t)g.kn * (P.prec == ENUF_FP64 ? kKtStride64 : kKtStride32) * esz);
     if (bytes) *bytes = off;
     if (plan) {
         plan->P = P;
@@ -384,7 +387,7 @@ void bind(enuf_plan_t p) {
     w.spec1 = at(w.spec1); w.spec2 = at(w.spec2); w.spec3 = at(w.spec3); w.spec4 = at(w.spec4);
     w.h = at(w.h); w.tab = at(w.tab); w.tabv = at(w.tabv); w.tabr = at(w.tabr);
     w.tw = at(w.tw); w.part = at(w.part); w.Edev = at(w.Edev); w.ktab = at(w.ktab);
-    p->g.ktab = p->g.slater_k ? w.ktab : nullptr;
+    p->g.ktab = p->g.kn > 0 ? w.ktab : nullptr;
 }
 
 // FP64 influence x deconvolution table over the half space kx = 0..nc:
@@ -424,23 +427,61 @@ enuf_status upload_tables(enuf_plan_t plan) {
             }
     CU(cudaMemcpy(plan->w.tab, D.data(), ntab * 8, cudaMemcpyHostToDevice));
     CU(cudaMemcpy(plan->w.tabv, Dv.data(), ntab * 8, cudaMemcpyHostToDevice));
-    if (g.slater_k) {
-        // J(r) = B1(r) - I(r) and its first two derivatives, formed in FP64 (the two
-        // terms nearly cancel over the cutoff range): u = J/r, f = (J - J' r)/r^2
-        std::vector<double> kt((size_t)(g.kn + 1) * 3);
-        for (int j = 0; j <= g.kn; ++j) {
-            const double r = j * g.kh, be = g.beta, e = std::exp(-2.0 * be * r);
-            double I[3];
-            slater_kernel(g.alpha, be, r, I);
-            kt[3 * (size_t)j] = 1.0 - (1.0 + be * r) * e - I[0];
-            kt[3 * (size_t)j + 1] = be * (1.0 + 2.0 * be * r) * e - I[1];
-            kt[3 * (size_t)j + 2] = -4.0 * be * be * be * r * e - I[2];
+    if (g.kn > 0) {
+        // J(r) = r u(r) and its first two derivatives at the nodes r = j h, in FP64:
+        // J = erfc(alpha r) - (1 + beta r) e^{-2 beta r} (the Slater term for beta > 0),
+        // or with the form factor in k space J = B1(r) - I(r) (the two terms nearly
+        // cancel over the cutoff range, so they are formed here, not in the kernel)
+        const int kn = g.kn;
+        std::vector<double> J((size_t)(kn + 1) * 3);
+        const double al = g.alpha, be = g.beta, c2a = 2.0 * al / std::sqrt(M_PI);
+        for (int j = 0; j <= kn; ++j) {
+            const double r = j * g.kh;
+            double* y = &J[3 * (size_t)j];
+            if (g.slater_k) {
+                const double e = std::exp(-2.0 * be * r);
+                double I[3];
+                slater_kernel(al, be, r, I);
+                y[0] = 1.0 - (1.0 + be * r) * e - I[0];
+                y[1] = be * (1.0 + 2.0 * be * r) * e - I[1];
+                y[2] = -4.0 * be * be * be * r * e - I[2];
+            } else {
+                const double ea = c2a * std::exp(-al * al * r * r);
+                y[0] = std::erfc(al * r);
+                y[1] = -ea;
+                y[2] = 2.0 * al * al * r * ea;
+                if (be > 0) {
+                    const double e = std::exp(-2.0 * be * r);
+                    y[0] -= (1.0 + be * r) * e;
+                    y[1] += be * (1.0 + 2.0 * be * r) * e;
+                    y[2] -= 4.0 * be * be * be * r * e;
+                }
+            }
         }
-        if (plan->prec == ENUF_FP32) {
-            std::vector<float> ktf(kt.begin(), kt.end());
-            CU(cudaMemcpy(plan->w.ktab, ktf.data(), ktf.size() * 4, cudaMemcpyHostToDevice));
+        // quintic Hermite interpolant on [j h, (j + 1) h] in t = r/h - j, power basis:
+        // c0 = y0, c1 = h y0', c2 = h^2 y0''/2, and c3..c5 from the values at t = 1
+        const bool f64 = plan->prec == ENUF_FP64;
+        const int st = f64 ? kKtStride64 : kKtStride32;
+        std::vector<double> C((size_t)kn * st, 0.0);
+        const double h = g.kh;
+        for (int j = 0; j < kn; ++j) {
+            const double* a = &J[3 * (size_t)j];
+            const double* b = a + 3;
+            const double y0 = a[0], d0 = h * a[1], s0 = h * h * a[2];
+            const double y1 = b[0], d1 = h * b[1], s1 = h * h * b[2];
+            double* c = &C[(size_t)j * st];
+            c[0] = y0;
+            c[1] = d0;
+            c[2] = 0.5 * s0;
+            c[3] = 10.0 * (y1 - y0) - 6.0 * d0 - 4.0 * d1 - 1.5 * s0 + 0.5 * s1;
+            c[4] = -15.0 * (y1 - y0) + 8.0 * d0 + 7.0 * d1 + 1.5 * s0 - s1;
+            c[5] = 6.0 * (y1 - y0) - 3.0 * d0 - 3.0 * d1 - 0.5 * s0 + 0.5 * s1;
+        }
+        if (f64) {
+            CU(cudaMemcpy(plan->w.ktab, C.data(), C.size() * 8, cudaMemcpyHostToDevice));
         } else {
-            CU(cudaMemcpy(plan->w.ktab, kt.data(), kt.size() * 8, cudaMemcpyHostToDevice));
+            std::vector<float> cf(C.begin(), C.end());
+            CU(cudaMemcpy(plan->w.ktab, cf.data(), cf.size() * 4, cudaMemcpyHostToDevice));
         }
     }
     std::vector<double> tw(2 * n);
@@ -823,7 +864,8 @@ enuf_status dpd_create(enuf_plan_t plan, const dpd_params* params, int n, const 
     if (params->ntypes < 1 || !params->a) return fail(plan, ENUF_ERR_INVALID, "ntypes < 1 or a == NULL");
     if (!(params->dt > 0)) return fail(plan, ENUF_ERR_INVALID, "dt must be > 0");
     const double L = plan->P.L;
-    if (L < 3.0) return fail(plan, ENUF_ERR_INVALID, "DPD needs L >= 3 (cell list of edge >= 1, 3 cells per edge)");
+    if (std::floor(L / (1.0 + 1e-5)) < 3.0)
+        return fail(plan, ENUF_ERR_INVALID, "DPD needs L >= 3 (1 + 1e-5): 3 cells of edge > 1 per box edge");
     for (int i = 0; i < n; ++i)
         if (type[i] < 0 || type[i] >= params->ntypes) return fail(plan, ENUF_ERR_INVALID, "type[%d] out of range", i);
     for (int k = 0; k < 2 * n_bonds; ++k)

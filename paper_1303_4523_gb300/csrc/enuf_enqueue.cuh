@@ -98,12 +98,18 @@ cudaError_t configure_kernels(int max_smem) {
     set((const void*)k_fft_z<R>);
     set((const void*)k_fft_iy<R>);
     set((const void*)k_fft_ix<R>);
-    set((const void*)k_spread_col<R, 8>);
-    set((const void*)k_spread_col<R, 10>);
-    set((const void*)k_spread_col<R, 12>);
-    set((const void*)k_spread_col<R, 16>);
-    set((const void*)k_spread_col<R, 20>);
-    set((const void*)k_spread_col<R, 24>);
+    set((const void*)k_spread_col<R, 8, false>);
+    set((const void*)k_spread_col<R, 8, true>);
+    set((const void*)k_spread_col<R, 10, false>);
+    set((const void*)k_spread_col<R, 10, true>);
+    set((const void*)k_spread_col<R, 12, false>);
+    set((const void*)k_spread_col<R, 12, true>);
+    set((const void*)k_spread_col<R, 16, false>);
+    set((const void*)k_spread_col<R, 16, true>);
+    set((const void*)k_spread_col<R, 20, false>);
+    set((const void*)k_spread_col<R, 20, true>);
+    set((const void*)k_spread_col<R, 24, false>);
+    set((const void*)k_spread_col<R, 24, true>);
     set((const void*)k_fft_xy<R>);
     set((const void*)k_fft_yx<R>);
     set((const void*)k_real<R>);
@@ -147,13 +153,15 @@ void enqueue_bin(const Geo& g, const Work& w, int N, const R* pos, const R* q, R
 // Kernels enqueue_bin launches.
 inline int bin_kernels(const Geo& g, const Work& w) { return (g.bin_last ? 2 : 4) + (w.wb ? 1 : 0); }
 
-// Spreading: the column-stationary kernel for the common tile edges, the
+// Spreading: for the common tile edges the column-stationary kernel (FP32)
+// or its slab form (FP64, where the FP64 instruction count decides), the
 // work-item kernel with shared-memory atomics otherwise (or without weights).
 template <typename R, int T>
 inline void launch_col(const Geo& g, const Work& w, R* grid, cudaStream_t s, bool pdl) {
     using V = typename V4<R>::T;
-    launch(pdl, true, k_spread_col<R, T>, g.ntiles, col_threads(T), col_smem<R>(T), s, g, (const int*)w.tstart,
-           static_cast<const V*>(w.sq), (const int*)w.sb, static_cast<const R*>(w.wb), grid);
+    constexpr bool SLAB = sizeof(R) == 8;
+    launch(pdl, true, k_spread_col<R, T, SLAB>, g.ntiles, spread2_threads<SLAB>(T), col_smem<R>(T, SLAB), s, g,
+           (const int*)w.tstart, static_cast<const V*>(w.sq), (const int*)w.sb, static_cast<const R*>(w.wb), grid);
 }
 
 template <typename R>

@@ -37,12 +37,16 @@ struct Geo {
     double c_self;   // -kappa alpha / sqrt(pi)           (E_self = c_self * sum q^2)
     double c_neut;   // -kappa pi / (2 V alpha^2)         (E_neutral = c_neut * Q^2)
     double c_recip;  // kappa / (2 pi L)                  (E_recip = c_recip * sum D |F|^2)
-    int slater_k;    // 1: Slater form factor in k space, tabulated real-space kernel
-    int kn;          // kernel table intervals on [0, r_c]
+    int slater_k;    // 1: Slater form factor in k space (real-space kernel J = B1 - I)
+    int kn;          // real-space kernel table intervals on [0, r_c] (0: no table)
     double kinv;     // kn / r_c
     double kh;       // r_c / kn
-    const void* ktab;  // real [kn + 1][3]: J, J', J'' at r = j kh, J = B1 - I (k-space Slater)
+    const void* ktab;  // real [kn][kKtStride]: quintic coefficients of J(r) = r u(r) per interval
 };
+
+// Row length of the real-space kernel table (16-byte aligned rows).
+constexpr int kKtStride64 = 6;   // c_0..c_5 in double
+constexpr int kKtStride32 = 8;   // c_0..c_5 in float, 2 padding
 
 // Lines per CTA of each FFT pass.
 struct FftShape {
@@ -88,7 +92,7 @@ struct Work {
     double* tabv;    // [nc+1][K][K] D(k) times the virial weight 1 - 2 pi^2 k^2/(alpha L)^2
     void* tabr;      // real copy of tab
     void* tw;        // cplx [n] twiddles e^{-2 pi i t/n}
-    void* ktab;      // real [kn + 1][3] k-space Slater kernel table (slater_k = 1)
+    void* ktab;      // real [kn][kKtStride] real-space kernel table (FP64, or slater_k = 1)
     double* part;    // per-block partial sums
     double* Edev;    // [16] reduced totals
     // partial-sum segments (offsets into part, in doubles)

@@ -45,9 +45,22 @@ __device__ __forceinline__ float r_erfc(float x) { return erfcf(x); }
 __device__ __forceinline__ double r_erfc(double x) { return erfc(x); }
 __device__ __forceinline__ float r_sqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double r_sqrt(double x) { return sqrt(x); }
-// 1/sqrt: the hardware approximation in float (2 ulp), the exact quotient in double
+// 1/sqrt: the hardware approximation in float (2 ulp). In double, Newton's
+// iteration for x^{-1/2}, y <- y + y (1/2 - (x/2) y^2), from the float value:
+// the relative error e goes to ~(3/2) e^2 per step, 2^-21 -> 2^-41 -> rounding
+// (within 2 ulp), in 3 multiplies and 4 fused multiply-adds on the FP64 units
+// instead of a correctly rounded square root and quotient. Outside the normal
+// float range of x the quotient is taken.
 __device__ __forceinline__ float r_rsqrt(float x) { return rsqrtf(x); }
-__device__ __forceinline__ double r_rsqrt(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ double r_rsqrt(double x) {
+    const float xf = (float)x;
+    if (!(xf > 1e-30f && xf < 1e30f)) return 1.0 / sqrt(x);
+    double y = (double)rsqrtf(xf);
+    const double h = 0.5 * x;
+    y = fma(y, fma(-h, y * y, 0.5), y);
+    y = fma(y, fma(-h, y * y, 0.5), y);
+    return y;
+}
 
 // ---------------------------------------------------------------------------
 // Coordinates. Wrapping and grid coordinates are computed in double with the
@@ -584,6 +597,18 @@ __device__ __forceinline__ unsigned tap_mask(int b, int o, int T, int n, int ntd
     return m;
 }
 
+// Slots [lo, lo + cnt) of the tile (lines o .. o + T - 1) that hold the taps in
+// mask m != 0: contiguous taps on contiguous slots, else (taps or slots wrap
+// around a grid of few tiles) the whole tile, whose other slots weigh 0.
+__device__ __forceinline__ int tap_slots(unsigned m, int b, int o, int T, int n, int p) {
+    const int t0 = __ffs(m) - 1, t1 = 31 - __clz(m), c = __popc(m);
+    int s0 = b - p + 1 + t0 - o;   // in (-n - p, n + p)
+    s0 += s0 < 0 ? n : 0;
+    s0 -= s0 >= n ? n : 0;
+    const bool run = c == t1 - t0 + 1 && s0 + c <= T;
+    return run ? (s0 | c << 5) : (T << 5);
+}
+
 template <typename R>
 __global__ void __launch_bounds__(kSpreadThreads, 5) k_spread(Geo g, const int* __restrict__ tstart,
                                                            const typename V4<R>::T* __restrict__ sq,
@@ -743,27 +768,42 @@ __global__ void __launch_bounds__(kSpreadThreads, 5) k_spread(Geo g, const int* 
 constexpr int kColCand = 512;    // candidates staged per round
 constexpr int kColItems = 128;   // items per weight batch
 
+//
+// SLAB (the FP64 form): the same staging, but the tile is accumulated in
+// shared memory and each of the 4 warps owns a slab of z-planes; per item a
+// warp whose slab meets the item's z-range spreads the item's footprint
+// (its slots in x and y, lanes over the footprint's columns) into its planes.
+// The FP64 units are then spent on the item's taps only: the column form
+// multiplies every column of the tile by every z-slot, zero or not, and on
+// GB300's few FP64 units that was ~4x the instructions.
+constexpr int kSlabThreads = 128;
 __host__ __device__ constexpr int col_threads(int T) { return T * T <= 128 ? 128 : ((T * T + 31) / 32) * 32; }
+template <bool SLAB>
+__host__ __device__ constexpr int spread2_threads(int T) { return SLAB ? kSlabThreads : col_threads(T); }
 
 template <typename R>
-__host__ __device__ constexpr int col_smem(int T) {
-    return kColCand * (4 + 4 + 8 + (int)sizeof(R)) + kColItems * 3 * T * (int)sizeof(R);
+__host__ __device__ constexpr int col_smem(int T, bool slab = false) {
+    return kColCand * (4 + 4 + 8 + (int)sizeof(R)) + kColItems * 3 * T * (int)sizeof(R) +
+           (slab ? T * T * T * (int)sizeof(R) : 0);
 }
 
-template <typename R, int T>
-__global__ void __launch_bounds__(col_threads(T)) k_spread_col(Geo g, const int* __restrict__ tstart,
-                                                               const typename V4<R>::T* __restrict__ sq,
-                                                               const int* __restrict__ sb,
-                                                               const R* __restrict__ wb, R* __restrict__ grid) {
+template <typename R, int T, bool SLAB>
+__global__ void __launch_bounds__(spread2_threads<SLAB>(T)) k_spread_col(Geo g, const int* __restrict__ tstart,
+                                                                        const typename V4<R>::T* __restrict__ sq,
+                                                                        const int* __restrict__ sb,
+                                                                        const R* __restrict__ wb,
+                                                                        R* __restrict__ grid) {
     pdl_enter();
-    constexpr int NT = col_threads(T);
+    constexpr int NT = spread2_threads<SLAB>(T);
     constexpr int NW = NT / 32;
+    constexpr int SZ = (T + NW - 1) / NW;   // SLAB: z-planes per warp
     extern __shared__ __align__(16) unsigned char smraw[];
     R* wt = reinterpret_cast<R*>(smraw);                        // [kColItems][3][T]
     R* cq = wt + kColItems * 3 * T;                             // [kColCand] charges
     int* cslot = reinterpret_cast<int*>(cq + kColCand);         // [kColCand] sorted slots
     int* cbase = cslot + kColCand;                              // [kColCand] packed bases
-    int2* items = reinterpret_cast<int2*>(cbase + kColCand);    // [kColCand] (candidate, masks)
+    int2* items = reinterpret_cast<int2*>(cbase + kColCand);    // [kColCand] (candidate, slot ranges)
+    R* acc_s = reinterpret_cast<R*>(items + kColCand);          // SLAB: [T][T][T] tile
     __shared__ int nb_start[27], nb_pre[28];
     __shared__ int nnb, nitems;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -801,10 +841,15 @@ __global__ void __launch_bounds__(col_threads(T)) k_spread_col(Geo g, const int*
     __syncthreads();
     const int P2 = 2 * g.p, n = g.n;
     const int cx = tid % T, cy = tid / T;   // this thread's column (tid < T^2)
-    const bool owner = tid < T * T;
-    R acc[T];
+    const bool owner = !SLAB && tid < T * T;
+    R acc[SLAB ? 1 : T];
+    const int z0w = warp * SZ, z1w = min(T, z0w + SZ);   // SLAB: this warp's planes
+    if constexpr (SLAB) {
+        for (int e = z0w * T * T + lane; e < z1w * T * T; e += 32) acc_s[e] = (R)0;
+    } else {
 #pragma unroll
-    for (int z = 0; z < T; ++z) acc[z] = (R)0;
+        for (int z = 0; z < T; ++z) acc[z] = (R)0;
+    }
     const int total = nb_pre[nnb];
     for (int cb = 0; cb < total; cb += kColCand) {
         const int cn = min(kColCand, total - cb);
@@ -832,11 +877,17 @@ __global__ void __launch_bounds__(col_threads(T)) k_spread_col(Geo g, const int*
                 if (my) mz = tap_mask((pb >> 20) & 1023, o[2], T, n, g.ntd, g.p);
             }
             const bool keep = mz != 0u;
+            int rg = 0;   // SLAB: slot ranges (lo | cnt << 5) of x, y, z at bits 0, 10, 20
+            if (SLAB && keep) {
+                const int pb = cbase[c];
+                rg = tap_slots(mx, pb & 1023, o[0], T, n, g.p) | tap_slots(my, (pb >> 10) & 1023, o[1], T, n, g.p) << 10 |
+                     tap_slots(mz, (pb >> 20) & 1023, o[2], T, n, g.p) << 20;
+            }
             const unsigned bal = __ballot_sync(0xffffffffu, keep);
             int basei = 0;
             if (lane == 0 && bal) basei = atomicAdd(&nitems, __popc(bal));
             basei = __shfl_sync(0xffffffffu, basei, 0);
-            if (keep) items[basei + __popc(bal & ((1u << lane) - 1u))] = make_int2(c, 0);
+            if (keep) items[basei + __popc(bal & ((1u << lane) - 1u))] = make_int2(c, rg);
         }
         __syncthreads();
         const int ni = nitems;
@@ -858,7 +909,26 @@ __global__ void __launch_bounds__(col_threads(T)) k_spread_col(Geo g, const int*
                 wt[e] = v;
             }
             __syncthreads();
-            if (owner) {
+            if constexpr (SLAB) {
+                for (int i = 0; i < nb; ++i) {
+                    const int rg = items[ib + i].y;
+                    const int lz = (rg >> 20) & 31, hz = lz + ((rg >> 25) & 31);
+                    const int za = max(lz, z0w), zb = min(hz, z1w);
+                    if (za >= zb) continue;   // warp-uniform
+                    const int lx = rg & 31, nx = (rg >> 5) & 31, ly = (rg >> 10) & 31, ny = (rg >> 15) & 31;
+                    const R* wi = wt + i * 3 * T;
+                    // xy -> (ix, iy) by a float reciprocal: xy < 576 and the true quotient of
+                    // xy + 1/2 is at least 1/48 away from an integer, far above the error
+                    const float inx = 1.0f / (float)nx;
+                    for (int xy = lane; xy < nx * ny; xy += 32) {
+                        const int iy = (int)(((float)xy + 0.5f) * inx);
+                        const int x = lx + xy - iy * nx, y = ly + iy;
+                        const R w = wi[x] * wi[T + y];
+                        R* a = acc_s + y * T + x;
+                        for (int z = za; z < zb; ++z) a[z * T * T] += w * wi[2 * T + z];
+                    }
+                }
+            } else if (owner) {
                 for (int i = 0; i < nb; ++i) {
                     const R* wi = wt + i * 3 * T;
                     const R w = wi[cx] * wi[T + cy];
@@ -871,7 +941,13 @@ __global__ void __launch_bounds__(col_threads(T)) k_spread_col(Geo g, const int*
             __syncthreads();
         }
     }
-    if (owner) {
+    if constexpr (SLAB) {   // each warp writes its own planes, rows of T points
+        const size_t n2 = (size_t)n * n;
+        for (int e = z0w * T * T + lane; e < z1w * T * T; e += 32) {
+            const int z = e / (T * T), r = e - z * T * T, y = r / T, x = r - y * T;
+            grid[(size_t)(o[2] + z) * n2 + (size_t)(o[1] + y) * n + (o[0] + x)] = acc_s[e];
+        }
+    } else if (owner) {
         R* col = grid + ((size_t)o[2] * n + (o[1] + cy)) * n + (o[0] + cx);
         const size_t n2 = (size_t)n * n;
 #pragma unroll
@@ -1376,34 +1452,51 @@ constexpr int real_smem_bytes() {   // FP64 adds the float copy, the staged slot
            (sizeof(R) == 8 ? real_cap<R>() * ((int)sizeof(float4) + 4) + (kRealThreads / 32) * 64 * 4 : 0);
 }
 
-// Pair energy u(r) and radial force f(r) = -du/dr of the real-space sum:
-// erfc(alpha r)/r minus the Slater correction (1 + beta r) e^{-2 beta r}/r;
-// with the Slater form factor in k space (kt != null), phi_S(r) - I(r)/r =
-// J(r)/r with J = B1 - I from the quintic Hermite table kt[j] = (J, J', J'')
-// at r = j h, and f = (J - J' r)/r^2.
+// Kernel table: per interval [j h, (j + 1) h] of [0, r_c] the power-basis
+// coefficients c_0..c_5 of the quintic Hermite interpolant of J in t = r/h - j
+// (J, J', J'' matched at both ends); kKtStride64 / kKtStride32 values per
+// interval (16-byte aligned rows: 6 doubles, or 6 floats padded to 8).
+template <typename R>
+__device__ __forceinline__ void kt_load(const R* __restrict__ kt, int j, R (&c)[6]) {
+    if constexpr (sizeof(R) == 8) {
+        const double2* a = reinterpret_cast<const double2*>(kt + kKtStride64 * j);
+        const double2 a0 = __ldg(a), a1 = __ldg(a + 1), a2 = __ldg(a + 2);
+        c[0] = a0.x; c[1] = a0.y; c[2] = a1.x; c[3] = a1.y; c[4] = a2.x; c[5] = a2.y;
+    } else {
+        const float4* a = reinterpret_cast<const float4*>(kt + kKtStride32 * j);
+        const float4 a0 = __ldg(a), a1 = __ldg(a + 1);
+        c[0] = a0.x; c[1] = a0.y; c[2] = a0.z; c[3] = a0.w; c[4] = a1.x; c[5] = a1.y;
+    }
+}
+
+// Pair energy u(r) and radial force f(r) = -du/dr of the real-space sum,
+// u = J(r)/r with J = erfc(alpha r) - (1 + beta r) e^{-2 beta r} (the
+// Slater correction, beta > 0), or with the Slater form factor in k space
+// J = B1 - I. With a table (kt != null: FP64, and the k-space form factor)
+// J and dJ/dt come from one Horner pass over the interval's coefficients and
+// f = (J - J' r)/r^2; otherwise erfc and exp are evaluated directly.
 template <typename R>
 __device__ __forceinline__ void real_pair(R r2, R al, R c2a, R be, bool slater, R& u, R& fr_over_r, R& f_r,
-                                          const R* __restrict__ kt = nullptr, int kn = 0, R kinv = 0, R kh = 0) {
+                                          const R* __restrict__ kt = nullptr, int kn = 0, R kinv = 0) {
     const R ir = r_rsqrt(r2);
     const R r = r2 * ir;
     if (kt) {
         const R x = r * kinv;
         int j = (int)x;
-        j = j < 0 ? 0 : (j >= kn ? kn - 1 : j);
+        j = j >= kn ? kn - 1 : j;   // x >= 0
         const R t = x - (R)j;
-        const R* a = kt + 3 * j;
-        const R y0 = a[0], d0 = a[1] * kh, s0 = a[2] * kh * kh;
-        const R y1 = a[3], d1 = a[4] * kh, s1 = a[5] * kh * kh;
-        const R t2 = t * t, t3 = t2 * t, t4 = t3 * t, t5 = t4 * t;
-        const R J = y0 * ((R)1 - (R)10 * t3 + (R)15 * t4 - (R)6 * t5) + d0 * (t - (R)6 * t3 + (R)8 * t4 - (R)3 * t5) +
-                    s0 * (R)0.5 * (t2 - (R)3 * t3 + (R)3 * t4 - t5) + y1 * ((R)10 * t3 - (R)15 * t4 + (R)6 * t5) +
-                    d1 * ((R)-4 * t3 + (R)7 * t4 - (R)3 * t5) + s1 * (R)0.5 * (t3 - (R)2 * t4 + t5);
-        const R dJ = (y0 * ((R)-30 * t2 + (R)60 * t3 - (R)30 * t4) + d0 * ((R)1 - (R)18 * t2 + (R)32 * t3 - (R)15 * t4) +
-                      s0 * (R)0.5 * ((R)2 * t - (R)9 * t2 + (R)12 * t3 - (R)5 * t4) +
-                      y1 * ((R)30 * t2 - (R)60 * t3 + (R)30 * t4) + d1 * ((R)-12 * t2 + (R)28 * t3 - (R)15 * t4) +
-                      s1 * (R)0.5 * ((R)3 * t2 - (R)8 * t3 + (R)5 * t4)) * kinv;
-        const R ff = (J - dJ * r) * ir * ir;
-        u = J * ir;
+        R c[6];
+        kt_load<R>(kt, j, c);
+        R d = c[5];
+        R p = fma(c[5], t, c[4]);
+#pragma unroll
+        for (int k = 3; k >= 0; --k) {
+            d = fma(d, t, p);
+            p = fma(p, t, c[k]);
+        }
+        // J = p, J' r = (dJ/dt) (1/h) r = d x
+        const R ff = fma(-d, x, p) * ir * ir;
+        u = p * ir;
         fr_over_r = ff * ir;
         f_r = ff * r;
         return;
@@ -1439,7 +1532,7 @@ __device__ __forceinline__ void real_drain(const Geo& g, const V* qu, const int*
         const V e = qu[lane];
         const R r2 = dist2(e.x, e.y, e.z);
         R u, fo, fr;
-        real_pair<R>(r2, al, c2a, be, slater, u, fo, fr, static_cast<const R*>(g.ktab), g.kn, (R)g.kinv, (R)g.kh);
+        real_pair<R>(r2, al, c2a, be, slater, u, fo, fr, static_cast<const R*>(g.ktab), g.kn, (R)g.kinv);
         const R qq = kap * qi * e.w;
         const R gx = qq * fo * e.x, gy = qq * fo * e.y, gz = qq * fo * e.z;
         fx += gx;
@@ -1454,6 +1547,41 @@ __device__ __forceinline__ void real_drain(const Geo& g, const V* qu, const int*
         const R ws = HALF ? (R)1 : (R)0.5;   // energy and virial per pair
         eacc += ws * qq * u;
         wacc += ws * qq * fr;
+    }
+}
+
+// Staged FP64: the queue holds the staged index of candidates that passed
+// the float pre-test; the double displacement, the exact cutoff decision and
+// the pair run here, on full warps (the sweep's candidates pass the float
+// test on a few lanes at a time, and every FP64 instruction costs the whole
+// warp's issue on GB300's FP64 units).
+template <typename R, typename V>
+__device__ __forceinline__ void real_drain_staged(const Geo& g, const V& pi, const V* stg, const int* stgslot,
+                                                  const int* quj, int m, int lane, R L, R hL, R rc2, R kap, R al,
+                                                  R c2a, R be, bool slater, const V* __restrict__ sw,
+                                                  R* __restrict__ F, R& fx, R& fy, R& fz, R& eacc, R& wacc) {
+    if (lane < m) {
+        const int f = quj[lane];
+        const V pj = stg[f];
+        const R dx = min_image(pi.x, pj.x, L, hL);
+        const R dy = min_image(pi.y, pj.y, L, hL);
+        const R dz = min_image(pi.z, pj.z, L, hL);
+        const R r2 = dist2(dx, dy, dz);
+        if (r2 < rc2 && r2 > (R)0) {
+            R u, fo, fr;
+            real_pair<R>(r2, al, c2a, be, slater, u, fo, fr, static_cast<const R*>(g.ktab), g.kn, (R)g.kinv);
+            const R qq = kap * pi.w * pj.w;
+            const R gx = qq * fo * dx, gy = qq * fo * dy, gz = qq * fo * dz;
+            fx += gx;
+            fy += gy;
+            fz += gz;
+            const int j = real_as_int(sw[stgslot[f]].w);
+            atomicAdd(&F[3 * j], -gx);
+            atomicAdd(&F[3 * j + 1], -gy);
+            atomicAdd(&F[3 * j + 2], -gz);
+            eacc += qq * u;
+            wacc += qq * fr;
+        }
     }
 }
 
@@ -1528,7 +1656,9 @@ __device__ __forceinline__ void real_beads(const Geo& g, int c0, int c1, int sel
                     const float rz = min_image(pif.z, b.z, Lf, hLf);
                     cand = dist2(rx, ry, rz) <= r2hi;
                 }
-                if (cand) {
+                if (PRE) {
+                    hit = cand;   // decided exactly in the drain
+                } else if (cand) {
                     V pj;
                     pj = STAGED ? stg[f] : sq[gs];
                     dx = min_image(pi.x, pj.x, L, hL);
@@ -1540,21 +1670,30 @@ __device__ __forceinline__ void real_beads(const Geo& g, int c0, int c1, int sel
                 }
                 const unsigned m = __ballot_sync(0xffffffffu, hit);
                 if (hit) {
-                    V e;
-                    e.x = dx; e.y = dy; e.z = dz; e.w = qj;
                     const int at = cnt + __popc(m & ((1u << lane) - 1u));
-                    qu[at] = e;
-                    if (real_half<R>()) quj[at] = gs;
+                    if (PRE) {
+                        quj[at] = f;
+                    } else {
+                        V e;
+                        e.x = dx; e.y = dy; e.z = dz; e.w = qj;
+                        qu[at] = e;
+                        if (real_half<R>()) quj[at] = gs;
+                    }
                 }
                 cnt += __popc(m);
             }
             if (cnt >= 32 || (last && cnt > 0)) {
                 const int m = min(cnt, 32);
                 __syncwarp();
-                real_drain<R, V>(g, qu, quj, m, lane, pi.w, kap, al, c2a, be, slater, sw, F, fx, fy, fz, eacc, wacc);
+                if constexpr (PRE)
+                    real_drain_staged<R, V>(g, pi, stg, stgslot, quj, m, lane, L, hL, rc2, kap, al, c2a, be, slater,
+                                            sw, F, fx, fy, fz, eacc, wacc);
+                else
+                    real_drain<R, V>(g, qu, quj, m, lane, pi.w, kap, al, c2a, be, slater, sw, F, fx, fy, fz, eacc,
+                                     wacc);
                 __syncwarp();
                 if (lane < cnt - m) {
-                    qu[lane] = qu[m + lane];
+                    if (!PRE) qu[lane] = qu[m + lane];
                     if (real_half<R>()) quj[lane] = quj[m + lane];
                 }
                 __syncwarp();
@@ -1764,8 +1903,9 @@ __device__ __forceinline__ R dpd_theta(uint64_t seed, uint64_t step, int i, int 
     const uint32_t lo = (uint32_t)min(i, j), hi = (uint32_t)max(i, j);
     const uint32_t w = philox_word0(lo, hi, (uint32_t)step, (uint32_t)(step >> 32), (uint32_t)seed,
                                     (uint32_t)(seed >> 32));
-    const R u = ((R)w + (R)0.5) * (R)2.3283064365386962890625e-10;  // 2^-32
-    return (R)1.7320508075688772935 * ((R)2 * u - (R)1);
+    // sqrt3 (2 u - 1) with u = (w + 1/2) 2^-32
+    return fma((R)w, (R)(2.0 * 1.7320508075688772935 * 2.3283064365386962890625e-10),
+               (R)(1.7320508075688772935 * (2.3283064365386962890625e-10 - 1.0)));
 }
 
 // DPD pair forces (Eq. 2-7, R_c = 1) + bonds (Sec. 2), added into F (which
@@ -1785,9 +1925,13 @@ __device__ __forceinline__ R dpd_theta(uint64_t seed, uint64_t step, int i, int 
 // once. The staged force array is added to F once per block. The harmonic
 // bonds run as one thread per bond into F.
 //
-// FP64: the cutoff test r^2 < 1 is taken on a float copy of the staged
-// positions first and redone in double only inside a band around 1 (and
-// near 0) that covers the float error, so the decision is the double one.
+// The staged copies are unwrapped: the halo cells that lie across a box
+// face are shifted by L, so the plain difference of two staged positions is
+// the minimum image of every pair within r = 1 (cell edge >= 1) and no pair
+// needs the wrap test. FP64: the cutoff test r^2 < 1 is taken on a float copy
+// of the staged positions first and redone in double only inside a band
+// around 1 (and near 0) that covers the float error, so the decision is the
+// double one.
 constexpr int kDpdThreads = 256;
 constexpr int kDpdCap = 896;     // staged beads
 constexpr int kDpdMaxB = 4;      // cells per block edge
@@ -1803,7 +1947,7 @@ constexpr int dpd_smem_bytes() {
 template <typename R, typename V, bool STAGED>
 __device__ __forceinline__ void dpd_pairs(const bool valid, const int2 e, const V* __restrict__ P,
                                           const V* __restrict__ Pv, R* fh, R* __restrict__ F,
-                                          const R* __restrict__ atab, int ntypes, R L, R hL, R gam, R sig, R rdt,
+                                          const R* __restrict__ atab, int ntypes, R L, R hL, R gam, R srdt,
                                           uint64_t seed, uint64_t step, R& ec) {
     const int lane = threadIdx.x & 31;
     R fx = 0, fy = 0, fz = 0;
@@ -1811,9 +1955,11 @@ __device__ __forceinline__ void dpd_pairs(const bool valid, const int2 e, const 
     if (valid) {
         const V pi = P[e.x], vi = Pv[e.x];
         const V pj = P[e.y], vj = Pv[e.y];
-        const R rx = min_image(pi.x, pj.x, L, hL);
-        const R ry = min_image(pi.y, pj.y, L, hL);
-        const R rz = min_image(pi.z, pj.z, L, hL);
+        // staged copies are unwrapped into one frame around the block: the
+        // plain difference is the minimum image for every pair within r = 1
+        const R rx = STAGED ? pi.x - pj.x : min_image(pi.x, pj.x, L, hL);
+        const R ry = STAGED ? pi.y - pj.y : min_image(pi.y, pj.y, L, hL);
+        const R rz = STAGED ? pi.z - pj.z : min_image(pi.z, pj.z, L, hL);
         const R r2 = dist2(rx, ry, rz);
         const R ir = r_rsqrt(r2);
         const R r = r2 * ir;
@@ -1821,9 +1967,11 @@ __device__ __forceinline__ void dpd_pairs(const bool valid, const int2 e, const 
         const int i = real_as_int(pi.w), j = real_as_int(pj.w);
         const int ti = real_as_int(vi.w), tj = real_as_int(vj.w);
         const R a = atab[ti * ntypes + tj];
-        const R vr = ((vi.x - vj.x) * rx + (vi.y - vj.y) * ry + (vi.z - vj.z) * rz) * ir;
+        const R vd = (vi.x - vj.x) * rx + (vi.y - vj.y) * ry + (vi.z - vj.z) * rz;   // r_ij . v_ij
         const R th = dpd_theta<R>(seed, step, i, j);
-        const R fm = (a * w - gam * w * w * vr + sig * w * th * rdt) * ir;
+        // Eq. 3-5 with w^D = (w^R)^2 = w^2: |F| = w (a - gamma w (r.v)/r + sigma theta/sqrt(dt))
+        const R wi = w * ir;
+        const R fm = wi * fma(-gam * wi, vd, fma(srdt, th, a));
         fx = fm * rx;
         fy = fm * ry;
         fz = fm * rz;
@@ -1836,7 +1984,7 @@ __device__ __forceinline__ void dpd_pairs(const bool valid, const int2 e, const 
             atomicAdd(&F[3 * j + 1], -fy);
             atomicAdd(&F[3 * j + 2], -fz);
         }
-        ec += (R)0.5 * a * w * w;
+        ec = fma(a * w, w, ec);   // a w^2; halved once per block
         key = e.x;
         oi = i;
     }
@@ -1870,12 +2018,13 @@ __device__ __forceinline__ void dpd_pairs(const bool valid, const int2 e, const 
     }
 }
 
-// The exact cutoff decision 0 < r^2 < 1 in the working precision.
-template <typename R, typename V>
+// The exact cutoff decision 0 < r^2 < 1 in the working precision (WRAP:
+// minimum image of wrapped positions; else the unwrapped staged frame).
+template <typename R, typename V, bool WRAP>
 __device__ __forceinline__ bool dpd_within(const V& pi, const V& pj, R L, R hL) {
-    const R rx = min_image(pi.x, pj.x, L, hL);
-    const R ry = min_image(pi.y, pj.y, L, hL);
-    const R rz = min_image(pi.z, pj.z, L, hL);
+    const R rx = WRAP ? min_image(pi.x, pj.x, L, hL) : pi.x - pj.x;
+    const R ry = WRAP ? min_image(pi.y, pj.y, L, hL) : pi.y - pj.y;
+    const R rz = WRAP ? min_image(pi.z, pj.z, L, hL) : pi.z - pj.z;
     const R r2 = dist2(rx, ry, rz);
     return r2 < (R)1 && r2 > (R)0;
 }
@@ -1899,7 +2048,7 @@ __device__ __forceinline__ void dpd_cells(const DpdDev& d, int H, int B3, const 
     constexpr int nseg = STAGED ? 5 : kDpdSegU;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const R L = (R)d.L, hL = (R)(0.5 * d.L);
-    const R gam = (R)d.gamma, sig = (R)d.sigma, rdt = (R)d.rdt;
+    const R gam = (R)d.gamma, srdt = (R)(d.sigma * d.rdt);
     int cnt = 0;   // queued pairs of this warp, carried across its cells
     for (int cc = warp; cc < B3; cc += NW) {
         const int h = chalo[cc];
@@ -1968,13 +2117,10 @@ __device__ __forceinline__ void dpd_cells(const DpdDev& d, int H, int B3, const 
                 if (vj && (STAGED ? j > me : (s != 0 || j > me))) {
                     if constexpr (PRE) {
                         const float4 a = Pf[me];
-                        const float rx = min_image(a.x, pjf.x, band.L, band.hL);
-                        const float ry = min_image(a.y, pjf.y, band.L, band.hL);
-                        const float rz = min_image(a.z, pjf.z, band.L, band.hL);
-                        const float r2 = dist2(rx, ry, rz);
-                        if (r2 <= band.hi) hit = (r2 < band.lo && r2 > band.lo0) || dpd_within<R, V>(P[me], pj, L, hL);
+                        const float r2 = dist2(a.x - pjf.x, a.y - pjf.y, a.z - pjf.z);
+                        if (r2 <= band.hi) hit = (r2 < band.lo && r2 > band.lo0) || dpd_within<R, V, false>(P[me], pj, L, hL);
                     } else {
-                        hit = dpd_within<R, V>(P[me], pj, L, hL);
+                        hit = dpd_within<R, V, !STAGED>(P[me], pj, L, hL);
                     }
                 }
                 const unsigned m = __ballot_sync(0xffffffffu, hit);
@@ -1982,7 +2128,7 @@ __device__ __forceinline__ void dpd_cells(const DpdDev& d, int H, int B3, const 
                 cnt += __popc(m);
                 if (cnt >= 32) {
                     __syncwarp();
-                    dpd_pairs<R, V, STAGED>(true, queue[lane], P, Pv, fh, F, atab, d.ntypes, L, hL, gam, sig, rdt,
+                    dpd_pairs<R, V, STAGED>(true, queue[lane], P, Pv, fh, F, atab, d.ntypes, L, hL, gam, srdt,
                                             d.seed, step, ec);
                     __syncwarp();
                     if (lane < cnt - 32) queue[lane] = queue[32 + lane];
@@ -1994,7 +2140,7 @@ __device__ __forceinline__ void dpd_cells(const DpdDev& d, int H, int B3, const 
     }
     __syncwarp();
     if (cnt > 0)
-        dpd_pairs<R, V, STAGED>(lane < cnt, queue[lane], P, Pv, fh, F, atab, d.ntypes, L, hL, gam, sig, rdt, d.seed,
+        dpd_pairs<R, V, STAGED>(lane < cnt, queue[lane], P, Pv, fh, F, atab, d.ntypes, L, hL, gam, srdt, d.seed,
                                 step, ec);
 }
 
@@ -2016,6 +2162,7 @@ __global__ void __launch_bounds__(kDpdThreads, sizeof(R) == 4 ? 4 : 2)
     constexpr int HMAX = (kDpdMaxB + 2) * (kDpdMaxB + 2) * (kDpdMaxB + 2);
     __shared__ int hoff[HMAX + 1], gst[HMAX];
     __shared__ int chalo[kDpdMaxB * kDpdMaxB * kDpdMaxB];
+    __shared__ unsigned char hsh[HMAX];   // per halo cell: 2 bits per axis, 1: -L, 2: +L
     const uint64_t step = *stepp;
     const int ncd = d.ncd, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     int2* queue = queues + warp * 64;
@@ -2035,10 +2182,12 @@ __global__ void __launch_bounds__(kDpdThreads, sizeof(R) == 4 ? 4 : 2)
                 const R xj = wrap_r(pos[3 * j + t], d.L, d.xmaxf);
                 dd[t] = min_image(xi, xj, L, hL);
             }
-            const R r = r_sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
-            eb += (R)0.5 * Kb * (r - r0b) * (r - r0b);
-            if (r > (R)0) {
-                const R fm = -Kb * (r - r0b) / r;
+            const R r2 = dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2];
+            const R ir = r2 > (R)0 ? r_rsqrt(r2) : (R)0;
+            const R dr = r2 * ir - r0b;   // r - r0
+            eb = fma(Kb * dr, dr, eb);    // K (r - r0)^2; halved once per block
+            if (r2 > (R)0) {
+                const R fm = -Kb * dr * ir;
 #pragma unroll
                 for (int t = 0; t < 3; ++t) {
                     atomicAdd(&F[3 * i + t], fm * dd[t]);
@@ -2047,8 +2196,9 @@ __global__ void __launch_bounds__(kDpdThreads, sizeof(R) == 4 ? 4 : 2)
             }
         }
     }
-    // float band of the FP64 cutoff test: float positions and L carry at most
-    // L 2^-24 each, so |r2f - r2| <= 1.3e-6 L + 3e-7 for r2 near 1
+    // float band of the FP64 cutoff test: the staged float positions (in
+    // [-1 - L/3, 4L/3]) carry at most (4L/3 + 1) 2^-24 each, so for r2 near 1
+    // |r2f - r2| <= 7e-7 (L + 1) + 3e-7
     DpdBand band;
     band.L = (float)d.L;
     band.hL = (float)(0.5 * d.L);
@@ -2061,12 +2211,14 @@ __global__ void __launch_bounds__(kDpdThreads, sizeof(R) == 4 ? 4 : 2)
         const int c0x = bx * B, c0y = by * B, c0z = bz * B;
         if (tid < H3) {   // halo cell ranges (H^3 <= 216 cells)
             const int hx = tid % H, hy = (tid / H) % H, hz = tid / (H * H);
-            const int cx = (c0x - 1 + hx + ncd) % ncd, cy = (c0y - 1 + hy + ncd) % ncd,
-                      cz = (c0z - 1 + hz + ncd) % ncd;
+            const int ux = c0x - 1 + hx, uy = c0y - 1 + hy, uz = c0z - 1 + hz;   // unwrapped
+            const int cx = (ux + ncd) % ncd, cy = (uy + ncd) % ncd, cz = (uz + ncd) % ncd;
             const int c = (cz * ncd + cy) * ncd + cx;
             const int st = cstart[c];
             gst[tid] = st;
             hoff[tid] = cstart[c + 1] - st;
+            auto code = [&](int u) { return u < 0 ? 1 : (u >= ncd ? 2 : 0); };
+            hsh[tid] = (unsigned char)(code(ux) | code(uy) << 2 | code(uz) << 4);
         }
         if (tid < B3) {   // central cells of this block (clipped at the box edge)
             const int ix = tid % B, iy = (tid / B) % B, iz = tid / (B * B);
@@ -2109,7 +2261,17 @@ __global__ void __launch_bounds__(kDpdThreads, sizeof(R) == 4 ? 4 : 2)
                     if (hoff[mid] <= f) lo = mid; else hi = mid;
                 }
                 const int j = gst[lo] + f - hoff[lo];
-                const V p = sp[j];
+                V p = sp[j];
+                // the halo is H <= ncd distinct cells: shift the cells across
+                // the box faces into one frame (cell edge >= 1, so beads of
+                // adjacent halo cells are within r = 1 only as this image)
+                const int sc = hsh[lo];
+                if (sc) {
+                    auto sh = [&](int c) { return c == 1 ? -L : (c == 2 ? L : (R)0); };
+                    p.x += sh(sc & 3);
+                    p.y += sh((sc >> 2) & 3);
+                    p.z += sh(sc >> 4);
+                }
                 spos[f] = p;
                 svel[f] = sv[j];
                 if (F64) spf[f] = make_float4((float)p.x, (float)p.y, (float)p.z, 0.f);
@@ -2130,7 +2292,7 @@ __global__ void __launch_bounds__(kDpdThreads, sizeof(R) == 4 ? 4 : 2)
         }
         __syncthreads();
     }
-    double e1 = (double)ec, e2 = (double)eb;
+    double e1 = 0.5 * (double)ec, e2 = 0.5 * (double)eb;
     block_sum2(e1, e2);
     if (threadIdx.x == 0) {
         dpart[2 * blockIdx.x] = e1;

@@ -122,6 +122,33 @@ def test_bad_inputs_are_rejected(enuf):
     plan.close()
 
 
+def test_box_needs_three_cells_per_edge(enuf):
+    """The staged DPD halo (block of B <= ncd - 2 cells plus one cell on each
+    side) holds distinct cells only with ncd >= 3 cells of edge > 1: L = 3
+    gives ncd = 2 (the edge rule keeps cells longer than 1 + 1e-5) and is
+    rejected, L = 3.01 runs."""
+    dp = W.dpd_params(5)
+    rng = np.random.default_rng(11)
+    n = 64
+    for L, ok in [(3.0, False), (3.01, True)]:
+        pos = rng.uniform(0.0, L, (n, 3))
+        vel = rng.normal(0.0, 1.0, (n, 3))
+        types = np.zeros(n, np.int32)
+        q = np.zeros(n)
+        plan = enuf.Plan(enuf.make_params(L=L, alpha=1.0, r_cut=1.4, beta=0.0, kappa=1.0, M=4, p=2), n)
+        args = (plan, dp["a"], dp["gamma"], dp["sigma"], dp["dt"], pos, vel, types, q, np.zeros((0, 2), np.int32))
+        if ok:
+            sysm = enuf.DpdSystem(*args)
+            sysm.step(2)
+            _, _, F, _ = sysm.get_state()
+            assert np.all(np.isfinite(F))
+            sysm.close()
+        else:
+            with pytest.raises(enuf.EnufError):
+                enuf.DpdSystem(*args)
+        plan.close()
+
+
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 1e-5)])
 def test_full_size_polyelectrolyte_sampled(enuf, prec, tol):
     """The bench workload (81000 beads, L = 30): initial ENUF-DPD force of 256
