@@ -1384,41 +1384,47 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Geo g, const int* __r
                 const R d = fr[t] + (R)(g.p - 1 - lane);   // n x - l
                 const R w = wb ? wb[(size_t)s * 3 * P2 + t * P2 + lane] : wn * r_exp(-d * d * rb);
                 wts[warp][t][lane] = w;
-                dwts[warp][t][lane] = (R)-2 * d * rb * w;
+                if (grad) dwts[warp][t][lane] = (R)-2 * d * rb * w;
             }
         }
         __syncwarp();
         R ax = 0, ay = 0, az = 0;
+        // lanes over the (x, y) taps, the z taps summed first and weighted by
+        // the column's x-y weight once; ab -> (a, b) by a float reciprocal
+        // (ab < 256, so the quotient of ab + 1/2 is 1/32 from an integer)
         if (grad) {   // one field: sum_l grad Psi(n x - l) h(l)
             for (int ab = lane; ab < P2 * P2; ab += 32) {
                 const int b = (int)(((float)ab + 0.5f) * iP2);
                 const int a = ab - b * P2;
-                const R wx = wts[warp][0][a], wy = wts[warp][1][b];
-                const R cx = dwts[warp][0][a] * wy, cy = wx * dwts[warp][1][b], cz = wx * wy;
                 const int rowo = lix[warp][1][b] * n + lix[warp][0][a];
+                R s0 = 0, s1 = 0;   // sum_z psi h, sum_z psi' h
                 for (int c = 0; c < P2; ++c) {
                     const R hv = h0[lix[warp][2][c] + rowo];
-                    const R t = hv * wts[warp][2][c];
-                    ax += cx * t;
-                    ay += cy * t;
-                    az += cz * (hv * dwts[warp][2][c]);
+                    s0 = fma(wts[warp][2][c], hv, s0);
+                    s1 = fma(dwts[warp][2][c], hv, s1);
                 }
+                const R wx = wts[warp][0][a], wy = wts[warp][1][b];
+                ax = fma(dwts[warp][0][a] * wy, s0, ax);
+                ay = fma(wx * dwts[warp][1][b], s0, ay);
+                az = fma(wx * wy, s1, az);
             }
         } else {
-            // lanes over the (x, y) taps, a loop over z; ab -> (a, b) by a float
-            // reciprocal (ab < 256, so the quotient of ab + 1/2 is 1/32 from an integer)
             for (int ab = lane; ab < P2 * P2; ab += 32) {
                 const int b = (int)(((float)ab + 0.5f) * iP2);
                 const int a = ab - b * P2;
-                const R wab = wts[warp][0][a] * wts[warp][1][b];
                 const int rowo = lix[warp][1][b] * n + lix[warp][0][a];
+                R s0 = 0, s1 = 0, s2 = 0;   // sum_z psi h_a
                 for (int c = 0; c < P2; ++c) {
-                    const R w = wab * wts[warp][2][c];
+                    const R w = wts[warp][2][c];
                     const int off = lix[warp][2][c] + rowo;   // z index pre-scaled by n^2
-                    ax += w * h0[off];
-                    ay += w * h1[off];
-                    az += w * h2[off];
+                    s0 = fma(w, h0[off], s0);
+                    s1 = fma(w, h1[off], s1);
+                    s2 = fma(w, h2[off], s2);
                 }
+                const R wab = wts[warp][0][a] * wts[warp][1][b];
+                ax = fma(wab, s0, ax);
+                ay = fma(wab, s1, ay);
+                az = fma(wab, s2, az);
             }
         }
         ax = warp_sum_r(ax);
@@ -1994,8 +2000,9 @@ __device__ __forceinline__ void dpd_pairs(const bool valid, const int2 e, const 
     const unsigned heads = __ballot_sync(0xffffffffu, head);
     const unsigned after = lane == 31 ? 0u : heads & (0xffffffffu << (lane + 1));
     const int end = after ? __ffs(after) - 1 : 32;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
+    // levels up to the longest run of the batch (typically 2-3 of 5)
+    const int longest = __reduce_max_sync(0xffffffffu, head ? end - lane : 0);
+    for (int o = 1; o < longest; o <<= 1) {
         const R ax = __shfl_down_sync(0xffffffffu, fx, o);
         const R ay = __shfl_down_sync(0xffffffffu, fy, o);
         const R az = __shfl_down_sync(0xffffffffu, fz, o);
