@@ -2179,15 +2179,16 @@ __global__ void __launch_bounds__(kDpdThreads, sizeof(R) == 4 ? 4 : 2)
     R ec = 0, eb = 0;
     // harmonic bonds (Sec. 2): one thread per bond, +f to i and -f to j
     {
-        const R Kb = (R)d.K_bond, r0b = (R)d.r0_bond;
+        const R Kb = (R)d.K_bond, r0b = (R)d.r0_bond, iL = (R)(1.0 / d.L);
         for (int k = blockIdx.x * blockDim.x + tid; k < d.nbonds; k += gridDim.x * blockDim.x) {
             const int i = bnd[2 * k], j = bnd[2 * k + 1];
             R dd[3];
 #pragma unroll
             for (int t = 0; t < 3; ++t) {
-                const R xi = wrap_r(pos[3 * i + t], d.L, d.xmaxf);
-                const R xj = wrap_r(pos[3 * j + t], d.L, d.xmaxf);
-                dd[t] = min_image(xi, xj, L, hL);
+                // minimum image of the raw (unwrapped) difference; a bond is far
+                // shorter than L/2, so d/L is never near a half-integer
+                const R dx = pos[3 * i + t] - pos[3 * j + t];
+                dd[t] = dx - L * rint(dx * iL);
             }
             const R r2 = dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2];
             const R ir = r2 > (R)0 ? r_rsqrt(r2) : (R)0;
