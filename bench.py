@@ -426,7 +426,8 @@ def run_sizes(args):
     hbm = peaks["hbm_gbs"]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     rows = []
-    for N in (3000, 24000, 81000, 192000, 375000, 3000000):
+    sizes = (3000, 24000, 81000, 192000, 375000, 3000000)
+    for N in (sizes if not args.sizes_n else [N for N in sizes if N in args.sizes_n]):
         s = W.electrolyte_sweep(N) if N < 3_000_000 else W.electrolyte(N, seed_offset=499)
         row = {"N": N, "L": round(s.L, 3), "M": s.M}
         for key, prec, dt, esz, deriv in (("fp32", "fp32", torch.float32, 4, 0), ("fp64", "fp64", torch.float64, 8, 0),
@@ -579,6 +580,8 @@ def main():
                     help="main: the bench line; sizes/batch/serve: the scaling sweep, the 64-system batch and the "
                          "serving load (each prints its own JSON line)")
     ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--sizes-n", type=int, nargs="*", default=None,
+                    help="--mode sizes: run only these system sizes (of 3000 24000 81000 192000 375000 3000000)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 

@@ -90,6 +90,11 @@ CASES = {
                              (1000, 10.0, 200)),
     "tile12_M36_p6": (dict(L=20.0, alpha=0.8, r_cut=4.0, beta=4.0, kappa=1.1, M=36, p=6, tile=12),
                       (4000, 20.0, 500)),
+    # the largest tile edges, two tiles per axis: windows that wrap around the grid
+    "tile20_M20_p4": (dict(L=12.0, alpha=1.0, r_cut=3.0, beta=4.0, kappa=1.0, M=20, p=4, tile=20),
+                      (1500, 12.0, 300)),
+    "tile24_M24_p5": (dict(L=14.0, alpha=1.0, r_cut=3.0, beta=2.0, kappa=1.0, M=24, p=5, tile=24),
+                      (2000, 14.0, 400)),
 }
 
 
