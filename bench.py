@@ -290,8 +290,9 @@ def e2e_run(args, s, dp, P, torch, enuf):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
         _check(lib.dpd_set_state(sysm.h, _ptr(pos), _ptr(vel), _ptr(F), step), plan.h)
-        sysm.step(1, want_energy=True)
-        step = sysm.get_state_into(pos, vel, F)
+        sysm.step(1)
+        step = sysm.get_state_into(pos, vel, F)   # waits for the step
+        sysm.step(0, want_energy=True)            # the step's energies (copied to pinned memory in the graph)
     dt = time.perf_counter() - t0
     sysm.close()
     plan.close()

@@ -100,6 +100,9 @@ typedef struct {
     int    fft_kernels;        /* FFT kernels per evaluation: 3 with the fused plane passes
                                   (see enuf_params.fft_path), else 5 */
     size_t device_bytes;       /* device memory the plan holds */
+    int    fft_stages;         /* Stockham stages of one length-n line transform */
+    int    fft_radix[8];       /* their radices in order (2, 3, 4, 5, 8; FP32 grids
+                                  from n = 128 on also 6, 10, 12, 16, 20) */
 } enuf_plan_info;
 
 /* Create a plan for systems of up to n_max beads with the given parameters

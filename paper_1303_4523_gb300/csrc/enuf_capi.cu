@@ -44,22 +44,43 @@ int grid_rule(double L) {
     return std::max(best, 8);
 }
 
-bool fft_radices(int n, FftPlanDev& fp) {
+// The fewest Stockham stages of length n over a radix set; ties go to the
+// earlier radix of the list. 0 stages: not factorable.
+std::vector<int> radix_plan(int n, bool composite) {
+    static const int kRad[] = {20, 16, 12, 10, 8, 6, 5, 4, 3, 2};
+    std::vector<int> best(n + 1, 1 << 20), pick(n + 1, 0), out;
+    best[1] = 0;
+    for (int m = 2; m <= n; ++m) {
+        if (n % m) continue;   // only divisors of n occur
+        for (int r : kRad)
+            if ((composite || (r <= 8 && r != 6)) && m % r == 0 && best[m / r] + 1 < best[m]) {
+                best[m] = best[m / r] + 1;
+                pick[m] = r;
+            }
+    }
+    if (best[n] >= (1 << 20)) return out;
+    for (int m = n; m > 1; m /= pick[m]) out.push_back(pick[m]);
+    return out;
+}
+
+// Radices 2, 3, 4, 5, 8; in float (the composite radices 6, 10, 12, 16, 20 of
+// the float kernels) the composite plan when it saves a stage and n >= 128.
+// Every stage is one pass over the lines in shared memory with its index
+// arithmetic, whatever its radix, but a large radix leaves n/r butterflies
+// per line: measured, two-stage plans were slower below n = 128 (too few
+// butterflies to fill a CTA) and 3-8% faster from n = 128 to 320.
+bool fft_radices(int n, FftPlanDev& fp, bool composite) {
     fp.n = n;
     fp.nst = 0;
-    int m = n;
-    auto push = [&](int r) {
-        if (fp.nst >= 8) return false;
-        fp.rad[fp.nst++] = r;
-        m /= r;
-        return true;
-    };
-    while (m % 8 == 0) if (!push(8)) return false;
-    while (m % 4 == 0) if (!push(4)) return false;
-    while (m % 2 == 0) if (!push(2)) return false;
-    while (m % 3 == 0) if (!push(3)) return false;
-    while (m % 5 == 0) if (!push(5)) return false;
-    return m == 1;
+    if (n < 2) return false;
+    std::vector<int> plan = radix_plan(n, false);
+    if (composite && n >= 128) {
+        const std::vector<int> alt = radix_plan(n, true);
+        if (!alt.empty() && (plan.empty() || alt.size() < plan.size())) plan = alt;
+    }
+    if (plan.empty() || plan.size() > 8) return false;
+    for (int r : plan) fp.rad[fp.nst++] = r;
+    return true;
 }
 
 // Largest float strictly below L: a float x lies in [0, L) iff 0 <= x <= this.
@@ -196,7 +217,8 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
     const int n = P.sigma_s * M;
     if (n > 1024) return fail(plan, ENUF_ERR_UNSUPPORTED, "grid n = %d > 1024", n);
     FftPlanDev fp{};
-    if (!fft_radices(n, fp)) return fail(plan, ENUF_ERR_UNSUPPORTED, "grid n = %d is not 2^a 3^b 5^c", n);
+    if (!fft_radices(n, fp, P.prec == ENUF_FP32))
+        return fail(plan, ENUF_ERR_UNSUPPORTED, "grid n = %d is not 2^a 3^b 5^c", n);
     if (2 * P.p > n) return fail(plan, ENUF_ERR_INVALID, "window 2p = %d wider than the grid", 2 * P.p);
     // tile edge: divides n, >= p, histogram fits in shared memory
     // the spreading kernel holds a T^3 tile of the grid in shared memory: T <= 24
@@ -288,6 +310,9 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
     {
         const long long plane = (long long)(n + n * ls) * csz;
         fs.fused = (P.prec == ENUF_FP32 && plane <= 100 * 1024 && P.fft_path == 0) ? 1 : 0;
+        fs.composite = 0;
+        for (int st = 0; st < fp.nst; ++st)
+            if (fp.rad[st] > 8 || fp.rad[st] == 6) fs.composite = 1;
         fs.smem_xy = fs.smem_yx = (int)plane;
         fs.t_xy = fs.t_yx = 512;
     }
@@ -659,6 +684,8 @@ enuf_status enuf_get_info(enuf_plan_t plan, enuf_plan_info* info) {
     info->n_max = plan->n_max;
     info->fft_kernels = plan->fs.fused ? 3 : 5;
     info->device_bytes = plan->dbytes;
+    info->fft_stages = plan->fp.nst;
+    for (int i = 0; i < 8; ++i) info->fft_radix[i] = i < plan->fp.nst ? plan->fp.rad[i] : 0;
     return ENUF_OK;
 }
 
@@ -973,13 +1000,12 @@ enuf_status dpd_set_state(dpd_system_t sys, const void* pos, const void* vel, co
     if (pos) CU(cudaMemcpyAsync(sys->d.pos, pos, b, cudaMemcpyHostToDevice, plan->stream));
     if (vel) CU(cudaMemcpyAsync(sys->d.vel, vel, b, cudaMemcpyHostToDevice, plan->stream));
     CU(cudaMemcpyAsync(sys->d.step_dev, &step, 8, cudaMemcpyHostToDevice, plan->stream));
+    if (F) CU(cudaMemcpyAsync(sys->d.F, F, b, cudaMemcpyHostToDevice, plan->stream));
+    // one synchronisation: the caller may reuse its buffers (and the step
+    // value on this stack frame is read) once the copies have completed
     CU(cudaStreamSynchronize(plan->stream));
     sys->step = step;
-    if (F) {
-        CU(cudaMemcpyAsync(sys->d.F, F, b, cudaMemcpyHostToDevice, plan->stream));
-        CU(cudaStreamSynchronize(plan->stream));
-        return ENUF_OK;
-    }
+    if (F) return ENUF_OK;
     return initial_force(sys);
 }
 

@@ -98,6 +98,15 @@ cudaError_t configure_kernels(int max_smem) {
     set((const void*)k_fft_z<R>);
     set((const void*)k_fft_iy<R>);
     set((const void*)k_fft_ix<R>);
+    if constexpr (sizeof(R) == 4) {
+        set((const void*)k_fft_x<R, true>);
+        set((const void*)k_fft_y<R, true>);
+        set((const void*)k_fft_z<R, true>);
+        set((const void*)k_fft_iy<R, true>);
+        set((const void*)k_fft_ix<R, true>);
+        set((const void*)k_fft_xy<R, true>);
+        set((const void*)k_fft_yx<R, true>);
+    }
     set((const void*)k_spread_col<R, 8, false>);
     set((const void*)k_spread_col<R, 8, true>);
     set((const void*)k_spread_col<R, 10, false>);
@@ -182,6 +191,38 @@ inline void enqueue_spread(const Geo& g, const Work& w, R* grid, cudaStream_t s,
            static_cast<const V*>(w.sq), static_cast<const V*>(w.sw), (const int*)w.sb, grid);
 }
 
+// The FFT passes of one evaluation (fused plane passes or five line passes);
+// CR selects the kernels compiled with the composite radices.
+template <typename R, bool CR>
+void enqueue_fft(const Geo& g, const FftShape& fs, const FftPlanDev& fp, const Work& w, cudaStream_t s0, bool pdl,
+                 LaunchLog* log) {
+    using C = typename Cx<R>::T;
+    const C* tw = static_cast<const C*>(w.tw);
+    if (fs.fused) {   // whole z-planes in shared memory: x+y, z (+convolve), y+x
+        launch(pdl, true, k_fft_xy<R, CR>, g.n, fs.t_xy, fs.smem_xy, s0, g, fp, static_cast<const R*>(w.grid),
+               tw, static_cast<C*>(w.spec2));
+        launch(pdl, true, k_fft_z<R, CR>, fs.grid_z, fs.tz, fs.smem_z, s0, g, fp, static_cast<const C*>(w.spec2),
+               tw, (const double*)w.tab, (const double*)w.tabv, static_cast<const R*>(w.tabr),
+               static_cast<C*>(w.spec3), w.part + w.off_recip, fs.lz, 1);
+        launch(pdl, true, k_fft_yx<R, CR>, g.nf * g.n, fs.t_yx, fs.smem_yx, s0, g, fp, static_cast<const C*>(w.spec3),
+               tw, static_cast<R*>(w.h));
+        log->kernels += 4;
+    } else {
+        launch(pdl, true, k_fft_x<R, CR>, fs.grid_x, fs.tx, fs.smem_x, s0, g, fp, static_cast<const R*>(w.grid),
+               tw, static_cast<C*>(w.spec1), fs.lx);
+        launch(pdl, true, k_fft_y<R, CR>, dim3(g.nc + 1, fs.grid_y_z), fs.ty, fs.smem_y, s0, g, fp,
+               static_cast<const C*>(w.spec1), tw, static_cast<C*>(w.spec2), fs.ly);
+        launch(pdl, true, k_fft_z<R, CR>, fs.grid_z, fs.tz, fs.smem_z, s0, g, fp, static_cast<const C*>(w.spec2),
+               tw, (const double*)w.tab, (const double*)w.tabv, static_cast<const R*>(w.tabr),
+               static_cast<C*>(w.spec3), w.part + w.off_recip, fs.lz, 0);
+        launch(pdl, true, k_fft_iy<R, CR>, fs.grid_iy, fs.tiy, fs.smem_iy, s0, g, fp, static_cast<const C*>(w.spec3),
+               tw, static_cast<C*>(w.spec4), fs.liy);
+        launch(pdl, true, k_fft_ix<R, CR>, fs.grid_ix, fs.tix, fs.smem_ix, s0, g, fp, static_cast<const C*>(w.spec4),
+               tw, static_cast<R*>(w.h), fs.lix);
+        log->kernels += 6;
+    }
+}
+
 template <typename R>
 cudaError_t enqueue_enuf(const Geo& g, const FftShape& fs, const FftPlanDev& fp, const Work& w,
                          const EvalArgs& a, cudaStream_t s0, cudaStream_t s1, cudaEvent_t evFork,
@@ -216,28 +257,13 @@ cudaError_t enqueue_enuf(const Geo& g, const FftShape& fs, const FftPlanDev& fp,
     enqueue_spread<R>(g, w, static_cast<R*>(w.grid), s0, pdl);
     rec(ev, 1, false, s0);
     rec(ev, 2, true, s0);
-    if (fs.fused) {   // whole z-planes in shared memory: x+y, z (+convolve), y+x
-        launch(pdl, true, k_fft_xy<R>, g.n, fs.t_xy, fs.smem_xy, s0, g, fp, static_cast<const R*>(w.grid),
-               (const C*)tw, static_cast<C*>(w.spec2));
-        launch(pdl, true, k_fft_z<R>, fs.grid_z, fs.tz, fs.smem_z, s0, g, fp, static_cast<const C*>(w.spec2),
-               (const C*)tw, (const double*)w.tab, (const double*)w.tabv, static_cast<const R*>(w.tabr),
-               static_cast<C*>(w.spec3), w.part + w.off_recip, fs.lz, 1);
-        launch(pdl, true, k_fft_yx<R>, g.nf * g.n, fs.t_yx, fs.smem_yx, s0, g, fp, static_cast<const C*>(w.spec3),
-               (const C*)tw, static_cast<R*>(w.h));
-        log->kernels += 4;
+    if constexpr (sizeof(R) == 4) {
+        if (fs.composite)
+            enqueue_fft<R, true>(g, fs, fp, w, s0, pdl, log);
+        else
+            enqueue_fft<R, false>(g, fs, fp, w, s0, pdl, log);
     } else {
-        launch(pdl, true, k_fft_x<R>, fs.grid_x, fs.tx, fs.smem_x, s0, g, fp, static_cast<const R*>(w.grid),
-               (const C*)tw, static_cast<C*>(w.spec1), fs.lx);
-        launch(pdl, true, k_fft_y<R>, dim3(g.nc + 1, fs.grid_y_z), fs.ty, fs.smem_y, s0, g, fp,
-               static_cast<const C*>(w.spec1), (const C*)tw, static_cast<C*>(w.spec2), fs.ly);
-        launch(pdl, true, k_fft_z<R>, fs.grid_z, fs.tz, fs.smem_z, s0, g, fp, static_cast<const C*>(w.spec2),
-               (const C*)tw, (const double*)w.tab, (const double*)w.tabv, static_cast<const R*>(w.tabr),
-               static_cast<C*>(w.spec3), w.part + w.off_recip, fs.lz, 0);
-        launch(pdl, true, k_fft_iy<R>, fs.grid_iy, fs.tiy, fs.smem_iy, s0, g, fp, static_cast<const C*>(w.spec3),
-               (const C*)tw, static_cast<C*>(w.spec4), fs.liy);
-        launch(pdl, true, k_fft_ix<R>, fs.grid_ix, fs.tix, fs.smem_ix, s0, g, fp, static_cast<const C*>(w.spec4),
-               (const C*)tw, static_cast<R*>(w.h), fs.lix);
-        log->kernels += 6;
+        enqueue_fft<R, false>(g, fs, fp, w, s0, pdl, log);
     }
     rec(ev, 2, false, s0);
 

@@ -1,4 +1,4 @@
-// enuf_fft.cuh -- batched shared-memory FFT of length n = 2^a 3^b 5^c (n <= 512).
+// enuf_fft.cuh -- batched shared-memory FFT of length n = 2^a 3^b 5^c (n <= 1024).
 //
 // The 3-D transforms of the NFFT (the "standard FFT" of Sec. 3.3 inside the
 // transposed and conjugated NFFT, Eq. 13-14) are done one dimension at a time;
@@ -8,8 +8,13 @@
 // x[j + r n/R], twiddles element r by w^{r k n/(Ns R)} (k = j mod Ns,
 // w = e^{-+2 pi i/n}), does an R-point DFT and writes the results to
 // (j - k) R + k + m Ns. After the last stage the line is in natural order.
+// Radices 2, 3, 4, 5, 8 and the composites 6, 10, 12, 16, 20 (two small DFTs
+// in registers with compile-time twiddles), so most lengths take two stages.
 #pragma once
 #include <cuda_runtime.h>
+
+#include <type_traits>
+#include <utility>
 
 namespace enuf {
 
@@ -150,6 +155,109 @@ template <typename R, bool INV> struct SmallDft<R, 5, INV> {
     }
 };
 
+// Compile-time loop: f(std::integral_constant<int, i>) for i = 0 .. N-1.
+template <typename F, int... I>
+__device__ __forceinline__ void sfor_(F&& f, std::integer_sequence<int, I...>) {
+    (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, typename F>
+__device__ __forceinline__ void sfor(F&& f) {
+    sfor_(f, std::make_integer_sequence<int, N>{});
+}
+
+// cos and sin of 2 pi m / N, evaluated by the compiler: the angle is reduced
+// to [0, pi/2) by its quadrant (exact integer arithmetic), then Taylor series
+// to 30 terms (the last term is below 1e-60 there).
+struct Root {
+    double c, s;
+};
+__host__ __device__ constexpr double taylor_cos(double x) {
+    double sum = 1.0, t = 1.0;
+    for (int k = 1; k < 30; ++k) {
+        t *= -x * x / ((2.0 * k - 1.0) * (2.0 * k));
+        sum += t;
+    }
+    return sum;
+}
+__host__ __device__ constexpr double taylor_sin(double x) {
+    double sum = x, t = x;
+    for (int k = 1; k < 30; ++k) {
+        t *= -x * x / ((2.0 * k) * (2.0 * k + 1.0));
+        sum += t;
+    }
+    return sum;
+}
+__host__ __device__ constexpr Root unit_root(int m, int N) {
+    m = ((m % N) + N) % N;
+    const int q = 4 * m / N;            // quadrant
+    const int rn = 4 * m - q * N;       // remaining angle (pi/2) rn / N in [0, pi/2)
+    const double r = 1.57079632679489661923 * rn / N;
+    const double c = taylor_cos(r), sn = taylor_sin(r);
+    return q == 0 ? Root{c, sn} : q == 1 ? Root{-sn, c} : q == 2 ? Root{-c, -sn} : Root{sn, -c};
+}
+
+// a omega^M with omega = e^{-2 pi i/N} (forward) or e^{+2 pi i/N} (inverse);
+// the quarter turns are exact rotations.
+template <int M, int N, bool INV, typename R, typename C>
+__device__ __forceinline__ C twiddle_const(C a) {
+    constexpr int m = M % N;
+    if constexpr (m == 0) {
+        return a;
+    } else if constexpr (4 * m == N) {
+        return rot_i<C, INV>(a);
+    } else if constexpr (2 * m == N) {
+        a.x = -a.x;
+        a.y = -a.y;
+        return a;
+    } else if constexpr (4 * m == 3 * N) {
+        return rot_i<C, !INV>(a);
+    } else {
+        constexpr Root w = unit_root(m, N);
+        const R c = (R)w.c, sn = INV ? (R)w.s : (R)-w.s;
+        C r;
+        r.x = a.x * c - a.y * sn;
+        r.y = a.x * sn + a.y * c;
+        return r;
+    }
+}
+
+// Composite radix N1 N2 in registers (Cooley-Tukey): input index N2 n1 + n2,
+// N2 DFTs of length N1 over n1, twiddle omega_{N1 N2}^{n2 k1}, N1 DFTs of
+// length N2 over n2; output index k1 + N1 k2 (natural order).
+template <typename R, int N1, int N2, bool INV>
+struct CompositeDft {
+    template <typename C>
+    __device__ __forceinline__ static void run(C* v) {
+        constexpr int RR = N1 * N2;
+        C y[RR];   // y[n2 N1 + k1]
+        sfor<N2>([&](auto n2c) {
+            constexpr int n2 = decltype(n2c)::value;
+            C a[N1];
+#pragma unroll
+            for (int n1 = 0; n1 < N1; ++n1) a[n1] = v[N2 * n1 + n2];
+            SmallDft<R, N1, INV>::run(a);
+            sfor<N1>([&](auto k1c) {
+                constexpr int k1 = decltype(k1c)::value;
+                y[n2 * N1 + k1] = twiddle_const<n2 * k1, RR, INV, R>(a[k1]);
+            });
+        });
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) {
+            C b[N2];
+#pragma unroll
+            for (int n2 = 0; n2 < N2; ++n2) b[n2] = y[n2 * N1 + k1];
+            SmallDft<R, N2, INV>::run(b);
+#pragma unroll
+            for (int k2 = 0; k2 < N2; ++k2) v[k1 + N1 * k2] = b[k2];
+        }
+    }
+};
+template <typename R, bool INV> struct SmallDft<R, 6, INV> : CompositeDft<R, 2, 3, INV> {};
+template <typename R, bool INV> struct SmallDft<R, 10, INV> : CompositeDft<R, 2, 5, INV> {};
+template <typename R, bool INV> struct SmallDft<R, 12, INV> : CompositeDft<R, 4, 3, INV> {};
+template <typename R, bool INV> struct SmallDft<R, 16, INV> : CompositeDft<R, 4, 4, INV> {};
+template <typename R, bool INV> struct SmallDft<R, 20, INV> : CompositeDft<R, 4, 5, INV> {};
+
 // One Stockham stage over nlines lines (line l at offset l*ls, swizzled inside).
 template <typename R, int RAD, bool INV>
 __device__ __forceinline__ void fft_stage(const typename Cx<R>::T* __restrict__ src,
@@ -187,7 +295,10 @@ __device__ __forceinline__ void fft_stage(const typename Cx<R>::T* __restrict__ 
 
 // Transform nlines lines held in b0; b1 is scratch of the same size. Returns
 // the buffer holding the result. Contains __syncthreads (call from all threads).
-template <typename R, bool INV>
+// CR: the composite radices 6, 10, 12, 16, 20 are compiled in (the plan's
+// radix list decides which instance runs; they raise the kernels' register
+// count, so plans without them run the CR = false instance).
+template <typename R, bool INV, bool CR = false>
 __device__ typename Cx<R>::T* fft_lines(typename Cx<R>::T* b0, typename Cx<R>::T* b1,
                                         const typename Cx<R>::T* tw, const FftPlanDev& fp,
                                         int nlines, int ls) {
@@ -197,12 +308,23 @@ __device__ typename Cx<R>::T* fft_lines(typename Cx<R>::T* b0, typename Cx<R>::T
     int Ns = 1;
     for (int st = 0; st < fp.nst; ++st) {
         const int rad = fp.rad[st];
+        if constexpr (CR) {
+            switch (rad) {
+                case 16: fft_stage<R, 16, INV>(src, dst, tw, fp.n, Ns, nlines, ls); break;
+                case 20: fft_stage<R, 20, INV>(src, dst, tw, fp.n, Ns, nlines, ls); break;
+                case 12: fft_stage<R, 12, INV>(src, dst, tw, fp.n, Ns, nlines, ls); break;
+                case 10: fft_stage<R, 10, INV>(src, dst, tw, fp.n, Ns, nlines, ls); break;
+                case 6: fft_stage<R, 6, INV>(src, dst, tw, fp.n, Ns, nlines, ls); break;
+                default: break;
+            }
+        }
         switch (rad) {
             case 8: fft_stage<R, 8, INV>(src, dst, tw, fp.n, Ns, nlines, ls); break;
             case 4: fft_stage<R, 4, INV>(src, dst, tw, fp.n, Ns, nlines, ls); break;
             case 2: fft_stage<R, 2, INV>(src, dst, tw, fp.n, Ns, nlines, ls); break;
             case 3: fft_stage<R, 3, INV>(src, dst, tw, fp.n, Ns, nlines, ls); break;
-            default: fft_stage<R, 5, INV>(src, dst, tw, fp.n, Ns, nlines, ls); break;
+            case 5: fft_stage<R, 5, INV>(src, dst, tw, fp.n, Ns, nlines, ls); break;
+            default: break;
         }
         __syncthreads();
         C* t = src; src = dst; dst = t;

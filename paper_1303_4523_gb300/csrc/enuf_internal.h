@@ -62,6 +62,7 @@ struct FftShape {
     // (two kernels instead of four); spec2 is then plane-major [z][kx][ky]
     int fused;
     int t_xy, t_yx, smem_xy, smem_yx;
+    int composite;   // the radix plan uses 6, 10, 12, 16 or 20 (FP32): the CR kernel instances
 };
 
 // Device workspace of one plan (all pointers device memory, one allocation).

@@ -959,7 +959,7 @@ __global__ void __launch_bounds__(spread2_threads<SLAB>(T)) k_spread_col(Geo g, 
 // a3: forward FFT pass along x (R2C, two real rows per complex line), keep
 // k_x = 0..nc; output spec1[z][kx][y].
 // ---------------------------------------------------------------------------
-template <typename R>
+template <typename R, bool CR = false>
 __global__ void __launch_bounds__(256) k_fft_x(Geo g, FftPlanDev fp, const R* __restrict__ grid,
                                               const typename Cx<R>::T* __restrict__ twg,
                                               typename Cx<R>::T* __restrict__ spec1, int LP) {
@@ -985,7 +985,7 @@ __global__ void __launch_bounds__(256) k_fft_x(Geo g, FftPlanDev fp, const R* __
         b0[c * ls + swz<C>(x)] = v;
     }
     __syncthreads();
-    C* res = fft_lines<R, false>(b0, b1, tw, fp, nl, ls);
+    C* res = fft_lines<R, false, CR>(b0, b1, tw, fp, nl, ls);
     // split the two real transforms: A = (Z_k + conj Z_{n-k})/2, B = -i (Z_k - conj Z_{n-k})/2
     for (int idx = threadIdx.x; idx < nl * nc1; idx += blockDim.x) {
         const int k = qdiv(idx, nl, rnl), c = idx - k * nl;
@@ -1005,7 +1005,7 @@ __global__ void __launch_bounds__(256) k_fft_x(Geo g, FftPlanDev fp, const R* __
 }
 
 // forward pass along y for lines (z, kx), keep |ky| <= nc; output spec2[kx][ky][z]
-template <typename R>
+template <typename R, bool CR = false>
 __global__ void __launch_bounds__(256) k_fft_y(Geo g, FftPlanDev fp, const typename Cx<R>::T* __restrict__ spec1,
                                               const typename Cx<R>::T* __restrict__ twg,
                                               typename Cx<R>::T* __restrict__ spec2, int LB) {
@@ -1028,7 +1028,7 @@ __global__ void __launch_bounds__(256) k_fft_y(Geo g, FftPlanDev fp, const typen
         b0[c * ls + swz<C>(y)] = spec1[((size_t)(z0 + c) * nc1 + kx) * n + y];
     }
     __syncthreads();
-    C* res = fft_lines<R, false>(b0, b1, tw, fp, nl, ls);
+    C* res = fft_lines<R, false, CR>(b0, b1, tw, fp, nl, ls);
     for (int idx = threadIdx.x; idx < nl * K; idx += blockDim.x) {
         const int ki = qdiv(idx, nl, rnl), c = idx - ki * nl;
         const int ky = ki - g.nc;
@@ -1040,7 +1040,7 @@ __global__ void __launch_bounds__(256) k_fft_y(Geo g, FftPlanDev fp, const typen
 // fields G_a = -i k_a D F (a = x, y, z; Eq. 24) or, in gradient mode, the one
 // field G = D F; all fields of the CTA's lines inverse-transformed together;
 // output spec3[a][z][kx][ky].
-template <typename R>
+template <typename R, bool CR = false>
 __global__ void __launch_bounds__(256) k_fft_z(Geo g, FftPlanDev fp, const typename Cx<R>::T* __restrict__ spec2,
                                               const typename Cx<R>::T* __restrict__ twg,
                                               const double* __restrict__ tab, const double* __restrict__ tabv,
@@ -1074,7 +1074,7 @@ __global__ void __launch_bounds__(256) k_fft_z(Geo g, FftPlanDev fp, const typen
         }
     }
     __syncthreads();
-    C* Fh = fft_lines<R, false>(b0, b1, tw, fp, nl, ls);
+    C* Fh = fft_lines<R, false, CR>(b0, b1, tw, fp, nl, ls);
     // energy and virial of the kept modes (half space kx >= 0, kx > 0 counted twice)
     Kahan ke, kw;
     for (int idx = threadIdx.x; idx < nl * K; idx += blockDim.x) {
@@ -1122,7 +1122,7 @@ __global__ void __launch_bounds__(256) k_fft_z(Geo g, FftPlanDev fp, const typen
         X[(a * nl + c) * ls + swz<C>(m)] = v;
     }
     __syncthreads();
-    C* res = fft_lines<R, true>(X, Y, tw, fp, nf * nl, ls);
+    C* res = fft_lines<R, true, CR>(X, Y, tw, fp, nf * nl, ls);
     for (int idx = threadIdx.x; idx < nf * per; idx += blockDim.x) {
         const int a = qdiv(idx, per, rper), e = idx - a * per;
         const int z = qdiv(e, nl, rnl), c = e - z * nl;
@@ -1134,7 +1134,7 @@ __global__ void __launch_bounds__(256) k_fft_z(Geo g, FftPlanDev fp, const typen
 // n real rows as n/2 complex lines (two rows each), FFT along x, split into
 // the two half spectra kx = 0..nc, FFT of the nc + 1 columns along y, keep
 // |ky| <= nc; output spec2[z][kx][ky] (plane-major).
-template <typename R>
+template <typename R, bool CR = false>
 __global__ void __launch_bounds__(512) k_fft_xy(Geo g, FftPlanDev fp, const R* __restrict__ grid,
                                                const typename Cx<R>::T* __restrict__ twg,
                                                typename Cx<R>::T* __restrict__ spec2) {
@@ -1158,7 +1158,7 @@ __global__ void __launch_bounds__(512) k_fft_xy(Geo g, FftPlanDev fp, const R* _
         L0[c * ls + swz<C>(x)] = v;
     }
     __syncthreads();
-    C* X = fft_lines<R, false>(L0, L1, tw, fp, h, ls);
+    C* X = fft_lines<R, false, CR>(L0, L1, tw, fp, h, ls);
     C* P = X == L0 ? L1 : L0;   // [nc+1][ls] columns over y, then scratch
     C* S = P + nc1 * ls;        // 2 (nc + 1) = n/2: P and S fill the other buffer
     // split the two real transforms: A = (Z_k + conj Z_{n-k})/2, B = -i (Z_k - conj Z_{n-k})/2
@@ -1175,7 +1175,7 @@ __global__ void __launch_bounds__(512) k_fft_xy(Geo g, FftPlanDev fp, const R* _
         P[k * ls + swz<C>(2 * c + 1)] = B;
     }
     __syncthreads();
-    C* Y = fft_lines<R, false>(P, S, tw, fp, nc1, ls);
+    C* Y = fft_lines<R, false, CR>(P, S, tw, fp, nc1, ls);
     C* out = spec2 + (size_t)z * nc1 * K;
     for (int idx = threadIdx.x; idx < nc1 * K; idx += blockDim.x) {
         const int kx = qdiv(idx, K, rK), ki = idx - kx * K;
@@ -1188,7 +1188,7 @@ __global__ void __launch_bounds__(512) k_fft_xy(Geo g, FftPlanDev fp, const R* _
 // grids): the plane spec3[a][z][kx][ky], zero-padded to n along y, inverse
 // FFT of the nc + 1 columns, then two Hermitian rows per complex line
 // (C2R) inverse along x; output h[a][z][y][x].
-template <typename R>
+template <typename R, bool CR = false>
 __global__ void __launch_bounds__(512) k_fft_yx(Geo g, FftPlanDev fp, const typename Cx<R>::T* __restrict__ spec3,
                                                const typename Cx<R>::T* __restrict__ twg, R* __restrict__ h) {
     pdl_enter();
@@ -1215,7 +1215,7 @@ __global__ void __launch_bounds__(512) k_fft_yx(Geo g, FftPlanDev fp, const type
         P[kx * ls + swz<C>(m)] = v;
     }
     __syncthreads();
-    C* Yc = fft_lines<R, true>(P, S, tw, fp, nc1, ls);   // [kx][y], in L0
+    C* Yc = fft_lines<R, true, CR>(P, S, tw, fp, nc1, ls);   // [kx][y], in L0
     // x lines: row pair (2c, 2c+1) as A + i B with the Hermitian extension
     for (int idx = threadIdx.x; idx < hn * n; idx += blockDim.x) {
         const int c = qdiv(idx, n, rn), m = idx - c * n;
@@ -1239,7 +1239,7 @@ __global__ void __launch_bounds__(512) k_fft_yx(Geo g, FftPlanDev fp, const type
         L1[c * ls + swz<C>(m)] = zz;
     }
     __syncthreads();
-    C* Xr = fft_lines<R, true>(L1, L0, tw, fp, hn, ls);
+    C* Xr = fft_lines<R, true, CR>(L1, L0, tw, fp, hn, ls);
     R* out = h + (size_t)az * n * n;
     for (int idx = threadIdx.x; idx < hn * n; idx += blockDim.x) {
         const int c = qdiv(idx, n, rn), x = idx - c * n;
@@ -1250,7 +1250,7 @@ __global__ void __launch_bounds__(512) k_fft_yx(Geo g, FftPlanDev fp, const type
 }
 
 // inverse pass along y for lines (a, z, kx): K inputs zero-padded to n; output spec4[a][z][y][kx]
-template <typename R>
+template <typename R, bool CR = false>
 __global__ void __launch_bounds__(256) k_fft_iy(Geo g, FftPlanDev fp, const typename Cx<R>::T* __restrict__ spec3,
                                                const typename Cx<R>::T* __restrict__ twg,
                                                typename Cx<R>::T* __restrict__ spec4, int LB) {
@@ -1279,7 +1279,7 @@ __global__ void __launch_bounds__(256) k_fft_iy(Geo g, FftPlanDev fp, const type
         b0[c * ls + swz<C>(m)] = v;
     }
     __syncthreads();
-    C* res = fft_lines<R, true>(b0, b1, tw, fp, nl, ls);
+    C* res = fft_lines<R, true, CR>(b0, b1, tw, fp, nl, ls);
     for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
         const int y = qdiv(idx, nl, rnl), c = idx - y * nl;
         const int l = l0 + c;
@@ -1289,7 +1289,7 @@ __global__ void __launch_bounds__(256) k_fft_iy(Geo g, FftPlanDev fp, const type
 }
 
 // inverse pass along x (C2R, two Hermitian rows per complex line); output h[a][z][y][x]
-template <typename R>
+template <typename R, bool CR = false>
 __global__ void __launch_bounds__(256) k_fft_ix(Geo g, FftPlanDev fp, const typename Cx<R>::T* __restrict__ spec4,
                                                const typename Cx<R>::T* __restrict__ twg,
                                                R* __restrict__ h, int LP) {
@@ -1331,7 +1331,7 @@ __global__ void __launch_bounds__(256) k_fft_ix(Geo g, FftPlanDev fp, const type
         b0[c * ls + swz<C>(m)] = z;
     }
     __syncthreads();
-    C* res = fft_lines<R, true>(b0, b1, tw, fp, nl, ls);
+    C* res = fft_lines<R, true, CR>(b0, b1, tw, fp, nl, ls);
     for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
         const int c = qdiv(idx, n, rn), x = idx - c * n;
         const C v = res[c * ls + swz<C>(x)];

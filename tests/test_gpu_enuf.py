@@ -95,6 +95,10 @@ CASES = {
                       (1500, 12.0, 300)),
     "tile24_M24_p5": (dict(L=14.0, alpha=1.0, r_cut=3.0, beta=2.0, kappa=1.0, M=24, p=5, tile=24),
                       (2000, 14.0, 400)),
+    # grids from n = 128 on: FP32 plans with the composite radices 16, 20, 12
+    "radix16_M64_p4": (dict(L=20.0, alpha=1.0, r_cut=3.0, beta=4.0, kappa=1.0, M=64, p=4), (2000, 20.0, 400)),
+    "radix20_M80_p3": (dict(L=24.0, alpha=1.0, r_cut=3.0, beta=4.0, kappa=1.0, M=80, p=3), (2500, 24.0, 400)),
+    "radix12_M96_p4": (dict(L=24.0, alpha=1.0, r_cut=3.0, beta=0.0, kappa=1.0, M=96, p=4), (2500, 24.0, 400)),
 }
 
 
@@ -118,6 +122,21 @@ def test_energy_forces_parity(enuf, name, prec):
     # uncharged beads get exactly zero force
     assert np.all(F[q == 0] == 0.0)
     plan.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_fft_stage_plans(enuf, prec):
+    """The line transforms' radix plans: 2, 3, 4, 5, 8 (greedy order), and
+    in FP32 from n = 128 on the two-stage plans with the composite radices."""
+    want = {16: [8, 2], 32: [8, 4], 96: [8, 4, 3], 128: [8, 8, 2], 160: [8, 5, 4], 192: [8, 8, 3]}
+    if prec == "fp32":
+        want.update({128: [16, 8], 160: [20, 8], 192: [16, 12]})
+    for n, rad in want.items():
+        plan = enuf.Plan(enuf.make_params(prec=prec, L=2.0 * n, alpha=1.0, r_cut=3.0, beta=0.0, kappa=1.0,
+                                          M=n // 2, p=4), 16)
+        info = plan.info
+        assert list(info.fft_radix[:info.fft_stages]) == rad, (n, list(info.fft_radix[:info.fft_stages]))
+        plan.close()
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
