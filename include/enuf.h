@@ -221,6 +221,13 @@ enuf_status dpd_get_state(dpd_system_t sys, void* pos, void* vel, void* F, uint6
 enuf_status dpd_set_state(dpd_system_t sys, const void* pos, const void* vel, const void* F, uint64_t step);
 /* Current total force (HOST real[n][3]). */
 enuf_status dpd_get_forces(dpd_system_t sys, void* F);
+/* Host-state step: copies pos, vel, F (HOST real[n][3]; pinned memory lets the
+ * copies run at full speed; a NULL array keeps the device copy) to the device,
+ * advances nsteps steps (step counter unchanged by the upload), copies the new
+ * pos, vel and F back into the same arrays and synchronises once. E as in
+ * dpd_step (may be NULL). Equivalent to dpd_set_state(pos, vel, F, step) +
+ * dpd_step + dpd_get_state with one host synchronisation instead of three. */
+enuf_status dpd_step_host(dpd_system_t sys, int nsteps, void* pos, void* vel, void* F, double* E);
 /* Device pointers of the resident state (real[n][3] each; owned by the system). */
 enuf_status dpd_device_state(dpd_system_t sys, void** pos, void** vel, void** F);
 void dpd_destroy(dpd_system_t sys);

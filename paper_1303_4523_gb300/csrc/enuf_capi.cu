@@ -1011,6 +1011,29 @@ enuf_status dpd_set_state(dpd_system_t sys, const void* pos, const void* vel, co
 
 enuf_status dpd_get_forces(dpd_system_t sys, void* F) { return dpd_get_state(sys, nullptr, nullptr, F, nullptr); }
 
+enuf_status dpd_step_host(dpd_system_t sys, int nsteps, void* pos, void* vel, void* F, double* E) {
+    if (!sys) return ENUF_ERR_INVALID;
+    enuf_plan_t plan = sys->plan;
+    if (nsteps < 0) return fail(plan, ENUF_ERR_INVALID, "nsteps < 0");
+    if (!sys->gstep || sys->g_timing != plan->ev.on) {
+        enuf_status st = capture_step(sys);
+        if (st != ENUF_OK) return st;
+    }
+    const size_t b = (size_t)sys->d.N * 3 * plan->rsz;
+    if (pos) CU(cudaMemcpyAsync(sys->d.pos, pos, b, cudaMemcpyHostToDevice, plan->stream));
+    if (vel) CU(cudaMemcpyAsync(sys->d.vel, vel, b, cudaMemcpyHostToDevice, plan->stream));
+    if (F) CU(cudaMemcpyAsync(sys->d.F, F, b, cudaMemcpyHostToDevice, plan->stream));
+    for (int s = 0; s < nsteps; ++s) CU(cudaGraphLaunch(sys->gstep, plan->stream));
+    sys->step += (uint64_t)nsteps;
+    if (pos) CU(cudaMemcpyAsync(pos, sys->d.pos, b, cudaMemcpyDeviceToHost, plan->stream));
+    if (vel) CU(cudaMemcpyAsync(vel, sys->d.vel, b, cudaMemcpyDeviceToHost, plan->stream));
+    if (F) CU(cudaMemcpyAsync(F, sys->d.F, b, cudaMemcpyDeviceToHost, plan->stream));
+    CU(cudaStreamSynchronize(plan->stream));
+    if (E)
+        for (int i = 0; i < 8; ++i) E[i] = plan->hE[i];
+    return ENUF_OK;
+}
+
 enuf_status dpd_device_state(dpd_system_t sys, void** pos, void** vel, void** F) {
     if (!sys) return ENUF_ERR_INVALID;
     if (pos) *pos = sys->d.pos;

@@ -76,6 +76,7 @@ def _load():
         "dpd_get_state": (st, [vp, vp, vp, vp, C.POINTER(C.c_uint64)]),
         "dpd_set_state": (st, [vp, vp, vp, vp, C.c_uint64]),
         "dpd_get_forces": (st, [vp, vp]),
+        "dpd_step_host": (st, [vp, C.c_int, vp, vp, vp, C.POINTER(C.c_double)]),
         "dpd_device_state": (st, [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp)]),
         "dpd_destroy": (None, [vp]),
         "enuf_batch_plan": (st, [i, C.POINTER(enuf_params), C.POINTER(C.c_int), vp, C.POINTER(vp)]),
@@ -97,7 +98,7 @@ EXPORTED = ("enuf_plan", "enuf_footprint", "enuf_get_info", "enuf_energy_forces"
             "enuf_energy_forces_host", "enuf_debug_buffer", "enuf_enable_timing",
             "enuf_stage_time", "enuf_launches_per_eval", "enuf_destroy", "enuf_status_string",
             "enuf_last_error", "dpd_create", "dpd_step", "dpd_get_state", "dpd_set_state",
-            "dpd_get_forces", "dpd_device_state", "dpd_destroy", "enuf_batch_plan",
+            "dpd_get_forces", "dpd_step_host", "dpd_device_state", "dpd_destroy", "enuf_batch_plan",
             "enuf_batch_energy_forces", "enuf_batch_launches", "enuf_batch_destroy",
             "enuf_spread_noalloc")
 
@@ -302,6 +303,14 @@ class DpdSystem:
         p, v, f = C.c_void_p(), C.c_void_p(), C.c_void_p()
         _check(lib.dpd_device_state(self.h, C.byref(p), C.byref(v), C.byref(f)), self.plan.h)
         return p.value, v.value, f.value
+
+    def step_host(self, pos, vel, F, nsteps=1, want_energy=False):
+        """Upload the HOST state (arrays of the plan's dtype, pinned tensors or numpy),
+        advance nsteps, copy the new state back into the same arrays; one host
+        synchronisation. Returns the energies (as step) or None."""
+        E = (C.c_double * 8)() if want_energy else None
+        _check(lib.dpd_step_host(self.h, int(nsteps), _ptr(pos), _ptr(vel), _ptr(F), E), self.plan.h)
+        return np.array(E[:]) if want_energy else None
 
     def get_state_into(self, pos=None, vel=None, F=None):
         """Copy state into caller-provided HOST buffers; returns the step."""

@@ -106,6 +106,36 @@ def test_restart_resumes_exactly(enuf):
     plan.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_step_host_equals_set_step_get(enuf, prec):
+    """dpd_step_host (upload, steps, download, one synchronisation) gives the
+    state and energies of set_state + step + get_state (to rounding: the bead
+    order inside a binning tile follows shared-memory atomics)."""
+    s = _system()
+    dp = W.dpd_params(5)
+    pos, vel, q = _prep(prec, s)
+    plan, sysm, _, _ = _make(enuf, prec, s, pos, vel, q, dp)
+    sysm.step(3)
+    p0, v0, F0, st0 = sysm.get_state()
+    Ea = sysm.step(2, want_energy=True)
+    pa, va, Fa, sa = sysm.get_state()
+    sysm.set_state(p0, v0, F0, st0)
+    pb, vb, Fb = p0.copy(), v0.copy(), F0.copy()
+    Eb = sysm.step_host(pb, vb, Fb, 2, want_energy=True)
+    assert sysm.get_state()[3] == sa == st0 + 2
+    rt = 1e-5 if prec == "fp32" else 1e-11
+    assert np.allclose(pa, pb, rtol=rt, atol=rt) and np.allclose(va, vb, rtol=rt, atol=rt)
+    assert _rel(Fb, Fa) < rt
+    assert np.allclose(Ea, Eb, rtol=rt, atol=rt * np.abs(Ea).max())
+    # NULL arrays keep the device copies and are not written back
+    pc = pb.copy()
+    sysm.step_host(pc, None, None, 1)
+    pd, _, _, _ = sysm.get_state()
+    assert np.array_equal(pc, pd)
+    sysm.close()
+    plan.close()
+
+
 def test_bad_inputs_are_rejected(enuf):
     s = _system()
     dp = W.dpd_params(5)
