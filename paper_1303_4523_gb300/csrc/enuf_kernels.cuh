@@ -1525,8 +1525,9 @@ __device__ __forceinline__ void real_pair(R r2, R al, R c2a, R be, bool slater, 
 // One lane per queued pair (lanes < m).
 // FP64 evaluates each pair once (Newton's third law: +f for bead i in the
 // lane, -f to bead j, original index from its sorted slot, atomically): the
-// erfc/exp run on the FP64 units and halving them pays for the atomics. FP32
-// evaluates both directions (each bead only adds into its own force).
+// pair arithmetic runs on the few FP64 units and halving it pays for the
+// atomics. FP32 evaluates both directions (each bead only adds into its own
+// force), measured faster there.
 template <typename R> __host__ __device__ constexpr bool real_half() { return sizeof(R) == 8; }
 
 template <typename R, typename V>
@@ -1728,8 +1729,8 @@ __device__ __forceinline__ void real_beads(const Geo& g, int c0, int c1, int sel
 // Eq. 27-28). One CTA per grid tile: the beads of the tiles within r_c (the
 // stencil) are staged in shared memory with coalesced loads; one warp per
 // bead of the central tile runs over the staged candidates; accepted pairs
-// are compacted in a per-warp queue so the erfc/exp arithmetic runs on full
-// warps.
+// are compacted in a per-warp queue so the pair arithmetic (erfc and exp in
+// FP32, the tabulated kernel in FP64) runs on full warps.
 template <typename R>
 __global__ void __launch_bounds__(kRealThreads) k_real(Geo g, const int* __restrict__ tstart,
                                                        const typename V4<R>::T* __restrict__ sq,
