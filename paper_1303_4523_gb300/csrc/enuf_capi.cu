@@ -917,7 +917,15 @@ enuf_status dpd_create(enuf_plan_t plan, const dpd_params* params, int n, const 
     d.r0_bond = params->r0_bond;
     d.seed = params->seed;
     d.rdt = 1.0 / std::sqrt(params->dt);
+    // cell blocks of B^3 cells: the largest B <= 4 (and <= ncd - 2, so the
+    // (B + 2)^3 halo holds distinct cells) whose mean halo population stays
+    // below 85% of the staging capacity (density 3: B = 4; density 4: B = 3)
     d.B = std::max(1, std::min(4, d.ncd - 2));
+    {
+        const double cell = L / d.ncd;
+        const double per_cell = (double)n / (L * L * L) * cell * cell * cell;
+        while (d.B > 1 && (d.B + 2) * (d.B + 2) * (d.B + 2) * per_cell > 0.85 * kDpdCap) --d.B;
+    }
     d.cinv = (double)d.ncd / L;
     d.xmaxf = largest_float_below(L);
     const size_t rs = plan->rsz;

@@ -44,6 +44,10 @@ struct Geo {
     const void* ktab;  // real [kn][kKtStride]: quintic coefficients of J(r) = r u(r) per interval
 };
 
+// Beads of one DPD cell block plus its halo that the pair kernel stages in
+// shared memory (blocks with more take the unstaged path).
+constexpr int kDpdCap = 896;
+
 // Row length of the real-space kernel table (16-byte aligned rows).
 constexpr int kKtStride64 = 6;   // c_0..c_5 in double
 constexpr int kKtStride32 = 8;   // c_0..c_5 in float, 2 padding

@@ -1940,7 +1940,8 @@ __device__ __forceinline__ R dpd_theta(uint64_t seed, uint64_t step, int i, int 
 // around 1 (and near 0) that covers the float error, so the decision is the
 // double one.
 constexpr int kDpdThreads = 256;
-constexpr int kDpdCap = 896;     // staged beads
+// kDpdCap (staged beads per block) is in enuf_internal.h: the host sizes the
+// cell blocks against it
 constexpr int kDpdMaxB = 4;      // cells per block edge
 constexpr int kDpdSegU = 14;     // unstaged half shell: single cells
 

@@ -224,3 +224,75 @@ def dpd_params(ntypes: int, seed: int = 1303, **over) -> dict:
     ps["a"] = a
     ps["seed"] = seed
     return ps
+
+
+# Table 1 DPD parameters of the paper's own runs (density 4, R_c = 7.829 A):
+# a_ii = 78.67, a_ij = a_ii + 2.05 chi with chi = 0.87 between the
+# polyelectrolyte and the solvent, gamma = 6.74, sigma = 3.67, dt = 0.02,
+# lambda = 0.65, harmonic bonds K^S = 64 about r_eq = 0.7 (Sec. 5).
+PAPER_DPD = dict(a_ii=78.67, chi=0.87, gamma=6.74, sigma=3.67, dt=0.02, lambda_vv=0.65,
+                 K_bond=64.0, r0_bond=0.7)
+
+
+def paper_dpd_params(seed: int = 1303) -> dict:
+    """DPD parameters of Table 1 for bead types 0 solvent, 1 monomer, 2
+    counterion, 3 salt cation, 4 salt anion: every pair a_ii except monomer
+    with any other type, a_ii + 2.05 chi."""
+    p = PAPER_DPD
+    a = np.full((5, 5), p["a_ii"])
+    a_ps = p["a_ii"] + 2.05 * p["chi"]
+    for t in (0, 2, 3, 4):
+        a[1, t] = a[t, 1] = a_ps
+    return dict(a=a, gamma=p["gamma"], sigma=p["sigma"], dt=p["dt"], lambda_vv=p["lambda_vv"],
+                K_bond=p["K_bond"], r0_bond=p["r0_bond"], seed=seed)
+
+
+def single_polyelectrolyte(f: float, L: float = 30.0, density: float = 4.0, n_p: int = 48,
+                           seed_offset: int = 60) -> System:
+    """Table 3 set 5 (Sec. 5): one chain of n_p beads (random walk with the bond
+    length r_eq = 0.7), round(f n_p) of them evenly spaced with q = -1, as many
+    +1 counterions, the rest neutral solvent (N = density L^3). Bead types:
+    0 solvent, 1 monomer, 2 counterion. Paper parameter set for the
+    electrostatics, M from the grid rule."""
+    rng = _rng(seed_offset)
+    N = int(round(density * L ** 3))
+    nq = int(round(f * n_p))
+    pos = np.empty((N, 3))
+    q = np.zeros(N)
+    types = np.zeros(N, dtype=np.int32)
+    start = rng.uniform(0.0, L, size=3)
+    for m in range(n_p):
+        if m == 0:
+            pos[0] = start
+        else:
+            d = rng.normal(size=3)
+            pos[m] = pos[m - 1] + PAPER_DPD["r0_bond"] * d / np.linalg.norm(d)
+        types[m] = 1
+    for k in range(nq):
+        q[(k * n_p + n_p // 2) // nq if nq else 0] = -1.0
+    pos[n_p:n_p + nq] = rng.uniform(0.0, L, size=(nq, 3))
+    q[n_p:n_p + nq] = 1.0
+    types[n_p:n_p + nq] = 2
+    pos[n_p + nq:] = rng.uniform(0.0, L, size=(N - n_p - nq, 3))
+    pos = np.mod(pos, L)
+    bonds = np.array([(m - 1, m) for m in range(1, n_p)], dtype=np.int32).reshape(-1, 2)
+    return System(name=f"single polyelectrolyte N={N} L={L:g} N_p={n_p} f={f}", L=float(L), pos=pos,
+                  vel=_velocities(rng, N), q=q, types=types, bonds=bonds, M=grid_rule(L),
+                  params=dict(PAPER_SET))
+
+
+def electrolyte_rdf_system(L: float = 10.0, density: float = 4.0, n_ions: int = 132,
+                           seed_offset: int = 61) -> System:
+    """Table 3 set 3: N = density L^3 beads (4000 at L = 10), n_ions cations
+    (+1, type 3), n_ions anions (-1, type 4), the rest neutral (type 0), all
+    uniform; paper parameter set, M from the grid rule."""
+    rng = _rng(seed_offset)
+    N = int(round(density * L ** 3))
+    pos = rng.uniform(0.0, L, size=(N, 3))
+    q = np.zeros(N)
+    types = np.zeros(N, dtype=np.int32)
+    q[:n_ions], types[:n_ions] = 1.0, 3
+    q[n_ions:2 * n_ions], types[n_ions:2 * n_ions] = -1.0, 4
+    return System(name=f"electrolyte N={N} L={L:g} ions={n_ions}+{n_ions}", L=float(L), pos=pos,
+                  vel=_velocities(rng, N), q=q, types=types, bonds=np.zeros((0, 2), np.int32),
+                  M=grid_rule(L), params=dict(PAPER_SET))

@@ -60,6 +60,23 @@ def test_initial_force_parity(enuf, prec, tol):
     plan.close()
 
 
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 1e-5)])
+def test_density4_force_parity(enuf, prec, tol):
+    """The paper's density 4 (Table 1): the cell blocks shrink to 3^3 so their
+    halos stay within the staging capacity; forces against the oracle."""
+    s = W.polyelectrolyte(L=10.0, density=4.0, n_chains=2, chain_len=48, f=1.0, salt_fraction=0.05,
+                          seed_offset=44)
+    dp = W.dpd_params(5)
+    pos, vel, q = _prep(prec, s)
+    plan, sysm, Po, Do = _make(enuf, prec, s, pos, vel, q, dp)
+    _, _, F, _ = sysm.get_state()
+    Fr, _ = orc.total_forces(Po, Do, pos, vel, s.types, q, s.bonds, step=0)
+    assert _rel(F.astype(np.float64), Fr) < tol
+    sysm.step(2)
+    sysm.close()
+    plan.close()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_trajectory_parity(enuf, prec):
     """Three modified velocity-Verlet steps; positions, velocities, forces and
