@@ -234,7 +234,6 @@ cudaError_t enqueue_enuf(const Geo& g, const FftShape& fs, const FftPlanDev& fp,
     R* F = static_cast<R*>(a.F);
     V* sq = static_cast<V*>(w.sq);
     V* sw = static_cast<V*>(w.sw);
-    C* tw = static_cast<C*>(w.tw);
     const bool pdl = pdl_ok(ev);
     rec(ev, 0, true, s0);
     enqueue_bin<R>(g, w, a.N, pos, q, a.zeroF ? F : nullptr, s0, pdl);

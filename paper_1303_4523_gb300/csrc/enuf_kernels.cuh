@@ -1751,10 +1751,6 @@ __global__ void __launch_bounds__(kRealThreads) k_real(Geo g, const int* __restr
     __shared__ int wtot[NW];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     V* qu = queue + warp * 64;
-    const R L = (R)g.L, hL = (R)(0.5 * g.L);
-    const R rc2 = (R)(g.rc * g.rc);
-    const R al = (R)g.alpha, c2a = (R)g.c2a, be = (R)g.beta, kap = (R)g.kappa;
-    const bool slater = g.beta > 0.0;
     R eacc = 0, wacc = 0;
     for (int tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x) {
         const int tx = tile % g.ntd, ty = (tile / g.ntd) % g.ntd, tz = tile / (g.ntd * g.ntd);
