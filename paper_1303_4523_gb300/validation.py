@@ -3,12 +3,15 @@ systems, not parity): the mean radius of gyration of a single polyelectrolyte
 against its charge fraction f (Table 3 set 5; the paper finds the fully
 ionised chain ~1.31 times larger than the neutral one) and the radial
 distribution functions of an electrolyte (Table 3 set 3; the paper observes
-g_+-(r) g_++/--(r) = g_00(r)^2).
+g_+-(r) g_++/--(r) = g_00(r)^2), and the chain's <Rg> under added Z:1 salt
+(Table 3 set 6; the paper finds the chain contracting, most with trivalent
+counterions, smallest near the neutralising ratio theta = 1).
 
 The trajectories come from DpdSystem (the CUDA step); the analysis is plain
 numpy on the host, on positions copied back every `every` steps.
 
     python -m paper_1303_4523_gb300.validation rg --f 0 1 --equil 50000 --steps 250000
+    python -m paper_1303_4523_gb300.validation rg --f 1 --theta 0.5 1 --valency 3
     python -m paper_1303_4523_gb300.validation rdf --equil 10000 --steps 200000
 """
 from __future__ import annotations
@@ -102,14 +105,16 @@ def _system(enuf, s, prec, kappa, seed):
 
 
 def run_polyelectrolyte(f: float, steps: int, equil: int, every: int = 100, prec: str = "fp32",
-                        kappa: float | None = None, seed: int = 1303, n_p: int = 48) -> dict:
+                        kappa: float | None = None, seed: int = 1303, n_p: int = 48, theta: float = 0.0,
+                        valency: int = 1) -> dict:
     """Table 3 set 5: one chain of n_p beads with charge fraction f in N =
     108000 beads (L = 30, density 4), Table 1 DPD parameters, the paper's
-    electrostatic set (kappa overrides its coupling). equil steps, then
-    `steps` steps sampled every `every`: <Rg> with its block standard error,
-    the mean bond length and kT from the kinetic energy."""
+    electrostatic set (kappa overrides its coupling); set 6: added Z:1 salt
+    at charge ratio theta. equil steps, then `steps` steps sampled every
+    `every`: <Rg> with its block standard error, the mean bond length and kT
+    from the kinetic energy."""
     from . import enuf
-    s = W.single_polyelectrolyte(f, n_p=n_p)
+    s = W.single_polyelectrolyte(f, n_p=n_p, theta=theta, valency=valency)
     plan, sysm, P = _system(enuf, s, prec, kappa, seed)
     sysm.step(equil)
     pos = np.empty((s.N, 3), plan.dtype_np)
@@ -128,7 +133,8 @@ def run_polyelectrolyte(f: float, steps: int, equil: int, every: int = 100, prec
     done = max(1, steps // every) * every
     sysm.close()
     plan.close()
-    return {"run": "rg", "f": f, "n_p": n_p, "N": s.N, "L": s.L, "prec": prec, "kappa": P["kappa"],
+    return {"run": "rg", "f": f, "theta": theta, "valency": valency, "n_p": n_p, "N": s.N, "L": s.L,
+            "prec": prec, "kappa": P["kappa"],
             "equil": equil, "steps": done, "every": every, "rg_mean": float(np.mean(rg)),
             "rg_sem": block_sem(np.array(rg)), "bond_mean": float(np.mean(bond)),
             "kT": float(2.0 * np.mean(kin) / (3.0 * s.N)), "ms_per_step": 1000.0 * wall / done}
@@ -181,6 +187,8 @@ def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("run", choices=["rg", "rdf"])
     ap.add_argument("--f", type=float, nargs="*", default=[0.0, 1.0], help="charge fractions (rg)")
+    ap.add_argument("--theta", type=float, nargs="*", default=[0.0], help="added-salt charge ratios (rg)")
+    ap.add_argument("--valency", type=int, default=1, help="salt cation valency (rg)")
     ap.add_argument("--steps", type=int, default=250000)
     ap.add_argument("--equil", type=int, default=50000)
     ap.add_argument("--every", type=int, default=100)
@@ -189,7 +197,9 @@ def main(argv=None):
     a = ap.parse_args(argv)
     if a.run == "rg":
         for f in a.f:
-            print(json.dumps(run_polyelectrolyte(f, a.steps, a.equil, a.every, a.prec, a.kappa)), flush=True)
+            for th in a.theta:
+                print(json.dumps(run_polyelectrolyte(f, a.steps, a.equil, a.every, a.prec, a.kappa, theta=th,
+                                                     valency=a.valency)), flush=True)
     else:
         print(json.dumps(run_electrolyte_rdf(a.steps, a.equil, max(a.every, 200), a.prec, a.kappa)), flush=True)
 

@@ -248,12 +248,14 @@ def paper_dpd_params(seed: int = 1303) -> dict:
 
 
 def single_polyelectrolyte(f: float, L: float = 30.0, density: float = 4.0, n_p: int = 48,
-                           seed_offset: int = 60) -> System:
+                           seed_offset: int = 60, theta: float = 0.0, valency: int = 1) -> System:
     """Table 3 set 5 (Sec. 5): one chain of n_p beads (random walk with the bond
     length r_eq = 0.7), round(f n_p) of them evenly spaced with q = -1, as many
-    +1 counterions, the rest neutral solvent (N = density L^3). Bead types:
-    0 solvent, 1 monomer, 2 counterion. Paper parameter set for the
-    electrostatics, M from the grid rule."""
+    +1 counterions, the rest neutral solvent (N = density L^3). Set 6: added
+    Z:1 salt whose cations (+valency) carry theta times the chain's charge,
+    round(theta f n_p / valency) of them, with theta f n_p anions (-1).
+    Bead types: 0 solvent, 1 monomer, 2 counterion, 3 salt cation, 4 salt
+    anion. Paper parameter set for the electrostatics, M from the grid rule."""
     rng = _rng(seed_offset)
     N = int(round(density * L ** 3))
     nq = int(round(f * n_p))
@@ -273,11 +275,15 @@ def single_polyelectrolyte(f: float, L: float = 30.0, density: float = 4.0, n_p:
     pos[n_p:n_p + nq] = rng.uniform(0.0, L, size=(nq, 3))
     q[n_p:n_p + nq] = 1.0
     types[n_p:n_p + nq] = 2
+    k = n_p + nq
+    n_cat, n_an = int(round(theta * nq / valency)), int(round(theta * nq))
+    q[k:k + n_cat], types[k:k + n_cat] = float(valency), 3
+    q[k + n_cat:k + n_cat + n_an], types[k + n_cat:k + n_cat + n_an] = -1.0, 4
     pos[n_p + nq:] = rng.uniform(0.0, L, size=(N - n_p - nq, 3))
     pos = np.mod(pos, L)
     bonds = np.array([(m - 1, m) for m in range(1, n_p)], dtype=np.int32).reshape(-1, 2)
-    return System(name=f"single polyelectrolyte N={N} L={L:g} N_p={n_p} f={f}", L=float(L), pos=pos,
-                  vel=_velocities(rng, N), q=q, types=types, bonds=bonds, M=grid_rule(L),
+    return System(name=f"single polyelectrolyte N={N} L={L:g} N_p={n_p} f={f} salt theta={theta} z={valency}",
+                  L=float(L), pos=pos, vel=_velocities(rng, N), q=q, types=types, bonds=bonds, M=grid_rule(L),
                   params=dict(PAPER_SET))
 
 

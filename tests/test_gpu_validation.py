@@ -14,10 +14,10 @@ def built():
     build.build()
 
 
-@pytest.mark.parametrize("f", [0.0, 1.0])
-def test_single_polyelectrolyte_run(built, f):
+@pytest.mark.parametrize("f,theta,valency", [(0.0, 0.0, 1), (1.0, 0.0, 1), (1.0, 1.0, 3)])
+def test_single_polyelectrolyte_run(built, f, theta, valency):
     from paper_1303_4523_gb300 import validation as V
-    out = V.run_polyelectrolyte(f, steps=400, equil=400, every=100)
+    out = V.run_polyelectrolyte(f, steps=400, equil=400, every=100, theta=theta, valency=valency)
     assert out["N"] == 108000 and out["steps"] == 400
     assert abs(out["kT"] - 1.0) < 0.05                  # DPD thermostat at kT = 1
     assert 0.6 < out["bond_mean"] < 0.9                 # harmonic bonds about r_eq = 0.7
