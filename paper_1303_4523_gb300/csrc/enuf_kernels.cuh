@@ -1923,10 +1923,12 @@ __device__ __forceinline__ R dpd_theta(uint64_t seed, uint64_t step, int i, int 
 // Each lane takes one candidate j and loops over the cell's beads i; accepted
 // pairs go to a per-warp queue kept across the warp's cells, and the pair arithmetic
 // (Philox draw, weights, dissipation) runs on full warps. -f goes to j with
-// one shared-memory atomic per pair; the +f of a run of pairs with the same
-// i is summed in the warp first (queue runs are contiguous in i), then added
-// once. The staged force array is added to F once per block. The harmonic
-// bonds run as one thread per bond into F.
+// one global reduction per component and pair (executed in L2: shared-memory
+// float adds are compare-and-swap loops on this part, and in FP64 each of
+// their iterations costs an add on the few FP64 units); the +f of a run of
+// pairs with the same i is summed in the warp first (queue runs are
+// contiguous in i), then added once. The harmonic bonds run as one thread per
+// bond into F.
 //
 // The staged copies are unwrapped: the halo cells that lie across a box
 // face are shifted by L, so the plain difference of two staged positions is
@@ -1943,14 +1945,14 @@ constexpr int kDpdSegU = 14;     // unstaged half shell: single cells
 
 template <typename R>
 constexpr int dpd_smem_bytes() {
-    return 2 * kDpdCap * (int)sizeof(typename V4<R>::T) + 3 * kDpdCap * (int)sizeof(R) +
-           (sizeof(R) == 8 ? kDpdCap * (int)sizeof(float4) : 0) + (kDpdThreads / 32) * 64 * 8;
+    return 2 * kDpdCap * (int)sizeof(typename V4<R>::T) + (sizeof(R) == 8 ? kDpdCap * (int)sizeof(float4) : 0) +
+           (kDpdThreads / 32) * 64 * 8;
 }
 
 // One warp-wide batch of up to 32 queued pairs (valid lanes), all lanes call.
 template <typename R, typename V, bool STAGED>
 __device__ __forceinline__ void dpd_pairs(const bool valid, const int2 e, const V* __restrict__ P,
-                                          const V* __restrict__ Pv, R* fh, R* __restrict__ F,
+                                          const V* __restrict__ Pv, R* __restrict__ F,
                                           const R* __restrict__ atab, int ntypes, R L, R hL, R gam, R srdt,
                                           uint64_t seed, uint64_t step, R& ec) {
     const int lane = threadIdx.x & 31;
@@ -1979,15 +1981,10 @@ __device__ __forceinline__ void dpd_pairs(const bool valid, const int2 e, const 
         fx = fm * rx;
         fy = fm * ry;
         fz = fm * rz;
-        if (STAGED) {
-            atomicAdd(&fh[3 * e.y], -fx);
-            atomicAdd(&fh[3 * e.y + 1], -fy);
-            atomicAdd(&fh[3 * e.y + 2], -fz);
-        } else {
-            atomicAdd(&F[3 * j], -fx);
-            atomicAdd(&F[3 * j + 1], -fy);
-            atomicAdd(&F[3 * j + 2], -fz);
-        }
+        // -f to bead j: a global reduction (executed in L2, no compare-and-swap loop)
+        atomicAdd(&F[3 * j], -fx);
+        atomicAdd(&F[3 * j + 1], -fy);
+        atomicAdd(&F[3 * j + 2], -fz);
         ec = fma(a * w, w, ec);   // a w^2; halved once per block
         key = e.x;
         oi = i;
@@ -2011,15 +2008,9 @@ __device__ __forceinline__ void dpd_pairs(const bool valid, const int2 e, const 
         }
     }
     if (head && key >= 0) {
-        if (STAGED) {
-            atomicAdd(&fh[3 * key], fx);
-            atomicAdd(&fh[3 * key + 1], fy);
-            atomicAdd(&fh[3 * key + 2], fz);
-        } else {
-            atomicAdd(&F[3 * oi], fx);
-            atomicAdd(&F[3 * oi + 1], fy);
-            atomicAdd(&F[3 * oi + 2], fz);
-        }
+        atomicAdd(&F[3 * oi], fx);
+        atomicAdd(&F[3 * oi + 1], fy);
+        atomicAdd(&F[3 * oi + 2], fz);
     }
 }
 
@@ -2045,7 +2036,7 @@ template <typename R, bool STAGED>
 __device__ __forceinline__ void dpd_cells(const DpdDev& d, int H, int B3, const int* chalo, const int* hoff,
                                           const int* gst, const typename V4<R>::T* __restrict__ P,
                                           const typename V4<R>::T* __restrict__ Pv, const float4* Pf,
-                                          const DpdBand band, R* fh, int2* queue, const R* __restrict__ atab,
+                                          const DpdBand band, int2* queue, const R* __restrict__ atab,
                                           uint64_t step, R* __restrict__ F, R& ec) {
     using V = typename V4<R>::T;
     constexpr int NW = kDpdThreads / 32;
@@ -2133,7 +2124,7 @@ __device__ __forceinline__ void dpd_cells(const DpdDev& d, int H, int B3, const 
                 cnt += __popc(m);
                 if (cnt >= 32) {
                     __syncwarp();
-                    dpd_pairs<R, V, STAGED>(true, queue[lane], P, Pv, fh, F, atab, d.ntypes, L, hL, gam, srdt,
+                    dpd_pairs<R, V, STAGED>(true, queue[lane], P, Pv, F, atab, d.ntypes, L, hL, gam, srdt,
                                             d.seed, step, ec);
                     __syncwarp();
                     if (lane < cnt - 32) queue[lane] = queue[32 + lane];
@@ -2145,7 +2136,7 @@ __device__ __forceinline__ void dpd_cells(const DpdDev& d, int H, int B3, const 
     }
     __syncwarp();
     if (cnt > 0)
-        dpd_pairs<R, V, STAGED>(lane < cnt, queue[lane], P, Pv, fh, F, atab, d.ntypes, L, hL, gam, srdt, d.seed,
+        dpd_pairs<R, V, STAGED>(lane < cnt, queue[lane], P, Pv, F, atab, d.ntypes, L, hL, gam, srdt, d.seed,
                                 step, ec);
 }
 
@@ -2162,8 +2153,7 @@ __global__ void __launch_bounds__(kDpdThreads, sizeof(R) == 4 ? 4 : 2)
     V* spos = reinterpret_cast<V*>(smraw);                                  // [kDpdCap]
     V* svel = spos + kDpdCap;                                               // [kDpdCap]
     float4* spf = reinterpret_cast<float4*>(svel + kDpdCap);                // [kDpdCap] (FP64 only)
-    R* fh = reinterpret_cast<R*>(spf + (F64 ? kDpdCap : 0));                // [kDpdCap][3]
-    int2* queues = reinterpret_cast<int2*>(fh + 3 * kDpdCap);               // [NW][64]
+    int2* queues = reinterpret_cast<int2*>(spf + (F64 ? kDpdCap : 0));      // [NW][64]
     constexpr int HMAX = (kDpdMaxB + 2) * (kDpdMaxB + 2) * (kDpdMaxB + 2);
     __shared__ int hoff[HMAX + 1], gst[HMAX];
     __shared__ int chalo[kDpdMaxB * kDpdMaxB * kDpdMaxB];
@@ -2282,20 +2272,12 @@ __global__ void __launch_bounds__(kDpdThreads, sizeof(R) == 4 ? 4 : 2)
                 svel[f] = sv[j];
                 if (F64) spf[f] = make_float4((float)p.x, (float)p.y, (float)p.z, 0.f);
             }
-            for (int k = tid; k < 3 * total; k += blockDim.x) fh[k] = (R)0;
         }
         __syncthreads();
         if (staged)
-            dpd_cells<R, true>(d, H, B3, chalo, hoff, gst, spos, svel, spf, band, fh, queue, atab, step, F, ec);
+            dpd_cells<R, true>(d, H, B3, chalo, hoff, gst, spos, svel, spf, band, queue, atab, step, F, ec);
         else
-            dpd_cells<R, false>(d, H, B3, chalo, hoff, gst, sp, sv, spf, band, fh, queue, atab, step, F, ec);
-        __syncthreads();
-        if (staged) {   // add the block's contributions to F
-            for (int k = tid; k < 3 * total; k += blockDim.x) {
-                const R v = fh[k];
-                if (v != (R)0) atomicAdd(&F[3 * real_as_int(spos[k / 3].w) + k % 3], v);
-            }
-        }
+            dpd_cells<R, false>(d, H, B3, chalo, hoff, gst, sp, sv, spf, band, queue, atab, step, F, ec);
         __syncthreads();
     }
     double e1 = 0.5 * (double)ec, e2 = 0.5 * (double)eb;
