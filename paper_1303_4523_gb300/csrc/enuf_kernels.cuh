@@ -1925,10 +1925,10 @@ __device__ __forceinline__ R dpd_theta(uint64_t seed, uint64_t step, int i, int 
 // (Philox draw, weights, dissipation) runs on full warps. -f goes to j with
 // one global reduction per component and pair (executed in L2: shared-memory
 // float adds are compare-and-swap loops on this part, and in FP64 each of
-// their iterations costs an add on the few FP64 units); the +f of a run of
-// pairs with the same i is summed in the warp first (queue runs are
-// contiguous in i), then added once. The harmonic bonds run as one thread per
-// bond into F.
+// their iterations costs an add on the few FP64 units); in FP32 the +f of a
+// run of pairs with the same i is summed in the warp first (queue runs are
+// contiguous in i), then added once, in FP64 it goes per pair too. The
+// harmonic bonds run as one thread per bond into F.
 //
 // The staged copies are unwrapped: the halo cells that lie across a box
 // face are shifted by L, so the plain difference of two staged positions is
@@ -1988,6 +1988,17 @@ __device__ __forceinline__ void dpd_pairs(const bool valid, const int2 e, const 
         ec = fma(a * w, w, ec);   // a w^2; halved once per block
         key = e.x;
         oi = i;
+    }
+    if constexpr (sizeof(R) == 8) {
+        // FP64: +f to bead i per pair as well (the segmented sum below would
+        // run its adds and double shuffles on the few FP64 units)
+        if (key >= 0) {
+            atomicAdd(&F[3 * oi], fx);
+            atomicAdd(&F[3 * oi + 1], fy);
+            atomicAdd(&F[3 * oi + 2], fz);
+        }
+        (void)lane;
+        return;
     }
     // runs of equal i: sum each run into its first lane (segmented suffix sums)
     const int prev = __shfl_up_sync(0xffffffffu, key, 1);
