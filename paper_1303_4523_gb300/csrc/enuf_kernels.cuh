@@ -1427,6 +1427,13 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Geo g, const int* __r
                 az = fma(wab, s2, az);
             }
         }
+        if constexpr (sizeof(R) == 8) {   // each lane's share as a global reduction (a warp
+            const int i = real_as_int(wv.w);   // sum would run 15 adds on the FP64 units)
+            const R f = pref * qs;
+            atomicAdd(&F[3 * i], f * ax);
+            atomicAdd(&F[3 * i + 1], f * ay);
+            atomicAdd(&F[3 * i + 2], f * az);
+        } else {
         ax = warp_sum_r(ax);
         ay = warp_sum_r(ay);
         az = warp_sum_r(az);
@@ -1436,6 +1443,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Geo g, const int* __r
             F[3 * i] += f * ax;
             F[3 * i + 1] += f * ay;
             F[3 * i + 2] += f * az;
+        }
         }
         __syncwarp();
     }
@@ -1707,6 +1715,12 @@ __device__ __forceinline__ void real_beads(const Geo& g, int c0, int c1, int sel
                 cnt -= m;
             }
         }
+        if constexpr (sizeof(R) == 8) {   // each lane's share as a global reduction: a warp
+            const int i = real_as_int(sw[s].w);   // sum would run 15 adds on the FP64 units
+            atomicAdd(&F[3 * i], fx);
+            atomicAdd(&F[3 * i + 1], fy);
+            atomicAdd(&F[3 * i + 2], fz);
+        } else {
         fx = warp_sum_r(fx);
         fy = warp_sum_r(fy);
         fz = warp_sum_r(fz);
@@ -1721,6 +1735,7 @@ __device__ __forceinline__ void real_beads(const Geo& g, int c0, int c1, int sel
                 F[3 * i + 1] += fy;
                 F[3 * i + 2] += fz;
             }
+        }
         }
     }
 }
