@@ -161,8 +161,12 @@ __device__ __forceinline__ R warp_sum_r(R v) {
 // Block sum of two doubles; result valid in thread 0. Uses 64 doubles of shared memory.
 __device__ __forceinline__ void block_sum2(double& a, double& b) {
     __shared__ double red[2][32];
-    a = warp_sum(a);
-    b = warp_sum(b);
+    // warps holding only zeros skip their shuffle tree (its adds run on the
+    // few FP64 units); the branch is uniform over the warp
+    if (__any_sync(0xffffffffu, a != 0.0 || b != 0.0)) {
+        a = warp_sum(a);
+        b = warp_sum(b);
+    }
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     __syncthreads();
     if (l == 0) { red[0][w] = a; red[1][w] = b; }
@@ -337,11 +341,7 @@ __global__ void __launch_bounds__(1024) k_bin_count(Geo g, int N, const R* __res
         int basei = 0;
         if (lane == 0 && m) basei = atomicAdd(&scount, __popc(m));
         basei = __shfl_sync(0xffffffffu, basei, 0);
-        if (charged) {
-            slist[basei + __popc(m & ((1u << lane) - 1u))] = i;
-            s1 += (double)qi;
-            s2 += (double)qi * (double)qi;
-        }
+        if (charged) slist[basei + __popc(m & ((1u << lane) - 1u))] = i;
     }
     __syncthreads();
     const int nc = scount;
@@ -359,6 +359,10 @@ __global__ void __launch_bounds__(1024) k_bin_count(Geo g, int N, const R* __res
         const int o = i0 + k;
         typename V4<R>::T a, c;
         a.x = xw[0]; a.y = xw[1]; a.z = xw[2]; a.w = q[i];
+        // charge sums over the compacted beads: only the block's first warps
+        // hold nonzero partials, the rest skip the reduction tree
+        s1 += (double)a.w;
+        s2 += (double)a.w * (double)a.w;
         c.x = fr[0]; c.y = fr[1]; c.z = fr[2]; c.w = int_as_real(i, (R)0);
         ctile[o] = tile;
         cpos[o] = a;
