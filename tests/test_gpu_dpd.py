@@ -153,6 +153,41 @@ def test_step_host_equals_set_step_get(enuf, prec):
     plan.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_step_host_with_pinned_buffers(enuf, prec):
+    """Pinned host tensors through dpd_step_host, one step at a time, match
+    pageable arrays advanced two steps from the same state; other pinned
+    tensors work the same way."""
+    s = _system()
+    dp = W.dpd_params(5)
+    pos, vel, q = _prep(prec, s)
+    plan, sysm, _, _ = _make(enuf, prec, s, pos, vel, q, dp)
+    dt = torch.float32 if prec == "fp32" else torch.float64
+    sysm.step(2)
+    p0, v0, F0, st0 = sysm.get_state()
+    # direct path (pageable arrays), two steps
+    pa, va, Fa = p0.copy(), v0.copy(), F0.copy()
+    sysm.step_host(pa, va, Fa, 2)
+    # pinned tensors, two single steps from the same state
+    sysm.set_state(p0, v0, F0, st0)
+    tp, tv, tF = (torch.from_numpy(a.copy()).pin_memory() for a in (p0, v0, F0))
+    E1 = sysm.step_host(tp, tv, tF, 1, want_energy=True)
+    sysm.step_host(tp, tv, tF, 1)
+    assert sysm.get_state()[3] == st0 + 2
+    rt = 1e-5 if prec == "fp32" else 1e-11
+    assert np.allclose(tp.numpy(), pa, rtol=rt, atol=rt) and np.allclose(tv.numpy(), va, rtol=rt, atol=rt)
+    assert _rel(tF.numpy().astype(np.float64), Fa.astype(np.float64)) < rt
+    assert np.isfinite(E1).all() and E1[6] > 0
+    # other pinned arrays
+    up, uv, uF = (t.clone().pin_memory() for t in (tp, tv, tF))
+    sysm.step_host(up, uv, uF, 1)
+    gp, _, _, st = sysm.get_state()
+    assert st == st0 + 3 and np.array_equal(up.numpy(), gp)
+    assert tp.dtype == dt
+    sysm.close()
+    plan.close()
+
+
 def test_bad_inputs_are_rejected(enuf):
     s = _system()
     dp = W.dpd_params(5)
