@@ -64,3 +64,31 @@ def test_status_strings_and_invalid_params_without_gpu():
         assert e.status == 5
     else:
         raise AssertionError("accepted n = 28")
+
+
+def test_method_switches_are_validated_without_gpu():
+    """The method switches and the tile edge are checked by the plan's host
+    logic; gradient mode holds one force field instead of three."""
+    from paper_1303_4523_gb300 import build
+    build.build()
+    from paper_1303_4523_gb300 import enuf
+    base = dict(L=30.0, alpha=0.975, r_cut=3.0, beta=4.0, kappa=1.1, M=48, p=4)
+    for bad in (dict(deriv=2), dict(slater_k=1, beta=0.0), dict(slater_k=2), dict(fft_path=2), dict(tile=7),
+                dict(tile=48), dict(tile=3)):
+        kw = dict(base)
+        kw.update(bad)
+        try:
+            enuf.enuf_footprint(enuf.make_params(**kw), 100)
+        except enuf.EnufError as e:
+            assert e.status == 1, bad
+        else:
+            raise AssertionError(f"accepted {bad}")
+    for ok in (dict(deriv=1), dict(slater_k=1), dict(fft_path=1), dict(tile=12), dict(tile=24)):
+        kw = dict(base)
+        kw.update(ok)
+        assert enuf.enuf_footprint(enuf.make_params(**kw), 100) > 0, ok
+    n3 = 96 ** 3
+    for prec, esz in (("fp64", 8), ("fp32", 4)):
+        ik = enuf.enuf_footprint(enuf.make_params(prec=prec, **base), 81000)
+        grad = enuf.enuf_footprint(enuf.make_params(prec=prec, deriv=1, **base), 81000)
+        assert ik - grad >= 2 * n3 * esz   # two real fields fewer (and their spectra)
