@@ -168,6 +168,15 @@ enuf_status enuf_enable_timing(enuf_plan_t plan, int on);
 enuf_status enuf_stage_time(enuf_plan_t plan, int stage, float* ms);
 /* Number of kernel launches one evaluation (or one DPD step) enqueues. */
 int enuf_launches_per_eval(enuf_plan_t plan);
+/* Device index checks of a library built with -DENUF_CHECK (the debug
+ * build): *mask receives the failure bits recorded since the last reset
+ * (bit k = check site k of the kernels; 0 = every check held; always 0 in a
+ * release build), after synchronising the plan's stream; reset != 0 clears
+ * them. The checks record and skip nothing else: a set bit means the result
+ * of that evaluation is not to be trusted. */
+enuf_status enuf_check_word(enuf_plan_t plan, unsigned int* mask, int reset);
+/* 1 when the library was built with the device index checks, else 0. */
+int enuf_built_with_checks(void);
 
 void enuf_destroy(enuf_plan_t plan);
 const char* enuf_status_string(enuf_status s);

@@ -2,7 +2,9 @@
 
 The three translation units (C ABI, FP32 kernels, FP64 kernels) compile in
 parallel; the shared library links the CUDA runtime statically so it loads
-next to any PyTorch build.
+next to any PyTorch build. build(check=True) makes the debug build
+libenuf_check.so (-DENUF_CHECK: device index checks that record failure
+bits, see enuf_check_word).
 """
 from __future__ import annotations
 
@@ -16,6 +18,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libenuf.so")
+BUILD_CHECK = os.path.join(HERE, "_build_check")
+LIB_CHECK = os.path.join(HERE, "libenuf_check.so")
 SOURCES = ["enuf_capi.cu", "enuf_k32.cu", "enuf_k64.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
@@ -34,14 +38,16 @@ def _stale(obj, src):
     return os.path.getmtime(obj) < max(os.path.getmtime(d) for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, check: bool = False) -> str:
+    bdir, lib = (BUILD_CHECK, LIB_CHECK) if check else (BUILD, LIB)
+    extra = ["-DENUF_CHECK"] if check else []
+    os.makedirs(bdir, exist_ok=True)
     jobs = []
     for s in SOURCES:
         src = os.path.join(CSRC, s)
-        obj = os.path.join(BUILD, s.replace(".cu", ".o"))
+        obj = os.path.join(bdir, s.replace(".cu", ".o"))
         if force or _stale(obj, src):
-            jobs.append([NVCC, *_flags(), "-c", src, "-o", obj])
+            jobs.append([NVCC, *_flags(extra), "-c", src, "-o", obj])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -53,13 +59,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         list(ex.map(run, jobs))
-    objs = [os.path.join(BUILD, s.replace(".cu", ".o")) for s in SOURCES]
-    if jobs or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    objs = [os.path.join(bdir, s.replace(".cu", ".o")) for s in SOURCES]
+    if jobs or not os.path.exists(lib) or os.path.getmtime(lib) < max(os.path.getmtime(o) for o in objs):
+        tmp = lib + f".tmp{os.getpid()}"
         run([NVCC, *ARCH, "-shared", "-o", tmp, *objs])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, check="--check" in sys.argv))

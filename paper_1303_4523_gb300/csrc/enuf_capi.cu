@@ -322,6 +322,7 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
     g.c2a = 2.0 * P.alpha / std::sqrt(M_PI);
     g.xmaxf = largest_float_below(P.L);
     g.slater_k = P.slater_k;
+    g.nmax = std::max(n_max, 1);
     if (P.slater_k || P.prec == ENUF_FP64) {
         // real-space kernel table on [0, r_c]: quintic Hermite nodes every <= 0.004
         // (interpolation error of J' ~ h^5, far below FP64 parity)
@@ -366,7 +367,7 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
     const size_t ncmp = (size_t)g.nbin * g.chunk;   // compacted-bead slots
     size_t o_cnt = take((size_t)g.nbin * 4), o_bhist = take((size_t)g.nbin * g.ntiles * 4),
            o_boff = take((size_t)g.nbin * g.ntiles * 4), o_ttot = take((size_t)g.ntiles * 4),
-           o_tstart = take((size_t)(g.ntiles + 1) * 4), o_tk = take(16), o_ctile = take(ncmp * 4),
+           o_tstart = take((size_t)(g.ntiles + 1) * 4), o_tk = take(16), o_ck = take(16), o_ctile = take(ncmp * 4),
            o_cpos = take(ncmp * 4 * esz),
            o_cfrac = take(ncmp * 4 * esz), o_cbase = take(ncmp * 4),
            o_sq = take(nm * 4 * esz), o_sw = take(nm * 4 * esz), o_sb = take(nm * 4),
@@ -389,7 +390,8 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
         plan->fp = fp;
         // stash offsets; bound to the allocation in bind()
         w.cnt_blk = (int*)o_cnt; w.bhist = (int*)o_bhist; w.boff = (int*)o_boff; w.ttot = (int*)o_ttot;
-        w.tstart = (int*)o_tstart; w.ticket = (int*)o_tk; w.ctile = (int*)o_ctile; w.cpos = (void*)o_cpos; w.cfrac = (void*)o_cfrac;
+        w.tstart = (int*)o_tstart; w.ticket = (int*)o_tk; w.check = (unsigned int*)o_ck; w.ctile = (int*)o_ctile;
+        w.cpos = (void*)o_cpos; w.cfrac = (void*)o_cfrac;
         w.cbase = (int*)o_cbase;
         w.sq = (void*)o_sq; w.sw = (void*)o_sw; w.sb = (int*)o_sb; w.wb = (void*)o_wb; w.grid = (void*)o_grid;
         w.spec1 = (void*)o_s1; w.spec2 = (void*)o_s2; w.spec3 = (void*)o_s3; w.spec4 = (void*)o_s4;
@@ -406,13 +408,15 @@ void bind(enuf_plan_t p) {
     Work& w = p->w;
     auto at = [&](auto ptr) { return reinterpret_cast<decltype(ptr)>(b + reinterpret_cast<size_t>(ptr)); };
     w.cnt_blk = at(w.cnt_blk); w.bhist = at(w.bhist); w.boff = at(w.boff); w.ttot = at(w.ttot);
-    w.tstart = at(w.tstart); w.ticket = at(w.ticket); w.ctile = at(w.ctile); w.cpos = at(w.cpos); w.cfrac = at(w.cfrac);
+    w.tstart = at(w.tstart); w.ticket = at(w.ticket); w.check = at(w.check); w.ctile = at(w.ctile);
+    w.cpos = at(w.cpos); w.cfrac = at(w.cfrac);
     w.cbase = at(w.cbase);
     w.sq = at(w.sq); w.sw = at(w.sw); w.sb = at(w.sb); w.wb = at(w.wb); w.grid = at(w.grid);
     w.spec1 = at(w.spec1); w.spec2 = at(w.spec2); w.spec3 = at(w.spec3); w.spec4 = at(w.spec4);
     w.h = at(w.h); w.tab = at(w.tab); w.tabv = at(w.tabv); w.tabr = at(w.tabr);
     w.tw = at(w.tw); w.part = at(w.part); w.Edev = at(w.Edev); w.ktab = at(w.ktab);
     p->g.ktab = p->g.kn > 0 ? w.ktab : nullptr;
+    p->g.check = w.check;
 }
 
 // FP64 influence x deconvolution table over the half space kx = 0..nc:
@@ -689,6 +693,22 @@ enuf_status enuf_get_info(enuf_plan_t plan, enuf_plan_info* info) {
     return ENUF_OK;
 }
 
+enuf_status enuf_check_word(enuf_plan_t plan, unsigned int* mask, int reset) {
+    if (!plan || !mask) return ENUF_ERR_INVALID;
+    CU(cudaStreamSynchronize(plan->stream));
+    CU(cudaMemcpy(mask, plan->w.check, sizeof(unsigned int), cudaMemcpyDeviceToHost));
+    if (reset) CU(cudaMemset(plan->w.check, 0, sizeof(unsigned int)));
+    return ENUF_OK;
+}
+
+int enuf_built_with_checks(void) {
+#ifdef ENUF_CHECK
+    return 1;
+#else
+    return 0;
+#endif
+}
+
 enuf_status enuf_energy_forces(enuf_plan_t plan, int n, const void* pos, const void* q, void* F, double* E,
                                double* virial) {
     if (!plan) return ENUF_ERR_INVALID;
@@ -902,6 +922,7 @@ enuf_status dpd_create(enuf_plan_t plan, const dpd_params* params, int n, const 
     if (!sys) return ENUF_ERR_OOM;
     sys->plan = plan;
     DpdDev& d = sys->d;
+    d.check = plan->w.check;
     d.N = n;
     d.ntypes = params->ntypes;
     // cell edge L/ncd >= 1 + 1e-5: float rounding of x * ncd/L cannot put two

@@ -10,6 +10,20 @@
 namespace enuf {
 
 // Geometry and constants every kernel needs, passed by value.
+// Debug builds (-DENUF_CHECK): device-side index checks. ENUF_GUARD(word,
+// cond, bit) is cond, and when cond fails sets bit `bit` of the plan's check
+// word (read by enuf_check_word); the caller skips the access it guards.
+// Release builds compile it to true.
+#ifdef ENUF_CHECK
+__device__ __forceinline__ bool enuf_guard(unsigned int* word, bool ok, int bit) {
+    if (!ok && word != nullptr) atomicOr(word, 1u << bit);
+    return ok;
+}
+#define ENUF_GUARD(word, cond, bit) enuf_guard((word), (cond), (bit))
+#else
+#define ENUF_GUARD(word, cond, bit) true
+#endif
+
 struct Geo {
     int n;        // oversampled grid per dimension (sigma_s * M)
     int nc;       // kept modes per side, |k_t| <= nc
@@ -42,6 +56,8 @@ struct Geo {
     double kinv;     // kn / r_c
     double kh;       // r_c / kn
     const void* ktab;  // real [kn][kKtStride]: quintic coefficients of J(r) = r u(r) per interval
+    int nmax;          // capacity in beads (sorted charged-bead arrays)
+    unsigned int* check;  // debug builds: failure bits of the device index checks
 };
 
 // Beads of one DPD cell block plus its halo that the pair kernel stages in
@@ -78,6 +94,7 @@ struct Work {
     int* ttot;       // [ntiles] beads per tile
     int* tstart;     // [ntiles + 1]
     int* ticket;     // [4] arrival counters of last-block reductions (0 between launches)
+    unsigned int* check;  // [1] failure bits of the ENUF_CHECK index checks
     int* ctile;      // [nbin * chunk] tile of each compacted charged bead
     void* cpos;      // real4 [nbin * chunk] wrapped x, y, z, q of each compacted charged bead
     void* cfrac;     // real4 [nbin * chunk] fractional grid coordinates, original index bits
@@ -126,6 +143,7 @@ struct TotalsArgs {
 
 // DPD device state and cell list (one per system).
 struct DpdDev {
+    unsigned int* check;   // the plan's check word (debug builds)
     int N, ntypes, ncd, ncells;
     int B;             // cells per block edge of the DPD kernel (<= 4, B + 2 <= ncd)
     double L, gamma, sigma, dt, lambda_vv, K_bond, r0_bond;

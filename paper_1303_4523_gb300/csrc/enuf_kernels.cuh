@@ -346,6 +346,7 @@ __global__ void __launch_bounds__(1024) k_bin_count(Geo g, int N, const R* __res
     __syncthreads();
     const int nc = scount;
     for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+        if (!ENUF_GUARD(g.check, k < g.chunk, 1)) continue;   // the compacted list holds a chunk
         const int i = slist[k];
         R xw[3], fr[3];
         int bs[3];
@@ -355,6 +356,7 @@ __global__ void __launch_bounds__(1024) k_bin_count(Geo g, int N, const R* __res
             grid_coord_r(xw[t], g, bs[t], fr[t]);
         }
         const int tile = ((bs[2] / g.T) * g.ntd + bs[1] / g.T) * g.ntd + bs[0] / g.T;
+        if (!ENUF_GUARD(g.check, (unsigned)tile < (unsigned)g.ntiles, 0)) continue;
         atomicAdd(&hist[tile], 1);
         const int o = i0 + k;
         typename V4<R>::T a, c;
@@ -533,7 +535,9 @@ __global__ void __launch_bounds__(1024) k_bin_scatter(Geo g, const int* __restri
     for (int k = threadIdx.x; k < nc; k += blockDim.x) {
         const int o = i0 + k;
         const int t = ctile[o];
+        if (!ENUF_GUARD(g.check, (unsigned)t < (unsigned)g.ntiles, 2)) continue;
         const int slot = tstart[t] + boff[b * g.ntiles + t] + atomicAdd(&cur[t], 1);
+        if (!ENUF_GUARD(g.check, (unsigned)slot < (unsigned)g.nmax, 2)) continue;
         sq[slot] = cpos[o];
         sw[slot] = cfrac[o];
         sb[slot] = cbase[o];
@@ -891,7 +895,8 @@ __global__ void __launch_bounds__(spread2_threads<SLAB>(T)) k_spread_col(Geo g, 
             int basei = 0;
             if (lane == 0 && bal) basei = atomicAdd(&nitems, __popc(bal));
             basei = __shfl_sync(0xffffffffu, basei, 0);
-            if (keep) items[basei + __popc(bal & ((1u << lane) - 1u))] = make_int2(c, rg);
+            const int at = basei + __popc(bal & ((1u << lane) - 1u));
+            if (keep && ENUF_GUARD(g.check, at < kColCand, 3)) items[at] = make_int2(c, rg);
         }
         __syncthreads();
         const int ni = nitems;
@@ -927,6 +932,7 @@ __global__ void __launch_bounds__(spread2_threads<SLAB>(T)) k_spread_col(Geo g, 
                     for (int xy = lane; xy < nx * ny; xy += 32) {
                         const int iy = (int)(((float)xy + 0.5f) * inx);
                         const int x = lx + xy - iy * nx, y = ly + iy;
+                        if (!ENUF_GUARD(g.check, x < T && y < T && zb <= T, 4)) continue;
                         const R w = wi[x] * wi[T + y];
                         R* a = acc_s + y * T + x;
                         for (int z = za; z < zb; ++z) a[z * T * T] += w * wi[2 * T + z];
@@ -1403,7 +1409,9 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Geo g, const int* __r
                 const int rowo = lix[warp][1][b] * n + lix[warp][0][a];
                 R s0 = 0, s1 = 0;   // sum_z psi h, sum_z psi' h
                 for (int c = 0; c < P2; ++c) {
-                    const R hv = h0[lix[warp][2][c] + rowo];
+                    const int off = lix[warp][2][c] + rowo;
+                    if (!ENUF_GUARD(g.check, (size_t)off < n3, 5)) continue;
+                    const R hv = h0[off];
                     s0 = fma(wts[warp][2][c], hv, s0);
                     s1 = fma(dwts[warp][2][c], hv, s1);
                 }
@@ -1421,6 +1429,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Geo g, const int* __r
                 for (int c = 0; c < P2; ++c) {
                     const R w = wts[warp][2][c];
                     const int off = lix[warp][2][c] + rowo;   // z index pre-scaled by n^2
+                    if (!ENUF_GUARD(g.check, (size_t)off < n3, 5)) continue;
                     s0 = fma(w, h0[off], s0);
                     s1 = fma(w, h1[off], s1);
                     s2 = fma(w, h2[off], s2);
@@ -1690,13 +1699,15 @@ __device__ __forceinline__ void real_beads(const Geo& g, int c0, int c1, int sel
                 const unsigned m = __ballot_sync(0xffffffffu, hit);
                 if (hit) {
                     const int at = cnt + __popc(m & ((1u << lane) - 1u));
-                    if (PRE) {
-                        quj[at] = f;
-                    } else {
-                        V e;
-                        e.x = dx; e.y = dy; e.z = dz; e.w = qj;
-                        qu[at] = e;
-                        if (real_half<R>()) quj[at] = gs;
+                    if (ENUF_GUARD(g.check, at < 64, 7)) {   // the warp's queue holds 64
+                        if (PRE) {
+                            quj[at] = f;
+                        } else {
+                            V e;
+                            e.x = dx; e.y = dy; e.z = dz; e.w = qj;
+                            qu[at] = e;
+                            if (real_half<R>()) quj[at] = gs;
+                        }
                     }
                 }
                 cnt += __popc(m);
@@ -1778,6 +1789,7 @@ __global__ void __launch_bounds__(kRealThreads) k_real(Geo g, const int* __restr
         halo_dim(ty, g.rs, g.ntd, ylo, yc);
         halo_dim(tz, g.rs, g.ntd, zlo, zc);
         const int nh = xc * yc * zc;   // <= kRealHalo by construction of the plan
+        if (!ENUF_GUARD(g.check, nh <= kRealHalo, 6)) continue;   // uniform over the block
         // halo tile ranges and their exclusive prefix (block scan, <= 4 per thread)
         int cnt4[4], sum = 0;
 #pragma unroll
@@ -2150,7 +2162,8 @@ __device__ __forceinline__ void dpd_cells(const DpdDev& d, int H, int B3, const 
                     }
                 }
                 const unsigned m = __ballot_sync(0xffffffffu, hit);
-                if (hit) queue[cnt + __popc(m & ((1u << lane) - 1u))] = make_int2(me, j);
+                if (hit && ENUF_GUARD(d.check, cnt + __popc(m & ((1u << lane) - 1u)) < 64, 9))
+                    queue[cnt + __popc(m & ((1u << lane) - 1u))] = make_int2(me, j);
                 cnt += __popc(m);
                 if (cnt >= 32) {
                     __syncwarp();
@@ -2192,6 +2205,7 @@ __global__ void __launch_bounds__(kDpdThreads, sizeof(R) == 4 ? 4 : 2)
     const int ncd = d.ncd, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     int2* queue = queues + warp * 64;
     const int H = B + 2, H3 = H * H * H, B3 = B * B * B;
+    if (!ENUF_GUARD(d.check, H3 <= HMAX && B3 <= kDpdMaxB * kDpdMaxB * kDpdMaxB, 8)) return;
     const int nblk = (ncd + B - 1) / B;
     const R L = (R)d.L, hL = (R)(0.5 * d.L);
     R ec = 0, eb = 0;

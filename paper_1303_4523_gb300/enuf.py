@@ -16,7 +16,8 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libenuf.so")
+# ENUF_CHECK=1 in the environment loads the debug build (device index checks)
+LIB_PATH = os.path.join(_HERE, "libenuf_check.so" if os.environ.get("ENUF_CHECK") == "1" else "libenuf.so")
 
 ENUF_FP64, ENUF_FP32 = 0, 1
 ENUF_BUF_GRID, ENUF_BUF_FIELD = 0, 1
@@ -77,6 +78,8 @@ def _load():
         "dpd_set_state": (st, [vp, vp, vp, vp, C.c_uint64]),
         "dpd_get_forces": (st, [vp, vp]),
         "dpd_step_host": (st, [vp, C.c_int, vp, vp, vp, C.POINTER(C.c_double)]),
+        "enuf_check_word": (st, [vp, C.POINTER(C.c_uint), C.c_int]),
+        "enuf_built_with_checks": (C.c_int, []),
         "dpd_device_state": (st, [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp)]),
         "dpd_destroy": (None, [vp]),
         "enuf_batch_plan": (st, [i, C.POINTER(enuf_params), C.POINTER(C.c_int), vp, C.POINTER(vp)]),
@@ -98,7 +101,8 @@ EXPORTED = ("enuf_plan", "enuf_footprint", "enuf_get_info", "enuf_energy_forces"
             "enuf_energy_forces_host", "enuf_debug_buffer", "enuf_enable_timing",
             "enuf_stage_time", "enuf_launches_per_eval", "enuf_destroy", "enuf_status_string",
             "enuf_last_error", "dpd_create", "dpd_step", "dpd_get_state", "dpd_set_state",
-            "dpd_get_forces", "dpd_step_host", "dpd_device_state", "dpd_destroy", "enuf_batch_plan",
+            "dpd_get_forces", "dpd_step_host", "dpd_device_state", "enuf_check_word",
+            "enuf_built_with_checks", "dpd_destroy", "enuf_batch_plan",
             "enuf_batch_energy_forces", "enuf_batch_launches", "enuf_batch_destroy",
             "enuf_spread_noalloc")
 
@@ -240,6 +244,12 @@ class Plan:
 
     def launches(self):
         return lib.enuf_launches_per_eval(self.h)
+
+    def check_word(self, reset=True):
+        """Failure bits of the device index checks (debug build; 0 otherwise)."""
+        m = C.c_uint()
+        _check(lib.enuf_check_word(self.h, C.byref(m), int(reset)), self.h)
+        return m.value
 
     def close(self):
         if self.h:

@@ -92,3 +92,14 @@ def test_method_switches_are_validated_without_gpu():
         ik = enuf.enuf_footprint(enuf.make_params(prec=prec, **base), 81000)
         grad = enuf.enuf_footprint(enuf.make_params(prec=prec, deriv=1, **base), 81000)
         assert ik - grad >= 2 * n3 * esz   # two real fields fewer (and their spectra)
+
+
+def test_checked_build_exports_the_same_api():
+    """The debug build (-DENUF_CHECK, device index checks) compiles and exports
+    the same functions; each build reports whether it carries the checks."""
+    from paper_1303_4523_gb300 import build
+    rel = ctypes.CDLL(build.build())
+    chk = ctypes.CDLL(build.build(check=True))
+    for name in _declared():
+        assert hasattr(chk, name), name
+    assert rel.enuf_built_with_checks() == 0 and chk.enuf_built_with_checks() == 1
