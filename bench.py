@@ -103,8 +103,8 @@ class ClockSampler:
 
 
 def algorithmic_bytes(info, nq, N, esz, nf=3):
-    """Algorithmic DRAM bytes of one launch of each kernel group:
-    every array the stage must read or write, once. nf: force fields (3 for
+    """Algorithmic DRAM bytes of one launch of each kernel group: every array
+    the stage must read or write, once. nf: force fields (3 for
     ik-differentiation, 1 in gradient mode)."""
     n, nc = info.n, info.n_c
     K, nc1 = 2 * nc + 1, nc + 1

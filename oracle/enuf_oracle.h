@@ -13,14 +13,14 @@
  * cartesian in a cubic periodic box of edge L; they may lie outside [0, L)
  * and are wrapped with orc_wrap().
  *
- * Readings of points the paper leaves open (each is listed in the design doc):
+ * Readings of points the paper leaves open:
  *  - Slater smearing enters the real-space pair sum only, as the exact
- *    correction -(1+beta r) e^{-2 beta r}/r to the erfc term (Sec. 5,
- *    "B1 and B2 only applied on real space"); reciprocal space is the plain
- *    Ewald sum (Eq. 18).
+ *    correction -(1+beta r) e^{-2 beta r}/r to the erfc term (Sec. 5 applies
+ *    the corrections B1 and B2 to the real-space part alone); reciprocal
+ *    space is the plain Ewald sum (Eq. 18).
  *  - The garbled real-space force (Eq. 32) is taken as the exact gradient
  *    of Eq. 31.
- *  - The NFFT window (Sec. 4, "Gaussian type") is the Gaussian
+ *  - The NFFT window (Sec. 4 names only its Gaussian kind) is the Gaussian
  *    psi(u) = (pi b)^{-1/2} exp(-u^2/b), u in grid units, with
  *    b = 2 sigma p / ((2 sigma - 1) pi), truncated to 2p taps per dimension.
  *  - The mode set I_M (Eq. 9) is taken symmetric, |k_t| <= n_c = M/2 - 1.

@@ -1,6 +1,6 @@
 // enuf_fft.cuh -- batched shared-memory FFT of length n = 2^a 3^b 5^c (n <= 1024).
 //
-// The 3-D transforms of the NFFT (the "standard FFT" of Sec. 3.3 inside the
+// The 3-D transforms of the NFFT (the plain FFT step of Sec. 3.3 inside the
 // transposed and conjugated NFFT, Eq. 13-14) are done one dimension at a time;
 // each CTA loads a batch of lines into shared memory and runs this Stockham
 // auto-sort FFT on all of them. Stage s with radix R combines R sub-transforms
