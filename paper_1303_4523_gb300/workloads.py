@@ -22,10 +22,10 @@ SEED_BASE = 1303
 # Table 1 / Sec. 5 parameter sets, in reduced units (R_c = 1).
 #   "paper":    alpha = 0.20 A^-1 * 7.829 A = 1.566, r_c = 3, p = 2, n_c = 7 (M = 16),
 #               beta = 1.125 (lambda_e = 6.954 A), eps0 eps_r = 1 -> kappa = 1/(4 pi).
-#   "baseline": alpha = 0.975, r_c = 3, p = 4, lambda = 0.25 (beta = 4),
+#   "bench":    alpha = 0.975, r_c = 3, p = 4, lambda = 0.25 (beta = 4),
 #               kappa = Gamma/(4 pi) with Gamma = 13.87, M from the grid rule.
 PAPER_SET = dict(alpha=1.566, r_cut=3.0, p=2, beta=1.125, kappa=1.0 / (4.0 * math.pi))
-BASELINE_SET = dict(alpha=0.975, r_cut=3.0, p=4, beta=4.0, kappa=13.87 / (4.0 * math.pi))
+BENCH_SET = dict(alpha=0.975, r_cut=3.0, p=4, beta=4.0, kappa=13.87 / (4.0 * math.pi))
 
 # DPD parameters of the polyelectrolyte run (Groot-Warren values).
 DPD_SET = dict(a=25.0, gamma=4.5, sigma=3.0, dt=0.04, lambda_vv=0.65, K_bond=4.0, r0_bond=0.0)
@@ -106,12 +106,12 @@ def electrolyte(N: int, L: float | None = None, n_charged: int | None = None,
     return System(name=f"electrolyte N={N} L={L:.4g}", L=float(L), pos=pos,
                   vel=_velocities(rng, N), q=q, types=types,
                   bonds=np.zeros((0, 2), dtype=np.int32),
-                  M=M if M is not None else grid_rule(L), params=dict(pset or BASELINE_SET))
+                  M=M if M is not None else grid_rule(L), params=dict(pset or BENCH_SET))
 
 
-def electrolyte_small(pset: str = "baseline") -> System:
+def electrolyte_small(pset: str = "bench") -> System:
     """N = 3000 beads, L = 10, 300 charged (150 +1, 150 -1): density 3."""
-    ps = PAPER_SET if pset == "paper" else BASELINE_SET
+    ps = PAPER_SET if pset == "paper" else BENCH_SET
     return electrolyte(3000, 10.0, n_charged=300, seed_offset=0, pset=ps, M=16)
 
 
@@ -178,7 +178,7 @@ def polyelectrolyte(L: float = 30.0, density: float = 3.0, n_chains: int = 10,
     return System(name=f"polyelectrolyte N={N} L={L:g} chains={n_chains}x{chain_len} f={f}",
                   L=float(L), pos=pos, vel=_velocities(rng, N), q=q, types=types,
                   bonds=np.asarray(bonds, dtype=np.int32).reshape(-1, 2),
-                  M=grid_rule(L), params=dict(BASELINE_SET))
+                  M=grid_rule(L), params=dict(BENCH_SET))
 
 
 def batch_sweep(n_systems: int = 64, n_min: int = 3000, n_max: int = 81000,

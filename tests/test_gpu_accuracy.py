@@ -29,7 +29,7 @@ def _rel_rms(F, R):
     return math.sqrt(((F - R) ** 2).sum() / (R ** 2).sum())
 
 
-@pytest.mark.parametrize("pset", ["paper", "baseline"])
+@pytest.mark.parametrize("pset", ["paper", "bench"])
 def test_error_versus_p_against_direct_ewald(enuf, pset):
     s = W.electrolyte_small(pset)
     P = dict(L=s.L, M=s.M, **s.params)

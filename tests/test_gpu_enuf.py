@@ -80,7 +80,7 @@ def _sys_small(pset):
 CASES = {
     # name: (params, N, L, n_charged, seed)
     "paper_set_M16_p2": ("paper", None),
-    "baseline_set_M16_p4": ("baseline", None),
+    "bench_set_M16_p4": ("bench", None),
     "radix3_M24_p3": (dict(L=15.0, alpha=0.975, r_cut=3.0, beta=4.0, kappa=1.1, M=24, p=3), (3000, 15.0, 600)),
     "radix5_M20_p5_spherical": (dict(L=12.5, alpha=1.1, r_cut=3.0, beta=1.125, kappa=0.8, M=20, p=5, kmask=1),
                                 (2500, 12.5, 400)),
@@ -174,7 +174,7 @@ def test_gradient_mode_parity(enuf, name, prec):
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_gradient_mode_field_matches_oracle(enuf, prec):
-    P, pos, q = _sys_small("baseline")
+    P, pos, q = _sys_small("bench")
     P = dict(P, deriv=1)
     pos, q = _inputs(prec, pos, q)
     plan, F, E, Wv = _gpu(enuf, prec, P, pos, q)
@@ -189,7 +189,7 @@ def test_gradient_mode_field_matches_oracle(enuf, prec):
 def test_spread_grid_and_fields_match_oracle(enuf, prec):
     """Stage parity: the spread grid (Eq. 14, first half) and the three
     conjugated-NFFT fields before the gather (Eq. 25)."""
-    P, pos, q = _sys_small("baseline")
+    P, pos, q = _sys_small("bench")
     pos, q = _inputs(prec, pos, q)
     plan, F, E, Wv = _gpu(enuf, prec, P, pos, q)
     grid = plan.debug_buffer(enuf.ENUF_BUF_GRID).astype(np.float64)
@@ -247,7 +247,7 @@ def test_n_above_capacity_is_rejected(enuf):
 
 def test_repeat_and_pointer_change(enuf):
     """Graph replay gives the same result; new pointers trigger a new capture."""
-    P, pos, q = _sys_small("baseline")
+    P, pos, q = _sys_small("bench")
     plan = enuf.Plan(enuf.make_params(**P), len(q))
     tp = torch.tensor(pos, device="cuda")
     tq = torch.tensor(q, device="cuda")
@@ -274,7 +274,7 @@ def test_host_buffer_entry_point(enuf, prec):
 
 
 def test_stage_timing(enuf):
-    P, pos, q = _sys_small("baseline")
+    P, pos, q = _sys_small("bench")
     plan = enuf.Plan(enuf.make_params(**P), len(q))
     plan.enable_timing(True)
     tp = torch.tensor(pos, device="cuda")

@@ -21,7 +21,7 @@ def _charged(s):
 
 @pytest.fixture(scope="module")
 def small():
-    s = W.electrolyte_small("baseline")
+    s = W.electrolyte_small("bench")
     return s, *_charged(s)
 
 

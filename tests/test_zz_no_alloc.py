@@ -27,7 +27,7 @@ def test_noalloc_spread_matches_plan_grid(prec, tol):
     build.build()
     from paper_1303_4523_gb300 import enuf
 
-    s = W.electrolyte_small("baseline")
+    s = W.electrolyte_small("bench")
     params = enuf.make_params(prec=prec, L=s.L, M=s.M, **s.params)
     dt = torch.float32 if prec == "fp32" else torch.float64
     pos = torch.tensor(s.pos, dtype=dt, device="cuda")
