@@ -489,6 +489,14 @@ def run_batch(args):
         pos = [torch.tensor(s.pos, dtype=dt, device="cuda") for s in systems]
         q = [torch.tensor(s.q, dtype=dt, device="cuda") for s in systems]
         F = [torch.empty_like(p) for p in pos]
+        if args.autotune:
+            # tile edge and FFT path per system shape, measured once and cached
+            from paper_1303_4523_gb300 import autotune
+            cache = autotune.TuneCache()
+            t0 = time.perf_counter()
+            params = [autotune.tuned_params(p, s.N, a, c, cache=cache) for p, s, a, c in zip(params, systems, pos, q)]
+            out[prec + "_tune_s"] = round(time.perf_counter() - t0, 2)
+            out[prec + "_tiles"] = sorted({p.tile for p in params})
         b = enuf.Batch(params, [s.N for s in systems])
         for _ in range(3):
             b.energy_forces(pos, q, F, want_energy=False)
@@ -577,6 +585,8 @@ def main():
                     help="main: the bench line; sizes/batch/serve: the scaling sweep, the 64-system batch and the "
                          "serving load (each prints its own JSON line)")
     ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--autotune", action="store_true",
+                    help="--mode batch: pick each system's tile edge and FFT path by timing them (cached)")
     ap.add_argument("--sizes-n", type=int, nargs="*", default=None,
                     help="--mode sizes: run only these system sizes (of 3000 24000 81000 192000 375000 3000000)")
     args = ap.parse_args()

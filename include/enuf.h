@@ -87,7 +87,11 @@ typedef struct {
                              energy for converged sums. */
     int    fft_path;  /* 0: automatic (FP32 grids with n <= 112: whole z-planes in shared
                          memory, x+y and y+x fused); 1: always the five line passes x, y, z, y, x */
-    int    reserved[3];
+    int    fft_radix; /* radix schedule of the line transforms: 0 = automatic (the fewest
+                         stages over 2, 3, 4, 5, 8; FP32 grids from n = 128 on take the
+                         composite radices 6, 10, 12, 16, 20 when that saves a stage);
+                         1 = radices 2, 3, 4, 5, 8 only */
+    int    reserved[2];
 } enuf_params;
 
 typedef struct enuf_plan_s* enuf_plan_t;

@@ -1,0 +1,203 @@
+"""Autotuner for the launch choices of a plan that leave the method unchanged.
+
+Three plan parameters change which kernels run and how the oversampled grid
+is cut, but not what is computed (results agree to rounding):
+
+  tile      the spreading tile edge T (a divisor of n, p <= T <= 24). It sets
+            the spreading kernel (column form for T in 8, 10, 12, 16, 20, 24,
+            the work-item form otherwise), the binning histogram and the
+            real-space cell list, whose stencil is +-ceil(r_c / (T L / n))
+            tiles per axis.
+  fft_path  FP32 grids with n <= 112 run the FFT as whole z-planes in shared
+            memory (x and y passes fused); fft_path = 1 forces the five line
+            passes instead.
+  fft_radix the radix schedule of the line transforms: FP32 grids from
+            n = 128 on take composite radices (6, 10, 12, 16, 20) when that
+            saves a stage; fft_radix = 1 keeps radices 2, 3, 4, 5, 8.
+
+The library's own host validation (enuf_footprint) decides which tiles are
+legal, so the candidates never include a launch shape the plan would reject.
+Each candidate is timed on the device with CUDA events over repeated
+evaluations of the caller's system; the fastest is kept in a JSON cache keyed
+by everything that fixes the kernels' shapes and work: device name,
+precision, force mode, Slater placement, mode mask, n, p, the real-space
+cutoff in grid units and the charged-bead count (in powers of two).
+
+    from paper_1303_4523_gb300 import autotune
+    params = autotune.tuned_params(params, n_max, pos, q)   # device tensors
+
+The cache path is $ENUF_TUNE_CACHE, else ~/.cache/enuf_gb300/tune.json.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import json
+import math
+import os
+from typing import Callable
+
+from . import enuf
+
+CACHE_VERSION = 2
+MAX_TILE = 24
+FUSED_FFT_MAX_N = 112
+COMPOSITE_MIN_N = 128
+CHOICES = ("tile", "fft_path", "fft_radix")
+
+
+def default_cache_path() -> str:
+    return os.environ.get("ENUF_TUNE_CACHE") or os.path.join(os.path.expanduser("~"), ".cache", "enuf_gb300",
+                                                             "tune.json")
+
+
+def _copy(params: enuf.enuf_params, **over) -> enuf.enuf_params:
+    p = enuf.enuf_params()
+    C.memmove(C.byref(p), C.byref(params), C.sizeof(enuf.enuf_params))
+    for k, v in over.items():
+        setattr(p, k, v)
+    return p
+
+
+def grid_n(params: enuf.enuf_params) -> int:
+    """Oversampled grid edge n = sigma_s M (M from the plan's grid rule when 0)."""
+    M = params.M
+    if M == 0:
+        from .workloads import grid_rule
+        M = grid_rule(params.L)
+    return params.sigma_s * M
+
+
+def _legal(params: enuf.enuf_params, n_max: int) -> bool:
+    try:
+        enuf.enuf_footprint(params, n_max)
+    except enuf.EnufError:
+        return False
+    return True
+
+
+def candidates(params: enuf.enuf_params, n_max: int) -> list[dict]:
+    """Every (tile, fft_path, fft_radix) the plan accepts for these
+    parameters; the FFT choices only where they select different kernels."""
+    n = grid_n(params)
+    tiles = [T for T in range(max(1, params.p), MAX_TILE + 1)
+             if n % T == 0 and _legal(_copy(params, tile=T), n_max)]
+    fp32 = params.prec == enuf.ENUF_FP32
+    paths = [0, 1] if fp32 and n <= FUSED_FFT_MAX_N else [0]
+    radices = [0, 1] if fp32 and n >= COMPOSITE_MIN_N else [0]
+    return [{"tile": T, "fft_path": f, "fft_radix": r} for T in tiles for f in paths for r in radices]
+
+
+def cache_key(params: enuf.enuf_params, n_charged: int, device: str = "") -> str:
+    n = grid_n(params)
+    rc_grid = params.r_cut * n / params.L
+    qb = 0 if n_charged <= 0 else int(math.ceil(math.log2(n_charged)))
+    prec = "fp32" if params.prec == enuf.ENUF_FP32 else "fp64"
+    return (f"{device}|{prec}|deriv{params.deriv}|slater_k{params.slater_k}|kmask{params.kmask}"
+            f"|n{n}|p{params.p}|rc{round(rc_grid * 4) / 4:g}|q2^{qb}")
+
+
+class TuneCache:
+    """A JSON file of tuned choices: {"version": CACHE_VERSION, "entries":
+    {key: {"tile", "fft_path", "fft_radix", "ms", "timings"}}}; a file of
+    another version is ignored (and replaced on the next put)."""
+
+    def __init__(self, path: str | None = None):
+        self.path = path or default_cache_path()
+        self.entries: dict = {}
+        try:
+            with open(self.path) as f:
+                d = json.load(f)
+            if d.get("version") == CACHE_VERSION:
+                self.entries = dict(d.get("entries", {}))
+        except (OSError, ValueError):
+            pass
+
+    def get(self, key: str):
+        return self.entries.get(key)
+
+    def put(self, key: str, entry: dict):
+        self.entries[key] = entry
+        d = os.path.dirname(self.path)
+        if d:
+            os.makedirs(d, exist_ok=True)
+        tmp = self.path + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump({"version": CACHE_VERSION, "entries": self.entries}, f, indent=1, sort_keys=True)
+        os.replace(tmp, self.path)
+
+
+def time_on_device(params: enuf.enuf_params, n_max: int, pos, q, reps: int = 20, warmup: int = 3) -> float:
+    """Milliseconds per evaluation of one plan with these parameters: CUDA
+    events on the plan's stream around `reps` back-to-back evaluations, after
+    `warmup` untimed ones."""
+    import torch
+    plan = enuf.Plan(params, n_max)
+    try:
+        F = torch.empty_like(pos)
+        for _ in range(warmup):
+            plan.energy_forces(pos, q, F, want_energy=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(plan.stream)
+        for _ in range(reps):
+            plan.energy_forces(pos, q, F, want_energy=False)
+        e1.record(plan.stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+    finally:
+        plan.close()
+
+
+def _device_name() -> str:
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.get_device_name()
+    except ImportError:
+        pass
+    return ""
+
+
+def tune(params: enuf.enuf_params, n_max: int, pos, q, measure: Callable | None = None,
+         cache: TuneCache | None = None, device: str | None = None, force: bool = False) -> dict:
+    """The fastest candidate for this system, from the cache when present.
+
+    measure(params, n_max, pos, q) -> ms replaces the device timing (tests
+    pass a model of the cost). Returns {"tile", "fft_path", "fft_radix",
+    "ms", "timings", "key", "cached"}."""
+    measure = measure or time_on_device
+    cache = cache if cache is not None else TuneCache()
+    device = _device_name() if device is None else device
+    n_charged = int((q != 0).sum())
+    key = cache_key(params, n_charged, device)
+    hit = None if force else cache.get(key)
+    if hit is not None:
+        return dict(hit, key=key, cached=True)
+    cands = candidates(params, n_max)
+    if not cands:
+        raise enuf.EnufError(enuf.ENUF_ERR_UNSUPPORTED, "no legal tile for these parameters")
+    timings = []
+    for c in cands:
+        ms = float(measure(_copy(params, **c), n_max, pos, q))
+        timings.append(dict(c, ms=ms))
+    best = min(timings, key=lambda t: t["ms"])
+    entry = {k: best[k] for k in CHOICES}
+    entry.update(ms=best["ms"], timings=timings)
+    cache.put(key, entry)
+    return dict(entry, key=key, cached=False)
+
+
+def tuned_params(params: enuf.enuf_params, n_max: int, pos, q, **kw) -> enuf.enuf_params:
+    """A copy of params with the tuned tile edge and FFT choices filled in."""
+    r = tune(params, n_max, pos, q, **kw)
+    return _copy(params, **{k: r[k] for k in CHOICES})
+
+
+def cached_params(params: enuf.enuf_params, n_charged: int, cache: TuneCache | None = None,
+                  device: str | None = None) -> enuf.enuf_params:
+    """A copy of params with a cached choice filled in, or params unchanged
+    when this shape was never tuned (no timing runs here)."""
+    cache = cache if cache is not None else TuneCache()
+    device = _device_name() if device is None else device
+    hit = cache.get(cache_key(params, n_charged, device))
+    return params if hit is None else _copy(params, **{k: hit[k] for k in CHOICES})

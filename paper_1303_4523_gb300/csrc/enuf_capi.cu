@@ -212,12 +212,13 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
     if (P.slater_k != 0 && P.slater_k != 1) return fail(plan, ENUF_ERR_INVALID, "slater_k must be 0 or 1");
     if (P.slater_k && !(P.beta > 0)) return fail(plan, ENUF_ERR_INVALID, "slater_k = 1 needs beta > 0");
     if (P.fft_path != 0 && P.fft_path != 1) return fail(plan, ENUF_ERR_INVALID, "fft_path must be 0 or 1");
+    if (P.fft_radix != 0 && P.fft_radix != 1) return fail(plan, ENUF_ERR_INVALID, "fft_radix must be 0 or 1");
     const int M = P.M == 0 ? grid_rule(P.L) : P.M;
     if (M < 4 || (M & 1)) return fail(plan, ENUF_ERR_INVALID, "M must be even and >= 4 (got %d)", M);
     const int n = P.sigma_s * M;
     if (n > 1024) return fail(plan, ENUF_ERR_UNSUPPORTED, "grid n = %d > 1024", n);
     FftPlanDev fp{};
-    if (!fft_radices(n, fp, P.prec == ENUF_FP32))
+    if (!fft_radices(n, fp, P.prec == ENUF_FP32 && P.fft_radix == 0))
         return fail(plan, ENUF_ERR_UNSUPPORTED, "grid n = %d is not 2^a 3^b 5^c", n);
     if (2 * P.p > n) return fail(plan, ENUF_ERR_INVALID, "window 2p = %d wider than the grid", 2 * P.p);
     // tile edge: divides n, >= p, histogram fits in shared memory

@@ -20,6 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libenuf_check.so" if os.environ.get("ENUF_CHECK") == "1" else "libenuf.so")
 
 ENUF_FP64, ENUF_FP32 = 0, 1
+ENUF_OK, ENUF_ERR_INVALID, ENUF_ERR_OOM, ENUF_ERR_CUDA, ENUF_ERR_TIMEOUT, ENUF_ERR_UNSUPPORTED = range(6)
 ENUF_BUF_GRID, ENUF_BUF_FIELD = 0, 1
 STAGES = {"bin": 0, "spread": 1, "fft": 2, "gather": 3, "real": 4, "dpd": 5, "all": 6, "cell": 7}
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "CUDA error",
@@ -36,7 +37,8 @@ class enuf_params(C.Structure):
     _fields_ = [("L", C.c_double), ("alpha", C.c_double), ("r_cut", C.c_double),
                 ("beta", C.c_double), ("kappa", C.c_double), ("M", C.c_int), ("p", C.c_int),
                 ("sigma_s", C.c_int), ("kmask", C.c_int), ("prec", C.c_int), ("tile", C.c_int),
-                ("deriv", C.c_int), ("slater_k", C.c_int), ("fft_path", C.c_int), ("reserved", C.c_int * 3)]
+                ("deriv", C.c_int), ("slater_k", C.c_int), ("fft_path", C.c_int), ("fft_radix", C.c_int),
+                ("reserved", C.c_int * 2)]
 
 
 class enuf_plan_info(C.Structure):
@@ -114,11 +116,11 @@ def _check(status, handle=None, what=""):
 
 
 def make_params(L, alpha, r_cut, beta, kappa, M=0, p=4, sigma_s=2, kmask=0,
-                prec="fp64", tile=0, deriv=0, slater_k=0, fft_path=0) -> enuf_params:
+                prec="fp64", tile=0, deriv=0, slater_k=0, fft_path=0, fft_radix=0) -> enuf_params:
     pr = {"fp64": ENUF_FP64, "fp32": ENUF_FP32}[prec] if isinstance(prec, str) else int(prec)
     return enuf_params(float(L), float(alpha), float(r_cut), float(beta), float(kappa), int(M),
                        int(p), int(sigma_s), int(kmask), pr, int(tile), int(deriv), int(slater_k),
-                       int(fft_path), (C.c_int * 3)())
+                       int(fft_path), int(fft_radix), (C.c_int * 2)())
 
 
 def _ptr(x):

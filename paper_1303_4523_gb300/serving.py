@@ -210,9 +210,11 @@ def latency_stats(results: list[Result]) -> dict:
 class GpuBackend:
     """Runs requests through libenuf.so. One plan (and stream) per resident
     system key; force requests reuse the plan and its device buffers, DPD
-    requests a resident DpdSystem."""
+    requests a resident DpdSystem. With a tune cache (autotune.TuneCache),
+    systems that name no tile take the cached tile edge and FFT path of their
+    shape when there is one; nothing is timed while serving."""
 
-    def __init__(self, device: int = 0):
+    def __init__(self, device: int = 0, tune_cache=None):
         import torch
 
         from paper_1303_4523_gb300 import enuf
@@ -220,12 +222,17 @@ class GpuBackend:
         self.enuf = enuf
         self.device = torch.device("cuda", device)
         self.sys: dict[str, dict] = {}
+        self.tune_cache = tune_cache
 
     def _params(self, req: Request):
         s = req.system
         kw = dict(s.params)
         kw.setdefault("M", s.M)
-        return self.enuf.make_params(L=s.L, prec=req.prec, **kw)
+        p = self.enuf.make_params(L=s.L, prec=req.prec, **kw)
+        if self.tune_cache is not None and not kw.get("tile"):
+            from paper_1303_4523_gb300 import autotune
+            p = autotune.cached_params(p, int(np.count_nonzero(s.q)), cache=self.tune_cache)
+        return p
 
     def footprint(self, req: Request) -> int:
         s = req.system

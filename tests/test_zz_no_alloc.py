@@ -8,7 +8,7 @@ arrays and the library's fixed 16 MiB device scratch. The test calls it
 through the C ABI twice in a row and compares each result with the spread
 grid of the regular, plan-based entry point.
 
-This file is named so that pytest collects it last.
+This file is named so that pytest collects it after the plan-based tests.
 """
 import ctypes as C
 
