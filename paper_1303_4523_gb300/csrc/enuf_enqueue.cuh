@@ -128,8 +128,7 @@ cudaError_t configure_kernels(int max_smem) {
 
 template <typename R>
 int spread_smem(const Geo& g) {
-    const int T3 = g.T * g.T * g.T;
-    return kSpreadCap * (int)sizeof(typename V4<R>::T) + T3 * (int)sizeof(R) +
+    return kSpreadCap * (int)sizeof(typename V4<R>::T) + spread_tile_slots(g.T) * (int)sizeof(R) +
            (kSpreadThreads / 32) * 3 * kMaxTaps * ((int)sizeof(R) + 4) + kSpreadCap * 4 + kSpreadCap * 8;
 }
 

@@ -576,6 +576,10 @@ __global__ void __launch_bounds__(256) k_bin_weights(Geo g, const int* __restric
 constexpr int kSpreadThreads = 256;
 constexpr int kMaxTaps = 16;
 constexpr int kSpreadCap = 512;   // beads staged in shared memory per round
+// Shared slots of the work-item kernel's tile: T^3 rounded up to a multiple of
+// 4, so that the regions after it (the int2 work items last) stay 16-byte
+// aligned for odd T as well.
+__host__ __device__ constexpr int spread_tile_slots(int T) { return (T * T * T + 3) & ~3; }
 
 // Taps of a bead (base b, 2p taps from b - p + 1) that fall in the tile [o, o+T)
 // of a periodic grid of n points, as a bit mask over the taps. With at least
@@ -629,8 +633,8 @@ __global__ void __launch_bounds__(kSpreadThreads, 5) k_spread(Geo g, const int* 
     const int T = g.T, T3 = T * T * T;
     constexpr int NW = kSpreadThreads / 32;
     V* stg = reinterpret_cast<V*>(smraw);                          // [cap] (fx, fy, fz, q)
-    R* acc = reinterpret_cast<R*>(stg + kSpreadCap);                // [T^3]
-    R* wts = acc + T3;                                              // [NW][3][16]
+    R* acc = reinterpret_cast<R*>(stg + kSpreadCap);                // [T^3], padded to spread_tile_slots(T)
+    R* wts = acc + spread_tile_slots(T);                            // [NW][3][16]
     int* lix = reinterpret_cast<int*>(wts + NW * 3 * kMaxTaps);     // [NW][3][16]
     int* sbase = lix + NW * 3 * kMaxTaps;                           // [cap]
     int2* items = reinterpret_cast<int2*>(sbase + kSpreadCap);      // [cap] (bead | x mask, y mask | z mask)

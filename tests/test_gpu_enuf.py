@@ -95,6 +95,17 @@ CASES = {
                       (1500, 12.0, 300)),
     "tile24_M24_p5": (dict(L=14.0, alpha=1.0, r_cut=3.0, beta=2.0, kappa=1.0, M=24, p=5, tile=24),
                       (2000, 14.0, 400)),
+    # odd tile edges (work-item spreading; its shared regions stay aligned), one
+    # of them the plan's own choice: the smallest divisor of n = 36 at least
+    # r_c n / L = 8.5 grid points wide
+    "tile9_M18_p4": (dict(L=11.0, alpha=1.0, r_cut=3.0, beta=4.0, kappa=1.0, M=18, p=4, tile=9),
+                     (3000, 11.0, 400)),
+    "default_tile9_M18_p4": (dict(L=12.7, alpha=1.0, r_cut=3.0, beta=4.0, kappa=1.0, M=18, p=4),
+                             (3000, 12.7, 400)),
+    "tile5_M20_p5": (dict(L=12.5, alpha=1.1, r_cut=3.0, beta=1.125, kappa=0.8, M=20, p=5, tile=5),
+                     (2500, 12.5, 400)),
+    "tile15_M30_p3": (dict(L=18.0, alpha=1.0, r_cut=3.0, beta=4.0, kappa=1.0, M=30, p=3, tile=15),
+                      (4000, 18.0, 400)),
     # grids from n = 128 on: FP32 plans with the composite radices 16, 20, 12
     "radix16_M64_p4": (dict(L=20.0, alpha=1.0, r_cut=3.0, beta=4.0, kappa=1.0, M=64, p=4), (2000, 20.0, 400)),
     "radix20_M80_p3": (dict(L=24.0, alpha=1.0, r_cut=3.0, beta=4.0, kappa=1.0, M=80, p=3), (2500, 24.0, 400)),
@@ -122,6 +133,15 @@ def test_energy_forces_parity(enuf, name, prec):
     # uncharged beads get exactly zero force
     assert np.all(F[q == 0] == 0.0)
     plan.close()
+
+
+def test_default_tile_can_be_odd(enuf):
+    """The plan's own tile choice at n = 36, r_c n / L = 8.5: T = 9."""
+    P, _, _ = _case("default_tile9_M18_p4")
+    for prec in ("fp32", "fp64"):
+        plan = enuf.Plan(enuf.make_params(prec=prec, **P), 100)
+        assert (plan.info.n, plan.info.tile, plan.info.n_tiles) == (36, 9, 64)
+        plan.close()
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
