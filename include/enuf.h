@@ -113,7 +113,7 @@ typedef struct {
  * (Table 2 step 4). cuda_stream is a cudaStream_t (NULL: the plan creates
  * its own). Allocates the plan's device workspace and builds the FP64
  * influence/deconvolution table on the host. Errors: ENUF_ERR_INVALID for
- * n_max < 0, L <= 0, alpha <= 0, r_c outside (0, L/2], odd or too small M,
+ * n_max outside [0, 2^29], L <= 0, alpha <= 0, r_c outside (0, L/2], odd or too small M,
  * p outside [1, 8], sigma_s != 2, kappa not finite; ENUF_ERR_UNSUPPORTED when
  * no tile edge divides n; ENUF_ERR_OOM / ENUF_ERR_CUDA. *out is NULL on error. */
 enuf_status enuf_plan(const enuf_params* params, int n_max, void* cuda_stream, enuf_plan_t* out);

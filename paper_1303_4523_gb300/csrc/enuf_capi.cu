@@ -19,6 +19,7 @@ using namespace enuf;
 namespace {
 
 constexpr int kMaxTiles = 32768;      // shared-memory histogram limit (128 KB)
+constexpr int kMaxBeads = 1 << 29;    // the kernels index per-bead components as int (3 i + 2, 4 i + 3)
 constexpr int kMaxSmem = 200 * 1024;  // dynamic shared memory the kernels may request
 constexpr int kSMs = 152;
 
@@ -199,7 +200,7 @@ void slater_kernel(double alpha, double beta, double r, double* out) {
 }
 
 enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* bytes) {
-    if (n_max < 0) return fail(plan, ENUF_ERR_INVALID, "n_max < 0");
+    if (n_max < 0 || n_max > kMaxBeads) return fail(plan, ENUF_ERR_INVALID, "n_max = %d outside [0, 2^29]", n_max);
     if (!(P.L > 0) || !std::isfinite(P.L)) return fail(plan, ENUF_ERR_INVALID, "L must be > 0");
     if (!(P.alpha > 0) || !std::isfinite(P.alpha)) return fail(plan, ENUF_ERR_INVALID, "alpha must be > 0");
     if (!(P.r_cut > 0) || P.r_cut > 0.5 * P.L) return fail(plan, ENUF_ERR_INVALID, "r_cut must be in (0, L/2]");

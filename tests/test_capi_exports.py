@@ -57,6 +57,15 @@ def test_status_strings_and_invalid_params_without_gpu():
             assert e.status == 1, bad
         else:
             raise AssertionError(f"accepted {bad}")
+    # bead capacity: per-bead components are indexed as int, so n_max <= 2^29
+    assert enuf.enuf_footprint(ok, 1 << 29) > 16 * (1 << 29)
+    for bad_n in (-1, (1 << 29) + 1):
+        try:
+            enuf.enuf_footprint(ok, bad_n)
+        except enuf.EnufError as e:
+            assert e.status == 1, bad_n
+        else:
+            raise AssertionError(f"accepted n_max = {bad_n}")
     # a grid with a prime factor other than 2, 3, 5 is unsupported
     try:
         enuf.enuf_footprint(enuf.make_params(L=30.0, alpha=0.975, r_cut=3.0, beta=4.0, kappa=1.1, M=14, p=4), 10)
