@@ -952,15 +952,16 @@ enuf_status dpd_create(enuf_plan_t plan, const dpd_params* params, int n, const 
     d.cinv = (double)d.ncd / L;
     d.xmaxf = largest_float_below(L);
     const size_t rs = plan->rsz;
+    const size_t nz = (size_t)n;
     d.nbonds = n_bonds;
     size_t off = 0;
     auto take = [&](size_t b) { size_t o = off; off += align256(b); return o; };
-    const size_t o_pos = take(n * 3 * rs), o_vel = take(n * 3 * rs), o_v0 = take(n * 3 * rs),
-                 o_F = take(n * 3 * rs), o_q = take(n * rs), o_type = take(n * 4),
+    const size_t o_pos = take(nz * 3 * rs), o_vel = take(nz * 3 * rs), o_v0 = take(nz * 3 * rs),
+                 o_F = take(nz * 3 * rs), o_q = take(nz * rs), o_type = take(nz * 4),
                  o_atab = take((size_t)d.ntypes * d.ntypes * rs), o_bnd = take(std::max<size_t>(1, (size_t)n_bonds) * 8),
-                 o_ckey = take(n * 4),
+                 o_ckey = take(nz * 4),
                  o_ccount = take((size_t)d.ncells * 4), o_cstart = take(((size_t)d.ncells + 1) * 4),
-                 o_ccur = take(((size_t)d.ncells + 1) * 4), o_sp = take(n * 4 * rs), o_sv = take(n * 4 * rs),
+                 o_ccur = take(((size_t)d.ncells + 1) * 4), o_sp = take(nz * 4 * rs), o_sv = take(nz * 4 * rs),
                  o_step = take(8);
     cudaError_t e = cudaMalloc(&sys->dmem, off);
     if (e != cudaSuccess) {
@@ -982,10 +983,10 @@ enuf_status dpd_create(enuf_plan_t plan, const dpd_params* params, int n, const 
         if (rs == 4) reinterpret_cast<float*>(at.data())[k] = (float)params->a[k];
         else reinterpret_cast<double*>(at.data())[k] = params->a[k];
     }
-    if (cudaMemcpy(d.pos, pos, n * 3 * rs, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(d.vel, vel, n * 3 * rs, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(d.q, q, n * rs, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(d.type, type, n * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+    if (cudaMemcpy(d.pos, pos, nz * 3 * rs, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d.vel, vel, nz * 3 * rs, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d.q, q, nz * rs, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d.type, type, nz * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(d.atab, at.data(), at.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         (n_bonds > 0 && cudaMemcpy(d.bnd, bonds, (size_t)n_bonds * 8, cudaMemcpyHostToDevice) != cudaSuccess))
         return bail(fail(plan, ENUF_ERR_CUDA, "upload failed"));
