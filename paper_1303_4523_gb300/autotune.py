@@ -178,9 +178,16 @@ def tune(params: enuf.enuf_params, n_max: int, pos, q, measure: Callable | None 
         raise enuf.EnufError(enuf.ENUF_ERR_UNSUPPORTED, "no legal tile for these parameters")
     timings = []
     for c in cands:
-        ms = float(measure(_copy(params, **c), n_max, pos, q))
+        try:
+            ms = float(measure(_copy(params, **c), n_max, pos, q))
+        except enuf.EnufError as e:      # e.g. no device memory for this shape: skip it
+            timings.append(dict(c, ms=None, error=str(e)))
+            continue
         timings.append(dict(c, ms=ms))
-    best = min(timings, key=lambda t: t["ms"])
+    done = [t for t in timings if t["ms"] is not None]
+    if not done:
+        raise enuf.EnufError(enuf.ENUF_ERR_UNSUPPORTED, "every candidate failed: " + timings[0]["error"])
+    best = min(done, key=lambda t: t["ms"])
     entry = {k: best[k] for k in CHOICES}
     entry.update(ms=best["ms"], timings=timings)
     cache.put(key, entry)

@@ -167,3 +167,24 @@ def test_tune_picks_the_radix_schedule(mods, tmp_path):
     assert (r["tile"], r["fft_path"], r["fft_radix"]) == (5, 0, 1)
     tp = A.cached_params(params, 100, cache=A.TuneCache(str(tmp_path / "t.json")), device="dev")
     assert (tp.tile, tp.fft_radix) == (5, 1)
+
+
+def test_a_failing_candidate_is_skipped(mods, tmp_path):
+    A, E = mods
+    params = E.make_params(prec="fp64", **BASE)
+
+    def cost(p, *a):
+        if p.tile == 4:
+            raise E.EnufError(E.ENUF_ERR_OOM, "no room")
+        return float(p.tile)
+
+    r = A.tune(params, 1000, None, _q(), measure=cost, cache=A.TuneCache(str(tmp_path / "t.json")), device="dev")
+    assert r["tile"] == 6
+    failed = [t for t in r["timings"] if t["ms"] is None]
+    assert [t["tile"] for t in failed] == [4] and "no room" in failed[0]["error"]
+
+    def broken(p, *a):
+        raise E.EnufError(E.ENUF_ERR_OOM, "no room")
+
+    with pytest.raises(E.EnufError):
+        A.tune(params, 1000, None, _q(), measure=broken, cache=A.TuneCache(str(tmp_path / "u.json")), device="dev")
