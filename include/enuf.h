@@ -181,6 +181,14 @@ int enuf_launches_per_eval(enuf_plan_t plan);
 enuf_status enuf_check_word(enuf_plan_t plan, unsigned int* mask, int reset);
 /* 1 when the library was built with the device index checks, else 0. */
 int enuf_built_with_checks(void);
+/* Failure injection for tests, on the host: of the library's device
+ * allocations (a plan's workspace, the host-buffer staging of
+ * enuf_energy_forces_host, a DPD system's state) the next `after` proceed and
+ * the `count` that follow fail as if the device were out of memory, without
+ * calling the allocator; the call that made one returns ENUF_ERR_OOM and
+ * frees what it held. count = 0 ends the injection. Process-wide.
+ * Errors: ENUF_ERR_INVALID for a negative argument. */
+enuf_status enuf_debug_fail_allocs(int after, int count);
 
 void enuf_destroy(enuf_plan_t plan);
 const char* enuf_status_string(enuf_status s);

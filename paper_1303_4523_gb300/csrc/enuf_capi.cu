@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -24,6 +25,33 @@ constexpr int kMaxSmem = 200 * 1024;  // dynamic shared memory the kernels may r
 constexpr int kSMs = 152;
 
 bool g_configured[2] = {false, false};
+
+// Failure injection on the host (enuf_debug_fail_allocs): after g_fail_after
+// more device allocations of plans, host-buffer staging and DPD systems, the
+// next g_fail_count report cudaErrorMemoryAllocation without calling
+// cudaMalloc, so the out-of-memory paths run without exhausting the device.
+std::mutex g_fail_mu;
+int g_fail_after = 0, g_fail_count = 0;
+
+cudaError_t dev_alloc(void** p, size_t bytes) {
+    bool inject = false;
+    {
+        std::lock_guard<std::mutex> lock(g_fail_mu);
+        if (g_fail_count > 0) {
+            if (g_fail_after > 0) {
+                --g_fail_after;
+            } else {
+                --g_fail_count;
+                inject = true;
+            }
+        }
+    }
+    if (inject) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -663,7 +691,7 @@ enuf_status enuf_plan(const enuf_params* params, int n_max, void* cuda_stream, e
     for (int i = 0; i < kStageCount; ++i)
         if (cudaEventCreate(&plan->ev.start[i]) != cudaSuccess || cudaEventCreate(&plan->ev.stop[i]) != cudaSuccess)
             return bail(fail(plan, ENUF_ERR_CUDA, "event create failed"));
-    cudaError_t e = cudaMalloc(&plan->dmem, plan->dbytes);
+    cudaError_t e = dev_alloc(&plan->dmem, plan->dbytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         plan->dmem = nullptr;
@@ -711,6 +739,14 @@ int enuf_built_with_checks(void) {
 #endif
 }
 
+enuf_status enuf_debug_fail_allocs(int after, int count) {
+    if (after < 0 || count < 0) return ENUF_ERR_INVALID;
+    std::lock_guard<std::mutex> lock(g_fail_mu);
+    g_fail_after = after;
+    g_fail_count = count;
+    return ENUF_OK;
+}
+
 enuf_status enuf_energy_forces(enuf_plan_t plan, int n, const void* pos, const void* q, void* F, double* E,
                                double* virial) {
     if (!plan) return ENUF_ERR_INVALID;
@@ -739,7 +775,7 @@ enuf_status enuf_energy_forces_host(enuf_plan_t plan, int n, const void* pos, co
     if (n > 0 && (!pos || !q || !F)) return fail(plan, ENUF_ERR_INVALID, "null array");
     const size_t nm = (size_t)std::max(plan->n_max, 1);
     if (!plan->stage) {
-        cudaError_t e = cudaMalloc(&plan->stage, align256(nm * 3 * plan->rsz) * 2 + align256(nm * plan->rsz));
+        cudaError_t e = dev_alloc(&plan->stage, align256(nm * 3 * plan->rsz) * 2 + align256(nm * plan->rsz));
         if (e != cudaSuccess) {
             cudaGetLastError();
             plan->stage = nullptr;
@@ -963,7 +999,7 @@ enuf_status dpd_create(enuf_plan_t plan, const dpd_params* params, int n, const 
                  o_ccount = take((size_t)d.ncells * 4), o_cstart = take(((size_t)d.ncells + 1) * 4),
                  o_ccur = take(((size_t)d.ncells + 1) * 4), o_sp = take(nz * 4 * rs), o_sv = take(nz * 4 * rs),
                  o_step = take(8);
-    cudaError_t e = cudaMalloc(&sys->dmem, off);
+    cudaError_t e = dev_alloc(&sys->dmem, off);
     if (e != cudaSuccess) {
         cudaGetLastError();
         delete sys;

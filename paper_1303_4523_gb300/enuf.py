@@ -82,6 +82,7 @@ def _load():
         "dpd_step_host": (st, [vp, C.c_int, vp, vp, vp, C.POINTER(C.c_double)]),
         "enuf_check_word": (st, [vp, C.POINTER(C.c_uint), C.c_int]),
         "enuf_built_with_checks": (C.c_int, []),
+        "enuf_debug_fail_allocs": (st, [i, i]),
         "dpd_device_state": (st, [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp)]),
         "dpd_destroy": (None, [vp]),
         "enuf_batch_plan": (st, [i, C.POINTER(enuf_params), C.POINTER(C.c_int), vp, C.POINTER(vp)]),
@@ -104,7 +105,7 @@ EXPORTED = ("enuf_plan", "enuf_footprint", "enuf_get_info", "enuf_energy_forces"
             "enuf_stage_time", "enuf_launches_per_eval", "enuf_destroy", "enuf_status_string",
             "enuf_last_error", "dpd_create", "dpd_step", "dpd_get_state", "dpd_set_state",
             "dpd_get_forces", "dpd_step_host", "dpd_device_state", "enuf_check_word",
-            "enuf_built_with_checks", "dpd_destroy", "enuf_batch_plan",
+            "enuf_built_with_checks", "enuf_debug_fail_allocs", "dpd_destroy", "enuf_batch_plan",
             "enuf_batch_energy_forces", "enuf_batch_launches", "enuf_batch_destroy",
             "enuf_spread_noalloc")
 
@@ -169,6 +170,12 @@ class _Fence:
         if self.s is not None:
             self.cur.wait_stream(self.s)
         return False
+
+
+def debug_fail_allocs(count: int, after: int = 0) -> None:
+    """Failure injection: after `after` more device allocations of the
+    library, the next `count` fail as out of memory (count 0 ends it)."""
+    _check(lib.enuf_debug_fail_allocs(int(after), int(count)), what="enuf_debug_fail_allocs")
 
 
 def enuf_footprint(params: enuf_params, n_max: int) -> int:

@@ -66,6 +66,16 @@ def test_status_strings_and_invalid_params_without_gpu():
             assert e.status == 1, bad_n
         else:
             raise AssertionError(f"accepted n_max = {bad_n}")
+    # the allocation-failure injection is host state: set and cleared without a GPU
+    enuf.debug_fail_allocs(2, after=1)
+    enuf.debug_fail_allocs(0)
+    for bad_args in ((-1, 0), (0, -1)):
+        try:
+            enuf.debug_fail_allocs(*bad_args)
+        except enuf.EnufError as e:
+            assert e.status == 1
+        else:
+            raise AssertionError(f"accepted {bad_args}")
     # a grid with a prime factor other than 2, 3, 5 is unsupported
     try:
         enuf.enuf_footprint(enuf.make_params(L=30.0, alpha=0.975, r_cut=3.0, beta=4.0, kappa=1.1, M=14, p=4), 10)
