@@ -123,6 +123,11 @@ enuf_status enuf_footprint(const enuf_params* params, int n_max, size_t* bytes);
 
 enuf_status enuf_get_info(enuf_plan_t plan, enuf_plan_info* info);
 
+/* The derived sizes a plan with these parameters would have (info as
+ * enuf_get_info gives it), computed on the host: no device, no allocation.
+ * Errors: those of enuf_plan's parameter validation. */
+enuf_status enuf_plan_shape(const enuf_params* params, int n_max, enuf_plan_info* info);
+
 /* Electrostatic energy and forces (Eq. 16-25; Table 2 step 4).
  *   n      : number of beads, 0 <= n <= n_max
  *   pos    : device real[n][3]

@@ -15,8 +15,9 @@ is cut, but not what is computed (results agree to rounding):
             n = 128 on take composite radices (6, 10, 12, 16, 20) when that
             saves a stage; fft_radix = 1 keeps radices 2, 3, 4, 5, 8.
 
-The library's own host validation (enuf_footprint) decides which tiles are
-legal, so the candidates never include a launch shape the plan would reject.
+The library's own host logic (enuf_plan_shape) decides which tiles are legal
+and which choices differ, so the candidates never include a launch shape the
+plan would reject, nor two that run the same kernels.
 Each candidate is timed on the device with CUDA events over repeated
 evaluations of the caller's system; the fastest is kept in a JSON cache keyed
 by everything that fixes the kernels' shapes and work: device name,
@@ -67,24 +68,35 @@ def grid_n(params: enuf.enuf_params) -> int:
     return params.sigma_s * M
 
 
-def _legal(params: enuf.enuf_params, n_max: int) -> bool:
+def _shape(params: enuf.enuf_params, n_max: int):
+    """(tile, FFT kernels, radix schedule) of the plan, or None if it is rejected."""
     try:
-        enuf.enuf_footprint(params, n_max)
+        info = enuf.plan_shape(params, n_max)
     except enuf.EnufError:
-        return False
-    return True
+        return None
+    return info.tile, info.fft_kernels, tuple(info.fft_radix[:info.fft_stages])
 
 
 def candidates(params: enuf.enuf_params, n_max: int) -> list[dict]:
     """Every (tile, fft_path, fft_radix) the plan accepts for these
-    parameters; the FFT choices only where they select different kernels."""
+    parameters, one per distinct launch shape: the FFT choices only where
+    they select different kernels or radix schedules."""
     n = grid_n(params)
-    tiles = [T for T in range(max(1, params.p), MAX_TILE + 1)
-             if n % T == 0 and _legal(_copy(params, tile=T), n_max)]
     fp32 = params.prec == enuf.ENUF_FP32
     paths = [0, 1] if fp32 and n <= FUSED_FFT_MAX_N else [0]
     radices = [0, 1] if fp32 and n >= COMPOSITE_MIN_N else [0]
-    return [{"tile": T, "fft_path": f, "fft_radix": r} for T in tiles for f in paths for r in radices]
+    out, seen = [], set()
+    for T in range(max(1, params.p), MAX_TILE + 1):
+        if n % T:
+            continue
+        for f in paths:
+            for r in radices:
+                c = {"tile": T, "fft_path": f, "fft_radix": r}
+                shape = _shape(_copy(params, **c), n_max)
+                if shape is not None and shape not in seen:
+                    seen.add(shape)
+                    out.append(c)
+    return out
 
 
 def cache_key(params: enuf.enuf_params, n_charged: int, device: str = "") -> str:

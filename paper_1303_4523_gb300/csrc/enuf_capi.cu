@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -708,8 +709,7 @@ enuf_status enuf_plan(const enuf_params* params, int n_max, void* cuda_stream, e
     return ENUF_OK;
 }
 
-enuf_status enuf_get_info(enuf_plan_t plan, enuf_plan_info* info) {
-    if (!plan || !info) return ENUF_ERR_INVALID;
+static void fill_info(const enuf_plan_s* plan, enuf_plan_info* info) {
     info->M = plan->P.M;
     info->n = plan->g.n;
     info->n_c = plan->g.nc;
@@ -720,6 +720,21 @@ enuf_status enuf_get_info(enuf_plan_t plan, enuf_plan_info* info) {
     info->device_bytes = plan->dbytes;
     info->fft_stages = plan->fp.nst;
     for (int i = 0; i < 8; ++i) info->fft_radix[i] = i < plan->fp.nst ? plan->fp.rad[i] : 0;
+}
+
+enuf_status enuf_get_info(enuf_plan_t plan, enuf_plan_info* info) {
+    if (!plan || !info) return ENUF_ERR_INVALID;
+    fill_info(plan, info);
+    return ENUF_OK;
+}
+
+enuf_status enuf_plan_shape(const enuf_params* params, int n_max, enuf_plan_info* info) {
+    if (!params || !info) return ENUF_ERR_INVALID;
+    std::unique_ptr<enuf_plan_s> tmp(new (std::nothrow) enuf_plan_s());
+    if (!tmp) return ENUF_ERR_OOM;
+    const enuf_status st = derive(tmp.get(), *params, n_max, nullptr);
+    if (st != ENUF_OK) return st;
+    fill_info(tmp.get(), info);
     return ENUF_OK;
 }
 

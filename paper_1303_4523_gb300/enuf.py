@@ -64,6 +64,7 @@ def _load():
         "enuf_plan": (st, [C.POINTER(enuf_params), i, vp, C.POINTER(vp)]),
         "enuf_footprint": (st, [C.POINTER(enuf_params), i, C.POINTER(C.c_size_t)]),
         "enuf_get_info": (st, [vp, C.POINTER(enuf_plan_info)]),
+        "enuf_plan_shape": (st, [C.POINTER(enuf_params), i, C.POINTER(enuf_plan_info)]),
         "enuf_energy_forces": (st, [vp, i, vp, vp, vp, pd, pd]),
         "enuf_energy_forces_host": (st, [vp, i, vp, vp, vp, pd, pd]),
         "enuf_last_energies": (st, [vp, pd, pd]),
@@ -100,7 +101,8 @@ def _load():
 
 lib = _load()
 
-EXPORTED = ("enuf_plan", "enuf_footprint", "enuf_get_info", "enuf_energy_forces", "enuf_last_energies",
+EXPORTED = ("enuf_plan", "enuf_footprint", "enuf_get_info", "enuf_plan_shape", "enuf_energy_forces",
+            "enuf_last_energies",
             "enuf_energy_forces_host", "enuf_debug_buffer", "enuf_enable_timing",
             "enuf_stage_time", "enuf_launches_per_eval", "enuf_destroy", "enuf_status_string",
             "enuf_last_error", "dpd_create", "dpd_step", "dpd_get_state", "dpd_set_state",
@@ -176,6 +178,14 @@ def debug_fail_allocs(count: int, after: int = 0) -> None:
     """Failure injection: after `after` more device allocations of the
     library, the next `count` fail as out of memory (count 0 ends it)."""
     _check(lib.enuf_debug_fail_allocs(int(after), int(count)), what="enuf_debug_fail_allocs")
+
+
+def plan_shape(params: enuf_params, n_max: int) -> enuf_plan_info:
+    """Derived sizes of a plan with these parameters (tile edge, grid, FFT
+    kernels and radices, device bytes), from the host logic alone."""
+    info = enuf_plan_info()
+    _check(lib.enuf_plan_shape(C.byref(params), int(n_max), C.byref(info)), what="enuf_plan_shape")
+    return info
 
 
 def enuf_footprint(params: enuf_params, n_max: int) -> int:

@@ -43,6 +43,10 @@ def test_candidates_are_the_legal_tiles(mods):
     assert {x["fft_path"] for x in c} == {0} and {x["fft_radix"] for x in c} == {0, 1} and len(c) == 10
     c = A.candidates(E.make_params(prec="fp64", **big), 375000)
     assert {x["fft_radix"] for x in c} == {0} and len(c) == 5
+    # n = 512: only tile 16 keeps the histogram within 32768 tiles, and the composite
+    # schedule saves no stage there (16 16 2 against 8 8 8), so one candidate remains
+    c = A.candidates(E.make_params(prec="fp32", **dict(BASE, L=160.0, M=256)), 1000)
+    assert c == [{"tile": 16, "fft_path": 0, "fft_radix": 0}]
     # a wider window raises the smallest tile
     assert min(x["tile"] for x in A.candidates(E.make_params(prec="fp64", **dict(BASE, p=7)), 100)) == 8
     # every candidate is accepted by the plan's validation, every other tile rejected

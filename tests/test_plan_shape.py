@@ -1,0 +1,95 @@
+"""The plan's derived shape from the host logic alone (enuf_plan_shape): grid
+rule, tile edge, FFT path and radix schedule, workspace bytes. CPU only."""
+import pytest
+
+
+@pytest.fixture(scope="module")
+def enuf():
+    from paper_1303_4523_gb300 import build
+    build.build()
+    from paper_1303_4523_gb300 import enuf as E
+    return E
+
+
+def _shape(enuf, n_max=16, **kw):
+    return enuf.plan_shape(enuf.make_params(**kw), n_max)
+
+
+def _radices(info):
+    return list(info.fft_radix[:info.fft_stages])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_radix_schedules(enuf, prec):
+    """Fewest stages over 2, 3, 4, 5, 8; FP32 grids from n = 128 on take the
+    composite radices 6, 10, 12, 16, 20 when that saves a stage, unless
+    fft_radix = 1."""
+    want = {16: [8, 2], 32: [8, 4], 36: [4, 3, 3], 60: [5, 4, 3], 96: [8, 4, 3], 128: [8, 8, 2],
+            160: [8, 5, 4], 192: [8, 8, 3], 320: [8, 8, 5], 512: [8, 8, 8]}
+    if prec == "fp32":
+        want.update({128: [16, 8], 160: [20, 8], 192: [16, 12], 320: [20, 16]})
+    for n, rad in want.items():
+        kw = dict(prec=prec, L=2.0 * n, alpha=1.0, r_cut=3.0, beta=0.0, kappa=1.0, M=n // 2, p=4)
+        info = _shape(enuf, **kw)
+        assert info.n == n and _radices(info) == rad, (n, _radices(info))
+        prod = 1
+        for r in rad:
+            prod *= r
+        assert prod == n
+        plain = _radices(_shape(enuf, fft_radix=1, **kw))
+        assert all(r in (2, 3, 4, 5, 8) for r in plain) and len(plain) >= len(rad)
+        if prec == "fp64" or n < 128:
+            assert plain == rad
+
+
+def test_fft_path(enuf):
+    """FP32 grids up to n = 112 run the fused plane passes (3 kernels) unless
+    fft_path = 1; FP64 and larger grids run the five line passes."""
+    base = dict(alpha=1.0, r_cut=3.0, beta=4.0, kappa=1.0, p=4)
+    for M, L in ((16, 10.0), (48, 30.0), (54, 33.75)):
+        assert _shape(enuf, prec="fp32", M=M, L=L, **base).fft_kernels == 3
+        assert _shape(enuf, prec="fp32", M=M, L=L, fft_path=1, **base).fft_kernels == 5
+        assert _shape(enuf, prec="fp64", M=M, L=L, **base).fft_kernels == 5
+    assert _shape(enuf, prec="fp32", M=64, L=40.0, **base).fft_kernels == 5
+
+
+def test_tile_rule(enuf):
+    """Default tile: the smallest divisor of n that is >= p and at least r_c
+    wide (so the real-space stencil is 3^3 tiles), within the 24-point limit."""
+    base = dict(alpha=0.975, r_cut=3.0, beta=4.0, kappa=1.1, p=4, prec="fp32")
+    cases = [  # (L, M, tile): r_c n / L grid points
+        (30.0, 48, 12),   # 9.6 -> 12
+        (10.0, 16, 16),   # 9.6 -> 16
+        (12.7, 18, 9),    # 8.5 -> 9 (an odd edge)
+        (12.5, 20, 10),   # 9.6 -> 10
+        (100.0, 160, 10),  # 9.6 -> 10
+        (10.0, 32, 8),    # 19.2: no divisor of 64 in [20, 24] -> 8 (smallest >= 8)
+    ]
+    for L, M, T in cases:
+        info = _shape(enuf, L=L, M=M, **base)
+        assert info.tile == T, (L, M, info.tile)
+        assert info.n % info.tile == 0 and info.n_tiles == (info.n // info.tile) ** 3
+    # an explicit tile is kept
+    assert _shape(enuf, L=30.0, M=48, tile=8, **base).tile == 8
+
+
+def test_bytes_agree_with_footprint(enuf):
+    for kw in (dict(prec="fp32"), dict(prec="fp64"), dict(prec="fp32", deriv=1), dict(prec="fp64", slater_k=1)):
+        params = enuf.make_params(L=30.0, alpha=0.975, r_cut=3.0, beta=4.0, kappa=1.1, M=48, p=4, **kw)
+        assert enuf.plan_shape(params, 81000).device_bytes == enuf.enuf_footprint(params, 81000)
+        assert enuf.plan_shape(params, 81000).n_max == 81000
+    p32 = enuf.make_params(L=30.0, alpha=0.975, r_cut=3.0, beta=4.0, kappa=1.1, M=48, p=4, prec="fp32")
+    p64 = enuf.make_params(L=30.0, alpha=0.975, r_cut=3.0, beta=4.0, kappa=1.1, M=48, p=4, prec="fp64")
+    assert enuf.plan_shape(p32, 81000).device_bytes < enuf.plan_shape(p64, 81000).device_bytes
+    # M = 0: the grid rule's M (1.6 L to the nearest even 2^a 3^b 5^c)
+    info = _shape(enuf, L=30.0, alpha=0.975, r_cut=3.0, beta=4.0, kappa=1.1, M=0, p=4)
+    assert (info.M, info.n, info.n_c) == (48, 96, 23)
+
+
+def test_invalid_parameters_are_reported(enuf):
+    with pytest.raises(enuf.EnufError) as e:
+        _shape(enuf, L=30.0, alpha=0.975, r_cut=3.0, beta=4.0, kappa=1.1, M=47, p=4)
+    assert e.value.status == enuf.ENUF_ERR_INVALID
+    with pytest.raises(enuf.EnufError) as e:
+        _shape(enuf, L=30.0, alpha=0.975, r_cut=3.0, beta=4.0, kappa=1.1, M=14, p=4)
+    assert e.value.status == enuf.ENUF_ERR_UNSUPPORTED

@@ -52,6 +52,11 @@ def test_plan_and_staging_allocations(enuf):
     s, params, pos, q = _setup(enuf)
     plan0 = enuf.Plan(params, s.N)
     F0, E0 = _forces(plan0, pos, q)
+    # the host-only shape query describes the plan that was built
+    shape, info = enuf.plan_shape(params, s.N), plan0.info
+    for f in ("M", "n", "n_c", "tile", "n_tiles", "n_max", "fft_kernels", "device_bytes", "fft_stages"):
+        assert getattr(shape, f) == getattr(info, f), f
+    assert list(shape.fft_radix) == list(info.fft_radix)
     enuf.debug_fail_allocs(1)
     with pytest.raises(enuf.EnufError) as e:
         enuf.Plan(params, s.N)
