@@ -118,6 +118,17 @@ typedef struct {
  * no tile edge divides n; ENUF_ERR_OOM / ENUF_ERR_CUDA. *out is NULL on error. */
 enuf_status enuf_plan(const enuf_params* params, int n_max, void* cuda_stream, enuf_plan_t* out);
 
+/* Ewald parameters from a required accuracy delta (0 < delta < 1), by the two
+ * conditions of Eq. 29: alpha is the smallest value with
+ * erfc(alpha r_c) <= delta (the exact left side of the real-space condition),
+ * and the base grid M = 2 (n_c + 1) with n_c >= (alpha L / pi) sqrt(-ln delta),
+ * rounded up to an even 2^a 3^b 5^c integer. Reads params->L and
+ * params->r_cut; writes params->alpha and params->M, leaves the rest.
+ * Host only. Errors: ENUF_ERR_INVALID for delta outside (0, 1), L <= 0 or
+ * r_c outside (0, L/2]; ENUF_ERR_UNSUPPORTED when the grid would exceed
+ * n = 1024. */
+enuf_status enuf_accuracy_params(double delta, enuf_params* params);
+
 /* Device bytes a plan with these parameters would hold (admission control). */
 enuf_status enuf_footprint(const enuf_params* params, int n_max, size_t* bytes);
 

@@ -650,6 +650,29 @@ const char* enuf_status_string(enuf_status s) {
 
 const char* enuf_last_error(enuf_plan_t plan) { return plan ? plan->err : "no plan"; }
 
+enuf_status enuf_accuracy_params(double delta, enuf_params* params) {
+    if (!params || !(delta > 0.0 && delta < 1.0)) return ENUF_ERR_INVALID;
+    const double L = params->L, rc = params->r_cut;
+    if (!(L > 0.0) || !(rc > 0.0) || rc > 0.5 * L) return ENUF_ERR_INVALID;
+    // Eq. 29, real space: the smallest alpha with erfc(alpha r_c) <= delta
+    // (erfc falls monotonically; bisection on alpha r_c in [0, 40])
+    double lo = 0.0, hi = 40.0;
+    for (int it = 0; it < 200 && hi - lo > 1e-15 * hi; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        (std::erfc(mid) <= delta ? hi : lo) = mid;
+    }
+    const double alpha = hi / rc;
+    // Eq. 29, reciprocal space: n_c >= (alpha L / pi) sqrt(-ln delta); the
+    // base grid keeps n_c = M/2 - 1, rounded up to an even 2^a 3^b 5^c M
+    const int nc = (int)std::ceil(alpha * L / M_PI * std::sqrt(-std::log(delta)) - 1e-12);
+    int M = 2 * (nc + 1);
+    while (!smooth(M)) M += 2;
+    if (2 * M > 1024) return ENUF_ERR_UNSUPPORTED;
+    params->alpha = alpha;
+    params->M = M;
+    return ENUF_OK;
+}
+
 enuf_status enuf_footprint(const enuf_params* params, int n_max, size_t* bytes) {
     if (!params || !bytes) return ENUF_ERR_INVALID;
     return derive(nullptr, *params, n_max, bytes);

@@ -65,6 +65,7 @@ def _load():
         "enuf_footprint": (st, [C.POINTER(enuf_params), i, C.POINTER(C.c_size_t)]),
         "enuf_get_info": (st, [vp, C.POINTER(enuf_plan_info)]),
         "enuf_plan_shape": (st, [C.POINTER(enuf_params), i, C.POINTER(enuf_plan_info)]),
+        "enuf_accuracy_params": (st, [d, C.POINTER(enuf_params)]),
         "enuf_energy_forces": (st, [vp, i, vp, vp, vp, pd, pd]),
         "enuf_energy_forces_host": (st, [vp, i, vp, vp, vp, pd, pd]),
         "enuf_last_energies": (st, [vp, pd, pd]),
@@ -101,7 +102,8 @@ def _load():
 
 lib = _load()
 
-EXPORTED = ("enuf_plan", "enuf_footprint", "enuf_get_info", "enuf_plan_shape", "enuf_energy_forces",
+EXPORTED = ("enuf_plan", "enuf_footprint", "enuf_get_info", "enuf_plan_shape", "enuf_accuracy_params",
+            "enuf_energy_forces",
             "enuf_last_energies",
             "enuf_energy_forces_host", "enuf_debug_buffer", "enuf_enable_timing",
             "enuf_stage_time", "enuf_launches_per_eval", "enuf_destroy", "enuf_status_string",
@@ -178,6 +180,15 @@ def debug_fail_allocs(count: int, after: int = 0) -> None:
     """Failure injection: after `after` more device allocations of the
     library, the next `count` fail as out of memory (count 0 ends it)."""
     _check(lib.enuf_debug_fail_allocs(int(after), int(count)), what="enuf_debug_fail_allocs")
+
+
+def accuracy_params(delta: float, params: enuf_params) -> enuf_params:
+    """A copy of params with alpha and M chosen for accuracy delta by the two
+    conditions of Eq. 29 (from params.L and params.r_cut)."""
+    out = enuf_params()
+    C.memmove(C.byref(out), C.byref(params), C.sizeof(enuf_params))
+    _check(lib.enuf_accuracy_params(float(delta), C.byref(out)), what="enuf_accuracy_params")
+    return out
 
 
 def plan_shape(params: enuf_params, n_max: int) -> enuf_plan_info:
