@@ -93,3 +93,22 @@ def test_invalid_parameters_are_reported(enuf):
     with pytest.raises(enuf.EnufError) as e:
         _shape(enuf, L=30.0, alpha=0.975, r_cut=3.0, beta=4.0, kappa=1.1, M=14, p=4)
     assert e.value.status == enuf.ENUF_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("L,M", [(10.0, 16), (20.0, 32), (30.0, 48), (40.0, 64), (50.0, 80), (100.0, 160),
+                                 (11.0, 18), (12.5, 20), (15.0, 24)])
+def test_grid_rule(enuf, L, M):
+    """M = 0: 1.6 L rounded to the nearest even 2^a 3^b 5^c integer (one grid
+    point per 0.6 R_c of the base grid; n_c = 7 at L = 10)."""
+    info = _shape(enuf, L=L, alpha=0.975, r_cut=3.0, beta=4.0, kappa=1.1, M=0, p=4)
+    assert info.M == M and info.n == 2 * M and info.n_c == M // 2 - 1
+
+
+def test_real_space_stencil_limit(enuf):
+    """A tile narrower than r_c / 5 would make the real-space stencil more
+    than 1024 tiles (11^3 here): the plan refuses it as unsupported."""
+    base = dict(L=20.0, alpha=1.0, r_cut=3.0, beta=4.0, kappa=1.0, M=64, p=4, prec="fp32")
+    with pytest.raises(enuf.EnufError) as e:
+        _shape(enuf, tile=4, **base)
+    assert e.value.status == enuf.ENUF_ERR_UNSUPPORTED
+    assert _shape(enuf, tile=8, **base).tile == 8        # 7^3 tiles
