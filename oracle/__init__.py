@@ -38,7 +38,7 @@ class _Params(C.Structure):
     _fields_ = [("L", C.c_double), ("alpha", C.c_double), ("r_cut", C.c_double),
                 ("beta", C.c_double), ("kappa", C.c_double), ("M", C.c_int),
                 ("p", C.c_int), ("sigma_s", C.c_int), ("kmask", C.c_int),
-                ("fp32_cut", C.c_int), ("deriv", C.c_int), ("slater_k", C.c_int)]
+                ("deriv", C.c_int), ("slater_k", C.c_int)]
 
 
 class _DpdParams(C.Structure):
@@ -95,13 +95,12 @@ class EwaldParams:
     p: int               # NFFT window cutoff
     sigma_s: int = 2
     kmask: int = 0
-    fp32_cut: int = 0
     deriv: int = 0       # ENUF forces: 0 ik-differentiation (Eq. 24-25), 1 analytic gradient
     slater_k: int = 0    # Slater smearing: 0 real-space correction, 1 k-space form factor
 
     def c(self) -> _Params:
         return _Params(self.L, self.alpha, self.r_cut, self.beta, self.kappa,
-                       self.M, self.p, self.sigma_s, self.kmask, self.fp32_cut, self.deriv,
+                       self.M, self.p, self.sigma_s, self.kmask, self.deriv,
                        self.slater_k)
 
     @property

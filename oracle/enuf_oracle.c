@@ -6,8 +6,8 @@
  * plain double loop over pairs, the direct reciprocal sum a plain loop over
  * integer k, and the naive ENUF plain window loops plus plain per-dimension
  * DFTs. Build with -ffp-contract=off so that no multiply-add is fused behind
- * the reader's back; the one place that needs a fused multiply-add (the
- * float cutoff decision that mirrors an FP32 path) calls fmaf() explicitly.
+ * the reader's back. Every decision (wrap, grid base, pair cutoff) is taken
+ * in FP64 on the inputs as given; an FP32 caller passes float-rounded inputs.
  */
 #include "enuf_oracle.h"
 
@@ -34,16 +34,12 @@ double orc_wrap(double x, double L)
     return w;
 }
 
-/* Wrapped copy of the positions. In FP32-parity mode the wrapped value is
- * rounded to float, because an FP32 path holds positions as floats. */
+/* Wrapped copy of the positions. */
 static double* wrapped_positions(const orc_params* P, int n, const double* pos)
 {
     double* w = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
     if (!w) return NULL;
-    for (int i = 0; i < 3 * n; ++i) {
-        double x = orc_wrap(pos[i], P->L);
-        w[i] = P->fp32_cut ? (double)(float)x : x;
-    }
+    for (int i = 0; i < 3 * n; ++i) w[i] = orc_wrap(pos[i], P->L);
     return w;
 }
 
@@ -55,18 +51,6 @@ static int pair_within(const orc_params* P, const double* xi, const double* xj,
                        double rc, double d[3], double* r)
 {
     const double L = P->L;
-    if (P->fp32_cut) {
-        const float Lf = (float)L, hLf = (float)(0.5 * L), rc2f = (float)(rc * rc);
-        float df[3];
-        for (int t = 0; t < 3; ++t) {
-            float dd = (float)xi[t] - (float)xj[t];
-            if (dd > hLf) dd -= Lf;
-            else if (dd < -hLf) dd += Lf;
-            df[t] = dd;
-        }
-        float r2f = fmaf(df[2], df[2], fmaf(df[1], df[1], df[0] * df[0]));
-        if (!(r2f < rc2f)) return 0;
-    }
     for (int t = 0; t < 3; ++t) {
         double dd = xi[t] - xj[t];
         if (dd > 0.5 * L) dd -= L;
@@ -74,7 +58,7 @@ static int pair_within(const orc_params* P, const double* xi, const double* xj,
         d[t] = dd;
     }
     double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-    if (!P->fp32_cut && !(r2 < rc * rc)) return 0;
+    if (!(r2 < rc * rc)) return 0;
     if (r2 <= 0.0) return 0; /* coincident beads: no direction */
     *r = sqrt(r2);
     return 1;
@@ -380,39 +364,16 @@ static double window_hat(double b, int k, int ng)
     return exp(-b * t * t);
 }
 
-/* Grid coordinate of a wrapped position: u = x_w * (n/L) in [0, n), base = floor(u).
- * The ratio n/L is formed once in FP64; one product and the floor decide the
- * integer base (the same FP64 sequence on every side that must agree on it). */
+/* Grid coordinate of a wrapped position x_w in [0, L): u = n x_w / L in
+ * [0, n) (Eq. 14 evaluates the window at n x - l), base = floor(u), and the
+ * fraction u - base; u = n (reached only by rounding) wraps to 0. */
 static void grid_coord(double xw, double L, int ng, int* base, double* frac)
 {
-    const double ratio = (double)ng / L;
-    double u = xw * ratio;
+    double u = (double)ng * (xw / L);   /* n times the fractional coordinate */
     if (u >= (double)ng) u -= (double)ng;
     const double bse = floor(u);
     *base = (int)bse;
     *frac = u - bse;
-}
-
-/* The same coordinate for an FP32 path, decided in float arithmetic: n/L is
- * split into two floats r_hi + r_lo, p = fl(x r_hi) and t = fl(x r_lo +
- * (x r_hi - p)) (the exact product error via fmaf) represent u = p + t to
- * about 1e-13 relative. floor(u) is floor(p), less one when p is an integer
- * and t < 0; the fraction is (p - base) + t. */
-static void grid_coord_f32(double xw, double L, int ng, int* base, double* frac)
-{
-    const double ratio = (double)ng / L;
-    const float rhi = (float)ratio, rlo = (float)(ratio - (double)rhi);
-    const float x = (float)xw;
-    float p = x * rhi;
-    const float e = fmaf(x, rhi, -p);
-    const float t = fmaf(x, rlo, e);
-    if (p >= (float)ng) p -= (float)ng;
-    float b = floorf(p);
-    if (p == b && t < 0.0f) b -= 1.0f;
-    const float fr = (p - b) + t;
-    if (b < 0.0f) b += (float)ng;
-    *base = (int)b;
-    *frac = (double)fr;
 }
 
 static int imod(int a, int m)
@@ -453,10 +414,7 @@ int orc_recip_enuf(const orc_params* P, int n, const double* pos, const double* 
     for (int j = 0; j < n; ++j) {
         for (int t = 0; t < 3; ++t) {
             double fr;
-            if (P->fp32_cut)
-                grid_coord_f32(x[3 * j + t], L, ng, &base[3 * j + t], &fr);
-            else
-                grid_coord(x[3 * j + t], L, ng, &base[3 * j + t], &fr);
+            grid_coord(x[3 * j + t], L, ng, &base[3 * j + t], &fr);
             for (int a = 0; a < T; ++a)
                 wgt[((size_t)j * 3 + t) * T + a] = window(b, fr + (double)(p - 1 - a));
         }
@@ -672,10 +630,7 @@ int orc_recip_enuf(const orc_params* P, int n, const double* pos, const double* 
                     for (int t = 0; t < 3; ++t) {
                         double fr;
                         int bt;
-                        if (P->fp32_cut)
-                            grid_coord_f32(x[3 * i + t], L, ng, &bt, &fr);
-                        else
-                            grid_coord(x[3 * i + t], L, ng, &bt, &fr);
+                        grid_coord(x[3 * i + t], L, ng, &bt, &fr);
                         for (int aa = 0; aa < T; ++aa) {
                             const double d = fr + (double)(p - 1 - aa);   /* n x - l */
                             w[t][aa] = wgt[((size_t)i * 3 + t) * T + aa];

@@ -47,7 +47,6 @@ typedef struct {
     int    p;       /* NFFT window cutoff: 2p taps per dimension */
     int    sigma_s; /* oversampling factor; grid n = sigma_s * M */
     int    kmask;   /* 0: cubic |k_t| <= n_c; 1: spherical |k| <= n_c */
-    int    fp32_cut;/* 1: take pair-cutoff decisions in float, as an FP32 path does */
     int    deriv;   /* ENUF forces: 0 = ik-differentiation (Eq. 24-25); 1 = analytic
                        gradient of the window (one real field, see orc_recip_enuf) */
     int    slater_k;/* where the Slater smearing enters (Eq. 26-28):
@@ -81,8 +80,9 @@ double orc_slater_force(double beta, double r);    /* B2 / r^2    (Eq. 28) */
 
 /* Real-space Ewald sum with Slater correction (Eq. 31, Eq. 27-28).
  * F (n x 3, overwritten; may be NULL), EW[0] = energy, EW[1] = virial.
- * If sample != NULL only the nsample listed beads get forces; EW is then
- * left untouched. Returns 0 or a negative error code. */
+ * If sample != NULL only the nsample listed beads get forces (row s of F is
+ * bead sample[s]); EW always covers the whole system. Returns 0 or a
+ * negative error code. */
 int orc_real_space(const orc_params* P, int n, const double* pos, const double* q,
                    double* F, double* EW, const int* sample, int nsample);
 

@@ -1,9 +1,25 @@
 """GPU parity of the ENUF electrostatics path against the FP64 CPU oracle.
 
 Every comparison calls the CUDA path through the C ABI (libenuf.so via the
-ctypes binding) and the oracle on the same seeded inputs. Tolerances: FP64
-relative RMS force 1e-11 and relative energy 1e-12; FP32 relative RMS force
-1e-5 and relative energy 1e-6 (the stated targets of the FP32 path).
+ctypes binding) and the oracle on the same seeded inputs. The oracle is the
+plain FP64 one for both precisions: an FP32 run hands it the float-rounded
+inputs the GPU saw, and every decision (wrap, grid base, pair cutoff) is the
+oracle's own FP64 one.
+
+Tolerances (forces: the stated targets of the two paths; energies: derived
+from the arithmetic, each component on its own scale):
+- forces, relative RMS over all compared beads: FP64 1e-11, FP32 1e-5;
+- forces, bead by bead: |F_i - R_i| / max(|R_i|, rms_j |R_j|) below 100x the
+  RMS bound, so that a few bad beads cannot hide in the mean;
+- E_real, E_recip, E_self + E_neutral: each against its own magnitude, FP64
+  1e-12, FP32 1e-6 (pair and mode terms are formed in the working precision
+  and summed in FP64; FP32 real-space sums of alternating sign get the scale
+  of their absolute terms, which the oracle cannot give, so the FP32 real
+  part is bounded by 1e-6 of max(|E_real|, |E_self|));
+- E_total against |E_real| + |E_recip| + |E_self + E_neutral|, the scale its
+  rounding follows;
+- the virial W = sum r.f is a sum of force terms and gets the force bound
+  (FP64 1e-11, FP32 1e-5) on the scale |W_real| + |W_recip| + |W_neutral|.
 """
 import math
 
@@ -45,16 +61,23 @@ def _gpu(enuf, prec, P, pos, q, n_max=None):
     return plan, F.double().cpu().numpy(), E, Wv
 
 
-def _oparams(prec, P):
+def _oparams(P):
     """Oracle parameters: the GPU-only tiling and FFT-path choices do not change the result."""
-    return orc.EwaldParams(fp32_cut=1 if prec == "fp32" else 0,
-                           **{k: v for k, v in P.items() if k not in ("tile", "fft_path")})
+    return orc.EwaldParams(**{k: v for k, v in P.items() if k not in ("tile", "fft_path")})
 
 
-def _ref(prec, P, pos, q, sample=None):
-    Po = _oparams(prec, P)
-    F, E, Wv = orc.electrostatics(Po, pos, q, recip="enuf", sample=sample)
-    return F, E, Wv
+class Ref:
+    """The oracle's forces, energies and virial, with the virial's components."""
+
+    def __init__(self, P, pos, q, sample=None):
+        Po = _oparams(P)
+        Fr, ER = orc.real_space(Po, pos, q, sample)
+        Fk, EK, _, _ = orc.recip_enuf(Po, pos, q, sample)
+        ES = orc.self_neutral(Po, q)
+        self.F = Fr + Fk
+        self.E = np.array([ER[0], EK[0], ES[0] + ES[1], ER[0] + EK[0] + ES[0] + ES[1]])
+        self.W = ER[1] + EK[1] + ES[2]
+        self.Wscale = abs(ER[1]) + abs(EK[1]) + abs(ES[2])
 
 
 def _rel_rms(F, R):
@@ -62,14 +85,35 @@ def _rel_rms(F, R):
     return math.sqrt(((F - R) ** 2).sum() / den) if den > 0 else math.sqrt((F ** 2).sum())
 
 
-def _check(prec, F, E, Wv, Fr, Er, Wr):
+def _bead_max(F, R):
+    """Largest per-bead error |F_i - R_i| / max(|R_i|, rms_j |R_j|) over the charged beads."""
+    rn = np.linalg.norm(R, axis=1)
+    keep = rn > 0
+    if not keep.any():
+        return float(np.abs(F).max()) if F.size else 0.0
+    rms = math.sqrt((rn[keep] ** 2).mean())
+    return float((np.linalg.norm(F - R, axis=1)[keep] / np.maximum(rn[keep], rms)).max())
+
+
+def _check_energies(prec, E, Wv, ref):
+    t = TOL[prec]["E"]
+    Er = ref.E
+    own = [abs(Er[0]), abs(Er[1]), abs(Er[2])]
+    if prec == "fp32":
+        own[0] = max(own[0], abs(Er[2]))
+    for k in range(3):
+        assert abs(E[k] - Er[k]) <= t * own[k], (k, E, Er)
+    assert abs(E[3] - Er[3]) <= t * (abs(Er[0]) + abs(Er[1]) + abs(Er[2])), (E, Er)
+    assert abs(Wv - ref.W) <= TOL[prec]["F"] * ref.Wscale, (Wv, ref.W, ref.Wscale)
+
+
+def _check(prec, F, E, Wv, ref, sample=None):
     t = TOL[prec]
+    Fc = F if sample is None else F[sample]
     assert np.all(np.isfinite(F))
-    assert _rel_rms(F, Fr) < t["F"], _rel_rms(F, Fr)
-    scale = max(abs(Er[0]), abs(Er[1]), abs(Er[2]), 1e-300)
-    for k in range(4):
-        assert abs(E[k] - Er[k]) < t["E"] * scale, (k, E, Er)
-    assert abs(Wv - Wr) < 10 * t["E"] * max(abs(Wr), scale)
+    assert _rel_rms(Fc, ref.F) < t["F"], _rel_rms(Fc, ref.F)
+    assert _bead_max(Fc, ref.F) < 100 * t["F"], _bead_max(Fc, ref.F)
+    _check_energies(prec, E, Wv, ref)
 
 
 def _sys_small(pset):
@@ -128,8 +172,7 @@ def test_energy_forces_parity(enuf, name, prec):
     P, pos, q = _case(name)
     pos, q = _inputs(prec, pos, q)
     plan, F, E, Wv = _gpu(enuf, prec, P, pos, q)
-    Fr, Er, Wr = _ref(prec, P, pos, q)
-    _check(prec, F, E, Wv, Fr, Er, Wr)
+    _check(prec, F, E, Wv, Ref(P, pos, q))
     # uncharged beads get exactly zero force
     assert np.all(F[q == 0] == 0.0)
     plan.close()
@@ -170,8 +213,7 @@ def test_five_pass_fft_parity(enuf, name, prec, deriv):
     pos, q = _inputs(prec, pos, q)
     plan, F, E, Wv = _gpu(enuf, prec, P, pos, q)
     assert plan.info.fft_kernels == 5
-    Fr, Er, Wr = _ref(prec, P, pos, q)
-    _check(prec, F, E, Wv, Fr, Er, Wr)
+    _check(prec, F, E, Wv, Ref(P, pos, q))
     plan.close()
 
 
@@ -184,8 +226,7 @@ def test_gradient_mode_parity(enuf, name, prec):
     P = dict(P, deriv=1)
     pos, q = _inputs(prec, pos, q)
     plan, F, E, Wv = _gpu(enuf, prec, P, pos, q)
-    Fr, Er, Wr = _ref(prec, P, pos, q)
-    _check(prec, F, E, Wv, Fr, Er, Wr)
+    _check(prec, F, E, Wv, Ref(P, pos, q))
     assert np.all(F[q == 0] == 0.0)
     h = plan.debug_buffer(enuf.ENUF_BUF_FIELD)
     assert h.shape[0] == 1
@@ -199,7 +240,7 @@ def test_gradient_mode_field_matches_oracle(enuf, prec):
     pos, q = _inputs(prec, pos, q)
     plan, F, E, Wv = _gpu(enuf, prec, P, pos, q)
     h = plan.debug_buffer(enuf.ENUF_BUF_FIELD).astype(np.float64)
-    _, _, _, h_ref = orc.recip_enuf(_oparams(prec, P), pos, q, want_h=True)
+    _, _, _, h_ref = orc.recip_enuf(_oparams(P), pos, q, want_h=True)
     t = TOL[prec]["stage"]
     assert np.abs(h - h_ref).max() < 10 * t * np.abs(h_ref).max()
     plan.close()
@@ -214,7 +255,7 @@ def test_spread_grid_and_fields_match_oracle(enuf, prec):
     plan, F, E, Wv = _gpu(enuf, prec, P, pos, q)
     grid = plan.debug_buffer(enuf.ENUF_BUF_GRID).astype(np.float64)
     h = plan.debug_buffer(enuf.ENUF_BUF_FIELD).astype(np.float64)
-    Po = _oparams(prec, P)
+    Po = _oparams(P)
     _, _, g_ref, h_ref = orc.recip_enuf(Po, pos, q, want_grid=True, want_h=True)
     t = TOL[prec]["stage"]
     assert np.abs(grid - g_ref).max() < t * np.abs(g_ref).max()
@@ -241,17 +282,18 @@ def test_edge_cases(enuf, prec):
     for qq in cases:
         p_, q_ = _inputs(prec, pos, qq)
         plan, F, E, Wv = _gpu(enuf, prec, P, p_, q_, n_max=1000)
-        Fr, Er, Wr = _ref(prec, P, p_, q_)
+        ref = Ref(P, p_, q_)
         if np.all(qq == 0):
             assert np.all(F == 0.0) and np.all(E == 0.0)
         elif np.count_nonzero(qq) == 1:
             # a lone charge feels only the NFFT's spurious self-force (exactly 0 in
             # the Ewald sum): compare on the scale of a unit pair force at r = 1
             f0 = P["kappa"] * 4.0
-            assert np.abs(F - Fr).max() < TOL[prec]["F"] * f0 and np.abs(Fr).max() < 1e-3 * f0
-            assert np.allclose(E, Er, rtol=TOL[prec]["E"], atol=TOL[prec]["E"] * abs(Er[2]))
+            assert np.abs(F - ref.F).max() < TOL[prec]["F"] * f0 and np.abs(ref.F).max() < 1e-3 * f0
+            assert E[0] == 0.0 and ref.E[0] == 0.0
+            _check_energies(prec, E, Wv, ref)
         else:
-            _check(prec, F, E, Wv, Fr, Er, Wr)
+            _check(prec, F, E, Wv, ref)
         plan.close()
 
 
@@ -353,16 +395,15 @@ def test_full_size_sampled(enuf, prec, which):
     rng = np.random.default_rng(9)
     ch = np.nonzero(q)[0]
     sample = np.sort(rng.choice(ch, 256, replace=False))
-    Fr, Er, Wr = _ref(prec, P, pos, q, sample=sample)
-    t = TOL[prec]
-    assert _rel_rms(F[sample], Fr) < t["F"]
-    scale = max(abs(Er[0]), abs(Er[1]))
-    for k in range(4):
-        assert abs(E[k] - Er[k]) < t["E"] * scale, (k, E, Er)
-    # properties at any size: net force (ik differentiation, symmetric mode set)
-    # and zero force on the neutral beads
-    Fk = F.sum(0)
-    assert np.abs(Fk).max() < (1e-8 if prec == "fp64" else 2e-2) * np.abs(F).max()
+    _check(prec, F, E, Wv, Ref(P, pos, q, sample=sample), sample=sample)
+    # properties at any size: the net force vanishes (ik differentiation with
+    # a symmetric mode set, real-space pairs in both directions) up to the
+    # rounding of the per-bead forces, which adds up like a random walk:
+    # |sum F| <= c eps sqrt(N_q) rms|F| with the working precision's eps
+    ch = q != 0
+    rms = math.sqrt((F[ch] ** 2).sum(1).mean())
+    eps = 2.2e-16 if prec == "fp64" else 1.2e-7
+    assert np.abs(F.sum(0)).max() < 1e3 * eps * math.sqrt(ch.sum()) * rms, (F.sum(0), rms)
     assert np.all(F[q == 0] == 0.0)
     plan.close()
 
@@ -377,12 +418,7 @@ def test_full_size_gradient_mode_sampled(enuf, prec):
     plan, F, E, Wv = _gpu(enuf, prec, P, pos, q)
     rng = np.random.default_rng(19)
     sample = np.sort(rng.choice(np.nonzero(q)[0], 256, replace=False))
-    Fr, Er, Wr = _ref(prec, P, pos, q, sample=sample)
-    t = TOL[prec]
-    assert _rel_rms(F[sample], Fr) < t["F"]
-    scale = max(abs(Er[0]), abs(Er[1]))
-    for k in range(4):
-        assert abs(E[k] - Er[k]) < t["E"] * scale, (k, E, Er)
+    _check(prec, F, E, Wv, Ref(P, pos, q, sample=sample), sample=sample)
     assert np.all(F[q == 0] == 0.0)
     plan.close()
 
@@ -399,8 +435,7 @@ def test_kspace_slater_parity(enuf, name, prec):
     P = dict(P, slater_k=1)
     pos, q = _inputs(prec, pos, q)
     plan, F, E, Wv = _gpu(enuf, prec, P, pos, q)
-    Fr, Er, Wr = _ref(prec, P, pos, q)
-    _check(prec, F, E, Wv, Fr, Er, Wr)
+    _check(prec, F, E, Wv, Ref(P, pos, q))
     plan.close()
 
 
@@ -417,10 +452,5 @@ def test_full_size_kspace_slater_sampled(enuf, prec):
     plan, F, E, Wv = _gpu(enuf, prec, P, pos, q)
     rng = np.random.default_rng(29)
     sample = np.sort(rng.choice(np.nonzero(q)[0], 128, replace=False))
-    Fr, Er, Wr = _ref(prec, P, pos, q, sample=sample)
-    t = TOL[prec]
-    assert _rel_rms(F[sample], Fr) < t["F"]
-    scale = max(abs(Er[0]), abs(Er[1]))
-    for k in range(4):
-        assert abs(E[k] - Er[k]) < t["E"] * scale, (k, E, Er)
+    _check(prec, F, E, Wv, Ref(P, pos, q, sample=sample), sample=sample)
     plan.close()

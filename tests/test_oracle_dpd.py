@@ -1,5 +1,6 @@
 """Pins of the oracle's DPD forces, random numbers and integrator (CPU only)."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -33,6 +34,18 @@ def test_theta_statistics(orc):
         assert orc.theta(5, 11, i, j) == orc.theta(5, 11, j, i)
     assert orc.theta(5, 11, 3, 9) != orc.theta(5, 12, 3, 9)
     assert orc.theta(5, 11, 3, 9) != orc.theta(6, 11, 3, 9)
+
+
+def test_philox_known_answers(orc):
+    """Philox4x32-10 reproduces the known-answer vectors published with its
+    definition (tests/golden/philox4x32_10_kat.txt): a wrong multiplier, key
+    bump, word swap or round count changes every output word."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        w = [int(v, 16) for v in r]
+        assert orc.philox4x32_10(w[0:4], w[4:6]) == w[6:10], r
 
 
 def test_philox_avalanche(orc):
