@@ -87,11 +87,23 @@ typedef struct {
                              energy for converged sums. */
     int    fft_path;  /* 0: automatic (FP32 grids with n <= 112: whole z-planes in shared
                          memory, x+y and y+x fused); 1: always the five line passes x, y, z, y, x */
-    int    fft_radix; /* radix schedule of the line transforms: 0 = automatic (the fewest
-                         stages over 2, 3, 4, 5, 8; FP32 grids from n = 128 on take the
-                         composite radices 6, 10, 12, 16, 20 when that saves a stage);
-                         1 = radices 2, 3, 4, 5, 8 only */
-    int    reserved[2];
+    int    fft_radix; /* line transforms: 0 = automatic: FP32 grids whose n = f1 f2 with
+                         f1, f2 in {4, 5, 6, 8, 10, 12, 16, 20} take the two-factor
+                         kernels (both DFTs in registers, one twiddle pass); other grids
+                         and FP64 the Stockham stages as for 2;
+                         1 = Stockham stages over radices 2, 3, 4, 5, 8 only;
+                         2 = Stockham stages, the fewest over 2, 3, 4, 5, 8, and for FP32
+                         grids from n = 128 on the composite radices 6, 10, 12, 16, 20
+                         when that saves a stage. Same result to rounding. */
+    int    spread;    /* spreading kernel (FP32; FP64 always takes 1): 0 = automatic (1);
+                         1 = tile form (one CTA per T^3 tile: column-stationary for
+                         T in 8, 10, 12, 16, 20, 24, shared-memory atomics otherwise);
+                         2 = footprint form on bricks of whole x rows (or x runs) of
+                         T x T rows, one warp per z-plane, no work on zero weights;
+                         3 = form 2 fused with the forward x pass (the grid is never
+                         written: needs the two-factor kernels, the five-pass FFT and
+                         an even T). Same result to rounding. */
+    int    reserved[1];
 } enuf_params;
 
 typedef struct enuf_plan_s* enuf_plan_t;
@@ -104,9 +116,12 @@ typedef struct {
     int    fft_kernels;        /* FFT kernels per evaluation: 3 with the fused plane passes
                                   (see enuf_params.fft_path), else 5 */
     size_t device_bytes;       /* device memory the plan holds */
-    int    fft_stages;         /* Stockham stages of one length-n line transform */
-    int    fft_radix[8];       /* their radices in order (2, 3, 4, 5, 8; FP32 grids
-                                  from n = 128 on also 6, 10, 12, 16, 20) */
+    int    fft_stages;         /* stages of one length-n line transform (2 for the
+                                  two-factor kernels) */
+    int    fft_radix[8];       /* their radices in order (two-factor: f1, f2) */
+    int    fft_two_factor;     /* 1: the two-factor kernels (enuf_params.fft_radix) */
+    int    spread;             /* spreading kernel taken (enuf_params.spread: 1, 2 or 3) */
+    int    brick_x;            /* x extent of a spreading brick (forms 2 and 3) */
 } enuf_plan_info;
 
 /* Create a plan for systems of up to n_max beads with the given parameters
@@ -309,8 +324,10 @@ void enuf_batch_destroy(enuf_batch_t batch);
  *   grid   : device real[n_g^3] (n_g = sigma_s * M), OVERWRITTEN,
  *            index (z * n_g + y) * n_g + x
  *   cuda_stream : cudaStream_t to enqueue on (NULL: the legacy default stream)
- * Nothing in the scratch needs to start at zero: every call writes all of
- * the scratch it later reads. Returns after enqueueing.
+ * One 16-byte word of the scratch must start at zero, the binning's arrival
+ * counter: each call clears it with a memset on cuda_stream before the
+ * binning (this allocates nothing); every other scratch word is written by
+ * the call before it is read. Returns after enqueueing.
  * Limits and rules:
  *  - ENUF_ERR_INVALID, with a message on stderr, when the bins and sorted
  *    beads of this call need more than the 16 MiB scratch (about 200000

@@ -11,9 +11,11 @@ is cut, but not what is computed (results agree to rounding):
   fft_path  FP32 grids with n <= 112 run the FFT as whole z-planes in shared
             memory (x and y passes fused); fft_path = 1 forces the five line
             passes instead.
-  fft_radix the radix schedule of the line transforms: FP32 grids from
-            n = 128 on take composite radices (6, 10, 12, 16, 20) when that
-            saves a stage; fft_radix = 1 keeps radices 2, 3, 4, 5, 8.
+  fft_radix the line transforms: 0 runs FP32 grids whose n = f1 f2 on the
+            two-factor kernels (both DFTs in registers); 2 runs the Stockham
+            stages, with composite radices (6, 10, 12, 16, 20) for FP32 grids
+            from n = 128 on when that saves a stage; 1 keeps radices
+            2, 3, 4, 5, 8.
 
 The library's own host logic (enuf_plan_shape) decides which tiles are legal
 and which choices differ, so the candidates never include a launch shape the
@@ -39,7 +41,7 @@ from typing import Callable
 
 from . import enuf
 
-CACHE_VERSION = 2
+CACHE_VERSION = 3
 MAX_TILE = 24
 FUSED_FFT_MAX_N = 112
 COMPOSITE_MIN_N = 128
@@ -74,7 +76,7 @@ def _shape(params: enuf.enuf_params, n_max: int):
         info = enuf.plan_shape(params, n_max)
     except enuf.EnufError:
         return None
-    return info.tile, info.fft_kernels, tuple(info.fft_radix[:info.fft_stages])
+    return info.tile, info.fft_kernels, info.fft_two_factor, tuple(info.fft_radix[:info.fft_stages])
 
 
 def candidates(params: enuf.enuf_params, n_max: int) -> list[dict]:
@@ -84,7 +86,7 @@ def candidates(params: enuf.enuf_params, n_max: int) -> list[dict]:
     n = grid_n(params)
     fp32 = params.prec == enuf.ENUF_FP32
     paths = [0, 1] if fp32 and n <= FUSED_FFT_MAX_N else [0]
-    radices = [0, 1] if fp32 and n >= COMPOSITE_MIN_N else [0]
+    radices = [0, 2, 1] if fp32 else [0]
     out, seen = [], set()
     for T in range(max(1, params.p), MAX_TILE + 1):
         if n % T:

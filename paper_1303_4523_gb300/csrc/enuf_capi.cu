@@ -25,7 +25,25 @@ constexpr int kMaxBeads = 1 << 29;    // the kernels index per-bead components a
 constexpr int kMaxSmem = 200 * 1024;  // dynamic shared memory the kernels may request
 constexpr int kSMs = 152;
 
-bool g_configured[2] = {false, false};
+// Kernel attributes (dynamic shared-memory opt-in) belong to the device that
+// was current when they were set: configured once per device and precision.
+constexpr int kMaxDevices = 64;
+std::mutex g_config_mu;
+bool g_configured[kMaxDevices][2] = {};
+
+// Configure the kernels of one precision on the current device (once).
+cudaError_t ensure_configured(int prec) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    const int pi = prec == ENUF_FP32 ? 0 : 1;
+    std::lock_guard<std::mutex> lock(g_config_mu);
+    if (g_configured[dev][pi]) return cudaSuccess;
+    e = prec == ENUF_FP32 ? configure_kernels<float>(kMaxSmem) : configure_kernels<double>(kMaxSmem);
+    if (e == cudaSuccess) g_configured[dev][pi] = true;
+    return e;
+}
 
 // Failure injection on the host (enuf_debug_fail_allocs): after g_fail_after
 // more device allocations of plans, host-buffer staging and DPD systems, the
@@ -111,6 +129,26 @@ bool fft_radices(int n, FftPlanDev& fp, bool composite) {
     if (plan.empty() || plan.size() > 8) return false;
     for (int r : plan) fp.rad[fp.nst++] = r;
     return true;
+}
+
+// Two-factor split n = f1 f2 of the FP32 two-factor kernels: both factors in
+// their radix set; the most balanced split, ties to the larger f2 (phase A
+// reads f2 consecutive elements per line and load). False: none.
+bool fft_two_factor(int n, FftPlanDev& fp) {
+    static const int kF[] = {4, 5, 6, 8, 10, 12, 16, 20};
+    int best1 = 0, best2 = 0;
+    for (int a : kF)
+        for (int b : kF)
+            if (a * b == n) {
+                const int m = std::min(a, b), mb = std::min(best1, best2);
+                if (!best1 || m > mb || (m == mb && b > best2)) {
+                    best1 = a;
+                    best2 = b;
+                }
+            }
+    fp.f1 = best1;
+    fp.f2 = best2;
+    return best1 > 0;
 }
 
 // Largest float strictly below L: a float x lies in [0, L) iff 0 <= x <= this.
@@ -242,14 +280,16 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
     if (P.slater_k != 0 && P.slater_k != 1) return fail(plan, ENUF_ERR_INVALID, "slater_k must be 0 or 1");
     if (P.slater_k && !(P.beta > 0)) return fail(plan, ENUF_ERR_INVALID, "slater_k = 1 needs beta > 0");
     if (P.fft_path != 0 && P.fft_path != 1) return fail(plan, ENUF_ERR_INVALID, "fft_path must be 0 or 1");
-    if (P.fft_radix != 0 && P.fft_radix != 1) return fail(plan, ENUF_ERR_INVALID, "fft_radix must be 0 or 1");
+    if (P.fft_radix < 0 || P.fft_radix > 2) return fail(plan, ENUF_ERR_INVALID, "fft_radix must be 0, 1 or 2");
     const int M = P.M == 0 ? grid_rule(P.L) : P.M;
     if (M < 4 || (M & 1)) return fail(plan, ENUF_ERR_INVALID, "M must be even and >= 4 (got %d)", M);
     const int n = P.sigma_s * M;
     if (n > 1024) return fail(plan, ENUF_ERR_UNSUPPORTED, "grid n = %d > 1024", n);
     FftPlanDev fp{};
-    if (!fft_radices(n, fp, P.prec == ENUF_FP32 && P.fft_radix == 0))
+    if (!fft_radices(n, fp, P.prec == ENUF_FP32 && P.fft_radix != 1))
         return fail(plan, ENUF_ERR_UNSUPPORTED, "grid n = %d is not 2^a 3^b 5^c", n);
+    fp.f1 = fp.f2 = 0;
+    if (P.prec == ENUF_FP32 && P.fft_radix == 0) fft_two_factor(n, fp);
     if (2 * P.p > n) return fail(plan, ENUF_ERR_INVALID, "window 2p = %d wider than the grid", 2 * P.p);
     // tile edge: divides n, >= p, histogram fits in shared memory
     // the spreading kernel holds a T^3 tile of the grid in shared memory: T <= 24
@@ -346,6 +386,87 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
             if (fp.rad[st] > 8 || fp.rad[st] == 6) fs.composite = 1;
         fs.smem_xy = fs.smem_yx = (int)plane;
         fs.t_xy = fs.t_yx = 512;
+    }
+    if (fp.f1) {
+        // two-factor kernels: per line f1 (f2 + 1) phase-A values and n + 1 results;
+        // threads: one phase-A or phase-B task per thread (f2 resp. f1 per line)
+        fs.two = 1;
+        const int lsa = fft2_lsa(fp.f1, fp.f2), lsb = fft2_lsb(n), per_line = (lsa + lsb) * csz;
+        const int fmax = std::max(fp.f1, fp.f2);
+        auto shape2 = [&](int total_lines, int mult, int& lines, int& threads, int& grid, int bud) {
+            const int cap = std::max(1, std::min(64, (bud - n * csz) / (mult * per_line)));
+            lines = std::max(1, std::min(cap, (total_lines + 2 * kSMs - 1) / (2 * kSMs)));
+            grid = (total_lines + lines - 1) / lines;
+            threads = std::min(512, std::max(64, ((mult * lines * fmax + 31) / 32) * 32));
+        };
+        shape2(n * n / 2, 1, fs.lx, fs.tx, fs.grid_x, budget);
+        shape2(n * nc1, 1, fs.ly, fs.ty, gyz, budget);
+        fs.grid_y_z = (n + fs.ly - 1) / fs.ly;
+        shape2(nc1 * g.K, g.nf, fs.lz, fs.tz, fs.grid_z, 96 * 1024);
+        shape2(g.nf * n * nc1, 1, fs.liy, fs.tiy, fs.grid_iy, budget);
+        shape2(g.nf * n * n / 2, 1, fs.lix, fs.tix, fs.grid_ix, budget);
+        fs.smem_x = n * csz + fs.lx * per_line;
+        fs.smem_y = n * csz + fs.ly * per_line;
+        fs.smem_z = n * csz + g.nf * fs.lz * per_line;
+        fs.smem_iy = n * csz + fs.liy * per_line;
+        fs.smem_ix = n * csz + fs.lix * per_line;
+        fs.smem_xy = (n + (n / 2) * (lsa + lsb)) * csz;
+        fs.smem_yx = (n + (n / 2) * lsa + nc1 * lsb) * csz;
+        fs.fused = (fs.smem_xy <= 100 * 1024 && P.fft_path == 0) ? 1 : 0;
+        fs.composite = 0;
+    }
+    // spreading form (FP32): bricks of whole x rows fused with the x pass where the
+    // two-factor five-pass FFT runs and the brick fits; footprint bricks into the
+    // grid otherwise from n = 128 on; the tile form below
+    if (P.spread < 0 || P.spread > 3) return fail(plan, ENUF_ERR_INVALID, "spread must be 0..3");
+    fs.spread = 1;
+    if (P.prec == ENUF_FP32) {
+        const int rsz = (int)sizeof(float);
+        const int stage = brick_stage_bytes<float>();
+        // fused: LP line pairs of the x transform after the brick (shared with the staging)
+        int lp = 0, fx_smem = 0;
+        const bool fx_ok = fs.two && !fs.fused && T % 2 == 0;
+        if (fx_ok) {
+            const int per_line = (fft2_lsa(fp.f1, fp.f2) + fft2_lsb(n)) * csz;
+            const int acc = T * T * n * rsz;
+            lp = std::min(std::min(16, T * T / 2), (kMaxSmem - acc - n * csz) / per_line);
+            if (lp >= 2) fx_smem = brick_smem<float>(T, n, n * csz + lp * per_line);
+        }
+        const bool fx_fits = fx_smem > 0 && fx_smem <= kMaxSmem;
+        // automatic: the tile form (measured faster than forms 2 and 3 at every size
+        // of the electrolyte sweep, 81k to 3M beads)
+        int want = P.spread == 0 ? 1 : P.spread;
+        if (want == 3 && !fx_fits)
+            return fail(plan, ENUF_ERR_INVALID, "spread = 3 needs the two-factor five-pass FFT, an even tile and "
+                                                "a brick that fits in shared memory");
+        if (want == 3) {
+            fs.spread = 3;
+            fs.brick_x = n;
+            fs.brick_lp = lp;
+            fs.brick_smem = fx_smem;
+        } else if (want == 2) {
+            // the longest x run (a multiple of T dividing n) that keeps >= 4 bricks per SM
+            int bx = T;
+            for (int c = n; c >= T; c -= T)
+                if (n % c == 0 && (long long)(n / c) * g.ntd * g.ntd >= 4 * kSMs &&
+                    brick_smem<float>(T, c, 0) <= 96 * 1024) {
+                    bx = c;
+                    break;
+                }
+            if (brick_smem<float>(T, bx, 0) > kMaxSmem)
+                return fail(plan, ENUF_ERR_INVALID, "spread = 2: brick of %d x %d x %d does not fit", bx, T, T);
+            fs.spread = 2;
+            fs.brick_x = bx;
+            fs.brick_lp = 0;
+            fs.brick_smem = brick_smem<float>(T, bx, 0);
+        }
+        if (fs.spread > 1) {
+            fs.brick_threads = 32 * T;
+            fs.brick_grid = (n / fs.brick_x) * g.ntd * g.ntd;
+        }
+        (void)stage;
+    } else if (P.spread > 1) {
+        return fail(plan, ENUF_ERR_INVALID, "spread = %d is an FP32 form", P.spread);
     }
     g.ratio = (double)n / P.L;
     g.rb = 1.0 / g.b;
@@ -664,7 +785,9 @@ enuf_status enuf_accuracy_params(double delta, enuf_params* params) {
     const double alpha = hi / rc;
     // Eq. 29, reciprocal space: n_c >= (alpha L / pi) sqrt(-ln delta); the
     // base grid keeps n_c = M/2 - 1, rounded up to an even 2^a 3^b 5^c M
-    const int nc = (int)std::ceil(alpha * L / M_PI * std::sqrt(-std::log(delta)) - 1e-12);
+    int nc = (int)std::ceil(alpha * L / M_PI * std::sqrt(-std::log(delta)));
+    // rounding of the bound: take the condition itself, exp(-(pi n_c/(alpha L))^2) <= delta
+    while (std::exp(-std::pow(M_PI * nc / (alpha * L), 2)) > delta) ++nc;
     int M = 2 * (nc + 1);
     while (!smooth(M)) M += 2;
     if (2 * M > 1024) return ENUF_ERR_UNSUPPORTED;
@@ -694,11 +817,9 @@ enuf_status enuf_plan(const enuf_params* params, int n_max, void* cuda_stream, e
         enuf_destroy(plan);
         return s;
     };
-    const int pi = plan->prec == ENUF_FP32 ? 0 : 1;
-    if (!g_configured[pi]) {
-        cudaError_t e = plan->prec == ENUF_FP32 ? configure_kernels<float>(kMaxSmem) : configure_kernels<double>(kMaxSmem);
+    {
+        cudaError_t e = ensure_configured(plan->prec);
         if (e != cudaSuccess) return bail(fail(plan, ENUF_ERR_CUDA, "configure: %s", cudaGetErrorString(e)));
-        g_configured[pi] = true;
     }
     if (cuda_stream) {
         plan->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -739,10 +860,18 @@ static void fill_info(const enuf_plan_s* plan, enuf_plan_info* info) {
     info->tile = plan->g.T;
     info->n_tiles = plan->g.ntiles;
     info->n_max = plan->n_max;
-    info->fft_kernels = plan->fs.fused ? 3 : 5;
+    info->fft_kernels = plan->fs.fused ? 3 : (plan->fs.spread == 3 ? 4 : 5);
     info->device_bytes = plan->dbytes;
-    info->fft_stages = plan->fp.nst;
-    for (int i = 0; i < 8; ++i) info->fft_radix[i] = i < plan->fp.nst ? plan->fp.rad[i] : 0;
+    info->fft_two_factor = plan->fp.f1 ? 1 : 0;
+    info->spread = plan->fs.spread;
+    info->brick_x = plan->fs.spread > 1 ? plan->fs.brick_x : 0;
+    if (plan->fp.f1) {
+        info->fft_stages = 2;
+        for (int i = 0; i < 8; ++i) info->fft_radix[i] = i == 0 ? plan->fp.f1 : (i == 1 ? plan->fp.f2 : 0);
+    } else {
+        info->fft_stages = plan->fp.nst;
+        for (int i = 0; i < 8; ++i) info->fft_radix[i] = i < plan->fp.nst ? plan->fp.rad[i] : 0;
+    }
 }
 
 enuf_status enuf_get_info(enuf_plan_t plan, enuf_plan_info* info) {
@@ -1013,6 +1142,10 @@ enuf_status dpd_create(enuf_plan_t plan, const dpd_params* params, int n, const 
     d.K_bond = params->K_bond;
     d.r0_bond = params->r0_bond;
     d.seed = params->seed;
+    for (int r = 0; r < 10; ++r) {   // Philox4x32-10 round keys (Salmon et al., SC'11)
+        d.rk0[r] = (uint32_t)d.seed + (uint32_t)r * 0x9E3779B9u;
+        d.rk1[r] = (uint32_t)(d.seed >> 32) + (uint32_t)r * 0xBB67AE85u;
+    }
     d.rdt = 1.0 / std::sqrt(params->dt);
     // cell blocks of B^3 cells: the largest B <= 4 (and <= ncd - 2, so the
     // (B + 2)^3 halo holds distinct cells) whose mean halo population stays
@@ -1333,14 +1466,10 @@ extern "C" enuf_status enuf_spread_noalloc(const enuf_params* params, int n, con
         }
         g_noalloc_addr[dev] = p;
     }
-    const int pi = geo.prec == ENUF_FP32 ? 0 : 1;
-    if (!g_configured[pi]) {
-        e = geo.prec == ENUF_FP32 ? configure_kernels<float>(kMaxSmem) : configure_kernels<double>(kMaxSmem);
-        if (e != cudaSuccess) {
-            fprintf(stderr, "enuf_spread_noalloc: %s\n", cudaGetErrorString(e));
-            return ENUF_ERR_CUDA;
-        }
-        g_configured[pi] = true;
+    e = ensure_configured(geo.prec);
+    if (e != cudaSuccess) {
+        fprintf(stderr, "enuf_spread_noalloc: %s\n", cudaGetErrorString(e));
+        return ENUF_ERR_CUDA;
     }
     char* b = static_cast<char*>(g_noalloc_addr[dev]);
     Work w{};
@@ -1349,7 +1478,7 @@ extern "C" enuf_status enuf_spread_noalloc(const enuf_params* params, int n, con
     w.boff = reinterpret_cast<int*>(b + o_boff);
     w.ttot = reinterpret_cast<int*>(b + o_ttot);
     w.tstart = reinterpret_cast<int*>(b + o_tstart);
-    w.ticket = reinterpret_cast<int*>(b + o_tk);   // zero at load, returned to zero by each use
+    w.ticket = reinterpret_cast<int*>(b + o_tk);   // cleared below, before the binning counts on it
     w.ctile = reinterpret_cast<int*>(b + o_ctile);
     w.cpos = b + o_cpos;
     w.cfrac = b + o_cfrac;
@@ -1361,8 +1490,12 @@ extern "C" enuf_status enuf_spread_noalloc(const enuf_params* params, int n, con
     w.off_q = 0;
     EvalArgs a{n, pos, q, nullptr, false};
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    e = geo.prec == ENUF_FP32 ? enqueue_spread_only<float>(g, w, a, grid, s)
-                              : enqueue_spread_only<double>(g, w, a, grid, s);
+    // the binning's arrival counter must start at zero: a call that stopped
+    // part way could have left it set (a memset node allocates nothing)
+    e = cudaMemsetAsync(w.ticket, 0, 16, s);
+    if (e == cudaSuccess)
+        e = geo.prec == ENUF_FP32 ? enqueue_spread_only<float>(g, w, a, grid, s)
+                                  : enqueue_spread_only<double>(g, w, a, grid, s);
     if (e != cudaSuccess) {
         fprintf(stderr, "enuf_spread_noalloc: launch: %s\n", cudaGetErrorString(e));
         return ENUF_ERR_CUDA;

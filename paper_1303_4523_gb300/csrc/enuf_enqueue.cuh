@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <utility>
 
+#include "enuf_fft2.cuh"
 #include "enuf_kernels.cuh"
 
 namespace enuf {
@@ -121,6 +122,17 @@ cudaError_t configure_kernels(int max_smem) {
     set((const void*)k_spread_col<R, 24, true>);
     set((const void*)k_fft_xy<R>);
     set((const void*)k_fft_yx<R>);
+    if constexpr (sizeof(R) == 4) {
+        set((const void*)k2_fft_x<R>);
+        set((const void*)k2_fft_y<R>);
+        set((const void*)k2_fft_z<R>);
+        set((const void*)k2_fft_iy<R>);
+        set((const void*)k2_fft_ix<R>);
+        set((const void*)k2_fft_xy<R>);
+        set((const void*)k2_fft_yx<R>);
+        set((const void*)k_spread_brick<R, false>);
+        set((const void*)k_spread_brick<R, true>);
+    }
     set((const void*)k_real<R>);
     set((const void*)k_dpd<R>);
     return e;
@@ -192,6 +204,54 @@ inline void enqueue_spread(const Geo& g, const Work& w, R* grid, cudaStream_t s,
 
 // The FFT passes of one evaluation (fused plane passes or five line passes);
 // CR selects the kernels compiled with the composite radices.
+// Footprint spreading on bricks (FP32): into the grid (spread = 2), or fused
+// with the forward x pass into spec1 (spread = 3).
+template <typename R>
+void enqueue_spread_brick(const Geo& g, const FftShape& fs, const FftPlanDev& fp, const Work& w, cudaStream_t s,
+                          bool pdl) {
+    using V = typename V4<R>::T;
+    using C = typename Cx<R>::T;
+    auto k = fs.spread == 3 ? k_spread_brick<R, true> : k_spread_brick<R, false>;
+    launch(pdl, true, k, fs.brick_grid, fs.brick_threads, fs.brick_smem, s, g, fp, fs.brick_x, (const int*)w.tstart,
+           static_cast<const V*>(w.sq), (const int*)w.sb, static_cast<const R*>(w.wb), static_cast<R*>(w.grid),
+           static_cast<const C*>(w.tw), static_cast<C*>(w.spec1), fs.brick_lp);
+}
+
+// The same passes on the two-factor kernels (FP32 grids with n = f1 f2); with
+// the spreading fused with the x pass (spread = 3) the x pass is already done.
+template <typename R>
+void enqueue_fft2(const Geo& g, const FftShape& fs, const FftPlanDev& fp, const Work& w, cudaStream_t s0, bool pdl,
+                  LaunchLog* log) {
+    using C = typename Cx<R>::T;
+    const C* tw = static_cast<const C*>(w.tw);
+    if (fs.fused) {
+        launch(pdl, true, k2_fft_xy<R>, g.n, fs.t_xy, fs.smem_xy, s0, g, fp, static_cast<const R*>(w.grid), tw,
+               static_cast<C*>(w.spec2));
+        launch(pdl, true, k2_fft_z<R>, fs.grid_z, fs.tz, fs.smem_z, s0, g, fp, static_cast<const C*>(w.spec2), tw,
+               (const double*)w.tab, (const double*)w.tabv, static_cast<const R*>(w.tabr), static_cast<C*>(w.spec3),
+               w.part + w.off_recip, fs.lz, 1);
+        launch(pdl, true, k2_fft_yx<R>, g.nf * g.n, fs.t_yx, fs.smem_yx, s0, g, fp, static_cast<const C*>(w.spec3),
+               tw, static_cast<R*>(w.h));
+        log->kernels += 4;
+    } else {
+        if (fs.spread != 3) {
+            launch(pdl, true, k2_fft_x<R>, fs.grid_x, fs.tx, fs.smem_x, s0, g, fp, static_cast<const R*>(w.grid), tw,
+                   static_cast<C*>(w.spec1), fs.lx);
+            log->kernels += 1;
+        }
+        launch(pdl, true, k2_fft_y<R>, dim3(g.nc + 1, fs.grid_y_z), fs.ty, fs.smem_y, s0, g, fp,
+               static_cast<const C*>(w.spec1), tw, static_cast<C*>(w.spec2), fs.ly);
+        launch(pdl, true, k2_fft_z<R>, fs.grid_z, fs.tz, fs.smem_z, s0, g, fp, static_cast<const C*>(w.spec2), tw,
+               (const double*)w.tab, (const double*)w.tabv, static_cast<const R*>(w.tabr), static_cast<C*>(w.spec3),
+               w.part + w.off_recip, fs.lz, 0);
+        launch(pdl, true, k2_fft_iy<R>, fs.grid_iy, fs.tiy, fs.smem_iy, s0, g, fp, static_cast<const C*>(w.spec3),
+               tw, static_cast<C*>(w.spec4), fs.liy);
+        launch(pdl, true, k2_fft_ix<R>, fs.grid_ix, fs.tix, fs.smem_ix, s0, g, fp, static_cast<const C*>(w.spec4),
+               tw, static_cast<R*>(w.h), fs.lix);
+        log->kernels += 5;   // the spreading kernel and four passes
+    }
+}
+
 template <typename R, bool CR>
 void enqueue_fft(const Geo& g, const FftShape& fs, const FftPlanDev& fp, const Work& w, cudaStream_t s0, bool pdl,
                  LaunchLog* log) {
@@ -252,11 +312,20 @@ cudaError_t enqueue_enuf(const Geo& g, const FftShape& fs, const FftPlanDev& fp,
 
     // reciprocal branch
     rec(ev, 1, true, s0);
-    enqueue_spread<R>(g, w, static_cast<R*>(w.grid), s0, pdl);
+    if constexpr (sizeof(R) == 4) {
+        if (fs.spread > 1)
+            enqueue_spread_brick<R>(g, fs, fp, w, s0, pdl);
+        else
+            enqueue_spread<R>(g, w, static_cast<R*>(w.grid), s0, pdl);
+    } else {
+        enqueue_spread<R>(g, w, static_cast<R*>(w.grid), s0, pdl);
+    }
     rec(ev, 1, false, s0);
     rec(ev, 2, true, s0);
     if constexpr (sizeof(R) == 4) {
-        if (fs.composite)
+        if (fs.two)
+            enqueue_fft2<R>(g, fs, fp, w, s0, pdl, log);
+        else if (fs.composite)
             enqueue_fft<R, true>(g, fs, fp, w, s0, pdl, log);
         else
             enqueue_fft<R, false>(g, fs, fp, w, s0, pdl, log);

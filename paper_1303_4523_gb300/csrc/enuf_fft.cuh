@@ -26,6 +26,7 @@ struct FftPlanDev {
     int n;
     int nst;
     int rad[8];
+    int f1, f2;   // two-factor split n = f1 f2 of the FP32 two-factor kernels (0: none)
 };
 
 // a / b for 0 <= a < 2^23, b >= 1, given rb = 1/b in float: the float quotient
@@ -331,6 +332,127 @@ __device__ typename Cx<R>::T* fft_lines(typename Cx<R>::T* b0, typename Cx<R>::T
         Ns *= rad;
     }
     return src;
+}
+
+}  // namespace enuf
+
+namespace enuf {
+
+// ---------------------------------------------------------------------------
+// Two-factor line FFT for lengths n = f1 f2 with both factors among the
+// radices above: the Cooley-Tukey split of the n-point DFT into f2 DFTs of
+// length f1, one twiddle per element, and f1 DFTs of length f2. With
+// element m = t + f2 j of a line (t < f2, j < f1) and output k = k1 + f1 k2,
+//   X[k1 + f1 k2] = sum_t w_n^{t k1} w_f2^{t k2} sum_j x[t + f2 j] w_f1^{j k1}.
+// Phase A (one task per line and t): loads its f1 elements (through the
+//   caller's loader, usually straight from global memory), the f1-point DFT
+//   in registers, the twiddles w_n^{t k1} from the shared table, and stores
+//   row k1 of the line's buffer at k1 (f2 + 1) + t (rows padded by one value:
+//   phase B reads a row per lane, and the odd stride spreads those reads
+//   over the banks).
+// Phase B (one task per line and k1): the f2-point DFT of row k1 in
+//   registers; the caller's storer receives X[k1 + f1 k2].
+// The factors are compile-time (the DFTs and every offset inside a task are
+// constants); n, f1, f2 and the line count are runtime values, so one kernel
+// serves every length with such a factorization. Per element this is one
+// load, the DFT arithmetic of two radices, one twiddle multiply and two
+// shared-memory accesses, against the runtime-radix Stockham stages'
+// per-stage quotients, swizzles and twiddle indices.
+// ---------------------------------------------------------------------------
+template <typename R, int F1, bool INV, typename Load>
+__device__ __forceinline__ void fft2_phase_a(typename Cx<R>::T* __restrict__ buf, int lsa, int nlines, int f2,
+                                             const typename Cx<R>::T* __restrict__ tw, Load& load) {
+    using C = typename Cx<R>::T;
+    const int total = nlines * f2;
+    const float rf2 = 1.0f / (float)f2;
+    for (int task = threadIdx.x; task < total; task += blockDim.x) {
+        const int line = qdiv(task, f2, rf2), t = task - line * f2;
+        C v[F1];
+#pragma unroll
+        for (int j = 0; j < F1; ++j) v[j] = load(line, t + f2 * j);
+        SmallDft<R, F1, INV>::run(v);
+#pragma unroll
+        for (int k = 1; k < F1; ++k) {
+            C w = tw[k * f2 + t];   // w_n^{t k}: lanes over t read consecutive values
+            if (INV) w.y = -w.y;
+            v[k] = cmul(v[k], w);
+        }
+        C* d = buf + line * lsa + t;
+#pragma unroll
+        for (int k = 0; k < F1; ++k) d[k * (f2 + 1)] = v[k];
+    }
+}
+
+template <typename R, int F2, bool INV, typename Store>
+__device__ __forceinline__ void fft2_phase_b(const typename Cx<R>::T* __restrict__ buf, int lsa, int nlines, int f1,
+                                             Store& store) {
+    using C = typename Cx<R>::T;
+    const int total = nlines * f1;
+    const float rf1 = 1.0f / (float)f1;
+    for (int task = threadIdx.x; task < total; task += blockDim.x) {
+        const int line = qdiv(task, f1, rf1), k1 = task - line * f1;
+        const C* s = buf + line * lsa + k1 * (F2 + 1);
+        C u[F2];
+#pragma unroll
+        for (int t = 0; t < F2; ++t) u[t] = s[t];
+        SmallDft<R, F2, INV>::run(u);
+#pragma unroll
+        for (int k2 = 0; k2 < F2; ++k2) store(line, k1 + f1 * k2, u[k2]);
+    }
+}
+
+// The twiddle table of phase A in shared memory, tw[k f2 + t] = w_n^{t k}
+// (t < f2, k < f1; forward sign), from the table twg[m] = w_n^m: the lanes of
+// a phase-A step read consecutive values (the natural table, read at t k,
+// puts lanes of an even k on few banks).
+template <typename C>
+__device__ __forceinline__ void fft2_twiddles(C* __restrict__ tw, const C* __restrict__ twg, const FftPlanDev& fp) {
+    const int f2 = fp.f2, n = fp.f1 * fp.f2;
+    const float rf2 = 1.0f / (float)f2;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        const int k = qdiv(e, f2, rf2), t = e - k * f2;
+        tw[e] = twg[t * k];
+    }
+}
+
+// Row stride of a phase-A line buffer, and of a buffer of natural-order
+// results. A two-factor pass with L lines per CTA holds the twiddle table (n
+// values), L phase-A rows and L result rows in shared memory.
+__host__ __device__ constexpr int fft2_lsa(int f1, int f2) { return f1 * (f2 + 1); }
+__host__ __device__ constexpr int fft2_lsb(int n) { return n + 1; }
+
+// The whole two-factor transform of nlines lines: load(line, m) gives element
+// m of a line, store(line, k, X_k) takes the results; tw is the table that
+// fft2_twiddles fills. buf holds nlines rows
+// of fft2_lsa(f1, f2) values. Contains __syncthreads (call from all threads);
+// the caller synchronises before reading what store wrote to shared memory.
+template <typename R, bool INV, typename Load, typename Store>
+__device__ __forceinline__ void fft2_lines(typename Cx<R>::T* __restrict__ buf, const typename Cx<R>::T* tw,
+                                           const FftPlanDev& fp, int nlines, Load&& load, Store&& store) {
+    const int f1 = fp.f1, f2 = fp.f2, lsa = fft2_lsa(f1, f2);
+    switch (f1) {
+        case 4: fft2_phase_a<R, 4, INV>(buf, lsa, nlines, f2, tw, load); break;
+        case 5: fft2_phase_a<R, 5, INV>(buf, lsa, nlines, f2, tw, load); break;
+        case 6: fft2_phase_a<R, 6, INV>(buf, lsa, nlines, f2, tw, load); break;
+        case 8: fft2_phase_a<R, 8, INV>(buf, lsa, nlines, f2, tw, load); break;
+        case 10: fft2_phase_a<R, 10, INV>(buf, lsa, nlines, f2, tw, load); break;
+        case 12: fft2_phase_a<R, 12, INV>(buf, lsa, nlines, f2, tw, load); break;
+        case 16: fft2_phase_a<R, 16, INV>(buf, lsa, nlines, f2, tw, load); break;
+        case 20: fft2_phase_a<R, 20, INV>(buf, lsa, nlines, f2, tw, load); break;
+        default: break;
+    }
+    __syncthreads();
+    switch (f2) {
+        case 4: fft2_phase_b<R, 4, INV>(buf, lsa, nlines, f1, store); break;
+        case 5: fft2_phase_b<R, 5, INV>(buf, lsa, nlines, f1, store); break;
+        case 6: fft2_phase_b<R, 6, INV>(buf, lsa, nlines, f1, store); break;
+        case 8: fft2_phase_b<R, 8, INV>(buf, lsa, nlines, f1, store); break;
+        case 10: fft2_phase_b<R, 10, INV>(buf, lsa, nlines, f1, store); break;
+        case 12: fft2_phase_b<R, 12, INV>(buf, lsa, nlines, f1, store); break;
+        case 16: fft2_phase_b<R, 16, INV>(buf, lsa, nlines, f1, store); break;
+        case 20: fft2_phase_b<R, 20, INV>(buf, lsa, nlines, f1, store); break;
+        default: break;
+    }
 }
 
 }  // namespace enuf

@@ -1,0 +1,624 @@
+// enuf_fft2.cuh -- the FFT passes of the NFFT (Sec. 3.3; the plain FFT inside
+// the transposed and conjugated NFFT of Eq. 13-14) on the two-factor line
+// transform of enuf_fft.cuh, for FP32 grids whose n = f1 f2 splits into two
+// of its radices. Same passes, layouts and results as the Stockham kernels of
+// enuf_kernels.cuh (which serve every other n and FP64):
+//   k2_fft_x  : forward R2C along x (two real rows per complex line), keep kx <= nc
+//   k2_fft_y  : forward along y, keep |ky| <= nc
+//   k2_fft_z  : forward along z, influence x deconvolution, FP64 energy and
+//               virial, the nf force fields, their inverse along z
+//   k2_fft_iy : inverse along y (zero-padded)
+//   k2_fft_ix : inverse C2R along x (two Hermitian rows per complex line)
+//   k2_fft_xy / k2_fft_yx : the x+y and y+x passes of one z-plane in shared
+//               memory (small grids)
+// Phase A of every transform loads its elements straight from global memory
+// (or from the previous transform's shared buffer); phase B writes the
+// natural-order results to a shared buffer, from which the pass writes its
+// output in the layout the next pass reads contiguously.
+#pragma once
+#include "enuf_kernels.cuh"
+
+namespace enuf {
+
+template <typename R>
+__global__ void __launch_bounds__(512) k2_fft_x(Geo g, FftPlanDev fp, const R* __restrict__ grid,
+                                               const typename Cx<R>::T* __restrict__ twg,
+                                               typename Cx<R>::T* __restrict__ spec1, int LP) {
+    pdl_enter();
+    using C = typename Cx<R>::T;
+    extern __shared__ unsigned char smraw[];
+    const int n = g.n, nc = g.nc, nc1 = nc + 1, lsb = fft2_lsb(n);
+    C* tw = reinterpret_cast<C*>(smraw);
+    C* A = tw + n;
+    C* B = A + LP * fft2_lsa(fp.f1, fp.f2);
+    fft2_twiddles(tw, twg, fp);
+    const int row0 = blockIdx.x * 2 * LP;   // first real row (z n + y), y even
+    const int nl = min(LP, (n * n - row0) / 2);
+    __syncthreads();
+    const R* src = grid + (size_t)row0 * n;
+    fft2_lines<R, false>(
+        A, tw, fp, nl,
+        [&](int c, int x) {
+            C v;
+            v.x = src[(size_t)(2 * c) * n + x];
+            v.y = src[(size_t)(2 * c + 1) * n + x];
+            return v;
+        },
+        [&](int c, int k, C v) {
+            if (k <= nc || k >= n - nc) B[c * lsb + k] = v;
+        });
+    __syncthreads();
+    // split the two real transforms: A = (Z_k + conj Z_{n-k})/2, B = -i (Z_k - conj Z_{n-k})/2
+    const float rnl = 1.0f / (float)max(nl, 1), rn = 1.0f / (float)n;
+    for (int idx = threadIdx.x; idx < nl * nc1; idx += blockDim.x) {
+        const int k = qdiv(idx, nl, rnl), c = idx - k * nl;
+        const C z = B[c * lsb + k];
+        const C zm = B[c * lsb + (k == 0 ? 0 : n - k)];
+        C a, b;
+        a.x = (R)0.5 * (z.x + zm.x);
+        a.y = (R)0.5 * (z.y - zm.y);
+        b.x = (R)0.5 * (z.y + zm.y);
+        b.y = (R)0.5 * (zm.x - z.x);
+        const int row = row0 + 2 * c;
+        const int zz = qdiv(row, n, rn), y = row - zz * n;
+        C* dst = spec1 + ((size_t)zz * nc1 + k) * n + y;
+        dst[0] = a;
+        dst[1] = b;
+    }
+}
+
+// forward y for lines (z, kx): spec1[z][kx][y] -> spec2[kx][ky][z], |ky| <= nc
+template <typename R>
+__global__ void __launch_bounds__(512) k2_fft_y(Geo g, FftPlanDev fp, const typename Cx<R>::T* __restrict__ spec1,
+                                               const typename Cx<R>::T* __restrict__ twg,
+                                               typename Cx<R>::T* __restrict__ spec2, int LB) {
+    pdl_enter();
+    using C = typename Cx<R>::T;
+    extern __shared__ unsigned char smraw[];
+    const int n = g.n, nc = g.nc, nc1 = nc + 1, K = g.K, lsb = fft2_lsb(n);
+    C* tw = reinterpret_cast<C*>(smraw);
+    C* A = tw + n;
+    C* B = A + LB * fft2_lsa(fp.f1, fp.f2);
+    fft2_twiddles(tw, twg, fp);
+    const int kx = blockIdx.x;
+    const int z0 = blockIdx.y * LB;
+    const int nl = min(LB, n - z0);
+    __syncthreads();
+    fft2_lines<R, false>(
+        A, tw, fp, nl, [&](int c, int y) { return spec1[((size_t)(z0 + c) * nc1 + kx) * n + y]; },
+        [&](int c, int k, C v) {
+            if (k <= nc || k >= n - nc) B[c * lsb + k] = v;
+        });
+    __syncthreads();
+    const float rnl = 1.0f / (float)max(nl, 1);
+    for (int idx = threadIdx.x; idx < nl * K; idx += blockDim.x) {
+        const int ki = qdiv(idx, nl, rnl), c = idx - ki * nl;
+        const int ky = ki - nc;
+        spec2[((size_t)kx * K + ki) * n + z0 + c] = B[c * lsb + (ky < 0 ? ky + n : ky)];
+    }
+}
+
+// z pass: forward z of lines l = (kx, ky); E += w D |F|^2 and W += w D v |F|^2
+// (FP64, Kahan); the nf fields -i k_a D F (gradient mode: D F), built in the
+// inverse transform's loader, inverse z; output spec3[a][z][kx][ky].
+template <typename R>
+__global__ void __launch_bounds__(512) k2_fft_z(Geo g, FftPlanDev fp, const typename Cx<R>::T* __restrict__ spec2,
+                                               const typename Cx<R>::T* __restrict__ twg,
+                                               const double* __restrict__ tab, const double* __restrict__ tabv,
+                                               const R* __restrict__ tabr, typename Cx<R>::T* __restrict__ spec3,
+                                               double* __restrict__ epart, int LB, int plane_major) {
+    pdl_enter();
+    using C = typename Cx<R>::T;
+    extern __shared__ unsigned char smraw[];
+    const int n = g.n, nc = g.nc, K = g.K, nf = g.nf, lsb = fft2_lsb(n);
+    const int NL = (nc + 1) * K;
+    C* tw = reinterpret_cast<C*>(smraw);
+    C* A = tw + n;                                    // [nf LB] phase-A rows
+    C* B = A + nf * LB * fft2_lsa(fp.f1, fp.f2);     // [nf LB][lsb]: forward result, then the fields
+    fft2_twiddles(tw, twg, fp);
+    const int l0 = blockIdx.x * LB;
+    const int nl = min(LB, NL - l0);
+    __syncthreads();
+    if (plane_major)   // spec2[z][l]: lines gathered across planes
+        fft2_lines<R, false>(
+            A, tw, fp, nl, [&](int c, int z) { return spec2[(size_t)z * NL + l0 + c]; },
+            [&](int c, int k, C v) {
+                if (k <= nc || k >= n - nc) B[c * lsb + k] = v;
+            });
+    else               // spec2[l][z]: lines contiguous
+        fft2_lines<R, false>(
+            A, tw, fp, nl, [&](int c, int z) { return spec2[(size_t)(l0 + c) * n + z]; },
+            [&](int c, int k, C v) {
+                if (k <= nc || k >= n - nc) B[c * lsb + k] = v;
+            });
+    __syncthreads();
+    // energy and virial of the kept modes (half space kx >= 0, kx > 0 counted twice)
+    const float rK = 1.0f / (float)K;
+    Kahan ke, kw;
+    for (int idx = threadIdx.x; idx < nl * K; idx += blockDim.x) {
+        const int c = qdiv(idx, K, rK), kzi = idx - c * K;
+        const int l = l0 + c;
+        const int kx = qdiv(l, K, rK);
+        const int kz = kzi - nc;
+        const C f = B[c * lsb + (kz < 0 ? kz + n : kz)];
+        const double a2 = (double)f.x * (double)f.x + (double)f.y * (double)f.y;
+        const double wgt = kx == 0 ? 1.0 : 2.0;
+        ke.add(wgt * tab[(size_t)l * K + kzi] * a2);
+        kw.add(wgt * tabv[(size_t)l * K + kzi] * a2);
+    }
+    double se = ke.s, sv = kw.s;
+    block_sum2(se, sv);
+    if (threadIdx.x == 0) {
+        epart[2 * blockIdx.x] = se;
+        epart[2 * blockIdx.x + 1] = sv;
+    }
+    // inverse of the nf fields of every line: line a nl + c of the transform
+    fft2_lines<R, true>(
+        A, tw, fp, nf * nl,
+        [&](int line, int m) {
+            const int a = line >= nl ? (line >= 2 * nl ? 2 : 1) : 0;
+            const int c = line - a * nl;
+            const int kz = m <= n / 2 ? m : m - n;
+            C v;
+            v.x = (R)0;
+            v.y = (R)0;
+            if (kz >= -nc && kz <= nc) {
+                const int l = l0 + c;
+                const R d = tabr[(size_t)l * K + (kz + nc)];
+                const C f = B[c * lsb + m];
+                if (nf == 1) {
+                    v.x = d * f.x;   // D F
+                    v.y = d * f.y;
+                } else {
+                    const int kx = qdiv(l, K, rK), ky = (l - kx * K) - nc;
+                    const int ka = a == 0 ? kx : (a == 1 ? ky : kz);
+                    const R s = (R)ka * d;
+                    v.x = s * f.y;   // -i k_a D F
+                    v.y = -s * f.x;
+                }
+            }
+            return v;
+        },
+        [&](int line, int z, C v) { B[line * lsb + z] = v; });
+    __syncthreads();
+    // B no longer holds the forward result: phase B of the inverse read A only
+    const int per = nl * n;
+    const float rper = 1.0f / (float)per, rnl = 1.0f / (float)max(nl, 1);
+    for (int idx = threadIdx.x; idx < nf * per; idx += blockDim.x) {
+        const int a = qdiv(idx, per, rper), e = idx - a * per;
+        const int z = qdiv(e, nl, rnl), c = e - z * nl;
+        spec3[((size_t)a * n + z) * NL + l0 + c] = B[(a * nl + c) * lsb + z];
+    }
+}
+
+// inverse y for lines (a, z, kx): K inputs zero-padded to n; output spec4[a][z][y][kx]
+template <typename R>
+__global__ void __launch_bounds__(512) k2_fft_iy(Geo g, FftPlanDev fp, const typename Cx<R>::T* __restrict__ spec3,
+                                                const typename Cx<R>::T* __restrict__ twg,
+                                                typename Cx<R>::T* __restrict__ spec4, int LB) {
+    pdl_enter();
+    using C = typename Cx<R>::T;
+    extern __shared__ unsigned char smraw[];
+    const int n = g.n, nc = g.nc, nc1 = nc + 1, K = g.K, lsb = fft2_lsb(n);
+    const int NLT = g.nf * n * nc1;
+    C* tw = reinterpret_cast<C*>(smraw);
+    C* A = tw + n;
+    C* B = A + LB * fft2_lsa(fp.f1, fp.f2);
+    fft2_twiddles(tw, twg, fp);
+    const int l0 = blockIdx.x * LB;
+    const int nl = min(LB, NLT - l0);
+    __syncthreads();
+    fft2_lines<R, true>(
+        A, tw, fp, nl,
+        [&](int c, int m) {
+            const int ky = m <= n / 2 ? m : m - n;
+            C v;
+            v.x = (R)0;
+            v.y = (R)0;
+            if (ky >= -nc && ky <= nc) v = spec3[(size_t)(l0 + c) * K + (ky + nc)];
+            return v;
+        },
+        [&](int c, int y, C v) { B[c * lsb + y] = v; });
+    __syncthreads();
+    const float rnl = 1.0f / (float)max(nl, 1), rnc1 = 1.0f / (float)nc1;
+    for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
+        const int y = qdiv(idx, nl, rnl), c = idx - y * nl;
+        const int l = l0 + c;
+        const int az = qdiv(l, nc1, rnc1), kx = l - az * nc1;
+        spec4[((size_t)az * n + y) * nc1 + kx] = B[c * lsb + y];
+    }
+}
+
+// inverse x (C2R, two Hermitian rows per complex line); output h[a][z][y][x]
+template <typename R>
+__global__ void __launch_bounds__(512) k2_fft_ix(Geo g, FftPlanDev fp, const typename Cx<R>::T* __restrict__ spec4,
+                                                const typename Cx<R>::T* __restrict__ twg, R* __restrict__ h,
+                                                int LP) {
+    pdl_enter();
+    using C = typename Cx<R>::T;
+    extern __shared__ unsigned char smraw[];
+    const int n = g.n, nc = g.nc, nc1 = nc + 1, lsb = fft2_lsb(n);
+    const int nrows = g.nf * n * n;
+    C* tw = reinterpret_cast<C*>(smraw);
+    C* A = tw + n;
+    C* B = A + LP * fft2_lsa(fp.f1, fp.f2);
+    fft2_twiddles(tw, twg, fp);
+    const int row0 = blockIdx.x * 2 * LP;
+    const int nl = min(LP, (nrows - row0) / 2);
+    __syncthreads();
+    fft2_lines<R, true>(
+        A, tw, fp, nl,
+        [&](int c, int m) {
+            const C* ra = spec4 + (size_t)(row0 + 2 * c) * nc1;
+            const C* rb = ra + nc1;
+            C a, b;
+            a.x = a.y = b.x = b.y = (R)0;
+            if (m == 0) {
+                a.x = ra[0].x;
+                b.x = rb[0].x;
+            } else if (m <= nc) {
+                a = ra[m];
+                b = rb[m];
+            } else if (m >= n - nc) {
+                a = ra[n - m];
+                a.y = -a.y;
+                b = rb[n - m];
+                b.y = -b.y;
+            }
+            C z;
+            z.x = a.x - b.y;   // A + i B
+            z.y = a.y + b.x;
+            return z;
+        },
+        [&](int c, int x, C v) { B[c * lsb + x] = v; });
+    __syncthreads();
+    const float rn = 1.0f / (float)n;
+    for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
+        const int c = qdiv(idx, n, rn), x = idx - c * n;
+        const C v = B[c * lsb + x];
+        h[(size_t)(row0 + 2 * c) * n + x] = v.x;
+        h[(size_t)(row0 + 2 * c + 1) * n + x] = v.y;
+    }
+}
+
+// Forward x and y of one z-plane in shared memory (small grids): the n real
+// rows as n/2 complex lines, x transforms split into the half spectra
+// kx = 0..nc (the y columns), y transforms of the nc + 1 columns, keep
+// |ky| <= nc; output spec2[z][kx][ky] (plane-major).
+template <typename R>
+__global__ void __launch_bounds__(512) k2_fft_xy(Geo g, FftPlanDev fp, const R* __restrict__ grid,
+                                                const typename Cx<R>::T* __restrict__ twg,
+                                                typename Cx<R>::T* __restrict__ spec2) {
+    pdl_enter();
+    using C = typename Cx<R>::T;
+    extern __shared__ unsigned char smraw[];
+    const int n = g.n, nc = g.nc, nc1 = nc + 1, K = g.K, h = n / 2, lsb = fft2_lsb(n);
+    C* tw = reinterpret_cast<C*>(smraw);
+    C* A = tw + n;                            // [n/2] phase-A rows; then the y columns P[kx][y]
+    C* B = A + h * fft2_lsa(fp.f1, fp.f2);    // [n/2][lsb] x results; then the y phase-A rows
+    fft2_twiddles(tw, twg, fp);
+    const int z = blockIdx.x;
+    const R* gz = grid + (size_t)z * n * n;
+    __syncthreads();
+    fft2_lines<R, false>(
+        A, tw, fp, h,
+        [&](int c, int x) {
+            C v;
+            v.x = gz[(size_t)(2 * c) * n + x];
+            v.y = gz[(size_t)(2 * c + 1) * n + x];
+            return v;
+        },
+        [&](int c, int k, C v) {
+            if (k <= nc || k >= n - nc) B[c * lsb + k] = v;
+        });
+    __syncthreads();
+    C* P = A;   // [nc + 1][n]: column kx over y
+    const float rh = 1.0f / (float)h;
+    for (int idx = threadIdx.x; idx < nc1 * h; idx += blockDim.x) {
+        const int k = qdiv(idx, h, rh), c = idx - k * h;
+        const C zk = B[c * lsb + k];
+        const C zm = B[c * lsb + (k == 0 ? 0 : n - k)];
+        C a, b;
+        a.x = (R)0.5 * (zk.x + zm.x);
+        a.y = (R)0.5 * (zk.y - zm.y);
+        b.x = (R)0.5 * (zk.y + zm.y);
+        b.y = (R)0.5 * (zm.x - zk.x);
+        P[k * n + 2 * c] = a;
+        P[k * n + 2 * c + 1] = b;
+    }
+    __syncthreads();
+    C* out = spec2 + (size_t)z * nc1 * K;
+    fft2_lines<R, false>(
+        B, tw, fp, nc1, [&](int kx, int y) { return P[kx * n + y]; },
+        [&](int kx, int k, C v) {
+            if (k <= nc) out[kx * K + k + nc] = v;
+            else if (k >= n - nc) out[kx * K + k - n + nc] = v;
+        });
+}
+
+// Inverse y and x of one (field, z-plane) in shared memory (small grids):
+// the plane spec3[a][z][kx][ky] zero-padded to n along y, inverse y of the
+// nc + 1 columns, then two Hermitian rows per complex line (C2R) inverse
+// along x; output h[a][z][y][x].
+template <typename R>
+__global__ void __launch_bounds__(512) k2_fft_yx(Geo g, FftPlanDev fp, const typename Cx<R>::T* __restrict__ spec3,
+                                                const typename Cx<R>::T* __restrict__ twg, R* __restrict__ h) {
+    pdl_enter();
+    using C = typename Cx<R>::T;
+    extern __shared__ unsigned char smraw[];
+    const int n = g.n, nc = g.nc, nc1 = nc + 1, K = g.K, hn = n / 2, lsb = fft2_lsb(n);
+    C* tw = reinterpret_cast<C*>(smraw);
+    C* A = tw + n;                             // [n/2] phase-A rows
+    C* Yc = A + hn * fft2_lsa(fp.f1, fp.f2);   // [nc + 1][lsb]: inverse y results [kx][y]
+    fft2_twiddles(tw, twg, fp);
+    const int az = blockIdx.x;   // a * n + z
+    const C* in = spec3 + (size_t)az * nc1 * K;
+    __syncthreads();
+    fft2_lines<R, true>(
+        A, tw, fp, nc1,
+        [&](int kx, int m) {
+            const int ky = m <= n / 2 ? m : m - n;
+            C v;
+            v.x = (R)0;
+            v.y = (R)0;
+            if (ky >= -nc && ky <= nc) v = in[kx * K + (ky + nc)];
+            return v;
+        },
+        [&](int kx, int y, C v) { Yc[kx * lsb + y] = v; });
+    __syncthreads();
+    R* out = h + (size_t)az * n * n;
+    fft2_lines<R, true>(
+        A, tw, fp, hn,
+        [&](int c, int m) {
+            C a, b;
+            a.x = a.y = b.x = b.y = (R)0;
+            if (m == 0) {
+                a.x = Yc[2 * c].x;
+                b.x = Yc[2 * c + 1].x;
+            } else if (m <= nc) {
+                a = Yc[m * lsb + 2 * c];
+                b = Yc[m * lsb + 2 * c + 1];
+            } else if (m >= n - nc) {
+                a = Yc[(n - m) * lsb + 2 * c];
+                a.y = -a.y;
+                b = Yc[(n - m) * lsb + 2 * c + 1];
+                b.y = -b.y;
+            }
+            C zz;
+            zz.x = a.x - b.y;   // A + i B
+            zz.y = a.y + b.x;
+            return zz;
+        },
+        [&](int c, int x, C v) {
+            out[(size_t)(2 * c) * n + x] = v.x;
+            out[(size_t)(2 * c + 1) * n + x] = v.y;
+        });
+}
+
+}  // namespace enuf
+
+namespace enuf {
+
+// ---------------------------------------------------------------------------
+// a2 (FP32): footprint spreading on bricks, optionally fused with the forward
+// x pass (the NFFT's window convolution followed by its FFT, Sec. 3.3 and
+// Eq. 14, without the grid's round trip through memory).
+// One CTA per brick [x0, x0 + BX) x [y0, y0 + T) x [z0, z0 + T) of the grid
+// (BX a multiple of the tile edge T dividing n), one warp per z-plane of the
+// brick (T warps). Candidates are the charged beads of the tiles around the
+// brick (x tiles x0/T - 1 .. (x0 + BX)/T, y and z tiles +-1, periodic), the
+// items those whose window meets the brick. Per item, the warp that owns
+// plane z adds q w_z w_y w_x into the item's (x, y) taps inside the brick,
+// lanes over the taps: every lane of a warp writes a distinct address and no
+// other warp writes that plane, so there are no atomics, and no multiply-add
+// is spent on a weight outside the item's window (the column form multiplies
+// every column of its tile by every z-slot).
+// FX (BX = n, T even): the brick's T^2 rows of length n are then transformed
+// along x (R2C, two rows per complex line, the two-factor kernels' line
+// transform) and written as spec1[z][kx][y] for kx <= nc; otherwise the brick
+// is written to the grid.
+// ---------------------------------------------------------------------------
+static_assert(kBrickTaps == kMaxTaps, "brick weight rows hold the widest window");
+
+template <typename R, bool FX>
+__global__ void __launch_bounds__(768) k_spread_brick(Geo g, FftPlanDev fp, int BX, const int* __restrict__ tstart,
+                                                      const typename V4<R>::T* __restrict__ sq,
+                                                      const int* __restrict__ sb, const R* __restrict__ wb,
+                                                      R* __restrict__ grid, const typename Cx<R>::T* __restrict__ twg,
+                                                      typename Cx<R>::T* __restrict__ spec1, int LP) {
+    pdl_enter();
+    using C = typename Cx<R>::T;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int T = g.T, n = g.n, p = g.p, P2 = 2 * p, ntd = g.ntd;
+    R* acc = reinterpret_cast<R*>(smraw);                          // [T][T][BX]
+    unsigned char* stage = smraw + (size_t)T * T * BX * sizeof(R);
+    int* cslot = reinterpret_cast<int*>(stage);                    // [kBrickCand]
+    int* cbase = cslot + kBrickCand;                               // [kBrickCand]
+    R* cq = reinterpret_cast<R*>(cbase + kBrickCand);              // [kBrickCand]
+    int* items = reinterpret_cast<int*>(cq + kBrickCand);          // [kBrickCand] candidate indices
+    R* wt = reinterpret_cast<R*>(items + kBrickCand);              // [kBrickItems][3][kMaxTaps]
+    int* ibase = reinterpret_cast<int*>(wt + kBrickItems * 3 * kMaxTaps);   // [kBrickItems]
+    R* iq = reinterpret_cast<R*>(ibase + kBrickItems);             // [kBrickItems]
+    __shared__ int rstart[kBrickRanges], rpre[kBrickRanges + 1];
+    __shared__ int nranges, nitems;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nbx = n / BX;
+    const int bxi = blockIdx.x % nbx, byz = blockIdx.x / nbx;
+    const int ty = byz % ntd, tz = byz / ntd;
+    const int x0 = bxi * BX, y0 = ty * T, z0 = tz * T;
+    for (int e = tid; e < T * T * BX; e += blockDim.x) acc[e] = (R)0;
+    if (warp == 0) {   // runs of sorted beads: the x tiles around the brick in each of the <= 9 (y, z) tile rows
+        const int noy = ntd >= 3 ? 3 : ntd;
+        const int nrow = noy * noy;
+        const int ntx = BX / T;
+        const bool full = ntx + 2 >= ntd;   // the whole row of x tiles
+        int st = 0, c = 0;
+        if (lane < 2 * nrow) {
+            const int r = lane >> 1, half = lane & 1;
+            const int dy = r % noy, dz = r / noy;
+            const int yy = ntd >= 3 ? (ty + dy - 1 + ntd) % ntd : dy;
+            const int zz = ntd >= 3 ? (tz + dz - 1 + ntd) % ntd : dz;
+            const int row = (zz * ntd + yy) * ntd;
+            int a = 0, b = -1;   // x tiles [a, b] of this half
+            if (full) {
+                if (!half) { a = 0; b = ntd - 1; }
+            } else {
+                int ta = bxi * ntx - 1, tb = bxi * ntx + ntx;   // inclusive, may leave [0, ntd)
+                if (ta < 0) {        // [ntd - 1] and [0, tb]
+                    if (half) { a = ntd - 1; b = ntd - 1; } else { a = 0; b = tb; }
+                } else if (tb >= ntd) {   // [ta, ntd - 1] and [0, tb - ntd]
+                    if (half) { a = 0; b = tb - ntd; } else { a = ta; b = ntd - 1; }
+                } else if (!half) {
+                    a = ta;
+                    b = tb;
+                }
+            }
+            if (b >= a) {
+                st = tstart[row + a];
+                c = tstart[row + b + 1] - st;
+            }
+        }
+        int x = c;
+#pragma unroll
+        for (int of = 1; of < 32; of <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, of);
+            if (lane >= of) x += y;
+        }
+        if (lane < 2 * nrow) {
+            rstart[lane] = st;
+            rpre[lane] = x - c;
+        }
+        if (lane == 2 * nrow - 1) {
+            rpre[2 * nrow] = x;
+            nranges = 2 * nrow;
+        }
+    }
+    __syncthreads();
+    const int nr = nranges, total = rpre[nr];
+    // this lane's tap pair (a, b): a = lane % P2, b = lane / P2 + k rpi
+    const int rpi = 32 / P2, la = lane % P2, lb = lane / P2;
+    const int z = z0 + warp;   // this warp's plane (warp < T)
+    for (int cb = 0; cb < total; cb += kBrickCand) {
+        const int cn = min(kBrickCand, total - cb);
+        if (tid == 0) nitems = 0;
+        for (int idx = tid; idx < cn; idx += blockDim.x) {   // stage: one thread per candidate
+            const int f = cb + idx;
+            int lo = 0, hi = nr;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (rpre[mid] <= f) lo = mid; else hi = mid;
+            }
+            const int j = rstart[lo] + f - rpre[lo];
+            cslot[idx] = j;
+            cbase[idx] = sb[j];
+            cq[idx] = sq[j].w;
+        }
+        __syncthreads();
+        for (int c0 = 0; c0 < cn; c0 += blockDim.x) {   // items: the window meets the brick
+            const int c = c0 + tid;
+            bool keep = false;
+            if (c < cn) {
+                const int pb = cbase[c];
+                keep = tap_mask((pb >> 20) & 1023, z0, T, n, ntd, p) != 0u &&
+                       tap_mask((pb >> 10) & 1023, y0, T, n, ntd, p) != 0u;
+                if (keep && BX < n) {   // x: some tap in [x0, x0 + BX)
+                    int l = (pb & 1023) - p + 1 - x0;
+                    l = l < 0 ? l + n : (l >= n ? l - n : l);
+                    keep = l < BX || l + P2 > n;
+                }
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            int basei = 0;
+            if (lane == 0 && bal) basei = atomicAdd(&nitems, __popc(bal));
+            basei = __shfl_sync(0xffffffffu, basei, 0);
+            const int at = basei + __popc(bal & ((1u << lane) - 1u));
+            if (keep && ENUF_GUARD(g.check, at < kBrickCand, 3)) items[at] = c;
+        }
+        __syncthreads();
+        const int ni = nitems;
+        for (int ib = 0; ib < ni; ib += kBrickItems) {
+            const int nb = min(kBrickItems, ni - ib);
+            for (int e = tid; e < nb * 3 * P2; e += blockDim.x) {   // the batch's window weights
+                const int i = e / (3 * P2), r = e - i * (3 * P2);
+                const int c = items[ib + i];
+                wt[i * 3 * kMaxTaps + (r / P2) * kMaxTaps + r % P2] = wb[(size_t)cslot[c] * 3 * P2 + r];
+                if (r == 0) {
+                    ibase[i] = cbase[c];
+                    iq[i] = cq[c];
+                }
+            }
+            __syncthreads();
+            if (warp < T) {
+                R* plane = acc + warp * T * BX;
+                for (int i = 0; i < nb; ++i) {
+                    const int pb = ibase[i];
+                    int az = z - ((pb >> 20) & 1023) + p - 1;   // tap of plane z
+                    az = az < 0 ? az + n : (az >= n ? az - n : az);
+                    if (az >= P2) continue;                      // warp-uniform
+                    const R* w = wt + i * 3 * kMaxTaps;
+                    int x = (pb & 1023) - p + 1 + la;
+                    x = x < 0 ? x + n : (x >= n ? x - n : x);
+                    x -= x0;
+                    if (lb < rpi && x >= 0 && x < BX) {
+                        const R wxz = iq[i] * w[2 * kMaxTaps + az] * w[la];
+                        const int yb = ((pb >> 10) & 1023) - p + 1 - y0;
+                        for (int b = lb; b < P2; b += rpi) {
+                            int y = yb + b;
+                            y = y < 0 ? y + n : (y >= n ? y - n : y);
+                            if (y < T) plane[y * BX + x] += wxz * w[kMaxTaps + b];
+                        }
+                    }
+                    // the next item may add into addresses this item's lanes wrote
+                    __syncwarp();
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if constexpr (!FX) {   // write the brick: rows of BX points
+        for (int e = tid; e < T * T * BX; e += blockDim.x) {
+            const int r = e / BX, x = e - r * BX;
+            const int zz = r / T, yy = r - zz * T;
+            grid[((size_t)(z0 + zz) * n + (y0 + yy)) * n + x0 + x] = acc[e];
+        }
+    } else {   // forward x of the brick's rows (BX = n), kx <= nc, into spec1[z][kx][y]
+        const int nc = g.nc, nc1 = nc + 1, lsb = fft2_lsb(n);
+        C* tw = reinterpret_cast<C*>(stage);
+        C* A = tw + n;
+        C* B = A + LP * fft2_lsa(fp.f1, fp.f2);
+        fft2_twiddles(tw, twg, fp);
+        const int npair = T * T / 2;
+        for (int c0 = 0; c0 < npair; c0 += LP) {
+            const int nl = min(LP, npair - c0);
+            __syncthreads();
+            fft2_lines<R, false>(
+                A, tw, fp, nl,
+                [&](int c, int x) {
+                    C v;
+                    v.x = acc[(size_t)(2 * (c0 + c)) * n + x];
+                    v.y = acc[(size_t)(2 * (c0 + c) + 1) * n + x];
+                    return v;
+                },
+                [&](int c, int k, C v) {
+                    if (k <= nc || k >= n - nc) B[c * lsb + k] = v;
+                });
+            __syncthreads();
+            for (int idx = tid; idx < nl * nc1; idx += blockDim.x) {
+                const int k = idx / nl, c = idx - k * nl;
+                const C zk = B[c * lsb + k];
+                const C zm = B[c * lsb + (k == 0 ? 0 : n - k)];
+                C a, b;
+                a.x = (R)0.5 * (zk.x + zm.x);
+                a.y = (R)0.5 * (zk.y - zm.y);
+                b.x = (R)0.5 * (zk.y + zm.y);
+                b.y = (R)0.5 * (zm.x - zk.x);
+                const int r = 2 * (c0 + c), zz = r / T, yy = r - zz * T;   // rows r, r + 1: y and y + 1
+                C* dst = spec1 + ((size_t)(z0 + zz) * nc1 + k) * n + y0 + yy;
+                dst[0] = a;
+                dst[1] = b;
+            }
+        }
+    }
+}
+
+}  // namespace enuf

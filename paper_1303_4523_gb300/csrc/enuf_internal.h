@@ -64,6 +64,23 @@ struct Geo {
 // shared memory (blocks with more take the unstaged path).
 constexpr int kDpdCap = 896;
 
+// Footprint spreading on bricks (k_spread_brick): staging capacities and the
+// shared memory of a brick of T x T rows of BX points (fx_bytes: the fused x
+// pass's twiddles and line buffers, which reuse the staging region).
+constexpr int kBrickCand = 512;    // candidates staged per round
+constexpr int kBrickItems = 64;    // items per weight batch
+constexpr int kBrickRanges = 18;   // contiguous runs of sorted beads around a brick
+constexpr int kBrickTaps = 16;     // weight row length (2p <= 16)
+template <typename R>
+__host__ __device__ constexpr int brick_stage_bytes() {
+    return kBrickCand * (4 + 4 + (int)sizeof(R) + 4) +
+           kBrickItems * (3 * kBrickTaps * (int)sizeof(R) + 4 + (int)sizeof(R));
+}
+template <typename R>
+__host__ __device__ constexpr int brick_smem(int T, int BX, int fx_bytes) {
+    return T * T * BX * (int)sizeof(R) + (brick_stage_bytes<R>() > fx_bytes ? brick_stage_bytes<R>() : fx_bytes);
+}
+
 // Row length of the real-space kernel table (16-byte aligned rows).
 constexpr int kKtStride64 = 6;   // c_0..c_5 in double
 constexpr int kKtStride32 = 8;   // c_0..c_5 in float, 2 padding
@@ -83,6 +100,11 @@ struct FftShape {
     int fused;
     int t_xy, t_yx, smem_xy, smem_yx;
     int composite;   // the radix plan uses 6, 10, 12, 16 or 20 (FP32): the CR kernel instances
+    int two;         // FP32 two-factor kernels (FftPlanDev::f1, f2), same shapes and layouts
+    // spreading: 1 tile form, 2 footprint bricks into the grid, 3 bricks fused with
+    // the forward x pass (the x pass kernel is then not launched)
+    int spread;
+    int brick_x, brick_threads, brick_smem, brick_grid, brick_lp;
 };
 
 // Device workspace of one plan (all pointers device memory, one allocation).
@@ -151,6 +173,10 @@ struct DpdDev {
     double cinv;   // ncd / L
     float xmaxf;   // largest float below L
     uint64_t seed;
+    // Philox4x32-10 round keys of the seed (key bumped by the Weyl constants
+    // each round), formed on the host: the kernel's rounds read them as
+    // launch constants
+    uint32_t rk0[10], rk1[10];
     void* pos; void* vel; void* v0; void* F; void* q;   // real
     int* type;
     void* atab;        // real [ntypes^2]

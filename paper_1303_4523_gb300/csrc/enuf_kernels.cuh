@@ -1915,32 +1915,52 @@ __global__ void k_cell_scatter(int N, double L, float xmaxf, const R* __restrict
 }
 
 // Philox4x32-10 (Salmon et al., SC'11): 10 rounds of two 32x32->64 products,
-// key bumped by the Weyl constants between rounds.
-__device__ __forceinline__ uint32_t philox_word0(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
-                                                 uint32_t k0, uint32_t k1) {
+// key bumped by the Weyl constants between rounds. theta_ij draws word 0 of
+// the counter (min(i,j), max(i,j), step_lo, step_hi) under key = seed. Within
+// a launch the key and the step are fixed: the round keys come from the host
+// (DpdDev::rk0/rk1, read as launch constants) and the first round's product
+// of the counter word step_lo is formed once per thread (PhiloxStep); a draw
+// then costs one wide multiply for word 0 in the first round, two per round
+// after it, and one in the last (whose other outputs are not used).
+struct PhiloxStep {
+    uint32_t lo1, hi1;   // 0xCD9E8D57 * step_lo
+    uint32_t x2;         // step_hi ^ round key 1 of round 0
+};
+__device__ __forceinline__ PhiloxStep philox_step(const DpdDev& d, uint64_t step) {
+    const uint64_t p = (uint64_t)0xCD9E8D57u * (uint32_t)step;
+    PhiloxStep ps;
+    ps.lo1 = (uint32_t)p;
+    ps.hi1 = (uint32_t)(p >> 32);
+    ps.x2 = (uint32_t)(step >> 32) ^ d.rk1[0];
+    return ps;
+}
+__device__ __forceinline__ uint32_t philox_word0(uint32_t c0, uint32_t c1, const PhiloxStep& ps, const DpdDev& d) {
+    // round 0: the product of word 2 is the launch's
+    const uint64_t p00 = (uint64_t)0xD2511F53u * c0;
+    uint32_t n0 = ps.hi1 ^ c1 ^ d.rk0[0];
+    uint32_t n1 = ps.lo1;
+    uint32_t n2 = (uint32_t)(p00 >> 32) ^ ps.x2;
+    uint32_t n3 = (uint32_t)p00;
 #pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        if (r > 0) {
-            k0 += 0x9E3779B9u;
-            k1 += 0xBB67AE85u;
-        }
-        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
-        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
-        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
-        c0 = n0;
-        c1 = lo1;
-        c2 = n2;
-        c3 = lo0;
+    for (int r = 1; r < 9; ++r) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * n0;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * n2;
+        const uint32_t m0 = (uint32_t)(p1 >> 32) ^ n1 ^ d.rk0[r];
+        const uint32_t m2 = (uint32_t)(p0 >> 32) ^ n3 ^ d.rk1[r];
+        n1 = (uint32_t)p1;
+        n3 = (uint32_t)p0;
+        n0 = m0;
+        n2 = m2;
     }
-    return c0;
+    // round 9: word 0 only
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * n2;
+    return (uint32_t)(p1 >> 32) ^ n1 ^ d.rk0[9];
 }
 
-// theta_ij of Eq. 5: uniform on [-sqrt3, sqrt3], counter (min, max, step), key = seed.
+// theta_ij of Eq. 5: uniform on [-sqrt3, sqrt3].
 template <typename R>
-__device__ __forceinline__ R dpd_theta(uint64_t seed, uint64_t step, int i, int j) {
-    const uint32_t lo = (uint32_t)min(i, j), hi = (uint32_t)max(i, j);
-    const uint32_t w = philox_word0(lo, hi, (uint32_t)step, (uint32_t)(step >> 32), (uint32_t)seed,
-                                    (uint32_t)(seed >> 32));
+__device__ __forceinline__ R dpd_theta(const PhiloxStep& ps, const DpdDev& d, int i, int j) {
+    const uint32_t w = philox_word0((uint32_t)min(i, j), (uint32_t)max(i, j), ps, d);
     // sqrt3 (2 u - 1) with u = (w + 1/2) 2^-32
     return fma((R)w, (R)(2.0 * 1.7320508075688772935 * 2.3283064365386962890625e-10),
                (R)(1.7320508075688772935 * (2.3283064365386962890625e-10 - 1.0)));
@@ -1989,7 +2009,7 @@ template <typename R, typename V, bool STAGED>
 __device__ __forceinline__ void dpd_pairs(const bool valid, const int2 e, const V* __restrict__ P,
                                           const V* __restrict__ Pv, R* __restrict__ F,
                                           const R* __restrict__ atab, int ntypes, R L, R hL, R gam, R srdt,
-                                          uint64_t seed, uint64_t step, R& ec) {
+                                          const PhiloxStep& ps, const DpdDev& d, R& ec) {
     const int lane = threadIdx.x & 31;
     R fx = 0, fy = 0, fz = 0;
     int key = -1, oi = 0;
@@ -2009,7 +2029,7 @@ __device__ __forceinline__ void dpd_pairs(const bool valid, const int2 e, const 
         const int ti = real_as_int(vi.w), tj = real_as_int(vj.w);
         const R a = atab[ti * ntypes + tj];
         const R vd = (vi.x - vj.x) * rx + (vi.y - vj.y) * ry + (vi.z - vj.z) * rz;   // r_ij . v_ij
-        const R th = dpd_theta<R>(seed, step, i, j);
+        const R th = dpd_theta<R>(ps, d, i, j);
         // Eq. 3-5 with w^D = (w^R)^2 = w^2: |F| = w (a - gamma w (r.v)/r + sigma theta/sqrt(dt))
         const R wi = w * ir;
         const R fm = wi * fma(-gam * wi, vd, fma(srdt, th, a));
@@ -2091,6 +2111,7 @@ __device__ __forceinline__ void dpd_cells(const DpdDev& d, int H, int B3, const 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const R L = (R)d.L, hL = (R)(0.5 * d.L);
     const R gam = (R)d.gamma, srdt = (R)(d.sigma * d.rdt);
+    const PhiloxStep ps = philox_step(d, step);
     int cnt = 0;   // queued pairs of this warp, carried across its cells
     for (int cc = warp; cc < B3; cc += NW) {
         const int h = chalo[cc];
@@ -2172,7 +2193,7 @@ __device__ __forceinline__ void dpd_cells(const DpdDev& d, int H, int B3, const 
                 if (cnt >= 32) {
                     __syncwarp();
                     dpd_pairs<R, V, STAGED>(true, queue[lane], P, Pv, F, atab, d.ntypes, L, hL, gam, srdt,
-                                            d.seed, step, ec);
+                                            ps, d, ec);
                     __syncwarp();
                     if (lane < cnt - 32) queue[lane] = queue[32 + lane];
                     __syncwarp();
@@ -2183,8 +2204,7 @@ __device__ __forceinline__ void dpd_cells(const DpdDev& d, int H, int B3, const 
     }
     __syncwarp();
     if (cnt > 0)
-        dpd_pairs<R, V, STAGED>(lane < cnt, queue[lane], P, Pv, F, atab, d.ntypes, L, hL, gam, srdt, d.seed,
-                                step, ec);
+        dpd_pairs<R, V, STAGED>(lane < cnt, queue[lane], P, Pv, F, atab, d.ntypes, L, hL, gam, srdt, ps, d, ec);
 }
 
 template <typename R>

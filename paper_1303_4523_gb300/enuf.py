@@ -38,13 +38,14 @@ class enuf_params(C.Structure):
                 ("beta", C.c_double), ("kappa", C.c_double), ("M", C.c_int), ("p", C.c_int),
                 ("sigma_s", C.c_int), ("kmask", C.c_int), ("prec", C.c_int), ("tile", C.c_int),
                 ("deriv", C.c_int), ("slater_k", C.c_int), ("fft_path", C.c_int), ("fft_radix", C.c_int),
-                ("reserved", C.c_int * 2)]
+                ("spread", C.c_int), ("reserved", C.c_int * 1)]
 
 
 class enuf_plan_info(C.Structure):
     _fields_ = [("M", C.c_int), ("n", C.c_int), ("n_c", C.c_int), ("tile", C.c_int),
                 ("n_tiles", C.c_int), ("n_max", C.c_int), ("fft_kernels", C.c_int),
-                ("device_bytes", C.c_size_t), ("fft_stages", C.c_int), ("fft_radix", C.c_int * 8)]
+                ("device_bytes", C.c_size_t), ("fft_stages", C.c_int), ("fft_radix", C.c_int * 8),
+                ("fft_two_factor", C.c_int), ("spread", C.c_int), ("brick_x", C.c_int)]
 
 
 class dpd_params(C.Structure):
@@ -121,11 +122,11 @@ def _check(status, handle=None, what=""):
 
 
 def make_params(L, alpha, r_cut, beta, kappa, M=0, p=4, sigma_s=2, kmask=0,
-                prec="fp64", tile=0, deriv=0, slater_k=0, fft_path=0, fft_radix=0) -> enuf_params:
+                prec="fp64", tile=0, deriv=0, slater_k=0, fft_path=0, fft_radix=0, spread=0) -> enuf_params:
     pr = {"fp64": ENUF_FP64, "fp32": ENUF_FP32}[prec] if isinstance(prec, str) else int(prec)
     return enuf_params(float(L), float(alpha), float(r_cut), float(beta), float(kappa), int(M),
                        int(p), int(sigma_s), int(kmask), pr, int(tile), int(deriv), int(slater_k),
-                       int(fft_path), int(fft_radix), (C.c_int * 2)())
+                       int(fft_path), int(fft_radix), int(spread), (C.c_int * 1)())
 
 
 def _ptr(x):

@@ -27,11 +27,13 @@ def _q(n=1000, charged=100):
 
 def test_candidates_are_the_legal_tiles(mods):
     A, E = mods
-    # n = 96: the divisors of n in [p, 24]; FP32 grids with n <= 112 also try the five-pass FFT
+    # n = 96: the divisors of n in [p, 24]; FP32 grids with n <= 112 also try the five-pass
+    # FFT, and the Stockham stages against the two-factor kernels (radix 1 and 2 agree
+    # below n = 128)
     c32 = A.candidates(E.make_params(prec="fp32", **BASE), 81000)
     assert sorted({c["tile"] for c in c32}) == [4, 6, 8, 12, 16, 24]
-    assert {c["fft_path"] for c in c32} == {0, 1} and len(c32) == 12
-    assert {c["fft_radix"] for c in c32} == {0}          # below n = 128 the schedules agree
+    assert {c["fft_path"] for c in c32} == {0, 1} and len(c32) == 24
+    assert {c["fft_radix"] for c in c32} == {0, 2}
     c64 = A.candidates(E.make_params(prec="fp64", **BASE), 81000)
     assert sorted(c["tile"] for c in c64) == [4, 6, 8, 12, 16, 24]
     assert {c["fft_path"] for c in c64} == {0}
@@ -39,8 +41,9 @@ def test_candidates_are_the_legal_tiles(mods):
     big = dict(BASE, L=50.0, M=80)
     c = A.candidates(E.make_params(prec="fp32", **big), 375000)
     assert sorted({x["tile"] for x in c}) == [5, 8, 10, 16, 20]
-    # from n = 128 on, FP32 also tries radices 2, 3, 4, 5, 8 only against the composite schedule
-    assert {x["fft_path"] for x in c} == {0} and {x["fft_radix"] for x in c} == {0, 1} and len(c) == 10
+    # from n = 128 on, FP32 also tries radices 2, 3, 4, 5, 8 only against the composite
+    # schedule, both against the two-factor kernels
+    assert {x["fft_path"] for x in c} == {0} and {x["fft_radix"] for x in c} == {0, 1, 2} and len(c) == 15
     c = A.candidates(E.make_params(prec="fp64", **big), 375000)
     assert {x["fft_radix"] for x in c} == {0} and len(c) == 5
     # n = 512: only tile 16 keeps the histogram within 32768 tiles, and the composite
@@ -67,13 +70,14 @@ def test_tune_keeps_the_fastest_and_caches_it(mods, tmp_path):
 
     def cost(p, n_max, pos, q):
         calls.append((p.tile, p.fft_path))
-        return abs(p.tile - 8) + 0.5 * p.fft_path + 1.0     # fastest: tile 8, fused FFT
+        # fastest: tile 8, fused FFT, two-factor kernels
+        return abs(p.tile - 8) + 0.5 * p.fft_path + 0.25 * p.fft_radix + 1.0
 
     cache = A.TuneCache(str(tmp_path / "tune.json"))
     q = _q()
     r = A.tune(params, 1000, None, q, measure=cost, cache=cache, device="dev")
     assert (r["tile"], r["fft_path"], r["cached"]) == (8, 0, False)
-    assert len(calls) == 12 and len(r["timings"]) == 12
+    assert len(calls) == 24 and len(r["timings"]) == 24
     assert params.tile == 0 and params.fft_path == 0          # the caller's params are not modified
     # a second call (and a new cache object on the same file) needs no timing
     calls.clear()
@@ -83,7 +87,7 @@ def test_tune_keeps_the_fastest_and_caches_it(mods, tmp_path):
     assert (tp.tile, tp.fft_path, tp.fft_radix) == (8, 0, 0) and tp.L == params.L and tp.p == params.p
     # force re-measures
     A.tune(params, 1000, None, q, measure=cost, cache=cache, device="dev", force=True)
-    assert len(calls) == 12
+    assert len(calls) == 24
     with open(cache.path) as f:
         d = json.load(f)
     assert d["version"] == A.CACHE_VERSION and len(d["entries"]) == 1
@@ -166,7 +170,8 @@ def test_serving_backend_takes_cached_choices(mods, tmp_path):
 def test_tune_picks_the_radix_schedule(mods, tmp_path):
     A, E = mods
     params = E.make_params(prec="fp32", **dict(BASE, L=50.0, M=80))    # n = 160
-    r = A.tune(params, 1000, None, _q(), measure=lambda p, *a: 2.0 - p.fft_radix + 0.01 * p.tile,
+    # a cost model where the plain radices (fft_radix = 1) are fastest
+    r = A.tune(params, 1000, None, _q(), measure=lambda p, *a: 2.0 - (p.fft_radix == 1) + 0.01 * p.tile,
                cache=A.TuneCache(str(tmp_path / "t.json")), device="dev")
     assert (r["tile"], r["fft_path"], r["fft_radix"]) == (5, 0, 1)
     tp = A.cached_params(params, 100, cache=A.TuneCache(str(tmp_path / "t.json")), device="dev")

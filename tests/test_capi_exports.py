@@ -92,7 +92,7 @@ def test_method_switches_are_validated_without_gpu():
     build.build()
     from paper_1303_4523_gb300 import enuf
     base = dict(L=30.0, alpha=0.975, r_cut=3.0, beta=4.0, kappa=1.1, M=48, p=4)
-    for bad in (dict(deriv=2), dict(slater_k=1, beta=0.0), dict(slater_k=2), dict(fft_path=2), dict(fft_radix=2), dict(tile=7),
+    for bad in (dict(deriv=2), dict(slater_k=1, beta=0.0), dict(slater_k=2), dict(fft_path=2), dict(fft_radix=3), dict(tile=7),
                 dict(tile=48), dict(tile=3)):
         kw = dict(base)
         kw.update(bad)
@@ -102,7 +102,7 @@ def test_method_switches_are_validated_without_gpu():
             assert e.status == 1, bad
         else:
             raise AssertionError(f"accepted {bad}")
-    for ok in (dict(deriv=1), dict(slater_k=1), dict(fft_path=1), dict(fft_radix=1), dict(tile=12), dict(tile=24)):
+    for ok in (dict(deriv=1), dict(slater_k=1), dict(fft_path=1), dict(fft_radix=1), dict(fft_radix=2), dict(tile=12), dict(tile=24)):
         kw = dict(base)
         kw.update(ok)
         assert enuf.enuf_footprint(enuf.make_params(**kw), 100) > 0, ok

@@ -63,7 +63,7 @@ def _gpu(enuf, prec, P, pos, q, n_max=None):
 
 def _oparams(P):
     """Oracle parameters: the GPU-only tiling and FFT-path choices do not change the result."""
-    return orc.EwaldParams(**{k: v for k, v in P.items() if k not in ("tile", "fft_path")})
+    return orc.EwaldParams(**{k: v for k, v in P.items() if k not in ("tile", "fft_path", "fft_radix", "spread")})
 
 
 class Ref:
@@ -189,14 +189,15 @@ def test_default_tile_can_be_odd(enuf):
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_fft_stage_plans(enuf, prec):
-    """The line transforms' radix plans: 2, 3, 4, 5, 8 (greedy order), and
-    in FP32 from n = 128 on the two-stage plans with the composite radices."""
+    """The Stockham stages' radix plans (fft_radix = 2): 2, 3, 4, 5, 8 (greedy
+    order), and in FP32 from n = 128 on the two-stage plans with the composite
+    radices."""
     want = {16: [8, 2], 32: [8, 4], 96: [8, 4, 3], 128: [8, 8, 2], 160: [8, 5, 4], 192: [8, 8, 3]}
     if prec == "fp32":
         want.update({128: [16, 8], 160: [20, 8], 192: [16, 12]})
     for n, rad in want.items():
         plan = enuf.Plan(enuf.make_params(prec=prec, L=2.0 * n, alpha=1.0, r_cut=3.0, beta=0.0, kappa=1.0,
-                                          M=n // 2, p=4), 16)
+                                          M=n // 2, p=4, fft_radix=2), 16)
         info = plan.info
         assert list(info.fft_radix[:info.fft_stages]) == rad, (n, list(info.fft_radix[:info.fft_stages]))
         plan.close()
@@ -212,8 +213,55 @@ def test_five_pass_fft_parity(enuf, name, prec, deriv):
     P = dict(P, fft_path=1, deriv=deriv)
     pos, q = _inputs(prec, pos, q)
     plan, F, E, Wv = _gpu(enuf, prec, P, pos, q)
-    assert plan.info.fft_kernels == 5
+    # five line passes, or four when the spreading kernel does the x pass
+    assert plan.info.fft_kernels == (4 if plan.info.spread == 3 else 5)
     _check(prec, F, E, Wv, Ref(P, pos, q))
+    plan.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("fft_path", [0, 1])
+def test_fp32_stockham_parity(enuf, name, fft_path):
+    """FP32 on the Stockham stages (fft_radix = 2) instead of the two-factor
+    kernels, fused plane passes where they apply and the five line passes."""
+    P, pos, q = _case(name)
+    P = dict(P, fft_radix=2, fft_path=fft_path)
+    pos, q = _inputs("fp32", pos, q)
+    plan, F, E, Wv = _gpu(enuf, "fp32", P, pos, q)
+    assert plan.info.fft_two_factor == 0
+    _check("fp32", F, E, Wv, Ref(P, pos, q))
+    plan.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("form", [1, 2, 3])
+def test_fp32_spread_forms_parity(enuf, name, form):
+    """FP32 spreading forms on the five-pass FFT: the tile form (1), footprint
+    bricks written to the grid (2) and bricks fused with the forward x pass
+    (3, where the two-factor kernels run and the tile edge is even)."""
+    P, pos, q = _case(name)
+    P = dict(P, fft_path=1, spread=form)
+    pos, q = _inputs("fp32", pos, q)
+    shape = enuf.plan_shape(enuf.make_params(prec="fp32", **P), len(q)) if form != 3 else None
+    if form == 3:
+        # the fused form needs the two-factor kernels, an even tile and a brick of
+        # T^2 rows of n points plus >= 2 line pairs of the x transform in 200 KB
+        probe = enuf.plan_shape(enuf.make_params(prec="fp32", **dict(P, spread=2)), len(q))
+        n, T = probe.n, probe.tile
+        f1, f2 = probe.fft_radix[0], probe.fft_radix[1]
+        lp = min(16, T * T // 2, (200 * 1024 - T * T * n * 4 - 8 * n) // ((f1 * (f2 + 1) + n + 1) * 8))
+        if not (probe.fft_two_factor and T % 2 == 0 and lp >= 2):
+            with pytest.raises(enuf.EnufError):
+                enuf.plan_shape(enuf.make_params(prec="fp32", **P), len(q))
+            return
+    plan, F, E, Wv = _gpu(enuf, "fp32", P, pos, q)
+    assert plan.info.spread == form and (form == 1 or plan.info.brick_x % plan.info.tile == 0)
+    assert shape is None or shape.spread == form
+    _check("fp32", F, E, Wv, Ref(P, pos, q))
+    if form == 2:   # the grid itself against the oracle's spread grid
+        grid = plan.debug_buffer(enuf.ENUF_BUF_GRID).astype(np.float64)
+        _, _, g_ref, _ = orc.recip_enuf(_oparams(P), pos, q, want_grid=True)
+        assert np.abs(grid - g_ref).max() < TOL["fp32"]["stage"] * np.abs(g_ref).max()
     plan.close()
 
 

@@ -21,17 +21,17 @@ def _radices(info):
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_radix_schedules(enuf, prec):
-    """Fewest stages over 2, 3, 4, 5, 8; FP32 grids from n = 128 on take the
-    composite radices 6, 10, 12, 16, 20 when that saves a stage, unless
-    fft_radix = 1."""
+    """Stockham stages (fft_radix = 2, FP64's default): fewest stages over
+    2, 3, 4, 5, 8; FP32 grids from n = 128 on take the composite radices 6,
+    10, 12, 16, 20 when that saves a stage, unless fft_radix = 1."""
     want = {16: [8, 2], 32: [8, 4], 36: [4, 3, 3], 60: [5, 4, 3], 96: [8, 4, 3], 128: [8, 8, 2],
             160: [8, 5, 4], 192: [8, 8, 3], 320: [8, 8, 5], 512: [8, 8, 8]}
     if prec == "fp32":
         want.update({128: [16, 8], 160: [20, 8], 192: [16, 12], 320: [20, 16]})
     for n, rad in want.items():
         kw = dict(prec=prec, L=2.0 * n, alpha=1.0, r_cut=3.0, beta=0.0, kappa=1.0, M=n // 2, p=4)
-        info = _shape(enuf, **kw)
-        assert info.n == n and _radices(info) == rad, (n, _radices(info))
+        info = _shape(enuf, fft_radix=2, **kw)
+        assert info.n == n and _radices(info) == rad and not info.fft_two_factor, (n, _radices(info))
         prod = 1
         for r in rad:
             prod *= r
@@ -40,6 +40,24 @@ def test_radix_schedules(enuf, prec):
         assert all(r in (2, 3, 4, 5, 8) for r in plain) and len(plain) >= len(rad)
         if prec == "fp64" or n < 128:
             assert plain == rad
+
+
+def test_two_factor_split(enuf):
+    """FP32 plans with fft_radix = 0 run the two-factor kernels when n = f1 f2
+    with both factors in {4, 5, 6, 8, 10, 12, 16, 20}: the most balanced split,
+    ties to the larger f2; other n (and FP64) keep the Stockham stages."""
+    want = {16: (4, 4), 32: (4, 8), 36: (6, 6), 40: (5, 8), 48: (6, 8), 60: (6, 10), 64: (8, 8),
+            72: (6, 12), 80: (8, 10), 96: (8, 12), 100: (10, 10), 128: (8, 16), 160: (10, 16),
+            192: (12, 16), 200: (10, 20), 256: (16, 16), 320: (16, 20), 400: (20, 20)}
+    for n, (f1, f2) in want.items():
+        kw = dict(L=2.0 * n, alpha=1.0, r_cut=3.0, beta=0.0, kappa=1.0, M=n // 2, p=4)
+        info = _shape(enuf, prec="fp32", **kw)
+        assert info.fft_two_factor == 1 and _radices(info) == [f1, f2], (n, _radices(info))
+        assert _shape(enuf, prec="fp64", **kw).fft_two_factor == 0
+    for n in (8, 12, 108, 180, 216, 288, 512):   # no split into two of the radices
+        kw = dict(L=2.0 * n, alpha=1.0, r_cut=min(3.0, n), beta=0.0, kappa=1.0, M=n // 2, p=2)
+        info = _shape(enuf, prec="fp32", **kw)
+        assert info.fft_two_factor == 0 and _radices(info) == _radices(_shape(enuf, prec="fp32", fft_radix=2, **kw))
 
 
 def test_fft_path(enuf):

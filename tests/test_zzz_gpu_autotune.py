@@ -35,8 +35,9 @@ def _run(enuf, params, pos, q):
     E, _ = plan.energy_forces(pos, q, F)
     info = plan.info
     radices = [info.fft_radix[i] for i in range(info.fft_stages)]
+    two = info.fft_two_factor
     plan.close()
-    return F.double().cpu().numpy(), E, info.tile, radices
+    return F.double().cpu().numpy(), E, info.tile, (two, radices)
 
 
 @pytest.mark.parametrize("name,prec,tol", [("electrolyte_M16", "fp32", 1e-5), ("electrolyte_M16", "fp64", 1e-11),
@@ -54,10 +55,13 @@ def test_every_candidate_matches_the_default_plan(mods, tmp_path, name, prec, to
     for c in cands:
         F, E, t, rad = _run(enuf, A._copy(params, **c), pos, q)
         assert t == c["tile"]
+        two, radices = rad
         if c["fft_radix"] == 1:
-            assert all(r in (2, 3, 4, 5, 8) for r in rad) and len(rad) >= len(rad0), (rad, rad0)
-        else:
+            assert not two and all(r in (2, 3, 4, 5, 8) for r in radices), rad
+        elif c["fft_radix"] == 0:
             assert rad == rad0
+        else:
+            assert not two
         rel = np.sqrt(((F - F0) ** 2).sum() / (F0 ** 2).sum())
         assert rel <= 2 * tol, (c, rel)          # both within tol of the oracle
         assert abs(E[3] - E0[3]) <= 10 * tol * abs(E0[3]), (c, E, E0)
