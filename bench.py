@@ -175,8 +175,8 @@ def run_ours(args, rank, world, dist):
         if dist is not None:
             dist.barrier()
 
-    def run_prec(prec, steps, warmup, timing, deriv=0):
-        plan = enuf.Plan(enuf.make_params(prec=prec, deriv=deriv, **P), s.N)
+    def run_prec(prec, steps, warmup, timing, deriv=0, pairs=0):
+        plan = enuf.Plan(enuf.make_params(prec=prec, deriv=deriv, pairs=pairs, **P), s.N)
         sysm = enuf.DpdSystem(plan, dp["a"], dp["gamma"], dp["sigma"], dp["dt"], s.pos, s.vel, s.types, s.q,
                               s.bonds, lambda_vv=dp["lambda_vv"], K_bond=dp["K_bond"], r0_bond=dp["r0_bond"],
                               seed=dp["seed"])
@@ -202,13 +202,15 @@ def run_ours(args, rank, world, dist):
         barrier()
         per = [a.elapsed_time(b) for a, b in ev]
         if timing:   # stage breakdown from a separate pass with per-stage events
+            # (with the pairs in one launch the "real" stage is that launch; "dpd" has no event)
+            names = [k for k in stage_ms if not (k == "dpd" and pairs == 0)]
             plan.enable_timing(True)
             for k in range(min(steps, 20) + 2):
                 with torch.cuda.stream(st):
                     flush.fill_(float(k))
                 sysm.step(1)
                 if k >= 2:
-                    for name in stage_ms:
+                    for name in names:
                         stage_ms[name].append(plan.stage_time(name))
             plan.enable_timing(False)
         E = sysm.step(0, want_energy=True)
@@ -222,6 +224,9 @@ def run_ours(args, rank, world, dist):
     per64, wall64, clk64, stage64, E64, _ = run_prec("fp64", steps64, args.warmup, False)
     # the same step with gradient-mode reciprocal forces (one inverse transform)
     perg, _, clkg, _, Eg, _ = run_prec("fp32", steps64, args.warmup, False, deriv=1)
+    # and with the DPD and real-space pairs as two launches (enuf_params.pairs = 1); its
+    # stage events time the DPD pair kernel in its own launch (the roofline below)
+    perp, _, _, stagep, _, launches_p = run_prec("fp32", steps64, args.warmup, True, pairs=1)
 
     tot32, tot64, totg = max_over_ranks(dist, [sum(per32), sum(per64), sum(perg)], "cuda")
     ms32 = tot32 / args.steps
@@ -238,6 +243,10 @@ def run_ours(args, rank, world, dist):
     plan.close()
     ab = algorithmic_bytes(info, s.n_charged, s.N, 4)
     means = {k: (sum(v) / len(v) if v else 0.0) for k, v in stage32.items()}
+    means_sep = {k: (sum(v) / len(v) if v else 0.0) for k, v in stagep.items()}
+    means["dpd"] = means_sep["dpd"]       # k_dpd in its own launch
+    means["pairs_fused"] = means["real"]  # the headline's one launch of DPD + real-space pairs
+    means["real"] = means_sep["real"]
     npairs, how = dpd_pair_count(s)
     sm_mhz = clk32.get("sm_mhz") or 2070.0
     peak_ops = ALU_LANES * sm_mhz * 1e6 / 1e12
@@ -278,6 +287,12 @@ def run_ours(args, rank, world, dist):
                                "ms_per_step": round(totg / len(perg), 5),
                                "p50": round(sorted(perg)[len(perg) // 2], 5), "steps": len(perg),
                                "note": "reciprocal forces as the gradient of the window (deriv = 1)"},
+        "fp32_separate_pairs": {"value": job_throughput(world, len(perp), sum(perp)),
+                             "ms_per_step": round(sum(perp) / len(perp), 5),
+                             "p50": round(sorted(perp)[len(perp) // 2], 5), "steps": len(perp),
+                             "launches_per_step": launches_p,
+                             "note": "DPD and real-space pairs as two launches (pairs = 1); the headline "
+                                     "runs them as one launch (pairs = 0)"},
         "fp32_over_fp64": round(ms64 / ms32, 2),
         "energies_fp32": [round(x, 6) for x in E32[:8]],
         "energies_fp64": [round(x, 6) for x in E64[:8]],
@@ -432,10 +447,12 @@ def run_sizes(args):
     for N in (sizes if not args.sizes_n else [N for N in sizes if N in args.sizes_n]):
         s = W.electrolyte_sweep(N) if N < 3_000_000 else W.electrolyte(N, seed_offset=499)
         row = {"N": N, "L": round(s.L, 3), "M": s.M}
-        for key, prec, dt, esz, deriv in (("fp32", "fp32", torch.float32, 4, 0), ("fp64", "fp64", torch.float64, 8, 0),
-                                          ("fp32_grad", "fp32", torch.float32, 4, 1)):
+        variants = (("fp32", "fp32", torch.float32, 4, 0), ("fp64", "fp64", torch.float64, 8, 0),
+                    ("fp32_grad", "fp32", torch.float32, 4, 1))
+        for key, prec, dt, esz, deriv in (variants[:1] if args.fp32_only else variants):
             P = dict(L=s.L, M=s.M, **s.params)
-            plan = enuf.Plan(enuf.make_params(prec=prec, deriv=deriv, **P), s.N)
+            sp = args.spread if prec == "fp32" else 0
+            plan = enuf.Plan(enuf.make_params(prec=prec, deriv=deriv, spread=sp, **P), s.N)
             plan.enable_timing(True)
             pos = torch.tensor(s.pos, dtype=dt, device="cuda")
             q = torch.tensor(s.q, dtype=dt, device="cuda")
@@ -516,7 +533,17 @@ def run_batch(args):
         torch.cuda.synchronize()
         ms_batch = e0.elapsed_time(e1) / reps
         launches = b.launches()
+        mode = b.mode()
         b.close()
+        # aggregate roofline of the ENUF chain: the scope's algorithmic bytes of
+        # spreading, FFT and gathering summed over the systems, per graph replay
+        esz = 4 if prec == "fp32" else 8
+        ab = 0
+        for p, sy in zip(params, systems):
+            info = enuf.plan_shape(p, sy.N)
+            a = algorithmic_bytes(info, sy.n_charged, sy.N, esz)
+            ab += a["spread"] + a["fft"] + a["gather"]
+        peaks, peak_kind = _peaks()
         plans = [enuf.Plan(p, s.N) for p, s in zip(params, systems)]
         for _ in range(2):
             for pl, a, c, f in zip(plans, pos, q, F):
@@ -531,7 +558,14 @@ def run_batch(args):
             pl.close()
         out[prec] = {"graph_ms": round(ms_batch, 4), "systems_per_s": round(64 * 1000 / ms_batch, 1),
                      "beads_per_s": round(out["beads"] * 1000 / ms_batch, 1), "launches": launches,
-                     "one_by_one_ms": round(seq_ms, 3)}
+                     "one_launch_sequence": bool(mode), "one_by_one_ms": round(seq_ms, 3),
+                     "roofline": {"bound": "hbm", "algorithmic_bytes": ab,
+                                  "achieved_gbs": round(ab / (ms_batch * 1e-3) / 1e9, 1),
+                                  "peak_gbs": peaks["hbm_gbs"], "peak_kind": peak_kind,
+                                  "frac": round(ab / (ms_batch * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
+                                  "note": "spread + FFT + gather bytes of all systems over the whole "
+                                          "evaluation graph (binning and real space included in the time); "
+                                          "working set per system L2-resident"}}
     return out
 
 
@@ -595,6 +629,10 @@ def main():
                     help="--mode batch: pick each system's tile edge and FFT path by timing them (cached)")
     ap.add_argument("--sizes-n", type=int, nargs="*", default=None,
                     help="--mode sizes: run only these system sizes (of 3000 24000 81000 192000 375000 3000000)")
+    ap.add_argument("--spread", type=int, default=0,
+                    help="--mode sizes: FP32 spreading kernel (enuf_params.spread: 0 auto, 1 tile form, "
+                         "2 footprint bricks, 3 bricks fused with the x pass)")
+    ap.add_argument("--fp32-only", action="store_true", help="--mode sizes: skip the FP64 and gradient-mode plans")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 

@@ -103,7 +103,11 @@ typedef struct {
                          3 = form 2 fused with the forward x pass (the grid is never
                          written: needs the two-factor kernels, the five-pass FFT and
                          an even T). Same result to rounding. */
-    int    reserved[1];
+    int    pairs;     /* DPD systems: 0 = the DPD pair forces and the real-space pairs in
+                         one launch whose blocks take either role, after both cell
+                         structures exist (default; measured faster at the 81000-bead
+                         polyelectrolyte); 1 = two launches, the DPD pairs right after
+                         the cell list. Same result to rounding. */
 } enuf_params;
 
 typedef struct enuf_plan_s* enuf_plan_t;
@@ -189,13 +193,17 @@ enuf_status enuf_debug_buffer(enuf_plan_t plan, int which, void* host, size_t by
 
 /* Kernel timing: when enabled, the next captured graph records CUDA events
  * around the kernels of the given stage; enuf_stage_time() returns the
- * device time of that stage in the last evaluation (ms). Stages: */
+ * device time of that stage in the last evaluation (ms). While timing is
+ * on, the two branches of an evaluation or step (binning -> spreading -> FFT,
+ * and the real-space / DPD pairs) run one after the other, so each stage's
+ * events time its kernels alone. Stages: */
 enum { ENUF_STAGE_BIN = 0,      /* charged-bead binning (3 kernels) */
        ENUF_STAGE_SPREAD = 1,   /* spreading kernel */
        ENUF_STAGE_FFT = 2,      /* the five FFT passes incl. the fused convolution */
        ENUF_STAGE_GATHER = 3,   /* gather kernel */
-       ENUF_STAGE_REAL = 4,     /* real-space electrostatics kernel */
-       ENUF_STAGE_DPD = 5,      /* DPD pair + bond kernel */
+       ENUF_STAGE_REAL = 4,     /* real-space electrostatics kernel (in a DPD step with
+                                   enuf_params.pairs = 0: the one launch of both pair sums) */
+       ENUF_STAGE_DPD = 5,      /* DPD pair + bond kernel (pairs = 1 only) */
        ENUF_STAGE_ALL = 6,      /* the whole evaluation / DPD step */
        ENUF_STAGE_CELL = 7,     /* all-bead cell list (3 kernels) */
        ENUF_NUM_STAGES = 8 };
@@ -291,8 +299,18 @@ void dpd_destroy(dpd_system_t sys);
 typedef struct enuf_batch_s* enuf_batch_t;
 
 /* One plan per system (params[s], capacity n[s]); all systems share the
- * given stream and are evaluated by one CUDA graph with one branch per
- * system. */
+ * given stream and are evaluated by one captured CUDA graph.
+ * When every system is FP32 and its plan runs the fused-plane two-factor
+ * FFT, the column spreading form and the one-kernel binning offsets (the
+ * defaults for grids up to n = 112 of n = f1 f2), the graph is one launch
+ * sequence for all systems: each kernel of the evaluation (binning, window
+ * weights, real space, spreading -- one launch per tile edge present --,
+ * the three FFT passes, gather) is launched once over the concatenated grids
+ * of all systems, its blocks reading their system's arguments from a device
+ * table; the systems' energies go to one device array read back by one
+ * copy. Otherwise the graph holds one branch per system (enuf_batch_mode).
+ * The batch tables are written when the arrays change between calls
+ * (after waiting for the previous evaluation). */
 enuf_status enuf_batch_plan(int nsys, const enuf_params* params, const int* n, void* cuda_stream,
                             enuf_batch_t* out);
 /* pos[s], q[s], F[s]: device pointers as in enuf_energy_forces, for n[s] beads.
@@ -301,6 +319,8 @@ enuf_status enuf_batch_energy_forces(enuf_batch_t batch, const void* const* pos,
                                      const void* const* q, void* const* F, double* E);
 /* Kernel launches in one replay of the batch graph. */
 int enuf_batch_launches(enuf_batch_t batch);
+/* 1: one launch sequence over all systems; 0: one graph branch per system. */
+int enuf_batch_mode(enuf_batch_t batch);
 void enuf_batch_destroy(enuf_batch_t batch);
 
 /* ------------------------------------------------------------------ */

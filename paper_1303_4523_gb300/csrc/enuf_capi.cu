@@ -402,7 +402,9 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
         shape2(n * n / 2, 1, fs.lx, fs.tx, fs.grid_x, budget);
         shape2(n * nc1, 1, fs.ly, fs.ty, gyz, budget);
         fs.grid_y_z = (n + fs.ly - 1) / fs.ly;
-        shape2(nc1 * g.K, g.nf, fs.lz, fs.tz, fs.grid_z, 96 * 1024);
+        // the z pass holds nf field lines per line (and ~83 registers a thread):
+        // a smaller budget keeps several CTAs per SM
+        shape2(nc1 * g.K, g.nf, fs.lz, fs.tz, fs.grid_z, 56 * 1024);
         shape2(g.nf * n * nc1, 1, fs.liy, fs.tiy, fs.grid_iy, budget);
         shape2(g.nf * n * n / 2, 1, fs.lix, fs.tix, fs.grid_ix, budget);
         fs.smem_x = n * csz + fs.lx * per_line;
@@ -419,6 +421,7 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
     // two-factor five-pass FFT runs and the brick fits; footprint bricks into the
     // grid otherwise from n = 128 on; the tile form below
     if (P.spread < 0 || P.spread > 3) return fail(plan, ENUF_ERR_INVALID, "spread must be 0..3");
+    if (P.pairs != 0 && P.pairs != 1) return fail(plan, ENUF_ERR_INVALID, "pairs must be 0 or 1");
     fs.spread = 1;
     if (P.prec == ENUF_FP32) {
         const int rsz = (int)sizeof(float);
@@ -684,14 +687,15 @@ enuf_status upload_tables(enuf_plan_t plan) {
 // fuse_totals: the gather's last block also reduces the energies (evaluations
 // outside a DPD step, where nothing follows the gather).
 enuf_status enqueue_eval(enuf_plan_t plan, const EvalArgs& a, cudaStream_t s0, cudaStream_t s1,
-                         cudaEvent_t evFork, cudaEvent_t evJoin, Events* ev, LaunchLog* log, bool fuse_totals) {
+                         cudaEvent_t evFork, cudaEvent_t evJoin, Events* ev, LaunchLog* log, bool fuse_totals,
+                         const DpdDev* dpd = nullptr) {
     cudaError_t e;
     if (plan->prec == ENUF_FP32)
         e = enqueue_enuf<float>(plan->g, plan->fs, plan->fp, plan->w, a, s0, s1, evFork, evJoin, ev, log,
-                                fuse_totals);
+                                fuse_totals, dpd);
     else
         e = enqueue_enuf<double>(plan->g, plan->fs, plan->fp, plan->w, a, s0, s1, evFork, evJoin, ev, log,
-                                 fuse_totals);
+                                 fuse_totals, dpd);
     if (e != cudaSuccess) return fail(plan, ENUF_ERR_CUDA, "enqueue: %s", cudaGetErrorString(e));
     return ENUF_OK;
 }
@@ -1035,15 +1039,18 @@ namespace {
 
 enuf_status enqueue_force_eval(dpd_system_t sys, cudaStream_t s0, cudaStream_t s1, Events* ev, LaunchLog* log) {
     enuf_plan_t plan = sys->plan;
+    if (ev && ev->on) s1 = s0;   // stage events: the branches one after the other
     // DPD pair + bond forces on s1 (F overwritten), after what s0 did so far
     CU(cudaEventRecord(plan->evA, s0));
     CU(cudaStreamWaitEvent(s1, plan->evA, 0));
-    cudaError_t e = plan->prec == ENUF_FP32 ? enqueue_dpd_forces<float>(plan->w, sys->d, s1, ev, log)
-                                            : enqueue_dpd_forces<double>(plan->w, sys->d, s1, ev, log);
+    // pairs = 0: the DPD pair forces run in the real-space launch (k_pairs)
+    const bool fuse = plan->P.pairs == 0;
+    cudaError_t e = plan->prec == ENUF_FP32 ? enqueue_dpd_forces<float>(plan->w, sys->d, s1, ev, log, !fuse)
+                                            : enqueue_dpd_forces<double>(plan->w, sys->d, s1, ev, log, !fuse);
     if (e != cudaSuccess) return fail(plan, ENUF_ERR_CUDA, "dpd enqueue: %s", cudaGetErrorString(e));
     // electrostatics added into F (real space follows the DPD kernel on s1)
     EvalArgs a{sys->d.N, sys->d.pos, sys->d.q, sys->d.F, false};
-    return enqueue_eval(plan, a, s0, s1, plan->evFork, plan->evJoin, ev, log, false);
+    return enqueue_eval(plan, a, s0, s1, plan->evFork, plan->evJoin, ev, log, false, fuse ? &sys->d : nullptr);
 }
 
 enuf_status initial_force(dpd_system_t sys) {
@@ -1306,7 +1313,45 @@ struct enuf_batch_s {
     std::vector<const void*> g_pos, g_q;
     std::vector<void*> g_F;
     int launches = 0;
+    // one launch sequence over all systems (FP32, see batch_eligible)
+    bool seq = false;
+    cudaStream_t aux = nullptr;
+    cudaEvent_t evFork = nullptr, evJoin = nullptr;
+    void* dtab = nullptr;      // argument tables and block maps
+    size_t dtab_bytes = 0;
+    double* dE = nullptr;      // [nsys][16] totals
+    double* hE = nullptr;      // pinned copy
+    BatchLaunch L{};
+    bool built = false;
 };
+
+namespace {
+
+// The batched kernels need each system's plan to run the fused-plane
+// two-factor FFT, the column spreading form (tile edges 8..24) and the
+// binning offsets in the last count block.
+bool batch_plan_ok(const enuf_plan_s* p) {
+    const int T = p->g.T;
+    const bool col = T == 8 || T == 10 || T == 12 || T == 16 || T == 20 || T == 24;
+    return p->prec == ENUF_FP32 && p->fs.two && p->fs.fused && p->fs.spread == 1 && col && p->g.bin_last &&
+           p->w.wb != nullptr;
+}
+
+BatchSys batch_sys(const enuf_plan_s* p, int n, const void* pos, const void* q, void* F, double* Edev) {
+    BatchSys x;
+    x.g = p->g;
+    x.fs = p->fs;
+    x.fp = p->fp;
+    x.w = p->w;
+    x.N = n;
+    x.pos = pos;
+    x.q = q;
+    x.F = F;
+    x.Edev = Edev;
+    return x;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -1333,14 +1378,93 @@ enuf_status enuf_batch_plan(int nsys, const enuf_params* params, const int* n, v
         if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return bail(ENUF_ERR_CUDA);
         b->evDone.push_back(e);
     }
+    bool seq = nsys < (1 << 11);
+    for (int s = 0; s < nsys && seq; ++s) seq = batch_plan_ok(b->plans[s]);
+    if (seq) {
+        std::vector<BatchSys> sys;
+        for (int s = 0; s < nsys; ++s) sys.push_back(batch_sys(b->plans[s], n[s], nullptr, nullptr, nullptr, nullptr));
+        b->dtab_bytes = batch_bytes<float>(sys.data(), nsys);
+        if (dev_alloc(&b->dtab, b->dtab_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            b->dtab = nullptr;
+            return bail(ENUF_ERR_OOM);
+        }
+        if (dev_alloc((void**)&b->dE, (size_t)nsys * 16 * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            b->dE = nullptr;
+            return bail(ENUF_ERR_OOM);
+        }
+        if (cudaMallocHost((void**)&b->hE, (size_t)nsys * 16 * sizeof(double)) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&b->aux, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->evFork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->evJoin, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(ENUF_ERR_CUDA);
+        }
+        b->seq = true;
+    }
     *out = b;
     return ENUF_OK;
 }
+
+namespace {
+
+// One launch sequence over all systems: the tables follow the caller's
+// arrays; the graph (launches reading the tables, one copy of the totals)
+// is captured once.
+enuf_status batch_seq_eval(enuf_batch_t b, const void* const* pos, const void* const* q, void* const* F, double* E) {
+    const int ns = (int)b->plans.size();
+    bool same = b->built;
+    for (int s = 0; same && s < ns; ++s) same = b->g_pos[s] == pos[s] && b->g_q[s] == q[s] && b->g_F[s] == F[s];
+    if (!same) {
+        // the previous evaluation may still read the tables
+        if (cudaStreamSynchronize(b->stream) != cudaSuccess) return ENUF_ERR_CUDA;
+        std::vector<BatchSys> sys;
+        for (int s = 0; s < ns; ++s) sys.push_back(batch_sys(b->plans[s], b->n[s], pos[s], q[s], F[s], b->dE + 16 * s));
+        BatchLaunch L{};
+        if (batch_build<float>(b->dtab, sys.data(), ns, &L) != cudaSuccess) return ENUF_ERR_CUDA;
+        b->L = L;
+        b->g_pos.assign(pos, pos + ns);
+        b->g_q.assign(q, q + ns);
+        b->g_F.assign(F, F + ns);
+        b->built = true;
+    }
+    if (!b->gexec) {
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return ENUF_ERR_CUDA;
+        LaunchLog log;
+        cudaError_t e = batch_enqueue<float>(b->L, b->stream, b->aux, b->evFork, b->evJoin, &log);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->hE, b->dE, (size_t)ns * 16 * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+        cudaError_t e2 = cudaStreamEndCapture(b->stream, &graph);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return ENUF_ERR_CUDA;
+        }
+        e = cudaGraphInstantiateWithFlags(&b->gexec, graph, cudaGraphInstantiateFlagUseNodePriority);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return ENUF_ERR_CUDA;
+        b->launches = log.kernels;
+    }
+    if (cudaGraphLaunch(b->gexec, b->stream) != cudaSuccess) return ENUF_ERR_CUDA;
+    if (E) {
+        if (cudaStreamSynchronize(b->stream) != cudaSuccess) return ENUF_ERR_CUDA;
+        for (int s = 0; s < ns; ++s)
+            for (int i = 0; i < 4; ++i) E[4 * s + i] = b->hE[16 * s + i];
+    }
+    return ENUF_OK;
+}
+
+}  // namespace
 
 enuf_status enuf_batch_energy_forces(enuf_batch_t b, const void* const* pos, const void* const* q, void* const* F,
                                      double* E) {
     if (!b || !pos || !q || !F) return ENUF_ERR_INVALID;
     const int ns = (int)b->plans.size();
+    for (int s = 0; s < ns; ++s)
+        if (b->n[s] > 0 && (!pos[s] || !q[s] || !F[s])) return ENUF_ERR_INVALID;
+    if (b->seq) return batch_seq_eval(b, pos, q, F, E);
     bool same = b->gexec && (int)b->g_pos.size() == ns;
     for (int s = 0; same && s < ns; ++s) same = b->g_pos[s] == pos[s] && b->g_q[s] == q[s] && b->g_F[s] == F[s];
     if (!same) {
@@ -1386,10 +1510,18 @@ enuf_status enuf_batch_energy_forces(enuf_batch_t b, const void* const* pos, con
 
 int enuf_batch_launches(enuf_batch_t b) { return b ? b->launches : 0; }
 
+int enuf_batch_mode(enuf_batch_t b) { return b && b->seq ? 1 : 0; }
+
 void enuf_batch_destroy(enuf_batch_t b) {
     if (!b) return;
     if (b->stream) cudaStreamSynchronize(b->stream);
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->dtab) cudaFree(b->dtab);
+    if (b->dE) cudaFree(b->dE);
+    if (b->hE) cudaFreeHost(b->hE);
+    if (b->aux) cudaStreamDestroy(b->aux);
+    if (b->evFork) cudaEventDestroy(b->evFork);
+    if (b->evJoin) cudaEventDestroy(b->evJoin);
     for (auto p : b->plans) enuf_destroy(p);
     for (auto e : b->evDone) cudaEventDestroy(e);
     if (b->evStart) cudaEventDestroy(b->evStart);

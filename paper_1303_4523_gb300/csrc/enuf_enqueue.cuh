@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <utility>
 
+#include "enuf_batch.cuh"
 #include "enuf_fft2.cuh"
 #include "enuf_kernels.cuh"
 
@@ -122,7 +123,17 @@ cudaError_t configure_kernels(int max_smem) {
     set((const void*)k_spread_col<R, 24, true>);
     set((const void*)k_fft_xy<R>);
     set((const void*)k_fft_yx<R>);
+    // the FFT passes prefer the largest shared-memory carve-out (several CTAs per SM)
+    auto carve = [&](const void* f) {
+        cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        if (r != cudaSuccess) e = r;
+    };
     if constexpr (sizeof(R) == 4) {
+        carve((const void*)k2_fft_x<R>);
+        carve((const void*)k2_fft_y<R>);
+        carve((const void*)k2_fft_z<R>);
+        carve((const void*)k2_fft_iy<R>);
+        carve((const void*)k2_fft_ix<R>);
         set((const void*)k2_fft_x<R>);
         set((const void*)k2_fft_y<R>);
         set((const void*)k2_fft_z<R>);
@@ -132,9 +143,22 @@ cudaError_t configure_kernels(int max_smem) {
         set((const void*)k2_fft_yx<R>);
         set((const void*)k_spread_brick<R, false>);
         set((const void*)k_spread_brick<R, true>);
+        set((const void*)kb_bin_count<R>);
+        set((const void*)kb_bin_scatter<R>);
+        set((const void*)kb_real<R>);
+        set((const void*)kb_spread_col<R, 8>);
+        set((const void*)kb_spread_col<R, 10>);
+        set((const void*)kb_spread_col<R, 12>);
+        set((const void*)kb_spread_col<R, 16>);
+        set((const void*)kb_spread_col<R, 20>);
+        set((const void*)kb_spread_col<R, 24>);
+        set((const void*)kb_fft_xy<R>);
+        set((const void*)kb_fft_z<R>);
+        set((const void*)kb_fft_yx<R>);
     }
     set((const void*)k_real<R>);
     set((const void*)k_dpd<R>);
+    set((const void*)k_pairs<R>);
     return e;
 }
 
@@ -285,7 +309,7 @@ void enqueue_fft(const Geo& g, const FftShape& fs, const FftPlanDev& fp, const W
 template <typename R>
 cudaError_t enqueue_enuf(const Geo& g, const FftShape& fs, const FftPlanDev& fp, const Work& w,
                          const EvalArgs& a, cudaStream_t s0, cudaStream_t s1, cudaEvent_t evFork,
-                         cudaEvent_t evJoin, Events* ev, LaunchLog* log, bool fuse_totals) {
+                         cudaEvent_t evJoin, Events* ev, LaunchLog* log, bool fuse_totals, const DpdDev* dpd) {
     using C = typename Cx<R>::T;
     using V = typename V4<R>::T;
     const R* pos = static_cast<const R*>(a.pos);
@@ -294,6 +318,9 @@ cudaError_t enqueue_enuf(const Geo& g, const FftShape& fs, const FftPlanDev& fp,
     V* sq = static_cast<V*>(w.sq);
     V* sw = static_cast<V*>(w.sw);
     const bool pdl = pdl_ok(ev);
+    // with per-stage events the two branches run one after the other, so that
+    // each stage's events time its kernels alone
+    if (ev && ev->on) s1 = s0;
     rec(ev, 0, true, s0);
     enqueue_bin<R>(g, w, a.N, pos, q, a.zeroF ? F : nullptr, s0, pdl);
     rec(ev, 0, false, s0);
@@ -304,8 +331,18 @@ cudaError_t enqueue_enuf(const Geo& g, const FftShape& fs, const FftPlanDev& fp,
     cudaStreamWaitEvent(s1, evFork, 0);
     rec(ev, 4, true, s1);
     const int real_smem = real_smem_bytes<R>();
-    launch(false, false, k_real<R>, w.nblk_real, kRealThreads, real_smem, s1, g, (const int*)w.tstart, (const V*)sq,
-           (const V*)sw, F, w.part + w.off_real);
+    if (dpd) {   // DPD pairs and real-space pairs in one launch
+        const DpdDev& d = *dpd;
+        launch(false, false, k_pairs<R>, w.nblk_dpd + w.nblk_real, kRealThreads,
+               std::max(real_smem, dpd_smem_bytes<R>()), s1, d, d.B, static_cast<const V*>(d.sp),
+               static_cast<const V*>(d.sv), (const int*)d.cstart, static_cast<const R*>(d.atab),
+               static_cast<const R*>(d.pos), (const int*)d.bnd, (const uint64_t*)d.step_dev, static_cast<R*>(d.F),
+               w.part + w.off_dpd, w.nblk_dpd, g, (const int*)w.tstart, (const V*)sq, (const V*)sw,
+               w.part + w.off_real);
+    } else {
+        launch(false, false, k_real<R>, w.nblk_real, kRealThreads, real_smem, s1, g, (const int*)w.tstart,
+               (const V*)sq, (const V*)sw, F, w.part + w.off_real);
+    }
     rec(ev, 4, false, s1);
     cudaEventRecord(evJoin, s1);
     log->kernels += 1;
@@ -353,7 +390,8 @@ cudaError_t enqueue_totals(const Geo& g, const Work& w, bool dpd, cudaStream_t s
 }
 
 template <typename R>
-cudaError_t enqueue_dpd_forces(const Work& w, const DpdDev& d, cudaStream_t s, Events* ev, LaunchLog* log) {
+cudaError_t enqueue_dpd_forces(const Work& w, const DpdDev& d, cudaStream_t s, Events* ev, LaunchLog* log,
+                               bool pair_kernel) {
     using V = typename V4<R>::T;
     const int blocks = (d.N + 255) / 256 > 0 ? (d.N + 255) / 256 : 1;
     const bool pdl = pdl_ok(ev);
@@ -366,6 +404,8 @@ cudaError_t enqueue_dpd_forces(const Work& w, const DpdDev& d, cudaStream_t s, E
            static_cast<const R*>(d.v0), (const int*)d.type, (const int*)d.ckey, d.ccur, static_cast<V*>(d.sp),
            static_cast<V*>(d.sv));
     rec(ev, 7, false, s);
+    log->kernels += 3;
+    if (!pair_kernel) return cudaGetLastError();   // the pairs run in k_pairs with the real space
     rec(ev, 5, true, s);
     const int dpd_smem = dpd_smem_bytes<R>();
     launch(pdl, false, k_dpd<R>, w.nblk_dpd, kDpdThreads, dpd_smem, s, d, d.B, static_cast<const V*>(d.sp),
@@ -373,7 +413,7 @@ cudaError_t enqueue_dpd_forces(const Work& w, const DpdDev& d, cudaStream_t s, E
            static_cast<const R*>(d.pos), (const int*)d.bnd, (const uint64_t*)d.step_dev, static_cast<R*>(d.F),
            w.part + w.off_dpd);
     rec(ev, 5, false, s);
-    log->kernels += 4;
+    log->kernels += 1;
     return cudaGetLastError();
 }
 
@@ -406,15 +446,21 @@ cudaError_t enqueue_spread_only(const Geo& g, const Work& w, const EvalArgs& a, 
     return cudaGetLastError();
 }
 
+}  // namespace enuf
+
+#include "enuf_batch_host.cuh"
+
+namespace enuf {
+
 #define ENUF_INSTANTIATE(R)                                                                                  \
     template cudaError_t configure_kernels<R>(int);                                                          \
     template int spread_smem<R>(const Geo&);                                                                 \
     template cudaError_t enqueue_enuf<R>(const Geo&, const FftShape&, const FftPlanDev&, const Work&,        \
                                          const EvalArgs&, cudaStream_t, cudaStream_t, cudaEvent_t,           \
-                                         cudaEvent_t, Events*, LaunchLog*, bool);                            \
+                                         cudaEvent_t, Events*, LaunchLog*, bool, const DpdDev*);             \
     template cudaError_t enqueue_totals<R>(const Geo&, const Work&, bool, cudaStream_t, LaunchLog*, bool);   \
     template cudaError_t enqueue_dpd_forces<R>(const Work&, const DpdDev&, cudaStream_t, Events*,            \
-                                               LaunchLog*);                                                  \
+                                               LaunchLog*, bool);                                            \
     template cudaError_t enqueue_vv_pre<R>(const DpdDev&, cudaStream_t, LaunchLog*);                         \
     template cudaError_t enqueue_vv_post<R>(const Geo&, const Work&, const DpdDev&, cudaStream_t, LaunchLog*,  \
                                             bool);                                                           \

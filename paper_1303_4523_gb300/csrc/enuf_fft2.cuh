@@ -102,11 +102,11 @@ __global__ void __launch_bounds__(512) k2_fft_y(Geo g, FftPlanDev fp, const type
 // (FP64, Kahan); the nf fields -i k_a D F (gradient mode: D F), built in the
 // inverse transform's loader, inverse z; output spec3[a][z][kx][ky].
 template <typename R>
-__global__ void __launch_bounds__(512) k2_fft_z(Geo g, FftPlanDev fp, const typename Cx<R>::T* __restrict__ spec2,
+__device__ __forceinline__ void k2_fft_z_body(Geo g, FftPlanDev fp, const typename Cx<R>::T* __restrict__ spec2,
                                                const typename Cx<R>::T* __restrict__ twg,
                                                const double* __restrict__ tab, const double* __restrict__ tabv,
                                                const R* __restrict__ tabr, typename Cx<R>::T* __restrict__ spec3,
-                                               double* __restrict__ epart, int LB, int plane_major) {
+                                               double* __restrict__ epart, int LB, int plane_major, Blk blk) {
     pdl_enter();
     using C = typename Cx<R>::T;
     extern __shared__ unsigned char smraw[];
@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(512) k2_fft_z(Geo g, FftPlanDev fp, const type
     C* A = tw + n;                                    // [nf LB] phase-A rows
     C* B = A + nf * LB * fft2_lsa(fp.f1, fp.f2);     // [nf LB][lsb]: forward result, then the fields
     fft2_twiddles(tw, twg, fp);
-    const int l0 = blockIdx.x * LB;
+    const int l0 = blk.id * LB;
     const int nl = min(LB, NL - l0);
     __syncthreads();
     if (plane_major)   // spec2[z][l]: lines gathered across planes
@@ -134,23 +134,24 @@ __global__ void __launch_bounds__(512) k2_fft_z(Geo g, FftPlanDev fp, const type
     __syncthreads();
     // energy and virial of the kept modes (half space kx >= 0, kx > 0 counted twice)
     const float rK = 1.0f / (float)K;
-    Kahan ke, kw;
+    // each thread adds a few modes in plain FP64 (the FP64 units are few); the
+    // compensated summation runs over the blocks' partials in the totals
+    double se = 0.0, sv = 0.0;
     for (int idx = threadIdx.x; idx < nl * K; idx += blockDim.x) {
         const int c = qdiv(idx, K, rK), kzi = idx - c * K;
         const int l = l0 + c;
         const int kx = qdiv(l, K, rK);
         const int kz = kzi - nc;
         const C f = B[c * lsb + (kz < 0 ? kz + n : kz)];
-        const double a2 = (double)f.x * (double)f.x + (double)f.y * (double)f.y;
-        const double wgt = kx == 0 ? 1.0 : 2.0;
-        ke.add(wgt * tab[(size_t)l * K + kzi] * a2);
-        kw.add(wgt * tabv[(size_t)l * K + kzi] * a2);
+        double a2 = fma((double)f.x, (double)f.x, (double)f.y * (double)f.y);
+        if (kx != 0) a2 += a2;   // the -kx half space
+        se = fma(tab[(size_t)l * K + kzi], a2, se);
+        sv = fma(tabv[(size_t)l * K + kzi], a2, sv);
     }
-    double se = ke.s, sv = kw.s;
     block_sum2(se, sv);
     if (threadIdx.x == 0) {
-        epart[2 * blockIdx.x] = se;
-        epart[2 * blockIdx.x + 1] = sv;
+        epart[2 * blk.id] = se;
+        epart[2 * blk.id + 1] = sv;
     }
     // inverse of the nf fields of every line: line a nl + c of the transform
     fft2_lines<R, true>(
@@ -189,6 +190,15 @@ __global__ void __launch_bounds__(512) k2_fft_z(Geo g, FftPlanDev fp, const type
         const int z = qdiv(e, nl, rnl), c = e - z * nl;
         spec3[((size_t)a * n + z) * NL + l0 + c] = B[(a * nl + c) * lsb + z];
     }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(512) k2_fft_z(Geo g, FftPlanDev fp, const typename Cx<R>::T* __restrict__ spec2,
+                                               const typename Cx<R>::T* __restrict__ twg,
+                                               const double* __restrict__ tab, const double* __restrict__ tabv,
+                                               const R* __restrict__ tabr, typename Cx<R>::T* __restrict__ spec3,
+                                               double* __restrict__ epart, int LB, int plane_major) {
+    k2_fft_z_body<R>(g, fp, spec2, twg, tab, tabv, tabr, spec3, epart, LB, plane_major, Blk{(int)blockIdx.x, (int)gridDim.x});
 }
 
 // inverse y for lines (a, z, kx): K inputs zero-padded to n; output spec4[a][z][y][kx]
@@ -272,12 +282,19 @@ __global__ void __launch_bounds__(512) k2_fft_ix(Geo g, FftPlanDev fp, const typ
         },
         [&](int c, int x, C v) { B[c * lsb + x] = v; });
     __syncthreads();
-    const float rn = 1.0f / (float)n;
-    for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
-        const int c = qdiv(idx, n, rn), x = idx - c * n;
-        const C v = B[c * lsb + x];
-        h[(size_t)(row0 + 2 * c) * n + x] = v.x;
-        h[(size_t)(row0 + 2 * c + 1) * n + x] = v.y;
+    // two consecutive x per thread (n is even): one 8-byte store on each row
+    const int hn = n / 2;
+    const float rhn = 1.0f / (float)hn;
+    for (int idx = threadIdx.x; idx < nl * hn; idx += blockDim.x) {
+        const int c = qdiv(idx, hn, rhn), x = 2 * (idx - c * hn);
+        const C v0 = B[c * lsb + x], v1 = B[c * lsb + x + 1];
+        typename Cx<R>::T ra, rb;   // (row 2c, row 2c + 1) at x, x + 1
+        ra.x = v0.x;
+        ra.y = v1.x;
+        rb.x = v0.y;
+        rb.y = v1.y;
+        *reinterpret_cast<typename Cx<R>::T*>(h + (size_t)(row0 + 2 * c) * n + x) = ra;
+        *reinterpret_cast<typename Cx<R>::T*>(h + (size_t)(row0 + 2 * c + 1) * n + x) = rb;
     }
 }
 
@@ -286,9 +303,9 @@ __global__ void __launch_bounds__(512) k2_fft_ix(Geo g, FftPlanDev fp, const typ
 // kx = 0..nc (the y columns), y transforms of the nc + 1 columns, keep
 // |ky| <= nc; output spec2[z][kx][ky] (plane-major).
 template <typename R>
-__global__ void __launch_bounds__(512) k2_fft_xy(Geo g, FftPlanDev fp, const R* __restrict__ grid,
+__device__ __forceinline__ void k2_fft_xy_body(Geo g, FftPlanDev fp, const R* __restrict__ grid,
                                                 const typename Cx<R>::T* __restrict__ twg,
-                                                typename Cx<R>::T* __restrict__ spec2) {
+                                                typename Cx<R>::T* __restrict__ spec2, Blk blk) {
     pdl_enter();
     using C = typename Cx<R>::T;
     extern __shared__ unsigned char smraw[];
@@ -297,7 +314,7 @@ __global__ void __launch_bounds__(512) k2_fft_xy(Geo g, FftPlanDev fp, const R* 
     C* A = tw + n;                            // [n/2] phase-A rows; then the y columns P[kx][y]
     C* B = A + h * fft2_lsa(fp.f1, fp.f2);    // [n/2][lsb] x results; then the y phase-A rows
     fft2_twiddles(tw, twg, fp);
-    const int z = blockIdx.x;
+    const int z = blk.id;
     const R* gz = grid + (size_t)z * n * n;
     __syncthreads();
     fft2_lines<R, false>(
@@ -336,13 +353,20 @@ __global__ void __launch_bounds__(512) k2_fft_xy(Geo g, FftPlanDev fp, const R* 
         });
 }
 
+template <typename R>
+__global__ void __launch_bounds__(512) k2_fft_xy(Geo g, FftPlanDev fp, const R* __restrict__ grid,
+                                                const typename Cx<R>::T* __restrict__ twg,
+                                                typename Cx<R>::T* __restrict__ spec2) {
+    k2_fft_xy_body<R>(g, fp, grid, twg, spec2, Blk{(int)blockIdx.x, (int)gridDim.x});
+}
+
 // Inverse y and x of one (field, z-plane) in shared memory (small grids):
 // the plane spec3[a][z][kx][ky] zero-padded to n along y, inverse y of the
 // nc + 1 columns, then two Hermitian rows per complex line (C2R) inverse
 // along x; output h[a][z][y][x].
 template <typename R>
-__global__ void __launch_bounds__(512) k2_fft_yx(Geo g, FftPlanDev fp, const typename Cx<R>::T* __restrict__ spec3,
-                                                const typename Cx<R>::T* __restrict__ twg, R* __restrict__ h) {
+__device__ __forceinline__ void k2_fft_yx_body(Geo g, FftPlanDev fp, const typename Cx<R>::T* __restrict__ spec3,
+                                                const typename Cx<R>::T* __restrict__ twg, R* __restrict__ h, Blk blk) {
     pdl_enter();
     using C = typename Cx<R>::T;
     extern __shared__ unsigned char smraw[];
@@ -351,7 +375,7 @@ __global__ void __launch_bounds__(512) k2_fft_yx(Geo g, FftPlanDev fp, const typ
     C* A = tw + n;                             // [n/2] phase-A rows
     C* Yc = A + hn * fft2_lsa(fp.f1, fp.f2);   // [nc + 1][lsb]: inverse y results [kx][y]
     fft2_twiddles(tw, twg, fp);
-    const int az = blockIdx.x;   // a * n + z
+    const int az = blk.id;   // a * n + z
     const C* in = spec3 + (size_t)az * nc1 * K;
     __syncthreads();
     fft2_lines<R, true>(
@@ -393,6 +417,12 @@ __global__ void __launch_bounds__(512) k2_fft_yx(Geo g, FftPlanDev fp, const typ
             out[(size_t)(2 * c) * n + x] = v.x;
             out[(size_t)(2 * c + 1) * n + x] = v.y;
         });
+}
+
+template <typename R>
+__global__ void __launch_bounds__(512) k2_fft_yx(Geo g, FftPlanDev fp, const typename Cx<R>::T* __restrict__ spec3,
+                                                const typename Cx<R>::T* __restrict__ twg, R* __restrict__ h) {
+    k2_fft_yx_body<R>(g, fp, spec3, twg, h, Blk{(int)blockIdx.x, (int)gridDim.x});
 }
 
 }  // namespace enuf

@@ -200,21 +200,67 @@ struct Events {
     bool on = false;
 };
 
+// One system of a batched launch sequence (FP32): its plan's geometry,
+// shapes, workspace and this evaluation's arrays; Edev receives its totals.
+struct BatchSys {
+    Geo g;
+    FftShape fs;
+    FftPlanDev fp;
+    Work w;
+    int N;
+    const void* pos;
+    const void* q;
+    void* F;
+    double* Edev;
+};
+
+// Launch parameters of one batched kernel: its argument table and block map
+// (device), the blocks of all systems together, threads and shared memory
+// (the largest any system needs).
+struct BatchKernel {
+    void* tab = nullptr;
+    int* cmap = nullptr;
+    int blocks = 0, threads = 0, smem = 0;
+    int T = 0;   // spreading: the tile edge of this group
+};
+struct BatchLaunch {
+    BatchKernel bin_count, bin_scatter, bin_weights, real, fft_xy, fft_z, fft_yx, gather;
+    BatchKernel spread[6];   // one per tile edge present (8, 10, 12, 16, 20, 24)
+    int nspread = 0;
+};
+
 template <typename R> cudaError_t configure_kernels(int max_smem);
 template <typename R> int spread_smem(const Geo& g);
+// dpd (a DPD step with fused pair kernels, or nullptr): the real-space launch
+// also runs the DPD pair forces (k_pairs), which enqueue_dpd_forces then leaves out.
 template <typename R>
 cudaError_t enqueue_enuf(const Geo& g, const FftShape& fs, const FftPlanDev& fp, const Work& w,
                          const EvalArgs& a, cudaStream_t s0, cudaStream_t s1, cudaEvent_t evFork,
-                         cudaEvent_t evJoin, Events* ev, LaunchLog* log, bool fuse_totals);
+                         cudaEvent_t evJoin, Events* ev, LaunchLog* log, bool fuse_totals,
+                         const DpdDev* dpd = nullptr);
 template <typename R>
 cudaError_t enqueue_totals(const Geo& g, const Work& w, bool dpd, cudaStream_t s, LaunchLog* log, bool pdl);
 template <typename R>
-cudaError_t enqueue_dpd_forces(const Work& w, const DpdDev& d, cudaStream_t s, Events* ev, LaunchLog* log);
+cudaError_t enqueue_dpd_forces(const Work& w, const DpdDev& d, cudaStream_t s, Events* ev, LaunchLog* log,
+                               bool pair_kernel = true);
 template <typename R>
 cudaError_t enqueue_vv_pre(const DpdDev& d, cudaStream_t s, LaunchLog* log);
 template <typename R>
 cudaError_t enqueue_vv_post(const Geo& g, const Work& w, const DpdDev& d, cudaStream_t s, LaunchLog* log, bool pdl);
 template <typename R>
 cudaError_t enqueue_spread_only(const Geo& g, const Work& w, const EvalArgs& a, void* grid_out, cudaStream_t s);
+// Batched launch sequence (FP32): a system qualifies when its plan runs the
+// fused-plane two-factor FFT, the column spreading form and the one-kernel
+// binning offsets. batch_bytes: the device tables' size; batch_build writes
+// them (argument tables and block maps) into dbuf and fills the launch
+// parameters; batch_enqueue launches the sequence (fork/join on s1 for the
+// real-space pairs).
+bool batch_eligible(const BatchSys& s);
+template <typename R> size_t batch_bytes(const BatchSys* sys, int nsys);
+template <typename R>
+cudaError_t batch_build(void* dbuf, const BatchSys* sys, int nsys, BatchLaunch* out);
+template <typename R>
+cudaError_t batch_enqueue(const BatchLaunch& L, cudaStream_t s0, cudaStream_t s1, cudaEvent_t evFork, cudaEvent_t evJoin,
+                          LaunchLog* log);
 
 }  // namespace enuf

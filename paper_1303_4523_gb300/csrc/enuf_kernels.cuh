@@ -39,6 +39,14 @@ __device__ __forceinline__ int real_as_int(double v) { return (int)__double_as_l
 // next grid launches at completion, with its launch work already done.
 __device__ __forceinline__ void pdl_enter() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// The block a kernel body works on: its index and the number of blocks of
+// its launch for this system. A single-system launch passes (blockIdx.x,
+// gridDim.x); a batched launch over many systems passes the block's index
+// within its system's share of the grid and that share's size.
+struct Blk {
+    int id, n;
+};
+
 __device__ __forceinline__ float r_exp(float x) { return expf(x); }
 __device__ __forceinline__ double r_exp(double x) { return exp(x); }
 __device__ __forceinline__ float r_erfc(float x) { return erfcf(x); }
@@ -240,12 +248,13 @@ static __device__ void totals_block(const Geo& g, const TotalsArgs& t) {
     }
 }
 
-// The last block of a kernel to finish (arrival counter) runs the totals.
-__device__ __forceinline__ void totals_if_last(const Geo& g, const TotalsArgs& t) {
+// The last block of a kernel to finish (arrival counter) runs the totals;
+// nblk: the blocks of the launch that count on this ticket.
+__device__ __forceinline__ void totals_if_last(const Geo& g, const TotalsArgs& t, int nblk) {
     __shared__ int last;
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(t.ticket, 1) == (int)(gridDim.x * gridDim.y) - 1;
+    if (threadIdx.x == 0) last = atomicAdd(t.ticket, 1) == nblk - 1;
     __syncthreads();
     if (!last) return;
     __threadfence();
@@ -305,14 +314,14 @@ __device__ __forceinline__ void block_exclusive_scan(const int* data, int count,
 }
 
 template <typename R>
-__global__ void __launch_bounds__(1024) k_bin_count(Geo g, int N, const R* __restrict__ pos,
+__device__ __forceinline__ void k_bin_count_body(Geo g, int N, const R* __restrict__ pos,
                                                    const R* __restrict__ q, int* __restrict__ cnt_blk,
                                                    int* __restrict__ bhist, int* __restrict__ ctile,
                                                    typename V4<R>::T* __restrict__ cpos,
                                                    typename V4<R>::T* __restrict__ cfrac, int* __restrict__ cbase,
                                                    R* __restrict__ Fzero, double* __restrict__ qpart,
                                                    int* __restrict__ ticket, int* __restrict__ boff,
-                                                   int* __restrict__ tstart) {
+                                                   int* __restrict__ tstart, Blk blk) {
     pdl_enter();
     extern __shared__ int sm_bin[];
     int* hist = sm_bin;                 // [ntiles]
@@ -321,7 +330,7 @@ __global__ void __launch_bounds__(1024) k_bin_count(Geo g, int N, const R* __res
     for (int t = threadIdx.x; t < g.ntiles; t += blockDim.x) hist[t] = 0;
     if (threadIdx.x == 0) scount = 0;
     __syncthreads();
-    const int b = blockIdx.x, lane = threadIdx.x & 31;
+    const int b = blk.id, lane = threadIdx.x & 31;
     const int i0 = b * g.chunk;
     const int i1 = min(N, i0 + g.chunk);
     double s1 = 0.0, s2 = 0.0;
@@ -385,7 +394,7 @@ __global__ void __launch_bounds__(1024) k_bin_count(Geo g, int N, const R* __res
     __shared__ int last;
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(ticket, 1) == (int)gridDim.x - 1;
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1) == (int)blk.n - 1;
     __syncthreads();
     if (!last) return;
     __threadfence();
@@ -406,6 +415,18 @@ __global__ void __launch_bounds__(1024) k_bin_count(Geo g, int N, const R* __res
     __syncthreads();
     block_exclusive_scan(hist, g.ntiles, tstart);
     if (threadIdx.x == 0) *ticket = 0;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(1024) k_bin_count(Geo g, int N, const R* __restrict__ pos,
+                                                   const R* __restrict__ q, int* __restrict__ cnt_blk,
+                                                   int* __restrict__ bhist, int* __restrict__ ctile,
+                                                   typename V4<R>::T* __restrict__ cpos,
+                                                   typename V4<R>::T* __restrict__ cfrac, int* __restrict__ cbase,
+                                                   R* __restrict__ Fzero, double* __restrict__ qpart,
+                                                   int* __restrict__ ticket, int* __restrict__ boff,
+                                                   int* __restrict__ tstart) {
+    k_bin_count_body<R>(g, N, pos, q, cnt_blk, bhist, ctile, cpos, cfrac, cbase, Fzero, qpart, ticket, boff, tstart, Blk{(int)blockIdx.x, (int)gridDim.x});
 }
 
 // One thread per tile: offsets of each block's beads inside the tile, and the tile total.
@@ -517,17 +538,17 @@ static __global__ void __launch_bounds__(256) k_tile_offsets(Geo g, const int* _
 }
 
 template <typename R>
-__global__ void __launch_bounds__(1024) k_bin_scatter(Geo g, const int* __restrict__ cnt_blk,
+__device__ __forceinline__ void k_bin_scatter_body(Geo g, const int* __restrict__ cnt_blk,
                                                      const int* __restrict__ ctile,
                                                      const typename V4<R>::T* __restrict__ cpos,
                                                      const typename V4<R>::T* __restrict__ cfrac,
                                                      const int* __restrict__ cbase, const int* __restrict__ boff,
                                                      const int* __restrict__ tstart,
                                                      typename V4<R>::T* __restrict__ sq,
-                                                     typename V4<R>::T* __restrict__ sw, int* __restrict__ sb) {
+                                                     typename V4<R>::T* __restrict__ sw, int* __restrict__ sb, Blk blk) {
     pdl_enter();
     extern __shared__ int cur[];   // [ntiles] running counts
-    const int b = blockIdx.x;
+    const int b = blk.id;
     for (int t = threadIdx.x; t < g.ntiles; t += blockDim.x) cur[t] = 0;
     __syncthreads();
     const int nc = cnt_blk[b];
@@ -544,20 +565,32 @@ __global__ void __launch_bounds__(1024) k_bin_scatter(Geo g, const int* __restri
     }
 }
 
+template <typename R>
+__global__ void __launch_bounds__(1024) k_bin_scatter(Geo g, const int* __restrict__ cnt_blk,
+                                                     const int* __restrict__ ctile,
+                                                     const typename V4<R>::T* __restrict__ cpos,
+                                                     const typename V4<R>::T* __restrict__ cfrac,
+                                                     const int* __restrict__ cbase, const int* __restrict__ boff,
+                                                     const int* __restrict__ tstart,
+                                                     typename V4<R>::T* __restrict__ sq,
+                                                     typename V4<R>::T* __restrict__ sw, int* __restrict__ sb) {
+    k_bin_scatter_body<R>(g, cnt_blk, ctile, cpos, cfrac, cbase, boff, tstart, sq, sw, sb, Blk{(int)blockIdx.x, (int)gridDim.x});
+}
+
 // Window weights of every sorted charged bead (Eq. 14), computed once and
 // read by the spreading and gathering kernels: wb[s][d][a] = psi(u_sd - l_a)
 // for the 2p taps a of dimension d. One thread per word, all SMs (in FP64 the
 // exponentials run on the FP64 units).
 template <typename R>
-__global__ void __launch_bounds__(256) k_bin_weights(Geo g, const int* __restrict__ tstart,
-                                                    const typename V4<R>::T* __restrict__ sw, R* __restrict__ wb) {
+__device__ __forceinline__ void k_bin_weights_body(Geo g, const int* __restrict__ tstart,
+                                                    const typename V4<R>::T* __restrict__ sw, R* __restrict__ wb, Blk blk) {
     pdl_enter();
     const int nq = tstart[g.ntiles];
     const int P2 = 2 * g.p, W = 3 * P2;
     const float rP2 = 1.0f / (float)P2;
     const R rb = (R)g.rb, wn = (R)g.wnorm;
     const long long tot = (long long)nq * W;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    for (long long e = (long long)blk.id * blockDim.x + threadIdx.x; e < tot; e += (long long)blk.n * blockDim.x) {
         const int s = (int)(e / W), r = (int)(e - (long long)s * W);
         const int d = qdiv(r, P2, rP2), a = r - d * P2;
         const typename V4<R>::T fr = sw[s];
@@ -565,6 +598,12 @@ __global__ void __launch_bounds__(256) k_bin_weights(Geo g, const int* __restric
         const R u = f + (R)(g.p - 1 - a);
         wb[e] = wn * r_exp(-u * u * rb);
     }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_bin_weights(Geo g, const int* __restrict__ tstart,
+                                                    const typename V4<R>::T* __restrict__ sw, R* __restrict__ wb) {
+    k_bin_weights_body<R>(g, tstart, sw, wb, Blk{(int)blockIdx.x, (int)gridDim.x});
 }
 
 // ---------------------------------------------------------------------------
@@ -800,11 +839,11 @@ __host__ __device__ constexpr int col_smem(int T, bool slab = false) {
 }
 
 template <typename R, int T, bool SLAB>
-__global__ void __launch_bounds__(spread2_threads<SLAB>(T)) k_spread_col(Geo g, const int* __restrict__ tstart,
+__device__ __forceinline__ void k_spread_col_body(Geo g, const int* __restrict__ tstart,
                                                                         const typename V4<R>::T* __restrict__ sq,
                                                                         const int* __restrict__ sb,
                                                                         const R* __restrict__ wb,
-                                                                        R* __restrict__ grid) {
+                                                                        R* __restrict__ grid, Blk blk) {
     pdl_enter();
     constexpr int NT = spread2_threads<SLAB>(T);
     constexpr int NW = NT / 32;
@@ -819,7 +858,7 @@ __global__ void __launch_bounds__(spread2_threads<SLAB>(T)) k_spread_col(Geo g, 
     __shared__ int nb_start[27], nb_pre[28];
     __shared__ int nnb, nitems;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tile = blockIdx.x;
+    const int tile = blk.id;
     const int tx = tile % g.ntd, ty = (tile / g.ntd) % g.ntd, tz = tile / (g.ntd * g.ntd);
     const int o[3] = {tx * T, ty * T, tz * T};
     const int no = g.ntd >= 3 ? 3 : g.ntd;
@@ -967,6 +1006,15 @@ __global__ void __launch_bounds__(spread2_threads<SLAB>(T)) k_spread_col(Geo g, 
 #pragma unroll
         for (int z = 0; z < T; ++z) col[z * n2] = acc[z];
     }
+}
+
+template <typename R, int T, bool SLAB>
+__global__ void __launch_bounds__(spread2_threads<SLAB>(T)) k_spread_col(Geo g, const int* __restrict__ tstart,
+                                                                        const typename V4<R>::T* __restrict__ sq,
+                                                                        const int* __restrict__ sb,
+                                                                        const R* __restrict__ wb,
+                                                                        R* __restrict__ grid) {
+    k_spread_col_body<R, T, SLAB>(g, tstart, sq, sb, wb, grid, Blk{(int)blockIdx.x, (int)gridDim.x});
 }
 
 // ---------------------------------------------------------------------------
@@ -1360,12 +1408,12 @@ __global__ void __launch_bounds__(256) k_fft_ix(Geo g, FftPlanDev fp, const type
 constexpr int kGatherThreads = 256;
 
 template <typename R>
-__global__ void __launch_bounds__(kGatherThreads) k_gather(Geo g, const int* __restrict__ tstart,
+__device__ __forceinline__ void k_gather_body(Geo g, const int* __restrict__ tstart,
                                                            const typename V4<R>::T* __restrict__ sq,
                                                            const typename V4<R>::T* __restrict__ sw,
                                                            const int* __restrict__ sb, const R* __restrict__ wb,
                                                            const R* __restrict__ h, R* __restrict__ F,
-                                                           TotalsArgs tot) {
+                                                           TotalsArgs tot, Blk blk) {
     pdl_enter();
     constexpr int NW = kGatherThreads / 32;
     __shared__ R wts[NW][3][kMaxTaps];
@@ -1383,7 +1431,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Geo g, const int* __r
     const R rb = (R)g.rb, wn = (R)g.wnorm;
     const R pref = (R)g.pref;
     const bool grad = g.nf == 1;
-    for (int s = blockIdx.x * NW + warp; s < Nq; s += gridDim.x * NW) {
+    for (int s = blk.id * NW + warp; s < Nq; s += blk.n * NW) {
         const typename V4<R>::T wv = sw[s];
         const R qs = sq[s].w;
         const int pb = sb[s];
@@ -1412,12 +1460,24 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Geo g, const int* __r
                 const int a = ab - b * P2;
                 const int rowo = lix[warp][1][b] * n + lix[warp][0][a];
                 R s0 = 0, s1 = 0;   // sum_z psi h, sum_z psi' h
-                for (int c = 0; c < P2; ++c) {
-                    const int off = lix[warp][2][c] + rowo;
-                    if (!ENUF_GUARD(g.check, (size_t)off < n3, 5)) continue;
-                    const R hv = h0[off];
-                    s0 = fma(wts[warp][2][c], hv, s0);
-                    s1 = fma(dwts[warp][2][c], hv, s1);
+                for (int c0 = 0; c0 < P2; c0 += 8) {   // loads of a group of 8 taps first
+                    R hv[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int c = c0 + u;
+                        hv[u] = (R)0;
+                        if (c < P2) {
+                            const int off = lix[warp][2][c] + rowo;
+                            if (ENUF_GUARD(g.check, (size_t)off < n3, 5)) hv[u] = h0[off];
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        if (c0 + u < P2) {
+                            s0 = fma(wts[warp][2][c0 + u], hv[u], s0);
+                            s1 = fma(dwts[warp][2][c0 + u], hv[u], s1);
+                        }
+                    }
                 }
                 const R wx = wts[warp][0][a], wy = wts[warp][1][b];
                 ax = fma(dwts[warp][0][a] * wy, s0, ax);
@@ -1430,13 +1490,31 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Geo g, const int* __r
                 const int a = ab - b * P2;
                 const int rowo = lix[warp][1][b] * n + lix[warp][0][a];
                 R s0 = 0, s1 = 0, s2 = 0;   // sum_z psi h_a
-                for (int c = 0; c < P2; ++c) {
-                    const R w = wts[warp][2][c];
-                    const int off = lix[warp][2][c] + rowo;   // z index pre-scaled by n^2
-                    if (!ENUF_GUARD(g.check, (size_t)off < n3, 5)) continue;
-                    s0 = fma(w, h0[off], s0);
-                    s1 = fma(w, h1[off], s1);
-                    s2 = fma(w, h2[off], s2);
+                // the z taps in groups of 8: the group's 24 loads issue before
+                // its multiply-adds (the taps' loads are independent; one
+                // memory latency per group instead of one per tap)
+                for (int c0 = 0; c0 < P2; c0 += 8) {
+                    R v0[8], v1[8], v2[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int c = c0 + u;
+                        v0[u] = v1[u] = v2[u] = (R)0;
+                        if (c < P2) {
+                            const int off = lix[warp][2][c] + rowo;   // z index pre-scaled by n^2
+                            if (ENUF_GUARD(g.check, (size_t)off < n3, 5)) {
+                                v0[u] = h0[off];
+                                v1[u] = h1[off];
+                                v2[u] = h2[off];
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const R w = c0 + u < P2 ? wts[warp][2][c0 + u] : (R)0;
+                        s0 = fma(w, v0[u], s0);
+                        s1 = fma(w, v1[u], s1);
+                        s2 = fma(w, v2[u], s2);
+                    }
                 }
                 const R wab = wts[warp][0][a] * wts[warp][1][b];
                 ax = fma(wab, s0, ax);
@@ -1464,7 +1542,17 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Geo g, const int* __r
         }
         __syncwarp();
     }
-    if (tot.Edev) totals_if_last(g, tot);
+    if (tot.Edev) totals_if_last(g, tot, blk.n);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kGatherThreads) k_gather(Geo g, const int* __restrict__ tstart,
+                                                           const typename V4<R>::T* __restrict__ sq,
+                                                           const typename V4<R>::T* __restrict__ sw,
+                                                           const int* __restrict__ sb, const R* __restrict__ wb,
+                                                           const R* __restrict__ h, R* __restrict__ F,
+                                                           TotalsArgs tot) {
+    k_gather_body<R>(g, tstart, sq, sw, sb, wb, h, F, tot, Blk{(int)blockIdx.x, (int)gridDim.x});
 }
 
 // ---------------------------------------------------------------------------
@@ -1743,17 +1831,11 @@ __device__ __forceinline__ void real_beads(const Geo& g, int c0, int c1, int sel
         fx = warp_sum_r(fx);
         fy = warp_sum_r(fy);
         fz = warp_sum_r(fz);
-        if (lane == 0) {
-            const int i = real_as_int(sw[s].w);
-            if (real_half<R>()) {   // other warps add into this bead's force as its partners
-                atomicAdd(&F[3 * i], fx);
-                atomicAdd(&F[3 * i + 1], fy);
-                atomicAdd(&F[3 * i + 2], fz);
-            } else {
-                F[3 * i] += fx;
-                F[3 * i + 1] += fy;
-                F[3 * i + 2] += fz;
-            }
+        if (lane == 0) {   // a global reduction: other warps (as partners, or the DPD
+            const int i = real_as_int(sw[s].w);   // blocks of a fused pair launch) add into F too
+            atomicAdd(&F[3 * i], fx);
+            atomicAdd(&F[3 * i + 1], fy);
+            atomicAdd(&F[3 * i + 2], fz);
         }
         }
     }
@@ -1766,10 +1848,10 @@ __device__ __forceinline__ void real_beads(const Geo& g, int c0, int c1, int sel
 // are compacted in a per-warp queue so the pair arithmetic (erfc and exp in
 // FP32, the tabulated kernel in FP64) runs on full warps.
 template <typename R>
-__global__ void __launch_bounds__(kRealThreads) k_real(Geo g, const int* __restrict__ tstart,
+__device__ __forceinline__ void k_real_body(Geo g, const int* __restrict__ tstart,
                                                        const typename V4<R>::T* __restrict__ sq,
                                                        const typename V4<R>::T* __restrict__ sw,
-                                                       R* __restrict__ F, double* __restrict__ rpart) {
+                                                       R* __restrict__ F, double* __restrict__ rpart, Blk blk) {
     pdl_enter();
     using V = typename V4<R>::T;
     constexpr int NW = kRealThreads / 32;
@@ -1786,7 +1868,7 @@ __global__ void __launch_bounds__(kRealThreads) k_real(Geo g, const int* __restr
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     V* qu = queue + warp * 64;
     R eacc = 0, wacc = 0;
-    for (int tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x) {
+    for (int tile = blk.id; tile < g.ntiles; tile += blk.n) {
         const int tx = tile % g.ntd, ty = (tile / g.ntd) % g.ntd, tz = tile / (g.ntd * g.ntd);
         int xlo, xc, ylo, yc, zlo, zc;
         halo_dim(tx, g.rs, g.ntd, xlo, xc);
@@ -1861,9 +1943,17 @@ __global__ void __launch_bounds__(kRealThreads) k_real(Geo g, const int* __restr
     double e = (double)eacc, w = (double)wacc;
     block_sum2(e, w);
     if (threadIdx.x == 0) {
-        rpart[2 * blockIdx.x] = e;
-        rpart[2 * blockIdx.x + 1] = w;
+        rpart[2 * blk.id] = e;
+        rpart[2 * blk.id + 1] = w;
     }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kRealThreads) k_real(Geo g, const int* __restrict__ tstart,
+                                                       const typename V4<R>::T* __restrict__ sq,
+                                                       const typename V4<R>::T* __restrict__ sw,
+                                                       R* __restrict__ F, double* __restrict__ rpart) {
+    k_real_body<R>(g, tstart, sq, sw, F, rpart, Blk{(int)blockIdx.x, (int)gridDim.x});
 }
 
 // ---------------------------------------------------------------------------
@@ -2208,11 +2298,10 @@ __device__ __forceinline__ void dpd_cells(const DpdDev& d, int H, int B3, const 
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kDpdThreads, sizeof(R) == 4 ? 4 : 2)
-    k_dpd(DpdDev d, int B, const typename V4<R>::T* __restrict__ sp, const typename V4<R>::T* __restrict__ sv,
+__device__ __forceinline__ void k_dpd_body(DpdDev d, int B, const typename V4<R>::T* __restrict__ sp, const typename V4<R>::T* __restrict__ sv,
           const int* __restrict__ cstart, const R* __restrict__ atab, const R* __restrict__ pos,
           const int* __restrict__ bnd, const uint64_t* __restrict__ stepp, R* __restrict__ F,
-          double* __restrict__ dpart) {
+          double* __restrict__ dpart, Blk bk) {
     pdl_enter();
     using V = typename V4<R>::T;
     constexpr bool F64 = sizeof(R) == 8;
@@ -2236,7 +2325,7 @@ __global__ void __launch_bounds__(kDpdThreads, sizeof(R) == 4 ? 4 : 2)
     // harmonic bonds (Sec. 2): one thread per bond, +f to i and -f to j
     {
         const R Kb = (R)d.K_bond, r0b = (R)d.r0_bond, iL = (R)(1.0 / d.L);
-        for (int k = blockIdx.x * blockDim.x + tid; k < d.nbonds; k += gridDim.x * blockDim.x) {
+        for (int k = bk.id * blockDim.x + tid; k < d.nbonds; k += bk.n * blockDim.x) {
             const int i = bnd[2 * k], j = bnd[2 * k + 1];
             R dd[3];
 #pragma unroll
@@ -2270,7 +2359,7 @@ __global__ void __launch_bounds__(kDpdThreads, sizeof(R) == 4 ? 4 : 2)
     band.lo0 = eps;
     band.lo = 1.0f - eps;
     band.hi = 1.0f + eps;
-    for (int blk = blockIdx.x; blk < nblk * nblk * nblk; blk += gridDim.x) {
+    for (int blk = bk.id; blk < nblk * nblk * nblk; blk += bk.n) {
         const int bx = blk % nblk, by = (blk / nblk) % nblk, bz = blk / (nblk * nblk);
         const int c0x = bx * B, c0y = by * B, c0z = bz * B;
         if (tid < H3) {   // halo cell ranges (H^3 <= 216 cells)
@@ -2351,9 +2440,38 @@ __global__ void __launch_bounds__(kDpdThreads, sizeof(R) == 4 ? 4 : 2)
     double e1 = 0.5 * (double)ec, e2 = 0.5 * (double)eb;
     block_sum2(e1, e2);
     if (threadIdx.x == 0) {
-        dpart[2 * blockIdx.x] = e1;
-        dpart[2 * blockIdx.x + 1] = e2;
+        dpart[2 * bk.id] = e1;
+        dpart[2 * bk.id + 1] = e2;
     }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kDpdThreads, sizeof(R) == 4 ? 4 : 2)
+    k_dpd(DpdDev d, int B, const typename V4<R>::T* __restrict__ sp, const typename V4<R>::T* __restrict__ sv,
+          const int* __restrict__ cstart, const R* __restrict__ atab, const R* __restrict__ pos,
+          const int* __restrict__ bnd, const uint64_t* __restrict__ stepp, R* __restrict__ F,
+          double* __restrict__ dpart) {
+    k_dpd_body<R>(d, B, sp, sv, cstart, atab, pos, bnd, stepp, F, dpart, Blk{(int)blockIdx.x, (int)gridDim.x});
+}
+
+// The DPD pair forces and the real-space electrostatic pairs in one launch
+// (horizontal fusion): blocks [0, nd) run the DPD body over the all-bead cell
+// list, the others the real-space body over the charged-bead tiles. Both add
+// into F (global reductions and per-bead sums) and write their own block
+// partials; launched once both cell structures exist.
+template <typename R>
+__global__ void __launch_bounds__(kDpdThreads, sizeof(R) == 4 ? 4 : 2)
+    k_pairs(DpdDev d, int B, const typename V4<R>::T* __restrict__ sp, const typename V4<R>::T* __restrict__ sv,
+            const int* __restrict__ cstart, const R* __restrict__ atab, const R* __restrict__ pos,
+            const int* __restrict__ bnd, const uint64_t* __restrict__ stepp, R* __restrict__ F,
+            double* __restrict__ dpart, int nd, Geo g, const int* __restrict__ tstart,
+            const typename V4<R>::T* __restrict__ sq, const typename V4<R>::T* __restrict__ sw,
+            double* __restrict__ rpart) {
+    static_assert(kDpdThreads == kRealThreads, "one block size for both roles");
+    if ((int)blockIdx.x < nd)
+        k_dpd_body<R>(d, B, sp, sv, cstart, atab, pos, bnd, stepp, F, dpart, Blk{(int)blockIdx.x, nd});
+    else
+        k_real_body<R>(g, tstart, sq, sw, F, rpart, Blk{(int)blockIdx.x - nd, (int)gridDim.x - nd});
 }
 
 // Table 2 steps 0-2 (m = 1): v0 = v + lambda F dt; v += F dt/2; r += v dt; step += 1.
@@ -2386,7 +2504,7 @@ __global__ void __launch_bounds__(256) k_vv_post(Geo g, int N, R dt, R* __restri
     }
     block_sum2(ke, dummy);
     if (threadIdx.x == 0) kpart[blockIdx.x] = ke;
-    if (tot.Edev) totals_if_last(g, tot);
+    if (tot.Edev) totals_if_last(g, tot, (int)gridDim.x);
 }
 
 // Standalone totals (one CTA), for evaluations outside a step graph.

@@ -38,7 +38,7 @@ class enuf_params(C.Structure):
                 ("beta", C.c_double), ("kappa", C.c_double), ("M", C.c_int), ("p", C.c_int),
                 ("sigma_s", C.c_int), ("kmask", C.c_int), ("prec", C.c_int), ("tile", C.c_int),
                 ("deriv", C.c_int), ("slater_k", C.c_int), ("fft_path", C.c_int), ("fft_radix", C.c_int),
-                ("spread", C.c_int), ("reserved", C.c_int * 1)]
+                ("spread", C.c_int), ("pairs", C.c_int)]
 
 
 class enuf_plan_info(C.Structure):
@@ -91,6 +91,7 @@ def _load():
         "enuf_batch_plan": (st, [i, C.POINTER(enuf_params), C.POINTER(C.c_int), vp, C.POINTER(vp)]),
         "enuf_batch_energy_forces": (st, [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), pd]),
         "enuf_batch_launches": (i, [vp]),
+        "enuf_batch_mode": (i, [vp]),
         "enuf_batch_destroy": (None, [vp]),
         "enuf_spread_noalloc": (st, [C.POINTER(enuf_params), i, vp, vp, vp, vp]),
     }
@@ -111,7 +112,7 @@ EXPORTED = ("enuf_plan", "enuf_footprint", "enuf_get_info", "enuf_plan_shape", "
             "enuf_last_error", "dpd_create", "dpd_step", "dpd_get_state", "dpd_set_state",
             "dpd_get_forces", "dpd_step_host", "dpd_device_state", "enuf_check_word",
             "enuf_built_with_checks", "enuf_debug_fail_allocs", "dpd_destroy", "enuf_batch_plan",
-            "enuf_batch_energy_forces", "enuf_batch_launches", "enuf_batch_destroy",
+            "enuf_batch_energy_forces", "enuf_batch_launches", "enuf_batch_mode", "enuf_batch_destroy",
             "enuf_spread_noalloc")
 
 
@@ -122,11 +123,12 @@ def _check(status, handle=None, what=""):
 
 
 def make_params(L, alpha, r_cut, beta, kappa, M=0, p=4, sigma_s=2, kmask=0,
-                prec="fp64", tile=0, deriv=0, slater_k=0, fft_path=0, fft_radix=0, spread=0) -> enuf_params:
+                prec="fp64", tile=0, deriv=0, slater_k=0, fft_path=0, fft_radix=0, spread=0,
+                pairs=0) -> enuf_params:
     pr = {"fp64": ENUF_FP64, "fp32": ENUF_FP32}[prec] if isinstance(prec, str) else int(prec)
     return enuf_params(float(L), float(alpha), float(r_cut), float(beta), float(kappa), int(M),
                        int(p), int(sigma_s), int(kmask), pr, int(tile), int(deriv), int(slater_k),
-                       int(fft_path), int(fft_radix), int(spread), (C.c_int * 1)())
+                       int(fft_path), int(fft_radix), int(spread), int(pairs))
 
 
 def _ptr(x):
@@ -372,7 +374,8 @@ class DpdSystem:
 
 
 class Batch:
-    """Owner of an enuf_batch_t: many systems, one captured graph."""
+    """Owner of an enuf_batch_t: many systems, one captured graph (one launch
+    sequence over all systems where every plan qualifies, see mode())."""
 
     def __init__(self, params_list, n_list, stream=None):
         ns = len(params_list)
@@ -397,6 +400,10 @@ class Batch:
 
     def launches(self):
         return lib.enuf_batch_launches(self.h)
+
+    def mode(self):
+        """1: one launch sequence over all systems; 0: one graph branch per system."""
+        return lib.enuf_batch_mode(self.h)
 
     def close(self):
         if self.h:

@@ -31,9 +31,9 @@ def _prep(prec, s):
     return cast(s.pos), cast(s.vel), cast(s.q)
 
 
-def _make(enuf, prec, s, pos, vel, q, dp):
+def _make(enuf, prec, s, pos, vel, q, dp, pairs=0):
     P = dict(L=s.L, M=s.M, **s.params)
-    plan = enuf.Plan(enuf.make_params(prec=prec, **P), s.N)
+    plan = enuf.Plan(enuf.make_params(prec=prec, pairs=pairs, **P), s.N)
     sysm = enuf.DpdSystem(plan, dp["a"], dp["gamma"], dp["sigma"], dp["dt"], pos, vel, s.types, q, s.bonds,
                           lambda_vv=dp["lambda_vv"], K_bond=dp["K_bond"], r0_bond=dp["r0_bond"], seed=dp["seed"])
     Po = orc.EwaldParams(**P)
@@ -59,13 +59,15 @@ def _check_forces(F, R, tol):
     assert _bead_max(F, R) < 100 * tol, _bead_max(F, R)
 
 
+@pytest.mark.parametrize("pairs", [0, 1])
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 1e-5)])
-def test_initial_force_parity(enuf, prec, tol):
-    """Table 2 steps 3-5 at step 0: DPD C + D + R/sqrt(dt) + bonds + electrostatics."""
+def test_initial_force_parity(enuf, prec, tol, pairs):
+    """Table 2 steps 3-5 at step 0: DPD C + D + R/sqrt(dt) + bonds + electrostatics
+    (pairs = 0: the DPD and real-space pairs in one launch; 1: two launches)."""
     s = _system()
     dp = W.dpd_params(5)
     pos, vel, q = _prep(prec, s)
-    plan, sysm, Po, Do = _make(enuf, prec, s, pos, vel, q, dp)
+    plan, sysm, Po, Do = _make(enuf, prec, s, pos, vel, q, dp, pairs)
     _, _, F, step = sysm.get_state()
     Fr, Er = orc.total_forces(Po, Do, pos, vel, s.types, q, s.bonds, step=0)
     assert step == 0
@@ -91,14 +93,15 @@ def test_density4_force_parity(enuf, prec, tol):
     plan.close()
 
 
+@pytest.mark.parametrize("pairs", [0, 1])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_trajectory_parity(enuf, prec):
+def test_trajectory_parity(enuf, prec, pairs):
     """Three modified velocity-Verlet steps; positions, velocities, forces and
     energies against the oracle's Table 2 integrator."""
     s = _system(valency=2)
     dp = W.dpd_params(5)
     pos, vel, q = _prep(prec, s)
-    plan, sysm, Po, Do = _make(enuf, prec, s, pos, vel, q, dp)
+    plan, sysm, Po, Do = _make(enuf, prec, s, pos, vel, q, dp, pairs)
     F0, _ = orc.total_forces(Po, Do, pos, vel, s.types, q, s.bonds, step=0)
     pr, vr, Fr, st, Er = orc.dpd_run(Po, Do, pos, vel, F0, s.types, q, s.bonds, step=0, nsteps=3)
     E = sysm.step(3, want_energy=True)
@@ -245,14 +248,15 @@ def test_box_needs_three_cells_per_edge(enuf):
         plan.close()
 
 
+@pytest.mark.parametrize("pairs", [0, 1])
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 1e-5)])
-def test_full_size_polyelectrolyte_sampled(enuf, prec, tol):
+def test_full_size_polyelectrolyte_sampled(enuf, prec, tol, pairs):
     """The bench workload (81000 beads, L = 30): initial ENUF-DPD force of 256
     sampled beads against the oracle bead by bead."""
     s = W.polyelectrolyte()
     dp = W.dpd_params(5)
     pos, vel, q = _prep(prec, s)
-    plan, sysm, Po, Do = _make(enuf, prec, s, pos, vel, q, dp)
+    plan, sysm, Po, Do = _make(enuf, prec, s, pos, vel, q, dp, pairs)
     _, _, F, _ = sysm.get_state()
     rng = np.random.default_rng(3)
     sample = np.sort(np.concatenate([rng.choice(np.nonzero(q)[0], 128, replace=False),

@@ -422,12 +422,60 @@ def test_batch_equals_single_plans(enuf, prec):
     b = enuf.Batch(params, [s.N for s in systems])
     E = b.energy_forces(pos_l, q_l, F_l)
     E2 = b.energy_forces(pos_l, q_l, F_l)
-    assert b.launches() == sum(6 + k for k in nfft)
+    if prec == "fp32":   # one launch sequence: 8 kernels and one spreading launch per tile edge
+        tiles = {enuf.plan_shape(p, s.N).tile for p, s in zip(params, systems)}
+        assert b.mode() == 1 and b.launches() == 8 + len(tiles)
+    else:                # FP64: one graph branch per system
+        assert b.mode() == 0 and b.launches() == sum(6 + k for k in nfft)
     for k, (Fs, Es) in enumerate(singles):
         Fb = F_l[k].double().cpu().numpy()
         tol = 1e-6 if prec == "fp32" else 1e-12
         assert _rel_rms(Fb, Fs) < tol
         assert np.allclose(E[k], Es, rtol=tol) and np.allclose(E2[k], Es, rtol=tol)
+    b.close()
+
+
+def test_batch_sequence_matches_oracle(enuf):
+    """The one-launch-sequence batch (FP32): five uneven systems of the batched
+    sweep (electrolytes and polyelectrolytes, different boxes, grids and tile
+    edges) against the FP64 oracle system by system; then new arrays for two
+    systems (the tables are rewritten) and the same results again."""
+    systems = W.batch_sweep(5, n_min=3000, n_max=12000)
+    params = [enuf.make_params(prec="fp32", L=s.L, M=s.M, **s.params) for s in systems]
+    shapes = [enuf.plan_shape(p, s.N) for p, s in zip(params, systems)]
+    assert len({sh.n for sh in shapes}) >= 2 and len({sh.tile for sh in shapes}) >= 2
+    inputs = [_inputs("fp32", s.pos, s.q) for s in systems]
+    pos_l = [torch.tensor(p, dtype=torch.float32, device="cuda") for p, _ in inputs]
+    q_l = [torch.tensor(q, dtype=torch.float32, device="cuda") for _, q in inputs]
+    F_l = [torch.full_like(p, float("nan")) for p in pos_l]
+    b = enuf.Batch(params, [s.N for s in systems])
+    assert b.mode() == 1
+    E = b.energy_forces(pos_l, q_l, F_l)
+    refs = []
+    for k, s in enumerate(systems):
+        P = dict(L=s.L, M=s.M, **s.params)
+        ref = Ref(P, *inputs[k])
+        refs.append(ref)
+        F = F_l[k].double().cpu().numpy()
+        assert np.all(F[inputs[k][1] == 0] == 0.0)
+        assert _rel_rms(F, ref.F) < TOL["fp32"]["F"] and _bead_max(F, ref.F) < 100 * TOL["fp32"]["F"], k
+        t = TOL["fp32"]["E"]
+        Er = ref.E
+        assert abs(E[k][1] - Er[1]) <= t * abs(Er[1]) and abs(E[k][2] - Er[2]) <= t * abs(Er[2]), (k, E[k], Er)
+        assert abs(E[k][0] - Er[0]) <= t * max(abs(Er[0]), abs(Er[2])), (k, E[k], Er)
+        assert abs(E[k][3] - Er[3]) <= t * (abs(Er[0]) + abs(Er[1]) + abs(Er[2])), (k, E[k], Er)
+    launches = b.launches()
+    # new arrays for systems 1 and 3 (same contents): tables rewritten, graph kept
+    pos2 = list(pos_l)
+    F2 = list(F_l)
+    for k in (1, 3):
+        pos2[k] = pos_l[k].clone()
+        F2[k] = torch.full_like(F_l[k], float("nan"))
+    E2 = b.energy_forces(pos2, q_l, F2)
+    assert b.launches() == launches
+    for k in range(len(systems)):
+        assert _rel_rms(F2[k].double().cpu().numpy(), refs[k].F) < TOL["fp32"]["F"]
+        assert np.allclose(E2[k], E[k], rtol=1e-6, atol=1e-6 * abs(refs[k].E[2]))
     b.close()
 
 

@@ -124,6 +124,31 @@ def test_batch_allocation(enuf):
         assert np.allclose(np.asarray(E)[k][:4], Ek[:4], rtol=1e-12)
 
 
+def test_batch_sequence_table_allocation(enuf):
+    """FP32 batch run as one launch sequence: after its three plans, the
+    allocation of the batch's argument tables fails; nothing is kept, and the
+    next batch works."""
+    systems = [W.electrolyte(N, seed_offset=960 + k) for k, N in enumerate([2000, 3000, 4000])]
+    params = [enuf.make_params(prec="fp32", L=s.L, M=s.M, **s.params) for s in systems]
+    pos = [torch.tensor(s.pos, dtype=torch.float32, device="cuda") for s in systems]
+    q = [torch.tensor(s.q, dtype=torch.float32, device="cuda") for s in systems]
+    F = [torch.empty_like(p) for p in pos]
+    enuf.debug_fail_allocs(1, after=3)                  # the tables, after three plans
+    with pytest.raises(enuf.EnufError) as e:
+        enuf.Batch(params, [s.N for s in systems])
+    assert e.value.status == enuf.ENUF_ERR_OOM
+    b = enuf.Batch(params, [s.N for s in systems])
+    assert b.mode() == 1
+    E = b.energy_forces(pos, q, F)
+    b.close()
+    for k, s in enumerate(systems):
+        plan = enuf.Plan(params[k], s.N)
+        Fk, Ek = _forces(plan, pos[k], q[k])
+        plan.close()
+        assert _rel(F[k].cpu().numpy().astype(np.float64), Fk.astype(np.float64)) < 1e-6
+        assert np.allclose(np.asarray(E)[k][:4], Ek[:4], rtol=1e-6)
+
+
 def test_serving_request_fails_alone(enuf):
     from paper_1303_4523_gb300.serving import GpuBackend, Request, Server, _spec_from
     specs = [_spec_from(W.electrolyte(N, seed_offset=950 + k), f"s{k}") for k, N in enumerate([2000, 3000, 4000])]
