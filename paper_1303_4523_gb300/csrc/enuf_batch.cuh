@@ -133,8 +133,9 @@ struct FftXYArgs {
     typename Cx<R>::T* spec2;
     int nblk;
 };
+// the batched plane passes run thousands of CTAs: two per SM (<= 64 registers)
 template <typename R>
-__global__ void __launch_bounds__(512) kb_fft_xy(const FftXYArgs<R>* __restrict__ tab, const int* __restrict__ cmap) {
+__global__ void __launch_bounds__(512, 2) kb_fft_xy(const FftXYArgs<R>* __restrict__ tab, const int* __restrict__ cmap) {
     pdl_enter();
     const int m = cmap[blockIdx.x];
     const FftXYArgs<R>& a = tab[m >> kBatchShift];
@@ -174,7 +175,7 @@ struct FftYXArgs {
     int nblk;
 };
 template <typename R>
-__global__ void __launch_bounds__(512) kb_fft_yx(const FftYXArgs<R>* __restrict__ tab, const int* __restrict__ cmap) {
+__global__ void __launch_bounds__(512, 2) kb_fft_yx(const FftYXArgs<R>* __restrict__ tab, const int* __restrict__ cmap) {
     pdl_enter();
     const int m = cmap[blockIdx.x];
     const FftYXArgs<R>& a = tab[m >> kBatchShift];
