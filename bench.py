@@ -286,6 +286,7 @@ def run_ours(args, rank, world, dist):
         "fp32_gradient_mode": {"value": job_throughput(world, len(perg), totg),
                                "ms_per_step": round(totg / len(perg), 5),
                                "p50": round(sorted(perg)[len(perg) // 2], 5), "steps": len(perg),
+                               "clocks": clkg,
                                "note": "reciprocal forces as the gradient of the window (deriv = 1)"},
         "fp32_separate_pairs": {"value": job_throughput(world, len(perp), sum(perp)),
                              "ms_per_step": round(sum(perp) / len(perp), 5),
@@ -450,7 +451,7 @@ def run_sizes(args):
         variants = (("fp32", "fp32", torch.float32, 4, 0), ("fp64", "fp64", torch.float64, 8, 0),
                     ("fp32_grad", "fp32", torch.float32, 4, 1))
         for key, prec, dt, esz, deriv in (variants[:1] if args.fp32_only else variants):
-            P = dict(L=s.L, M=s.M, **s.params)
+            P = dict(L=s.L, M=s.M, tile=args.tile, **s.params)
             sp = args.spread if prec == "fp32" else 0
             plan = enuf.Plan(enuf.make_params(prec=prec, deriv=deriv, spread=sp, **P), s.N)
             plan.enable_timing(True)
@@ -631,7 +632,7 @@ def main():
                     help="--mode sizes: run only these system sizes (of 3000 24000 81000 192000 375000 3000000)")
     ap.add_argument("--spread", type=int, default=0,
                     help="--mode sizes: FP32 spreading kernel (enuf_params.spread: 0 auto, 1 tile form, "
-                         "2 footprint bricks, 3 bricks fused with the x pass)")
+                         "2 footprint bricks, 3 bricks fused with the x pass, 4 scatter form)")
     ap.add_argument("--fp32-only", action="store_true", help="--mode sizes: skip the FP64 and gradient-mode plans")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)

@@ -102,7 +102,12 @@ typedef struct {
                          T x T rows, one warp per z-plane, no work on zero weights;
                          3 = form 2 fused with the forward x pass (the grid is never
                          written: needs the two-factor kernels, the five-pass FFT and
-                         an even T). Same result to rounding. */
+                         an even T);
+                         4 = scatter form: one CTA per region of T^3 (T >= 16) or 2^3
+                         tiles, each bead whose window meets the region spread by a
+                         warp with shared-memory atomics, work on its taps inside the
+                         region only (needs p = 4, the region dividing n and n >= 2
+                         (region + T + 8)). Same result to rounding. */
     int    pairs;     /* DPD systems: 0 = the DPD pair forces and the real-space pairs in
                          one launch whose blocks take either role, after both cell
                          structures exist (default; measured faster at the 81000-bead
@@ -124,7 +129,7 @@ typedef struct {
                                   two-factor kernels) */
     int    fft_radix[8];       /* their radices in order (two-factor: f1, f2) */
     int    fft_two_factor;     /* 1: the two-factor kernels (enuf_params.fft_radix) */
-    int    spread;             /* spreading kernel taken (enuf_params.spread: 1, 2 or 3) */
+    int    spread;             /* spreading kernel taken (enuf_params.spread: 1 to 4) */
     int    brick_x;            /* x extent of a spreading brick (forms 2 and 3) */
 } enuf_plan_info;
 

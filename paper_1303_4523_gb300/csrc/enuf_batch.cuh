@@ -195,13 +195,14 @@ struct GatherArgs {
     TotalsArgs tot;
     int nblk;
 };
-template <typename R>
+// PT: the tap count 2p when every system of the batch has the same window, else 0
+template <typename R, int PT>
 __global__ void __launch_bounds__(kGatherThreads, 4) kb_gather(const GatherArgs<R>* __restrict__ tab,
                                                             const int* __restrict__ cmap) {
     pdl_enter();
     const int m = cmap[blockIdx.x];
     const GatherArgs<R>& a = tab[m >> kBatchShift];
-    k_gather_body<R>(a.g, a.tstart, a.sq, a.sw, a.sb, a.wb, a.h, a.F, a.tot, Blk{m & kBatchLocal, a.nblk});
+    k_gather_body<R, PT>(a.g, a.tstart, a.sq, a.sw, a.sb, a.wb, a.h, a.F, a.tot, Blk{m & kBatchLocal, a.nblk});
 }
 
 }  // namespace enuf

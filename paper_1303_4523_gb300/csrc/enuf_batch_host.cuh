@@ -167,6 +167,9 @@ cudaError_t batch_build(void* dbuf, const BatchSys* sys, int nsys, BatchLaunch* 
         put(L.gather, a.data(), a.size() * sizeof(a[0]), m);
         L.gather.threads = kGatherThreads;
         L.gather.smem = 0;
+        L.gather.T = 2 * sys[0].g.p;   // the common tap count, or 0
+        for (int s = 1; s < nsys; ++s)
+            if (2 * sys[s].g.p != L.gather.T) L.gather.T = 0;
     }
     if (off > batch_bytes<R>(sys, nsys)) return cudaErrorInvalidValue;   // the tables outgrew their buffer
     *out = L;
@@ -205,7 +208,14 @@ cudaError_t batch_enqueue(const BatchLaunch& L, cudaStream_t s0, cudaStream_t s1
     run(true, true, kb_fft_z<R>, L.fft_z, (const FftZArgs<R>*)L.fft_z.tab, s0);
     run(true, true, kb_fft_yx<R>, L.fft_yx, (const FftYXArgs<R>*)L.fft_yx.tab, s0);
     cudaStreamWaitEvent(s0, evJoin, 0);
-    run(false, true, kb_gather<R>, L.gather, (const GatherArgs<R>*)L.gather.tab, s0);
+    const GatherArgs<R>* gtab = (const GatherArgs<R>*)L.gather.tab;
+    switch (L.gather.T) {
+        case 6: run(false, true, kb_gather<R, 6>, L.gather, gtab, s0); break;
+        case 8: run(false, true, kb_gather<R, 8>, L.gather, gtab, s0); break;
+        case 10: run(false, true, kb_gather<R, 10>, L.gather, gtab, s0); break;
+        case 12: run(false, true, kb_gather<R, 12>, L.gather, gtab, s0); break;
+        default: run(false, true, kb_gather<R, 0>, L.gather, gtab, s0); break;
+    }
     return cudaGetLastError();
 }
 

@@ -420,7 +420,7 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
     // spreading form (FP32): bricks of whole x rows fused with the x pass where the
     // two-factor five-pass FFT runs and the brick fits; footprint bricks into the
     // grid otherwise from n = 128 on; the tile form below
-    if (P.spread < 0 || P.spread > 3) return fail(plan, ENUF_ERR_INVALID, "spread must be 0..3");
+    if (P.spread < 0 || P.spread > 4) return fail(plan, ENUF_ERR_INVALID, "spread must be 0..4");
     if (P.pairs != 0 && P.pairs != 1) return fail(plan, ENUF_ERR_INVALID, "pairs must be 0 or 1");
     fs.spread = 1;
     if (P.prec == ENUF_FP32) {
@@ -439,6 +439,18 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
         // automatic: the tile form (measured faster than forms 2 and 3 at every size
         // of the electrolyte sweep, 81k to 3M beads)
         int want = P.spread == 0 ? 1 : P.spread;
+        // scatter form: regions of one tile (T = 16, 20, 24) or 2^3 tiles (T = 8, 10, 12)
+        const int scE = T >= 16 ? T : 2 * T, scRT = scE / T;
+        const bool sc_ok = 2 * P.p == 8 && (scE == 16 || scE == 20 || scE == 24) && g.ntd % scRT == 0 &&
+                           g.ntd >= scRT + 2 && n % 4 == 0 && n >= 2 * (scE + T + 2 * P.p);
+        if (want == 4 && !sc_ok)
+            return fail(plan, ENUF_ERR_INVALID, "spread = 4 needs p = 4, a tile edge of 8, 10, 12, 16, 20 or 24 "
+                                                "whose region (%d) divides n = %d, and n >= %d",
+                        scE, n, 2 * (scE + T + 2 * P.p));
+        if (want == 4) {
+            fs.spread = 4;
+            fs.sc_E = scE;
+        }
         if (want == 3 && !fx_fits)
             return fail(plan, ENUF_ERR_INVALID, "spread = 3 needs the two-factor five-pass FFT, an even tile and "
                                                 "a brick that fits in shared memory");
@@ -463,7 +475,7 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
             fs.brick_lp = 0;
             fs.brick_smem = brick_smem<float>(T, bx, 0);
         }
-        if (fs.spread > 1) {
+        if (fs.spread == 2 || fs.spread == 3) {
             fs.brick_threads = 32 * T;
             fs.brick_grid = (n / fs.brick_x) * g.ntd * g.ntd;
         }
@@ -868,7 +880,7 @@ static void fill_info(const enuf_plan_s* plan, enuf_plan_info* info) {
     info->device_bytes = plan->dbytes;
     info->fft_two_factor = plan->fp.f1 ? 1 : 0;
     info->spread = plan->fs.spread;
-    info->brick_x = plan->fs.spread > 1 ? plan->fs.brick_x : 0;
+    info->brick_x = plan->fs.spread == 2 || plan->fs.spread == 3 ? plan->fs.brick_x : 0;
     if (plan->fp.f1) {
         info->fft_stages = 2;
         for (int i = 0; i < 8; ++i) info->fft_radix[i] = i == 0 ? plan->fp.f1 : (i == 1 ? plan->fp.f2 : 0);

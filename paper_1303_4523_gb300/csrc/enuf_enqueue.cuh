@@ -143,6 +143,9 @@ cudaError_t configure_kernels(int max_smem) {
         set((const void*)k2_fft_yx<R>);
         set((const void*)k_spread_brick<R, false>);
         set((const void*)k_spread_brick<R, true>);
+        set((const void*)k_spread_sc<16, 8>);
+        set((const void*)k_spread_sc<20, 8>);
+        set((const void*)k_spread_sc<24, 8>);
         set((const void*)kb_bin_count<R>);
         set((const void*)kb_bin_scatter<R>);
         set((const void*)kb_real<R>);
@@ -241,6 +244,15 @@ void enqueue_spread_brick(const Geo& g, const FftShape& fs, const FftPlanDev& fp
            static_cast<const C*>(w.tw), static_cast<C*>(w.spec1), fs.brick_lp);
 }
 
+// Scatter-form spreading (FP32, spread = 4): one CTA per region of edge sc_E.
+inline void enqueue_spread_sc(const Geo& g, const FftShape& fs, const Work& w, cudaStream_t s, bool pdl) {
+    const int regions = (g.n / fs.sc_E) * (g.n / fs.sc_E) * (g.n / fs.sc_E);
+    auto k = fs.sc_E == 16 ? k_spread_sc<16, 8> : (fs.sc_E == 20 ? k_spread_sc<20, 8> : k_spread_sc<24, 8>);
+    launch(pdl, true, k, regions, kScThreads, sc_smem(fs.sc_E), s, g, (const int*)w.tstart,
+           static_cast<const float4*>(w.sq), (const int*)w.sb, static_cast<const float*>(w.wb),
+           static_cast<float*>(w.grid));
+}
+
 // The same passes on the two-factor kernels (FP32 grids with n = f1 f2); with
 // the spreading fused with the x pass (spread = 3) the x pass is already done.
 template <typename R>
@@ -306,6 +318,18 @@ void enqueue_fft(const Geo& g, const FftShape& fs, const FftPlanDev& fp, const W
     }
 }
 
+// the gather with its tap loops unrolled for the common window widths
+template <typename R>
+auto gather_kernel(int taps) {
+    switch (taps) {
+        case 6: return k_gather<R, 6>;
+        case 8: return k_gather<R, 8>;
+        case 10: return k_gather<R, 10>;
+        case 12: return k_gather<R, 12>;
+        default: return k_gather<R, 0>;
+    }
+}
+
 template <typename R>
 cudaError_t enqueue_enuf(const Geo& g, const FftShape& fs, const FftPlanDev& fp, const Work& w,
                          const EvalArgs& a, cudaStream_t s0, cudaStream_t s1, cudaEvent_t evFork,
@@ -350,7 +374,9 @@ cudaError_t enqueue_enuf(const Geo& g, const FftShape& fs, const FftPlanDev& fp,
     // reciprocal branch
     rec(ev, 1, true, s0);
     if constexpr (sizeof(R) == 4) {
-        if (fs.spread > 1)
+        if (fs.spread == 4)
+            enqueue_spread_sc(g, fs, w, s0, pdl);
+        else if (fs.spread > 1)
             enqueue_spread_brick<R>(g, fs, fp, w, s0, pdl);
         else
             enqueue_spread<R>(g, w, static_cast<R*>(w.grid), s0, pdl);
@@ -374,7 +400,7 @@ cudaError_t enqueue_enuf(const Geo& g, const FftShape& fs, const FftPlanDev& fp,
     cudaStreamWaitEvent(s0, evJoin, 0);
     rec(ev, 3, true, s0);
     // with fuse_totals the gather's last block also reduces the energies
-    launch(false, true, k_gather<R>, w.nblk_gather, kGatherThreads, 0, s0, g, (const int*)w.tstart, (const V*)sq,
+    launch(false, true, gather_kernel<R>(2 * g.p), w.nblk_gather, kGatherThreads, 0, s0, g, (const int*)w.tstart, (const V*)sq,
            (const V*)sw, (const int*)w.sb, static_cast<const R*>(w.wb), static_cast<const R*>(w.h), F,
            fuse_totals ? totals_args(g, w, false, 1) : no_totals());
     rec(ev, 3, false, s0);

@@ -102,9 +102,11 @@ struct FftShape {
     int composite;   // the radix plan uses 6, 10, 12, 16 or 20 (FP32): the CR kernel instances
     int two;         // FP32 two-factor kernels (FftPlanDev::f1, f2), same shapes and layouts
     // spreading: 1 tile form, 2 footprint bricks into the grid, 3 bricks fused with
-    // the forward x pass (the x pass kernel is then not launched)
+    // the forward x pass (the x pass kernel is then not launched), 4 scatter form
+    // over regions of edge sc_E
     int spread;
     int brick_x, brick_threads, brick_smem, brick_grid, brick_lp;
+    int sc_E;
 };
 
 // Device workspace of one plan (all pointers device memory, one allocation).
@@ -221,7 +223,7 @@ struct BatchKernel {
     void* tab = nullptr;
     int* cmap = nullptr;
     int blocks = 0, threads = 0, smem = 0;
-    int T = 0;   // spreading: the tile edge of this group
+    int T = 0;   // spreading: the tile edge of this group; gather: the common tap count 2p (0: mixed)
 };
 struct BatchLaunch {
     BatchKernel bin_count, bin_scatter, bin_weights, real, fft_xy, fft_z, fft_yx, gather;

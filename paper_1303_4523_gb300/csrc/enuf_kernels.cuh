@@ -1018,6 +1018,139 @@ __global__ void __launch_bounds__(spread2_threads<SLAB>(T)) k_spread_col(Geo g, 
 }
 
 // ---------------------------------------------------------------------------
+// a2, scatter form (FP32; large grids with few beads per grid point). One CTA
+// owns a region of RT^3 tiles, edge E = RT T (a template constant), held in
+// shared memory. Its candidates are the charged beads of the (RT + 2)^3 bins
+// around it: a window of 2p <= T taps reaches no farther than the next tile.
+// A warp tests 32 candidates at a time against the region; each bead whose
+// window meets it is then spread by the whole warp: lanes over its (x, y)
+// taps, an unrolled loop over its z taps, each product q w_x w_y w_z added to
+// the region with a shared-memory atomic. Work is spent only on the taps
+// that land in the region; the column form multiplies every column of its
+// tile by every z slot, which at ~100 grid points per charged bead is mostly
+// zeros. The region is written once, rows of E points as 16-byte stores.
+// The host admits it when 2p = PT, E is a multiple of T, RT <= 2 divides the
+// tiles per dimension ntd >= RT + 2, n % 4 = 0 and n >= 2 (E + T + PT): a
+// window's offset from the region origin is then unique modulo n.
+// ---------------------------------------------------------------------------
+constexpr int kScThreads = 256;
+// x pitch of the region in shared memory: the 8 x taps x 4 y rows of one
+// update land on 32 distinct banks when the pitch is 8 or 24 modulo 32
+__host__ __device__ constexpr int sc_pitch(int E) { return (E % 32 == 8 || E % 32 == 24) ? E : sc_pitch(E + 4); }
+__host__ __device__ constexpr int sc_smem(int E) { return E * E * sc_pitch(E) * (int)sizeof(float); }
+
+template <int E, int PT>
+__global__ void __launch_bounds__(kScThreads) k_spread_sc(Geo g, const int* __restrict__ tstart,
+                                                          const float4* __restrict__ sq, const int* __restrict__ sb,
+                                                          const float* __restrict__ wb, float* __restrict__ grid) {
+    pdl_enter();
+    static_assert(E % 4 == 0 && PT >= 2 && PT <= 16, "region edge and window");
+    constexpr int EP = sc_pitch(E);
+    constexpr int BPR = 32 / PT;               // y taps per round of lanes
+    constexpr int NR = (PT + BPR - 1) / BPR;   // rounds
+    constexpr int NW = kScThreads / 32;
+    constexpr unsigned FULL = 0xffffffffu;
+    extern __shared__ __align__(16) float acc[];   // [E][E][EP]
+    __shared__ int nb_start[64], nb_cnt[64], nb_chunk[65];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int T = g.T, RT = E / T, nr = g.ntd / RT;
+    const int rx = blockIdx.x % nr, ry = (blockIdx.x / nr) % nr, rz = blockIdx.x / (nr * nr);
+    const int ox = rx * E, oy = ry * E, oz = rz * E;
+    for (int e = tid; e < E * E * EP / 4; e += kScThreads) reinterpret_cast<float4*>(acc)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int nbd = RT + 2, nbins = nbd * nbd * nbd;   // <= 64
+    if (warp == 0) {   // the bins, their bead ranges and a prefix of their 32-bead chunks
+        int run = 0;
+        for (int k0 = 0; k0 < nbins; k0 += 32) {
+            const int k = k0 + lane;
+            int st = 0, cnt = 0;
+            if (k < nbins) {
+                const int dx = k % nbd, dy = (k / nbd) % nbd, dz = k / (nbd * nbd);
+                const int bx = (rx * RT + dx - 1 + g.ntd) % g.ntd;
+                const int by = (ry * RT + dy - 1 + g.ntd) % g.ntd;
+                const int bz = (rz * RT + dz - 1 + g.ntd) % g.ntd;
+                const int t = (bz * g.ntd + by) * g.ntd + bx;
+                st = tstart[t];
+                cnt = tstart[t + 1] - st;
+            }
+            const int ch = (cnt + 31) >> 5;
+            int x = ch;
+#pragma unroll
+            for (int of = 1; of < 32; of <<= 1) {
+                const int y = __shfl_up_sync(FULL, x, of);
+                if (lane >= of) x += y;
+            }
+            if (k < nbins) {
+                nb_start[k] = st;
+                nb_cnt[k] = cnt;
+                nb_chunk[k] = run + x - ch;
+            }
+            run += __shfl_sync(FULL, x, 31);
+        }
+        if (lane == 0) nb_chunk[nbins] = run;
+    }
+    __syncthreads();
+    const int p = g.p, n = g.n, hn = n >> 1;
+    const int a = lane % PT, b = lane / PT;
+    const bool lane_on = lane < BPR * PT;
+    const int nchunks = nb_chunk[nbins];
+    for (int h = warp; h < nchunks; h += NW) {
+        // the bin of chunk h: the last k with nb_chunk[k] <= h
+        const unsigned b0 = __ballot_sync(FULL, lane < nbins && nb_chunk[lane] <= h);
+        const unsigned b1 = __ballot_sync(FULL, lane + 32 < nbins && nb_chunk[lane + 32] <= h);
+        const int k = __popc(b0) + __popc(b1) - 1;
+        const int c0 = (h - nb_chunk[k]) * 32;
+        const int j = nb_start[k] + c0 + lane;
+        bool hit = false;
+        int pk = 0;
+        if (c0 + lane < nb_cnt[k]) {
+            const int pb = sb[j];
+            int d0 = (pb & 1023) - p + 1 - ox, d1 = ((pb >> 10) & 1023) - p + 1 - oy, d2 = ((pb >> 20) & 1023) - p + 1 - oz;
+            d0 += d0 < -hn ? n : (d0 >= hn ? -n : 0);
+            d1 += d1 < -hn ? n : (d1 >= hn ? -n : 0);
+            d2 += d2 < -hn ? n : (d2 >= hn ? -n : 0);
+            hit = d0 > -PT && d0 < E && d1 > -PT && d1 < E && d2 > -PT && d2 < E;
+            pk = (d0 + PT) | (d1 + PT) << 8 | (d2 + PT) << 16;   // each in [1, E + PT) < 256
+        }
+        unsigned m = __ballot_sync(FULL, hit);
+        while (m) {   // warp-uniform: one bead at a time
+            const int src = __ffs(m) - 1;
+            m &= m - 1;
+            const int js = __shfl_sync(FULL, j, src);
+            const int ps = __shfl_sync(FULL, pk, src);
+            const int dx = (ps & 255) - PT, dy = ((ps >> 8) & 255) - PT, dz = (ps >> 16) - PT;
+            const float w = lane < 3 * PT ? wb[(size_t)js * (3 * PT) + lane] : 0.f;   // x, y, z taps
+            const float q = sq[js].w;
+            const float wxq = __shfl_sync(FULL, w, a) * q;
+            float wz[PT];
+#pragma unroll
+            for (int c = 0; c < PT; ++c) wz[c] = __shfl_sync(FULL, w, 2 * PT + c);
+            const int x = dx + a;
+            const bool vx = lane_on && (unsigned)x < (unsigned)E;
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const int bb = b + r * BPR;
+                const float wy = __shfl_sync(FULL, w, PT + (bb < PT ? bb : PT - 1));
+                const int y = dy + bb;
+                const bool v = vx && bb < PT && (unsigned)y < (unsigned)E;
+                const float wxy = wxq * wy;
+                const int i0 = (dz * E + y) * EP + x;
+#pragma unroll
+                for (int c = 0; c < PT; ++c)
+                    if (v && (unsigned)(dz + c) < (unsigned)E) atomicAdd(&acc[i0 + c * E * EP], wxy * wz[c]);
+            }
+        }
+    }
+    __syncthreads();
+    constexpr int Q = E / 4;   // 16-byte pieces per row
+    for (int e = tid; e < E * E * Q; e += kScThreads) {
+        const int row = e / Q, cq = e - row * Q;
+        const int z = row / E, y = row - z * E;
+        const float4 v = *reinterpret_cast<const float4*>(acc + (z * E + y) * EP + 4 * cq);
+        *reinterpret_cast<float4*>(grid + ((size_t)(oz + z) * n + (oy + y)) * n + ox + 4 * cq) = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // a3: forward FFT pass along x (R2C, two real rows per complex line), keep
 // k_x = 0..nc; output spec1[z][kx][y].
 // ---------------------------------------------------------------------------
@@ -1407,7 +1540,12 @@ __global__ void __launch_bounds__(256) k_fft_ix(Geo g, FftPlanDev fp, const type
 // ---------------------------------------------------------------------------
 constexpr int kGatherThreads = 256;
 
-template <typename R>
+// PT > 0: the window's tap count 2p fixed at compile time. The tap loops are
+// then unrolled: the z taps' offsets and weights sit in registers and the
+// 3 x 2p loads of a column are all in flight at once (the runtime-count loop
+// waits on each tap's loads before the next: at 3M beads the gather was
+// bound by that latency, not by DRAM).
+template <typename R, int PT = 0>
 __device__ __forceinline__ void k_gather_body(Geo g, const int* __restrict__ tstart,
                                                            const typename V4<R>::T* __restrict__ sq,
                                                            const typename V4<R>::T* __restrict__ sw,
@@ -1459,7 +1597,63 @@ __device__ __forceinline__ void k_gather_body(Geo g, const int* __restrict__ tst
         // lanes over the (x, y) taps, the z taps summed first and weighted by
         // the column's x-y weight once; ab -> (a, b) by a float reciprocal
         // (ab < 256, so the quotient of ab + 1/2 is 1/32 from an integer)
-        if (grad) {   // one field: sum_l grad Psi(n x - l) h(l)
+        if constexpr (PT > 0) {
+            constexpr int NAB = PT * PT;
+            R wz[PT], dz[PT];
+            int oz[PT];
+#pragma unroll
+            for (int c = 0; c < PT; ++c) {
+                wz[c] = wts[warp][2][c];
+                dz[c] = grad ? dwts[warp][2][c] : (R)0;
+                oz[c] = lix[warp][2][c];
+            }
+#pragma unroll
+            for (int r = 0; r < (NAB + 31) / 32; ++r) {
+                const int ab = lane + 32 * r;
+                if (NAB % 32 != 0 && ab >= NAB) break;
+                const int b = ab / PT, a = ab - b * PT;
+                const int rowo = lix[warp][1][b] * n + lix[warp][0][a];
+                const R wx = wts[warp][0][a], wy = wts[warp][1][b];
+                if (grad) {   // one field: sum_l grad Psi(n x - l) h(l)
+                    R hv[PT];
+#pragma unroll
+                    for (int c = 0; c < PT; ++c) {
+                        const int off = oz[c] + rowo;
+                        hv[c] = ENUF_GUARD(g.check, (size_t)off < n3, 5) ? h0[off] : (R)0;
+                    }
+                    R s0 = 0, s1 = 0;
+#pragma unroll
+                    for (int c = 0; c < PT; ++c) {
+                        s0 = fma(wz[c], hv[c], s0);
+                        s1 = fma(dz[c], hv[c], s1);
+                    }
+                    ax = fma(dwts[warp][0][a] * wy, s0, ax);
+                    ay = fma(wx * dwts[warp][1][b], s0, ay);
+                    az = fma(wx * wy, s1, az);
+                } else {
+                    R h0v[PT], h1v[PT], h2v[PT];
+#pragma unroll
+                    for (int c = 0; c < PT; ++c) {
+                        int off = oz[c] + rowo;
+                        if (!ENUF_GUARD(g.check, (size_t)off < n3, 5)) off = 0;
+                        h0v[c] = h0[off];
+                        h1v[c] = h1[off];
+                        h2v[c] = h2[off];
+                    }
+                    R s0 = 0, s1 = 0, s2 = 0;
+#pragma unroll
+                    for (int c = 0; c < PT; ++c) {
+                        s0 = fma(wz[c], h0v[c], s0);
+                        s1 = fma(wz[c], h1v[c], s1);
+                        s2 = fma(wz[c], h2v[c], s2);
+                    }
+                    const R wab = wx * wy;
+                    ax = fma(wab, s0, ax);
+                    ay = fma(wab, s1, ay);
+                    az = fma(wab, s2, az);
+                }
+            }
+        } else if (grad) {   // one field: sum_l grad Psi(n x - l) h(l)
             for (int ab = lane; ab < P2 * P2; ab += 32) {
                 const int b = (int)(((float)ab + 0.5f) * iP2);
                 const int a = ab - b * P2;
@@ -1520,14 +1714,14 @@ __device__ __forceinline__ void k_gather_body(Geo g, const int* __restrict__ tst
     if (tot.Edev) totals_if_last(g, tot, blk.n);
 }
 
-template <typename R>
+template <typename R, int PT = 0>
 __global__ void __launch_bounds__(kGatherThreads) k_gather(Geo g, const int* __restrict__ tstart,
                                                            const typename V4<R>::T* __restrict__ sq,
                                                            const typename V4<R>::T* __restrict__ sw,
                                                            const int* __restrict__ sb, const R* __restrict__ wb,
                                                            const R* __restrict__ h, R* __restrict__ F,
                                                            TotalsArgs tot) {
-    k_gather_body<R>(g, tstart, sq, sw, sb, wb, h, F, tot, Blk{(int)blockIdx.x, (int)gridDim.x});
+    k_gather_body<R, PT>(g, tstart, sq, sw, sb, wb, h, F, tot, Blk{(int)blockIdx.x, (int)gridDim.x});
 }
 
 // ---------------------------------------------------------------------------

@@ -265,6 +265,50 @@ def test_fp32_spread_forms_parity(enuf, name, form):
     plan.close()
 
 
+# the scatter spreading form (spread = 4): p = 4, regions of 2^3 tiles for
+# T = 8, 10, 12 and of one tile for T = 16, 20, 24; (M, T), n = 2M
+SC_CASES = {"n128_T8_E16": (64, 8), "n160_T10_E20": (80, 10), "n144_T12_E24": (72, 12),
+            "n128_T16_E16": (64, 16), "n160_T20_E20": (80, 20), "n144_T24_E24": (72, 24)}
+
+
+def _sc_inputs(layout, L, seed):
+    """uniform: 3000 beads, 1200 charged; clustered: 1500 of the charged beads
+    packed into a cube of edge L/5 across the periodic corner (bins of tens of
+    beads, several 32-bead chunks each, many atomics on the same points);
+    sparse: 7 charged beads (most regions receive none)."""
+    rng = np.random.default_rng(seed)
+    if layout == "sparse":
+        pos = rng.uniform(0.0, L, (400, 3))
+        q = np.zeros(400)
+        q[:7] = [1.0, -1.0, 2.0, -2.0, 1.0, -0.5, -0.5]
+        return pos, q
+    n, nq = (3000, 1200) if layout == "uniform" else (3000, 2000)
+    pos = rng.uniform(0.0, L, (n, 3))
+    if layout == "clustered":
+        pos[:1500] = np.mod(rng.uniform(-0.1 * L, 0.1 * L, (1500, 3)), L)
+    q = np.zeros(n)
+    q[:nq] = np.where(np.arange(nq) % 2 == 0, 1.0, -1.0)
+    return pos, q
+
+
+@pytest.mark.parametrize("name", list(SC_CASES))
+@pytest.mark.parametrize("layout", ["uniform", "clustered", "sparse"])
+def test_fp32_scatter_spread_parity(enuf, name, layout):
+    """The scatter form's grid against the oracle's spread grid, and the
+    forces and energies of the evaluation on it, for every region edge."""
+    M, T = SC_CASES[name]
+    L = 0.2 * M
+    P = dict(L=L, alpha=1.0, r_cut=3.0, beta=4.0, kappa=1.0, M=M, p=4, tile=T, spread=4)
+    pos, q = _inputs("fp32", *_sc_inputs(layout, L, 7 + M + T))
+    plan, F, E, Wv = _gpu(enuf, "fp32", P, pos, q)
+    assert plan.info.spread == 4 and plan.info.tile == T
+    grid = plan.debug_buffer(enuf.ENUF_BUF_GRID).astype(np.float64)
+    _, _, g_ref, _ = orc.recip_enuf(_oparams(P), pos, q, want_grid=True)
+    assert np.abs(grid - g_ref).max() < TOL["fp32"]["stage"] * np.abs(g_ref).max()
+    _check("fp32", F, E, Wv, Ref(P, pos, q))
+    plan.close()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("name", list(CASES))
 def test_gradient_mode_parity(enuf, name, prec):

@@ -130,3 +130,18 @@ def test_real_space_stencil_limit(enuf):
         _shape(enuf, tile=4, **base)
     assert e.value.status == enuf.ENUF_ERR_UNSUPPORTED
     assert _shape(enuf, tile=8, **base).tile == 8        # 7^3 tiles
+
+
+def test_scatter_spread_admission(enuf):
+    """spread = 4 (the scatter form) is taken where its region rules hold and
+    refused otherwise: p != 4, a region of 2 tiles that does not divide the 9
+    tiles per axis, a grid too small for a unique window offset (n = 32 <
+    2 (16 + 8 + 8)), and FP64."""
+    base = dict(L=19.2, alpha=1.0, r_cut=3.0, beta=4.0, kappa=1.0, M=48, p=4, tile=12, spread=4)
+    assert _shape(enuf, prec="fp32", **base).spread == 4          # n = 96, region 24
+    assert _shape(enuf, prec="fp32", **dict(base, tile=16)).spread == 4   # region of one tile
+    for bad in (dict(p=3), dict(M=54, L=21.6), dict(M=16, L=6.4, tile=8)):
+        with pytest.raises(enuf.EnufError):
+            _shape(enuf, prec="fp32", **dict(base, **bad))
+    with pytest.raises(enuf.EnufError):
+        _shape(enuf, prec="fp64", **base)
