@@ -402,14 +402,15 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
         shape2(n * n / 2, 1, fs.lx, fs.tx, fs.grid_x, budget);
         shape2(n * nc1, 1, fs.ly, fs.ty, gyz, budget);
         fs.grid_y_z = (n + fs.ly - 1) / fs.ly;
-        // the z pass holds nf field lines per line (and ~83 registers a thread):
-        // a smaller budget keeps several CTAs per SM
-        shape2(nc1 * g.K, g.nf, fs.lz, fs.tz, fs.grid_z, 56 * 1024);
+        // the z pass holds one inverse line per line, two with three fields (and
+        // ~83 registers a thread): a smaller budget keeps several CTAs per SM
+        const int zmul = g.nf == 3 ? 2 : 1;
+        shape2(nc1 * g.K, zmul, fs.lz, fs.tz, fs.grid_z, 56 * 1024);
         shape2(g.nf * n * nc1, 1, fs.liy, fs.tiy, fs.grid_iy, budget);
         shape2(g.nf * n * n / 2, 1, fs.lix, fs.tix, fs.grid_ix, budget);
         fs.smem_x = n * csz + fs.lx * per_line;
         fs.smem_y = n * csz + fs.ly * per_line;
-        fs.smem_z = n * csz + g.nf * fs.lz * per_line;
+        fs.smem_z = n * csz + zmul * fs.lz * per_line;
         fs.smem_iy = n * csz + fs.liy * per_line;
         fs.smem_ix = n * csz + fs.lix * per_line;
         fs.smem_xy = (n + (n / 2) * (lsa + lsb)) * csz;
@@ -436,13 +437,15 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
             if (lp >= 2) fx_smem = brick_smem<float>(T, n, n * csz + lp * per_line);
         }
         const bool fx_fits = fx_smem > 0 && fx_smem <= kMaxSmem;
-        // automatic: the tile form (measured faster than forms 2 and 3 at every size
-        // of the electrolyte sweep, 81k to 3M beads)
-        int want = P.spread == 0 ? 1 : P.spread;
         // scatter form: regions of one tile (T = 16, 20, 24) or 2^3 tiles (T = 8, 10, 12)
         const int scE = T >= 16 ? T : 2 * T, scRT = scE / T;
         const bool sc_ok = 2 * P.p == 8 && (scE == 16 || scE == 20 || scE == 24) && g.ntd % scRT == 0 &&
                            g.ntd >= scRT + 2 && n % 4 == 0 && n >= 2 * (scE + T + 2 * P.p);
+        // automatic: the scatter form where it is admitted and the grid has at least
+        // 128 points per edge (measured faster than the tile form from the 192k-bead
+        // electrolyte, n = 128, to 3M; at n = 96 its 64 regions leave most SMs idle);
+        // the tile form otherwise (faster than forms 2 and 3 at every size measured)
+        int want = P.spread == 0 ? ((sc_ok && n >= 128) ? 4 : 1) : P.spread;
         if (want == 4 && !sc_ok)
             return fail(plan, ENUF_ERR_INVALID, "spread = 4 needs p = 4, a tile edge of 8, 10, 12, 16, 20 or 24 "
                                                 "whose region (%d) divides n = %d, and n >= %d",

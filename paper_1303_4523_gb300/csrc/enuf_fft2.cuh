@@ -99,8 +99,11 @@ __global__ void __launch_bounds__(512) k2_fft_y(Geo g, FftPlanDev fp, const type
 }
 
 // z pass: forward z of lines l = (kx, ky); E += w D |F|^2 and W += w D v |F|^2
-// (FP64, Kahan); the nf fields -i k_a D F (gradient mode: D F), built in the
-// inverse transform's loader, inverse z; output spec3[a][z][kx][ky].
+// (FP64, Kahan); the nf fields -i k_a D F (gradient mode: D F), inverse z;
+// output spec3[a][z][kx][ky]. kx and ky are constant along a z line, so the
+// x and y fields are kx G and ky G of one transform G = IFFT_z(-i D F): with
+// nf = 3 a line takes two inverse transforms (G and IFFT_z(-i kz D F)), built
+// in the inverse transform's loader.
 template <typename R>
 __device__ __forceinline__ void k2_fft_z_body(Geo g, FftPlanDev fp, const typename Cx<R>::T* __restrict__ spec2,
                                                const typename Cx<R>::T* __restrict__ twg,
@@ -112,9 +115,10 @@ __device__ __forceinline__ void k2_fft_z_body(Geo g, FftPlanDev fp, const typena
     extern __shared__ unsigned char smraw[];
     const int n = g.n, nc = g.nc, K = g.K, nf = g.nf, lsb = fft2_lsb(n);
     const int NL = (nc + 1) * K;
+    const int ni = nf == 3 ? 2 : 1;                  // inverse transforms per line
     C* tw = reinterpret_cast<C*>(smraw);
-    C* A = tw + n;                                    // [nf LB] phase-A rows
-    C* B = A + nf * LB * fft2_lsa(fp.f1, fp.f2);     // [nf LB][lsb]: forward result, then the fields
+    C* A = tw + n;                                    // [ni LB] phase-A rows
+    C* B = A + ni * LB * fft2_lsa(fp.f1, fp.f2);     // [ni LB][lsb]: forward result, then G (and Gz)
     fft2_twiddles(tw, twg, fp);
     const int l0 = blk.id * LB;
     const int nl = min(LB, NL - l0);
@@ -153,28 +157,26 @@ __device__ __forceinline__ void k2_fft_z_body(Geo g, FftPlanDev fp, const typena
         epart[2 * blk.id] = se;
         epart[2 * blk.id + 1] = sv;
     }
-    // inverse of the nf fields of every line: line a nl + c of the transform
+    // inverse transforms of every line: line b nl + c of the batch (b = 0: G,
+    // or D F in gradient mode; b = 1: Gz)
     fft2_lines<R, true>(
-        A, tw, fp, nf * nl,
+        A, tw, fp, ni * nl,
         [&](int line, int m) {
-            const int a = line >= nl ? (line >= 2 * nl ? 2 : 1) : 0;
-            const int c = line - a * nl;
+            const int b = line >= nl ? 1 : 0;
+            const int c = line - b * nl;
             const int kz = m <= n / 2 ? m : m - n;
             C v;
             v.x = (R)0;
             v.y = (R)0;
             if (kz >= -nc && kz <= nc) {
-                const int l = l0 + c;
-                const R d = tabr[(size_t)l * K + (kz + nc)];
+                const R d = tabr[(size_t)(l0 + c) * K + (kz + nc)];
                 const C f = B[c * lsb + m];
                 if (nf == 1) {
                     v.x = d * f.x;   // D F
                     v.y = d * f.y;
                 } else {
-                    const int kx = qdiv(l, K, rK), ky = (l - kx * K) - nc;
-                    const int ka = a == 0 ? kx : (a == 1 ? ky : kz);
-                    const R s = (R)ka * d;
-                    v.x = s * f.y;   // -i k_a D F
+                    const R s = b == 0 ? d : (R)kz * d;
+                    v.x = s * f.y;   // -i D F, -i kz D F
                     v.y = -s * f.x;
                 }
             }
@@ -188,7 +190,15 @@ __device__ __forceinline__ void k2_fft_z_body(Geo g, FftPlanDev fp, const typena
     for (int idx = threadIdx.x; idx < nf * per; idx += blockDim.x) {
         const int a = qdiv(idx, per, rper), e = idx - a * per;
         const int z = qdiv(e, nl, rnl), c = e - z * nl;
-        spec3[((size_t)a * n + z) * NL + l0 + c] = B[(a * nl + c) * lsb + z];
+        C v = B[((a == 2 ? nl : 0) + c) * lsb + z];
+        if (nf == 3 && a < 2) {   // kx G, ky G
+            const int l = l0 + c;
+            const int kx = qdiv(l, K, rK);
+            const R ka = (R)(a == 0 ? kx : (l - kx * K) - nc);
+            v.x *= ka;
+            v.y *= ka;
+        }
+        spec3[((size_t)a * n + z) * NL + l0 + c] = v;
     }
 }
 

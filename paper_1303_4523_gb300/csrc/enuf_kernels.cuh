@@ -1022,22 +1022,31 @@ __global__ void __launch_bounds__(spread2_threads<SLAB>(T)) k_spread_col(Geo g, 
 // owns a region of RT^3 tiles, edge E = RT T (a template constant), held in
 // shared memory. Its candidates are the charged beads of the (RT + 2)^3 bins
 // around it: a window of 2p <= T taps reaches no farther than the next tile.
-// A warp tests 32 candidates at a time against the region; each bead whose
-// window meets it is then spread by the whole warp: lanes over its (x, y)
-// taps, an unrolled loop over its z taps, each product q w_x w_y w_z added to
-// the region with a shared-memory atomic. Work is spent only on the taps
-// that land in the region; the column form multiplies every column of its
-// tile by every z slot, which at ~100 grid points per charged bead is mostly
-// zeros. The region is written once, rows of E points as 16-byte stores.
+// Warps test 32 candidates at a time against the region and append the beads
+// whose window meets it to a shared list; the list is then spread bead by
+// bead, a warp per bead: lanes over its (x, y) taps, a loop over the z taps
+// inside the region, each product q w_x w_y w_z added to the region. Work is
+// spent only on taps that land in the region (the column form multiplies
+// every column of its tile by every z slot, which at ~100 grid points per
+// charged bead is mostly zeros).
+//
+// The region accumulates in 32-bit fixed point with native integer shared
+// atomics (a float add to shared memory is a compare-and-swap loop): scale
+// S = 2^k with S B <= 2^30, B = sum over the region's beads of |q| w_max^3
+// bounding every point (w_max = the window's peak, psi(0)). Each term is
+// rounded to 1/S: at most B 2^-31 per term, below the float rounding of the
+// larger terms; the region is written once, rows of E points as 16-byte
+// stores, converted back to float.
 // The host admits it when 2p = PT, E is a multiple of T, RT <= 2 divides the
 // tiles per dimension ntd >= RT + 2, n % 4 = 0 and n >= 2 (E + T + PT): a
 // window's offset from the region origin is then unique modulo n.
 // ---------------------------------------------------------------------------
 constexpr int kScThreads = 256;
+constexpr int kScCap = 1024;   // listed beads per round = candidates per round
 // x pitch of the region in shared memory: the 8 x taps x 4 y rows of one
 // update land on 32 distinct banks when the pitch is 8 or 24 modulo 32
 __host__ __device__ constexpr int sc_pitch(int E) { return (E % 32 == 8 || E % 32 == 24) ? E : sc_pitch(E + 4); }
-__host__ __device__ constexpr int sc_smem(int E) { return E * E * sc_pitch(E) * (int)sizeof(float); }
+__host__ __device__ constexpr int sc_smem(int E) { return E * E * sc_pitch(E) * (int)sizeof(int) + kScCap * 16; }
 
 template <int E, int PT>
 __global__ void __launch_bounds__(kScThreads) k_spread_sc(Geo g, const int* __restrict__ tstart,
@@ -1050,15 +1059,18 @@ __global__ void __launch_bounds__(kScThreads) k_spread_sc(Geo g, const int* __re
     constexpr int NR = (PT + BPR - 1) / BPR;   // rounds
     constexpr int NW = kScThreads / 32;
     constexpr unsigned FULL = 0xffffffffu;
-    extern __shared__ __align__(16) float acc[];   // [E][E][EP]
-    __shared__ int nb_start[64], nb_cnt[64], nb_chunk[65];
+    extern __shared__ __align__(16) int acc[];            // [E][E][EP] fixed point
+    int4* items = reinterpret_cast<int4*>(acc + E * E * EP);   // [kScCap] (bead, offsets, q, -)
+    __shared__ int nb_start[64], nb_pre[65];
+    __shared__ int nitems;
+    __shared__ float wsum[NW];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int T = g.T, RT = E / T, nr = g.ntd / RT;
     const int rx = blockIdx.x % nr, ry = (blockIdx.x / nr) % nr, rz = blockIdx.x / (nr * nr);
     const int ox = rx * E, oy = ry * E, oz = rz * E;
-    for (int e = tid; e < E * E * EP / 4; e += kScThreads) reinterpret_cast<float4*>(acc)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int e = tid; e < E * E * EP / 4; e += kScThreads) reinterpret_cast<int4*>(acc)[e] = make_int4(0, 0, 0, 0);
     const int nbd = RT + 2, nbins = nbd * nbd * nbd;   // <= 64
-    if (warp == 0) {   // the bins, their bead ranges and a prefix of their 32-bead chunks
+    if (warp == 0) {   // the bins, their bead ranges and an exclusive prefix of their sizes
         int run = 0;
         for (int k0 = 0; k0 < nbins; k0 += 32) {
             const int k = k0 + lane;
@@ -1072,8 +1084,7 @@ __global__ void __launch_bounds__(kScThreads) k_spread_sc(Geo g, const int* __re
                 st = tstart[t];
                 cnt = tstart[t + 1] - st;
             }
-            const int ch = (cnt + 31) >> 5;
-            int x = ch;
+            int x = cnt;
 #pragma unroll
             for (int of = 1; of < 32; of <<= 1) {
                 const int y = __shfl_up_sync(FULL, x, of);
@@ -1081,72 +1092,129 @@ __global__ void __launch_bounds__(kScThreads) k_spread_sc(Geo g, const int* __re
             }
             if (k < nbins) {
                 nb_start[k] = st;
-                nb_cnt[k] = cnt;
-                nb_chunk[k] = run + x - ch;
+                nb_pre[k] = run + x - cnt;
             }
             run += __shfl_sync(FULL, x, 31);
         }
-        if (lane == 0) nb_chunk[nbins] = run;
+        if (lane == 0) {
+            nb_pre[nbins] = run;
+            nitems = 0;
+        }
     }
     __syncthreads();
     const int p = g.p, n = g.n, hn = n >> 1;
-    const int a = lane % PT, b = lane / PT;
-    const bool lane_on = lane < BPR * PT;
-    const int nchunks = nb_chunk[nbins];
-    for (int h = warp; h < nchunks; h += NW) {
-        // the bin of chunk h: the last k with nb_chunk[k] <= h
-        const unsigned b0 = __ballot_sync(FULL, lane < nbins && nb_chunk[lane] <= h);
-        const unsigned b1 = __ballot_sync(FULL, lane + 32 < nbins && nb_chunk[lane + 32] <= h);
-        const int k = __popc(b0) + __popc(b1) - 1;
-        const int c0 = (h - nb_chunk[k]) * 32;
-        const int j = nb_start[k] + c0 + lane;
-        bool hit = false;
-        int pk = 0;
-        if (c0 + lane < nb_cnt[k]) {
-            const int pb = sb[j];
-            int d0 = (pb & 1023) - p + 1 - ox, d1 = ((pb >> 10) & 1023) - p + 1 - oy, d2 = ((pb >> 20) & 1023) - p + 1 - oz;
-            d0 += d0 < -hn ? n : (d0 >= hn ? -n : 0);
-            d1 += d1 < -hn ? n : (d1 >= hn ? -n : 0);
-            d2 += d2 < -hn ? n : (d2 >= hn ? -n : 0);
-            hit = d0 > -PT && d0 < E && d1 > -PT && d1 < E && d2 > -PT && d2 < E;
-            pk = (d0 + PT) | (d1 + PT) << 8 | (d2 + PT) << 16;   // each in [1, E + PT) < 256
-        }
-        unsigned m = __ballot_sync(FULL, hit);
-        while (m) {   // warp-uniform: one bead at a time
-            const int src = __ffs(m) - 1;
-            m &= m - 1;
-            const int js = __shfl_sync(FULL, j, src);
-            const int ps = __shfl_sync(FULL, pk, src);
-            const int dx = (ps & 255) - PT, dy = ((ps >> 8) & 255) - PT, dz = (ps >> 16) - PT;
-            const float w = lane < 3 * PT ? wb[(size_t)js * (3 * PT) + lane] : 0.f;   // x, y, z taps
-            const float q = sq[js].w;
-            const float wxq = __shfl_sync(FULL, w, a) * q;
-            float wz[PT];
+    const int total = nb_pre[nbins];
+    // Candidates [f0, f1) of the bins' concatenation, 32 per warp step: the beads
+    // whose window meets the region, appended to the list (list) and/or their
+    // |q| summed.
+    auto scan = [&](int f0, int f1, bool list, float& qsum) {
+        for (int fb = f0 + 32 * warp; fb < f1; fb += 32 * NW) {
+            const int f = fb + lane;
+            bool hit = false;
+            int pk = 0, j = 0;
+            if (f < f1) {
+                // its bin: the last k with nb_pre[k] <= f (a non-empty bin)
+                int k = 0;
 #pragma unroll
-            for (int c = 0; c < PT; ++c) wz[c] = __shfl_sync(FULL, w, 2 * PT + c);
+                for (int st = 32; st > 0; st >>= 1)
+                    if (k + st < nbins && nb_pre[k + st] <= f) k += st;
+                j = nb_start[k] + f - nb_pre[k];
+                const int pb = sb[j];
+                int d0 = (pb & 1023) - p + 1 - ox, d1 = ((pb >> 10) & 1023) - p + 1 - oy;
+                int d2 = ((pb >> 20) & 1023) - p + 1 - oz;
+                d0 += d0 < -hn ? n : (d0 >= hn ? -n : 0);
+                d1 += d1 < -hn ? n : (d1 >= hn ? -n : 0);
+                d2 += d2 < -hn ? n : (d2 >= hn ? -n : 0);
+                hit = d0 > -PT && d0 < E && d1 > -PT && d1 < E && d2 > -PT && d2 < E;
+                pk = (d0 + PT) | (d1 + PT) << 8 | (d2 + PT) << 16;   // each in [1, E + PT) < 256
+            }
+            const float qj = hit ? sq[j].w : 0.f;
+            qsum += fabsf(qj);
+            if (list) {
+                const unsigned m = __ballot_sync(FULL, hit);
+                int at = 0;
+                if (lane == 0 && m) at = atomicAdd(&nitems, __popc(m));
+                at = __shfl_sync(FULL, at, 0) + __popc(m & ((1u << lane) - 1u));
+                if (hit) items[at] = make_int4(j, pk, __float_as_int(qj), 0);
+            }
+        }
+    };
+    // Spread the listed beads, q pre-multiplied by the scale S.
+    auto spread = [&](float S) {
+        const int a = lane % PT, b = lane / PT;
+        const bool lane_on = lane < BPR * PT;
+        const int ni = nitems;
+        for (int it = warp; it < ni; it += NW) {
+            const int4 rec = items[it];
+            const int dx = (rec.y & 255) - PT, dy = ((rec.y >> 8) & 255) - PT, dz = (rec.y >> 16) - PT;
+            const float w = lane < 3 * PT ? wb[(size_t)rec.x * (3 * PT) + lane] : 0.f;   // x, y, z taps
+            const float wxq = __shfl_sync(FULL, w, a) * (__int_as_float(rec.z) * S);
             const int x = dx + a;
             const bool vx = lane_on && (unsigned)x < (unsigned)E;
+            float wxy[NR];
+            int i0[NR];
+            bool v[NR];
 #pragma unroll
             for (int r = 0; r < NR; ++r) {
                 const int bb = b + r * BPR;
                 const float wy = __shfl_sync(FULL, w, PT + (bb < PT ? bb : PT - 1));
                 const int y = dy + bb;
-                const bool v = vx && bb < PT && (unsigned)y < (unsigned)E;
-                const float wxy = wxq * wy;
-                const int i0 = (dz * E + y) * EP + x;
-#pragma unroll
-                for (int c = 0; c < PT; ++c)
-                    if (v && (unsigned)(dz + c) < (unsigned)E) atomicAdd(&acc[i0 + c * E * EP], wxy * wz[c]);
+                v[r] = vx && bb < PT && (unsigned)y < (unsigned)E;
+                wxy[r] = wxq * wy;
+                i0[r] = (dz * E + y) * EP + x;
             }
+            const int clo = max(0, -dz), chi = min(PT, E - dz);   // z taps inside the region
+#pragma unroll
+            for (int r = 0; r < NR; ++r) i0[r] += clo * E * EP;
+            for (int c = clo; c < chi; ++c) {
+                const float wzc = __shfl_sync(FULL, w, 2 * PT + c);
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    if (v[r]) atomicAdd(&acc[i0[r]], __float2int_rn(wxy[r] * wzc));
+                    i0[r] += E * EP;
+                }
+            }
+        }
+    };
+    // the scale from the sum of |q| over the region's beads: in the listing pass
+    // when all candidates fit one round, else from a pass of its own
+    const bool one_round = total <= kScCap;
+    float qs = 0.f;
+    scan(0, total, one_round, qs);
+#pragma unroll
+    for (int of = 16; of > 0; of >>= 1) qs += __shfl_xor_sync(FULL, qs, of);
+    if (lane == 0) wsum[warp] = qs;
+    __syncthreads();
+    float B = 0.f;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) B += wsum[w];
+    const float wm = (float)g.wnorm;
+    B *= wm * wm * wm;
+    int ex = 0;
+    frexpf(B, &ex);                                   // B < 2^ex
+    const float S = B > 0.f ? ldexpf(1.f, min(126, 30 - ex)) : 1.f;   // S B < 2^30
+    if (one_round) {
+        spread(S);
+    } else {
+        for (int f0 = 0; f0 < total; f0 += kScCap) {
+            __syncthreads();
+            if (tid == 0) nitems = 0;
+            __syncthreads();
+            float dummy = 0.f;
+            scan(f0, min(total, f0 + kScCap), true, dummy);
+            __syncthreads();
+            spread(S);
         }
     }
     __syncthreads();
-    constexpr int Q = E / 4;   // 16-byte pieces per row
+    const float iS = 1.f / S;   // a power of two: exact
+    constexpr int Q = E / 4;    // 16-byte pieces per row
     for (int e = tid; e < E * E * Q; e += kScThreads) {
         const int row = e / Q, cq = e - row * Q;
         const int z = row / E, y = row - z * E;
-        const float4 v = *reinterpret_cast<const float4*>(acc + (z * E + y) * EP + 4 * cq);
-        *reinterpret_cast<float4*>(grid + ((size_t)(oz + z) * n + (oy + y)) * n + ox + 4 * cq) = v;
+        const int4 v = *reinterpret_cast<const int4*>(acc + (z * E + y) * EP + 4 * cq);
+        *reinterpret_cast<float4*>(grid + ((size_t)(oz + z) * n + (oy + y)) * n + ox + 4 * cq) =
+            make_float4((float)v.x * iS, (float)v.y * iS, (float)v.z * iS, (float)v.w * iS);
     }
 }
 
