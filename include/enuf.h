@@ -95,7 +95,7 @@ typedef struct {
                          2 = Stockham stages, the fewest over 2, 3, 4, 5, 8, and for FP32
                          grids from n = 128 on the composite radices 6, 10, 12, 16, 20
                          when that saves a stage. Same result to rounding. */
-    int    spread;    /* spreading kernel (FP32; FP64 always takes 1): 0 = automatic (1);
+    int    spread;    /* spreading kernel (FP32; FP64 always takes 1): 0 = automatic (below);
                          1 = tile form (one CTA per T^3 tile: column-stationary for
                          T in 8, 10, 12, 16, 20, 24, shared-memory atomics otherwise);
                          2 = footprint form on bricks of whole x rows (or x runs) of
@@ -105,9 +105,12 @@ typedef struct {
                          an even T);
                          4 = scatter form: one CTA per region of T^3 (T >= 16) or 2^3
                          tiles, each bead whose window meets the region spread by a
-                         warp with shared-memory atomics, work on its taps inside the
-                         region only (needs p = 4, the region dividing n and n >= 2
-                         (region + T + 8)). Same result to rounding. */
+                         warp with integer shared-memory atomics in 32-bit fixed point
+                         (scale 2^k with sum over the region's beads of |q| psi(0)^3
+                         below 2^30), work on its taps inside the region only (needs
+                         p = 4, the region dividing n and n >= 2 (region + T + 8)).
+                         Automatic (0): 4 where admitted and n >= 128, else 1.
+                         Same result to rounding. */
     int    pairs;     /* DPD systems: 0 = the DPD pair forces and the real-space pairs in
                          one launch whose blocks take either role, after both cell
                          structures exist (default; measured faster at the 81000-bead

@@ -400,8 +400,8 @@ cudaError_t enqueue_enuf(const Geo& g, const FftShape& fs, const FftPlanDev& fp,
     cudaStreamWaitEvent(s0, evJoin, 0);
     rec(ev, 3, true, s0);
     // with fuse_totals the gather's last block also reduces the energies
-    launch(false, true, gather_kernel<R>(2 * g.p), w.nblk_gather, kGatherThreads, 0, s0, g, (const int*)w.tstart, (const V*)sq,
-           (const V*)sw, (const int*)w.sb, static_cast<const R*>(w.wb), static_cast<const R*>(w.h), F,
+    launch(false, true, gather_kernel<R>(2 * g.p), w.nblk_gather, kGatherThreads, 0, s0, g, (const int*)w.tstart,
+           (const V*)sq, (const V*)sw, (const int*)w.sb, static_cast<const R*>(w.wb), static_cast<const R*>(w.h), F,
            fuse_totals ? totals_args(g, w, false, 1) : no_totals());
     rec(ev, 3, false, s0);
     log->kernels += 1;

@@ -1043,6 +1043,7 @@ __global__ void __launch_bounds__(spread2_threads<SLAB>(T)) k_spread_col(Geo g, 
 // ---------------------------------------------------------------------------
 constexpr int kScThreads = 256;
 constexpr int kScCap = 1024;   // listed beads per round = candidates per round
+
 // x pitch of the region in shared memory: the 8 x taps x 4 y rows of one
 // update land on 32 distinct banks when the pitch is 8 or 24 modulo 32
 __host__ __device__ constexpr int sc_pitch(int E) { return (E % 32 == 8 || E % 32 == 24) ? E : sc_pitch(E + 4); }
@@ -1667,6 +1668,7 @@ __device__ __forceinline__ void k_gather_body(Geo g, const int* __restrict__ tst
         // (ab < 256, so the quotient of ab + 1/2 is 1/32 from an integer)
         if constexpr (PT > 0) {
             constexpr int NAB = PT * PT;
+            constexpr int NRD = (NAB + 31) / 32;   // rounds of lanes over the (x, y) taps
             R wz[PT], dz[PT];
             int oz[PT];
 #pragma unroll
@@ -1675,50 +1677,88 @@ __device__ __forceinline__ void k_gather_body(Geo g, const int* __restrict__ tst
                 dz[c] = grad ? dwts[warp][2][c] : (R)0;
                 oz[c] = lix[warp][2][c];
             }
+            if (!grad && NRD <= 2) {
+                // three fields, at most two rounds: every round's loads issued before
+                // the sums (6 p loads in flight per lane)
+                R hv[NRD][3][PT];
+                bool on[NRD];
 #pragma unroll
-            for (int r = 0; r < (NAB + 31) / 32; ++r) {
-                const int ab = lane + 32 * r;
-                if (NAB % 32 != 0 && ab >= NAB) break;
-                const int b = ab / PT, a = ab - b * PT;
-                const int rowo = lix[warp][1][b] * n + lix[warp][0][a];
-                const R wx = wts[warp][0][a], wy = wts[warp][1][b];
-                if (grad) {   // one field: sum_l grad Psi(n x - l) h(l)
-                    R hv[PT];
-#pragma unroll
-                    for (int c = 0; c < PT; ++c) {
-                        const int off = oz[c] + rowo;
-                        hv[c] = ENUF_GUARD(g.check, (size_t)off < n3, 5) ? h0[off] : (R)0;
-                    }
-                    R s0 = 0, s1 = 0;
-#pragma unroll
-                    for (int c = 0; c < PT; ++c) {
-                        s0 = fma(wz[c], hv[c], s0);
-                        s1 = fma(dz[c], hv[c], s1);
-                    }
-                    ax = fma(dwts[warp][0][a] * wy, s0, ax);
-                    ay = fma(wx * dwts[warp][1][b], s0, ay);
-                    az = fma(wx * wy, s1, az);
-                } else {
-                    R h0v[PT], h1v[PT], h2v[PT];
+                for (int r = 0; r < NRD; ++r) {
+                    const int ab = lane + 32 * r;
+                    on[r] = NAB % 32 == 0 || ab < NAB;
+                    const int b = on[r] ? ab / PT : 0, a = on[r] ? ab - b * PT : 0;
+                    const int rowo = lix[warp][1][b] * n + lix[warp][0][a];
 #pragma unroll
                     for (int c = 0; c < PT; ++c) {
                         int off = oz[c] + rowo;
                         if (!ENUF_GUARD(g.check, (size_t)off < n3, 5)) off = 0;
-                        h0v[c] = h0[off];
-                        h1v[c] = h1[off];
-                        h2v[c] = h2[off];
+                        hv[r][0][c] = on[r] ? h0[off] : (R)0;
+                        hv[r][1][c] = on[r] ? h1[off] : (R)0;
+                        hv[r][2][c] = on[r] ? h2[off] : (R)0;
                     }
+                }
+#pragma unroll
+                for (int r = 0; r < NRD; ++r) {
+                    const int ab = lane + 32 * r;
+                    const int b = on[r] ? ab / PT : 0, a = on[r] ? ab - b * PT : 0;
                     R s0 = 0, s1 = 0, s2 = 0;
 #pragma unroll
                     for (int c = 0; c < PT; ++c) {
-                        s0 = fma(wz[c], h0v[c], s0);
-                        s1 = fma(wz[c], h1v[c], s1);
-                        s2 = fma(wz[c], h2v[c], s2);
+                        s0 = fma(wz[c], hv[r][0][c], s0);
+                        s1 = fma(wz[c], hv[r][1][c], s1);
+                        s2 = fma(wz[c], hv[r][2][c], s2);
                     }
-                    const R wab = wx * wy;
+                    const R wab = on[r] ? wts[warp][0][a] * wts[warp][1][b] : (R)0;
                     ax = fma(wab, s0, ax);
                     ay = fma(wab, s1, ay);
                     az = fma(wab, s2, az);
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < NRD; ++r) {
+                    const int ab = lane + 32 * r;
+                    if (NAB % 32 != 0 && ab >= NAB) break;
+                    const int b = ab / PT, a = ab - b * PT;
+                    const int rowo = lix[warp][1][b] * n + lix[warp][0][a];
+                    const R wx = wts[warp][0][a], wy = wts[warp][1][b];
+                    if (grad) {   // one field: sum_l grad Psi(n x - l) h(l)
+                        R hv[PT];
+#pragma unroll
+                        for (int c = 0; c < PT; ++c) {
+                            const int off = oz[c] + rowo;
+                            hv[c] = ENUF_GUARD(g.check, (size_t)off < n3, 5) ? h0[off] : (R)0;
+                        }
+                        R s0 = 0, s1 = 0;
+#pragma unroll
+                        for (int c = 0; c < PT; ++c) {
+                            s0 = fma(wz[c], hv[c], s0);
+                            s1 = fma(dz[c], hv[c], s1);
+                        }
+                        ax = fma(dwts[warp][0][a] * wy, s0, ax);
+                        ay = fma(wx * dwts[warp][1][b], s0, ay);
+                        az = fma(wx * wy, s1, az);
+                    } else {
+                        R h0v[PT], h1v[PT], h2v[PT];
+#pragma unroll
+                        for (int c = 0; c < PT; ++c) {
+                            int off = oz[c] + rowo;
+                            if (!ENUF_GUARD(g.check, (size_t)off < n3, 5)) off = 0;
+                            h0v[c] = h0[off];
+                            h1v[c] = h1[off];
+                            h2v[c] = h2[off];
+                        }
+                        R s0 = 0, s1 = 0, s2 = 0;
+#pragma unroll
+                        for (int c = 0; c < PT; ++c) {
+                            s0 = fma(wz[c], h0v[c], s0);
+                            s1 = fma(wz[c], h1v[c], s1);
+                            s2 = fma(wz[c], h2v[c], s2);
+                        }
+                        const R wab = wx * wy;
+                        ax = fma(wab, s0, ax);
+                        ay = fma(wab, s1, ay);
+                        az = fma(wab, s2, az);
+                    }
                 }
             }
         } else if (grad) {   // one field: sum_l grad Psi(n x - l) h(l)

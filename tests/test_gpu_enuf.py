@@ -63,7 +63,8 @@ def _gpu(enuf, prec, P, pos, q, n_max=None):
 
 def _oparams(P):
     """Oracle parameters: the GPU-only tiling and FFT-path choices do not change the result."""
-    return orc.EwaldParams(**{k: v for k, v in P.items() if k not in ("tile", "fft_path", "fft_radix", "spread")})
+    return orc.EwaldParams(**{k: v for k, v in P.items()
+                              if k not in ("tile", "fft_path", "fft_radix", "spread", "pairs")})
 
 
 class Ref:
