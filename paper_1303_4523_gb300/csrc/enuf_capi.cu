@@ -399,24 +399,43 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
             grid = (total_lines + lines - 1) / lines;
             threads = std::min(512, std::max(64, ((mult * lines * fmax + 31) / 32) * 32));
         };
-        shape2(n * n / 2, 1, fs.lx, fs.tx, fs.grid_x, budget);
+        // persistent passes (x, inverse y, inverse x): the next group's input (extra
+        // bytes per line) double-buffered in shared memory; ~72 KB keeps three CTAs
+        // per SM, the grid is what stays resident
+        auto pipe_shape = [&](int total_lines, int extra, int& lines, int& threads, int& grid, int& smem) {
+            lines = std::max(1, std::min(64, (72 * 1024 - n * csz - 16) / (per_line + extra)));
+            threads = std::min(512, std::max(64, ((lines * fmax + 31) / 32) * 32));
+            smem = n * csz + lines * (per_line + extra) + 16;   // + alignment of the input buffers
+            const int groups = (total_lines + lines - 1) / lines;
+            const int by_smem = (228 * 1024) / (smem + 1024), by_threads = 2048 / threads;
+            const int by_regs = 65536 / (64 * threads);
+            const int per_sm = std::max(1, std::min(std::min(by_smem, by_threads), std::min(by_regs, 32)));
+            grid = std::min(groups, per_sm * kSMs);
+        };
         shape2(n * nc1, 1, fs.ly, fs.ty, gyz, budget);
         fs.grid_y_z = (n + fs.ly - 1) / fs.ly;
         // the z pass holds one inverse line per line, two with three fields (and
         // ~83 registers a thread): a smaller budget keeps several CTAs per SM
         const int zmul = g.nf == 3 ? 2 : 1;
         shape2(nc1 * g.K, zmul, fs.lz, fs.tz, fs.grid_z, 56 * 1024);
-        shape2(g.nf * n * nc1, 1, fs.liy, fs.tiy, fs.grid_iy, budget);
-        shape2(g.nf * n * n / 2, 1, fs.lix, fs.tix, fs.grid_ix, budget);
-        fs.smem_x = n * csz + fs.lx * per_line;
-        fs.smem_y = n * csz + fs.ly * per_line;
         fs.smem_z = n * csz + zmul * fs.lz * per_line;
+        pipe_shape(n * n / 2, 4 * n * (int)sizeof(float), fs.lx, fs.tx, fs.grid_x, fs.smem_x);
+        // inverse y: one CTA per group (its input lines are contiguous already; the
+        // persistent form measured slower, 123 against 106 us at n = 320)
+        shape2(g.nf * n * nc1, 1, fs.liy, fs.tiy, fs.grid_iy, budget);
         fs.smem_iy = n * csz + fs.liy * per_line;
-        fs.smem_ix = n * csz + fs.lix * per_line;
+        pipe_shape(g.nf * n * n / 2, 4 * nc1 * csz, fs.lix, fs.tix, fs.grid_ix, fs.smem_ix);
+        fs.smem_y = n * csz + fs.ly * per_line;
         fs.smem_xy = (n + (n / 2) * (lsa + lsb)) * csz;
         fs.smem_yx = (n + (n / 2) * lsa + nc1 * lsb) * csz;
         fs.fused = (fs.smem_xy <= 100 * 1024 && P.fft_path == 0) ? 1 : 0;
         fs.composite = 0;
+        // five passes: the z pass persistent as well (lines contiguous in spec2);
+        // the fused plane path keeps one CTA per line group (spec2 plane-major)
+        if (!fs.fused) {
+            pipe_shape(nc1 * g.K, (zmul - 1) * per_line + 2 * n * csz, fs.lz, fs.tz, fs.grid_z, fs.smem_z);
+            fs.tz = std::min(512, std::max(64, ((zmul * fs.lz * fmax + 31) / 32) * 32));
+        }
     }
     // spreading form (FP32): bricks of whole x rows fused with the x pass where the
     // two-factor five-pass FFT runs and the brick fits; footprint bricks into the

@@ -132,11 +132,13 @@ cudaError_t configure_kernels(int max_smem) {
         carve((const void*)k2_fft_x<R>);
         carve((const void*)k2_fft_y<R>);
         carve((const void*)k2_fft_z<R>);
+        carve((const void*)k2_fft_zp<R>);
         carve((const void*)k2_fft_iy<R>);
         carve((const void*)k2_fft_ix<R>);
         set((const void*)k2_fft_x<R>);
         set((const void*)k2_fft_y<R>);
         set((const void*)k2_fft_z<R>);
+        set((const void*)k2_fft_zp<R>);
         set((const void*)k2_fft_iy<R>);
         set((const void*)k2_fft_ix<R>);
         set((const void*)k2_fft_xy<R>);
@@ -277,9 +279,9 @@ void enqueue_fft2(const Geo& g, const FftShape& fs, const FftPlanDev& fp, const 
         }
         launch(pdl, true, k2_fft_y<R>, dim3(g.nc + 1, fs.grid_y_z), fs.ty, fs.smem_y, s0, g, fp,
                static_cast<const C*>(w.spec1), tw, static_cast<C*>(w.spec2), fs.ly);
-        launch(pdl, true, k2_fft_z<R>, fs.grid_z, fs.tz, fs.smem_z, s0, g, fp, static_cast<const C*>(w.spec2), tw,
+        launch(pdl, true, k2_fft_zp<R>, fs.grid_z, fs.tz, fs.smem_z, s0, g, fp, static_cast<const C*>(w.spec2), tw,
                (const double*)w.tab, (const double*)w.tabv, static_cast<const R*>(w.tabr), static_cast<C*>(w.spec3),
-               w.part + w.off_recip, fs.lz, 0);
+               w.part + w.off_recip, fs.lz);
         launch(pdl, true, k2_fft_iy<R>, fs.grid_iy, fs.tiy, fs.smem_iy, s0, g, fp, static_cast<const C*>(w.spec3),
                tw, static_cast<C*>(w.spec4), fs.liy);
         launch(pdl, true, k2_fft_ix<R>, fs.grid_ix, fs.tix, fs.smem_ix, s0, g, fp, static_cast<const C*>(w.spec4),

@@ -11,60 +11,85 @@
 //   k2_fft_ix : inverse C2R along x (two Hermitian rows per complex line)
 //   k2_fft_xy / k2_fft_yx : the x+y and y+x passes of one z-plane in shared
 //               memory (small grids)
-// Phase A of every transform loads its elements straight from global memory
-// (or from the previous transform's shared buffer); phase B writes the
-// natural-order results to a shared buffer, from which the pass writes its
-// output in the layout the next pass reads contiguously.
+// The x, z (five-pass layout) and inverse x passes run persistent CTAs over
+// groups of lines whose input is one contiguous run of memory: the next
+// group's input is copied into shared memory asynchronously (cp.async, double
+// buffered) while the current group is transformed, and phase A reads it from
+// there. The y and inverse y passes and the fused plane kernels load phase A's
+// elements straight from global memory. Phase B writes the natural-order
+// results to a shared buffer, from which the pass writes its output in the
+// layout the next pass reads contiguously.
 #pragma once
 #include "enuf_kernels.cuh"
 
 namespace enuf {
 
+// Persistent CTAs over groups of LP line pairs (2 LP consecutive real rows,
+// one contiguous run of the grid), the next group's rows copied into shared
+// memory asynchronously while the current group is transformed.
 template <typename R>
 __global__ void __launch_bounds__(512) k2_fft_x(Geo g, FftPlanDev fp, const R* __restrict__ grid,
                                                const typename Cx<R>::T* __restrict__ twg,
                                                typename Cx<R>::T* __restrict__ spec1, int LP) {
     pdl_enter();
     using C = typename Cx<R>::T;
-    extern __shared__ unsigned char smraw[];
+    extern __shared__ __align__(16) unsigned char smraw[];
     const int n = g.n, nc = g.nc, nc1 = nc + 1, lsb = fft2_lsb(n);
+    const int npairs = n * n / 2, ngroups = (npairs + LP - 1) / LP, per = 2 * LP * n;
     C* tw = reinterpret_cast<C*>(smraw);
     C* A = tw + n;
     C* B = A + LP * fft2_lsa(fp.f1, fp.f2);
+    R* In = reinterpret_cast<R*>((reinterpret_cast<size_t>(B + LP * lsb) + 15) & ~(size_t)15);   // [2][per]
     fft2_twiddles(tw, twg, fp);
-    const int row0 = blockIdx.x * 2 * LP;   // first real row (z n + y), y even
-    const int nl = min(LP, (n * n - row0) / 2);
-    __syncthreads();
-    const R* src = grid + (size_t)row0 * n;
-    fft2_lines<R, false>(
-        A, tw, fp, nl,
-        [&](int c, int x) {
-            C v;
-            v.x = src[(size_t)(2 * c) * n + x];
-            v.y = src[(size_t)(2 * c + 1) * n + x];
-            return v;
-        },
-        [&](int c, int k, C v) {
-            if (k <= nc || k >= n - nc) B[c * lsb + k] = v;
-        });
-    __syncthreads();
-    // split the two real transforms: A = (Z_k + conj Z_{n-k})/2, B = -i (Z_k - conj Z_{n-k})/2
-    const float rnl = 1.0f / (float)max(nl, 1), rn = 1.0f / (float)n;
-    for (int idx = threadIdx.x; idx < nl * nc1; idx += blockDim.x) {
-        const int k = qdiv(idx, nl, rnl), c = idx - k * nl;
-        const C z = B[c * lsb + k];
-        const C zm = B[c * lsb + (k == 0 ? 0 : n - k)];
-        C a, b;
-        a.x = (R)0.5 * (z.x + zm.x);
-        a.y = (R)0.5 * (z.y - zm.y);
-        b.x = (R)0.5 * (z.y + zm.y);
-        b.y = (R)0.5 * (zm.x - z.x);
-        const int row = row0 + 2 * c;
-        const int zz = qdiv(row, n, rn), y = row - zz * n;
-        C* dst = spec1 + ((size_t)zz * nc1 + k) * n + y;
-        dst[0] = a;
-        dst[1] = b;
+    auto prefetch = [&](int grp, int buf) {
+        const int nl = min(LP, npairs - grp * LP);
+        cp_async_block(In + buf * per, grid + (size_t)grp * per, 2 * nl * n * (int)sizeof(R));
+        cp_async_commit();
+    };
+    int buf = 0;
+    if (blockIdx.x < ngroups) prefetch(blockIdx.x, 0);
+    const float rn = 1.0f / (float)n;
+    for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x, buf ^= 1) {
+        const int nxt = grp + gridDim.x;
+        if (nxt < ngroups) prefetch(nxt, buf ^ 1);
+        else cp_async_commit();
+        cp_async_wait_prior();
+        __syncthreads();
+        const R* src = In + buf * per;
+        const int row0 = grp * 2 * LP;   // first real row (z n + y), y even
+        const int nl = min(LP, npairs - grp * LP);
+        fft2_lines<R, false>(
+            A, tw, fp, nl,
+            [&](int c, int x) {
+                C v;
+                v.x = src[(2 * c) * n + x];
+                v.y = src[(2 * c + 1) * n + x];
+                return v;
+            },
+            [&](int c, int k, C v) {
+                if (k <= nc || k >= n - nc) B[c * lsb + k] = v;
+            });
+        __syncthreads();
+        // split the two real transforms: A = (Z_k + conj Z_{n-k})/2, B = -i (Z_k - conj Z_{n-k})/2
+        const float rnl = 1.0f / (float)max(nl, 1);
+        for (int idx = threadIdx.x; idx < nl * nc1; idx += blockDim.x) {
+            const int k = qdiv(idx, nl, rnl), c = idx - k * nl;
+            const C z = B[c * lsb + k];
+            const C zm = B[c * lsb + (k == 0 ? 0 : n - k)];
+            C a, b;
+            a.x = (R)0.5 * (z.x + zm.x);
+            a.y = (R)0.5 * (z.y - zm.y);
+            b.x = (R)0.5 * (z.y + zm.y);
+            b.y = (R)0.5 * (zm.x - z.x);
+            const int row = row0 + 2 * c;
+            const int zz = qdiv(row, n, rn), y = row - zz * n;
+            C* dst = spec1 + ((size_t)zz * nc1 + k) * n + y;
+            dst[0] = a;
+            dst[1] = b;
+        }
+        __syncthreads();
     }
+    cp_async_wait_all();
 }
 
 // forward y for lines (z, kx): spec1[z][kx][y] -> spec2[kx][ky][z], |ky| <= nc
@@ -104,43 +129,28 @@ __global__ void __launch_bounds__(512) k2_fft_y(Geo g, FftPlanDev fp, const type
 // x and y fields are kx G and ky G of one transform G = IFFT_z(-i D F): with
 // nf = 3 a line takes two inverse transforms (G and IFFT_z(-i kz D F)), built
 // in the inverse transform's loader.
-template <typename R>
-__device__ __forceinline__ void k2_fft_z_body(Geo g, FftPlanDev fp, const typename Cx<R>::T* __restrict__ spec2,
-                                               const typename Cx<R>::T* __restrict__ twg,
-                                               const double* __restrict__ tab, const double* __restrict__ tabv,
-                                               const R* __restrict__ tabr, typename Cx<R>::T* __restrict__ spec3,
-                                               double* __restrict__ epart, int LB, int plane_major, Blk blk) {
-    pdl_enter();
+// The z pass of lines l0 .. l0 + nl - 1 (tw filled, A and B as below): forward
+// transform of the lines (elements from load(c, z)), the energy and virial
+// sums of their kept modes added to se, sv, the inverse transforms, and the
+// fields written to spec3. Contains __syncthreads (call from all threads).
+template <typename R, typename Load>
+__device__ __forceinline__ void k2_z_lines(const Geo& g, const FftPlanDev& fp, const typename Cx<R>::T* tw,
+                                           typename Cx<R>::T* A, typename Cx<R>::T* B, int l0, int nl, Load&& load,
+                                           const double* __restrict__ tab, const double* __restrict__ tabv,
+                                           const R* __restrict__ tabr, typename Cx<R>::T* __restrict__ spec3,
+                                           double& se, double& sv) {
     using C = typename Cx<R>::T;
-    extern __shared__ unsigned char smraw[];
     const int n = g.n, nc = g.nc, K = g.K, nf = g.nf, lsb = fft2_lsb(n);
     const int NL = (nc + 1) * K;
-    const int ni = nf == 3 ? 2 : 1;                  // inverse transforms per line
-    C* tw = reinterpret_cast<C*>(smraw);
-    C* A = tw + n;                                    // [ni LB] phase-A rows
-    C* B = A + ni * LB * fft2_lsa(fp.f1, fp.f2);     // [ni LB][lsb]: forward result, then G (and Gz)
-    fft2_twiddles(tw, twg, fp);
-    const int l0 = blk.id * LB;
-    const int nl = min(LB, NL - l0);
+    const int ni = nf == 3 ? 2 : 1;   // inverse transforms per line
+    fft2_lines<R, false>(A, tw, fp, nl, load, [&](int c, int k, C v) {
+        if (k <= nc || k >= n - nc) B[c * lsb + k] = v;
+    });
     __syncthreads();
-    if (plane_major)   // spec2[z][l]: lines gathered across planes
-        fft2_lines<R, false>(
-            A, tw, fp, nl, [&](int c, int z) { return spec2[(size_t)z * NL + l0 + c]; },
-            [&](int c, int k, C v) {
-                if (k <= nc || k >= n - nc) B[c * lsb + k] = v;
-            });
-    else               // spec2[l][z]: lines contiguous
-        fft2_lines<R, false>(
-            A, tw, fp, nl, [&](int c, int z) { return spec2[(size_t)(l0 + c) * n + z]; },
-            [&](int c, int k, C v) {
-                if (k <= nc || k >= n - nc) B[c * lsb + k] = v;
-            });
-    __syncthreads();
-    // energy and virial of the kept modes (half space kx >= 0, kx > 0 counted twice)
-    const float rK = 1.0f / (float)K;
-    // each thread adds a few modes in plain FP64 (the FP64 units are few); the
+    // energy and virial of the kept modes (half space kx >= 0, kx > 0 counted twice);
+    // each thread adds a few modes in plain FP64 (the FP64 units are few), the
     // compensated summation runs over the blocks' partials in the totals
-    double se = 0.0, sv = 0.0;
+    const float rK = 1.0f / (float)K;
     for (int idx = threadIdx.x; idx < nl * K; idx += blockDim.x) {
         const int c = qdiv(idx, K, rK), kzi = idx - c * K;
         const int l = l0 + c;
@@ -151,11 +161,6 @@ __device__ __forceinline__ void k2_fft_z_body(Geo g, FftPlanDev fp, const typena
         if (kx != 0) a2 += a2;   // the -kx half space
         se = fma(tab[(size_t)l * K + kzi], a2, se);
         sv = fma(tabv[(size_t)l * K + kzi], a2, sv);
-    }
-    block_sum2(se, sv);
-    if (threadIdx.x == 0) {
-        epart[2 * blk.id] = se;
-        epart[2 * blk.id + 1] = sv;
     }
     // inverse transforms of every line: line b nl + c of the batch (b = 0: G,
     // or D F in gradient mode; b = 1: Gz)
@@ -203,12 +208,93 @@ __device__ __forceinline__ void k2_fft_z_body(Geo g, FftPlanDev fp, const typena
 }
 
 template <typename R>
+__device__ __forceinline__ void k2_fft_z_body(Geo g, FftPlanDev fp, const typename Cx<R>::T* __restrict__ spec2,
+                                               const typename Cx<R>::T* __restrict__ twg,
+                                               const double* __restrict__ tab, const double* __restrict__ tabv,
+                                               const R* __restrict__ tabr, typename Cx<R>::T* __restrict__ spec3,
+                                               double* __restrict__ epart, int LB, int plane_major, Blk blk) {
+    pdl_enter();
+    using C = typename Cx<R>::T;
+    extern __shared__ unsigned char smraw[];
+    const int n = g.n, NL = (g.nc + 1) * g.K;
+    const int ni = g.nf == 3 ? 2 : 1;
+    C* tw = reinterpret_cast<C*>(smraw);
+    C* A = tw + n;                                    // [ni LB] phase-A rows
+    C* B = A + ni * LB * fft2_lsa(fp.f1, fp.f2);     // [ni LB][lsb]: forward result, then G (and Gz)
+    fft2_twiddles(tw, twg, fp);
+    const int l0 = blk.id * LB;
+    const int nl = min(LB, NL - l0);
+    __syncthreads();
+    double se = 0.0, sv = 0.0;
+    if (plane_major)   // spec2[z][l]: lines gathered across planes
+        k2_z_lines<R>(g, fp, tw, A, B, l0, nl, [&](int c, int z) { return spec2[(size_t)z * NL + l0 + c]; }, tab,
+                      tabv, tabr, spec3, se, sv);
+    else               // spec2[l][z]: lines contiguous
+        k2_z_lines<R>(g, fp, tw, A, B, l0, nl, [&](int c, int z) { return spec2[(size_t)(l0 + c) * n + z]; }, tab,
+                      tabv, tabr, spec3, se, sv);
+    block_sum2(se, sv);
+    if (threadIdx.x == 0) {
+        epart[2 * blk.id] = se;
+        epart[2 * blk.id + 1] = sv;
+    }
+}
+
+template <typename R>
 __global__ void __launch_bounds__(512) k2_fft_z(Geo g, FftPlanDev fp, const typename Cx<R>::T* __restrict__ spec2,
                                                const typename Cx<R>::T* __restrict__ twg,
                                                const double* __restrict__ tab, const double* __restrict__ tabv,
                                                const R* __restrict__ tabr, typename Cx<R>::T* __restrict__ spec3,
                                                double* __restrict__ epart, int LB, int plane_major) {
     k2_fft_z_body<R>(g, fp, spec2, twg, tab, tabv, tabr, spec3, epart, LB, plane_major, Blk{(int)blockIdx.x, (int)gridDim.x});
+}
+
+// The z pass over lines contiguous in spec2 ([l][z], the five-pass layout) with
+// persistent CTAs: groups of LB lines, the next group's lines copied into
+// shared memory asynchronously while this one is transformed; one energy
+// partial per CTA.
+template <typename R>
+__global__ void __launch_bounds__(512) k2_fft_zp(Geo g, FftPlanDev fp, const typename Cx<R>::T* __restrict__ spec2,
+                                                const typename Cx<R>::T* __restrict__ twg,
+                                                const double* __restrict__ tab, const double* __restrict__ tabv,
+                                                const R* __restrict__ tabr, typename Cx<R>::T* __restrict__ spec3,
+                                                double* __restrict__ epart, int LB) {
+    pdl_enter();
+    using C = typename Cx<R>::T;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int n = g.n, NL = (g.nc + 1) * g.K, lsb = fft2_lsb(n);
+    const int ni = g.nf == 3 ? 2 : 1;
+    const int ngroups = (NL + LB - 1) / LB, per = LB * n;
+    C* tw = reinterpret_cast<C*>(smraw);
+    C* A = tw + n;
+    C* B = A + ni * LB * fft2_lsa(fp.f1, fp.f2);
+    C* In = reinterpret_cast<C*>((reinterpret_cast<size_t>(B + ni * LB * lsb) + 15) & ~(size_t)15);   // [2][per]
+    fft2_twiddles(tw, twg, fp);
+    auto prefetch = [&](int grp, int buf) {
+        const int nl = min(LB, NL - grp * LB);
+        cp_async_block(In + buf * per, spec2 + (size_t)grp * per, nl * n * (int)sizeof(C));
+        cp_async_commit();
+    };
+    int buf = 0;
+    if (blockIdx.x < ngroups) prefetch(blockIdx.x, 0);
+    double se = 0.0, sv = 0.0;
+    for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x, buf ^= 1) {
+        const int nxt = grp + gridDim.x;
+        if (nxt < ngroups) prefetch(nxt, buf ^ 1);
+        else cp_async_commit();
+        cp_async_wait_prior();
+        __syncthreads();
+        const C* Ig = In + buf * per;
+        const int l0 = grp * LB, nl = min(LB, NL - l0);
+        k2_z_lines<R>(g, fp, tw, A, B, l0, nl, [&](int c, int z) { return Ig[c * n + z]; }, tab, tabv, tabr, spec3,
+                      se, sv);
+        __syncthreads();
+    }
+    cp_async_wait_all();
+    block_sum2(se, sv);
+    if (threadIdx.x == 0) {
+        epart[2 * blockIdx.x] = se;
+        epart[2 * blockIdx.x + 1] = sv;
+    }
 }
 
 // inverse y for lines (a, z, kx): K inputs zero-padded to n; output spec4[a][z][y][kx]
@@ -249,63 +335,87 @@ __global__ void __launch_bounds__(512) k2_fft_iy(Geo g, FftPlanDev fp, const typ
     }
 }
 
-// inverse x (C2R, two Hermitian rows per complex line); output h[a][z][y][x]
+// inverse x (C2R, two Hermitian rows per complex line); output h[a][z][y][x].
+// Persistent CTAs over groups of LP line pairs: the 2 LP input rows of a group
+// are one contiguous run of spec4 (2 LP nc1 values, a multiple of 16 bytes at a
+// 16-byte offset), copied into shared memory with asynchronous 16-byte copies
+// one group ahead, so a group's transform runs while the next group's rows are
+// in flight (the pass was bound by the latency of its loads).
 template <typename R>
 __global__ void __launch_bounds__(512) k2_fft_ix(Geo g, FftPlanDev fp, const typename Cx<R>::T* __restrict__ spec4,
                                                 const typename Cx<R>::T* __restrict__ twg, R* __restrict__ h,
                                                 int LP) {
     pdl_enter();
     using C = typename Cx<R>::T;
-    extern __shared__ unsigned char smraw[];
+    extern __shared__ __align__(16) unsigned char smraw[];
     const int n = g.n, nc = g.nc, nc1 = nc + 1, lsb = fft2_lsb(n);
-    const int nrows = g.nf * n * n;
+    const int npairs = g.nf * n * n / 2;
+    const int ngroups = (npairs + LP - 1) / LP;
+    const int per = 2 * LP * nc1;   // input values of a group
     C* tw = reinterpret_cast<C*>(smraw);
     C* A = tw + n;
     C* B = A + LP * fft2_lsa(fp.f1, fp.f2);
+    C* In = reinterpret_cast<C*>((reinterpret_cast<size_t>(B + LP * lsb) + 15) & ~(size_t)15);   // [2][per]
     fft2_twiddles(tw, twg, fp);
-    const int row0 = blockIdx.x * 2 * LP;
-    const int nl = min(LP, (nrows - row0) / 2);
-    __syncthreads();
-    fft2_lines<R, true>(
-        A, tw, fp, nl,
-        [&](int c, int m) {
-            const C* ra = spec4 + (size_t)(row0 + 2 * c) * nc1;
-            const C* rb = ra + nc1;
-            C a, b;
-            a.x = a.y = b.x = b.y = (R)0;
-            if (m == 0) {
-                a.x = ra[0].x;
-                b.x = rb[0].x;
-            } else if (m <= nc) {
-                a = ra[m];
-                b = rb[m];
-            } else if (m >= n - nc) {
-                a = ra[n - m];
-                a.y = -a.y;
-                b = rb[n - m];
-                b.y = -b.y;
-            }
-            C z;
-            z.x = a.x - b.y;   // A + i B
-            z.y = a.y + b.x;
-            return z;
-        },
-        [&](int c, int x, C v) { B[c * lsb + x] = v; });
-    __syncthreads();
-    // two consecutive x per thread (n is even): one 8-byte store on each row
-    const int hn = n / 2;
-    const float rhn = 1.0f / (float)hn;
-    for (int idx = threadIdx.x; idx < nl * hn; idx += blockDim.x) {
-        const int c = qdiv(idx, hn, rhn), x = 2 * (idx - c * hn);
-        const C v0 = B[c * lsb + x], v1 = B[c * lsb + x + 1];
-        typename Cx<R>::T ra, rb;   // (row 2c, row 2c + 1) at x, x + 1
-        ra.x = v0.x;
-        ra.y = v1.x;
-        rb.x = v0.y;
-        rb.y = v1.y;
-        *reinterpret_cast<typename Cx<R>::T*>(h + (size_t)(row0 + 2 * c) * n + x) = ra;
-        *reinterpret_cast<typename Cx<R>::T*>(h + (size_t)(row0 + 2 * c + 1) * n + x) = rb;
+    auto prefetch = [&](int grp, int buf) {
+        const int nl = min(LP, npairs - grp * LP);
+        cp_async_block(In + buf * per, spec4 + (size_t)grp * per, 2 * nl * nc1 * (int)sizeof(C));
+        cp_async_commit();
+    };
+    int buf = 0;
+    if (blockIdx.x < ngroups) prefetch(blockIdx.x, 0);
+    for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x, buf ^= 1) {
+        const int nxt = grp + gridDim.x;
+        if (nxt < ngroups) prefetch(nxt, buf ^ 1);
+        else cp_async_commit();   // an empty group keeps the count of groups in flight
+        cp_async_wait_prior();    // this group's rows have arrived (the next may be in flight)
+        __syncthreads();
+        const C* Ig = In + buf * per;
+        const int row0 = grp * 2 * LP;
+        const int nl = min(LP, npairs - grp * LP);
+        fft2_lines<R, true>(
+            A, tw, fp, nl,
+            [&](int c, int m) {
+                const C* ra = Ig + 2 * c * nc1;
+                const C* rb = ra + nc1;
+                C a, b;
+                a.x = a.y = b.x = b.y = (R)0;
+                if (m == 0) {
+                    a.x = ra[0].x;
+                    b.x = rb[0].x;
+                } else if (m <= nc) {
+                    a = ra[m];
+                    b = rb[m];
+                } else if (m >= n - nc) {
+                    a = ra[n - m];
+                    a.y = -a.y;
+                    b = rb[n - m];
+                    b.y = -b.y;
+                }
+                C z;
+                z.x = a.x - b.y;   // A + i B
+                z.y = a.y + b.x;
+                return z;
+            },
+            [&](int c, int x, C v) { B[c * lsb + x] = v; });
+        __syncthreads();
+        // two consecutive x per thread (n is even): one 8-byte store on each row
+        const int hn = n / 2;
+        const float rhn = 1.0f / (float)hn;
+        for (int idx = threadIdx.x; idx < nl * hn; idx += blockDim.x) {
+            const int c = qdiv(idx, hn, rhn), x = 2 * (idx - c * hn);
+            const C v0 = B[c * lsb + x], v1 = B[c * lsb + x + 1];
+            typename Cx<R>::T ra, rb;   // (row 2c, row 2c + 1) at x, x + 1
+            ra.x = v0.x;
+            ra.y = v1.x;
+            rb.x = v0.y;
+            rb.y = v1.y;
+            *reinterpret_cast<typename Cx<R>::T*>(h + (size_t)(row0 + 2 * c) * n + x) = ra;
+            *reinterpret_cast<typename Cx<R>::T*>(h + (size_t)(row0 + 2 * c + 1) * n + x) = rb;
+        }
+        __syncthreads();   // A, B and this buffer are free for the next group
     }
+    cp_async_wait_all();
 }
 
 // Forward x and y of one z-plane in shared memory (small grids): the n real

@@ -39,6 +39,32 @@ __device__ __forceinline__ int real_as_int(double v) { return (int)__double_as_l
 // next grid launches at completion, with its launch work already done.
 __device__ __forceinline__ void pdl_enter() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// Asynchronous 16-byte global -> shared copies (both addresses 16-byte aligned),
+// grouped by commit; wait_prior waits for all groups but the most recent one.
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gsrc) : "memory");
+}
+// nbytes (a multiple of 8) from global to shared memory by the whole block:
+// 16-byte granules when both ends and the size allow, else 8-byte ones; the
+// caller commits the group
+__device__ __forceinline__ void cp_async_block(void* sdst, const void* gsrc, int nbytes) {
+    char* d = static_cast<char*>(sdst);
+    const char* src = static_cast<const char*>(gsrc);
+    if (((reinterpret_cast<size_t>(d) | reinterpret_cast<size_t>(src) | (size_t)nbytes) & 15) == 0) {
+        for (int e = threadIdx.x; e < nbytes / 16; e += blockDim.x) cp_async16(d + 16 * e, src + 16 * e);
+    } else {
+        for (int e = threadIdx.x; e < nbytes / 8; e += blockDim.x) cp_async8(d + 8 * e, src + 8 * e);
+    }
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // The block a kernel body works on: its index and the number of blocks of
 // its launch for this system. A single-system launch passes (blockIdx.x,
 // gridDim.x); a batched launch over many systems passes the block's index
