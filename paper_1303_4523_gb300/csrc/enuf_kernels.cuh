@@ -605,24 +605,43 @@ __global__ void __launch_bounds__(1024) k_bin_scatter(Geo g, const int* __restri
 
 // Window weights of every sorted charged bead (Eq. 14), computed once and
 // read by the spreading and gathering kernels: wb[s][d][a] = psi(u_sd - l_a)
-// for the 2p taps a of dimension d. One thread per word, all SMs (in FP64 the
-// exponentials run on the FP64 units).
+// for the 2p taps a of dimension d. One thread per (bead, dimension) writes
+// its 2p consecutive weights (16-byte stores when 2p is a multiple of 4 in
+// FP32); all SMs (in FP64 the exponentials run on the FP64 units).
 template <typename R>
 __device__ __forceinline__ void k_bin_weights_body(Geo g, const int* __restrict__ tstart,
                                                     const typename V4<R>::T* __restrict__ sw, R* __restrict__ wb, Blk blk) {
     pdl_enter();
     const int nq = tstart[g.ntiles];
-    const int P2 = 2 * g.p, W = 3 * P2;
-    const float rP2 = 1.0f / (float)P2;
+    const int P2 = 2 * g.p;
     const R rb = (R)g.rb, wn = (R)g.wnorm;
-    const long long tot = (long long)nq * W;
-    for (long long e = (long long)blk.id * blockDim.x + threadIdx.x; e < tot; e += (long long)blk.n * blockDim.x) {
-        const int s = (int)(e / W), r = (int)(e - (long long)s * W);
-        const int d = qdiv(r, P2, rP2), a = r - d * P2;
+    const int tot = 3 * nq;   // (bead, dimension) pairs; nq <= n_max < 2^29
+    for (int e = blk.id * blockDim.x + threadIdx.x; e < tot; e += blk.n * blockDim.x) {
+        const int s = e / 3, d = e - 3 * s;
         const typename V4<R>::T fr = sw[s];
         const R f = d == 0 ? fr.x : (d == 1 ? fr.y : fr.z);
-        const R u = f + (R)(g.p - 1 - a);
-        wb[e] = wn * r_exp(-u * u * rb);
+        R* out = wb + (size_t)e * P2;   // = wb + (s 3 + d) 2p
+        bool done = false;
+        if constexpr (sizeof(R) == 4) {
+            if ((P2 & 3) == 0) {
+                for (int a = 0; a < P2; a += 4) {
+                    float w4[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const R u = f + (R)(g.p - 1 - (a + k));
+                        w4[k] = wn * r_exp(-u * u * rb);
+                    }
+                    *reinterpret_cast<float4*>(out + a) = make_float4(w4[0], w4[1], w4[2], w4[3]);
+                }
+                done = true;
+            }
+        }
+        if (!done) {
+            for (int a = 0; a < P2; ++a) {
+                const R u = f + (R)(g.p - 1 - a);
+                out[a] = wn * r_exp(-u * u * rb);
+            }
+        }
     }
 }
 
@@ -1866,6 +1885,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Geo g, const int* __r
 constexpr int kRealThreads = 256;
 constexpr int kRealCap = 2048;     // staged beads (x, y, z, q)
 constexpr int kRealHalo = 1024;    // halo tiles (stencil up to 9 x 9 x 9 + 1 for the prefix)
+constexpr int kRealRound = 8;      // tiles staged together at most
 // FP64 also stages a float copy of the positions for the cutoff pre-test
 template <typename R> __host__ __device__ constexpr int real_cap() { return sizeof(R) == 8 ? 1536 : kRealCap; }
 template <typename R>
@@ -2015,11 +2035,11 @@ __device__ __forceinline__ void halo_dim(int t, int rs, int ntd, int& lo, int& c
     else { lo = t - rs; cnt = 2 * rs + 1; }
 }
 
-// Beads [c0, c1) of one tile against the nh-tile halo (total beads). STAGED:
-// candidates from the shared-memory copy; else from global memory through
-// the halo prefix.
+// Beads [c0, c1) of one tile against the nh-tile halo (total beads), this
+// warp's share being beads c0 + woff, c0 + woff + NW, ... STAGED: candidates
+// from the shared-memory copy; else from global memory through the halo prefix.
 template <typename R, bool STAGED>
-__device__ __forceinline__ void real_beads(const Geo& g, int c0, int c1, int selfbase, int total, int nh,
+__device__ __forceinline__ void real_beads(const Geo& g, int c0, int c1, int woff, int selfbase, int total, int nh,
                                            const typename V4<R>::T* stg, const float4* stgf, const int* stgslot,
                                            const int* hoff, const int* gst, const typename V4<R>::T* __restrict__ sq,
                                            const typename V4<R>::T* __restrict__ sw, typename V4<R>::T* qu, int* quj,
@@ -2037,7 +2057,7 @@ __device__ __forceinline__ void real_beads(const Geo& g, int c0, int c1, int sel
     const R rc2 = (R)(g.rc * g.rc);
     const R al = (R)g.alpha, c2a = (R)g.c2a, be = (R)g.beta, kap = (R)g.kappa;
     const bool slater = g.beta > 0.0;
-    for (int s = c0 + warp; s < c1; s += NW) {
+    for (int s = c0 + woff; s < c1; s += NW) {
         const V pi = sq[s];
         const float4 pif = make_float4((float)pi.x, (float)pi.y, (float)pi.z, 0.f);
         const int self = selfbase + (s - c0);   // the bead's own index in the halo order
@@ -2171,53 +2191,83 @@ __device__ __forceinline__ void k_real_body(Geo g, const int* __restrict__ tstar
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     V* qu = queue + warp * 64;
     R eacc = 0, wacc = 0;
-    for (int tile = blk.id; tile < g.ntiles; tile += blk.n) {
-        const int tx = tile % g.ntd, ty = (tile / g.ntd) % g.ntd, tz = tile / (g.ntd * g.ntd);
-        int xlo, xc, ylo, yc, zlo, zc;
-        halo_dim(tx, g.rs, g.ntd, xlo, xc);
-        halo_dim(ty, g.rs, g.ntd, ylo, yc);
-        halo_dim(tz, g.rs, g.ntd, zlo, zc);
-        const int nh = xc * yc * zc;   // <= kRealHalo by construction of the plan
-        if (!ENUF_GUARD(g.check, nh <= kRealHalo, 6)) continue;   // uniform over the block
-        // halo tile ranges and their exclusive prefix (block scan, <= 4 per thread)
-        int cnt4[4], sum = 0;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int h = 4 * tid + k;
-            cnt4[k] = 0;
-            if (h < nh) {
-                const int hx = h % xc, hy = (h / xc) % yc, hz = h / (xc * yc);
-                const int ax = (xlo + hx + g.ntd) % g.ntd, ay = (ylo + hy + g.ntd) % g.ntd,
-                          az = (zlo + hz + g.ntd) % g.ntd;
-                const int t = (az * g.ntd + ay) * g.ntd + ax;
-                const int st = tstart[t];
-                gst[h] = st;
-                cnt4[k] = tstart[t + 1] - st;
+    // Rounds of up to kRealRound tiles of this block's sequence whose halos fit
+    // the staging buffer together: each tile's halo is staged into its own
+    // segment, then the warps take the round's beads in turn across the tiles
+    // (a tile holds a few beads at large sizes, fewer than the warps), with no
+    // barrier between tiles. A tile whose halo alone does not fit runs by
+    // itself from global memory.
+    __shared__ int r_c0[kRealRound], r_c1[kRealRound], r_seg[kRealRound], r_self[kRealRound], r_tot[kRealRound];
+    __shared__ int r_cnt, r_used, r_next;
+    int tile = blk.id;
+    while (tile < g.ntiles) {
+        if (tid == 0) {
+            r_cnt = 0;
+            r_used = 0;
+        }
+        __syncthreads();
+        int t = tile;
+        while (t < g.ntiles) {
+            const int tx = t % g.ntd, ty = (t / g.ntd) % g.ntd, tz = t / (g.ntd * g.ntd);
+            int xlo, xc, ylo, yc, zlo, zc;
+            halo_dim(tx, g.rs, g.ntd, xlo, xc);
+            halo_dim(ty, g.rs, g.ntd, ylo, yc);
+            halo_dim(tz, g.rs, g.ntd, zlo, zc);
+            const int nh = xc * yc * zc;   // <= kRealHalo by construction of the plan
+            if (!ENUF_GUARD(g.check, nh <= kRealHalo, 6)) {   // uniform over the block
+                t += blk.n;
+                continue;
             }
-            sum += cnt4[k];
-        }
-        int x = sum;
+            // halo tile ranges and their exclusive prefix (block scan, <= 4 per thread)
+            int cnt4[4], sum = 0;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) wtot[warp] = x;
-        __syncthreads();
-        int run = x - sum;
-        for (int w = 0; w < warp; ++w) run += wtot[w];
-        int total = 0;
-        for (int w = 0; w < NW; ++w) total += wtot[w];
+            for (int k = 0; k < 4; ++k) {
+                const int h = 4 * tid + k;
+                cnt4[k] = 0;
+                if (h < nh) {
+                    const int hx = h % xc, hy = (h / xc) % yc, hz = h / (xc * yc);
+                    const int ax = (xlo + hx + g.ntd) % g.ntd, ay = (ylo + hy + g.ntd) % g.ntd,
+                              az = (zlo + hz + g.ntd) % g.ntd;
+                    const int tt = (az * g.ntd + ay) * g.ntd + ax;
+                    const int st = tstart[tt];
+                    gst[h] = st;
+                    cnt4[k] = tstart[tt + 1] - st;
+                }
+                sum += cnt4[k];
+            }
+            int x = sum;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int h = 4 * tid + k;
-            if (h < nh) hoff[h] = run;
-            run += cnt4[k];
-        }
-        if (tid == 0) hoff[nh] = total;
-        __syncthreads();
-        const bool staged = total <= CAP;
-        if (staged) {
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (lane == 31) wtot[warp] = x;
+            __syncthreads();
+            int run = x - sum;
+            for (int w = 0; w < warp; ++w) run += wtot[w];
+            int total = 0;
+            for (int w = 0; w < NW; ++w) total += wtot[w];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int h = 4 * tid + k;
+                if (h < nh) hoff[h] = run;
+                run += cnt4[k];
+            }
+            if (tid == 0) hoff[nh] = total;
+            __syncthreads();
+            const int used = r_used, cnt = r_cnt;
+            const int c0 = tstart[t], c1 = tstart[t + 1];
+            const int hc = (((tz - zlo + g.ntd) % g.ntd) * yc + (ty - ylo + g.ntd) % g.ntd) * xc +
+                           (tx - xlo + g.ntd) % g.ntd;
+            if (total > CAP) {
+                if (cnt == 0) {   // this tile alone, candidates from global memory
+                    real_beads<R, false>(g, c0, c1, warp, hoff[hc], total, nh, stg, stgf, stgslot, hoff, gst, sq,
+                                         sw, qu, quj + warp * 64, F, eacc, wacc);
+                    t += blk.n;
+                }
+                break;   // an oversized halo closes the round
+            }
+            if (used + total > CAP) break;   // staged with the next round
             for (int f = tid; f < total; f += blockDim.x) {
                 int lo = 0, hi = nh;   // last h with hoff[h] <= f
                 while (hi - lo > 1) {
@@ -2226,21 +2276,36 @@ __device__ __forceinline__ void k_real_body(Geo g, const int* __restrict__ tstar
                 }
                 const int gsl = gst[lo] + f - hoff[lo];
                 const V v = sq[gsl];
-                stg[f] = v;
-                if (real_half<R>()) stgslot[f] = gsl;
-                if (sizeof(R) == 8) stgf[f] = make_float4((float)v.x, (float)v.y, (float)v.z, 0.f);
+                stg[used + f] = v;
+                if (real_half<R>()) stgslot[used + f] = gsl;
+                if (sizeof(R) == 8) stgf[used + f] = make_float4((float)v.x, (float)v.y, (float)v.z, 0.f);
             }
+            if (tid == 0) {
+                r_c0[cnt] = c0;
+                r_c1[cnt] = c1;
+                r_seg[cnt] = used;
+                r_self[cnt] = hoff[hc];
+                r_tot[cnt] = total;
+                r_cnt = cnt + 1;
+                r_used = used + total;
+            }
+            __syncthreads();   // hoff, gst and the counters are read again for the next tile
+            t += blk.n;
+            if (r_cnt == kRealRound) break;
         }
+        if (tid == 0) r_next = t;
         __syncthreads();
-        // the central tile's own beads, one warp each
-        const int c0 = tstart[tile], c1 = tstart[tile + 1];
-        const int hc = (((tz - zlo + g.ntd) % g.ntd) * yc + (ty - ylo + g.ntd) % g.ntd) * xc + (tx - xlo + g.ntd) % g.ntd;
-        if (staged)
-            real_beads<R, true>(g, c0, c1, hoff[hc], total, nh, stg, stgf, stgslot, hoff, gst, sq, sw, qu,
-                                quj + warp * 64, F, eacc, wacc);
-        else
-            real_beads<R, false>(g, c0, c1, hoff[hc], total, nh, stg, stgf, stgslot, hoff, gst, sq, sw, qu,
-                                 quj + warp * 64, F, eacc, wacc);
+        // the round's beads, warps in turn across its tiles
+        const int cnt = r_cnt;
+        int before = 0;
+        for (int k = 0; k < cnt; ++k) {
+            const int c0 = r_c0[k], c1 = r_c1[k], seg = r_seg[k];
+            const int woff = ((warp - before) % NW + NW) % NW;
+            real_beads<R, true>(g, c0, c1, woff, r_self[k], r_tot[k], 0, stg + seg, stgf + seg, stgslot + seg, hoff,
+                                gst, sq, sw, qu, quj + warp * 64, F, eacc, wacc);
+            before += c1 - c0;
+        }
+        tile = r_next;
         __syncthreads();
     }
     double e = (double)eacc, w = (double)wacc;
