@@ -331,8 +331,18 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
             return fail(plan, ENUF_ERR_UNSUPPORTED, "real-space stencil of %d^3 tiles too large (r_cut/tile)", hs);
     }
     // binning blocks: the count kernel holds a chunk-sized list plus the tile
-    // histogram in shared memory (<= 200 KB)
-    g.chunk = std::min(16384, std::max(2048, (n_max + 63) / 64));
+    // histogram in shared memory (<= kBinSmem), one block per SM: chunks of at
+    // least 2048 beads, as few whole waves of kSMs blocks as the list allows
+    // (a partial second wave doubled the kernel's time at 3M beads)
+    {
+        const int room = kBinSmem / 4 - g.ntiles;   // list entries that fit beside the histogram
+        int waves = 1;
+        g.chunk = std::max(2048, (n_max + kSMs - 1) / kSMs);
+        while (g.chunk > room && g.chunk > 2048) {
+            ++waves;
+            g.chunk = std::max(2048, (n_max + waves * kSMs - 1) / (waves * kSMs));
+        }
+    }
     g.nbin = std::max(1, (n_max + g.chunk - 1) / g.chunk);
     // the last binning block walks ntiles x nbin counts: only when that is small
     g.bin_last = (long long)g.ntiles * g.nbin <= 65536 ? 1 : 0;

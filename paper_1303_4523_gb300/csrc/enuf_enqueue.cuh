@@ -93,6 +93,10 @@ cudaError_t configure_kernels(int max_smem) {
         if (r != cudaSuccess) e = r;
     };
     set((const void*)k_bin_count<R>);
+    // the count kernel may hold a whole SM's shared memory (its chunk list and
+    // the tile histogram; see the plan's chunk rule)
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute((const void*)k_bin_count<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBinSmem);
     set((const void*)k_bin_scatter<R>);
     set((const void*)k_spread<R>);
     set((const void*)k_fft_x<R>);
@@ -149,6 +153,9 @@ cudaError_t configure_kernels(int max_smem) {
         set((const void*)k_spread_sc<20, 8>);
         set((const void*)k_spread_sc<24, 8>);
         set((const void*)kb_bin_count<R>);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute((const void*)kb_bin_count<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kBinSmem);
         set((const void*)kb_bin_scatter<R>);
         set((const void*)kb_real<R>);
         set((const void*)kb_spread_col<R, 8>);

@@ -24,6 +24,10 @@ __device__ __forceinline__ bool enuf_guard(unsigned int* word, bool ok, int bit)
 #define ENUF_GUARD(word, cond, bit) true
 #endif
 
+// dynamic shared memory of the binning count kernel at most (its static share
+// is a few words; the part allows 227 KB per CTA)
+constexpr int kBinSmem = 224 * 1024;
+
 struct Geo {
     int n;        // oversampled grid per dimension (sigma_s * M)
     int nc;       // kept modes per side, |k_t| <= nc
