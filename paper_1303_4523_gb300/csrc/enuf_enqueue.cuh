@@ -434,10 +434,17 @@ cudaError_t enqueue_dpd_forces(const Work& w, const DpdDev& d, cudaStream_t s, E
     // the cell count also zeroes F, which the pair kernel adds into
     launch(false, false, k_cell_count<R>, blocks, 256, 0, s, d.N, d.ncd, d.L, d.cinv, d.xmaxf, static_cast<const R*>(d.pos),
            d.ckey, d.ccount, static_cast<R*>(d.F));
-    launch(pdl, false, k_scan, 1, 1024, 0, s, d.ccount, d.cstart, d.ncells, d.ccur, 1);
+    // the cell starts (and the scatter cursors): several CTAs without a
+    // wait for up to kScanMbMax cells, else one CTA; k_cell_scatter then
+    // clears the counts
+    if (d.ncells <= kScanMbMax)
+        launch(pdl, false, k_scan_mb, (d.ncells + kScanMbSpan - 1) / kScanMbSpan, 1024, 0, s,
+               (const int*)d.ccount, d.cstart, d.ncells, d.ccur);
+    else
+        launch(pdl, false, k_scan, 1, 1024, 0, s, d.ccount, d.cstart, d.ncells, d.ccur, 0);
     launch(pdl, false, k_cell_scatter<R>, blocks, 256, 0, s, d.N, d.L, d.xmaxf, static_cast<const R*>(d.pos),
            static_cast<const R*>(d.v0), (const int*)d.type, (const int*)d.ckey, d.ccur, static_cast<V*>(d.sp),
-           static_cast<V*>(d.sv));
+           static_cast<V*>(d.sv), d.ccount, d.ncells);
     rec(ev, 7, false, s);
     log->kernels += 3;
     if (!pair_kernel) return cudaGetLastError();   // the pairs run in k_pairs with the real space

@@ -536,6 +536,77 @@ static __global__ void __launch_bounds__(1024) k_scan(int* __restrict__ in, int*
     }
 }
 
+// Exclusive scan of in[0, count) into out[0, count] and aux (out[count] =
+// total) by ceil(count / kScanMbSpan) CTAs of 1024 threads, 4 elements per
+// thread: every CTA adds up all elements before its own span (16-byte loads)
+// and scans its span, so no CTA waits on another (for counts where that
+// redundant prefix read stays small; in must be 16-byte aligned and is not
+// modified).
+constexpr int kScanMbSpan = 4096;
+constexpr int kScanMbMax = 16 * kScanMbSpan;
+static __global__ void __launch_bounds__(1024) k_scan_mb(const int* __restrict__ in, int* __restrict__ out, int count,
+                                                         int* __restrict__ aux) {
+    pdl_enter();
+    __shared__ int wsum[32];
+    __shared__ int spre;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int base = blockIdx.x * kScanMbSpan;
+    int pre = 0;
+    for (int k = tid; k < base / 4; k += 1024) {
+        const int4 x = reinterpret_cast<const int4*>(in)[k];
+        pre += x.x + x.y + x.z + x.w;
+    }
+    pre = __reduce_add_sync(0xffffffffu, pre);
+    if (lane == 0) wsum[w] = pre;
+    __syncthreads();
+    if (w == 0) {
+        const int z = __reduce_add_sync(0xffffffffu, wsum[lane]);
+        if (lane == 0) spre = z;
+    }
+    __syncthreads();
+    const int i0 = base + 4 * tid;
+    int v[4];
+    if (i0 + 4 <= count) {
+        const int4 x = *reinterpret_cast<const int4*>(in + i0);
+        v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = i0 + k < count ? in[i0 + k] : 0;
+    }
+    const int sum = v[0] + v[1] + v[2] + v[3];
+    int x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int z = wsum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, z, o);
+            if (lane >= o) z += y;
+        }
+        wsum[lane] = z;
+    }
+    __syncthreads();
+    int run = spre + (x - sum) + (w > 0 ? wsum[w - 1] : 0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (i0 + k < count) {
+            out[i0 + k] = run;
+            if (aux) aux[i0 + k] = run;
+        }
+        run += v[k];
+    }
+    if (tid == 0 && base + kScanMbSpan >= count) {
+        out[count] = spre + wsum[31];
+        if (aux) aux[count] = spre + wsum[31];
+    }
+}
+
 // Separate tile offsets for large tile x block counts: one thread per tile
 // walks the per-block counts (coalesced) and writes each block's offset inside
 // the tile and the tile total (then k_scan gives the tile starts).
@@ -2350,12 +2421,15 @@ __global__ void k_cell_count(int N, int ncd, double L, double inv, float xmaxf, 
     }
 }
 
+// Also clears the cell counts for the next step's k_cell_count (the scan has
+// read them).
 template <typename R>
 __global__ void k_cell_scatter(int N, double L, float xmaxf, const R* __restrict__ pos, const R* __restrict__ v0,
                                const int* __restrict__ type, const int* __restrict__ ckey,
                                int* __restrict__ ccur, typename V4<R>::T* __restrict__ sp,
-                               typename V4<R>::T* __restrict__ sv) {
+                               typename V4<R>::T* __restrict__ sv, int* __restrict__ ccount, int ncells) {
     pdl_enter();
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) ccount[c] = 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
         const int slot = atomicAdd(&ccur[ckey[i]], 1);
         typename V4<R>::T a, b;
@@ -2427,21 +2501,20 @@ __device__ __forceinline__ R dpd_theta(const PhiloxStep& ps, const DpdDev& d, in
 // DPD pair forces (Eq. 2-7, R_c = 1) + bonds (Sec. 2), added into F (which
 // the caller zeroes): F[i] += F^C + F^D + F^R/sqrt(dt) + F^S. One CTA per B^3
 // block of cells; the beads of the (B+2)^3 halo cells are staged in shared
-// memory with coalesced loads, in halo-cell order. One warp per central cell
-// sweeps the cell's forward half shell (the cell itself with j > i, and the
-// 13 neighbouring cells lexicographically after it), so every pair is
-// evaluated once (Newton's third law; theta_ij is symmetric). In the staged
-// copy the half shell is 5 contiguous runs of slots (own cell + next cell,
-// the row (0,+1,*), the rows (+1,*,*)) and "forward" is just slot_j > slot_i.
-// Each lane takes one candidate j and loops over the cell's beads i; accepted
-// pairs go to a per-warp queue kept across the warp's cells, and the pair arithmetic
-// (Philox draw, weights, dissipation) runs on full warps. -f goes to j with
-// one global reduction per component and pair (executed in L2: shared-memory
-// float adds are compare-and-swap loops on this part, and in FP64 each of
-// their iterations costs an add on the few FP64 units); in FP32 the +f of a
-// run of pairs with the same i is summed in the warp first (queue runs are
-// contiguous in i), then added once, in FP64 it goes per pair too. The
-// harmonic bonds run as one thread per bond into F.
+// memory in halo-cell order (a warp per halo row: the H cells of a row along
+// x are one contiguous run of the staged order). Every pair is evaluated once
+// (Newton's third law; theta_ij is symmetric): a bead's partners are the
+// beads of its forward half shell -- the beads after it in its own cell and
+// the 13 neighbouring cells lexicographically after it, which in the staged
+// copy are 5 contiguous runs of slots. One lane per central bead walks its
+// runs (dpd_beads); the pairs within r = 1 go to a per-warp ring of pairs and
+// the pair arithmetic (Philox draw, weights, dissipation) runs on full warps.
+// The forces go out by global reductions, +f to i and -f to j (executed in
+// L2: shared-memory float adds are compare-and-swap loops on this part, and
+// in FP64 each of their iterations costs an add on the few FP64 units). The
+// harmonic bonds run as one thread per bond into F. A block whose halo holds
+// more beads than the staging capacity sweeps the global cell list instead,
+// one warp per central cell (dpd_cells).
 //
 // The staged copies are unwrapped: the halo cells that lie across a box
 // face are shifted by L, so the plain difference of two staged positions is
@@ -2455,15 +2528,22 @@ constexpr int kDpdThreads = 256;
 // cell blocks against it
 constexpr int kDpdMaxB = 4;      // cells per block edge
 constexpr int kDpdSegU = 14;     // unstaged half shell: single cells
+constexpr int kDpdU = 4;         // bead sweep: candidates per lane and iteration
+constexpr int kDpdQ = 256;       // bead sweep: pair ring per warp (>= 31 + 32 kDpdU, a power of 2)
+static_assert(kDpdQ >= 31 + 32 * kDpdU && (kDpdQ & (kDpdQ - 1)) == 0, "pair ring");
 
 template <typename R>
 constexpr int dpd_smem_bytes() {
     return 2 * kDpdCap * (int)sizeof(typename V4<R>::T) + (sizeof(R) == 8 ? kDpdCap * (int)sizeof(float4) : 0) +
-           (kDpdThreads / 32) * 64 * 8;
+           (kDpdThreads / 32) * kDpdQ * 8;
 }
 
-// One warp-wide batch of up to 32 queued pairs (valid lanes), all lanes call.
-template <typename R, typename V, bool STAGED>
+// One warp-wide batch of up to 32 queued pairs (valid lanes) of the global
+// cell list (wrapped positions: minimum image), all lanes call. The queue
+// holds runs of one i (dpd_cells loops over i inside a candidate chunk): in
+// FP32 the +f of a run is summed in the warp first, then added once; in FP64
+// it goes per pair (the segmented sum would run on the few FP64 units).
+template <typename R, typename V>
 __device__ __forceinline__ void dpd_pairs(const bool valid, const int2 e, const V* __restrict__ P,
                                           const V* __restrict__ Pv, R* __restrict__ F,
                                           const R* __restrict__ atab, int ntypes, R L, R hL, R gam, R srdt,
@@ -2474,11 +2554,9 @@ __device__ __forceinline__ void dpd_pairs(const bool valid, const int2 e, const 
     if (valid) {
         const V pi = P[e.x], vi = Pv[e.x];
         const V pj = P[e.y], vj = Pv[e.y];
-        // staged copies are unwrapped into one frame around the block: the
-        // plain difference is the minimum image for every pair within r = 1
-        const R rx = STAGED ? pi.x - pj.x : min_image(pi.x, pj.x, L, hL);
-        const R ry = STAGED ? pi.y - pj.y : min_image(pi.y, pj.y, L, hL);
-        const R rz = STAGED ? pi.z - pj.z : min_image(pi.z, pj.z, L, hL);
+        const R rx = min_image(pi.x, pj.x, L, hL);
+        const R ry = min_image(pi.y, pj.y, L, hL);
+        const R rz = min_image(pi.z, pj.z, L, hL);
         const R r2 = dist2(rx, ry, rz);
         const R ir = r_rsqrt(r2);
         const R r = r2 * ir;
@@ -2553,19 +2631,19 @@ struct DpdBand {   // float pre-test of the FP64 path: r2f > hi: out; lo0 < r2f 
     float L, hL, lo0, lo, hi;
 };
 
-// All central cells of one block, one warp per cell. STAGED: P/Pv are the
-// shared-memory copies (Pf the float copy of P when R is double) and slots
-// follow hoff; else global sorted arrays and slots follow gst.
-template <typename R, bool STAGED>
+// All central cells of one block on the global cell list (a block whose halo
+// overflows the staging capacity), one warp per cell: lanes over the
+// candidates of the cell's half shell (its own cell, the next along x and the
+// 12 cells of the rows after it, each looked up wrapped), a loop over the
+// cell's beads; positions are wrapped, so pairs take the minimum image.
+template <typename R>
 __device__ __forceinline__ void dpd_cells(const DpdDev& d, int H, int B3, const int* chalo, const int* hoff,
                                           const int* gst, const typename V4<R>::T* __restrict__ P,
-                                          const typename V4<R>::T* __restrict__ Pv, const float4* Pf,
-                                          const DpdBand band, int2* queue, const R* __restrict__ atab,
-                                          uint64_t step, R* __restrict__ F, R& ec) {
+                                          const typename V4<R>::T* __restrict__ Pv, int2* queue,
+                                          const R* __restrict__ atab, uint64_t step, R* __restrict__ F, R& ec) {
     using V = typename V4<R>::T;
     constexpr int NW = kDpdThreads / 32;
-    constexpr bool PRE = STAGED && sizeof(R) == 8;
-    constexpr int nseg = STAGED ? 5 : kDpdSegU;
+    constexpr int nseg = kDpdSegU;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const R L = (R)d.L, hL = (R)(0.5 * d.L);
     const R gam = (R)d.gamma, srdt = (R)(d.sigma * d.rdt);
@@ -2574,84 +2652,51 @@ __device__ __forceinline__ void dpd_cells(const DpdDev& d, int H, int B3, const 
     for (int cc = warp; cc < B3; cc += NW) {
         const int h = chalo[cc];
         if (h < 0) continue;
-        const int cb = STAGED ? hoff[h] : gst[h];
+        const int cb = gst[h];
         const int nself = hoff[h + 1] - hoff[h];
         if (nself == 0) continue;
-        // lane s < nseg: run s of the half shell as (start slot, length)
+        // lane s < nseg: cell s of the half shell as (start slot, length)
         int sst = 0, sln = 0;
         if (lane < nseg) {
-            if (STAGED) {
-                int h0, h1;
-                if (lane == 0) { h0 = h; h1 = h + 2; }
-                else if (lane == 1) { h0 = h + H - 1; h1 = h0 + 3; }
-                else { h0 = h + H * H + (lane - 3) * H - 1; h1 = h0 + 3; }
-                sst = hoff[h0];
-                sln = hoff[h1] - sst;
-            } else {
-                int hc;
-                if (lane == 0) hc = h;
-                else if (lane == 1) hc = h + 1;
-                else if (lane < 5) hc = h + H + (lane - 3);
-                else hc = h + H * H + ((lane - 5) / 3 - 1) * H + ((lane - 5) % 3 - 1);
-                sst = gst[hc];
-                sln = hoff[hc + 1] - hoff[hc];
-            }
+            int hc;
+            if (lane == 0) hc = h;
+            else if (lane == 1) hc = h + 1;
+            else if (lane < 5) hc = h + H + (lane - 3);
+            else hc = h + H * H + ((lane - 5) / 3 - 1) * H + ((lane - 5) % 3 - 1);
+            sst = gst[hc];
+            sln = hoff[hc + 1] - hoff[hc];
         }
-        int x = sln;   // inclusive prefix of the run lengths
+        int x = sln;   // inclusive prefix of the cell counts
 #pragma unroll
         for (int o = 1; o < 16; o <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;
         }
-        const int soff = x - sln;          // run s starts at map position soff
+        const int soff = x - sln;          // cell s starts at map position soff
         const int delta = sst - soff;      // slot = map position + delta
         const int mc = __shfl_sync(0xffffffffu, x, nseg - 1);
-        int bnd[4];                        // staged: run boundaries 1..4 in map positions
-        if constexpr (STAGED) {
-#pragma unroll
-            for (int s = 1; s < nseg; ++s) bnd[s - 1] = __shfl_sync(0xffffffffu, soff, s);
-        }
         // lanes over the map (one candidate j per lane per chunk), loop over the
         // cell's beads i (broadcast loads); queue runs are then runs of one i
         for (int jb = 0; jb < mc; jb += 32) {
             const int jf = jb + lane;
             int s = 0;
-            if constexpr (STAGED) {
-#pragma unroll
-                for (int k = 0; k < nseg - 1; ++k) s += jf >= bnd[k] ? 1 : 0;
-            } else {
-                for (int k = 1; k < nseg; ++k) s += jf >= __shfl_sync(0xffffffffu, soff, k) ? 1 : 0;
-            }
+            for (int k = 1; k < nseg; ++k) s += jf >= __shfl_sync(0xffffffffu, soff, k) ? 1 : 0;
             const int j = jf + __shfl_sync(0xffffffffu, delta, s);
             const bool vj = jf < mc;
             V pj;
-            float4 pjf;
-            if (vj) {
-                pj = P[j];
-                if constexpr (PRE) pjf = Pf[j];
-            }
+            if (vj) pj = P[j];
             for (int ii = 0; ii < nself; ++ii) {
                 const int me = cb + ii;
-                // forward only: staged slots are in halo order, so j > i; unstaged,
-                // only the cell itself (run 0) needs it
+                // forward only within the cell itself (run 0)
                 bool hit = false;
-                if (vj && (STAGED ? j > me : (s != 0 || j > me))) {
-                    if constexpr (PRE) {
-                        const float4 a = Pf[me];
-                        const float r2 = dist2(a.x - pjf.x, a.y - pjf.y, a.z - pjf.z);
-                        if (r2 <= band.hi) hit = (r2 < band.lo && r2 > band.lo0) || dpd_within<R, V, false>(P[me], pj, L, hL);
-                    } else {
-                        hit = dpd_within<R, V, !STAGED>(P[me], pj, L, hL);
-                    }
-                }
+                if (vj && (s != 0 || j > me)) hit = dpd_within<R, V, true>(P[me], pj, L, hL);
                 const unsigned m = __ballot_sync(0xffffffffu, hit);
                 if (hit && ENUF_GUARD(d.check, cnt + __popc(m & ((1u << lane) - 1u)) < 64, 9))
                     queue[cnt + __popc(m & ((1u << lane) - 1u))] = make_int2(me, j);
                 cnt += __popc(m);
                 if (cnt >= 32) {
                     __syncwarp();
-                    dpd_pairs<R, V, STAGED>(true, queue[lane], P, Pv, F, atab, d.ntypes, L, hL, gam, srdt,
-                                            ps, d, ec);
+                    dpd_pairs<R, V>(true, queue[lane], P, Pv, F, atab, d.ntypes, L, hL, gam, srdt, ps, d, ec);
                     __syncwarp();
                     if (lane < cnt - 32) queue[lane] = queue[32 + lane];
                     __syncwarp();
@@ -2661,8 +2706,135 @@ __device__ __forceinline__ void dpd_cells(const DpdDev& d, int H, int B3, const 
         }
     }
     __syncwarp();
+    if (cnt > 0) dpd_pairs<R, V>(lane < cnt, queue[lane], P, Pv, F, atab, d.ntypes, L, hL, gam, srdt, ps, d, ec);
+}
+
+// One warp-wide batch of up to 32 queued pairs (i, j) whose i are mostly
+// distinct (the bead sweep below queues one pair per lane and candidate):
+// +f to i and -f to j, each by one global reduction per component.
+template <typename R, typename V>
+__device__ __forceinline__ void dpd_pairs_red(const bool valid, const int2 e, const V* __restrict__ P,
+                                              const V* __restrict__ Pv, R* __restrict__ F,
+                                              const R* __restrict__ atab, int ntypes, R gam, R srdt,
+                                              const PhiloxStep& ps, const DpdDev& d, R& ec) {
+    if (!valid) return;
+    const V pi = P[e.x], vi = Pv[e.x];
+    const V pj = P[e.y], vj = Pv[e.y];
+    const R rx = pi.x - pj.x, ry = pi.y - pj.y, rz = pi.z - pj.z;   // unwrapped staged frame
+    const R r2 = dist2(rx, ry, rz);
+    const R ir = r_rsqrt(r2);
+    const R w = (R)1 - r2 * ir;
+    const int i = real_as_int(pi.w), j = real_as_int(pj.w);
+    const R a = atab[real_as_int(vi.w) * ntypes + real_as_int(vj.w)];
+    const R vd = (vi.x - vj.x) * rx + (vi.y - vj.y) * ry + (vi.z - vj.z) * rz;   // r_ij . v_ij
+    const R th = dpd_theta<R>(ps, d, i, j);
+    // Eq. 3-5 with w^D = (w^R)^2 = w^2: |F| = w (a - gamma w (r.v)/r + sigma theta/sqrt(dt))
+    const R wi = w * ir;
+    const R fm = wi * fma(-gam * wi, vd, fma(srdt, th, a));
+    const R fx = fm * rx, fy = fm * ry, fz = fm * rz;
+    atomicAdd(&F[3 * i], fx);
+    atomicAdd(&F[3 * i + 1], fy);
+    atomicAdd(&F[3 * i + 2], fz);
+    atomicAdd(&F[3 * j], -fx);
+    atomicAdd(&F[3 * j + 1], -fy);
+    atomicAdd(&F[3 * j + 2], -fz);
+    ec = fma(a * w, w, ec);   // a w^2; halved once per block
+}
+
+// The staged pair sweep with one lane per central bead: lane f of the block's
+// central beads (cpre: prefix of the central cells' counts) walks the forward
+// half shell of its cell -- the rest of its own cell and the next cell along
+// x (run 0: slots after its own), the row (0, +1, -1..1) (run 1) and the
+// three rows (+1, -1..1, -1..1) (runs 2-4), each a contiguous run of staged
+// slots -- one candidate per iteration. A warp tests 32 beads' candidates at
+// once; the pairs within r = 1 go to the warp's queue and are evaluated on
+// full warps. Against one warp per cell (lanes over candidates, a loop over
+// the cell's beads) this has no per-cell prefix of run lengths, no chunk
+// remainders and one test per candidate.
+template <typename R>
+__device__ __forceinline__ void dpd_beads(const DpdDev& d, int H, int B3, const int* chalo, const int* cpre,
+                                          const int* hoff, const typename V4<R>::T* __restrict__ P,
+                                          const typename V4<R>::T* __restrict__ Pv, const float4* Pf,
+                                          const DpdBand band, int2* queue, const R* __restrict__ atab,
+                                          uint64_t step, R* __restrict__ F, R& ec) {
+    using V = typename V4<R>::T;
+    constexpr int NW = kDpdThreads / 32;
+    constexpr bool PRE = sizeof(R) == 8;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const R L = (R)d.L, hL = (R)(0.5 * d.L);
+    const R gam = (R)d.gamma, srdt = (R)(d.sigma * d.rdt);
+    const PhiloxStep ps = philox_step(d, step);
+    const int nc = cpre[B3];
+    int cnt = 0, qh = 0;   // queued pairs of this warp, ring head
+    for (int base = warp * 32; base < nc; base += NW * 32) {
+        const int f = base + lane;
+        const bool own = f < nc;
+        int i = 0, h = 0;
+        if (own) {
+            int lo = 0, hi = B3;   // the central cell holding bead f
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (cpre[mid] <= f) lo = mid; else hi = mid;
+            }
+            h = chalo[lo];
+            i = hoff[h] + f - cpre[lo];
+        }
+        V pi;
+        float4 pif;
+        if (own) {
+            pi = P[i];
+            if constexpr (PRE) pif = Pf[i];
+        }
+        // the five runs one after the other (uniform over the warp); within a
+        // run, lane-local candidate t of the run, as long as the warp's longest
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            int j0 = 0, len = 0;
+            if (own) {
+                const int o = k == 0 ? 0 : (k == 1 ? H - 1 : H * H + (k - 3) * H - 1);
+                j0 = k == 0 ? i + 1 : hoff[h + o];
+                len = hoff[h + o + (k == 0 ? 2 : 3)] - j0;
+            }
+            const int mlen = __reduce_max_sync(0xffffffffu, len);
+            // kDpdU candidates per lane and iteration: their loads and tests
+            // are independent, then one ballot and append each
+            for (int t = 0; t < mlen; t += kDpdU) {
+                bool hit[kDpdU];
+#pragma unroll
+                for (int u = 0; u < kDpdU; ++u) {
+                    hit[u] = false;
+                    if (t + u < len) {
+                        const int j = j0 + t + u;
+                        if constexpr (PRE) {
+                            const float4 b = Pf[j];
+                            const float r2 = dist2(pif.x - b.x, pif.y - b.y, pif.z - b.z);
+                            if (r2 <= band.hi)
+                                hit[u] = (r2 < band.lo && r2 > band.lo0) || dpd_within<R, V, false>(pi, P[j], L, hL);
+                        } else {
+                            hit[u] = dpd_within<R, V, false>(pi, P[j], L, hL);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kDpdU; ++u) {
+                    const unsigned m = __ballot_sync(0xffffffffu, hit[u]);
+                    if (hit[u]) queue[(qh + cnt + __popc(m & ((1u << lane) - 1u))) & (kDpdQ - 1)] = make_int2(i, j0 + t + u);
+                    cnt += __popc(m);
+                }
+                while (cnt >= 32) {
+                    __syncwarp();
+                    dpd_pairs_red<R, V>(true, queue[(qh + lane) & (kDpdQ - 1)], P, Pv, F, atab, d.ntypes, gam, srdt,
+                                        ps, d, ec);
+                    qh += 32;
+                    cnt -= 32;
+                }
+            }
+        }
+    }
+    __syncwarp();
     if (cnt > 0)
-        dpd_pairs<R, V, STAGED>(lane < cnt, queue[lane], P, Pv, F, atab, d.ntypes, L, hL, gam, srdt, ps, d, ec);
+        dpd_pairs_red<R, V>(lane < cnt, queue[(qh + lane) & (kDpdQ - 1)], P, Pv, F, atab, d.ntypes, gam, srdt, ps, d,
+                            ec);
 }
 
 template <typename R>
@@ -2677,14 +2849,15 @@ __device__ __forceinline__ void k_dpd_body(DpdDev d, int B, const typename V4<R>
     V* spos = reinterpret_cast<V*>(smraw);                                  // [kDpdCap]
     V* svel = spos + kDpdCap;                                               // [kDpdCap]
     float4* spf = reinterpret_cast<float4*>(svel + kDpdCap);                // [kDpdCap] (FP64 only)
-    int2* queues = reinterpret_cast<int2*>(spf + (F64 ? kDpdCap : 0));      // [NW][64]
+    int2* queues = reinterpret_cast<int2*>(spf + (F64 ? kDpdCap : 0));      // [NW][kDpdQ]
     constexpr int HMAX = (kDpdMaxB + 2) * (kDpdMaxB + 2) * (kDpdMaxB + 2);
     __shared__ int hoff[HMAX + 1], gst[HMAX];
     __shared__ int chalo[kDpdMaxB * kDpdMaxB * kDpdMaxB];
+    __shared__ int cpre[kDpdMaxB * kDpdMaxB * kDpdMaxB + 1];   // prefix of the central cells' counts
     __shared__ unsigned char hsh[HMAX];   // per halo cell: 2 bits per axis, 1: -L, 2: +L
     const uint64_t step = *stepp;
     const int ncd = d.ncd, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    int2* queue = queues + warp * 64;
+    int2* queue = queues + warp * kDpdQ;
     const int H = B + 2, H3 = H * H * H, B3 = B * B * B;
     if (!ENUF_GUARD(d.check, H3 <= HMAX && B3 <= kDpdMaxB * kDpdMaxB * kDpdMaxB, 8)) return;
     const int nblk = (ncd + B - 1) / B;
@@ -2774,13 +2947,30 @@ __device__ __forceinline__ void k_dpd_body(DpdDev d, int B, const typename V4<R>
         __syncthreads();
         const int total = hoff[H3];
         const bool staged = total <= kDpdCap;
+        if (staged && warp == 0) {   // central cells' bead counts, exclusive prefix (B3 <= 64)
+            const int c0 = 2 * lane, c1 = 2 * lane + 1;
+            const int h0 = c0 < B3 ? chalo[c0] : -1, h1 = c1 < B3 ? chalo[c1] : -1;
+            const int n0 = h0 >= 0 ? hoff[h0 + 1] - hoff[h0] : 0;
+            const int n1 = h1 >= 0 ? hoff[h1 + 1] - hoff[h1] : 0;
+            int x = n0 + n1;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            const int ex = x - n0 - n1;
+            if (c0 < B3) cpre[c0] = ex;
+            if (c1 < B3) cpre[c1] = ex + n0;
+            if (lane == 31) cpre[B3] = x;
+        }
         if (staged) {
-            for (int f = tid; f < total; f += blockDim.x) {
-                int lo = 0, hi = H3;
-                while (hi - lo > 1) {
-                    const int mid = (lo + hi) >> 1;
-                    if (hoff[mid] <= f) lo = mid; else hi = mid;
-                }
+            // a warp per halo row (H cells along x, contiguous in the staged
+            // order); a lane finds its bead's cell among the row's H
+            for (int r = warp; r < H * H; r += kDpdThreads / 32)
+            for (int f = hoff[r * H] + lane; f < hoff[r * H + H]; f += 32) {
+                int lo = r * H;
+#pragma unroll
+                for (int q = 1; q < kDpdMaxB + 2; ++q) lo += (q < H && f >= hoff[r * H + q]) ? 1 : 0;
                 const int j = gst[lo] + f - hoff[lo];
                 V p = sp[j];
                 // the halo is H <= ncd distinct cells: shift the cells across
@@ -2800,9 +2990,9 @@ __device__ __forceinline__ void k_dpd_body(DpdDev d, int B, const typename V4<R>
         }
         __syncthreads();
         if (staged)
-            dpd_cells<R, true>(d, H, B3, chalo, hoff, gst, spos, svel, spf, band, queue, atab, step, F, ec);
+            dpd_beads<R>(d, H, B3, chalo, cpre, hoff, spos, svel, spf, band, queue, atab, step, F, ec);
         else
-            dpd_cells<R, false>(d, H, B3, chalo, hoff, gst, sp, sv, spf, band, queue, atab, step, F, ec);
+            dpd_cells<R>(d, H, B3, chalo, hoff, gst, sp, sv, queue, atab, step, F, ec);
         __syncthreads();
     }
     double e1 = 0.5 * (double)ec, e2 = 0.5 * (double)eb;

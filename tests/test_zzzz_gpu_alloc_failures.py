@@ -146,7 +146,8 @@ def test_batch_sequence_table_allocation(enuf):
         Fk, Ek = _forces(plan, pos[k], q[k])
         plan.close()
         assert _rel(F[k].cpu().numpy().astype(np.float64), Fk.astype(np.float64)) < 1e-6
-        assert np.allclose(np.asarray(E)[k][:4], Ek[:4], rtol=1e-6)
+        # FP32 pair sums of alternating sign: the scale of the self term (as the parity tests)
+        assert np.allclose(np.asarray(E)[k][:4], Ek[:4], rtol=1e-6, atol=1e-6 * abs(Ek[2]))
 
 
 def test_serving_request_fails_alone(enuf):
