@@ -173,6 +173,7 @@ struct enuf_plan_s {
     cudaStream_t stream = nullptr, aux = nullptr;
     bool own_stream = false;
     cudaEvent_t evFork = nullptr, evJoin = nullptr, evA = nullptr;
+    cudaEvent_t evZ = nullptr, evT = nullptr;   // DPD steps: the side stream's energy totals
     Geo g{};
     FftShape fs{};
     FftPlanDev fp{};
@@ -548,14 +549,15 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
     w.nblk_real = std::min(8 * kSMs, g.ntiles);   // one tile per CTA at most
     w.nblk_conv = fs.grid_z;
     w.nblk_dpd = 4 * kSMs;
-    w.nblk_kin = 4 * kSMs;
+    w.nblk_kin = kSMs;   // one block per SM: its FP64 block sum runs on each SM's few FP64 units once
     w.nblk_gather = 4 * kSMs;
     w.off_q = 0;
     w.off_real = w.off_q + 2 * g.nbin;
     w.off_recip = w.off_real + 2 * w.nblk_real;
     w.off_dpd = w.off_recip + 2 * w.nblk_conv;
     w.off_kin = w.off_dpd + 2 * w.nblk_dpd;
-    const int npart = w.off_kin + w.nblk_kin;
+    w.off_pre = w.off_kin + w.nblk_kin;
+    const int npart = w.off_pre + 8;
 
     const size_t nm = (size_t)std::max(n_max, 1);
     const size_t n3 = (size_t)n * n * n;
@@ -730,16 +732,19 @@ enuf_status upload_tables(enuf_plan_t plan) {
 
 // fuse_totals: the gather's last block also reduces the energies (evaluations
 // outside a DPD step, where nothing follows the gather).
+// step: a DPD step, whose energies but the kinetic one are reduced on the
+// side stream beside the gather (plan->evT then orders the closing kick).
 enuf_status enqueue_eval(enuf_plan_t plan, const EvalArgs& a, cudaStream_t s0, cudaStream_t s1,
                          cudaEvent_t evFork, cudaEvent_t evJoin, Events* ev, LaunchLog* log, bool fuse_totals,
-                         const DpdDev* dpd = nullptr) {
+                         const DpdDev* dpd = nullptr, bool step = false) {
     cudaError_t e;
+    cudaEvent_t evZ = step ? plan->evZ : nullptr, evT = step ? plan->evT : nullptr;
     if (plan->prec == ENUF_FP32)
         e = enqueue_enuf<float>(plan->g, plan->fs, plan->fp, plan->w, a, s0, s1, evFork, evJoin, ev, log,
-                                fuse_totals, dpd);
+                                fuse_totals, dpd, evZ, evT);
     else
         e = enqueue_enuf<double>(plan->g, plan->fs, plan->fp, plan->w, a, s0, s1, evFork, evJoin, ev, log,
-                                 fuse_totals, dpd);
+                                 fuse_totals, dpd, evZ, evT);
     if (e != cudaSuccess) return fail(plan, ENUF_ERR_CUDA, "enqueue: %s", cudaGetErrorString(e));
     return ENUF_OK;
 }
@@ -879,7 +884,9 @@ enuf_status enuf_plan(const enuf_params* params, int n_max, void* cuda_stream, e
     if (cudaStreamCreateWithFlags(&plan->aux, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&plan->evFork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&plan->evJoin, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&plan->evA, cudaEventDisableTiming) != cudaSuccess)
+        cudaEventCreateWithFlags(&plan->evA, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&plan->evZ, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&plan->evT, cudaEventDisableTiming) != cudaSuccess)
         return bail(fail(plan, ENUF_ERR_CUDA, "stream/event create failed"));
     for (int i = 0; i < kStageCount; ++i)
         if (cudaEventCreate(&plan->ev.start[i]) != cudaSuccess || cudaEventCreate(&plan->ev.stop[i]) != cudaSuccess)
@@ -1059,6 +1066,8 @@ void enuf_destroy(enuf_plan_t plan) {
     if (plan->evFork) cudaEventDestroy(plan->evFork);
     if (plan->evJoin) cudaEventDestroy(plan->evJoin);
     if (plan->evA) cudaEventDestroy(plan->evA);
+    if (plan->evZ) cudaEventDestroy(plan->evZ);
+    if (plan->evT) cudaEventDestroy(plan->evT);
     if (plan->aux) cudaStreamDestroy(plan->aux);
     if (plan->own_stream && plan->stream) cudaStreamDestroy(plan->stream);
     delete plan;
@@ -1081,7 +1090,10 @@ struct dpd_system_s {
 
 namespace {
 
-enuf_status enqueue_force_eval(dpd_system_t sys, cudaStream_t s0, cudaStream_t s1, Events* ev, LaunchLog* log) {
+// step: inside a step graph (the energies but the kinetic one are then
+// reduced beside the gather; the caller waits on plan->evT before the kick).
+enuf_status enqueue_force_eval(dpd_system_t sys, cudaStream_t s0, cudaStream_t s1, Events* ev, LaunchLog* log,
+                               bool step = false) {
     enuf_plan_t plan = sys->plan;
     if (ev && ev->on) s1 = s0;   // stage events: the branches one after the other
     // DPD pair + bond forces on s1 (F overwritten), after what s0 did so far
@@ -1094,7 +1106,7 @@ enuf_status enqueue_force_eval(dpd_system_t sys, cudaStream_t s0, cudaStream_t s
     if (e != cudaSuccess) return fail(plan, ENUF_ERR_CUDA, "dpd enqueue: %s", cudaGetErrorString(e));
     // electrostatics added into F (real space follows the DPD kernel on s1)
     EvalArgs a{sys->d.N, sys->d.pos, sys->d.q, sys->d.F, false};
-    return enqueue_eval(plan, a, s0, s1, plan->evFork, plan->evJoin, ev, log, false, fuse ? &sys->d : nullptr);
+    return enqueue_eval(plan, a, s0, s1, plan->evFork, plan->evJoin, ev, log, false, fuse ? &sys->d : nullptr, step);
 }
 
 enuf_status initial_force(dpd_system_t sys) {
@@ -1124,12 +1136,15 @@ enuf_status capture_step(dpd_system_t sys) {
     cudaError_t e = plan->prec == ENUF_FP32 ? enqueue_vv_pre<float>(sys->d, plan->stream, &log)
                                             : enqueue_vv_pre<double>(sys->d, plan->stream, &log);
     enuf_status st = e == cudaSuccess ? ENUF_OK : fail(plan, ENUF_ERR_CUDA, "vv_pre: %s", cudaGetErrorString(e));
-    if (st == ENUF_OK) st = enqueue_force_eval(sys, plan->stream, plan->aux, ev, &log);
+    if (st == ENUF_OK) st = enqueue_force_eval(sys, plan->stream, plan->aux, ev, &log, true);
     if (st == ENUF_OK) {
-        // the last block of the half kick reduces the step's energies
-        e = plan->prec == ENUF_FP32
-                ? enqueue_vv_post<float>(plan->g, plan->w, sys->d, plan->stream, &log, !plan->ev.on)
-                : enqueue_vv_post<double>(plan->g, plan->w, sys->d, plan->stream, &log, !plan->ev.on);
+        // the last block of the half kick adds the kinetic energy to the
+        // step's other energies (reduced beside the gather) and forms the totals
+        e = cudaStreamWaitEvent(plan->stream, plan->evT, 0);
+        if (e == cudaSuccess)
+            e = plan->prec == ENUF_FP32
+                    ? enqueue_vv_post<float>(plan->g, plan->w, sys->d, plan->stream, &log, false, true)
+                    : enqueue_vv_post<double>(plan->g, plan->w, sys->d, plan->stream, &log, false, true);
         if (e != cudaSuccess) st = fail(plan, ENUF_ERR_CUDA, "vv_post: %s", cudaGetErrorString(e));
     }
     if (st == ENUF_OK) {

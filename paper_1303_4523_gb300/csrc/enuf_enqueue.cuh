@@ -77,6 +77,7 @@ inline TotalsArgs totals_args(const Geo& g, const Work& w, bool dpd, int ticket)
     t.nkin = dpd ? w.nblk_kin : 0;
     t.Edev = w.Edev;
     t.ticket = w.ticket + ticket;
+    t.pre = nullptr;
     return t;
 }
 inline TotalsArgs no_totals() {
@@ -342,7 +343,8 @@ auto gather_kernel(int taps) {
 template <typename R>
 cudaError_t enqueue_enuf(const Geo& g, const FftShape& fs, const FftPlanDev& fp, const Work& w,
                          const EvalArgs& a, cudaStream_t s0, cudaStream_t s1, cudaEvent_t evFork,
-                         cudaEvent_t evJoin, Events* ev, LaunchLog* log, bool fuse_totals, const DpdDev* dpd) {
+                         cudaEvent_t evJoin, Events* ev, LaunchLog* log, bool fuse_totals, const DpdDev* dpd,
+                         cudaEvent_t evZ, cudaEvent_t evT) {
     using C = typename Cx<R>::T;
     using V = typename V4<R>::T;
     const R* pos = static_cast<const R*>(a.pos);
@@ -406,6 +408,16 @@ cudaError_t enqueue_enuf(const Geo& g, const FftShape& fs, const FftPlanDev& fp,
     }
     rec(ev, 2, false, s0);
 
+    if (evZ && evT) {   // a DPD step: its energies but the kinetic one, beside the gather
+        cudaEventRecord(evZ, s0);
+        cudaStreamWaitEvent(s1, evZ, 0);
+        TotalsArgs t = totals_args(g, w, true, 0);
+        t.pre = w.part + w.off_pre;
+        launch(false, false, k_totals_pre, 8, 256, 0, s1, t);
+        cudaEventRecord(evT, s1);
+        log->kernels += 1;
+    }
+
     cudaStreamWaitEvent(s0, evJoin, 0);
     rec(ev, 3, true, s0);
     // with fuse_totals the gather's last block also reduces the energies
@@ -468,11 +480,15 @@ cudaError_t enqueue_vv_pre(const DpdDev& d, cudaStream_t s, LaunchLog* log) {
     return cudaGetLastError();
 }
 
-// Step 6 of Table 2; the last block also reduces the step's energies.
+// Step 6 of Table 2; the last block also reduces the step's energies (pre:
+// all but the kinetic one were reduced by k_totals_pre).
 template <typename R>
-cudaError_t enqueue_vv_post(const Geo& g, const Work& w, const DpdDev& d, cudaStream_t s, LaunchLog* log, bool pdl) {
+cudaError_t enqueue_vv_post(const Geo& g, const Work& w, const DpdDev& d, cudaStream_t s, LaunchLog* log, bool pdl,
+                            bool pre) {
+    TotalsArgs t = totals_args(g, w, true, 2);
+    if (pre) t.pre = w.part + w.off_pre;
     launch(pdl, true, k_vv_post<R>, w.nblk_kin, 256, 0, s, g, d.N, (R)d.dt, static_cast<R*>(d.vel),
-           static_cast<const R*>(d.F), w.part + w.off_kin, totals_args(g, w, true, 2));
+           static_cast<const R*>(d.F), w.part + w.off_kin, t);
     log->kernels += 1;
     return cudaGetLastError();
 }
@@ -499,13 +515,14 @@ namespace enuf {
     template int spread_smem<R>(const Geo&);                                                                 \
     template cudaError_t enqueue_enuf<R>(const Geo&, const FftShape&, const FftPlanDev&, const Work&,        \
                                          const EvalArgs&, cudaStream_t, cudaStream_t, cudaEvent_t,           \
-                                         cudaEvent_t, Events*, LaunchLog*, bool, const DpdDev*);             \
+                                         cudaEvent_t, Events*, LaunchLog*, bool, const DpdDev*,              \
+                                         cudaEvent_t, cudaEvent_t);                                          \
     template cudaError_t enqueue_totals<R>(const Geo&, const Work&, bool, cudaStream_t, LaunchLog*, bool);   \
     template cudaError_t enqueue_dpd_forces<R>(const Work&, const DpdDev&, cudaStream_t, Events*,            \
                                                LaunchLog*, bool);                                            \
     template cudaError_t enqueue_vv_pre<R>(const DpdDev&, cudaStream_t, LaunchLog*);                         \
     template cudaError_t enqueue_vv_post<R>(const Geo&, const Work&, const DpdDev&, cudaStream_t, LaunchLog*,  \
-                                            bool);                                                           \
+                                            bool, bool);                                                     \
     template cudaError_t enqueue_spread_only<R>(const Geo&, const Work&, const EvalArgs&, void*, cudaStream_t);
 
 }  // namespace enuf

@@ -148,6 +148,7 @@ struct Work {
     // partial-sum segments (offsets into part, in doubles)
     int off_q, off_real, off_recip, off_dpd, off_kin;
     int nblk_real, nblk_conv, nblk_dpd, nblk_kin, nblk_gather;
+    int off_pre;   // 8 doubles: the step's quantities 0-7 reduced beside the gather
 };
 
 // Arguments of one electrostatics evaluation.
@@ -167,6 +168,9 @@ struct TotalsArgs {
     int off_q, nq, off_real, nreal, off_recip, nrecip, off_dpd, ndpd, off_kin, nkin;
     double* Edev;
     int* ticket;
+    // pre (or nullptr): quantities 0-7 already reduced (k_totals_pre); the
+    // closing totals then reduce the kinetic partials only
+    double* pre;
 };
 
 // DPD device state and cell list (one per system).
@@ -239,11 +243,14 @@ template <typename R> cudaError_t configure_kernels(int max_smem);
 template <typename R> int spread_smem(const Geo& g);
 // dpd (a DPD step with fused pair kernels, or nullptr): the real-space launch
 // also runs the DPD pair forces (k_pairs), which enqueue_dpd_forces then leaves out.
+// evZ, evT (DPD steps, or nullptr): after the FFT the side stream reduces the
+// step's energies other than the kinetic one (k_totals_pre, beside the
+// gather) and records evT, on which the closing half kick must wait.
 template <typename R>
 cudaError_t enqueue_enuf(const Geo& g, const FftShape& fs, const FftPlanDev& fp, const Work& w,
                          const EvalArgs& a, cudaStream_t s0, cudaStream_t s1, cudaEvent_t evFork,
                          cudaEvent_t evJoin, Events* ev, LaunchLog* log, bool fuse_totals,
-                         const DpdDev* dpd = nullptr);
+                         const DpdDev* dpd = nullptr, cudaEvent_t evZ = nullptr, cudaEvent_t evT = nullptr);
 template <typename R>
 cudaError_t enqueue_totals(const Geo& g, const Work& w, bool dpd, cudaStream_t s, LaunchLog* log, bool pdl);
 template <typename R>
@@ -252,7 +259,8 @@ cudaError_t enqueue_dpd_forces(const Work& w, const DpdDev& d, cudaStream_t s, E
 template <typename R>
 cudaError_t enqueue_vv_pre(const DpdDev& d, cudaStream_t s, LaunchLog* log);
 template <typename R>
-cudaError_t enqueue_vv_post(const Geo& g, const Work& w, const DpdDev& d, cudaStream_t s, LaunchLog* log, bool pdl);
+cudaError_t enqueue_vv_post(const Geo& g, const Work& w, const DpdDev& d, cudaStream_t s, LaunchLog* log, bool pdl,
+                            bool pre = false);
 template <typename R>
 cudaError_t enqueue_spread_only(const Geo& g, const Work& w, const EvalArgs& a, void* grid_out, cudaStream_t s);
 // Batched launch sequence (FP32): a system qualifies when its plan runs the

@@ -224,35 +224,61 @@ struct Kahan {
     }
 };
 
+// Totals quantity qd (0-8) of the 9 (Sum q, Sum q^2, E_real, W_real, E_recip,
+// W_recip, E_c, E_bond, E_kin): where its per-block partials sit.
+__device__ __forceinline__ void totals_src(const TotalsArgs& t, int qd, int& off, int& cnt, int& stride) {
+    if (qd < 2) { off = t.off_q + qd; cnt = t.nq; stride = 2; }
+    else if (qd < 4) { off = t.off_real + (qd - 2); cnt = t.nreal; stride = 2; }
+    else if (qd < 6) { off = t.off_recip + (qd - 4); cnt = t.nrecip; stride = 2; }
+    else if (qd < 8) { off = t.off_dpd + (qd - 6); cnt = t.ndpd; stride = 2; }
+    else { off = t.off_kin; cnt = t.nkin; stride = 1; }
+}
+
+// Kahan sum, per lane, of the partials i = first, first + step, ... of
+// quantity qd (eight independent loads in flight; partials come from other
+// blocks and kernels: loads bypass L1).
+__device__ __forceinline__ double kahan_lane(const TotalsArgs& t, int qd, int first, int step) {
+    int off, cnt, stride;
+    totals_src(t, qd, off, cnt, stride);
+    Kahan k;
+    for (int i0 = first; i0 < cnt; i0 += 8 * step) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = i0 + step * u;
+            v[u] = i < cnt ? __ldcg(&t.part[off + stride * i]) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) k.add(v[u]);
+    }
+    return k.s;
+}
+
 // Final FP64 totals (Kahan over the per-block partials) by one block of any
-// multiple of 32 threads: warp w reduces the quantities q with q mod (warps)
-// = w among the 9 (Sum q, Sum q^2, E_real, W_real, E_recip, W_recip, E_c,
-// E_bond, E_kin). Partials come from other blocks and kernels: loads bypass L1.
+// multiple of 32 threads: warp w reduces the quantities qd with qd mod (warps)
+// = w among the 9 (with t.pre: quantities 0-7 are read from pre and the
+// warps share the kinetic partials).
 // Edev: [0] E_real [1] E_recip [2] E_self+E_neutral [3] E_elec [4] E_conservative
 //       [5] E_bond [6] E_kinetic [7] virial_elec
 static __device__ void totals_block(const Geo& g, const TotalsArgs& t) {
     __shared__ double vals[9];
+    __shared__ double kin[32];
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int qd = w; qd < 9; qd += nw) {
-        int off, cnt, stride;
-        if (qd < 2) { off = t.off_q + qd; cnt = t.nq; stride = 2; }
-        else if (qd < 4) { off = t.off_real + (qd - 2); cnt = t.nreal; stride = 2; }
-        else if (qd < 6) { off = t.off_recip + (qd - 4); cnt = t.nrecip; stride = 2; }
-        else if (qd < 8) { off = t.off_dpd + (qd - 6); cnt = t.ndpd; stride = 2; }
-        else { off = t.off_kin; cnt = t.nkin; stride = 1; }
-        Kahan k;
-        for (int i0 = l; i0 < cnt; i0 += 32 * 8) {   // eight independent loads in flight
-            double v[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int i = i0 + 32 * u;
-                v[u] = i < cnt ? __ldcg(&t.part[off + stride * i]) : 0.0;
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) k.add(v[u]);
+    if (t.pre) {
+        if (threadIdx.x < 8) vals[threadIdx.x] = __ldcg(&t.pre[threadIdx.x]);
+        const double v = warp_sum(kahan_lane(t, 8, threadIdx.x, blockDim.x));
+        if (l == 0) kin[w] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+            for (int k = 0; k < nw; ++k) s += kin[k];
+            vals[8] = s;
         }
-        const double v = warp_sum(k.s);
-        if (l == 0) vals[qd] = v;
+    } else {
+        for (int qd = w; qd < 9; qd += nw) {
+            const double v = warp_sum(kahan_lane(t, qd, l, 32));
+            if (l == 0) vals[qd] = v;
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -271,6 +297,24 @@ static __device__ void totals_block(const Geo& g, const TotalsArgs& t) {
         Edev[6] = vals[8];
         Edev[7] = vals[3] + g.c_recip * vals[5] + 3.0 * e_neut;
         for (int i = 8; i < 16; ++i) Edev[i] = 0.0;
+    }
+}
+
+// Quantities 0-7 of a DPD step's totals, one block per quantity, launched on
+// the side stream once the pair kernels and the reciprocal (z) pass have
+// written their partials, so that it runs beside the gather; the step's
+// closing totals then add the kinetic partials only (t.pre).
+static __global__ void __launch_bounds__(256) k_totals_pre(TotalsArgs t) {
+    pdl_enter();
+    __shared__ double ws[8];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const double v = warp_sum(kahan_lane(t, blockIdx.x, threadIdx.x, blockDim.x));
+    if (l == 0) ws[w] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += ws[k];
+        t.pre[blockIdx.x] = s;
     }
 }
 
