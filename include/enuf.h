@@ -111,11 +111,13 @@ typedef struct {
                          p = 4, the region dividing n and n >= 2 (region + T + 8)).
                          Automatic (0): 4 where admitted and n >= 128, else 1.
                          Same result to rounding. */
-    int    pairs;     /* DPD systems: 0 = the DPD pair forces and the real-space pairs in
-                         one launch whose blocks take either role, after both cell
-                         structures exist (default; measured faster at the 81000-bead
-                         polyelectrolyte); 1 = two launches, the DPD pairs right after
-                         the cell list. Same result to rounding. */
+    int    pairs;     /* DPD systems: 1 = two launches, the DPD pairs right after the
+                         cell list (before the charged-bead binning is done), then the
+                         real-space pairs; 2 = one launch whose blocks take either role,
+                         after both cell structures exist. Automatic (0): 1 in FP32, 2 in
+                         FP64 (measured at the 81000-bead polyelectrolyte, interleaved:
+                         FP32 152.9 against 155.3 us, FP64 471 against 508 us per step).
+                         Same result to rounding. */
 } enuf_params;
 
 typedef struct enuf_plan_s* enuf_plan_t;
@@ -134,6 +136,7 @@ typedef struct {
     int    fft_two_factor;     /* 1: the two-factor kernels (enuf_params.fft_radix) */
     int    spread;             /* spreading kernel taken (enuf_params.spread: 1 to 4) */
     int    brick_x;            /* x extent of a spreading brick (forms 2 and 3) */
+    int    pairs;              /* DPD pair launches taken (enuf_params.pairs: 1 or 2) */
 } enuf_plan_info;
 
 /* Create a plan for systems of up to n_max beads with the given parameters
@@ -210,8 +213,8 @@ enum { ENUF_STAGE_BIN = 0,      /* charged-bead binning (3 kernels) */
        ENUF_STAGE_FFT = 2,      /* the five FFT passes incl. the fused convolution */
        ENUF_STAGE_GATHER = 3,   /* gather kernel */
        ENUF_STAGE_REAL = 4,     /* real-space electrostatics kernel (in a DPD step with
-                                   enuf_params.pairs = 0: the one launch of both pair sums) */
-       ENUF_STAGE_DPD = 5,      /* DPD pair + bond kernel (pairs = 1 only) */
+                                   one pair launch, pairs = 2: that launch of both pair sums) */
+       ENUF_STAGE_DPD = 5,      /* DPD pair + bond kernel (two pair launches, pairs = 1, only) */
        ENUF_STAGE_ALL = 6,      /* the whole evaluation / DPD step */
        ENUF_STAGE_CELL = 7,     /* all-bead cell list (3 kernels) */
        ENUF_NUM_STAGES = 8 };

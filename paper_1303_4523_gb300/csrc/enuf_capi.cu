@@ -452,7 +452,7 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
     // two-factor five-pass FFT runs and the brick fits; footprint bricks into the
     // grid otherwise from n = 128 on; the tile form below
     if (P.spread < 0 || P.spread > 4) return fail(plan, ENUF_ERR_INVALID, "spread must be 0..4");
-    if (P.pairs != 0 && P.pairs != 1) return fail(plan, ENUF_ERR_INVALID, "pairs must be 0 or 1");
+    if (P.pairs < 0 || P.pairs > 2) return fail(plan, ENUF_ERR_INVALID, "pairs must be 0, 1 or 2");
     fs.spread = 1;
     if (P.prec == ENUF_FP32) {
         const int rsz = (int)sizeof(float);
@@ -908,6 +908,10 @@ enuf_status enuf_plan(const enuf_params* params, int n_max, void* cuda_stream, e
     return ENUF_OK;
 }
 
+// DPD pair launches of a plan: 1 (two launches) or 2 (one launch); automatic:
+// two in FP32, one in FP64 (measured at the 81000-bead polyelectrolyte)
+static int pair_launches(const enuf_params& P) { return P.pairs ? P.pairs : (P.prec == ENUF_FP32 ? 1 : 2); }
+
 static void fill_info(const enuf_plan_s* plan, enuf_plan_info* info) {
     info->M = plan->P.M;
     info->n = plan->g.n;
@@ -920,6 +924,7 @@ static void fill_info(const enuf_plan_s* plan, enuf_plan_info* info) {
     info->fft_two_factor = plan->fp.f1 ? 1 : 0;
     info->spread = plan->fs.spread;
     info->brick_x = plan->fs.spread == 2 || plan->fs.spread == 3 ? plan->fs.brick_x : 0;
+    info->pairs = pair_launches(plan->P);
     if (plan->fp.f1) {
         info->fft_stages = 2;
         for (int i = 0; i < 8; ++i) info->fft_radix[i] = i == 0 ? plan->fp.f1 : (i == 1 ? plan->fp.f2 : 0);
@@ -1099,8 +1104,8 @@ enuf_status enqueue_force_eval(dpd_system_t sys, cudaStream_t s0, cudaStream_t s
     // DPD pair + bond forces on s1 (F overwritten), after what s0 did so far
     CU(cudaEventRecord(plan->evA, s0));
     CU(cudaStreamWaitEvent(s1, plan->evA, 0));
-    // pairs = 0: the DPD pair forces run in the real-space launch (k_pairs)
-    const bool fuse = plan->P.pairs == 0;
+    // one pair launch (pairs = 2): the DPD pair forces run in the real-space launch (k_pairs)
+    const bool fuse = pair_launches(plan->P) == 2;
     cudaError_t e = plan->prec == ENUF_FP32 ? enqueue_dpd_forces<float>(plan->w, sys->d, s1, ev, log, !fuse)
                                             : enqueue_dpd_forces<double>(plan->w, sys->d, s1, ev, log, !fuse);
     if (e != cudaSuccess) return fail(plan, ENUF_ERR_CUDA, "dpd enqueue: %s", cudaGetErrorString(e));

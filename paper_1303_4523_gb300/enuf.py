@@ -45,7 +45,8 @@ class enuf_plan_info(C.Structure):
     _fields_ = [("M", C.c_int), ("n", C.c_int), ("n_c", C.c_int), ("tile", C.c_int),
                 ("n_tiles", C.c_int), ("n_max", C.c_int), ("fft_kernels", C.c_int),
                 ("device_bytes", C.c_size_t), ("fft_stages", C.c_int), ("fft_radix", C.c_int * 8),
-                ("fft_two_factor", C.c_int), ("spread", C.c_int), ("brick_x", C.c_int)]
+                ("fft_two_factor", C.c_int), ("spread", C.c_int), ("brick_x", C.c_int),
+                ("pairs", C.c_int)]
 
 
 class dpd_params(C.Structure):

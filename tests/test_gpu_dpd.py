@@ -31,7 +31,7 @@ def _prep(prec, s):
     return cast(s.pos), cast(s.vel), cast(s.q)
 
 
-def _make(enuf, prec, s, pos, vel, q, dp, pairs=0):
+def _make(enuf, prec, s, pos, vel, q, dp, pairs=0):   # pairs 0: the precision's automatic form
     P = dict(L=s.L, M=s.M, **s.params)
     plan = enuf.Plan(enuf.make_params(prec=prec, pairs=pairs, **P), s.N)
     sysm = enuf.DpdSystem(plan, dp["a"], dp["gamma"], dp["sigma"], dp["dt"], pos, vel, s.types, q, s.bonds,
@@ -59,11 +59,11 @@ def _check_forces(F, R, tol):
     assert _bead_max(F, R) < 100 * tol, _bead_max(F, R)
 
 
-@pytest.mark.parametrize("pairs", [0, 1])
+@pytest.mark.parametrize("pairs", [1, 2])
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 1e-5)])
 def test_initial_force_parity(enuf, prec, tol, pairs):
     """Table 2 steps 3-5 at step 0: DPD C + D + R/sqrt(dt) + bonds + electrostatics
-    (pairs = 0: the DPD and real-space pairs in one launch; 1: two launches)."""
+    (pairs = 1: the DPD and real-space pairs in two launches; 2: one launch)."""
     s = _system()
     dp = W.dpd_params(5)
     pos, vel, q = _prep(prec, s)
@@ -93,7 +93,7 @@ def test_density4_force_parity(enuf, prec, tol):
     plan.close()
 
 
-@pytest.mark.parametrize("pairs", [0, 1])
+@pytest.mark.parametrize("pairs", [1, 2])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_trajectory_parity(enuf, prec, pairs):
     """Three modified velocity-Verlet steps; positions, velocities, forces and
@@ -248,7 +248,7 @@ def test_box_needs_three_cells_per_edge(enuf):
         plan.close()
 
 
-@pytest.mark.parametrize("pairs", [0, 1])
+@pytest.mark.parametrize("pairs", [1, 2])
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 1e-5)])
 def test_full_size_polyelectrolyte_sampled(enuf, prec, tol, pairs):
     """The bench workload (81000 beads, L = 30): initial ENUF-DPD force of 256
