@@ -338,11 +338,10 @@ enuf_status derive(enuf_plan_t plan, const enuf_params& P, int n_max, size_t* by
     {
         const int room = kBinSmem / 4 - g.ntiles;   // list entries that fit beside the histogram
         int waves = 1;
-        g.chunk = std::max(2048, (n_max + kSMs - 1) / kSMs);
-        while (g.chunk > room && g.chunk > 2048) {
-            ++waves;
-            g.chunk = std::max(2048, (n_max + waves * kSMs - 1) / (waves * kSMs));
-        }
+        // chunks are whole groups of 32 beads (the count kernel deals groups to its blocks)
+        auto chunk_for = [&](int w) { return std::max(2048, ((n_max + w * kSMs - 1) / (w * kSMs) + 31) & ~31); };
+        g.chunk = chunk_for(1);
+        while (g.chunk > room && g.chunk > 2048) g.chunk = chunk_for(++waves);
     }
     g.nbin = std::max(1, (n_max + g.chunk - 1) / g.chunk);
     // the last binning block walks ntiles x nbin counts: only when that is small

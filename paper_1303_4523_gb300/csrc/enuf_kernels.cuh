@@ -101,9 +101,22 @@ __device__ __forceinline__ double r_rsqrt(double x) {
 // exact operation sequence of the definition (no fused multiply-add), so the
 // integer decisions (grid base, tile, cell) are reproducible.
 // ---------------------------------------------------------------------------
+// q = floor(x / L) comes from a float quotient (off by at most one for
+// |x| < 2^20 L) corrected in double until 0 <= x - L q < L: the same q and w
+// as an FP64 division would give, without one (an FP64 division is a long
+// sequence on this part's few FP64 units, and DPD positions drift out of the
+// box, so most steps wrap many beads).
 __device__ __forceinline__ double wrap_pos(double x, double L) {
     if (x >= 0.0 && x < L) return x;
-    double w = __dsub_rn(x, __dmul_rn(L, floor(__ddiv_rn(x, L))));
+    double q = (double)floorf(__fdiv_rn((float)x, (float)L));
+    double w = __dsub_rn(x, __dmul_rn(L, q));
+    if (w < 0.0) {
+        q -= 1.0;
+        w = __dsub_rn(x, __dmul_rn(L, q));
+    } else if (w >= L) {
+        q += 1.0;
+        w = __dsub_rn(x, __dmul_rn(L, q));
+    }
     if (w >= L || w < 0.0) w = 0.0;
     return w;
 }
@@ -401,13 +414,18 @@ __device__ __forceinline__ void k_bin_count_body(Geo g, int N, const R* __restri
     if (threadIdx.x == 0) scount = 0;
     __syncthreads();
     const int b = blk.id, lane = threadIdx.x & 31;
-    const int i0 = b * g.chunk;
-    const int i1 = min(N, i0 + g.chunk);
+    const int i0 = b * g.chunk;   // the block's region of the compacted arrays
     double s1 = 0.0, s2 = 0.0;
-    for (int ib = i0; ib < i0 + g.chunk; ib += blockDim.x) {
-        const int i = ib + threadIdx.x;
+    // the beads, in groups of 32 consecutive ones (one warp's coalesced load),
+    // are dealt to the blocks round robin: charged beads that sit together in
+    // the input order (chains, counterions, salt) are spread over all blocks
+    // (at most chunk / 32 groups per block: chunk is a multiple of 32)
+    const int nwarp = blockDim.x >> 5, warp = threadIdx.x >> 5;
+    const int ngroups = (N + 31) >> 5;
+    for (int gi = b + warp * (int)blk.n; gi < ngroups; gi += nwarp * (int)blk.n) {
+        const int i = gi * 32 + lane;
         R qi = (R)0;
-        if (i < i1) {
+        if (i < N) {
             qi = q[i];
             if (Fzero) {
                 Fzero[3 * i] = (R)0;
