@@ -114,9 +114,9 @@ typedef struct {
     int    pairs;     /* DPD systems: 1 = two launches, the DPD pairs right after the
                          cell list (before the charged-bead binning is done), then the
                          real-space pairs; 2 = one launch whose blocks take either role,
-                         after both cell structures exist. Automatic (0): 1 in FP32, 2 in
-                         FP64 (measured at the 81000-bead polyelectrolyte, interleaved:
-                         FP32 152.9 against 155.3 us, FP64 471 against 508 us per step).
+                         after both cell structures exist. Automatic (0): 2 in FP32, 1 in
+                         FP64 (measured at the 81000-bead polyelectrolyte, interleaved
+                         steps: FP32 131.0 against 139.4 us, FP64 449.0 against 453.4 us).
                          Same result to rounding. */
 } enuf_params;
 

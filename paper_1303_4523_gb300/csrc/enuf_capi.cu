@@ -908,8 +908,8 @@ enuf_status enuf_plan(const enuf_params* params, int n_max, void* cuda_stream, e
 }
 
 // DPD pair launches of a plan: 1 (two launches) or 2 (one launch); automatic:
-// two in FP32, one in FP64 (measured at the 81000-bead polyelectrolyte)
-static int pair_launches(const enuf_params& P) { return P.pairs ? P.pairs : (P.prec == ENUF_FP32 ? 1 : 2); }
+// one in FP32, two in FP64 (measured at the 81000-bead polyelectrolyte)
+static int pair_launches(const enuf_params& P) { return P.pairs ? P.pairs : (P.prec == ENUF_FP32 ? 2 : 1); }
 
 static void fill_info(const enuf_plan_s* plan, enuf_plan_info* info) {
     info->M = plan->P.M;
