@@ -265,9 +265,12 @@ inline void enqueue_spread_sc(const Geo& g, const FftShape& fs, const Work& w, c
 
 // The same passes on the two-factor kernels (FP32 grids with n = f1 f2); with
 // the spreading fused with the x pass (spread = 3) the x pass is already done.
+// evZ (or nullptr) is recorded right after the z pass, whose blocks write the
+// reciprocal energy and virial partials (the kernel after it then launches
+// without programmatic dependent launch: its stream predecessor is the record).
 template <typename R>
 void enqueue_fft2(const Geo& g, const FftShape& fs, const FftPlanDev& fp, const Work& w, cudaStream_t s0, bool pdl,
-                  LaunchLog* log) {
+                  LaunchLog* log, cudaEvent_t evZ) {
     using C = typename Cx<R>::T;
     const C* tw = static_cast<const C*>(w.tw);
     if (fs.fused) {
@@ -276,8 +279,9 @@ void enqueue_fft2(const Geo& g, const FftShape& fs, const FftPlanDev& fp, const 
         launch(pdl, true, k2_fft_z<R>, fs.grid_z, fs.tz, fs.smem_z, s0, g, fp, static_cast<const C*>(w.spec2), tw,
                (const double*)w.tab, (const double*)w.tabv, static_cast<const R*>(w.tabr), static_cast<C*>(w.spec3),
                w.part + w.off_recip, fs.lz, 1);
-        launch(pdl, true, k2_fft_yx<R>, g.nf * g.n, fs.t_yx, fs.smem_yx, s0, g, fp, static_cast<const C*>(w.spec3),
-               tw, static_cast<R*>(w.h));
+        if (evZ) cudaEventRecord(evZ, s0);
+        launch(pdl && !evZ, true, k2_fft_yx<R>, g.nf * g.n, fs.t_yx, fs.smem_yx, s0, g, fp,
+               static_cast<const C*>(w.spec3), tw, static_cast<R*>(w.h));
         log->kernels += 4;
     } else {
         if (fs.spread != 3) {
@@ -290,8 +294,9 @@ void enqueue_fft2(const Geo& g, const FftShape& fs, const FftPlanDev& fp, const 
         launch(pdl, true, k2_fft_zp<R>, fs.grid_z, fs.tz, fs.smem_z, s0, g, fp, static_cast<const C*>(w.spec2), tw,
                (const double*)w.tab, (const double*)w.tabv, static_cast<const R*>(w.tabr), static_cast<C*>(w.spec3),
                w.part + w.off_recip, fs.lz);
-        launch(pdl, true, k2_fft_iy<R>, fs.grid_iy, fs.tiy, fs.smem_iy, s0, g, fp, static_cast<const C*>(w.spec3),
-               tw, static_cast<C*>(w.spec4), fs.liy);
+        if (evZ) cudaEventRecord(evZ, s0);
+        launch(pdl && !evZ, true, k2_fft_iy<R>, fs.grid_iy, fs.tiy, fs.smem_iy, s0, g, fp,
+               static_cast<const C*>(w.spec3), tw, static_cast<C*>(w.spec4), fs.liy);
         launch(pdl, true, k2_fft_ix<R>, fs.grid_ix, fs.tix, fs.smem_ix, s0, g, fp, static_cast<const C*>(w.spec4),
                tw, static_cast<R*>(w.h), fs.lix);
         log->kernels += 5;   // the spreading kernel and four passes
@@ -300,7 +305,7 @@ void enqueue_fft2(const Geo& g, const FftShape& fs, const FftPlanDev& fp, const 
 
 template <typename R, bool CR>
 void enqueue_fft(const Geo& g, const FftShape& fs, const FftPlanDev& fp, const Work& w, cudaStream_t s0, bool pdl,
-                 LaunchLog* log) {
+                 LaunchLog* log, cudaEvent_t evZ) {
     using C = typename Cx<R>::T;
     const C* tw = static_cast<const C*>(w.tw);
     if (fs.fused) {   // whole z-planes in shared memory: x+y, z (+convolve), y+x
@@ -309,8 +314,9 @@ void enqueue_fft(const Geo& g, const FftShape& fs, const FftPlanDev& fp, const W
         launch(pdl, true, k_fft_z<R, CR>, fs.grid_z, fs.tz, fs.smem_z, s0, g, fp, static_cast<const C*>(w.spec2),
                tw, (const double*)w.tab, (const double*)w.tabv, static_cast<const R*>(w.tabr),
                static_cast<C*>(w.spec3), w.part + w.off_recip, fs.lz, 1);
-        launch(pdl, true, k_fft_yx<R, CR>, g.nf * g.n, fs.t_yx, fs.smem_yx, s0, g, fp, static_cast<const C*>(w.spec3),
-               tw, static_cast<R*>(w.h));
+        if (evZ) cudaEventRecord(evZ, s0);
+        launch(pdl && !evZ, true, k_fft_yx<R, CR>, g.nf * g.n, fs.t_yx, fs.smem_yx, s0, g, fp,
+               static_cast<const C*>(w.spec3), tw, static_cast<R*>(w.h));
         log->kernels += 4;
     } else {
         launch(pdl, true, k_fft_x<R, CR>, fs.grid_x, fs.tx, fs.smem_x, s0, g, fp, static_cast<const R*>(w.grid),
@@ -320,8 +326,9 @@ void enqueue_fft(const Geo& g, const FftShape& fs, const FftPlanDev& fp, const W
         launch(pdl, true, k_fft_z<R, CR>, fs.grid_z, fs.tz, fs.smem_z, s0, g, fp, static_cast<const C*>(w.spec2),
                tw, (const double*)w.tab, (const double*)w.tabv, static_cast<const R*>(w.tabr),
                static_cast<C*>(w.spec3), w.part + w.off_recip, fs.lz, 0);
-        launch(pdl, true, k_fft_iy<R, CR>, fs.grid_iy, fs.tiy, fs.smem_iy, s0, g, fp, static_cast<const C*>(w.spec3),
-               tw, static_cast<C*>(w.spec4), fs.liy);
+        if (evZ) cudaEventRecord(evZ, s0);
+        launch(pdl && !evZ, true, k_fft_iy<R, CR>, fs.grid_iy, fs.tiy, fs.smem_iy, s0, g, fp,
+               static_cast<const C*>(w.spec3), tw, static_cast<C*>(w.spec4), fs.liy);
         launch(pdl, true, k_fft_ix<R, CR>, fs.grid_ix, fs.tix, fs.smem_ix, s0, g, fp, static_cast<const C*>(w.spec4),
                tw, static_cast<R*>(w.h), fs.lix);
         log->kernels += 6;
@@ -396,20 +403,22 @@ cudaError_t enqueue_enuf(const Geo& g, const FftShape& fs, const FftPlanDev& fp,
     }
     rec(ev, 1, false, s0);
     rec(ev, 2, true, s0);
+    // a DPD step records evZ after the z pass: the side stream then reduces the
+    // step's energies but the kinetic one while the last FFT pass and the gather run
+    const cudaEvent_t ez = evZ && evT ? evZ : nullptr;
     if constexpr (sizeof(R) == 4) {
         if (fs.two)
-            enqueue_fft2<R>(g, fs, fp, w, s0, pdl, log);
+            enqueue_fft2<R>(g, fs, fp, w, s0, pdl, log, ez);
         else if (fs.composite)
-            enqueue_fft<R, true>(g, fs, fp, w, s0, pdl, log);
+            enqueue_fft<R, true>(g, fs, fp, w, s0, pdl, log, ez);
         else
-            enqueue_fft<R, false>(g, fs, fp, w, s0, pdl, log);
+            enqueue_fft<R, false>(g, fs, fp, w, s0, pdl, log, ez);
     } else {
-        enqueue_fft<R, false>(g, fs, fp, w, s0, pdl, log);
+        enqueue_fft<R, false>(g, fs, fp, w, s0, pdl, log, ez);
     }
     rec(ev, 2, false, s0);
 
-    if (evZ && evT) {   // a DPD step: its energies but the kinetic one, beside the gather
-        cudaEventRecord(evZ, s0);
+    if (ez) {   // a DPD step: its energies but the kinetic one, beside the last pass and the gather
         cudaStreamWaitEvent(s1, evZ, 0);
         TotalsArgs t = totals_args(g, w, true, 0);
         t.pre = w.part + w.off_pre;
