@@ -186,7 +186,8 @@ enuf_status enuf_energy_forces(enuf_plan_t plan, int n, const void* pos, const v
  * synchronising: E = host double[8] laid out as dpd_step's E (the first four
  * entries are enuf_energy_forces' E), virial may be NULL. The caller must know
  * the work has finished (e.g. an event recorded after the call has completed);
- * every evaluation copies its totals to pinned host memory as its last step. */
+ * every evaluation copies its totals to pinned host memory as its last step;
+ * DPD steps copy theirs only when asked (dpd_copy_energies, or E given). */
 enuf_status enuf_last_energies(enuf_plan_t plan, double* E, double* virial);
 
 /* Same, with HOST pos, q and F: the call copies the inputs to the device,
@@ -281,6 +282,13 @@ enuf_status dpd_create(enuf_plan_t plan, const dpd_params* params, int n, const 
  *  dpd_create / dpd_set_state when no step has run since (nsteps = 0 reads
  *  them without stepping); synchronises when non-NULL. */
 enuf_status dpd_step(dpd_system_t sys, int nsteps, double* E);
+/* Stream-ordered copy of the energies of the last step (or force evaluation)
+ * of this system to the plan's pinned host buffer, read with
+ * enuf_last_energies once the work has completed. A step keeps its energies
+ * in device memory and copies them only when asked: by this call, or by
+ * dpd_step / dpd_step_host with E (each of which synchronises). Not in the
+ * paper (a host-interface detail). */
+enuf_status dpd_copy_energies(dpd_system_t sys);
 
 /* Checkpoint / restart: copy the state to or from HOST real[n][3] arrays
  * (any pointer may be NULL). The force F is part of the state because the

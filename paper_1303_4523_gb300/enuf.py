@@ -80,6 +80,7 @@ def _load():
         "enuf_last_error": (C.c_char_p, [vp]),
         "dpd_create": (st, [vp, C.POINTER(dpd_params), i, vp, vp, vp, vp, i, vp, C.POINTER(vp)]),
         "dpd_step": (st, [vp, i, pd]),
+        "dpd_copy_energies": (st, [vp]),
         "dpd_get_state": (st, [vp, vp, vp, vp, C.POINTER(C.c_uint64)]),
         "dpd_set_state": (st, [vp, vp, vp, vp, C.c_uint64]),
         "dpd_get_forces": (st, [vp, vp]),
@@ -110,7 +111,7 @@ EXPORTED = ("enuf_plan", "enuf_footprint", "enuf_get_info", "enuf_plan_shape", "
             "enuf_last_energies",
             "enuf_energy_forces_host", "enuf_debug_buffer", "enuf_enable_timing",
             "enuf_stage_time", "enuf_launches_per_eval", "enuf_destroy", "enuf_status_string",
-            "enuf_last_error", "dpd_create", "dpd_step", "dpd_get_state", "dpd_set_state",
+            "enuf_last_error", "dpd_create", "dpd_step", "dpd_copy_energies", "dpd_get_state", "dpd_set_state",
             "dpd_get_forces", "dpd_step_host", "dpd_device_state", "enuf_check_word",
             "enuf_built_with_checks", "enuf_debug_fail_allocs", "dpd_destroy", "enuf_batch_plan",
             "enuf_batch_energy_forces", "enuf_batch_launches", "enuf_batch_mode", "enuf_batch_destroy",
@@ -322,6 +323,11 @@ class DpdSystem:
         E = (C.c_double * 8)() if want_energy else None
         _check(lib.dpd_step(self.h, int(nsteps), E), self.plan.h)
         return np.array(E[:]) if want_energy else None
+
+    def copy_energies(self):
+        """Enqueue the copy of the last step's energies to the plan's host buffer
+        (read with Plan.last_energies() once the work has completed)."""
+        _check(lib.dpd_copy_energies(self.h), self.plan.h)
 
     def get_state(self):
         dt = self.plan.dtype_np

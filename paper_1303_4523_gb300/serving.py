@@ -279,6 +279,7 @@ class GpuBackend:
             ev.record(st)
             return (key, req, ev, hpos)
         ent["sys"].step(req.nsteps)
+        ent["sys"].copy_energies()   # a step keeps its energies on the device unless asked
         ev.record(st)
         return (key, req, ev, None)
 
