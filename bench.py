@@ -534,7 +534,8 @@ def run_batch(args):
             from paper_1303_4523_gb300 import autotune
             cache = autotune.TuneCache()
             t0 = time.perf_counter()
-            params = [autotune.tuned_params(p, s.N, a, c, cache=cache) for p, s, a, c in zip(params, systems, pos, q)]
+            params = [autotune.tuned_params(p, s.N, a, c, cache=cache, sequence=True)
+                      for p, s, a, c in zip(params, systems, pos, q)]
             out[prec + "_tune_s"] = round(time.perf_counter() - t0, 2)
             out[prec + "_tiles"] = sorted({p.tile for p in params})
         b = enuf.Batch(params, [s.N for s in systems])

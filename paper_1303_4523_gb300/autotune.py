@@ -30,6 +30,14 @@ cutoff in grid units and the charged-bead count (in powers of two).
     params = autotune.tuned_params(params, n_max, pos, q)   # device tensors
 
 The cache path is $ENUF_TUNE_CACHE, else ~/.cache/enuf_gb300/tune.json.
+
+For a batch (sequence=True) the FP32 candidates are restricted to the plans
+a batch can run as one launch sequence over all systems (two-factor fused
+FFT planes, the tile spreading form, a column-form tile edge): a faster
+single-system choice outside that set takes its system out of the sequence
+and costs the batch more than it saves (measured: the 64-system sweep tuned
+per system ran as 576 graph launches in 1.62 ms, against 1.33 ms for one
+sequence of 11 launches with the default tiles).
 """
 from __future__ import annotations
 
@@ -46,6 +54,7 @@ MAX_TILE = 24
 FUSED_FFT_MAX_N = 112
 COMPOSITE_MIN_N = 128
 CHOICES = ("tile", "fft_path", "fft_radix")
+SEQUENCE_TILES = (8, 10, 12, 16, 20, 24)   # the column spreading form's tile edges
 
 
 def default_cache_path() -> str:
@@ -79,10 +88,21 @@ def _shape(params: enuf.enuf_params, n_max: int):
     return info.tile, info.fft_kernels, info.fft_two_factor, tuple(info.fft_radix[:info.fft_stages])
 
 
-def candidates(params: enuf.enuf_params, n_max: int) -> list[dict]:
+def _sequence_ok(params: enuf.enuf_params, n_max: int) -> bool:
+    """Whether a batch can run this plan in its one launch sequence."""
+    try:
+        info = enuf.plan_shape(params, n_max)
+    except enuf.EnufError:
+        return False
+    return (params.prec == enuf.ENUF_FP32 and info.fft_two_factor == 1 and info.fft_kernels == 3
+            and info.spread == 1 and info.tile in SEQUENCE_TILES)
+
+
+def candidates(params: enuf.enuf_params, n_max: int, sequence: bool = False) -> list[dict]:
     """Every (tile, fft_path, fft_radix) the plan accepts for these
     parameters, one per distinct launch shape: the FFT choices only where
-    they select different kernels or radix schedules."""
+    they select different kernels or radix schedules. sequence: only those a
+    batch runs in its one launch sequence, where there are any."""
     n = grid_n(params)
     fp32 = params.prec == enuf.ENUF_FP32
     paths = [0, 1] if fp32 and n <= FUSED_FFT_MAX_N else [0]
@@ -98,16 +118,20 @@ def candidates(params: enuf.enuf_params, n_max: int) -> list[dict]:
                 if shape is not None and shape not in seen:
                     seen.add(shape)
                     out.append(c)
+    if sequence and fp32:
+        seq = [c for c in out if _sequence_ok(_copy(params, **c), n_max)]
+        if seq:
+            return seq
     return out
 
 
-def cache_key(params: enuf.enuf_params, n_charged: int, device: str = "") -> str:
+def cache_key(params: enuf.enuf_params, n_charged: int, device: str = "", sequence: bool = False) -> str:
     n = grid_n(params)
     rc_grid = params.r_cut * n / params.L
     qb = 0 if n_charged <= 0 else int(math.ceil(math.log2(n_charged)))
     prec = "fp32" if params.prec == enuf.ENUF_FP32 else "fp64"
     return (f"{device}|{prec}|deriv{params.deriv}|slater_k{params.slater_k}|kmask{params.kmask}"
-            f"|n{n}|p{params.p}|rc{round(rc_grid * 4) / 4:g}|q2^{qb}")
+            f"|n{n}|p{params.p}|rc{round(rc_grid * 4) / 4:g}|q2^{qb}" + ("|sequence" if sequence else ""))
 
 
 class TuneCache:
@@ -173,8 +197,10 @@ def _device_name() -> str:
 
 
 def tune(params: enuf.enuf_params, n_max: int, pos, q, measure: Callable | None = None,
-         cache: TuneCache | None = None, device: str | None = None, force: bool = False) -> dict:
-    """The fastest candidate for this system, from the cache when present.
+         cache: TuneCache | None = None, device: str | None = None, force: bool = False,
+         sequence: bool = False) -> dict:
+    """The fastest candidate for this system, from the cache when present
+    (sequence: among those a batch runs in its one launch sequence).
 
     measure(params, n_max, pos, q) -> ms replaces the device timing (tests
     pass a model of the cost). Returns {"tile", "fft_path", "fft_radix",
@@ -183,11 +209,11 @@ def tune(params: enuf.enuf_params, n_max: int, pos, q, measure: Callable | None 
     cache = cache if cache is not None else TuneCache()
     device = _device_name() if device is None else device
     n_charged = int((q != 0).sum())
-    key = cache_key(params, n_charged, device)
+    key = cache_key(params, n_charged, device, sequence)
     hit = None if force else cache.get(key)
     if hit is not None:
         return dict(hit, key=key, cached=True)
-    cands = candidates(params, n_max)
+    cands = candidates(params, n_max, sequence)
     if not cands:
         raise enuf.EnufError(enuf.ENUF_ERR_UNSUPPORTED, "no legal tile for these parameters")
     timings = []

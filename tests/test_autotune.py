@@ -197,3 +197,23 @@ def test_a_failing_candidate_is_skipped(mods, tmp_path):
 
     with pytest.raises(E.EnufError):
         A.tune(params, 1000, None, _q(), measure=broken, cache=A.TuneCache(str(tmp_path / "u.json")), device="dev")
+
+
+def test_batch_candidates_keep_the_launch_sequence(mods, tmp_path):
+    """For a batch (sequence=True) the FP32 candidates are the plans a batch runs in
+    its one launch sequence: two-factor fused FFT planes, the tile spreading form and
+    a column-form tile edge; FP64 batches (one graph branch per system) are unchanged."""
+    A, E = mods
+    p32 = E.make_params(prec="fp32", **BASE)
+    seq = A.candidates(p32, 81000, sequence=True)
+    assert seq and all(A._sequence_ok(A._copy(p32, **c), 81000) for c in seq)
+    assert sorted({c["tile"] for c in seq}) == [8, 12, 16, 24]
+    assert {(c["fft_path"], c["fft_radix"]) for c in seq} == {(0, 0)}
+    p64 = E.make_params(prec="fp64", **BASE)
+    assert A.candidates(p64, 81000, sequence=True) == A.candidates(p64, 81000)
+    # the cost model prefers tile 4 (outside the sequence); a batch tune picks among the rest
+    cache = A.TuneCache(str(tmp_path / "t.json"))
+    cost = lambda prm, n, pos, q: float(prm.tile)   # noqa: E731
+    single = A.tune(p32, 81000, None, _q(), measure=cost, cache=cache, device="dev")
+    batch = A.tune(p32, 81000, None, _q(), measure=cost, cache=cache, device="dev", sequence=True)
+    assert single["tile"] == 4 and batch["tile"] == 8 and single["key"] != batch["key"]
