@@ -145,3 +145,17 @@ def test_scatter_spread_admission(enuf):
             _shape(enuf, prec="fp32", **dict(base, **bad))
     with pytest.raises(enuf.EnufError):
         _shape(enuf, prec="fp64", **base)
+
+
+def test_pair_launch_form(enuf):
+    """enuf_params.pairs: 1 two launches, 2 one launch, 0 the measured automatic
+    form (one launch in FP32, two in FP64); anything else is rejected."""
+    kw = dict(L=30.0, alpha=0.975, r_cut=3.0, beta=4.0, kappa=1.1, M=48, p=4)
+    assert _shape(enuf, 81000, prec="fp32", **kw).pairs == 2
+    assert _shape(enuf, 81000, prec="fp64", **kw).pairs == 1
+    for prec in ("fp32", "fp64"):
+        for form in (1, 2):
+            assert _shape(enuf, 81000, prec=prec, pairs=form, **kw).pairs == form
+    for bad in (-1, 3):
+        with pytest.raises(enuf.EnufError):
+            _shape(enuf, 81000, prec="fp32", pairs=bad, **kw)
